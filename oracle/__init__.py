@@ -1,0 +1,215 @@
+"""CPU oracle of the sparse four-view matching stage -- TEST INFRASTRUCTURE.
+
+``sff_oracle.c`` states, in plain C loops, what the CUDA path must compute
+(SceneFlowFields Sec. 3.1-3.2).  Only tests, the smoke check and the
+benchmark's CPU-baseline leg may import this package; the product path never
+does.  It shares no code with the CUDA path.
+
+This module compiles the C file with gcc (``build()``) and marshals numpy
+arrays to it through ctypes.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sff_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+NF = 48
+EMPTY = np.iinfo(np.int32).max
+
+
+class Params(ctypes.Structure):
+    """Method parameters (Sec. 5 values plus the stated readings)."""
+    _fields_ = [("num_scales", ctypes.c_int32), ("iterations", ctypes.c_int32), ("tau_c", ctypes.c_int32),
+                ("region_min", ctypes.c_int32), ("tau_r", ctypes.c_int32), ("quant_shift", ctypes.c_int32),
+                ("knn_temporal", ctypes.c_int32), ("knn_epipolar", ctypes.c_int32)]
+
+
+def default_params(**over) -> Params:
+    p = dict(num_scales=4, iterations=12, tau_c=1, region_min=150, tau_r=1, quant_shift=4,
+             knn_temporal=4, knn_epipolar=2)
+    p.update(over)
+    return Params(**p)
+
+
+SEED_DTYPE = np.dtype([("x", "<i2"), ("y", "<i2"), ("u", "<i2"), ("v", "<i2"), ("d0", "<i2"), ("d1", "<i2"),
+                       ("cost", "<i4"), ("cerr", "u1"), ("pad", "u1", (3,))])
+assert SEED_DTYPE.itemsize == 20
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into oracle/liboracle.so (gcc, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11", _SRC, "-o", tmp])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        P = ctypes.c_void_p
+        i32 = ctypes.c_int32
+        L.sffo_features.argtypes = [P, i32, i32, ctypes.POINTER(Params), P, P]
+        L.sffo_smooth.argtypes = [P, i32, i32, i32, P]
+        L.sffo_match_views.argtypes = [P, P, P, P, i32, i32, i32, ctypes.c_uint64, ctypes.POINTER(Params), P, P]
+        L.sffo_consistency_check.argtypes = [P, P, P, P, i32, i32, ctypes.POINTER(Params), P, P]
+        L.sffo_region_filter.argtypes = [P, P, i32, i32, ctypes.POINTER(Params), P]
+        L.sffo_consistency_filter.argtypes = [P, P, P, P, i32, i32, ctypes.POINTER(Params), P, P]
+        L.sffo_emit_seeds.argtypes = [P, P, P, P, i32, i32, P, i32]
+        L.sffo_emit_seeds.restype = i32
+        L.sffo_philox4x32_10.argtypes = [P, P, P]
+        L.sffo_rs_offset.argtypes = [ctypes.c_uint32, i32]
+        L.sffo_rs_offset.restype = i32
+        L.sffo_wht8x8.argtypes = [P, P]
+        L.sffo_walsh_matrix.argtypes = [P]
+        L.sffo_coef_order.argtypes = [P, P]
+        L.sffo_cost.argtypes = [P, P, P, P, i32, i32, i32, i32, i32, P]
+        L.sffo_cost.restype = i32
+        L.sffo_set_threads.argtypes = [i32]
+        L.sffo_get_threads.restype = i32
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def set_threads(n: int) -> None:
+    lib().sffo_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return lib().sffo_get_threads()
+
+
+def smooth(img: np.ndarray, s: int) -> np.ndarray:
+    img = np.ascontiguousarray(img, np.uint8)
+    h, w, _ = img.shape
+    out = np.empty_like(img)
+    lib().sffo_smooth(_p(img), w, h, s, _p(out))
+    return out
+
+
+def features(img: np.ndarray, params: Params = None):
+    """Features of one RGB uint8 image: (feat [S,H,W,48] int8, norm [S,H,W] int32)."""
+    params = params or default_params()
+    img = np.ascontiguousarray(img, np.uint8)
+    h, w, _ = img.shape
+    S = params.num_scales
+    feat = np.empty((S, h, w, NF), np.int8)
+    norm = np.empty((S, h, w), np.int32)
+    lib().sffo_features(_p(img), w, h, ctypes.byref(params), _p(feat), _p(norm))
+    return feat, norm
+
+
+def match_views(f_ref, f_tmp, f_ste, f_crs, mirror: int, seed: int, params: Params = None):
+    params = params or default_params()
+    S, h, w, _ = f_ref.shape
+    field = np.empty((h, w, 4), np.int16)
+    cost = np.empty((h, w), np.int32)
+    lib().sffo_match_views(_p(f_ref), _p(f_tmp), _p(f_ste), _p(f_crs), w, h, int(mirror), int(seed) & (2**64 - 1),
+                           ctypes.byref(params), _p(field), _p(cost))
+    return field, cost
+
+
+def consistency_check(fwd, fwd_cost, inv, inv_cost, params: Params = None):
+    params = params or default_params()
+    h, w, _ = fwd.shape
+    keep = np.empty((h, w), np.uint8)
+    cerr = np.empty((h, w), np.uint8)
+    lib().sffo_consistency_check(_p(fwd), _p(fwd_cost), _p(inv), _p(inv_cost), w, h, ctypes.byref(params),
+                                 _p(keep), _p(cerr))
+    return keep, cerr
+
+
+def region_filter(fwd, fwd_cost, keep, params: Params = None):
+    params = params or default_params()
+    h, w, _ = fwd.shape
+    keep = np.ascontiguousarray(keep, np.uint8).copy()
+    lib().sffo_region_filter(_p(fwd), _p(fwd_cost), w, h, ctypes.byref(params), _p(keep))
+    return keep
+
+
+def consistency_filter(fwd, fwd_cost, inv, inv_cost, params: Params = None):
+    params = params or default_params()
+    h, w, _ = fwd.shape
+    keep = np.empty((h, w), np.uint8)
+    cerr = np.empty((h, w), np.uint8)
+    lib().sffo_consistency_filter(_p(fwd), _p(fwd_cost), _p(inv), _p(inv_cost), w, h, ctypes.byref(params),
+                                  _p(keep), _p(cerr))
+    return keep, cerr
+
+
+def emit_seeds(fwd, fwd_cost, keep, cerr):
+    h, w, _ = fwd.shape
+    cap = ((w + 2) // 3) * ((h + 2) // 3)
+    out = np.zeros(cap, SEED_DTYPE)
+    n = lib().sffo_emit_seeds(_p(fwd), _p(fwd_cost), _p(keep), _p(cerr), w, h, _p(out), cap)
+    return out[:n]
+
+
+def philox4x32_10(ctr, key):
+    c = np.ascontiguousarray(ctr, np.uint32)
+    k = np.ascontiguousarray(key, np.uint32)
+    out = np.empty(4, np.uint32)
+    lib().sffo_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def rs_offset(r: int, n: int) -> int:
+    return lib().sffo_rs_offset(ctypes.c_uint32(r), n)
+
+
+def wht8x8(patch) -> np.ndarray:
+    p = np.ascontiguousarray(patch, np.int32).reshape(8, 8)
+    out = np.empty((8, 8), np.int32)
+    lib().sffo_wht8x8(_p(p), _p(out))
+    return out
+
+
+def walsh_matrix() -> np.ndarray:
+    out = np.empty((8, 8), np.int32)
+    lib().sffo_walsh_matrix(_p(out))
+    return out
+
+
+def coef_order():
+    ky = np.empty(16, np.int32)
+    kx = np.empty(16, np.int32)
+    lib().sffo_coef_order(_p(ky), _p(kx))
+    return ky, kx
+
+
+def cost(f_ref, f_tmp, f_ste, f_crs, mirror, px, py, u):
+    """Cost of vector u at pixel (px, py); features of ONE scale, [H,W,48]."""
+    h, w, _ = f_ref.shape
+    uu = np.ascontiguousarray(u, np.int16)
+    return lib().sffo_cost(_p(f_ref), _p(f_tmp), _p(f_ste), _p(f_crs), w, h, int(mirror), px, py, _p(uu))
+
+
+def run_quad(L0, R0, L1, R1, seed: int, params: Params = None):
+    """The whole stage on one quad: features, forward and inverse fields,
+    consistency + region filter, seeds.  Returns a dict of numpy arrays."""
+    params = params or default_params()
+    fL0, nL0 = features(L0, params)
+    fR0, nR0 = features(R0, params)
+    fL1, nL1 = features(L1, params)
+    fR1, nR1 = features(R1, params)
+    fwd, fwd_cost = match_views(fL0, fL1, fR0, fR1, 0, seed, params)
+    inv, inv_cost = match_views(fR1, fR0, fL1, fL0, 1, seed, params)
+    keep, cerr = consistency_filter(fwd, fwd_cost, inv, inv_cost, params)
+    seeds = emit_seeds(fwd, fwd_cost, keep, cerr)
+    return dict(feat=(fL0, fR0, fL1, fR1), norm=(nL0, nR0, nL1, nR1), fwd=fwd, fwd_cost=fwd_cost, inv=inv,
+                inv_cost=inv_cost, keep=keep, cerr=cerr, seeds=seeds)

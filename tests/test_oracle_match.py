@@ -1,0 +1,157 @@
+"""Pins of the oracle's initialisation and propagation (Sec. 3.1).
+
+Propagation with random search is a heuristic without a closed-form result,
+so it is pinned by what must hold for any correct implementation:
+  - exhaustive nearest-neighbour initialisation on tiny images;
+  - every final cost is the true cost of the final vector and is bounded
+    below by the exhaustive minimum over all vectors;
+  - costs never increase from one iteration to the next;
+  - exact recovery of integer shifts and ground-truth recovery on a
+    rendered scene;
+  - results do not depend on the number of threads.
+"""
+import numpy as np
+import pytest
+
+import scenegen
+
+EMPTY = np.iinfo(np.int32).max
+
+
+def _feats(orc, imgs, params):
+    return [orc.features(im, params)[0] for im in imgs]
+
+
+def _ssd(a, b):
+    d = a.astype(np.int64) - b.astype(np.int64)
+    return (d * d).sum(-1)
+
+
+def test_init_exhaustive(orc):
+    # 16x16 image, scales {0, 1}: the coarsest grid G_1 has 64 points; with
+    # K_T = 64 every temporal point is a leaf, so the initial vector is the
+    # exhaustive argmin of the cost with ties resolved by leaf rank.
+    imgs = scenegen.random_images(16, 16, 21)
+    p = orc.default_params(num_scales=2, iterations=0, knn_temporal=64, knn_epipolar=2)
+    Fall = _feats(orc, imgs, p)  # images L0, R0, L1, R1
+    for mirror in (0, 1):
+        sg = -1 if mirror else 1
+        roles = (0, 2, 1, 3) if not mirror else (3, 1, 2, 0)  # ref, temporal, stereo, cross
+        fld, cost = orc.match_views(*(Fall[i] for i in roles), mirror, 1, p)
+        ref, tmp, ste, crs = (Fall[i][1] for i in roles)  # scale-1 features
+        grid = [(x, y) for y in range(0, 16, 2) for x in range(0, 16, 2)]
+        for (px, py) in grid:
+            a = ref[py, px]
+            best = None
+            for (tx, ty) in grid:
+                dT = int(_ssd(a, tmp[ty, tx]))
+                for sx in range(0, 16, 2):
+                    if sg * (px - sx) < 0:
+                        continue
+                    dS = int(_ssd(a, ste[py, sx]))
+                    for cx in range(0, 16, 2):
+                        if sg * (tx - cx) < 0:
+                            continue
+                        dX = int(_ssd(a, crs[ty, cx]))
+                        key = (dT + dS + dX, dT, ty * 16 + tx, dS, py * 16 + sx, dX, ty * 16 + cx)
+                        vec = (tx - px, ty - py, sg * (px - sx), sg * (tx - cx))
+                        if best is None or key < best[0]:
+                            best = (key, vec)
+            assert tuple(int(v) for v in fld[py, px]) == best[1], (mirror, px, py)
+        # non-grid points of the finest scale stay empty without iterations
+        assert (cost[1::2, :] == EMPTY).all() and (cost[:, 1::2] == EMPTY).all()
+
+
+def test_init_knn_leaves(orc):
+    # with K_T = 4 the chosen temporal match is one of the 4 nearest grid points
+    imgs = scenegen.random_images(40, 24, 22)
+    p = orc.default_params(num_scales=2, iterations=0)
+    F = _feats(orc, imgs, p)
+    fld, _ = orc.match_views(F[0], F[2], F[1], F[3], 0, 1, p)
+    ref, tmp = F[0][1], F[2][1]
+    gy, gx = np.mgrid[0:24:2, 0:40:2]
+    for py in range(0, 24, 2):
+        for px in range(0, 40, 2):
+            d = _ssd(ref[py, px][None, None], tmp[0:24:2, 0:40:2])
+            order = sorted(zip(d.ravel().tolist(), (gy * 40 + gx).ravel().tolist()))[:4]
+            t = (py + int(fld[py, px, 1])) * 40 + px + int(fld[py, px, 0])
+            assert t in [i for _, i in order]
+
+
+def test_costs_are_true_costs_and_bounded_below(orc):
+    imgs = scenegen.random_images(20, 14, 23)
+    p = orc.default_params(num_scales=1, iterations=12)
+    F = _feats(orc, imgs, p)
+    fld, cost = orc.match_views(F[0], F[2], F[1], F[3], 0, 77, p)
+    ref, ste, tmp, crs = (f[0] for f in F)
+    h, w = 14, 20
+    hits = 0
+    for py in range(h):
+        for px in range(w):
+            c = int(cost[py, px])
+            assert c != EMPTY
+            assert c == orc.cost(ref, tmp, ste, crs, 0, px, py, fld[py, px])
+            a = ref[py, px]
+            dS = min(int(_ssd(a, ste[py, sx])) for sx in range(0, px + 1))
+            dTX = min(int(_ssd(a, tmp[ty, tx])) + min(int(_ssd(a, crs[ty, cx])) for cx in range(0, tx + 1))
+                      for ty in range(h) for tx in range(w))
+            assert c >= dS + dTX
+            hits += c == dS + dTX
+    assert hits > 0
+
+
+def test_monotone_over_iterations(orc):
+    imgs = scenegen.random_images(48, 32, 24)
+    prev = None
+    for it in range(0, 9):
+        p = orc.default_params(num_scales=1, iterations=it, knn_temporal=4)
+        F = _feats(orc, imgs, p)
+        _, cost = orc.match_views(F[0], F[2], F[1], F[3], 0, 5, p)
+        if prev is not None:
+            assert (cost.astype(np.int64) <= prev).all()
+        prev = cost.astype(np.int64)
+
+
+def test_threads_do_not_change_results(orc):
+    q = scenegen.make_named("planes_256x80", 3)
+    before = orc.get_threads()
+    try:
+        orc.set_threads(1)
+        r1 = orc.run_quad(*q.images(), seed=99)
+        orc.set_threads(4)
+        r4 = orc.run_quad(*q.images(), seed=99)
+    finally:
+        orc.set_threads(before)
+    for k in ("fwd", "fwd_cost", "inv", "inv_cost", "keep", "cerr"):
+        assert np.array_equal(r1[k], r4[k]), k
+    assert np.array_equal(r1["seeds"], r4["seeds"])
+
+
+@pytest.mark.parametrize("uvdd", [(3, -2, 5, 4), (-6, 3, 2, 9), (11, 0, 14, 12)])
+def test_exact_recovery_of_integer_shifts(orc, uvdd):
+    u, v, d0, d1 = uvdd
+    q = scenegen.make_shift_quad(160, 96, 31, u=u, v=v, d0=d0, d1=d1)
+    r = orc.run_quad(*q.images(), seed=3)
+    fwd = r["fwd"].astype(np.int64)
+    m = 40
+    interior = fwd[m:-m, m:-m]
+    assert (interior == np.array(uvdd)).all()
+    # inverse field recovers the true inverse vector
+    iu = np.array([-(u - d1 + d0), -v, d1, d0])
+    assert (r["inv"].astype(np.int64)[m:-m, m:-m] == iu).all()
+    # the interior is kept by the filter and its seeds are exact
+    assert r["keep"][m:-m, m:-m].all()
+    sd = r["seeds"]
+    inner = (sd["x"] >= m) & (sd["x"] < 160 - m) & (sd["y"] >= m) & (sd["y"] < 96 - m)
+    assert inner.sum() > 0
+    assert (sd["u"][inner] == u).all() and (sd["d1"][inner] == d1).all()
+
+
+def test_ground_truth_recovery_planes(orc):
+    q = scenegen.make_named("planes_256x80", 1)
+    r = orc.run_quad(*q.images(), seed=1234)
+    vis = ~q.occluded
+    keep = r["keep"].astype(bool) & vis
+    err = np.abs(r["fwd"].astype(np.float64) - q.gt).max(-1)
+    assert keep.sum() / vis.sum() > 0.8        # density of kept matches
+    assert (err[keep] > 3).mean() < 0.03       # outliers among kept matches
