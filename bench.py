@@ -1,0 +1,351 @@
+"""Benchmark of the four-view matching stage (features, forward and inverse
+fields, consistency/region filter, seeds) on one 1242x375 driving-shaped
+quad per GPU.
+
+Metric: matched pixels per second = W*H of the reference image L0 per step,
+divided by the step time, summed over ranks (weak scaling: every rank matches
+its own quad; no data-path collective).
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sff|reference]
+
+--impl reference times the CPU oracle (the plain C statement of the method)
+on the host cores, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import scenegen  # noqa: E402
+
+WORKLOAD = "driving_1242x375"
+SCENE_SEED = 2
+MATCH_SEED = 2024
+METRIC = "4-view matched px/s per GB300 (bit-exact), batched vs plain; serving p50/p99 ms"
+L2_FLUSH_BYTES = 256 << 20
+FALLBACK_HBM_GBS = 6800.0
+
+# Algorithmic bytes per unit of work of each kernel (units in `_units`):
+#   k_half_step   per active grid pixel: own + written state 24 B, reference
+#                 record 64 B, one 64 B target record per view (3 views)
+#   k_features    per pixel and scale: packed smoothed pixel 4 B in, 64 B record out
+#   k_smooth      per pixel: 3 B in, 4 B out per scale
+ALGO_BYTES = {"k_half_step": 24 + 64 + 3 * 64, "k_features": 4 + 64}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="sff", choices=["sff", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self._t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    v = d[k]
+                    return float(v["value"] if isinstance(v, dict) else v), "measured"
+        except (ValueError, KeyError, TypeError):
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from profiles/dram_traffic.txt, or None
+    when missing or taken on a different version of the kernel's source."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    for line in open(p):
+        f = line.split()
+        if len(f) >= 4 and f[0] == kernel and not line.startswith("#"):
+            src = os.path.join(ROOT, "paper_1710_10096_gb300", "csrc", f[3])
+            if os.path.exists(src) and hashlib.sha1(open(src, "rb").read()).hexdigest()[:12] == f[2]:
+                return float(f[1])
+    return None
+
+
+def _units(kernel: str, w: int, h: int, params) -> float:
+    """Units of work of `kernel` in one step (summed over its launches)."""
+    S, I = params.num_scales, params.iterations
+    if kernel == "k_half_step":
+        # 2 fields x per scale: I iterations x 2 colours cover every grid pixel once per iteration
+        total = 0
+        for s in range(S):
+            n = 1 << s
+            total += ((w + n - 1) // n) * ((h + n - 1) // n) * I
+        return 2.0 * total
+    if kernel == "k_features":
+        return 4.0 * S * w * h
+    return 0.0
+
+
+def cpu_baseline(q, seed, target_s=12.0):
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    px = q.width * q.height
+    times, ref = [], None
+    t_all = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        ref = oracle.run_quad(*q.images(), seed=seed)
+        times.append(time.perf_counter() - t0)
+        if time.perf_counter() - t_all > target_s or len(times) >= 8:
+            break
+    return {"value": px / statistics.mean(times), "unit": "px/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(times)} full {q.width}x{q.height} quads (features, both fields, filter, seeds), "
+                      f"{cores} OpenMP threads, {statistics.mean(times):.2f} s each"}, ref
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    q = scenegen.make_named(WORKLOAD, SCENE_SEED)
+    # calibrate on one warm-up; shrink each step to a band of rows if the whole
+    # run would exceed about two minutes
+    t0 = time.perf_counter()
+    oracle.run_quad(*q.images(), seed=MATCH_SEED)
+    t_full = time.perf_counter() - t0
+    rows = q.height
+    budget = 120.0
+    if (args.steps + args.warmup) * t_full > budget:
+        rows = max(48, int(q.height * budget / ((args.steps + args.warmup) * t_full)))
+    imgs = [im[:rows].copy() for im in q.images()]
+    for _ in range(max(0, args.warmup - 1)):
+        oracle.run_quad(*imgs, seed=MATCH_SEED)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.run_quad(*imgs, seed=MATCH_SEED)
+        times.append(time.perf_counter() - t0)
+    px = q.width * rows
+    value = px / statistics.mean(times)
+    sample = (f"{'full quad' if rows == q.height else f'band of the first {rows} rows of'} {q.width}x{q.height} "
+              f"per step, {cores} OpenMP threads")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "px/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "width": q.width, "height": rows, "quads_per_step": 1},
+            "cpu_baseline": {"value": value, "unit": "px/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "px/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import paper_1710_10096_gb300 as sff
+
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sff.build()
+
+    q = scenegen.make_named(WORKLOAD, SCENE_SEED + rank)
+    params = sff.default_params()
+    m = sff.QuadMatcher(q.width, q.height, params, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    host_in = torch.empty((4, q.height, q.width, 3), dtype=torch.uint8).pin_memory()
+    for k, im in enumerate(q.images()):
+        host_in[k].copy_(torch.as_tensor(im))
+    dev_in = host_in.to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    # plain launches first (warm-up, and the per-kernel profile of one step)
+    with torch.cuda.stream(stream):
+        for _ in range(max(1, args.warmup)):
+            m.run(*dev_in.unbind(0), seed=MATCH_SEED, stream=stream)
+        stream.synchronize()
+        sff.profile_enable(True)
+        prof_steps = max(3, min(args.steps, 10))
+        for _ in range(prof_steps):
+            flush.zero_()
+            m.run(*dev_in.unbind(0), seed=MATCH_SEED, stream=stream)
+        stream.synchronize()
+        prof = sff.profile_collect()
+        sff.profile_enable(False)
+
+    # the timed region: CUDA-graph replays of the whole stage on resident inputs
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        m.run(*dev_in.unbind(0), seed=MATCH_SEED, stream=stream)
+        stream.synchronize()
+        with torch.cuda.graph(graph, stream=stream):
+            m.run(*dev_in.unbind(0), seed=MATCH_SEED, stream=torch.cuda.current_stream())
+        for _ in range(args.warmup):
+            graph.replay()
+        stream.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    torch.cuda.synchronize(dev)
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.zero_()  # L2 flush, outside the step's events
+            ev[k][0].record(stream)
+            graph.replay()
+            ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_step = statistics.mean(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([t_step], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_step = float(t.item())
+    px = q.width * q.height
+    value = px * world / t_step
+
+    # end to end through the public host API: pinned host images in, seeds out
+    e2e_times = []
+    with torch.cuda.stream(stream):
+        for k in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            dev_in.copy_(host_in, non_blocking=True)
+            graph.replay()
+            host_seeds = m.seeds.to("cpu", non_blocking=True)
+            host_count = m.count.to("cpu", non_blocking=True)
+            stream.synchronize()
+            if k >= args.warmup:
+                e2e_times.append(time.perf_counter() - t0)
+    n_seeds = int(host_count.item())
+    e2e = {"value": px * world / statistics.mean(e2e_times), "unit": "px/s",
+           "h2d_bytes_per_step": int(host_in.numel()), "d2h_bytes_per_step": int(m.seeds.numel() + 4)}
+
+    # roofline of the dominant kernel (largest share of profiled time)
+    launches_per_step = sum(v[0] for v in prof.values()) / prof_steps
+    dom = max(prof, key=lambda k: prof[k][1])
+    dom_launches, dom_ms = prof[dom]
+    peak, peak_src = measured_peak_hbm()
+    roof = None
+    if dom in ALGO_BYTES:
+        units = _units(dom, q.width, q.height, params) * prof_steps
+        bytes_per_launch = ALGO_BYTES[dom] * units / dom_launches
+        achieved = bytes_per_launch / (dom_ms / dom_launches / 1e3) / 1e9
+        tr = ncu_traffic(dom)
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": tr, "peak_source": peak_src,
+                "algo_bytes_per_launch": bytes_per_launch, "avg_launch_us": 1e3 * dom_ms / dom_launches}
+    total_prof = sum(v[1] for v in prof.values())
+    kernels = {k: {"launches_per_step": v[0] / prof_steps, "ms_per_step": v[1] / prof_steps,
+                   "share": v[1] / total_prof} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+
+    line = {"metric": METRIC, "value": value, "unit": "px/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "width": q.width, "height": q.height, "quads_per_step": 1,
+                       "parallelism": f"replicas{world}", "cuda_graph": True,
+                       "l2": "flushed between timed steps (256 MB write outside the step events)",
+                       "params": params.as_dict(), "scene_seed": SCENE_SEED, "match_seed": MATCH_SEED},
+            "roofline": roof, "gpu_launches": int(round(launches_per_step * args.steps)),
+            "e2e": e2e, "clocks": clk, "kernels": kernels, "seeds": n_seeds}
+    if rank == 0 and not args.no_cpu_baseline:
+        cb, ref = cpu_baseline(q, MATCH_SEED)
+        line["cpu_baseline"] = cb
+        got = sff.seeds_to_numpy(host_seeds.numpy(), min(n_seeds, m.capacity))
+        line["bit_exact"] = bool(got.tobytes() == ref["seeds"].tobytes() and n_seeds == len(ref["seeds"])
+                                 and np.array_equal(m.fwd.cpu().numpy(), ref["fwd"])
+                                 and np.array_equal(m.inv.cpu().numpy(), ref["inv"]))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

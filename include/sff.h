@@ -1,0 +1,199 @@
+/*
+ * sff.h -- C ABI of the GB300 (sm_103a) implementation of SceneFlowFields'
+ * sparse four-view matching stage (Schuster, Wasenmueller, Kuschk, Bailer,
+ * Stricker, "SceneFlowFields: Dense Interpolation of Sparse Scene Flow
+ * Correspondences", WACV 2018).
+ *
+ * Problem statement (Sec. 3): two rectified stereo pairs L0 = I_l^0,
+ * R0 = I_r^0 (time t0) and L1 = I_l^1, R1 = I_r^1 (time t1).  For every pixel
+ * p of the reference view the stage estimates the scene flow vector
+ * u = (u, v, d0, d1): optical flow (u, v) to L1 and the disparities d0 (to R0)
+ * and d1 (L1 to R1), so that the three correspondences of Eq. 1 are
+ *     temporal  L1 at p + (u, v)
+ *     stereo    R0 at p + (-d0, 0)
+ *     cross     R1 at p + (u - d1, v).
+ * The four calls below are the four parts of Sec. 3.1-3.2:
+ *     sff_features            Walsh-Hadamard patch features on a scale space
+ *     sff_match_views         initialisation + multi-scale propagation + random search
+ *     sff_consistency_filter  forward/inverse consistency check + region filter
+ *     sff_emit_seeds          3x3 sparsification into seeds (Sec. 3.2)
+ *
+ * Conventions for every call:
+ *   - Pointers named *_dev, and every image/pyramid/field buffer, are DEVICE
+ *     pointers owned by the caller; the library never allocates, frees or
+ *     retains them.  `params` is a HOST pointer read during the call only.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  All work is
+ *     enqueued asynchronously on it; results are valid once the stream has
+ *     reached the point of the call.  No call synchronises the host.
+ *   - `workspace`/`workspace_bytes` is caller-owned device scratch of at
+ *     least sff_workspace_bytes() bytes, 256-byte aligned; its contents are
+ *     undefined between calls.  Calls that share one workspace must be
+ *     ordered (same stream or event-ordered).
+ *   - Images are W x H with 8 <= W, H and W, H <= 16384; all four images of a
+ *     quad have the same size.  Rows of images are `pitch_bytes` apart,
+ *     pixels are 3 interleaved uint8 channels (RGB).
+ *   - Return value: SFF_OK (0) or a negative SFF_ERR_* code.  Argument errors
+ *     are detected on the host before anything is enqueued.  SFF_ERR_CUDA
+ *     reports a launch failure (cudaGetLastError()).
+ */
+#ifndef SFF_H
+#define SFF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SFF_OK 0
+#define SFF_ERR_ARG (-1)        /* invalid argument (null pointer, size, alignment, params) */
+#define SFF_ERR_CUDA (-2)       /* a CUDA launch or API call failed */
+#define SFF_ERR_WORKSPACE (-3)  /* workspace smaller than sff_workspace_bytes() */
+
+#define SFF_FEATURES 48         /* int8 features per pixel and scale: 3 channels x 16 */
+#define SFF_RECORD_BYTES 64     /* bytes per pixel and scale in a pyramid */
+#define SFF_MAX_SCALES 4
+#define SFF_MAX_KNN 8
+#define SFF_EMPTY_COST 2147483647 /* cost of a pixel that holds no vector yet */
+
+/* Method parameters.  Defaults (sff_default_params) are the paper's values
+ * (Sec. 5: k = 3 subscales, 12 iterations, tau_c = 1, s_c = 150) and the
+ * readings of the points the paper leaves open. */
+typedef struct sff_params {
+    int32_t num_scales;   /* k + 1 scales, stride 2^s at scale s; 1..4 (Sec. 3.1, Sec. 5: k = 3) */
+    int32_t iterations;   /* propagation + random-search iterations per scale; 0..64 (Sec. 5: 12) */
+    int32_t tau_c;        /* consistency threshold in px; 0..255 (Sec. 3.1, Sec. 5: 1) */
+    int32_t region_min;   /* minimum region size s_c; >= 0 (Sec. 3.1, Sec. 5: 150) */
+    int32_t tau_r;        /* region rule: max-norm vector difference <= tau_r; 0..255 (default 1) */
+    int32_t quant_shift;  /* feature quantisation: floor(coef / 2^quant_shift), 0..8 (default 4) */
+    int32_t knn_temporal; /* K_T nearest neighbours of the temporal search; 1..8 (default 4) */
+    int32_t knn_epipolar; /* K_E nearest neighbours per epipolar row; 1..8 (default 2) */
+} sff_params;
+
+/* One seed of Sec. 3.2: pixel (x, y) of L0, its vector and its scores. 20 bytes. */
+typedef struct sff_seed {
+    int16_t x, y, u, v, d0, d1;
+    int32_t cost;   /* matching cost at scale 0 */
+    uint8_t cerr;   /* consistency error: sum of |round-trip differences| */
+    uint8_t pad[3];
+} sff_seed;
+
+/* Fills *out with the default parameters.  Returns SFF_ERR_ARG if out is NULL. */
+int sff_default_params(sff_params* out);
+
+/* Bytes of one image's feature pyramid: num_scales * H * W * 64.
+ * Layout [scale][y][x] of 64-byte records: bytes 0..47 the int8 features
+ * (channel-major, 16 coefficients per channel in the order of sff_features),
+ * bytes 48..51 the int32 sum of squared features, bytes 52..63 zero.
+ * Returns 0 for invalid arguments. */
+size_t sff_pyramid_bytes(int32_t width, int32_t height, const sff_params* params);
+
+/* Device scratch needed by any call below for a W x H quad.  0 if invalid. */
+size_t sff_workspace_bytes(int32_t width, int32_t height, const sff_params* params);
+
+/* Walsh-Hadamard patch features of one image at every scale (Sec. 3.1,
+ * "Initialization": WHT features as in FlowFields; "Multi-Scale
+ * Propagation": scale s smooths the image and samples every n = 2^s-th
+ * pixel, all positions staying at full resolution).
+ *   Scale space: S_s = round-half-up mean of the n x n box with offsets
+ *   -n/2..n/2-1 around each pixel, edges replicated; S_0 = image.
+ *   Patch of pixel (x, y): P_c[i][j] = S_s(x + n(j-3), y + n(i-3))_c,
+ *   i, j = 0..7, coordinates clamped to the image (boundary replication).
+ *   Coefficients T_c = H P_c H^T with H the 8x8 Walsh matrix in sequency
+ *   order; the 16 AC coefficients (ky, kx) with the lowest ky+kx (ties: lower
+ *   ky) are kept per channel and quantised to clamp(floor(T / 2^quant_shift),
+ *   -128, 127).
+ * rgb_dev: W x H x 3 uint8, rows pitch_bytes apart (pitch >= 3W).
+ * pyramid_dev: sff_pyramid_bytes() bytes, 16-byte aligned; fully overwritten. */
+int sff_features(const uint8_t* rgb_dev, int32_t width, int32_t height, int32_t pitch_bytes,
+                 const sff_params* params, uint8_t* pyramid_dev,
+                 void* workspace, size_t workspace_bytes, void* stream);
+
+/* One dense scene-flow field (Sec. 3.1, "Initialization" and "Multi-Scale
+ * Propagation"; "Consistency Check" for the inverse field).
+ *   Cost of u at p (Eq. 1, with squared L2 distances of the WHT features of
+ *   the pixel's patch in place of the summed Euclidean SIFTFlow distances):
+ *   SSD(ref(p), temporal(p + (u, v))) + SSD(ref(p), stereo(p + (-sigma d0, 0)))
+ *   + SSD(ref(p), cross(p + (u - sigma d1, v))), each position clamped to
+ *   the image; sigma = +1 (mirror = 0) or -1 (mirror = 1).
+ *   Forward field: ref = L0, temporal = L1, stereo = R0, cross = R1, mirror 0.
+ *   Inverse field: ref = R1, temporal = R0, stereo = L1, cross = L0, mirror 1
+ *   ("temporal order as well as points of view are swapped").
+ *   Initialisation on the coarsest grid only: exact K_T nearest temporal
+ *   grid points, K_E nearest stereo points on the pixel's row (d0 >= 0) and
+ *   K_E nearest cross points on each temporal candidate's row (d1 >= 0); all
+ *   combinations scored, lowest cost wins (ties: first combination).
+ *   Then for each scale from coarse to fine: points of the coarser grid keep
+ *   their vector (cost re-scored), the other grid points start empty; then
+ *   `iterations` times: two synchronous half-steps over the two grid colours
+ *   ((x + y) / n even first), each grid pixel taking the lowest-cost of its
+ *   own vector and those of its two predecessors along the sweep direction
+ *   (cycling (+x,+y), (-x,-y), (+x,-y), (-x,+y)), replaced only on strictly
+ *   lower cost; then random search: every non-empty grid pixel adds to each
+ *   component the rounded value of a uniform draw on ]-n, n[ (Philox4x32-10,
+ *   key = seed, counter = (y W + x, iteration, scale + 4 mirror, 0)),
+ *   clamps d0, d1 >= 0 and keeps the candidate if its cost is strictly lower.
+ * pyr_*_dev: pyramids from sff_features of the same size and params.
+ * field_dev: [H][W][4] int16 (u, v, d0, d1), 8-byte aligned; cost_dev: [H][W]
+ * int32, SFF_EMPTY_COST where a pixel holds no vector.  Both overwritten. */
+int sff_match_views(const uint8_t* pyr_ref_dev, const uint8_t* pyr_temporal_dev,
+                    const uint8_t* pyr_stereo_dev, const uint8_t* pyr_cross_dev,
+                    int32_t width, int32_t height, int32_t mirror, uint64_t seed,
+                    const sff_params* params, int16_t* field_dev, int32_t* cost_dev,
+                    void* workspace, size_t workspace_bytes, void* stream);
+
+/* Consistency check and region filter (Sec. 3.1, "Consistency Check").
+ *   For L0 pixel p with forward vector u, q = p + (u - d1, v) in R1 and w the
+ *   inverse vector at q: differences (w.u + u - d1 + d0, w.v + v, w.d0 - d1,
+ *   w.d1 - d0); p is kept iff all |differences| <= tau_c; cerr = min(255,
+ *   sum |differences|).  Pixels without a vector, with q outside the image
+ *   or without an inverse vector at q are rejected with cerr = 255.
+ *   Region filter: kept pixels form 4-connected regions where neighbours
+ *   differ by at most tau_r in every component; a region that a rejected
+ *   4-neighbour (with a vector) could join by the same rule and that has
+ *   fewer than region_min pixels is removed.
+ * keep_dev: [H][W] uint8 0/1; cerr_dev: [H][W] uint8.  Both overwritten. */
+int sff_consistency_filter(const int16_t* fwd_dev, const int32_t* fwd_cost_dev,
+                           const int16_t* inv_dev, const int32_t* inv_cost_dev,
+                           int32_t width, int32_t height, const sff_params* params,
+                           uint8_t* keep_dev, uint8_t* cerr_dev,
+                           void* workspace, size_t workspace_bytes, void* stream);
+
+/* Sparsification (Sec. 3.2): for each non-overlapping 3x3 block (anchored at
+ * (0, 0), partial blocks at the right/bottom edges included) the kept pixel
+ * with the lowest cerr, then lowest cost, then lowest raster index becomes a
+ * seed.  Seeds are written in block raster order.
+ * seeds_dev: room for `capacity` seeds; seeds past `capacity` are dropped.
+ * count_dev: device int32, receives the total number of seeds (which may
+ * exceed capacity).  ceil(W/3) * ceil(H/3) is always enough. */
+int sff_emit_seeds(const int16_t* fwd_dev, const int32_t* fwd_cost_dev,
+                   const uint8_t* keep_dev, const uint8_t* cerr_dev,
+                   int32_t width, int32_t height, sff_seed* seeds_dev, int32_t capacity,
+                   int32_t* count_dev, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Per-kernel timing (no counterpart in the paper: measurement support).
+ * While enabled, every kernel launch of the library is bracketed by two
+ * CUDA events recorded on the launch's stream.  Enabling or disabling
+ * discards what was recorded.  Not usable while a stream is being captured
+ * into a CUDA graph: keep it disabled around stream capture. */
+typedef struct sff_kernel_time {
+    char name[40];       /* kernel name */
+    int32_t launches;    /* launches recorded */
+    double total_ms;     /* summed event-to-event time */
+} sff_kernel_time;
+
+int sff_profile_enable(int32_t on);
+
+/* Waits for the recorded events, writes up to `capacity` per-kernel totals
+ * (first-launch order) and the number of distinct kernels to *n_out, then
+ * clears the record.  Host pointers. */
+int sff_profile_collect(sff_kernel_time* out, int32_t capacity, int32_t* n_out);
+
+/* Human-readable name of a status code (static string). */
+const char* sff_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFF_H */

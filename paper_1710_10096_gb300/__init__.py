@@ -1,0 +1,263 @@
+"""SceneFlowFields sparse four-view matching stage on GB300 (sm_103a).
+
+Python binding of libsff.so (C ABI in include/sff.h).  This module only
+marshals arguments: every step of the stage -- features, initialisation,
+propagation, random search, consistency/region filter, seeds -- runs in the
+library's CUDA kernels.  PyTorch supplies device memory and streams.  There is
+no CPU fallback: if libsff.so is missing or cannot be loaded, every call
+raises.
+
+Paper: Schuster et al., "SceneFlowFields: Dense Interpolation of Sparse Scene
+Flow Correspondences", WACV 2018, Sec. 3.1-3.2.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+__all__ = ["Params", "SffError", "default_params", "pyramid_bytes", "workspace_bytes", "features", "match_views",
+           "consistency_filter", "emit_seeds", "QuadMatcher", "SEED_DTYPE", "lib", "build"]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsff.so")
+EMPTY_COST = 2147483647
+RECORD_BYTES = 64
+_lib = None
+
+
+class SffError(RuntimeError):
+    pass
+
+
+class Params(ctypes.Structure):
+    """sff_params of include/sff.h."""
+    _fields_ = [("num_scales", ctypes.c_int32), ("iterations", ctypes.c_int32), ("tau_c", ctypes.c_int32),
+                ("region_min", ctypes.c_int32), ("tau_r", ctypes.c_int32), ("quant_shift", ctypes.c_int32),
+                ("knn_temporal", ctypes.c_int32), ("knn_epipolar", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class KernelTime(ctypes.Structure):
+    """sff_kernel_time of include/sff.h."""
+    _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int32), ("total_ms", ctypes.c_double)]
+
+
+def profile_enable(on: bool = True) -> None:
+    """Bracket every library kernel launch with CUDA events (sff_profile_enable)."""
+    _check(lib().sff_profile_enable(1 if on else 0), "sff_profile_enable")
+
+
+def profile_collect() -> dict:
+    """{kernel name: (launches, total ms)} of the launches recorded since enabling."""
+    cap = 64
+    buf = (KernelTime * cap)()
+    n = ctypes.c_int32(0)
+    _check(lib().sff_profile_collect(buf, cap, ctypes.byref(n)), "sff_profile_collect")
+    return {buf[k].name.decode(): (buf[k].launches, buf[k].total_ms) for k in range(min(n.value, cap))}
+
+
+# sff_seed of include/sff.h
+SEED_DTYPE = np.dtype([("x", "<i2"), ("y", "<i2"), ("u", "<i2"), ("v", "<i2"), ("d0", "<i2"), ("d1", "<i2"),
+                       ("cost", "<i4"), ("cerr", "u1"), ("pad", "u1", (3,))])
+assert SEED_DTYPE.itemsize == 20
+
+
+def build(force: bool = False) -> str:
+    from . import buildlib as _b
+    return _b.build(force=force)
+
+
+def lib():
+    """Loads libsff.so; raises SffError when it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise SffError(f"{LIB_PATH} is missing: build it with paper_1710_10096_gb300.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, i32, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_size_t
+        PP = ctypes.POINTER(Params)
+        L.sff_default_params.argtypes = [PP]
+        L.sff_default_params.restype = i32
+        L.sff_pyramid_bytes.argtypes = [i32, i32, PP]
+        L.sff_pyramid_bytes.restype = sz
+        L.sff_workspace_bytes.argtypes = [i32, i32, PP]
+        L.sff_workspace_bytes.restype = sz
+        L.sff_features.argtypes = [P, i32, i32, i32, PP, P, P, sz, P]
+        L.sff_features.restype = i32
+        L.sff_match_views.argtypes = [P, P, P, P, i32, i32, i32, ctypes.c_uint64, PP, P, P, P, sz, P]
+        L.sff_match_views.restype = i32
+        L.sff_consistency_filter.argtypes = [P, P, P, P, i32, i32, PP, P, P, P, sz, P]
+        L.sff_consistency_filter.restype = i32
+        L.sff_emit_seeds.argtypes = [P, P, P, P, i32, i32, P, i32, P, P, sz, P]
+        L.sff_emit_seeds.restype = i32
+        L.sff_profile_enable.argtypes = [i32]
+        L.sff_profile_enable.restype = i32
+        L.sff_profile_collect.argtypes = [ctypes.POINTER(KernelTime), i32, ctypes.POINTER(i32)]
+        L.sff_profile_collect.restype = i32
+        L.sff_status_string.argtypes = [i32]
+        L.sff_status_string.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise SffError(f"{what}: {lib().sff_status_string(status).decode()} ({status})")
+
+
+def default_params(**overrides) -> Params:
+    p = Params()
+    _check(lib().sff_default_params(ctypes.byref(p)), "sff_default_params")
+    for k, v in overrides.items():
+        setattr(p, k, int(v))
+    return p
+
+
+def pyramid_bytes(width: int, height: int, params: Params = None) -> int:
+    params = params or default_params()
+    return lib().sff_pyramid_bytes(width, height, ctypes.byref(params))
+
+
+def workspace_bytes(width: int, height: int, params: Params = None) -> int:
+    params = params or default_params()
+    return lib().sff_workspace_bytes(width, height, ctypes.byref(params))
+
+
+def _ptr(t) -> int:
+    return t.data_ptr()
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _nbytes(t) -> int:
+    return t.numel() * t.element_size()
+
+
+def features(rgb, pyramid, workspace, params: Params = None, stream=None) -> None:
+    """sff_features on a [H, W, 3] uint8 CUDA tensor (rows may be padded)."""
+    params = params or default_params()
+    assert rgb.is_cuda and rgb.dtype.itemsize == 1 and rgb.dim() == 3 and rgb.shape[2] == 3
+    assert rgb.stride(2) == 1 and rgb.stride(1) == 3
+    h, w = rgb.shape[0], rgb.shape[1]
+    _check(lib().sff_features(_ptr(rgb), w, h, rgb.stride(0), ctypes.byref(params), _ptr(pyramid), _ptr(workspace),
+                              _nbytes(workspace), _stream(stream)), "sff_features")
+
+
+def match_views(pyr_ref, pyr_temporal, pyr_stereo, pyr_cross, width: int, height: int, mirror: int, seed: int,
+                field, cost, workspace, params: Params = None, stream=None) -> None:
+    """sff_match_views; field [H, W, 4] int16 and cost [H, W] int32 CUDA tensors."""
+    params = params or default_params()
+    _check(lib().sff_match_views(_ptr(pyr_ref), _ptr(pyr_temporal), _ptr(pyr_stereo), _ptr(pyr_cross), width,
+                                 height, int(mirror), int(seed) & (2 ** 64 - 1), ctypes.byref(params), _ptr(field),
+                                 _ptr(cost), _ptr(workspace), _nbytes(workspace), _stream(stream)),
+           "sff_match_views")
+
+
+def consistency_filter(fwd, fwd_cost, inv, inv_cost, keep, cerr, workspace, params: Params = None,
+                       stream=None) -> None:
+    params = params or default_params()
+    h, w = fwd.shape[0], fwd.shape[1]
+    _check(lib().sff_consistency_filter(_ptr(fwd), _ptr(fwd_cost), _ptr(inv), _ptr(inv_cost), w, h,
+                                        ctypes.byref(params), _ptr(keep), _ptr(cerr), _ptr(workspace),
+                                        _nbytes(workspace), _stream(stream)), "sff_consistency_filter")
+
+
+def emit_seeds(fwd, fwd_cost, keep, cerr, seeds, capacity: int, count, workspace, stream=None) -> None:
+    """seeds: CUDA uint8 tensor of >= 20 * capacity bytes; count: CUDA int32 tensor [1]."""
+    h, w = fwd.shape[0], fwd.shape[1]
+    assert _nbytes(seeds) >= 20 * capacity
+    _check(lib().sff_emit_seeds(_ptr(fwd), _ptr(fwd_cost), _ptr(keep), _ptr(cerr), w, h, _ptr(seeds), capacity,
+                                _ptr(count), _ptr(workspace), _nbytes(workspace), _stream(stream)), "sff_emit_seeds")
+
+
+def seed_capacity(width: int, height: int) -> int:
+    return ((width + 2) // 3) * ((height + 2) // 3)
+
+
+def seeds_to_numpy(seeds_bytes: np.ndarray, count: int) -> np.ndarray:
+    return np.frombuffer(np.ascontiguousarray(seeds_bytes).tobytes(), SEED_DTYPE)[:count].copy()
+
+
+class QuadMatcher:
+    """Device buffers for W x H quads and the four calls of the stage in order.
+
+    run() works on CUDA tensors already on the device; run_host() takes host
+    arrays, copies them in, runs the stage and copies the seeds back.
+    """
+
+    def __init__(self, width: int, height: int, params: Params = None, device="cuda"):
+        import torch
+        self.width, self.height = int(width), int(height)
+        self.params = params or default_params()
+        self.device = torch.device(device)
+        w, h = self.width, self.height
+        pb = pyramid_bytes(w, h, self.params)
+        wb = workspace_bytes(w, h, self.params)
+        if pb == 0 or wb == 0:
+            raise SffError(f"invalid size {w}x{h} or parameters")
+        u8 = dict(dtype=torch.uint8, device=self.device)
+        self.pyr = [torch.empty(pb, **u8) for _ in range(4)]  # L0, R0, L1, R1
+        self.workspace = torch.empty(wb, **u8)
+        self.fwd = torch.empty((h, w, 4), dtype=torch.int16, device=self.device)
+        self.inv = torch.empty((h, w, 4), dtype=torch.int16, device=self.device)
+        self.fwd_cost = torch.empty((h, w), dtype=torch.int32, device=self.device)
+        self.inv_cost = torch.empty((h, w), dtype=torch.int32, device=self.device)
+        self.keep = torch.empty((h, w), **u8)
+        self.cerr = torch.empty((h, w), **u8)
+        self.capacity = seed_capacity(w, h)
+        self.seeds = torch.empty(20 * self.capacity, **u8)
+        self.count = torch.zeros(1, dtype=torch.int32, device=self.device)
+        self._host_in = None
+
+    def run(self, L0, R0, L1, R1, seed: int, stream=None):
+        """All four calls on device images; returns (seeds bytes tensor, count tensor)."""
+        p = self.params
+        for img, pyr in zip((L0, R0, L1, R1), self.pyr):
+            features(img, pyr, self.workspace, p, stream)
+        pL0, pR0, pL1, pR1 = self.pyr
+        match_views(pL0, pL1, pR0, pR1, self.width, self.height, 0, seed, self.fwd, self.fwd_cost, self.workspace,
+                    p, stream)
+        match_views(pR1, pR0, pL1, pL0, self.width, self.height, 1, seed, self.inv, self.inv_cost, self.workspace,
+                    p, stream)
+        consistency_filter(self.fwd, self.fwd_cost, self.inv, self.inv_cost, self.keep, self.cerr, self.workspace,
+                           p, stream)
+        emit_seeds(self.fwd, self.fwd_cost, self.keep, self.cerr, self.seeds, self.capacity, self.count,
+                   self.workspace, stream)
+        return self.seeds, self.count
+
+    def run_host(self, L0, R0, L1, R1, seed: int, stream=None) -> np.ndarray:
+        """Host images in, host seeds out (pinned staging, copies on `stream`)."""
+        import torch
+        h, w = self.height, self.width
+        if self._host_in is None:
+            self._host_in = torch.empty((4, h, w, 3), dtype=torch.uint8).pin_memory()
+            self._dev_in = torch.empty((4, h, w, 3), dtype=torch.uint8, device=self.device)
+            self._host_seeds = torch.empty(20 * self.capacity, dtype=torch.uint8).pin_memory()
+            self._host_count = torch.empty(1, dtype=torch.int32).pin_memory()
+        for k, img in enumerate((L0, R0, L1, R1)):
+            self._host_in[k].copy_(torch.as_tensor(np.ascontiguousarray(img)))
+        s = stream if stream is not None else torch.cuda.current_stream()
+        with torch.cuda.stream(s):
+            self._dev_in.copy_(self._host_in, non_blocking=True)
+            self.run(*self._dev_in.unbind(0), seed=seed, stream=s)
+            self._host_count.copy_(self.count, non_blocking=True)
+            self._host_seeds.copy_(self.seeds, non_blocking=True)
+        s.synchronize()
+        n = int(self._host_count.item())
+        return seeds_to_numpy(self._host_seeds[:20 * min(n, self.capacity)].numpy(), n)
+
+    @property
+    def h2d_bytes(self) -> int:
+        return 4 * self.height * self.width * 3
+
+    @property
+    def d2h_bytes(self) -> int:
+        return 4 + 20 * self.capacity

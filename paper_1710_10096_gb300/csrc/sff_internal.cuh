@@ -1,0 +1,149 @@
+// Internal definitions shared by the CUDA translation units of libsff.
+//
+// Data layout in HBM (one quad of W x H images):
+//   pyramid  [scale][y][x] 64-byte records: 48 int8 WHT features, int32 norm
+//            (sum of squared features), 12 zero bytes.  A record is two
+//            32-byte sectors, so one candidate lookup costs exactly 2 sectors.
+//   field    [y][x] int16x4 (u, v, d0, d1): one 8-byte load per pixel.
+//   cost     [y][x] int32, SFF_EMPTY_COST where no vector is held yet.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sff.h"
+
+namespace sff {
+
+constexpr int kRec = SFF_RECORD_BYTES;
+constexpr int kEmpty = SFF_EMPTY_COST;
+
+__host__ __device__ __forceinline__ int clampi(int a, int lo, int hi) { return a < lo ? lo : (a > hi ? hi : a); }
+
+__host__ __device__ __forceinline__ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Reference feature held in registers: 12 packed int8x4 words and the norm.
+struct RefFeat {
+    int a[12];
+    int n;
+};
+
+__device__ __forceinline__ void load_ref(const uint8_t* rec, RefFeat& r) {
+    const int4* p = reinterpret_cast<const int4*>(rec);
+    int4 q0 = __ldg(p), q1 = __ldg(p + 1), q2 = __ldg(p + 2);
+    r.a[0] = q0.x; r.a[1] = q0.y; r.a[2] = q0.z; r.a[3] = q0.w;
+    r.a[4] = q1.x; r.a[5] = q1.y; r.a[6] = q1.z; r.a[7] = q1.w;
+    r.a[8] = q2.x; r.a[9] = q2.y; r.a[10] = q2.z; r.a[11] = q2.w;
+    r.n = __ldg(reinterpret_cast<const int*>(rec + 48));
+}
+
+// Sum of squared differences of two int8 feature vectors, as
+// |a|^2 + |b|^2 - 2 a.b with the dot product on dp4a (exact in int32).
+__device__ __forceinline__ int ssd_rec(const RefFeat& r, const uint8_t* rec) {
+    const int4* p = reinterpret_cast<const int4*>(rec);
+    int4 q0 = __ldg(p), q1 = __ldg(p + 1), q2 = __ldg(p + 2);
+    int nb = __ldg(reinterpret_cast<const int*>(rec + 48));
+    int d = 0;
+    d = __dp4a(r.a[0], q0.x, d); d = __dp4a(r.a[1], q0.y, d);
+    d = __dp4a(r.a[2], q0.z, d); d = __dp4a(r.a[3], q0.w, d);
+    d = __dp4a(r.a[4], q1.x, d); d = __dp4a(r.a[5], q1.y, d);
+    d = __dp4a(r.a[6], q1.z, d); d = __dp4a(r.a[7], q1.w, d);
+    d = __dp4a(r.a[8], q2.x, d); d = __dp4a(r.a[9], q2.y, d);
+    d = __dp4a(r.a[10], q2.z, d); d = __dp4a(r.a[11], q2.w, d);
+    return r.n + nb - 2 * d;
+}
+
+// The four views of one field at one scale (record pointers of that scale).
+struct Views {
+    const uint8_t* ref;
+    const uint8_t* tmp;
+    const uint8_t* ste;
+    const uint8_t* crs;
+    int w, h, sigma;
+};
+
+__device__ __forceinline__ const uint8_t* rec_at(const uint8_t* base, int w, int x, int y) {
+    return base + ((size_t)y * w + x) * kRec;
+}
+
+// Eq. 1 with WHT-feature SSD: temporal p+(u,v), stereo p+(-sigma d0, 0),
+// cross p+(u - sigma d1, v), positions clamped to the image.
+__device__ __forceinline__ int cost_of(const Views& V, const RefFeat& r, int px, int py, int u, int v, int d0,
+                                       int d1) {
+    int tx = clampi(px + u, 0, V.w - 1);
+    int ty = clampi(py + v, 0, V.h - 1);
+    int sx = clampi(px - V.sigma * d0, 0, V.w - 1);
+    int cx = clampi(px + u - V.sigma * d1, 0, V.w - 1);
+    return ssd_rec(r, rec_at(V.tmp, V.w, tx, ty)) + ssd_rec(r, rec_at(V.ste, V.w, sx, py)) +
+           ssd_rec(r, rec_at(V.crs, V.w, cx, ty));
+}
+
+// Field element pack/unpack: int16x4 in one 64-bit word.
+struct Vec4 {
+    int u, v, d0, d1;
+};
+
+__device__ __forceinline__ Vec4 unpack_vec(uint2 w) {
+    Vec4 r;
+    r.u = (int)(int16_t)(w.x & 0xffffu);
+    r.v = (int)(int16_t)(w.x >> 16);
+    r.d0 = (int)(int16_t)(w.y & 0xffffu);
+    r.d1 = (int)(int16_t)(w.y >> 16);
+    return r;
+}
+
+__device__ __forceinline__ uint2 pack_vec(const Vec4& a) {
+    uint2 w;
+    w.x = ((uint32_t)(uint16_t)a.u) | ((uint32_t)(uint16_t)a.v << 16);
+    w.y = ((uint32_t)(uint16_t)a.d0) | ((uint32_t)(uint16_t)a.d1 << 16);
+    return w;
+}
+
+// Philox4x32-10 counter-based generator (Salmon, Moraes, Dror, Shaw, SC'11):
+// ten rounds of two 32x32->64 multiplies with xor/permute, key advanced by
+// the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// Offset of the random search: nearest integer to a uniform value on ]-n, n[,
+// from r as floor((floor(r * 4n / 2^32) + 1) / 2) - n.
+__device__ __forceinline__ int rs_offset(uint32_t r, int n) {
+    uint32_t j = __umulhi(r, (uint32_t)(4 * n));
+    return (int)((j + 1) >> 1) - n;
+}
+
+// ---------------------------------------------------------------------------
+// host-side helpers
+
+// Optional per-kernel event timing (sff_profile_enable).  SFF_LAUNCH wraps
+// every kernel launch of the library.
+bool profiling();
+void profile_mark(const char* name, cudaStream_t st, bool after);
+
+#define SFF_LAUNCH(kernel, grid, block, smem, stream, ...)                       \
+    do {                                                                         \
+        if (::sff::profiling()) ::sff::profile_mark(#kernel, stream, false);     \
+        kernel<<<grid, block, smem, stream>>>(__VA_ARGS__);                      \
+        if (::sff::profiling()) ::sff::profile_mark(#kernel, stream, true);      \
+    } while (0)
+
+int check_size(int w, int h);
+int check_params(const sff_params* p);
+size_t features_ws_bytes(int w, int h, const sff_params& p);
+size_t match_ws_bytes(int w, int h, const sff_params& p);
+size_t filter_ws_bytes(int w, int h);
+size_t seeds_ws_bytes(int w, int h);
+int launch_status();
+
+}  // namespace sff

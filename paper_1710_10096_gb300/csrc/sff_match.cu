@@ -1,0 +1,326 @@
+// One dense scene-flow field: exact nearest-neighbour initialisation on the
+// coarsest grid, then per scale inheritance + propagation half-steps with
+// random search (Sec. 3.1, "Initialization", "Multi-Scale Propagation").
+//
+// k_knn_partial:  temporal K-NN, all-pairs over the coarsest grid; candidate
+//                 tiles staged in shared memory and broadcast to the 128
+//                 queries of a CTA; candidates split over blockIdx.y so the
+//                 grid covers the SMs.  Each thread keeps a sorted top-8 of
+//                 (distance, grid index) in registers.
+// k_init_select:  merges the partial top-8 lists, finds the nearest epipolar
+//                 stereo / cross points and keeps the best combination.  The
+//                 cost is the sum of the three independent distances, so for a
+//                 given temporal leaf the first-ranked epipolar leaves give
+//                 the lowest cost and win every tie; the result equals scoring
+//                 all K_T x K_E x K_E combinations in order.
+// k_inherit:      grid points of the coarser scale keep their vector and are
+//                 re-scored at this scale; the others start empty.
+// k_half_step:    one colour of the checkerboard.  Fused with the random
+//                 search of that colour: the search after iteration i of
+//                 colour 1 runs at the end of its half-step of iteration i,
+//                 the search of colour 0 at the start of its half-step of
+//                 iteration i+1 (or in a final pass).  Both orders read the
+//                 same values as the plain order "half-step 0, half-step 1,
+//                 random search", because a half-step only reads the other
+//                 colour and the search only reads the pixel itself.
+#include "sff_internal.cuh"
+
+namespace sff {
+namespace {
+
+constexpr int kKnnThreads = 128;
+constexpr int kKnnTile = 64;
+constexpr int kMaxParts = 8;
+
+__device__ __forceinline__ bool less_di(int d, int i, int d2, int i2) { return d < d2 || (d == d2 && i < i2); }
+
+__device__ __forceinline__ void top8_insert(int (&d)[8], int (&id)[8], int nd, int ni) {
+    if (!less_di(nd, ni, d[7], id[7])) return;
+#pragma unroll
+    for (int k = 7; k >= 0; --k) {
+        bool lt_prev = (k > 0) && less_di(nd, ni, d[k > 0 ? k - 1 : 0], id[k > 0 ? k - 1 : 0]);
+        if (lt_prev) {
+            d[k] = d[k - 1];
+            id[k] = id[k - 1];
+        } else if (less_di(nd, ni, d[k], id[k])) {
+            d[k] = nd;
+            id[k] = ni;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kKnnThreads) k_knn_partial(const uint8_t* __restrict__ ref,
+                                                              const uint8_t* __restrict__ tmp, int w, int n, int gw,
+                                                              int gq, int parts, int2* __restrict__ partial) {
+    __shared__ int4 tile[kKnnTile][4];
+    const int qi = blockIdx.x * kKnnThreads + threadIdx.x;
+    const bool active = qi < gq;
+    RefFeat r;
+    if (active) load_ref(rec_at(ref, w, (qi % gw) * n, (qi / gw) * n), r);
+    const int per = (gq + parts - 1) / parts;
+    const int c0 = blockIdx.y * per;
+    const int c1 = min(gq, c0 + per);
+    int bd[8], bi[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        bd[k] = 0x7fffffff;
+        bi[k] = 0x7fffffff;
+    }
+    for (int base = c0; base < c1; base += kKnnTile) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < kKnnTile * 4; t += kKnnThreads) {
+            int c = base + t / 4;
+            if (c < c1) tile[t / 4][t % 4] = __ldg(reinterpret_cast<const int4*>(rec_at(tmp, w, (c % gw) * n, (c / gw) * n)) + (t % 4));
+        }
+        __syncthreads();
+        const int cnt = min(kKnnTile, c1 - base);
+        if (active) {
+            for (int k = 0; k < cnt; ++k) {
+                int4 q0 = tile[k][0], q1 = tile[k][1], q2 = tile[k][2];
+                int nb = tile[k][3].x;
+                int dd = 0;
+                dd = __dp4a(r.a[0], q0.x, dd); dd = __dp4a(r.a[1], q0.y, dd);
+                dd = __dp4a(r.a[2], q0.z, dd); dd = __dp4a(r.a[3], q0.w, dd);
+                dd = __dp4a(r.a[4], q1.x, dd); dd = __dp4a(r.a[5], q1.y, dd);
+                dd = __dp4a(r.a[6], q1.z, dd); dd = __dp4a(r.a[7], q1.w, dd);
+                dd = __dp4a(r.a[8], q2.x, dd); dd = __dp4a(r.a[9], q2.y, dd);
+                dd = __dp4a(r.a[10], q2.z, dd); dd = __dp4a(r.a[11], q2.w, dd);
+                top8_insert(bd, bi, r.n + nb - 2 * dd, base + k);
+            }
+        }
+    }
+    if (active) {
+        int2* dst = partial + ((size_t)blockIdx.y * gq + qi) * 8;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) dst[k] = make_int2(bd[k], bi[k]);
+    }
+}
+
+// nearest grid point on row y (grid coordinates), constrained by sigma
+__device__ __forceinline__ void row_nearest(const RefFeat& r, const uint8_t* img, int w, int n, int gw, int y,
+                                            int xlim, int sigma, int& best_d, int& best_x) {
+    best_d = 0x7fffffff;
+    best_x = -1;
+    for (int g = 0; g < gw; ++g) {
+        int x = g * n;
+        if (sigma * (xlim - x) < 0) continue;
+        int d = ssd_rec(r, rec_at(img, w, x, y));
+        if (d < best_d) {  // ascending x: ties keep the lower raster index
+            best_d = d;
+            best_x = x;
+        }
+    }
+}
+
+__global__ void k_init_select(Views V, int n, int gw, int gq, int parts, int knn, const int2* __restrict__ partial,
+                              uint2* __restrict__ field, int* __restrict__ cost) {
+    const int qi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (qi >= gq) return;
+    const int px = (qi % gw) * n, py = (qi / gw) * n;
+    RefFeat r;
+    load_ref(rec_at(V.ref, V.w, px, py), r);
+    int bd[8], bi[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        bd[k] = 0x7fffffff;
+        bi[k] = 0x7fffffff;
+    }
+    for (int p = 0; p < parts; ++p) {
+        const int2* src = partial + ((size_t)p * gq + qi) * 8;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            int2 e = src[k];
+            if (e.x != 0x7fffffff) top8_insert(bd, bi, e.x, e.y);
+        }
+    }
+    int ds, sx;
+    row_nearest(r, V.ste, V.w, n, gw, py, px, V.sigma, ds, sx);
+    int best_c = 0x7fffffff;
+    Vec4 best = {0, 0, 0, 0};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if (k >= knn || bd[k] == 0x7fffffff) break;
+        const int tx = (bi[k] % gw) * n, ty = (bi[k] / gw) * n;
+        int dx_, cx;
+        row_nearest(r, V.crs, V.w, n, gw, ty, tx, V.sigma, dx_, cx);
+        int c = bd[k] + ds + dx_;
+        if (c < best_c) {
+            best_c = c;
+            best.u = tx - px;
+            best.v = ty - py;
+            best.d0 = V.sigma * (px - sx);
+            best.d1 = V.sigma * (tx - cx);
+        }
+    }
+    const size_t i = (size_t)py * V.w + px;
+    field[i] = pack_vec(best);
+    cost[i] = best_c;
+}
+
+__global__ void k_inherit(Views V, int n, int gw, int gh, uint2* __restrict__ field, int* __restrict__ cost) {
+    const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y;
+    if (gx >= gw || gy >= gh) return;
+    const int x = gx * n, y = gy * n;
+    const size_t i = (size_t)y * V.w + x;
+    const bool coarse = ((gx | gy) & 1) == 0;
+    int c = coarse ? cost[i] : kEmpty;
+    if (c != kEmpty) {
+        RefFeat r;
+        load_ref(rec_at(V.ref, V.w, x, y), r);
+        Vec4 a = unpack_vec(field[i]);
+        cost[i] = cost_of(V, r, x, y, a.u, a.v, a.d0, a.d1);
+    } else {
+        cost[i] = kEmpty;
+        field[i] = make_uint2(0u, 0u);
+    }
+}
+
+struct HalfStep {
+    int n, s, gw, colour, dx, dy, prop, rs_before, rs_after, mirror;
+    uint2 key;
+};
+
+__device__ __forceinline__ void random_search(const Views& V, const RefFeat& r, const HalfStep& H, int it, int x,
+                                              int y, uint32_t pix, Vec4& cur, int& c, bool& changed) {
+    uint4 rnd = philox4x32_10(make_uint4(pix, (uint32_t)it, (uint32_t)(H.s + 4 * H.mirror), 0u), H.key);
+    Vec4 cand;
+    cand.u = (int)(int16_t)(cur.u + rs_offset(rnd.x, H.n));
+    cand.v = (int)(int16_t)(cur.v + rs_offset(rnd.y, H.n));
+    cand.d0 = (int)(int16_t)max(0, cur.d0 + rs_offset(rnd.z, H.n));
+    cand.d1 = (int)(int16_t)max(0, cur.d1 + rs_offset(rnd.w, H.n));
+    if (cand.u == cur.u && cand.v == cur.v && cand.d0 == cur.d0 && cand.d1 == cur.d1) return;
+    int cc = cost_of(V, r, x, y, cand.u, cand.v, cand.d0, cand.d1);
+    if (cc < c) {
+        c = cc;
+        cur = cand;
+        changed = true;
+    }
+}
+
+__global__ void k_half_step(Views V, HalfStep H, uint2* __restrict__ field, int* __restrict__ cost) {
+    const int gy = blockIdx.y;
+    const int gx = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((H.colour + gy) & 1);
+    if (gx >= H.gw) return;
+    const int x = gx * H.n, y = gy * H.n;
+    const size_t i = (size_t)y * V.w + x;
+    int c = cost[i];
+    if (!H.prop && c == kEmpty) return;
+    Vec4 cur = unpack_vec(field[i]);
+    RefFeat r;
+    load_ref(rec_at(V.ref, V.w, x, y), r);
+    bool changed = false;
+    if (H.rs_before >= 0 && c != kEmpty) random_search(V, r, H, H.rs_before, x, y, (uint32_t)i, cur, c, changed);
+    if (H.prop) {
+        const int ax = x - H.dx * H.n;
+        if (ax >= 0 && ax < V.w) {
+            const size_t j = (size_t)y * V.w + ax;
+            const int cj = cost[j];
+            if (cj != kEmpty) {
+                Vec4 a = unpack_vec(field[j]);
+                int ca = cost_of(V, r, x, y, a.u, a.v, a.d0, a.d1);
+                if (ca < c) {
+                    c = ca;
+                    cur = a;
+                    changed = true;
+                }
+            }
+        }
+        const int by = y - H.dy * H.n;
+        if (by >= 0 && by < V.h) {
+            const size_t j = (size_t)by * V.w + x;
+            const int cj = cost[j];
+            if (cj != kEmpty) {
+                Vec4 b = unpack_vec(field[j]);
+                int cb = cost_of(V, r, x, y, b.u, b.v, b.d0, b.d1);
+                if (cb < c) {
+                    c = cb;
+                    cur = b;
+                    changed = true;
+                }
+            }
+        }
+    }
+    if (H.rs_after >= 0 && c != kEmpty) random_search(V, r, H, H.rs_after, x, y, (uint32_t)i, cur, c, changed);
+    if (changed) {
+        field[i] = pack_vec(cur);
+        cost[i] = c;
+    }
+}
+
+int knn_parts(int gq) {
+    int ctas = (gq + kKnnThreads - 1) / kKnnThreads;
+    int parts = (2 * 152 + ctas - 1) / ctas;
+    parts = parts < 1 ? 1 : (parts > kMaxParts ? kMaxParts : parts);
+    while (parts > 1 && gq / parts < kKnnTile) --parts;
+    return parts;
+}
+
+}  // namespace
+
+size_t match_ws_bytes(int w, int h, const sff_params& p) {
+    const int n = 1 << (p.num_scales - 1);
+    const size_t gq = (size_t)((w + n - 1) / n) * ((h + n - 1) / n);
+    return align256(kMaxParts * gq * 8 * sizeof(int2));
+}
+
+}  // namespace sff
+
+extern "C" int sff_match_views(const uint8_t* pyr_ref_dev, const uint8_t* pyr_temporal_dev,
+                               const uint8_t* pyr_stereo_dev, const uint8_t* pyr_cross_dev, int32_t width,
+                               int32_t height, int32_t mirror, uint64_t seed, const sff_params* params,
+                               int16_t* field_dev, int32_t* cost_dev, void* workspace, size_t workspace_bytes,
+                               void* stream) {
+    using namespace sff;
+    if (check_size(width, height) || check_params(params)) return SFF_ERR_ARG;
+    if (!pyr_ref_dev || !pyr_temporal_dev || !pyr_stereo_dev || !pyr_cross_dev || !field_dev || !cost_dev ||
+        !workspace)
+        return SFF_ERR_ARG;
+    if (mirror != 0 && mirror != 1) return SFF_ERR_ARG;
+    if (((uintptr_t)pyr_ref_dev | (uintptr_t)pyr_temporal_dev | (uintptr_t)pyr_stereo_dev |
+         (uintptr_t)pyr_cross_dev) & 15)
+        return SFF_ERR_ARG;
+    if (((uintptr_t)field_dev & 7) || ((uintptr_t)cost_dev & 3) || ((uintptr_t)workspace & 255)) return SFF_ERR_ARG;
+    if (workspace_bytes < match_ws_bytes(width, height, *params)) return SFF_ERR_WORKSPACE;
+
+    cudaStream_t st = (cudaStream_t)stream;
+    const int S = params->num_scales, I = params->iterations;
+    const size_t plane = (size_t)width * height * kRec;
+    uint2* field = reinterpret_cast<uint2*>(field_dev);
+    const int sigma = mirror ? -1 : 1;
+    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    static const int kDirs[4][2] = {{1, 1}, {-1, -1}, {1, -1}, {-1, 1}};
+
+    for (int s = S - 1; s >= 0; --s) {
+        const int n = 1 << s;
+        const int gw = (width + n - 1) / n, gh = (height + n - 1) / n;
+        Views V{pyr_ref_dev + s * plane, pyr_temporal_dev + s * plane, pyr_stereo_dev + s * plane,
+                pyr_cross_dev + s * plane, width, height, sigma};
+        if (s == S - 1) {
+            const int gq = gw * gh;
+            const int parts = knn_parts(gq);
+            int2* partial = reinterpret_cast<int2*>(workspace);
+            dim3 g1((gq + kKnnThreads - 1) / kKnnThreads, parts);
+            SFF_LAUNCH(k_knn_partial, g1, kKnnThreads, 0, st, V.ref, V.tmp, width, n, gw, gq, parts, partial);
+            SFF_LAUNCH(k_init_select, (gq + 127) / 128, 128, 0, st, V, n, gw, gq, parts, params->knn_temporal, partial, field,
+                                                            cost_dev);
+        } else {
+            dim3 g((gw + 127) / 128, gh);
+            SFF_LAUNCH(k_inherit, g, 128, 0, st, V, n, gw, gh, field, cost_dev);
+        }
+        const int half_w = (gw + 1) / 2;
+        dim3 g((half_w + 127) / 128, gh);
+        for (int it = 0; it < I; ++it) {
+            HalfStep H{n, s, gw, 0, kDirs[it % 4][0], kDirs[it % 4][1], 1, it - 1, -1, mirror, key};
+            SFF_LAUNCH(k_half_step, g, 128, 0, st, V, H, field, cost_dev);
+            H.colour = 1;
+            H.rs_before = -1;
+            H.rs_after = it;
+            SFF_LAUNCH(k_half_step, g, 128, 0, st, V, H, field, cost_dev);
+        }
+        if (I > 0) {
+            HalfStep H{n, s, gw, 0, 0, 0, 0, I - 1, -1, mirror, key};
+            SFF_LAUNCH(k_half_step, g, 128, 0, st, V, H, field, cost_dev);
+        }
+    }
+    return launch_status();
+}

@@ -1,0 +1,101 @@
+// Opt-in per-kernel timing: CUDA events recorded on the launch stream
+// before and after each kernel launch, summed per kernel name on collect.
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "sff_internal.cuh"
+
+namespace sff {
+namespace {
+
+struct Mark {
+    const char* name;
+    cudaEvent_t start, stop;
+};
+
+std::mutex g_mu;
+bool g_on = false;
+std::vector<Mark> g_marks;
+std::vector<cudaEvent_t> g_pool;
+cudaEvent_t g_pending = nullptr;
+
+cudaEvent_t take_event() {
+    if (!g_pool.empty()) {
+        cudaEvent_t e = g_pool.back();
+        g_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void release_all() {
+    for (auto& m : g_marks) {
+        g_pool.push_back(m.start);
+        g_pool.push_back(m.stop);
+    }
+    g_marks.clear();
+    if (g_pending) g_pool.push_back(g_pending);
+    g_pending = nullptr;
+}
+
+}  // namespace
+
+bool profiling() { return g_on; }
+
+void profile_mark(const char* name, cudaStream_t st, bool after) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!after) {
+        g_pending = take_event();
+        cudaEventRecord(g_pending, st);
+    } else {
+        cudaEvent_t stop = take_event();
+        cudaEventRecord(stop, st);
+        g_marks.push_back(Mark{name, g_pending, stop});
+        g_pending = nullptr;
+    }
+}
+
+}  // namespace sff
+
+extern "C" int sff_profile_enable(int32_t on) {
+    std::lock_guard<std::mutex> lk(sff::g_mu);
+    sff::release_all();
+    sff::g_on = on != 0;
+    return SFF_OK;
+}
+
+extern "C" int sff_profile_collect(sff_kernel_time* out, int32_t capacity, int32_t* n_out) {
+    if (!n_out || capacity < 0 || (capacity > 0 && !out)) return SFF_ERR_ARG;
+    std::lock_guard<std::mutex> lk(sff::g_mu);
+    std::vector<std::string> names;
+    std::vector<double> ms;
+    std::vector<int> count;
+    int status = SFF_OK;
+    for (auto& m : sff::g_marks) {
+        if (cudaEventSynchronize(m.stop) != cudaSuccess) status = SFF_ERR_CUDA;
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, m.start, m.stop) != cudaSuccess) status = SFF_ERR_CUDA;
+        size_t k = 0;
+        while (k < names.size() && names[k] != m.name) ++k;
+        if (k == names.size()) {
+            names.emplace_back(m.name);
+            ms.push_back(0.0);
+            count.push_back(0);
+        }
+        ms[k] += t;
+        count[k] += 1;
+    }
+    for (size_t k = 0; k < names.size() && (int)k < capacity; ++k) {
+        size_t len = names[k].size() < 39 ? names[k].size() : 39;
+        names[k].copy(out[k].name, len);
+        out[k].name[len] = 0;
+        out[k].launches = count[k];
+        out[k].total_ms = ms[k];
+    }
+    *n_out = (int32_t)names.size();
+    sff::release_all();
+    return status;
+}

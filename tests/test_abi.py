@@ -1,0 +1,96 @@
+"""The C ABI without a GPU: libsff.so builds for sm_103a, loads, exports
+every function include/sff.h declares, and rejects invalid arguments on the
+host before anything reaches CUDA."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sff.h")
+
+
+@pytest.fixture(scope="module")
+def sff():
+    import paper_1710_10096_gb300 as sff
+    sff.build()
+    return sff
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sff_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_four_calls():
+    names = declared_functions()
+    for n in ("sff_features", "sff_match_views", "sff_consistency_filter", "sff_emit_seeds"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(sff):
+    L = ctypes.CDLL(sff.LIB_PATH)
+    for name in declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_default_params_are_the_papers(sff):
+    p = sff.default_params()
+    # Sec. 5: k = 3 subscales (+ full resolution), 12 iterations, tau_c = 1, s_c = 150
+    assert (p.num_scales, p.iterations, p.tau_c, p.region_min) == (4, 12, 1, 150)
+    assert (p.tau_r, p.quant_shift, p.knn_temporal, p.knn_epipolar) == (1, 4, 4, 2)
+
+
+def test_sizes(sff):
+    p = sff.default_params()
+    assert sff.pyramid_bytes(1242, 375, p) == 4 * 1242 * 375 * 64
+    assert sff.pyramid_bytes(7, 100, p) == 0  # below the minimum size
+    assert sff.pyramid_bytes(16385, 100, p) == 0
+    ws = sff.workspace_bytes(1242, 375, p)
+    assert ws >= 3 * 1242 * 375 * 4 and ws % 256 == 0
+    bad = sff.default_params(num_scales=5)
+    assert sff.workspace_bytes(64, 64, bad) == 0
+
+
+def test_status_strings(sff):
+    L = sff.lib()
+    assert L.sff_status_string(0) == b"ok"
+    assert L.sff_status_string(-1) == b"invalid argument"
+    assert L.sff_status_string(-3) == b"workspace too small"
+
+
+def test_argument_errors_without_gpu(sff):
+    L = sff.lib()
+    p = sff.default_params()
+    P = ctypes.byref(p)
+    fake = ctypes.c_void_p(0x10000)  # never dereferenced: every call below fails validation first
+    null = ctypes.c_void_p(0)
+    ws = sff.workspace_bytes(64, 48, p)
+    # null pointers
+    assert L.sff_features(null, 64, 48, 192, P, fake, fake, ws, null) == -1
+    # bad sizes / pitch / params
+    assert L.sff_features(fake, 7, 48, 192, P, fake, fake, ws, null) == -1
+    assert L.sff_features(fake, 64, 48, 100, P, fake, fake, ws, null) == -1
+    bad = sff.default_params(knn_temporal=9)
+    assert L.sff_features(fake, 64, 48, 192, ctypes.byref(bad), fake, fake, ws, null) == -1
+    # misaligned pyramid
+    assert L.sff_features(fake, 64, 48, 192, P, ctypes.c_void_p(0x10008), fake, ws, null) == -1
+    # workspace too small
+    assert L.sff_features(fake, 64, 48, 192, P, fake, fake, 16, null) == -3
+    assert L.sff_match_views(fake, fake, fake, fake, 64, 48, 2, 1, P, fake, fake, fake, ws, null) == -1
+    assert L.sff_match_views(fake, fake, fake, fake, 64, 48, 0, 1, P, fake, fake, fake, 0, null) == -3
+    assert L.sff_consistency_filter(fake, fake, fake, null, 64, 48, P, fake, fake, fake, ws, null) == -1
+    assert L.sff_emit_seeds(fake, fake, fake, fake, 64, 48, fake, -1, fake, fake, ws, null) == -1
+    assert L.sff_emit_seeds(fake, fake, fake, fake, 64, 48, fake, 10, fake, fake, 0, null) == -3
+
+
+def test_product_path_has_no_oracle_dependency():
+    # the package and its CUDA sources never reference the oracle
+    pkg = os.path.join(ROOT, "paper_1710_10096_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in text.replace("oracle-", ""), os.path.join(dirpath, f)

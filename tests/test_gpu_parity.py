@@ -1,0 +1,222 @@
+"""CUDA path vs the CPU oracle, bit for bit, through the C ABI.
+
+Every output of the stage is integer: features, vectors, costs, keep masks,
+consistency errors and seeds must be identical.  Sizes span several CTAs
+and ragged tails (widths not multiples of the 128-thread rows or of the
+scale strides), the minimum 8x8 image, and the full 1242x375 and 1024x436
+workloads in the launch configuration the benchmark times.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import scenegen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle
+    import paper_1710_10096_gb300 as sff
+    sff.build()
+    oracle.build()
+    oracle.set_threads(os.cpu_count() or 1)
+    return torch, sff, oracle
+
+
+def _oparams(orc, p):
+    return orc.default_params(**p.as_dict())
+
+
+def _gpu_features(torch, sff, img, p):
+    h, w, _ = img.shape
+    pyr = torch.empty(sff.pyramid_bytes(w, h, p), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(sff.workspace_bytes(w, h, p), dtype=torch.uint8, device="cuda")
+    sff.features(torch.as_tensor(img).cuda(), pyr, ws, p)
+    torch.cuda.synchronize()
+    rec = pyr.cpu().numpy().reshape(p.num_scales, h, w, 64)
+    return pyr, rec
+
+
+@pytest.mark.parametrize("size", [(8, 8), (37, 23), (130, 70), (256, 80), (300, 9)])
+@pytest.mark.parametrize("qshift", [4, 0])
+def test_features_bit_exact(env, size, qshift):
+    torch, sff, orc = env
+    w, h = size
+    img = scenegen.random_images(w, h, seed=w * 1000 + h, n=1)[0]
+    p = sff.default_params(quant_shift=qshift)
+    _, rec = _gpu_features(torch, sff, img, p)
+    feat, norm = orc.features(img, _oparams(orc, p))
+    assert np.array_equal(rec[..., :48].view(np.int8), feat)
+    assert np.array_equal(rec[..., 48:52].copy().view(np.int32)[..., 0], norm)
+    assert (rec[..., 52:] == 0).all()
+
+
+def _match_both(env, imgs, p, seed):
+    torch, sff, orc = env
+    h, w, _ = imgs[0].shape
+    pyrs = [_gpu_features(torch, sff, im, p)[0] for im in imgs]
+    ws = torch.empty(sff.workspace_bytes(w, h, p), dtype=torch.uint8, device="cuda")
+    op = _oparams(orc, p)
+    feats = [orc.features(im, op)[0] for im in imgs]
+    out = []
+    for mirror, roles in ((0, (0, 2, 1, 3)), (1, (3, 1, 2, 0))):
+        field = torch.empty((h, w, 4), dtype=torch.int16, device="cuda")
+        cost = torch.empty((h, w), dtype=torch.int32, device="cuda")
+        sff.match_views(*(pyrs[i] for i in roles), w, h, mirror, seed, field, cost, ws, p)
+        torch.cuda.synchronize()
+        of, oc = orc.match_views(*(feats[i] for i in roles), mirror, seed, op)
+        out.append((field.cpu().numpy(), cost.cpu().numpy(), of, oc))
+    return out
+
+
+@pytest.mark.parametrize("size,params", [
+    ((64, 48), {}),
+    ((37, 23), {}),
+    ((8, 8), {}),
+    ((130, 70), {"iterations": 5}),
+    ((96, 40), {"num_scales": 1, "iterations": 3}),
+    ((96, 40), {"num_scales": 2, "iterations": 0}),
+    ((96, 40), {"num_scales": 3, "knn_temporal": 1, "knn_epipolar": 1}),
+    ((150, 66), {"knn_temporal": 8, "knn_epipolar": 8}),
+])
+def test_match_views_random_images(env, size, params):
+    torch, sff, orc = env
+    w, h = size
+    imgs = scenegen.random_images(w, h, seed=7 + w + h)
+    p = sff.default_params(**params)
+    for gf, gc, of, oc in _match_both(env, imgs, p, seed=0x1234567890ABCDEF):
+        assert np.array_equal(gc, oc)
+        assert np.array_equal(gf, of)
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_match_views_planes_scene(env, seed):
+    torch, sff, orc = env
+    q = scenegen.make_named("planes_256x80", seed)
+    p = sff.default_params()
+    for gf, gc, of, oc in _match_both(env, list(q.images()), p, seed=seed * 31):
+        assert np.array_equal(gc, oc)
+        assert np.array_equal(gf, of)
+
+
+def _run_gpu_quad(torch, sff, q, seed, p=None):
+    m = sff.QuadMatcher(q.width, q.height, p)
+    dev = [torch.as_tensor(im).cuda() for im in q.images()]
+    seeds, count = m.run(*dev, seed=seed)
+    torch.cuda.synchronize()
+    n = int(count.item())
+    return m, sff.seeds_to_numpy(seeds.cpu().numpy(), min(n, m.capacity)), n
+
+
+def _assert_quad_equal(m, got_seeds, n, ref):
+    assert np.array_equal(m.fwd_cost.cpu().numpy(), ref["fwd_cost"])
+    assert np.array_equal(m.fwd.cpu().numpy(), ref["fwd"])
+    assert np.array_equal(m.inv_cost.cpu().numpy(), ref["inv_cost"])
+    assert np.array_equal(m.inv.cpu().numpy(), ref["inv"])
+    assert np.array_equal(m.cerr.cpu().numpy(), ref["cerr"])
+    assert np.array_equal(m.keep.cpu().numpy(), ref["keep"])
+    assert n == len(ref["seeds"])
+    assert got_seeds.tobytes() == ref["seeds"].tobytes()
+
+
+@pytest.mark.parametrize("name,seed", [("planes_256x80", 1), ("planes_256x80", 5)])
+def test_full_stage_small(env, name, seed):
+    torch, sff, orc = env
+    q = scenegen.make_named(name, seed)
+    m, got, n = _run_gpu_quad(torch, sff, q, seed=seed)
+    ref = orc.run_quad(*q.images(), seed=seed)
+    _assert_quad_equal(m, got, n, ref)
+
+
+def test_full_stage_shift_scene(env):
+    torch, sff, orc = env
+    q = scenegen.make_shift_quad(160, 96, 31, u=-6, v=3, d0=2, d1=9)
+    m, got, n = _run_gpu_quad(torch, sff, q, seed=3)
+    ref = orc.run_quad(*q.images(), seed=3)
+    _assert_quad_equal(m, got, n, ref)
+    assert (m.fwd.cpu().numpy()[40:-40, 40:-40] == np.array([-6, 3, 2, 9])).all()
+
+
+@pytest.mark.parametrize("name", ["driving_1242x375", "movie_1024x436"])
+def test_full_stage_full_size(env, name):
+    torch, sff, orc = env
+    q = scenegen.make_named(name, 2)
+    m, got, n = _run_gpu_quad(torch, sff, q, seed=2024)
+    ref = orc.run_quad(*q.images(), seed=2024)
+    _assert_quad_equal(m, got, n, ref)
+
+
+def test_filter_and_seeds_on_oracle_fields(env):
+    # the filter and the seed emission in isolation, fed the oracle's fields
+    torch, sff, orc = env
+    q = scenegen.make_named("planes_256x80", 4)
+    ref = orc.run_quad(*q.images(), seed=9)
+    h, w = q.height, q.width
+    p = sff.default_params(region_min=60)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a)).cuda()
+    fwd, fc, inv, ic = t(ref["fwd"]), t(ref["fwd_cost"]), t(ref["inv"]), t(ref["inv_cost"])
+    keep = torch.empty((h, w), dtype=torch.uint8, device="cuda")
+    cerr = torch.empty((h, w), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(sff.workspace_bytes(w, h, p), dtype=torch.uint8, device="cuda")
+    sff.consistency_filter(fwd, fc, inv, ic, keep, cerr, ws, p)
+    okeep, ocerr = orc.consistency_filter(ref["fwd"], ref["fwd_cost"], ref["inv"], ref["inv_cost"],
+                                          _oparams(orc, p))
+    torch.cuda.synchronize()
+    assert np.array_equal(keep.cpu().numpy(), okeep)
+    assert np.array_equal(cerr.cpu().numpy(), ocerr)
+    # seeds with too small a capacity: the count is still the total
+    cap = sff.seed_capacity(w, h)
+    seeds = torch.zeros(20 * cap, dtype=torch.uint8, device="cuda")
+    count = torch.zeros(1, dtype=torch.int32, device="cuda")
+    sff.emit_seeds(fwd, fc, keep, cerr, seeds, 10, count, ws)
+    torch.cuda.synchronize()
+    osd = orc.emit_seeds(ref["fwd"], ref["fwd_cost"], okeep, ocerr)
+    assert int(count.item()) == len(osd)
+    assert sff.seeds_to_numpy(seeds.cpu().numpy(), 10).tobytes() == osd[:10].tobytes()
+    assert (seeds.cpu().numpy()[200:] == 0).all()
+
+
+def test_region_filter_random_pieces(env):
+    # union-find components vs the oracle's BFS on fields with many small regions
+    torch, sff, orc = env
+    rng = np.random.default_rng(12)
+    h, w = 200, 333
+    fwd = rng.integers(-2, 3, (h, w, 4)).astype(np.int16)  # neighbours often within tau_r
+    fwd[..., 0] += (rng.integers(0, 4, (h // 10 + 1, w // 10 + 1)) * 5).repeat(10, 0).repeat(10, 1)[:h, :w]
+    fc = np.zeros((h, w), np.int32)
+    fc[rng.random((h, w)) < 0.05] = 2147483647
+    inv = np.zeros_like(fwd)
+    ic = np.zeros_like(fc)
+    # consistency: feed an inverse that makes ~70 % pass
+    for y in range(h):
+        for x in range(w):
+            u, v, d0, d1 = (int(a) for a in fwd[y, x])
+            qx, qy = x + u - d1, y + v
+            if 0 <= qx < w and 0 <= qy < h and rng.random() < 0.7:
+                inv[qy, qx] = (-(u - d1 + d0), -v, d1, d0)
+    p = sff.default_params(region_min=25)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a)).cuda()
+    keep = torch.empty((h, w), dtype=torch.uint8, device="cuda")
+    cerr = torch.empty((h, w), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(sff.workspace_bytes(w, h, p), dtype=torch.uint8, device="cuda")
+    sff.consistency_filter(t(fwd), t(fc), t(inv), t(ic), keep, cerr, ws, p)
+    okeep, ocerr = orc.consistency_filter(fwd, fc, inv, ic, _oparams(orc, p))
+    torch.cuda.synchronize()
+    assert np.array_equal(cerr.cpu().numpy(), ocerr)
+    assert np.array_equal(keep.cpu().numpy(), okeep)
+
+
+def test_run_host_matches_device_path(env):
+    torch, sff, orc = env
+    q = scenegen.make_named("planes_256x80", 6)
+    m = sff.QuadMatcher(q.width, q.height)
+    a = m.run_host(*q.images(), seed=77)
+    b = m.run_host(*q.images(), seed=77)
+    ref = orc.run_quad(*q.images(), seed=77)
+    assert a.tobytes() == ref["seeds"].tobytes() == b.tobytes()
