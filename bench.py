@@ -48,7 +48,7 @@ ALGO_BYTES = {"k_half_step": 24 + 64 + 3 * 64, "k_features": 4 + 64}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sff", choices=["sff", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
