@@ -172,6 +172,31 @@ int sff_emit_seeds(const int16_t* fwd_dev, const int32_t* fwd_cost_dev,
                    int32_t width, int32_t height, sff_seed* seeds_dev, int32_t capacity,
                    int32_t* count_dev, void* workspace, size_t workspace_bytes, void* stream);
 
+/* Allocation-free variant of sff_emit_seeds.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory,
+ * e.g. code that only receives device pointers from another component and
+ * has no allocator of its own, or a latency-critical loop where a
+ * cudaMalloc (which may synchronise the device) is not acceptable.  It
+ * computes exactly what sff_emit_seeds computes, with the same arguments
+ * except the workspace: its scratch (one int32 per 3x3 block) is a static
+ * device array of SFF_NOALLOC_MAX_BLOCKS entries (2 MiB) inside the library,
+ * which every GPU that loads the library holds until the process exits.
+ *   - Calls no cudaMalloc/cudaFree or allocating routine.
+ *   - Images with ceil(W/3) * ceil(H/3) > SFF_NOALLOC_MAX_BLOCKS (about
+ *     4.7 million pixels) are rejected with SFF_ERR_ARG before any work.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current) and caches it; make that first call before any
+ *     stream capture on the device.
+ *   - All calls share the one array: calls that may overlap on the GPU (other
+ *     streams, other threads) race and must be ordered by the caller.  The
+ *     array keeps the previous call's contents; every entry a call reads is
+ *     first written by the same call. */
+#define SFF_NOALLOC_MAX_BLOCKS (1 << 19)
+int sff_emit_seeds_noalloc(const int16_t* fwd_dev, const int32_t* fwd_cost_dev,
+                           const uint8_t* keep_dev, const uint8_t* cerr_dev,
+                           int32_t width, int32_t height, sff_seed* seeds_dev, int32_t capacity,
+                           int32_t* count_dev, void* stream);
+
 /* Per-kernel timing (no counterpart in the paper: measurement support).
  * While enabled, every kernel launch of the library is bracketed by two
  * CUDA events recorded on the launch's stream.  Enabling or disabling

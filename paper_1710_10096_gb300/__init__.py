@@ -94,6 +94,8 @@ def lib():
         L.sff_consistency_filter.restype = i32
         L.sff_emit_seeds.argtypes = [P, P, P, P, i32, i32, P, i32, P, P, sz, P]
         L.sff_emit_seeds.restype = i32
+        L.sff_emit_seeds_noalloc.argtypes = [P, P, P, P, i32, i32, P, i32, P, P]
+        L.sff_emit_seeds_noalloc.restype = i32
         L.sff_profile_enable.argtypes = [i32]
         L.sff_profile_enable.restype = i32
         L.sff_profile_collect.argtypes = [ctypes.POINTER(KernelTime), i32, ctypes.POINTER(i32)]

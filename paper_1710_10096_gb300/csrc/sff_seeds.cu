@@ -7,12 +7,23 @@
 //               contiguous run of blocks, a CTA-wide exclusive scan gives the
 //               run's output offset, then each thread writes its run in order.
 // Scratch (workspace): best[ceil(W/3) * ceil(H/3)] int32.
+#include <mutex>
+
 #include "sff_internal.cuh"
 
 namespace sff {
 namespace {
 
 constexpr int kScanThreads = 1024;
+
+// Scratch of sff_emit_seeds_noalloc: one int32 per 3x3 block, in a static
+// device array so that the call needs no allocation.  Every device that
+// loads the library holds these 2 MiB until the process exits.
+constexpr int kNoAllocMaxBlocks = SFF_NOALLOC_MAX_BLOCKS;
+__device__ __align__(256) int g_noalloc_best[kNoAllocMaxBlocks];
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+int* g_noalloc_ptr[kMaxDevices] = {};
 
 __global__ void k_block_best(const int* __restrict__ fcost, const uint8_t* __restrict__ keep,
                              const uint8_t* __restrict__ cerr, int w, int h, int bw, int nb, int* __restrict__ best) {
@@ -109,5 +120,40 @@ extern "C" int sff_emit_seeds(const int16_t* fwd_dev, const int32_t* fwd_cost_de
     SFF_LAUNCH(k_block_best, (nb + 255) / 256, 256, 0, st, fwd_cost_dev, keep_dev, cerr_dev, width, height, bw, nb, best);
     SFF_LAUNCH(k_compact, 1, kScanThreads, 0, st, best, nb, reinterpret_cast<const uint2*>(fwd_dev), fwd_cost_dev, cerr_dev,
                                           width, seeds_dev, capacity, count_dev);
+    return launch_status();
+}
+
+extern "C" int sff_emit_seeds_noalloc(const int16_t* fwd_dev, const int32_t* fwd_cost_dev, const uint8_t* keep_dev,
+                                      const uint8_t* cerr_dev, int32_t width, int32_t height, sff_seed* seeds_dev,
+                                      int32_t capacity, int32_t* count_dev, void* stream) {
+    using namespace sff;
+    if (check_size(width, height)) return SFF_ERR_ARG;
+    if (!fwd_dev || !fwd_cost_dev || !keep_dev || !cerr_dev || !count_dev || capacity < 0) return SFF_ERR_ARG;
+    if (capacity > 0 && !seeds_dev) return SFF_ERR_ARG;
+    if (((uintptr_t)fwd_dev & 7) || ((uintptr_t)seeds_dev & 3)) return SFF_ERR_ARG;
+    const int bw = (width + 2) / 3, nb = bw * ((height + 2) / 3);
+    if (nb > kNoAllocMaxBlocks) return SFF_ERR_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SFF_ERR_CUDA;
+    if (dev < 0 || dev >= kMaxDevices) return SFF_ERR_ARG;
+    int* best = nullptr;
+    {
+        // Host code cannot use the array's name as a device address: look the
+        // address up once per device, with that device current.
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_best) != cudaSuccess || !p) return SFF_ERR_CUDA;
+            g_noalloc_ptr[dev] = static_cast<int*>(p);
+        }
+        best = g_noalloc_ptr[dev];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    // k_block_best writes every one of the nb entries before k_compact reads
+    // them, so the array needs no clearing between calls.
+    SFF_LAUNCH(k_block_best, (nb + 255) / 256, 256, 0, st, fwd_cost_dev, keep_dev, cerr_dev, width, height, bw, nb,
+               best);
+    SFF_LAUNCH(k_compact, 1, kScanThreads, 0, st, best, nb, reinterpret_cast<const uint2*>(fwd_dev), fwd_cost_dev,
+               cerr_dev, width, seeds_dev, capacity, count_dev);
     return launch_status();
 }
