@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sff", choices=["sff", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(scenegen.CONFIG_SIZES),
+                    help="scene (profiling uses the small planes_256x80 case)")
     return ap.parse_args()
 
 
@@ -234,7 +236,7 @@ def main():
     dev = torch.device("cuda", local)
     sff.build()
 
-    q = scenegen.make_named(WORKLOAD, SCENE_SEED + rank)
+    q = scenegen.make_named(args.workload, SCENE_SEED + rank)
     params = sff.default_params()
     m = sff.QuadMatcher(q.width, q.height, params, device=dev)
     stream = torch.cuda.Stream(device=dev)
@@ -328,7 +330,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "px/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int8", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "width": q.width, "height": q.height, "quads_per_step": 1,
+            "config": {"workload": args.workload, "width": q.width, "height": q.height, "quads_per_step": 1,
                        "parallelism": f"replicas{world}", "cuda_graph": True,
                        "l2": "flushed between timed steps (256 MB write outside the step events)",
                        "params": params.as_dict(), "scene_seed": SCENE_SEED, "match_seed": MATCH_SEED},

@@ -178,9 +178,10 @@ int sff_emit_seeds(const int16_t* fwd_dev, const int32_t* fwd_cost_dev,
  * has no allocator of its own, or a latency-critical loop where a
  * cudaMalloc (which may synchronise the device) is not acceptable.  It
  * computes exactly what sff_emit_seeds computes, with the same arguments
- * except the workspace: its scratch (one int32 per 3x3 block) is a static
- * device array of SFF_NOALLOC_MAX_BLOCKS entries (2 MiB) inside the library,
- * which every GPU that loads the library holds until the process exits.
+ * except the workspace: its scratch (one int32 per 3x3 block and one per
+ * 256 blocks) is a static device array of SFF_NOALLOC_MAX_BLOCKS + 2048
+ * int32 (about 2 MiB) inside the library, which every GPU that loads the
+ * library holds until the process exits.
  *   - Calls no cudaMalloc/cudaFree or allocating routine.
  *   - Images with ceil(W/3) * ceil(H/3) > SFF_NOALLOC_MAX_BLOCKS (about
  *     4.7 million pixels) are rejected with SFF_ERR_ARG before any work.

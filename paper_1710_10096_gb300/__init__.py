@@ -195,11 +195,12 @@ class QuadMatcher:
     arrays, copies them in, runs the stage and copies the seeds back.
     """
 
-    def __init__(self, width: int, height: int, params: Params = None, device="cuda"):
+    def __init__(self, width: int, height: int, params: Params = None, device="cuda", concurrent: bool = True):
         import torch
         self.width, self.height = int(width), int(height)
         self.params = params or default_params()
         self.device = torch.device(device)
+        self.concurrent = concurrent
         w, h = self.width, self.height
         pb = pyramid_bytes(w, h, self.params)
         wb = workspace_bytes(w, h, self.params)
@@ -207,7 +208,11 @@ class QuadMatcher:
             raise SffError(f"invalid size {w}x{h} or parameters")
         u8 = dict(dtype=torch.uint8, device=self.device)
         self.pyr = [torch.empty(pb, **u8) for _ in range(4)]  # L0, R0, L1, R1
-        self.workspace = torch.empty(wb, **u8)
+        # one workspace per concurrent stream: features of the four images run
+        # on four streams, the forward and inverse fields on two
+        self.workspaces = [torch.empty(wb, **u8) for _ in range(4 if concurrent else 1)]
+        self.workspace = self.workspaces[0]
+        self._side = [torch.cuda.Stream(device=self.device) for _ in range(3)] if concurrent else []
         self.fwd = torch.empty((h, w, 4), dtype=torch.int16, device=self.device)
         self.inv = torch.empty((h, w, 4), dtype=torch.int16, device=self.device)
         self.fwd_cost = torch.empty((h, w), dtype=torch.int32, device=self.device)
@@ -221,18 +226,43 @@ class QuadMatcher:
 
     def run(self, L0, R0, L1, R1, seed: int, stream=None):
         """All four calls on device images; returns (seeds bytes tensor, count tensor)."""
+        import torch
         p = self.params
-        for img, pyr in zip((L0, R0, L1, R1), self.pyr):
-            features(img, pyr, self.workspace, p, stream)
+        main = stream if stream is not None else torch.cuda.current_stream(self.device)
         pL0, pR0, pL1, pR1 = self.pyr
-        match_views(pL0, pL1, pR0, pR1, self.width, self.height, 0, seed, self.fwd, self.fwd_cost, self.workspace,
-                    p, stream)
-        match_views(pR1, pR0, pL1, pL0, self.width, self.height, 1, seed, self.inv, self.inv_cost, self.workspace,
-                    p, stream)
+        if not self.concurrent:
+            for img, pyr in zip((L0, R0, L1, R1), self.pyr):
+                features(img, pyr, self.workspace, p, main)
+            match_views(pL0, pL1, pR0, pR1, self.width, self.height, 0, seed, self.fwd, self.fwd_cost,
+                        self.workspace, p, main)
+            match_views(pR1, pR0, pL1, pL0, self.width, self.height, 1, seed, self.inv, self.inv_cost,
+                        self.workspace, p, main)
+        else:
+            streams = [main] + self._side
+            fork = torch.cuda.Event()
+            fork.record(main)
+            for st in self._side:
+                st.wait_event(fork)
+            for img, pyr, ws, st in zip((L0, R0, L1, R1), self.pyr, self.workspaces, streams):
+                features(img, pyr, ws, p, st)
+            for st in self._side:
+                done = torch.cuda.Event()
+                done.record(st)
+                main.wait_event(done)
+            fork2 = torch.cuda.Event()
+            fork2.record(main)
+            self._side[0].wait_event(fork2)
+            match_views(pL0, pL1, pR0, pR1, self.width, self.height, 0, seed, self.fwd, self.fwd_cost,
+                        self.workspaces[0], p, main)
+            match_views(pR1, pR0, pL1, pL0, self.width, self.height, 1, seed, self.inv, self.inv_cost,
+                        self.workspaces[1], p, self._side[0])
+            join = torch.cuda.Event()
+            join.record(self._side[0])
+            main.wait_event(join)
         consistency_filter(self.fwd, self.fwd_cost, self.inv, self.inv_cost, self.keep, self.cerr, self.workspace,
-                           p, stream)
+                           p, main)
         emit_seeds(self.fwd, self.fwd_cost, self.keep, self.cerr, self.seeds, self.capacity, self.count,
-                   self.workspace, stream)
+                   self.workspace, main)
         return self.seeds, self.count
 
     def run_host(self, L0, R0, L1, R1, seed: int, stream=None) -> np.ndarray:

@@ -4,13 +4,15 @@
 //                in R1 and compare the round trip of all three
 //                correspondences.
 // Region filter: connected components of kept pixels (4-neighbours whose
-//                vectors differ by at most tau_r) by union-find.  Unions
-//                always hang the larger root under the smaller one with
-//                atomicMin, so every component ends with its minimum raster
-//                index as root, independent of scheduling.  Then the size of
-//                each component and whether a rejected neighbour could join
-//                it are accumulated on the root, and small joinable
-//                components are removed.
+//                vectors differ by at most tau_r) by union-find, first inside
+//                32x32 tiles in shared memory (k_cc_local), then across tile
+//                borders in global memory (k_cc_border).  Unions always hang
+//                the larger root under the smaller one with atomicMin, so
+//                every component ends with its minimum raster index as root,
+//                independent of scheduling.  Then the size of each component
+//                and whether a rejected neighbour could join it are
+//                accumulated on the root (k_cc_stats), and small joinable
+//                components are removed (k_cc_remove).
 // Scratch (workspace): parent[H*W], size[H*W], joinable[H*W] int32.
 #include "sff_internal.cuh"
 
@@ -58,7 +60,7 @@ __device__ __forceinline__ int find_root(const int* parent, int x) {
 }
 
 // Each round either finishes or moves a root to a strictly smaller index, so
-// the loop ends after at most a few steps per element.
+// the loop ends after a few steps per element.
 __device__ void unite(int* parent, int a, int b) {
     while (true) {
         a = find_root(parent, a);
@@ -75,53 +77,118 @@ __device__ void unite(int* parent, int a, int b) {
     }
 }
 
-__global__ void k_cc_init(const uint8_t* __restrict__ keep, int np, int* __restrict__ parent, int* __restrict__ size,
-                          int* __restrict__ joinable) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= np) return;
-    parent[i] = keep[i] ? i : -1;
-    size[i] = 0;
-    joinable[i] = 0;
+constexpr int kTile = 32;  // union-find tile: 32 x 32 pixels, 256 threads
+
+__device__ __forceinline__ int find_local(volatile int* lp, int k) {
+    int p = lp[k];
+    while (p != k) {
+        k = p;
+        p = lp[k];
+    }
+    return k;
 }
 
-__global__ void k_cc_union(const uint2* __restrict__ fwd, const uint8_t* __restrict__ keep, int w, int h, int tau_r,
-                           int* parent) {
+__device__ void unite_local(int* lp, int a, int b) {
+    while (true) {
+        a = find_local(lp, a);
+        b = find_local(lp, b);
+        if (a == b) return;
+        if (a < b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        const int old = atomicMin(lp + a, b);
+        if (old == a) return;
+        a = old;
+    }
+}
+
+// Components inside one tile in shared memory.  Local indices follow raster
+// order, so a local root is the minimum raster index of its local component;
+// every kept pixel's parent becomes its local root.  Also clears size and
+// joinable for the tile's pixels.
+__global__ void __launch_bounds__(256) k_cc_local(const uint2* __restrict__ fwd, const uint8_t* __restrict__ keep,
+                                                  int w, int h, int tau_r, int* __restrict__ parent,
+                                                  int* __restrict__ size, int* __restrict__ joinable) {
+    __shared__ int lp[kTile * kTile];
+    __shared__ uint2 lf[kTile * kTile];
+    __shared__ uint8_t lk[kTile * kTile];
+    const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
+    for (int k = threadIdx.x; k < kTile * kTile; k += blockDim.x) {
+        const int x = x0 + (k % kTile), y = y0 + (k / kTile);
+        const bool inside = x < w && y < h;
+        const size_t i = (size_t)y * w + x;
+        const bool kk = inside && keep[i];
+        lk[k] = kk;
+        lf[k] = kk ? fwd[i] : make_uint2(0u, 0u);
+        lp[k] = kk ? k : -1;
+        if (inside) {
+            size[i] = 0;
+            joinable[i] = 0;
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < kTile * kTile; k += blockDim.x) {
+        if (!lk[k]) continue;
+        const int lx = k % kTile, ly = k / kTile;
+        if (lx + 1 < kTile && lk[k + 1] && close_vec(lf[k], lf[k + 1], tau_r)) unite_local(lp, k, k + 1);
+        if (ly + 1 < kTile && lk[k + kTile] && close_vec(lf[k], lf[k + kTile], tau_r)) unite_local(lp, k, k + kTile);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < kTile * kTile; k += blockDim.x) {
+        if (!lk[k]) continue;
+        const int r = find_local(lp, k);
+        parent[(size_t)(y0 + k / kTile) * w + x0 + k % kTile] = (y0 + r / kTile) * w + x0 + r % kTile;
+    }
+}
+
+// Unions across tile borders only (right column and bottom row of each tile).
+__global__ void k_cc_border(const uint2* __restrict__ fwd, const uint8_t* __restrict__ keep, int w, int h,
+                            int tau_r, int* parent) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= w) return;
+    const bool right = (x % kTile) == kTile - 1 && x + 1 < w;
+    const bool down = (y % kTile) == kTile - 1 && y + 1 < h;
+    if (!right && !down) return;
     const int i = y * w + x;
     if (!keep[i]) return;
     const uint2 a = fwd[i];
-    if (x + 1 < w && keep[i + 1] && close_vec(a, fwd[i + 1], tau_r)) unite(parent, i, i + 1);
-    if (y + 1 < h && keep[i + w] && close_vec(a, fwd[i + w], tau_r)) unite(parent, i, i + w);
+    if (right && keep[i + 1] && close_vec(a, fwd[i + 1], tau_r)) unite(parent, i, i + 1);
+    if (down && keep[i + w] && close_vec(a, fwd[i + w], tau_r)) unite(parent, i, i + w);
 }
 
+// Root of every kept pixel (written back to parent), component sizes with
+// one atomic per distinct root per warp, and the "a rejected neighbour
+// could join" flag.
 __global__ void k_cc_stats(const uint2* __restrict__ fwd, const int* __restrict__ fcost,
                            const uint8_t* __restrict__ keep, int w, int h, int tau_r, int* parent, int* size,
                            int* joinable) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    if (x >= w) return;
     const int i = y * w + x;
-    if (!keep[i]) return;
-    const int root = find_root(parent, i);
-    atomicAdd(size + root, 1);
-    const uint2 a = fwd[i];
-    const int nx[4] = {x + 1, x - 1, x, x};
-    const int ny[4] = {y, y, y + 1, y - 1};
+    const bool kept = x < w && keep[i];
+    int root = -1;
     bool join = false;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        if (nx[k] < 0 || nx[k] >= w || ny[k] < 0 || ny[k] >= h) continue;
-        const int j = ny[k] * w + nx[k];
-        if (!keep[j] && fcost[j] != kEmpty && close_vec(a, fwd[j], tau_r)) join = true;
+    if (kept) {
+        root = find_root(parent, i);
+        parent[i] = root;
+        const uint2 a = fwd[i];
+        if (x + 1 < w && !keep[i + 1] && fcost[i + 1] != kEmpty && close_vec(a, fwd[i + 1], tau_r)) join = true;
+        if (x > 0 && !keep[i - 1] && fcost[i - 1] != kEmpty && close_vec(a, fwd[i - 1], tau_r)) join = true;
+        if (y + 1 < h && !keep[i + w] && fcost[i + w] != kEmpty && close_vec(a, fwd[i + w], tau_r)) join = true;
+        if (y > 0 && !keep[i - w] && fcost[i - w] != kEmpty && close_vec(a, fwd[i - w], tau_r)) join = true;
     }
+    const unsigned peers = __match_any_sync(0xffffffffu, root);
+    const int lane = threadIdx.x & 31;
+    if (kept && lane == __ffs(peers) - 1) atomicAdd(size + root, __popc(peers));
     if (join) atomicOr(joinable + root, 1);
 }
 
-__global__ void k_cc_remove(uint8_t* __restrict__ keep, int np, const int* parent, const int* __restrict__ size,
-                            const int* __restrict__ joinable, int region_min) {
+__global__ void k_cc_remove(uint8_t* __restrict__ keep, int np, const int* __restrict__ parent,
+                            const int* __restrict__ size, const int* __restrict__ joinable, int region_min) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= np || !keep[i]) return;
-    const int root = find_root(parent, i);
+    const int root = parent[i];
     if (joinable[root] && size[root] < region_min) keep[i] = 0;
 }
 
@@ -155,8 +222,9 @@ extern "C" int sff_consistency_filter(const int16_t* fwd_dev, const int32_t* fwd
     const int g1 = (np + 255) / 256;
     SFF_LAUNCH(k_consistency, g2, b2, 0, st, fwd, fwd_cost_dev, inv, inv_cost_dev, width, height, params->tau_c, keep_dev,
                                      cerr_dev);
-    SFF_LAUNCH(k_cc_init, g1, 256, 0, st, keep_dev, np, parent, size, joinable);
-    SFF_LAUNCH(k_cc_union, g2, b2, 0, st, fwd, keep_dev, width, height, params->tau_r, parent);
+    dim3 gt((width + kTile - 1) / kTile, (height + kTile - 1) / kTile);
+    SFF_LAUNCH(k_cc_local, gt, 256, 0, st, fwd, keep_dev, width, height, params->tau_r, parent, size, joinable);
+    SFF_LAUNCH(k_cc_border, g2, b2, 0, st, fwd, keep_dev, width, height, params->tau_r, parent);
     SFF_LAUNCH(k_cc_stats, g2, b2, 0, st, fwd, fwd_cost_dev, keep_dev, width, height, params->tau_r, parent, size,
                                   joinable);
     SFF_LAUNCH(k_cc_remove, g1, 256, 0, st, keep_dev, np, parent, size, joinable, params->region_min);

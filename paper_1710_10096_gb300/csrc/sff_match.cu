@@ -30,7 +30,7 @@ namespace {
 
 constexpr int kKnnThreads = 128;
 constexpr int kKnnTile = 64;
-constexpr int kMaxParts = 8;
+constexpr int kMaxParts = 16;
 
 __device__ __forceinline__ bool less_di(int d, int i, int d2, int i2) { return d < d2 || (d == d2 && i < i2); }
 
@@ -75,17 +75,36 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn_partial(const uint8_t* __re
         __syncthreads();
         const int cnt = min(kKnnTile, c1 - base);
         if (active) {
-            for (int k = 0; k < cnt; ++k) {
-                int4 q0 = tile[k][0], q1 = tile[k][1], q2 = tile[k][2];
-                int nb = tile[k][3].x;
-                int dd = 0;
-                dd = __dp4a(r.a[0], q0.x, dd); dd = __dp4a(r.a[1], q0.y, dd);
-                dd = __dp4a(r.a[2], q0.z, dd); dd = __dp4a(r.a[3], q0.w, dd);
-                dd = __dp4a(r.a[4], q1.x, dd); dd = __dp4a(r.a[5], q1.y, dd);
-                dd = __dp4a(r.a[6], q1.z, dd); dd = __dp4a(r.a[7], q1.w, dd);
-                dd = __dp4a(r.a[8], q2.x, dd); dd = __dp4a(r.a[9], q2.y, dd);
-                dd = __dp4a(r.a[10], q2.z, dd); dd = __dp4a(r.a[11], q2.w, dd);
-                top8_insert(bd, bi, r.n + nb - 2 * dd, base + k);
+            int k = 0;
+            for (; k + 1 < cnt; k += 2) {  // two candidates: two independent dp4a chains
+                const int4 p0 = tile[k][0], p1 = tile[k][1], p2 = tile[k][2];
+                const int4 r0 = tile[k + 1][0], r1 = tile[k + 1][1], r2 = tile[k + 1][2];
+                int e = 0, f = 0;
+                e = __dp4a(r.a[0], p0.x, e); f = __dp4a(r.a[0], r0.x, f);
+                e = __dp4a(r.a[1], p0.y, e); f = __dp4a(r.a[1], r0.y, f);
+                e = __dp4a(r.a[2], p0.z, e); f = __dp4a(r.a[2], r0.z, f);
+                e = __dp4a(r.a[3], p0.w, e); f = __dp4a(r.a[3], r0.w, f);
+                e = __dp4a(r.a[4], p1.x, e); f = __dp4a(r.a[4], r1.x, f);
+                e = __dp4a(r.a[5], p1.y, e); f = __dp4a(r.a[5], r1.y, f);
+                e = __dp4a(r.a[6], p1.z, e); f = __dp4a(r.a[6], r1.z, f);
+                e = __dp4a(r.a[7], p1.w, e); f = __dp4a(r.a[7], r1.w, f);
+                e = __dp4a(r.a[8], p2.x, e); f = __dp4a(r.a[8], r2.x, f);
+                e = __dp4a(r.a[9], p2.y, e); f = __dp4a(r.a[9], r2.y, f);
+                e = __dp4a(r.a[10], p2.z, e); f = __dp4a(r.a[10], r2.z, f);
+                e = __dp4a(r.a[11], p2.w, e); f = __dp4a(r.a[11], r2.w, f);
+                top8_insert(bd, bi, r.n + tile[k][3].x - 2 * e, base + k);
+                top8_insert(bd, bi, r.n + tile[k + 1][3].x - 2 * f, base + k + 1);
+            }
+            if (k < cnt) {
+                const int4 p0 = tile[k][0], p1 = tile[k][1], p2 = tile[k][2];
+                int e = 0;
+                e = __dp4a(r.a[0], p0.x, e); e = __dp4a(r.a[1], p0.y, e);
+                e = __dp4a(r.a[2], p0.z, e); e = __dp4a(r.a[3], p0.w, e);
+                e = __dp4a(r.a[4], p1.x, e); e = __dp4a(r.a[5], p1.y, e);
+                e = __dp4a(r.a[6], p1.z, e); e = __dp4a(r.a[7], p1.w, e);
+                e = __dp4a(r.a[8], p2.x, e); e = __dp4a(r.a[9], p2.y, e);
+                e = __dp4a(r.a[10], p2.z, e); e = __dp4a(r.a[11], p2.w, e);
+                top8_insert(bd, bi, r.n + tile[k][3].x - 2 * e, base + k);
             }
         }
     }
@@ -96,29 +115,41 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn_partial(const uint8_t* __re
     }
 }
 
-// nearest grid point on row y (grid coordinates), constrained by sigma
-__device__ __forceinline__ void row_nearest(const RefFeat& r, const uint8_t* img, int w, int n, int gw, int y,
-                                            int xlim, int sigma, int& best_d, int& best_x) {
-    best_d = 0x7fffffff;
-    best_x = -1;
-    for (int g = 0; g < gw; ++g) {
-        int x = g * n;
+// Nearest grid point of row y by (distance, x), constrained by sigma, found by
+// one warp: lane l scans grid columns l, l+32, ...; then a warp argmin.
+__device__ __forceinline__ void warp_row_nearest(const RefFeat& r, const uint8_t* img, int w, int n, int gw, int y,
+                                                 int xlim, int sigma, int lane, int& best_d, int& best_x) {
+    int bd = 0x7fffffff, bx = 0x7fffffff;
+    for (int g = lane; g < gw; g += 32) {
+        const int x = g * n;
         if (sigma * (xlim - x) < 0) continue;
-        int d = ssd_rec(r, rec_at(img, w, x, y));
-        if (d < best_d) {  // ascending x: ties keep the lower raster index
-            best_d = d;
-            best_x = x;
+        const int d = ssd_rec(r, rec_at(img, w, x, y));
+        if (d < bd) {  // ascending x within the lane: ties keep the lower x
+            bd = d;
+            bx = x;
         }
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const int od = __shfl_xor_sync(0xffffffffu, bd, o), ox = __shfl_xor_sync(0xffffffffu, bx, o);
+        if (od < bd || (od == bd && ox < bx)) {
+            bd = od;
+            bx = ox;
+        }
+    }
+    best_d = bd;
+    best_x = bx;
 }
 
 __global__ void k_init_select(Views V, int n, int gw, int gq, int parts, int knn, const int2* __restrict__ partial,
                               uint2* __restrict__ field, int* __restrict__ cost) {
-    const int qi = blockIdx.x * blockDim.x + threadIdx.x;
-    if (qi >= gq) return;
+    const int qi = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (qi >= gq) return;  // warp-uniform
     const int px = (qi % gw) * n, py = (qi / gw) * n;
     RefFeat r;
     load_ref(rec_at(V.ref, V.w, px, py), r);
+    // merge the partial top-8 lists (every lane the same, reads broadcast)
     int bd[8], bi[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -129,21 +160,21 @@ __global__ void k_init_select(Views V, int n, int gw, int gq, int parts, int knn
         const int2* src = partial + ((size_t)p * gq + qi) * 8;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            int2 e = src[k];
+            const int2 e = src[k];
             if (e.x != 0x7fffffff) top8_insert(bd, bi, e.x, e.y);
         }
     }
     int ds, sx;
-    row_nearest(r, V.ste, V.w, n, gw, py, px, V.sigma, ds, sx);
+    warp_row_nearest(r, V.ste, V.w, n, gw, py, px, V.sigma, lane, ds, sx);
     int best_c = 0x7fffffff;
     Vec4 best = {0, 0, 0, 0};
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         if (k >= knn || bd[k] == 0x7fffffff) break;
         const int tx = (bi[k] % gw) * n, ty = (bi[k] / gw) * n;
-        int dx_, cx;
-        row_nearest(r, V.crs, V.w, n, gw, ty, tx, V.sigma, dx_, cx);
-        int c = bd[k] + ds + dx_;
+        int dxc, cx;
+        warp_row_nearest(r, V.crs, V.w, n, gw, ty, tx, V.sigma, lane, dxc, cx);
+        const int c = bd[k] + ds + dxc;
         if (c < best_c) {
             best_c = c;
             best.u = tx - px;
@@ -152,9 +183,11 @@ __global__ void k_init_select(Views V, int n, int gw, int gq, int parts, int knn
             best.d1 = V.sigma * (tx - cx);
         }
     }
-    const size_t i = (size_t)py * V.w + px;
-    field[i] = pack_vec(best);
-    cost[i] = best_c;
+    if (lane == 0) {
+        const size_t i = (size_t)py * V.w + px;
+        field[i] = pack_vec(best);
+        cost[i] = best_c;
+    }
 }
 
 __global__ void k_inherit(Views V, int n, int gw, int gh, uint2* __restrict__ field, int* __restrict__ cost) {
@@ -180,8 +213,41 @@ struct HalfStep {
     uint2 key;
 };
 
-__device__ __forceinline__ void random_search(const Views& V, const RefFeat& r, const HalfStep& H, int it, int x,
-                                              int y, uint32_t pix, Vec4& cur, int& c, bool& changed) {
+// k_half_step works with four lanes per pixel.  Lane q of a group holds
+// bytes 16q..16q+15 of the pixel's reference record (lanes 0-2: 16 feature
+// bytes each, lane 3: the norm) and loads the same quarter of every target
+// record, so one warp-wide 16-byte load fetches eight whole records.  The
+// partial sums of the three views are combined with two shuffles inside the
+// group: SSD = |a|^2 + |b|^2 - 2 a.b.
+constexpr int kLanes = 4;
+constexpr int kHalfThreads = 256;
+constexpr int kHalfPixels = kHalfThreads / kLanes;
+
+__device__ __forceinline__ int quarter_part(const int4& a, const uint8_t* rec, int q) {
+    const int4 t = __ldg(reinterpret_cast<const int4*>(rec) + q);
+    int d = __dp4a(a.x, t.x, 0);
+    d = __dp4a(a.y, t.y, d);
+    d = __dp4a(a.z, t.z, d);
+    d = __dp4a(a.w, t.w, d);
+    return q < 3 ? -2 * d : a.x + t.x;
+}
+
+__device__ __forceinline__ int group_cost(const Views& V, const int4& a, int q, unsigned gmask, int px, int py,
+                                          const Vec4& c) {
+    const int tx = clampi(px + c.u, 0, V.w - 1);
+    const int ty = clampi(py + c.v, 0, V.h - 1);
+    const int sx = clampi(px - V.sigma * c.d0, 0, V.w - 1);
+    const int cx = clampi(px + c.u - V.sigma * c.d1, 0, V.w - 1);
+    int part = quarter_part(a, rec_at(V.tmp, V.w, tx, ty), q) + quarter_part(a, rec_at(V.ste, V.w, sx, py), q) +
+               quarter_part(a, rec_at(V.crs, V.w, cx, ty), q);
+    part += __shfl_xor_sync(gmask, part, 1);
+    part += __shfl_xor_sync(gmask, part, 2);
+    return part;
+}
+
+__device__ __forceinline__ void random_search(const Views& V, const int4& a, int q, unsigned gmask,
+                                              const HalfStep& H, int it, int x, int y, uint32_t pix, Vec4& cur,
+                                              int& c, bool& changed) {
     uint4 rnd = philox4x32_10(make_uint4(pix, (uint32_t)it, (uint32_t)(H.s + 4 * H.mirror), 0u), H.key);
     Vec4 cand;
     cand.u = (int)(int16_t)(cur.u + rs_offset(rnd.x, H.n));
@@ -189,7 +255,7 @@ __device__ __forceinline__ void random_search(const Views& V, const RefFeat& r, 
     cand.d0 = (int)(int16_t)max(0, cur.d0 + rs_offset(rnd.z, H.n));
     cand.d1 = (int)(int16_t)max(0, cur.d1 + rs_offset(rnd.w, H.n));
     if (cand.u == cur.u && cand.v == cur.v && cand.d0 == cur.d0 && cand.d1 == cur.d1) return;
-    int cc = cost_of(V, r, x, y, cand.u, cand.v, cand.d0, cand.d1);
+    const int cc = group_cost(V, a, q, gmask, x, y, cand);
     if (cc < c) {
         c = cc;
         cur = cand;
@@ -197,51 +263,45 @@ __device__ __forceinline__ void random_search(const Views& V, const RefFeat& r, 
     }
 }
 
-__global__ void k_half_step(Views V, HalfStep H, uint2* __restrict__ field, int* __restrict__ cost) {
+__device__ __forceinline__ void try_neighbour(const Views& V, const int4& a, int q, unsigned gmask,
+                                              const uint2* field, const int* cost, size_t j, int x, int y, Vec4& cur,
+                                              int& c, bool& changed) {
+    const int cj = cost[j];
+    if (cj == kEmpty) return;
+    const Vec4 b = unpack_vec(field[j]);
+    const int cb = group_cost(V, a, q, gmask, x, y, b);
+    if (cb < c) {
+        c = cb;
+        cur = b;
+        changed = true;
+    }
+}
+
+__global__ void __launch_bounds__(kHalfThreads) k_half_step(Views V, HalfStep H, uint2* __restrict__ field,
+                                                             int* __restrict__ cost) {
+    const int q = threadIdx.x & (kLanes - 1);
+    const unsigned gmask = 0xFu << (threadIdx.x & 28);
     const int gy = blockIdx.y;
-    const int gx = 2 * (blockIdx.x * blockDim.x + threadIdx.x) + ((H.colour + gy) & 1);
-    if (gx >= H.gw) return;
+    const int gx = 2 * (blockIdx.x * kHalfPixels + (int)(threadIdx.x >> 2)) + ((H.colour + gy) & 1);
+    if (gx >= H.gw) return;  // the whole group leaves together
     const int x = gx * H.n, y = gy * H.n;
     const size_t i = (size_t)y * V.w + x;
     int c = cost[i];
     if (!H.prop && c == kEmpty) return;
     Vec4 cur = unpack_vec(field[i]);
-    RefFeat r;
-    load_ref(rec_at(V.ref, V.w, x, y), r);
+    const int4 a = __ldg(reinterpret_cast<const int4*>(rec_at(V.ref, V.w, x, y)) + q);
     bool changed = false;
-    if (H.rs_before >= 0 && c != kEmpty) random_search(V, r, H, H.rs_before, x, y, (uint32_t)i, cur, c, changed);
+    if (H.rs_before >= 0 && c != kEmpty)
+        random_search(V, a, q, gmask, H, H.rs_before, x, y, (uint32_t)i, cur, c, changed);
     if (H.prop) {
         const int ax = x - H.dx * H.n;
-        if (ax >= 0 && ax < V.w) {
-            const size_t j = (size_t)y * V.w + ax;
-            const int cj = cost[j];
-            if (cj != kEmpty) {
-                Vec4 a = unpack_vec(field[j]);
-                int ca = cost_of(V, r, x, y, a.u, a.v, a.d0, a.d1);
-                if (ca < c) {
-                    c = ca;
-                    cur = a;
-                    changed = true;
-                }
-            }
-        }
+        if (ax >= 0 && ax < V.w) try_neighbour(V, a, q, gmask, field, cost, (size_t)y * V.w + ax, x, y, cur, c, changed);
         const int by = y - H.dy * H.n;
-        if (by >= 0 && by < V.h) {
-            const size_t j = (size_t)by * V.w + x;
-            const int cj = cost[j];
-            if (cj != kEmpty) {
-                Vec4 b = unpack_vec(field[j]);
-                int cb = cost_of(V, r, x, y, b.u, b.v, b.d0, b.d1);
-                if (cb < c) {
-                    c = cb;
-                    cur = b;
-                    changed = true;
-                }
-            }
-        }
+        if (by >= 0 && by < V.h) try_neighbour(V, a, q, gmask, field, cost, (size_t)by * V.w + x, x, y, cur, c, changed);
     }
-    if (H.rs_after >= 0 && c != kEmpty) random_search(V, r, H, H.rs_after, x, y, (uint32_t)i, cur, c, changed);
-    if (changed) {
+    if (H.rs_after >= 0 && c != kEmpty)
+        random_search(V, a, q, gmask, H, H.rs_after, x, y, (uint32_t)i, cur, c, changed);
+    if (changed && q == 0) {
         field[i] = pack_vec(cur);
         cost[i] = c;
     }
@@ -249,7 +309,7 @@ __global__ void k_half_step(Views V, HalfStep H, uint2* __restrict__ field, int*
 
 int knn_parts(int gq) {
     int ctas = (gq + kKnnThreads - 1) / kKnnThreads;
-    int parts = (2 * 152 + ctas - 1) / ctas;
+    int parts = (4 * 152 + ctas - 1) / ctas;
     parts = parts < 1 ? 1 : (parts > kMaxParts ? kMaxParts : parts);
     while (parts > 1 && gq / parts < kKnnTile) --parts;
     return parts;
@@ -301,25 +361,25 @@ extern "C" int sff_match_views(const uint8_t* pyr_ref_dev, const uint8_t* pyr_te
             int2* partial = reinterpret_cast<int2*>(workspace);
             dim3 g1((gq + kKnnThreads - 1) / kKnnThreads, parts);
             SFF_LAUNCH(k_knn_partial, g1, kKnnThreads, 0, st, V.ref, V.tmp, width, n, gw, gq, parts, partial);
-            SFF_LAUNCH(k_init_select, (gq + 127) / 128, 128, 0, st, V, n, gw, gq, parts, params->knn_temporal, partial, field,
+            SFF_LAUNCH(k_init_select, (gq + 7) / 8, 256, 0, st, V, n, gw, gq, parts, params->knn_temporal, partial, field,
                                                             cost_dev);
         } else {
             dim3 g((gw + 127) / 128, gh);
             SFF_LAUNCH(k_inherit, g, 128, 0, st, V, n, gw, gh, field, cost_dev);
         }
         const int half_w = (gw + 1) / 2;
-        dim3 g((half_w + 127) / 128, gh);
+        dim3 g((half_w + kHalfPixels - 1) / kHalfPixels, gh);
         for (int it = 0; it < I; ++it) {
             HalfStep H{n, s, gw, 0, kDirs[it % 4][0], kDirs[it % 4][1], 1, it - 1, -1, mirror, key};
-            SFF_LAUNCH(k_half_step, g, 128, 0, st, V, H, field, cost_dev);
+            SFF_LAUNCH(k_half_step, g, kHalfThreads, 0, st, V, H, field, cost_dev);
             H.colour = 1;
             H.rs_before = -1;
             H.rs_after = it;
-            SFF_LAUNCH(k_half_step, g, 128, 0, st, V, H, field, cost_dev);
+            SFF_LAUNCH(k_half_step, g, kHalfThreads, 0, st, V, H, field, cost_dev);
         }
         if (I > 0) {
             HalfStep H{n, s, gw, 0, 0, 0, 0, I - 1, -1, mirror, key};
-            SFF_LAUNCH(k_half_step, g, 128, 0, st, V, H, field, cost_dev);
+            SFF_LAUNCH(k_half_step, g, kHalfThreads, 0, st, V, H, field, cost_dev);
         }
     }
     return launch_status();

@@ -2,11 +2,11 @@
 // kept match with the lowest consistency error (then cost, then raster
 // index), compacted in block raster order.
 //
-// k_block_best: one thread per block -> raster index of its best pixel or -1.
-// k_compact:    one CTA of 1024 threads: each thread counts the seeds of a
-//               contiguous run of blocks, a CTA-wide exclusive scan gives the
-//               run's output offset, then each thread writes its run in order.
-// Scratch (workspace): best[ceil(W/3) * ceil(H/3)] int32.
+// k_block_best:  one thread per block -> raster index of its best pixel or
+//                -1, and the number of seeds of each chunk of 256 blocks.
+// k_scan_chunks: one CTA: exclusive scan of the chunk counts, total count.
+// k_write_seeds: rank inside the chunk by warp ballots + chunk offset.
+// Scratch (workspace): best[ceil(W/3) * ceil(H/3)] and one int32 per chunk.
 #include <mutex>
 
 #include "sff_internal.cuh"
@@ -14,52 +14,59 @@
 namespace sff {
 namespace {
 
+constexpr int kChunk = 256;        // 3x3 blocks per CTA of k_block_best / k_write_seeds
 constexpr int kScanThreads = 1024;
 
-// Scratch of sff_emit_seeds_noalloc: one int32 per 3x3 block, in a static
-// device array so that the call needs no allocation.  Every device that
-// loads the library holds these 2 MiB until the process exits.
+// Scratch of sff_emit_seeds_noalloc, in a static device array so that the
+// call needs no allocation: one int32 per 3x3 block plus one per chunk of
+// 256 blocks.  Every device that loads the library holds it until exit.
 constexpr int kNoAllocMaxBlocks = SFF_NOALLOC_MAX_BLOCKS;
-__device__ __align__(256) int g_noalloc_best[kNoAllocMaxBlocks];
+constexpr int kNoAllocInts = kNoAllocMaxBlocks + kNoAllocMaxBlocks / kChunk;
+__device__ __align__(256) int g_noalloc_scratch[kNoAllocInts];
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 int* g_noalloc_ptr[kMaxDevices] = {};
 
-__global__ void k_block_best(const int* __restrict__ fcost, const uint8_t* __restrict__ keep,
-                             const uint8_t* __restrict__ cerr, int w, int h, int bw, int nb, int* __restrict__ best) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nb) return;
-    const int bx = (b % bw) * 3, by = (b / bw) * 3;
-    int bi = -1, be = 0, bc = 0;
-    for (int y = by; y < min(by + 3, h); ++y)
-        for (int x = bx; x < min(bx + 3, w); ++x) {
-            const int i = y * w + x;
-            if (!keep[i]) continue;
-            const int e = cerr[i], c = fcost[i];
-            if (bi < 0 || e < be || (e == be && c < bc)) {  // raster order: ties keep the earlier pixel
-                bi = i;
-                be = e;
-                bc = c;
+// One thread per block: raster index of its best kept pixel or -1; one count
+// of found seeds per CTA.
+__global__ void __launch_bounds__(kChunk) k_block_best(const int* __restrict__ fcost, const uint8_t* __restrict__ keep,
+                                                       const uint8_t* __restrict__ cerr, int w, int h, int bw, int nb,
+                                                       int* __restrict__ best, int* __restrict__ chunk_count) {
+    const int b = blockIdx.x * kChunk + threadIdx.x;
+    int bi = -1;
+    if (b < nb) {
+        const int bx = (b % bw) * 3, by = (b / bw) * 3;
+        int be = 0, bc = 0;
+        for (int y = by; y < min(by + 3, h); ++y)
+            for (int x = bx; x < min(bx + 3, w); ++x) {
+                const int i = y * w + x;
+                if (!keep[i]) continue;
+                const int e = cerr[i], c = fcost[i];
+                if (bi < 0 || e < be || (e == be && c < bc)) {  // raster order: ties keep the earlier pixel
+                    bi = i;
+                    be = e;
+                    bc = c;
+                }
             }
-        }
-    best[b] = bi;
+        best[b] = bi;
+    }
+    const int n = __syncthreads_count(bi >= 0);
+    if (threadIdx.x == 0) chunk_count[blockIdx.x] = n;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_compact(const int* __restrict__ best, int nb, const uint2* __restrict__ fwd,
-                                                         const int* __restrict__ fcost, const uint8_t* __restrict__ cerr,
-                                                         int w, sff_seed* __restrict__ out, int capacity,
-                                                         int* __restrict__ count) {
+// One CTA: exclusive scan of the chunk counts in place; the total to *count.
+__global__ void __launch_bounds__(kScanThreads) k_scan_chunks(int* __restrict__ chunk, int nchunks,
+                                                             int* __restrict__ count) {
     __shared__ int warp_sums[kScanThreads / 32];
     const int t = threadIdx.x;
-    const int per = (nb + kScanThreads - 1) / kScanThreads;
-    const int b0 = min(nb, t * per), b1 = min(nb, b0 + per);
+    const int per = (nchunks + kScanThreads - 1) / kScanThreads;
+    const int c0 = min(nchunks, t * per), c1 = min(nchunks, c0 + per);
     int mine = 0;
-    for (int b = b0; b < b1; ++b) mine += best[b] >= 0;
-    // inclusive scan within the warp, then across warps
+    for (int c = c0; c < c1; ++c) mine += chunk[c];
     int v = mine;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        int u = __shfl_up_sync(0xffffffffu, v, o);
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
         if ((t & 31) >= o) v += u;
     }
     if ((t & 31) == 31) warp_sums[t >> 5] = v;
@@ -68,38 +75,80 @@ __global__ void __launch_bounds__(kScanThreads) k_compact(const int* __restrict_
         int s = warp_sums[t];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            int u = __shfl_up_sync(0xffffffffu, s, o);
+            const int u = __shfl_up_sync(0xffffffffu, s, o);
             if (t >= o) s += u;
         }
         warp_sums[t] = s;  // inclusive over warps
     }
     __syncthreads();
     int pos = v - mine + ((t >> 5) ? warp_sums[(t >> 5) - 1] : 0);
-    for (int b = b0; b < b1; ++b) {
-        const int i = best[b];
-        if (i < 0) continue;
-        if (pos < capacity) {
-            const Vec4 a = unpack_vec(fwd[i]);
-            sff_seed sd;
-            sd.x = (int16_t)(i % w);
-            sd.y = (int16_t)(i / w);
-            sd.u = (int16_t)a.u;
-            sd.v = (int16_t)a.v;
-            sd.d0 = (int16_t)a.d0;
-            sd.d1 = (int16_t)a.d1;
-            sd.cost = fcost[i];
-            sd.cerr = cerr[i];
-            sd.pad[0] = sd.pad[1] = sd.pad[2] = 0;
-            out[pos] = sd;
-        }
-        ++pos;
+    for (int c = c0; c < c1; ++c) {
+        const int k = chunk[c];
+        chunk[c] = pos;
+        pos += k;
     }
     if (t == kScanThreads - 1) *count = pos;
 }
 
+// Same grid as k_block_best: rank of each found seed inside its CTA (warp
+// ballots + warp offsets) plus the chunk offset gives its output slot.
+__global__ void __launch_bounds__(kChunk) k_write_seeds(const int* __restrict__ best, int nb,
+                                                        const int* __restrict__ chunk_off,
+                                                        const uint2* __restrict__ fwd, const int* __restrict__ fcost,
+                                                        const uint8_t* __restrict__ cerr, int w,
+                                                        sff_seed* __restrict__ out, int capacity) {
+    __shared__ int warp_base[kChunk / 32];
+    const int b = blockIdx.x * kChunk + threadIdx.x;
+    const int i = b < nb ? best[b] : -1;
+    const unsigned ballot = __ballot_sync(0xffffffffu, i >= 0);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) warp_base[wid] = __popc(ballot);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int k = 0; k < kChunk / 32; ++k) {
+            const int n = warp_base[k];
+            warp_base[k] = acc;
+            acc += n;
+        }
+    }
+    __syncthreads();
+    if (i < 0) return;
+    const int pos = chunk_off[blockIdx.x] + warp_base[wid] + __popc(ballot & ((1u << lane) - 1u));
+    if (pos >= capacity) return;
+    const Vec4 a = unpack_vec(fwd[i]);
+    sff_seed sd;
+    sd.x = (int16_t)(i % w);
+    sd.y = (int16_t)(i / w);
+    sd.u = (int16_t)a.u;
+    sd.v = (int16_t)a.v;
+    sd.d0 = (int16_t)a.d0;
+    sd.d1 = (int16_t)a.d1;
+    sd.cost = fcost[i];
+    sd.cerr = cerr[i];
+    sd.pad[0] = sd.pad[1] = sd.pad[2] = 0;
+    out[pos] = sd;
+}
+
+int launch_seeds(const int16_t* fwd_dev, const int32_t* fwd_cost_dev, const uint8_t* keep_dev,
+                 const uint8_t* cerr_dev, int width, int height, sff_seed* seeds_dev, int capacity, int* count_dev,
+                 int* best, int* chunk, cudaStream_t st) {
+    const int bw = (width + 2) / 3, nb = bw * ((height + 2) / 3);
+    const int nchunks = (nb + kChunk - 1) / kChunk;
+    SFF_LAUNCH(k_block_best, nchunks, kChunk, 0, st, fwd_cost_dev, keep_dev, cerr_dev, width, height, bw, nb, best,
+               chunk);
+    SFF_LAUNCH(k_scan_chunks, 1, kScanThreads, 0, st, chunk, nchunks, count_dev);
+    SFF_LAUNCH(k_write_seeds, nchunks, kChunk, 0, st, best, nb, chunk, reinterpret_cast<const uint2*>(fwd_dev),
+               fwd_cost_dev, cerr_dev, width, seeds_dev, capacity);
+    return launch_status();
+}
+
 }  // namespace
 
-size_t seeds_ws_bytes(int w, int h) { return align256((size_t)((w + 2) / 3) * ((h + 2) / 3) * sizeof(int)); }
+size_t seeds_ws_bytes(int w, int h) {
+    const size_t nb = (size_t)((w + 2) / 3) * ((h + 2) / 3);
+    return align256(nb * sizeof(int)) + align256((nb + kChunk - 1) / kChunk * sizeof(int));
+}
 
 }  // namespace sff
 
@@ -114,13 +163,11 @@ extern "C" int sff_emit_seeds(const int16_t* fwd_dev, const int32_t* fwd_cost_de
     if (capacity > 0 && !seeds_dev) return SFF_ERR_ARG;
     if (((uintptr_t)fwd_dev & 7) || ((uintptr_t)seeds_dev & 3) || ((uintptr_t)workspace & 255)) return SFF_ERR_ARG;
     if (workspace_bytes < seeds_ws_bytes(width, height)) return SFF_ERR_WORKSPACE;
-    cudaStream_t st = (cudaStream_t)stream;
-    const int bw = (width + 2) / 3, nb = bw * ((height + 2) / 3);
+    const size_t nb = (size_t)((width + 2) / 3) * ((height + 2) / 3);
     int* best = reinterpret_cast<int*>(workspace);
-    SFF_LAUNCH(k_block_best, (nb + 255) / 256, 256, 0, st, fwd_cost_dev, keep_dev, cerr_dev, width, height, bw, nb, best);
-    SFF_LAUNCH(k_compact, 1, kScanThreads, 0, st, best, nb, reinterpret_cast<const uint2*>(fwd_dev), fwd_cost_dev, cerr_dev,
-                                          width, seeds_dev, capacity, count_dev);
-    return launch_status();
+    int* chunk = reinterpret_cast<int*>((char*)workspace + align256(nb * sizeof(int)));
+    return launch_seeds(fwd_dev, fwd_cost_dev, keep_dev, cerr_dev, width, height, seeds_dev, capacity, count_dev,
+                        best, chunk, (cudaStream_t)stream);
 }
 
 extern "C" int sff_emit_seeds_noalloc(const int16_t* fwd_dev, const int32_t* fwd_cost_dev, const uint8_t* keep_dev,
@@ -131,29 +178,25 @@ extern "C" int sff_emit_seeds_noalloc(const int16_t* fwd_dev, const int32_t* fwd
     if (!fwd_dev || !fwd_cost_dev || !keep_dev || !cerr_dev || !count_dev || capacity < 0) return SFF_ERR_ARG;
     if (capacity > 0 && !seeds_dev) return SFF_ERR_ARG;
     if (((uintptr_t)fwd_dev & 7) || ((uintptr_t)seeds_dev & 3)) return SFF_ERR_ARG;
-    const int bw = (width + 2) / 3, nb = bw * ((height + 2) / 3);
+    const int nb = ((width + 2) / 3) * ((height + 2) / 3);
     if (nb > kNoAllocMaxBlocks) return SFF_ERR_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return SFF_ERR_CUDA;
     if (dev < 0 || dev >= kMaxDevices) return SFF_ERR_ARG;
-    int* best = nullptr;
+    int* scratch = nullptr;
     {
         // Host code cannot use the array's name as a device address: look the
         // address up once per device, with that device current.
         std::lock_guard<std::mutex> lk(g_noalloc_mu);
         if (!g_noalloc_ptr[dev]) {
             void* p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_best) != cudaSuccess || !p) return SFF_ERR_CUDA;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SFF_ERR_CUDA;
             g_noalloc_ptr[dev] = static_cast<int*>(p);
         }
-        best = g_noalloc_ptr[dev];
+        scratch = g_noalloc_ptr[dev];
     }
-    cudaStream_t st = (cudaStream_t)stream;
-    // k_block_best writes every one of the nb entries before k_compact reads
-    // them, so the array needs no clearing between calls.
-    SFF_LAUNCH(k_block_best, (nb + 255) / 256, 256, 0, st, fwd_cost_dev, keep_dev, cerr_dev, width, height, bw, nb,
-               best);
-    SFF_LAUNCH(k_compact, 1, kScanThreads, 0, st, best, nb, reinterpret_cast<const uint2*>(fwd_dev), fwd_cost_dev,
-               cerr_dev, width, seeds_dev, capacity, count_dev);
-    return launch_status();
+    // Every scratch entry a call reads is written earlier in the same call
+    // (block bests and chunk counts by k_block_best), so nothing is cleared.
+    return launch_seeds(fwd_dev, fwd_cost_dev, keep_dev, cerr_dev, width, height, seeds_dev, capacity, count_dev,
+                        scratch, scratch + kNoAllocMaxBlocks, (cudaStream_t)stream);
 }

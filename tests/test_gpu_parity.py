@@ -105,8 +105,8 @@ def test_match_views_planes_scene(env, seed):
         assert np.array_equal(gf, of)
 
 
-def _run_gpu_quad(torch, sff, q, seed, p=None):
-    m = sff.QuadMatcher(q.width, q.height, p)
+def _run_gpu_quad(torch, sff, q, seed, p=None, concurrent=True):
+    m = sff.QuadMatcher(q.width, q.height, p, concurrent=concurrent)
     dev = [torch.as_tensor(im).cuda() for im in q.images()]
     seeds, count = m.run(*dev, seed=seed)
     torch.cuda.synchronize()
@@ -125,11 +125,12 @@ def _assert_quad_equal(m, got_seeds, n, ref):
     assert got_seeds.tobytes() == ref["seeds"].tobytes()
 
 
-@pytest.mark.parametrize("name,seed", [("planes_256x80", 1), ("planes_256x80", 5)])
-def test_full_stage_small(env, name, seed):
+@pytest.mark.parametrize("name,seed,concurrent", [("planes_256x80", 1, True), ("planes_256x80", 5, True),
+                                                  ("planes_256x80", 5, False)])
+def test_full_stage_small(env, name, seed, concurrent):
     torch, sff, orc = env
     q = scenegen.make_named(name, seed)
-    m, got, n = _run_gpu_quad(torch, sff, q, seed=seed)
+    m, got, n = _run_gpu_quad(torch, sff, q, seed=seed, concurrent=concurrent)
     ref = orc.run_quad(*q.images(), seed=seed)
     _assert_quad_equal(m, got, n, ref)
 
