@@ -39,10 +39,10 @@ FALLBACK_HBM_GBS = 6800.0
 
 # Algorithmic bytes per unit of work of each kernel (units in `_units`):
 #   k_half_step   per active grid pixel: own + written state 24 B, reference
-#                 record 64 B, one 64 B target record per view (3 views)
-#   k_features    per pixel and scale: packed smoothed pixel 4 B in, 64 B record out
-#   k_smooth      per pixel: 3 B in, 4 B out per scale
-ALGO_BYTES = {"k_half_step": 24 + 64 + 3 * 64, "k_features": 4 + 64}
+#                 record 48 B + norm 4 B, one 52 B target record per view
+#   k_features    per pixel and scale: packed smoothed pixel 4 B in, 48 B
+#                 record + 4 B norm out
+ALGO_BYTES = {"k_half_step": 24 + 52 + 3 * 52, "k_features": 4 + 52}
 
 
 def parse():

@@ -52,7 +52,8 @@ extern "C" {
 #define SFF_ERR_WORKSPACE (-3)  /* workspace smaller than sff_workspace_bytes() */
 
 #define SFF_FEATURES 48         /* int8 features per pixel and scale: 3 channels x 16 */
-#define SFF_RECORD_BYTES 64     /* bytes per pixel and scale in a pyramid */
+#define SFF_FEATURE_BYTES 48    /* bytes of one feature record */
+#define SFF_PYRAMID_PIXEL_BYTES 52 /* pyramid bytes per pixel and scale: record + int32 norm */
 #define SFF_MAX_SCALES 4
 #define SFF_MAX_KNN 8
 #define SFF_EMPTY_COST 2147483647 /* cost of a pixel that holds no vector yet */
@@ -82,10 +83,10 @@ typedef struct sff_seed {
 /* Fills *out with the default parameters.  Returns SFF_ERR_ARG if out is NULL. */
 int sff_default_params(sff_params* out);
 
-/* Bytes of one image's feature pyramid: num_scales * H * W * 64.
- * Layout [scale][y][x] of 64-byte records: bytes 0..47 the int8 features
- * (channel-major, 16 coefficients per channel in the order of sff_features),
- * bytes 48..51 the int32 sum of squared features, bytes 52..63 zero.
+/* Bytes of one image's feature pyramid: num_scales * H * W * 52.
+ * Layout: [scale][y][x] 48-byte records of int8 features (channel-major, 16
+ * coefficients per channel in the order of sff_features), followed by
+ * [scale][y][x] int32 norms (the sum of squared features of each record).
  * Returns 0 for invalid arguments. */
 size_t sff_pyramid_bytes(int32_t width, int32_t height, const sff_params* params);
 
@@ -142,6 +143,19 @@ int sff_match_views(const uint8_t* pyr_ref_dev, const uint8_t* pyr_temporal_dev,
                     int32_t width, int32_t height, int32_t mirror, uint64_t seed,
                     const sff_params* params, int16_t* field_dev, int32_t* cost_dev,
                     void* workspace, size_t workspace_bytes, void* stream);
+
+/* Both fields of a quad in one pass (Sec. 3.1: the matching field of L0 and
+ * the inverse field of R1 used by "Consistency Check").  Identical results to
+ *   sff_match_views(L0, L1, R0, R1, mirror 0) -> fwd, fwd_cost
+ *   sff_match_views(R1, R0, L1, L0, mirror 1) -> inv, inv_cost
+ * with the same seed and params; the two fields share every kernel launch
+ * (half the launches, one L2 fill of each scale's features for both).
+ * pyr_*_dev: pyramids of L0, R0, L1, R1; outputs as in sff_match_views. */
+int sff_match_quad(const uint8_t* pyr_l0_dev, const uint8_t* pyr_r0_dev,
+                   const uint8_t* pyr_l1_dev, const uint8_t* pyr_r1_dev,
+                   int32_t width, int32_t height, uint64_t seed, const sff_params* params,
+                   int16_t* fwd_dev, int32_t* fwd_cost_dev, int16_t* inv_dev, int32_t* inv_cost_dev,
+                   void* workspace, size_t workspace_bytes, void* stream);
 
 /* Consistency check and region filter (Sec. 3.1, "Consistency Check").
  *   For L0 pixel p with forward vector u, q = p + (u - d1, v) in R1 and w the

@@ -23,7 +23,7 @@ __all__ = ["Params", "SffError", "default_params", "pyramid_bytes", "workspace_b
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsff.so")
 EMPTY_COST = 2147483647
-RECORD_BYTES = 64
+FEATURE_BYTES = 48
 _lib = None
 
 
@@ -90,6 +90,8 @@ def lib():
         L.sff_features.restype = i32
         L.sff_match_views.argtypes = [P, P, P, P, i32, i32, i32, ctypes.c_uint64, PP, P, P, P, sz, P]
         L.sff_match_views.restype = i32
+        L.sff_match_quad.argtypes = [P, P, P, P, i32, i32, ctypes.c_uint64, PP, P, P, P, P, P, sz, P]
+        L.sff_match_quad.restype = i32
         L.sff_consistency_filter.argtypes = [P, P, P, P, i32, i32, PP, P, P, P, sz, P]
         L.sff_consistency_filter.restype = i32
         L.sff_emit_seeds.argtypes = [P, P, P, P, i32, i32, P, i32, P, P, sz, P]
@@ -163,6 +165,26 @@ def match_views(pyr_ref, pyr_temporal, pyr_stereo, pyr_cross, width: int, height
            "sff_match_views")
 
 
+def match_quad(pyr_l0, pyr_r0, pyr_l1, pyr_r1, width: int, height: int, seed: int, fwd, fwd_cost, inv, inv_cost,
+               workspace, params: Params = None, stream=None) -> None:
+    """sff_match_quad: forward field of L0 and inverse field of R1 in shared launches."""
+    params = params or default_params()
+    _check(lib().sff_match_quad(_ptr(pyr_l0), _ptr(pyr_r0), _ptr(pyr_l1), _ptr(pyr_r1), width, height,
+                                int(seed) & (2 ** 64 - 1), ctypes.byref(params), _ptr(fwd), _ptr(fwd_cost), _ptr(inv),
+                                _ptr(inv_cost), _ptr(workspace), _nbytes(workspace), _stream(stream)),
+           "sff_match_quad")
+
+
+def split_pyramid(pyr, width: int, height: int, params: Params = None):
+    """(features [S, H, W, 48] int8, norms [S, H, W] int32) views of a pyramid buffer."""
+    import torch
+    params = params or default_params()
+    S, np_ = params.num_scales, width * height
+    feat = pyr[:S * np_ * FEATURE_BYTES].view(torch.int8).view(S, height, width, FEATURE_BYTES)
+    norm = pyr[S * np_ * FEATURE_BYTES:S * np_ * (FEATURE_BYTES + 4)].view(torch.int32).view(S, height, width)
+    return feat, norm
+
+
 def consistency_filter(fwd, fwd_cost, inv, inv_cost, keep, cerr, workspace, params: Params = None,
                        stream=None) -> None:
     params = params or default_params()
@@ -208,8 +230,9 @@ class QuadMatcher:
             raise SffError(f"invalid size {w}x{h} or parameters")
         u8 = dict(dtype=torch.uint8, device=self.device)
         self.pyr = [torch.empty(pb, **u8) for _ in range(4)]  # L0, R0, L1, R1
-        # one workspace per concurrent stream: features of the four images run
-        # on four streams, the forward and inverse fields on two
+        # one workspace per concurrent stream: the features of the four images
+        # run on four streams; both fields then share the launches of
+        # sff_match_quad
         self.workspaces = [torch.empty(wb, **u8) for _ in range(4 if concurrent else 1)]
         self.workspace = self.workspaces[0]
         self._side = [torch.cuda.Stream(device=self.device) for _ in range(3)] if concurrent else []
@@ -249,16 +272,8 @@ class QuadMatcher:
                 done = torch.cuda.Event()
                 done.record(st)
                 main.wait_event(done)
-            fork2 = torch.cuda.Event()
-            fork2.record(main)
-            self._side[0].wait_event(fork2)
-            match_views(pL0, pL1, pR0, pR1, self.width, self.height, 0, seed, self.fwd, self.fwd_cost,
-                        self.workspaces[0], p, main)
-            match_views(pR1, pR0, pL1, pL0, self.width, self.height, 1, seed, self.inv, self.inv_cost,
-                        self.workspaces[1], p, self._side[0])
-            join = torch.cuda.Event()
-            join.record(self._side[0])
-            main.wait_event(join)
+            match_quad(pL0, pR0, pL1, pR1, self.width, self.height, seed, self.fwd, self.fwd_cost, self.inv,
+                       self.inv_cost, self.workspace, p, main)
         consistency_filter(self.fwd, self.fwd_cost, self.inv, self.inv_cost, self.keep, self.cerr, self.workspace,
                            p, main)
         emit_seeds(self.fwd, self.fwd_cost, self.keep, self.cerr, self.seeds, self.capacity, self.count,

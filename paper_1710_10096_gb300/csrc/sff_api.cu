@@ -39,7 +39,7 @@ extern "C" int sff_default_params(sff_params* out) {
 
 extern "C" size_t sff_pyramid_bytes(int32_t width, int32_t height, const sff_params* params) {
     if (sff::check_size(width, height) || sff::check_params(params)) return 0;
-    return (size_t)params->num_scales * width * height * SFF_RECORD_BYTES;
+    return (size_t)params->num_scales * width * height * SFF_PYRAMID_PIXEL_BYTES;
 }
 
 extern "C" size_t sff_workspace_bytes(int32_t width, int32_t height, const sff_params* params) {

@@ -9,7 +9,7 @@
 //             R + 65536 G (every intermediate stays below 2^31 in magnitude,
 //             so packed adds and subtracts are exact).  The 16 kept
 //             coefficients are read out through the sequency->natural index
-//             map, quantised and written as one 64-byte record.
+//             map, quantised and written as one 48-byte record plus its norm.
 #include "sff_internal.cuh"
 
 namespace sff {
@@ -71,7 +71,7 @@ __device__ __forceinline__ void fwht8(int (&a)[8]) {
 __device__ __forceinline__ int lo16(int x) { return (x << 16) >> 16; }
 
 __global__ void k_features(const uint32_t* __restrict__ sm, int w, int h, int s, int qshift,
-                           uint8_t* __restrict__ out) {
+                           uint8_t* __restrict__ out, int* __restrict__ norm_out) {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y;
     if (x >= w) return;
@@ -135,16 +135,16 @@ __global__ void k_features(const uint32_t* __restrict__ sm, int w, int h, int s,
             norm += v * v;
         }
     }
-    int words[16];
+    int words[12];
 #pragma unroll
     for (int k = 0; k < 12; ++k)
         words[k] = (int)((uint32_t)(uint8_t)f[4 * k] | ((uint32_t)(uint8_t)f[4 * k + 1] << 8) |
                          ((uint32_t)(uint8_t)f[4 * k + 2] << 16) | ((uint32_t)(uint8_t)f[4 * k + 3] << 24));
-    words[12] = norm;
-    words[13] = words[14] = words[15] = 0;
-    int4* dst = reinterpret_cast<int4*>(out + ((size_t)y * w + x) * kRec);
+    const size_t i = (size_t)y * w + x;
+    int4* dst = reinterpret_cast<int4*>(out + i * kFeat);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) dst[k] = make_int4(words[4 * k], words[4 * k + 1], words[4 * k + 2], words[4 * k + 3]);
+    for (int k = 0; k < 3; ++k) dst[k] = make_int4(words[4 * k], words[4 * k + 1], words[4 * k + 2], words[4 * k + 3]);
+    norm_out[i] = norm;
 }
 
 }  // namespace
@@ -167,8 +167,10 @@ extern "C" int sff_features(const uint8_t* rgb_dev, int32_t width, int32_t heigh
     uint32_t* sm = (uint32_t*)workspace;
     dim3 blk(128), grd((width + 127) / 128, height);
     SFF_LAUNCH(k_smooth, grd, blk, 0, st, rgb_dev, pitch_bytes, width, height, params->num_scales, sm);
+    const size_t np = (size_t)width * height;
+    int* norms = reinterpret_cast<int*>(pyramid_dev + (size_t)params->num_scales * np * kFeat);
     for (int s = 0; s < params->num_scales; ++s)
-        SFF_LAUNCH(k_features, grd, blk, 0, st, sm + (size_t)s * width * height, width, height, s, params->quant_shift,
-                                        pyramid_dev + (size_t)s * width * height * kRec);
+        SFF_LAUNCH(k_features, grd, blk, 0, st, sm + s * np, width, height, s, params->quant_shift,
+                   pyramid_dev + s * np * kFeat, norms + s * np);
     return launch_status();
 }

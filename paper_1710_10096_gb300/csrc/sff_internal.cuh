@@ -1,9 +1,10 @@
 // Internal definitions shared by the CUDA translation units of libsff.
 //
-// Data layout in HBM (one quad of W x H images):
-//   pyramid  [scale][y][x] 64-byte records: 48 int8 WHT features, int32 norm
-//            (sum of squared features), 12 zero bytes.  A record is two
-//            32-byte sectors, so one candidate lookup costs exactly 2 sectors.
+// Data layout in HBM (one quad of W x H images, S scales):
+//   pyramid  [scale][y][x] 48-byte feature records (int8, channel-major),
+//            then [scale][y][x] int32 norms (sum of squared features).
+//            Three 16-byte loads fetch a record; the norms of neighbouring
+//            pixels share cache lines.
 //   field    [y][x] int16x4 (u, v, d0, d1): one 8-byte load per pixel.
 //   cost     [y][x] int32, SFF_EMPTY_COST where no vector is held yet.
 #pragma once
@@ -15,12 +16,26 @@
 
 namespace sff {
 
-constexpr int kRec = SFF_RECORD_BYTES;
+constexpr int kFeat = SFF_FEATURE_BYTES;
 constexpr int kEmpty = SFF_EMPTY_COST;
 
 __host__ __device__ __forceinline__ int clampi(int a, int lo, int hi) { return a < lo ? lo : (a > hi ? hi : a); }
 
 __host__ __device__ __forceinline__ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// One image at one scale: its feature records and norms.
+struct Plane {
+    const uint8_t* f;
+    const int* nrm;
+};
+
+__host__ __device__ __forceinline__ Plane plane_of(const uint8_t* pyr, int s, int S, int w, int h) {
+    const size_t np = (size_t)w * h;
+    Plane P;
+    P.f = pyr + (size_t)s * np * kFeat;
+    P.nrm = reinterpret_cast<const int*>(pyr + (size_t)S * np * kFeat) + (size_t)s * np;
+    return P;
+}
 
 // Reference feature held in registers: 12 packed int8x4 words and the norm.
 struct RefFeat {
@@ -28,21 +43,21 @@ struct RefFeat {
     int n;
 };
 
-__device__ __forceinline__ void load_ref(const uint8_t* rec, RefFeat& r) {
-    const int4* p = reinterpret_cast<const int4*>(rec);
+__device__ __forceinline__ void load_ref(const Plane& P, size_t i, RefFeat& r) {
+    const int4* p = reinterpret_cast<const int4*>(P.f + i * kFeat);
     int4 q0 = __ldg(p), q1 = __ldg(p + 1), q2 = __ldg(p + 2);
     r.a[0] = q0.x; r.a[1] = q0.y; r.a[2] = q0.z; r.a[3] = q0.w;
     r.a[4] = q1.x; r.a[5] = q1.y; r.a[6] = q1.z; r.a[7] = q1.w;
     r.a[8] = q2.x; r.a[9] = q2.y; r.a[10] = q2.z; r.a[11] = q2.w;
-    r.n = __ldg(reinterpret_cast<const int*>(rec + 48));
+    r.n = __ldg(P.nrm + i);
 }
 
 // Sum of squared differences of two int8 feature vectors, as
 // |a|^2 + |b|^2 - 2 a.b with the dot product on dp4a (exact in int32).
-__device__ __forceinline__ int ssd_rec(const RefFeat& r, const uint8_t* rec) {
-    const int4* p = reinterpret_cast<const int4*>(rec);
+__device__ __forceinline__ int ssd_at(const RefFeat& r, const Plane& P, size_t i) {
+    const int4* p = reinterpret_cast<const int4*>(P.f + i * kFeat);
     int4 q0 = __ldg(p), q1 = __ldg(p + 1), q2 = __ldg(p + 2);
-    int nb = __ldg(reinterpret_cast<const int*>(rec + 48));
+    int nb = __ldg(P.nrm + i);
     int d = 0;
     d = __dp4a(r.a[0], q0.x, d); d = __dp4a(r.a[1], q0.y, d);
     d = __dp4a(r.a[2], q0.z, d); d = __dp4a(r.a[3], q0.w, d);
@@ -53,18 +68,13 @@ __device__ __forceinline__ int ssd_rec(const RefFeat& r, const uint8_t* rec) {
     return r.n + nb - 2 * d;
 }
 
-// The four views of one field at one scale (record pointers of that scale).
+// The four views of one field at one scale.
 struct Views {
-    const uint8_t* ref;
-    const uint8_t* tmp;
-    const uint8_t* ste;
-    const uint8_t* crs;
+    Plane ref, tmp, ste, crs;
     int w, h, sigma;
 };
 
-__device__ __forceinline__ const uint8_t* rec_at(const uint8_t* base, int w, int x, int y) {
-    return base + ((size_t)y * w + x) * kRec;
-}
+__device__ __forceinline__ size_t pix(int w, int x, int y) { return (size_t)y * w + x; }
 
 // Eq. 1 with WHT-feature SSD: temporal p+(u,v), stereo p+(-sigma d0, 0),
 // cross p+(u - sigma d1, v), positions clamped to the image.
@@ -74,8 +84,8 @@ __device__ __forceinline__ int cost_of(const Views& V, const RefFeat& r, int px,
     int ty = clampi(py + v, 0, V.h - 1);
     int sx = clampi(px - V.sigma * d0, 0, V.w - 1);
     int cx = clampi(px + u - V.sigma * d1, 0, V.w - 1);
-    return ssd_rec(r, rec_at(V.tmp, V.w, tx, ty)) + ssd_rec(r, rec_at(V.ste, V.w, sx, py)) +
-           ssd_rec(r, rec_at(V.crs, V.w, cx, ty));
+    return ssd_at(r, V.tmp, pix(V.w, tx, ty)) + ssd_at(r, V.ste, pix(V.w, sx, py)) +
+           ssd_at(r, V.crs, pix(V.w, cx, ty));
 }
 
 // Field element pack/unpack: int16x4 in one 64-bit word.

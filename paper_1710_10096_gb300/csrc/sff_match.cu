@@ -1,28 +1,36 @@
-// One dense scene-flow field: exact nearest-neighbour initialisation on the
+// Dense scene-flow fields: exact nearest-neighbour initialisation on the
 // coarsest grid, then per scale inheritance + propagation half-steps with
 // random search (Sec. 3.1, "Initialization", "Multi-Scale Propagation").
+//
+// Every kernel works on one or two fields at once (blockIdx.z): the forward
+// field of L0 and the inverse field of R1 read the same four pyramids, so
+// running them in the same launches halves the launch count, doubles the
+// parallelism of the small coarse-scale launches and lets one L2 fill of a
+// scale's features serve both fields.
 //
 // k_knn_partial:  temporal K-NN, all-pairs over the coarsest grid; candidate
 //                 tiles staged in shared memory and broadcast to the 128
 //                 queries of a CTA; candidates split over blockIdx.y so the
 //                 grid covers the SMs.  Each thread keeps a sorted top-8 of
 //                 (distance, grid index) in registers.
-// k_init_select:  merges the partial top-8 lists, finds the nearest epipolar
-//                 stereo / cross points and keeps the best combination.  The
-//                 cost is the sum of the three independent distances, so for a
-//                 given temporal leaf the first-ranked epipolar leaves give
-//                 the lowest cost and win every tie; the result equals scoring
-//                 all K_T x K_E x K_E combinations in order.
+// k_init_select:  one warp per query: merges the partial top-8 lists, finds
+//                 the nearest epipolar stereo / cross points and keeps the
+//                 best combination.  The cost is the sum of the three
+//                 independent distances, so for a given temporal leaf the
+//                 first-ranked epipolar leaves give the lowest cost and win
+//                 every tie; the result equals scoring all K_T x K_E x K_E
+//                 combinations in order.
 // k_inherit:      grid points of the coarser scale keep their vector and are
 //                 re-scored at this scale; the others start empty.
-// k_half_step:    one colour of the checkerboard.  Fused with the random
-//                 search of that colour: the search after iteration i of
-//                 colour 1 runs at the end of its half-step of iteration i,
-//                 the search of colour 0 at the start of its half-step of
-//                 iteration i+1 (or in a final pass).  Both orders read the
-//                 same values as the plain order "half-step 0, half-step 1,
-//                 random search", because a half-step only reads the other
-//                 colour and the search only reads the pixel itself.
+// k_half_step:    one colour of the checkerboard, four lanes per pixel.
+//                 Fused with the random search of that colour: the search
+//                 after iteration i of colour 1 runs at the end of its
+//                 half-step of iteration i, the search of colour 0 at the
+//                 start of its half-step of iteration i+1 (or in a final
+//                 pass).  Both orders read the same values as the plain order
+//                 "half-step 0, half-step 1, random search", because a
+//                 half-step only reads the other colour and the search only
+//                 reads the pixel itself.
 #include "sff_internal.cuh"
 
 namespace sff {
@@ -31,6 +39,20 @@ namespace {
 constexpr int kKnnThreads = 128;
 constexpr int kKnnTile = 64;
 constexpr int kMaxParts = 16;
+
+// One field: its views at the current scale and its output.
+struct Field {
+    Views V;
+    uint2* field;
+    int* cost;
+    int mirror;
+};
+
+struct Fields {
+    Field f[2];
+};
+
+__device__ __forceinline__ const Field& pick(const Fields& F) { return blockIdx.z ? F.f[1] : F.f[0]; }
 
 __device__ __forceinline__ bool less_di(int d, int i, int d2, int i2) { return d < d2 || (d == d2 && i < i2); }
 
@@ -49,14 +71,24 @@ __device__ __forceinline__ void top8_insert(int (&d)[8], int (&id)[8], int nd, i
     }
 }
 
-__global__ void __launch_bounds__(kKnnThreads) k_knn_partial(const uint8_t* __restrict__ ref,
-                                                              const uint8_t* __restrict__ tmp, int w, int n, int gw,
-                                                              int gq, int parts, int2* __restrict__ partial) {
-    __shared__ int4 tile[kKnnTile][4];
+__device__ __forceinline__ int dot12(const int (&a)[12], const int4& p0, const int4& p1, const int4& p2) {
+    int e = 0;
+    e = __dp4a(a[0], p0.x, e); e = __dp4a(a[1], p0.y, e); e = __dp4a(a[2], p0.z, e); e = __dp4a(a[3], p0.w, e);
+    e = __dp4a(a[4], p1.x, e); e = __dp4a(a[5], p1.y, e); e = __dp4a(a[6], p1.z, e); e = __dp4a(a[7], p1.w, e);
+    e = __dp4a(a[8], p2.x, e); e = __dp4a(a[9], p2.y, e); e = __dp4a(a[10], p2.z, e); e = __dp4a(a[11], p2.w, e);
+    return e;
+}
+
+__global__ void __launch_bounds__(kKnnThreads) k_knn_partial(Fields F, int n, int gw, int gq, int parts,
+                                                              int2* __restrict__ partial) {
+    __shared__ int4 tile[kKnnTile][3];
+    __shared__ int tnorm[kKnnTile];
+    const Field& A = pick(F);
+    const int w = A.V.w;
     const int qi = blockIdx.x * kKnnThreads + threadIdx.x;
     const bool active = qi < gq;
     RefFeat r;
-    if (active) load_ref(rec_at(ref, w, (qi % gw) * n, (qi / gw) * n), r);
+    if (active) load_ref(A.V.ref, pix(w, (qi % gw) * n, (qi / gw) * n), r);
     const int per = (gq + parts - 1) / parts;
     const int c0 = blockIdx.y * per;
     const int c1 = min(gq, c0 + per);
@@ -69,47 +101,32 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn_partial(const uint8_t* __re
     for (int base = c0; base < c1; base += kKnnTile) {
         __syncthreads();
         for (int t = threadIdx.x; t < kKnnTile * 4; t += kKnnThreads) {
-            int c = base + t / 4;
-            if (c < c1) tile[t / 4][t % 4] = __ldg(reinterpret_cast<const int4*>(rec_at(tmp, w, (c % gw) * n, (c / gw) * n)) + (t % 4));
+            const int c = base + t / 4, part = t % 4;
+            if (c >= c1) continue;
+            const size_t i = pix(w, (c % gw) * n, (c / gw) * n);
+            if (part < 3)
+                tile[t / 4][part] = __ldg(reinterpret_cast<const int4*>(A.V.tmp.f + i * kFeat) + part);
+            else
+                tnorm[t / 4] = __ldg(A.V.tmp.nrm + i);
         }
         __syncthreads();
         const int cnt = min(kKnnTile, c1 - base);
         if (active) {
             int k = 0;
             for (; k + 1 < cnt; k += 2) {  // two candidates: two independent dp4a chains
-                const int4 p0 = tile[k][0], p1 = tile[k][1], p2 = tile[k][2];
-                const int4 r0 = tile[k + 1][0], r1 = tile[k + 1][1], r2 = tile[k + 1][2];
-                int e = 0, f = 0;
-                e = __dp4a(r.a[0], p0.x, e); f = __dp4a(r.a[0], r0.x, f);
-                e = __dp4a(r.a[1], p0.y, e); f = __dp4a(r.a[1], r0.y, f);
-                e = __dp4a(r.a[2], p0.z, e); f = __dp4a(r.a[2], r0.z, f);
-                e = __dp4a(r.a[3], p0.w, e); f = __dp4a(r.a[3], r0.w, f);
-                e = __dp4a(r.a[4], p1.x, e); f = __dp4a(r.a[4], r1.x, f);
-                e = __dp4a(r.a[5], p1.y, e); f = __dp4a(r.a[5], r1.y, f);
-                e = __dp4a(r.a[6], p1.z, e); f = __dp4a(r.a[6], r1.z, f);
-                e = __dp4a(r.a[7], p1.w, e); f = __dp4a(r.a[7], r1.w, f);
-                e = __dp4a(r.a[8], p2.x, e); f = __dp4a(r.a[8], r2.x, f);
-                e = __dp4a(r.a[9], p2.y, e); f = __dp4a(r.a[9], r2.y, f);
-                e = __dp4a(r.a[10], p2.z, e); f = __dp4a(r.a[10], r2.z, f);
-                e = __dp4a(r.a[11], p2.w, e); f = __dp4a(r.a[11], r2.w, f);
-                top8_insert(bd, bi, r.n + tile[k][3].x - 2 * e, base + k);
-                top8_insert(bd, bi, r.n + tile[k + 1][3].x - 2 * f, base + k + 1);
+                const int e = dot12(r.a, tile[k][0], tile[k][1], tile[k][2]);
+                const int f = dot12(r.a, tile[k + 1][0], tile[k + 1][1], tile[k + 1][2]);
+                top8_insert(bd, bi, r.n + tnorm[k] - 2 * e, base + k);
+                top8_insert(bd, bi, r.n + tnorm[k + 1] - 2 * f, base + k + 1);
             }
             if (k < cnt) {
-                const int4 p0 = tile[k][0], p1 = tile[k][1], p2 = tile[k][2];
-                int e = 0;
-                e = __dp4a(r.a[0], p0.x, e); e = __dp4a(r.a[1], p0.y, e);
-                e = __dp4a(r.a[2], p0.z, e); e = __dp4a(r.a[3], p0.w, e);
-                e = __dp4a(r.a[4], p1.x, e); e = __dp4a(r.a[5], p1.y, e);
-                e = __dp4a(r.a[6], p1.z, e); e = __dp4a(r.a[7], p1.w, e);
-                e = __dp4a(r.a[8], p2.x, e); e = __dp4a(r.a[9], p2.y, e);
-                e = __dp4a(r.a[10], p2.z, e); e = __dp4a(r.a[11], p2.w, e);
-                top8_insert(bd, bi, r.n + tile[k][3].x - 2 * e, base + k);
+                const int e = dot12(r.a, tile[k][0], tile[k][1], tile[k][2]);
+                top8_insert(bd, bi, r.n + tnorm[k] - 2 * e, base + k);
             }
         }
     }
     if (active) {
-        int2* dst = partial + ((size_t)blockIdx.y * gq + qi) * 8;
+        int2* dst = partial + (((size_t)blockIdx.z * parts + blockIdx.y) * gq + qi) * 8;
 #pragma unroll
         for (int k = 0; k < 8; ++k) dst[k] = make_int2(bd[k], bi[k]);
     }
@@ -117,13 +134,13 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn_partial(const uint8_t* __re
 
 // Nearest grid point of row y by (distance, x), constrained by sigma, found by
 // one warp: lane l scans grid columns l, l+32, ...; then a warp argmin.
-__device__ __forceinline__ void warp_row_nearest(const RefFeat& r, const uint8_t* img, int w, int n, int gw, int y,
+__device__ __forceinline__ void warp_row_nearest(const RefFeat& r, const Plane& img, int w, int n, int gw, int y,
                                                  int xlim, int sigma, int lane, int& best_d, int& best_x) {
     int bd = 0x7fffffff, bx = 0x7fffffff;
     for (int g = lane; g < gw; g += 32) {
         const int x = g * n;
         if (sigma * (xlim - x) < 0) continue;
-        const int d = ssd_rec(r, rec_at(img, w, x, y));
+        const int d = ssd_at(r, img, pix(w, x, y));
         if (d < bd) {  // ascending x within the lane: ties keep the lower x
             bd = d;
             bx = x;
@@ -141,14 +158,15 @@ __device__ __forceinline__ void warp_row_nearest(const RefFeat& r, const uint8_t
     best_x = bx;
 }
 
-__global__ void k_init_select(Views V, int n, int gw, int gq, int parts, int knn, const int2* __restrict__ partial,
-                              uint2* __restrict__ field, int* __restrict__ cost) {
+__global__ void k_init_select(Fields F, int n, int gw, int gq, int parts, int knn, const int2* __restrict__ partial) {
+    const Field& A = pick(F);
+    const Views& V = A.V;
     const int qi = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (qi >= gq) return;  // warp-uniform
     const int px = (qi % gw) * n, py = (qi / gw) * n;
     RefFeat r;
-    load_ref(rec_at(V.ref, V.w, px, py), r);
+    load_ref(V.ref, pix(V.w, px, py), r);
     // merge the partial top-8 lists (every lane the same, reads broadcast)
     int bd[8], bi[8];
 #pragma unroll
@@ -157,7 +175,7 @@ __global__ void k_init_select(Views V, int n, int gw, int gq, int parts, int knn
         bi[k] = 0x7fffffff;
     }
     for (int p = 0; p < parts; ++p) {
-        const int2* src = partial + ((size_t)p * gq + qi) * 8;
+        const int2* src = partial + (((size_t)blockIdx.z * parts + p) * gq + qi) * 8;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int2 e = src[k];
@@ -184,47 +202,53 @@ __global__ void k_init_select(Views V, int n, int gw, int gq, int parts, int knn
         }
     }
     if (lane == 0) {
-        const size_t i = (size_t)py * V.w + px;
-        field[i] = pack_vec(best);
-        cost[i] = best_c;
+        const size_t i = pix(V.w, px, py);
+        A.field[i] = pack_vec(best);
+        A.cost[i] = best_c;
     }
 }
 
-__global__ void k_inherit(Views V, int n, int gw, int gh, uint2* __restrict__ field, int* __restrict__ cost) {
+__global__ void k_inherit(Fields F, int n, int gw, int gh) {
+    const Field& A = pick(F);
+    const Views& V = A.V;
     const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y;
     if (gx >= gw || gy >= gh) return;
     const int x = gx * n, y = gy * n;
-    const size_t i = (size_t)y * V.w + x;
+    const size_t i = pix(V.w, x, y);
     const bool coarse = ((gx | gy) & 1) == 0;
-    int c = coarse ? cost[i] : kEmpty;
+    const int c = coarse ? A.cost[i] : kEmpty;
     if (c != kEmpty) {
         RefFeat r;
-        load_ref(rec_at(V.ref, V.w, x, y), r);
-        Vec4 a = unpack_vec(field[i]);
-        cost[i] = cost_of(V, r, x, y, a.u, a.v, a.d0, a.d1);
+        load_ref(V.ref, i, r);
+        const Vec4 a = unpack_vec(A.field[i]);
+        A.cost[i] = cost_of(V, r, x, y, a.u, a.v, a.d0, a.d1);
     } else {
-        cost[i] = kEmpty;
-        field[i] = make_uint2(0u, 0u);
+        A.cost[i] = kEmpty;
+        A.field[i] = make_uint2(0u, 0u);
     }
 }
 
 struct HalfStep {
-    int n, s, gw, colour, dx, dy, prop, rs_before, rs_after, mirror;
+    int n, s, gw, colour, dx, dy, prop, rs_before, rs_after;
     uint2 key;
 };
 
-// k_half_step works with four lanes per pixel.  Lane q of a group holds
-// bytes 16q..16q+15 of the pixel's reference record (lanes 0-2: 16 feature
-// bytes each, lane 3: the norm) and loads the same quarter of every target
-// record, so one warp-wide 16-byte load fetches eight whole records.  The
-// partial sums of the three views are combined with two shuffles inside the
-// group: SSD = |a|^2 + |b|^2 - 2 a.b.
+// k_half_step works with four lanes per pixel.  Lanes 0-2 of a group hold
+// one 16-byte quarter each of the pixel's reference record, lane 3 its norm;
+// every target record is loaded the same way, so one warp-wide 16-byte load
+// fetches eight whole records.  The partial sums of the three views are
+// combined with two shuffles inside the group: SSD = |a|^2 + |b|^2 - 2 a.b.
 constexpr int kLanes = 4;
 constexpr int kHalfThreads = 256;
 constexpr int kHalfPixels = kHalfThreads / kLanes;
 
-__device__ __forceinline__ int quarter_part(const int4& a, const uint8_t* rec, int q) {
-    const int4 t = __ldg(reinterpret_cast<const int4*>(rec) + q);
+__device__ __forceinline__ int4 load_quarter(const Plane& P, size_t i, int q) {
+    if (q < 3) return __ldg(reinterpret_cast<const int4*>(P.f + i * kFeat) + q);
+    return make_int4(__ldg(P.nrm + i), 0, 0, 0);
+}
+
+__device__ __forceinline__ int quarter_part(const int4& a, const Plane& P, size_t i, int q) {
+    const int4 t = load_quarter(P, i, q);
     int d = __dp4a(a.x, t.x, 0);
     d = __dp4a(a.y, t.y, d);
     d = __dp4a(a.z, t.z, d);
@@ -238,17 +262,17 @@ __device__ __forceinline__ int group_cost(const Views& V, const int4& a, int q, 
     const int ty = clampi(py + c.v, 0, V.h - 1);
     const int sx = clampi(px - V.sigma * c.d0, 0, V.w - 1);
     const int cx = clampi(px + c.u - V.sigma * c.d1, 0, V.w - 1);
-    int part = quarter_part(a, rec_at(V.tmp, V.w, tx, ty), q) + quarter_part(a, rec_at(V.ste, V.w, sx, py), q) +
-               quarter_part(a, rec_at(V.crs, V.w, cx, ty), q);
+    int part = quarter_part(a, V.tmp, pix(V.w, tx, ty), q) + quarter_part(a, V.ste, pix(V.w, sx, py), q) +
+               quarter_part(a, V.crs, pix(V.w, cx, ty), q);
     part += __shfl_xor_sync(gmask, part, 1);
     part += __shfl_xor_sync(gmask, part, 2);
     return part;
 }
 
 __device__ __forceinline__ void random_search(const Views& V, const int4& a, int q, unsigned gmask,
-                                              const HalfStep& H, int it, int x, int y, uint32_t pix, Vec4& cur,
-                                              int& c, bool& changed) {
-    uint4 rnd = philox4x32_10(make_uint4(pix, (uint32_t)it, (uint32_t)(H.s + 4 * H.mirror), 0u), H.key);
+                                              const HalfStep& H, int mirror, int it, int x, int y, uint32_t pixel,
+                                              Vec4& cur, int& c, bool& changed) {
+    uint4 rnd = philox4x32_10(make_uint4(pixel, (uint32_t)it, (uint32_t)(H.s + 4 * mirror), 0u), H.key);
     Vec4 cand;
     cand.u = (int)(int16_t)(cur.u + rs_offset(rnd.x, H.n));
     cand.v = (int)(int16_t)(cur.v + rs_offset(rnd.y, H.n));
@@ -277,33 +301,34 @@ __device__ __forceinline__ void try_neighbour(const Views& V, const int4& a, int
     }
 }
 
-__global__ void __launch_bounds__(kHalfThreads) k_half_step(Views V, HalfStep H, uint2* __restrict__ field,
-                                                             int* __restrict__ cost) {
+__global__ void __launch_bounds__(kHalfThreads) k_half_step(Fields F, HalfStep H) {
+    const Field& A = pick(F);
+    const Views& V = A.V;
     const int q = threadIdx.x & (kLanes - 1);
     const unsigned gmask = 0xFu << (threadIdx.x & 28);
     const int gy = blockIdx.y;
     const int gx = 2 * (blockIdx.x * kHalfPixels + (int)(threadIdx.x >> 2)) + ((H.colour + gy) & 1);
     if (gx >= H.gw) return;  // the whole group leaves together
     const int x = gx * H.n, y = gy * H.n;
-    const size_t i = (size_t)y * V.w + x;
-    int c = cost[i];
+    const size_t i = pix(V.w, x, y);
+    int c = A.cost[i];
     if (!H.prop && c == kEmpty) return;
-    Vec4 cur = unpack_vec(field[i]);
-    const int4 a = __ldg(reinterpret_cast<const int4*>(rec_at(V.ref, V.w, x, y)) + q);
+    Vec4 cur = unpack_vec(A.field[i]);
+    const int4 a = load_quarter(V.ref, i, q);
     bool changed = false;
     if (H.rs_before >= 0 && c != kEmpty)
-        random_search(V, a, q, gmask, H, H.rs_before, x, y, (uint32_t)i, cur, c, changed);
+        random_search(V, a, q, gmask, H, A.mirror, H.rs_before, x, y, (uint32_t)i, cur, c, changed);
     if (H.prop) {
         const int ax = x - H.dx * H.n;
-        if (ax >= 0 && ax < V.w) try_neighbour(V, a, q, gmask, field, cost, (size_t)y * V.w + ax, x, y, cur, c, changed);
+        if (ax >= 0 && ax < V.w) try_neighbour(V, a, q, gmask, A.field, A.cost, pix(V.w, ax, y), x, y, cur, c, changed);
         const int by = y - H.dy * H.n;
-        if (by >= 0 && by < V.h) try_neighbour(V, a, q, gmask, field, cost, (size_t)by * V.w + x, x, y, cur, c, changed);
+        if (by >= 0 && by < V.h) try_neighbour(V, a, q, gmask, A.field, A.cost, pix(V.w, x, by), x, y, cur, c, changed);
     }
     if (H.rs_after >= 0 && c != kEmpty)
-        random_search(V, a, q, gmask, H, H.rs_after, x, y, (uint32_t)i, cur, c, changed);
+        random_search(V, a, q, gmask, H, A.mirror, H.rs_after, x, y, (uint32_t)i, cur, c, changed);
     if (changed && q == 0) {
-        field[i] = pack_vec(cur);
-        cost[i] = c;
+        A.field[i] = pack_vec(cur);
+        A.cost[i] = c;
     }
 }
 
@@ -315,13 +340,73 @@ int knn_parts(int gq) {
     return parts;
 }
 
-}  // namespace
-
-size_t match_ws_bytes(int w, int h, const sff_params& p) {
+size_t knn_field_bytes(int w, int h, const sff_params& p) {
     const int n = 1 << (p.num_scales - 1);
     const size_t gq = (size_t)((w + n - 1) / n) * ((h + n - 1) / n);
-    return align256(kMaxParts * gq * 8 * sizeof(int2));
+    return (size_t)kMaxParts * gq * 8 * sizeof(int2);
 }
+
+// The stage of Sec. 3.1 for nf = 1 or 2 fields sharing the launches.
+struct FieldSpec {
+    const uint8_t *ref, *tmp, *ste, *crs;
+    int16_t* field;
+    int32_t* cost;
+    int mirror;
+};
+
+int run_fields(const FieldSpec* spec, int nf, int width, int height, uint64_t seed, const sff_params& P,
+               void* workspace, cudaStream_t st) {
+    const int S = P.num_scales, I = P.iterations;
+    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    static const int kDirs[4][2] = {{1, 1}, {-1, -1}, {1, -1}, {-1, 1}};
+    Fields F{};
+    for (int s = S - 1; s >= 0; --s) {
+        const int n = 1 << s;
+        const int gw = (width + n - 1) / n, gh = (height + n - 1) / n;
+        for (int k = 0; k < nf; ++k) {
+            const FieldSpec& fs = spec[k];
+            F.f[k].V = Views{plane_of(fs.ref, s, S, width, height), plane_of(fs.tmp, s, S, width, height),
+                             plane_of(fs.ste, s, S, width, height), plane_of(fs.crs, s, S, width, height), width,
+                             height, fs.mirror ? -1 : 1};
+            F.f[k].field = reinterpret_cast<uint2*>(fs.field);
+            F.f[k].cost = fs.cost;
+            F.f[k].mirror = fs.mirror;
+        }
+        if (s == S - 1) {
+            const int gq = gw * gh;
+            const int parts = knn_parts(gq);
+            int2* partial = reinterpret_cast<int2*>(workspace);
+            dim3 g1((gq + kKnnThreads - 1) / kKnnThreads, parts, nf);
+            SFF_LAUNCH(k_knn_partial, g1, kKnnThreads, 0, st, F, n, gw, gq, parts, partial);
+            dim3 g2((gq + 7) / 8, 1, nf);
+            SFF_LAUNCH(k_init_select, g2, 256, 0, st, F, n, gw, gq, parts, P.knn_temporal, partial);
+        } else {
+            dim3 g((gw + 127) / 128, gh, nf);
+            SFF_LAUNCH(k_inherit, g, 128, 0, st, F, n, gw, gh);
+        }
+        const int half_w = (gw + 1) / 2;
+        dim3 g((half_w + kHalfPixels - 1) / kHalfPixels, gh, nf);
+        for (int it = 0; it < I; ++it) {
+            HalfStep H{n, s, gw, 0, kDirs[it % 4][0], kDirs[it % 4][1], 1, it - 1, -1, key};
+            SFF_LAUNCH(k_half_step, g, kHalfThreads, 0, st, F, H);
+            H.colour = 1;
+            H.rs_before = -1;
+            H.rs_after = it;
+            SFF_LAUNCH(k_half_step, g, kHalfThreads, 0, st, F, H);
+        }
+        if (I > 0) {
+            HalfStep H{n, s, gw, 0, 0, 0, 0, I - 1, -1, key};
+            SFF_LAUNCH(k_half_step, g, kHalfThreads, 0, st, F, H);
+        }
+    }
+    return launch_status();
+}
+
+bool misaligned_pyr(const uint8_t* p) { return ((uintptr_t)p & 15) != 0; }
+
+}  // namespace
+
+size_t match_ws_bytes(int w, int h, const sff_params& p) { return align256(2 * knn_field_bytes(w, h, p)); }
 
 }  // namespace sff
 
@@ -336,51 +421,32 @@ extern "C" int sff_match_views(const uint8_t* pyr_ref_dev, const uint8_t* pyr_te
         !workspace)
         return SFF_ERR_ARG;
     if (mirror != 0 && mirror != 1) return SFF_ERR_ARG;
-    if (((uintptr_t)pyr_ref_dev | (uintptr_t)pyr_temporal_dev | (uintptr_t)pyr_stereo_dev |
-         (uintptr_t)pyr_cross_dev) & 15)
+    if (misaligned_pyr(pyr_ref_dev) || misaligned_pyr(pyr_temporal_dev) || misaligned_pyr(pyr_stereo_dev) ||
+        misaligned_pyr(pyr_cross_dev))
         return SFF_ERR_ARG;
     if (((uintptr_t)field_dev & 7) || ((uintptr_t)cost_dev & 3) || ((uintptr_t)workspace & 255)) return SFF_ERR_ARG;
     if (workspace_bytes < match_ws_bytes(width, height, *params)) return SFF_ERR_WORKSPACE;
+    FieldSpec f{pyr_ref_dev, pyr_temporal_dev, pyr_stereo_dev, pyr_cross_dev, field_dev, cost_dev, mirror};
+    return run_fields(&f, 1, width, height, seed, *params, workspace, (cudaStream_t)stream);
+}
 
-    cudaStream_t st = (cudaStream_t)stream;
-    const int S = params->num_scales, I = params->iterations;
-    const size_t plane = (size_t)width * height * kRec;
-    uint2* field = reinterpret_cast<uint2*>(field_dev);
-    const int sigma = mirror ? -1 : 1;
-    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
-    static const int kDirs[4][2] = {{1, 1}, {-1, -1}, {1, -1}, {-1, 1}};
-
-    for (int s = S - 1; s >= 0; --s) {
-        const int n = 1 << s;
-        const int gw = (width + n - 1) / n, gh = (height + n - 1) / n;
-        Views V{pyr_ref_dev + s * plane, pyr_temporal_dev + s * plane, pyr_stereo_dev + s * plane,
-                pyr_cross_dev + s * plane, width, height, sigma};
-        if (s == S - 1) {
-            const int gq = gw * gh;
-            const int parts = knn_parts(gq);
-            int2* partial = reinterpret_cast<int2*>(workspace);
-            dim3 g1((gq + kKnnThreads - 1) / kKnnThreads, parts);
-            SFF_LAUNCH(k_knn_partial, g1, kKnnThreads, 0, st, V.ref, V.tmp, width, n, gw, gq, parts, partial);
-            SFF_LAUNCH(k_init_select, (gq + 7) / 8, 256, 0, st, V, n, gw, gq, parts, params->knn_temporal, partial, field,
-                                                            cost_dev);
-        } else {
-            dim3 g((gw + 127) / 128, gh);
-            SFF_LAUNCH(k_inherit, g, 128, 0, st, V, n, gw, gh, field, cost_dev);
-        }
-        const int half_w = (gw + 1) / 2;
-        dim3 g((half_w + kHalfPixels - 1) / kHalfPixels, gh);
-        for (int it = 0; it < I; ++it) {
-            HalfStep H{n, s, gw, 0, kDirs[it % 4][0], kDirs[it % 4][1], 1, it - 1, -1, mirror, key};
-            SFF_LAUNCH(k_half_step, g, kHalfThreads, 0, st, V, H, field, cost_dev);
-            H.colour = 1;
-            H.rs_before = -1;
-            H.rs_after = it;
-            SFF_LAUNCH(k_half_step, g, kHalfThreads, 0, st, V, H, field, cost_dev);
-        }
-        if (I > 0) {
-            HalfStep H{n, s, gw, 0, 0, 0, 0, I - 1, -1, mirror, key};
-            SFF_LAUNCH(k_half_step, g, kHalfThreads, 0, st, V, H, field, cost_dev);
-        }
-    }
-    return launch_status();
+extern "C" int sff_match_quad(const uint8_t* pyr_l0_dev, const uint8_t* pyr_r0_dev, const uint8_t* pyr_l1_dev,
+                              const uint8_t* pyr_r1_dev, int32_t width, int32_t height, uint64_t seed,
+                              const sff_params* params, int16_t* fwd_dev, int32_t* fwd_cost_dev, int16_t* inv_dev,
+                              int32_t* inv_cost_dev, void* workspace, size_t workspace_bytes, void* stream) {
+    using namespace sff;
+    if (check_size(width, height) || check_params(params)) return SFF_ERR_ARG;
+    if (!pyr_l0_dev || !pyr_r0_dev || !pyr_l1_dev || !pyr_r1_dev || !fwd_dev || !fwd_cost_dev || !inv_dev ||
+        !inv_cost_dev || !workspace)
+        return SFF_ERR_ARG;
+    if (misaligned_pyr(pyr_l0_dev) || misaligned_pyr(pyr_r0_dev) || misaligned_pyr(pyr_l1_dev) ||
+        misaligned_pyr(pyr_r1_dev))
+        return SFF_ERR_ARG;
+    if (((uintptr_t)fwd_dev & 7) || ((uintptr_t)inv_dev & 7) || ((uintptr_t)fwd_cost_dev & 3) ||
+        ((uintptr_t)inv_cost_dev & 3) || ((uintptr_t)workspace & 255))
+        return SFF_ERR_ARG;
+    if (workspace_bytes < match_ws_bytes(width, height, *params)) return SFF_ERR_WORKSPACE;
+    FieldSpec f[2] = {{pyr_l0_dev, pyr_l1_dev, pyr_r0_dev, pyr_r1_dev, fwd_dev, fwd_cost_dev, 0},
+                      {pyr_r1_dev, pyr_r0_dev, pyr_l1_dev, pyr_l0_dev, inv_dev, inv_cost_dev, 1}};
+    return run_fields(f, 2, width, height, seed, *params, workspace, (cudaStream_t)stream);
 }

@@ -26,7 +26,7 @@ def declared_functions():
 
 def test_header_declares_the_four_calls():
     names = declared_functions()
-    for n in ("sff_features", "sff_match_views", "sff_consistency_filter", "sff_emit_seeds"):
+    for n in ("sff_features", "sff_match_views", "sff_match_quad", "sff_consistency_filter", "sff_emit_seeds"):
         assert n in names
 
 
@@ -45,7 +45,7 @@ def test_default_params_are_the_papers(sff):
 
 def test_sizes(sff):
     p = sff.default_params()
-    assert sff.pyramid_bytes(1242, 375, p) == 4 * 1242 * 375 * 64
+    assert sff.pyramid_bytes(1242, 375, p) == 4 * 1242 * 375 * 52
     assert sff.pyramid_bytes(7, 100, p) == 0  # below the minimum size
     assert sff.pyramid_bytes(16385, 100, p) == 0
     ws = sff.workspace_bytes(1242, 375, p)
@@ -81,6 +81,8 @@ def test_argument_errors_without_gpu(sff):
     assert L.sff_features(fake, 64, 48, 192, P, fake, fake, 16, null) == -3
     assert L.sff_match_views(fake, fake, fake, fake, 64, 48, 2, 1, P, fake, fake, fake, ws, null) == -1
     assert L.sff_match_views(fake, fake, fake, fake, 64, 48, 0, 1, P, fake, fake, fake, 0, null) == -3
+    assert L.sff_match_quad(fake, fake, fake, null, 64, 48, 1, P, fake, fake, fake, fake, fake, ws, null) == -1
+    assert L.sff_match_quad(fake, fake, fake, fake, 64, 48, 1, P, fake, fake, fake, fake, fake, 0, null) == -3
     assert L.sff_consistency_filter(fake, fake, fake, null, 64, 48, P, fake, fake, fake, ws, null) == -1
     assert L.sff_emit_seeds(fake, fake, fake, fake, 64, 48, fake, -1, fake, fake, ws, null) == -1
     assert L.sff_emit_seeds(fake, fake, fake, fake, 64, 48, fake, 10, fake, fake, 0, null) == -3

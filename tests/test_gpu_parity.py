@@ -39,8 +39,8 @@ def _gpu_features(torch, sff, img, p):
     ws = torch.empty(sff.workspace_bytes(w, h, p), dtype=torch.uint8, device="cuda")
     sff.features(torch.as_tensor(img).cuda(), pyr, ws, p)
     torch.cuda.synchronize()
-    rec = pyr.cpu().numpy().reshape(p.num_scales, h, w, 64)
-    return pyr, rec
+    feat, norm = sff.split_pyramid(pyr, w, h, p)
+    return pyr, (feat.cpu().numpy(), norm.cpu().numpy())
 
 
 @pytest.mark.parametrize("size", [(8, 8), (37, 23), (130, 70), (256, 80), (300, 9)])
@@ -50,11 +50,10 @@ def test_features_bit_exact(env, size, qshift):
     w, h = size
     img = scenegen.random_images(w, h, seed=w * 1000 + h, n=1)[0]
     p = sff.default_params(quant_shift=qshift)
-    _, rec = _gpu_features(torch, sff, img, p)
+    _, (gfeat, gnorm) = _gpu_features(torch, sff, img, p)
     feat, norm = orc.features(img, _oparams(orc, p))
-    assert np.array_equal(rec[..., :48].view(np.int8), feat)
-    assert np.array_equal(rec[..., 48:52].copy().view(np.int32)[..., 0], norm)
-    assert (rec[..., 52:] == 0).all()
+    assert np.array_equal(gfeat, feat)
+    assert np.array_equal(gnorm, norm)
 
 
 def _match_both(env, imgs, p, seed):
@@ -93,6 +92,26 @@ def test_match_views_random_images(env, size, params):
     for gf, gc, of, oc in _match_both(env, imgs, p, seed=0x1234567890ABCDEF):
         assert np.array_equal(gc, oc)
         assert np.array_equal(gf, of)
+
+
+@pytest.mark.parametrize("size,params", [((256, 80), {}), ((37, 23), {}), ((96, 40), {"num_scales": 2}),
+                                         ((130, 70), {"iterations": 3, "knn_temporal": 8})])
+def test_match_quad_equals_two_match_views(env, size, params):
+    # both fields in shared launches == the two single-field calls (and the oracle)
+    torch, sff, orc = env
+    w, h = size
+    imgs = scenegen.random_images(w, h, seed=3 * w + h)
+    p = sff.default_params(**params)
+    pyrs = [_gpu_features(torch, sff, im, p)[0] for im in imgs]
+    ws = torch.empty(sff.workspace_bytes(w, h, p), dtype=torch.uint8, device="cuda")
+    out = [torch.empty((h, w, 4), dtype=torch.int16, device="cuda") for _ in range(2)]
+    cst = [torch.empty((h, w), dtype=torch.int32, device="cuda") for _ in range(2)]
+    sff.match_quad(*pyrs, w, h, 99, out[0], cst[0], out[1], cst[1], ws, p)
+    torch.cuda.synchronize()
+    (f0, c0, of0, oc0), (f1, c1, of1, oc1) = _match_both(env, imgs, p, seed=99)
+    assert np.array_equal(out[0].cpu().numpy(), f0) and np.array_equal(cst[0].cpu().numpy(), c0)
+    assert np.array_equal(out[1].cpu().numpy(), f1) and np.array_equal(cst[1].cpu().numpy(), c1)
+    assert np.array_equal(f0, of0) and np.array_equal(f1, of1)
 
 
 @pytest.mark.parametrize("seed", [1, 2])
