@@ -8,12 +8,11 @@
 // parallelism of the small coarse-scale launches and lets one L2 fill of a
 // scale's features serve both fields.
 //
-// k_knn_partial:  temporal K-NN, all-pairs over the coarsest grid; candidate
-//                 tiles staged in shared memory and broadcast to the 128
-//                 queries of a CTA; candidates split over blockIdx.y so the
-//                 grid covers the SMs.  Each thread keeps a sorted top-8 of
-//                 (distance, grid index) in registers.
-// k_init_select:  one warp per query: merges the partial top-8 lists, finds
+// k_knn:          temporal K-NN, all-pairs over the coarsest grid, one warp
+//                 per query; candidate tiles staged in shared memory and
+//                 shared by the 16 queries of a CTA; a sorted top-8 of
+//                 (distance, grid index) spread over lanes 0-7.
+// k_init_select:  one warp per query: takes the temporal top-K, finds
 //                 the nearest epipolar stereo / cross points and keeps the
 //                 best combination.  The cost is the sum of the three
 //                 independent distances, so for a given temporal leaf the
@@ -36,9 +35,9 @@
 namespace sff {
 namespace {
 
-constexpr int kKnnThreads = 128;
-constexpr int kKnnTile = 64;
-constexpr int kMaxParts = 16;
+constexpr int kKnnThreads = 512;
+constexpr int kKnnWarps = kKnnThreads / 32;
+constexpr int kKnnTile = 256;
 
 // One field: its views at the current scale and its output.
 struct Field {
@@ -79,30 +78,28 @@ __device__ __forceinline__ int dot12(const int (&a)[12], const int4& p0, const i
     return e;
 }
 
-__global__ void __launch_bounds__(kKnnThreads) k_knn_partial(Fields F, int n, int gw, int gq, int parts,
-                                                              int2* __restrict__ partial) {
+// Temporal K-NN of one query per warp.  Lane l scores candidate l of each
+// batch of 32 (read from a shared-memory tile that all the CTA's queries
+// share); a ballot against the current 8th-best (distance, index) keeps the
+// rare candidates that enter the list, and each of them is inserted into the
+// sorted top-8 held by lanes 0-7 with warp-uniform shuffles.
+__global__ void __launch_bounds__(kKnnThreads) k_knn(Fields F, int n, int gw, int gq, int2* __restrict__ best8) {
     __shared__ int4 tile[kKnnTile][3];
     __shared__ int tnorm[kKnnTile];
     const Field& A = pick(F);
     const int w = A.V.w;
-    const int qi = blockIdx.x * kKnnThreads + threadIdx.x;
-    const bool active = qi < gq;
+    const int lane = threadIdx.x & 31;
+    const int qi = blockIdx.x * kKnnWarps + (threadIdx.x >> 5);
+    const bool active = qi < gq;  // warp-uniform
     RefFeat r;
     if (active) load_ref(A.V.ref, pix(w, (qi % gw) * n, (qi / gw) * n), r);
-    const int per = (gq + parts - 1) / parts;
-    const int c0 = blockIdx.y * per;
-    const int c1 = min(gq, c0 + per);
-    int bd[8], bi[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        bd[k] = 0x7fffffff;
-        bi[k] = 0x7fffffff;
-    }
-    for (int base = c0; base < c1; base += kKnnTile) {
+    int ld = 0x7fffffff, li = 0x7fffffff;  // entry `lane` of the sorted top-8 (lanes 0-7)
+    int thr_d = 0x7fffffff, thr_i = 0x7fffffff;
+    for (int base = 0; base < gq; base += kKnnTile) {
         __syncthreads();
         for (int t = threadIdx.x; t < kKnnTile * 4; t += kKnnThreads) {
             const int c = base + t / 4, part = t % 4;
-            if (c >= c1) continue;
+            if (c >= gq) continue;
             const size_t i = pix(w, (c % gw) * n, (c / gw) * n);
             if (part < 3)
                 tile[t / 4][part] = __ldg(reinterpret_cast<const int4*>(A.V.tmp.f + i * kFeat) + part);
@@ -110,26 +107,36 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn_partial(Fields F, int n, in
                 tnorm[t / 4] = __ldg(A.V.tmp.nrm + i);
         }
         __syncthreads();
-        const int cnt = min(kKnnTile, c1 - base);
-        if (active) {
-            int k = 0;
-            for (; k + 1 < cnt; k += 2) {  // two candidates: two independent dp4a chains
-                const int e = dot12(r.a, tile[k][0], tile[k][1], tile[k][2]);
-                const int f = dot12(r.a, tile[k + 1][0], tile[k + 1][1], tile[k + 1][2]);
-                top8_insert(bd, bi, r.n + tnorm[k] - 2 * e, base + k);
-                top8_insert(bd, bi, r.n + tnorm[k + 1] - 2 * f, base + k + 1);
-            }
-            if (k < cnt) {
-                const int e = dot12(r.a, tile[k][0], tile[k][1], tile[k][2]);
-                top8_insert(bd, bi, r.n + tnorm[k] - 2 * e, base + k);
+        if (!active) continue;
+        const int cnt = min(kKnnTile, gq - base);
+        for (int b = 0; b < cnt; b += 32) {
+            const int k = b + lane;
+            int d = 0x7fffffff;
+            if (k < cnt) d = r.n + tnorm[k] - 2 * dot12(r.a, tile[k][0], tile[k][1], tile[k][2]);
+            const int idx = base + k;
+            unsigned enter = __ballot_sync(0xffffffffu, k < cnt && less_di(d, idx, thr_d, thr_i));
+            while (enter) {
+                const int src = __ffs(enter) - 1;
+                enter &= enter - 1;
+                const int nd = __shfl_sync(0xffffffffu, d, src), ni = __shfl_sync(0xffffffffu, idx, src);
+                if (!less_di(nd, ni, thr_d, thr_i)) continue;  // the threshold moved meanwhile
+                const int pos = __popc(__ballot_sync(0xffffffffu, lane < 8 && !less_di(nd, ni, ld, li)));
+                const int pd = __shfl_up_sync(0xffffffffu, ld, 1), pi = __shfl_up_sync(0xffffffffu, li, 1);
+                if (lane < 8) {
+                    if (lane > pos) {
+                        ld = pd;
+                        li = pi;
+                    } else if (lane == pos) {
+                        ld = nd;
+                        li = ni;
+                    }
+                }
+                thr_d = __shfl_sync(0xffffffffu, ld, 7);
+                thr_i = __shfl_sync(0xffffffffu, li, 7);
             }
         }
     }
-    if (active) {
-        int2* dst = partial + (((size_t)blockIdx.z * parts + blockIdx.y) * gq + qi) * 8;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) dst[k] = make_int2(bd[k], bi[k]);
-    }
+    if (active && lane < 8) best8[((size_t)blockIdx.z * gq + qi) * 8 + lane] = make_int2(ld, li);
 }
 
 // Nearest grid point of row y by (distance, x), constrained by sigma, found by
@@ -158,7 +165,7 @@ __device__ __forceinline__ void warp_row_nearest(const RefFeat& r, const Plane& 
     best_x = bx;
 }
 
-__global__ void k_init_select(Fields F, int n, int gw, int gq, int parts, int knn, const int2* __restrict__ partial) {
+__global__ void k_init_select(Fields F, int n, int gw, int gq, int knn, const int2* __restrict__ best8) {
     const Field& A = pick(F);
     const Views& V = A.V;
     const int qi = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
@@ -167,20 +174,14 @@ __global__ void k_init_select(Fields F, int n, int gw, int gq, int parts, int kn
     const int px = (qi % gw) * n, py = (qi / gw) * n;
     RefFeat r;
     load_ref(V.ref, pix(V.w, px, py), r);
-    // merge the partial top-8 lists (every lane the same, reads broadcast)
+    // the query's temporal top-8 (every lane the same, reads broadcast)
     int bd[8], bi[8];
+    const int2* src = best8 + ((size_t)blockIdx.z * gq + qi) * 8;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        bd[k] = 0x7fffffff;
-        bi[k] = 0x7fffffff;
-    }
-    for (int p = 0; p < parts; ++p) {
-        const int2* src = partial + (((size_t)blockIdx.z * parts + p) * gq + qi) * 8;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int2 e = src[k];
-            if (e.x != 0x7fffffff) top8_insert(bd, bi, e.x, e.y);
-        }
+        const int2 e = src[k];
+        bd[k] = e.x;
+        bi[k] = e.y;
     }
     int ds, sx;
     warp_row_nearest(r, V.ste, V.w, n, gw, py, px, V.sigma, lane, ds, sx);
@@ -256,51 +257,41 @@ __device__ __forceinline__ int quarter_part(const int4& a, const Plane& P, size_
     return q < 3 ? -2 * d : a.x + t.x;
 }
 
-__device__ __forceinline__ int group_cost(const Views& V, const int4& a, int q, unsigned gmask, int px, int py,
-                                          const Vec4& c) {
+// Partial (this lane's quarter) of the cost of vector c at (px, py).
+__device__ __forceinline__ int group_part(const Views& V, const int4& a, int q, int px, int py, const Vec4& c) {
     const int tx = clampi(px + c.u, 0, V.w - 1);
     const int ty = clampi(py + c.v, 0, V.h - 1);
     const int sx = clampi(px - V.sigma * c.d0, 0, V.w - 1);
     const int cx = clampi(px + c.u - V.sigma * c.d1, 0, V.w - 1);
-    int part = quarter_part(a, V.tmp, pix(V.w, tx, ty), q) + quarter_part(a, V.ste, pix(V.w, sx, py), q) +
-               quarter_part(a, V.crs, pix(V.w, cx, ty), q);
+    return quarter_part(a, V.tmp, pix(V.w, tx, ty), q) + quarter_part(a, V.ste, pix(V.w, sx, py), q) +
+           quarter_part(a, V.crs, pix(V.w, cx, ty), q);
+}
+
+__device__ __forceinline__ int group_sum(int part, unsigned gmask) {
     part += __shfl_xor_sync(gmask, part, 1);
     part += __shfl_xor_sync(gmask, part, 2);
     return part;
 }
 
-__device__ __forceinline__ void random_search(const Views& V, const int4& a, int q, unsigned gmask,
-                                              const HalfStep& H, int mirror, int it, int x, int y, uint32_t pixel,
-                                              Vec4& cur, int& c, bool& changed) {
-    uint4 rnd = philox4x32_10(make_uint4(pixel, (uint32_t)it, (uint32_t)(H.s + 4 * mirror), 0u), H.key);
-    Vec4 cand;
+// Random-search candidate of iteration `it` around `cur`; false when it
+// equals `cur` (its cost could not be strictly lower).
+__device__ __forceinline__ bool rs_candidate(const HalfStep& H, int mirror, int it, uint32_t pixel, const Vec4& cur,
+                                             Vec4& cand) {
+    const uint4 rnd = philox4x32_10(make_uint4(pixel, (uint32_t)it, (uint32_t)(H.s + 4 * mirror), 0u), H.key);
     cand.u = (int)(int16_t)(cur.u + rs_offset(rnd.x, H.n));
     cand.v = (int)(int16_t)(cur.v + rs_offset(rnd.y, H.n));
     cand.d0 = (int)(int16_t)max(0, cur.d0 + rs_offset(rnd.z, H.n));
     cand.d1 = (int)(int16_t)max(0, cur.d1 + rs_offset(rnd.w, H.n));
-    if (cand.u == cur.u && cand.v == cur.v && cand.d0 == cur.d0 && cand.d1 == cur.d1) return;
-    const int cc = group_cost(V, a, q, gmask, x, y, cand);
-    if (cc < c) {
-        c = cc;
-        cur = cand;
-        changed = true;
-    }
+    return !(cand.u == cur.u && cand.v == cur.v && cand.d0 == cur.d0 && cand.d1 == cur.d1);
 }
 
-__device__ __forceinline__ void try_neighbour(const Views& V, const int4& a, int q, unsigned gmask,
-                                              const uint2* field, const int* cost, size_t j, int x, int y, Vec4& cur,
-                                              int& c, bool& changed) {
-    const int cj = cost[j];
-    if (cj == kEmpty) return;
-    const Vec4 b = unpack_vec(field[j]);
-    const int cb = group_cost(V, a, q, gmask, x, y, b);
-    if (cb < c) {
-        c = cb;
-        cur = b;
-        changed = true;
-    }
-}
-
+// One half-step of one pixel.  The costs of the candidates that do not
+// depend on each other -- the random-search candidate that precedes the
+// propagation (colour 0) and the two predecessors -- are evaluated with all
+// their loads in flight together; the strict-less-than comparisons then run
+// in the order random search, horizontal, vertical, exactly as if evaluated
+// one after the other.  The random search that follows the propagation
+// (colour 1) depends on its result and comes last.
 __global__ void __launch_bounds__(kHalfThreads) k_half_step(Fields F, HalfStep H) {
     const Field& A = pick(F);
     const Views& V = A.V;
@@ -311,39 +302,70 @@ __global__ void __launch_bounds__(kHalfThreads) k_half_step(Fields F, HalfStep H
     if (gx >= H.gw) return;  // the whole group leaves together
     const int x = gx * H.n, y = gy * H.n;
     const size_t i = pix(V.w, x, y);
+    // own state, both predecessors' states and the reference quarter at once
+    const int ax = x - H.dx * H.n, by = y - H.dy * H.n;
+    const bool has_a = H.prop && ax >= 0 && ax < V.w;
+    const bool has_b = H.prop && by >= 0 && by < V.h;
+    const size_t ja = has_a ? pix(V.w, ax, y) : i, jb = has_b ? pix(V.w, x, by) : i;
     int c = A.cost[i];
+    const uint2 wc = A.field[i];
+    const int ca_own = A.cost[ja], cb_own = A.cost[jb];
+    const uint2 wa = A.field[ja], wb = A.field[jb];
     if (!H.prop && c == kEmpty) return;
-    Vec4 cur = unpack_vec(A.field[i]);
     const int4 a = load_quarter(V.ref, i, q);
+    Vec4 cur = unpack_vec(wc);
     bool changed = false;
-    if (H.rs_before >= 0 && c != kEmpty)
-        random_search(V, a, q, gmask, H, A.mirror, H.rs_before, x, y, (uint32_t)i, cur, c, changed);
-    if (H.prop) {
-        const int ax = x - H.dx * H.n;
-        if (ax >= 0 && ax < V.w) try_neighbour(V, a, q, gmask, A.field, A.cost, pix(V.w, ax, y), x, y, cur, c, changed);
-        const int by = y - H.dy * H.n;
-        if (by >= 0 && by < V.h) try_neighbour(V, a, q, gmask, A.field, A.cost, pix(V.w, x, by), x, y, cur, c, changed);
+
+    Vec4 cr;
+    const bool do_rs = H.rs_before >= 0 && c != kEmpty && rs_candidate(H, A.mirror, H.rs_before, (uint32_t)i, cur, cr);
+    const bool do_a = has_a && ca_own != kEmpty;
+    const bool do_b = has_b && cb_own != kEmpty;
+    const Vec4 va = unpack_vec(wa), vb = unpack_vec(wb);
+    const int pr = do_rs ? group_part(V, a, q, x, y, cr) : 0;
+    const int pa = do_a ? group_part(V, a, q, x, y, va) : 0;
+    const int pb = do_b ? group_part(V, a, q, x, y, vb) : 0;
+    if (do_rs) {
+        const int cc = group_sum(pr, gmask);
+        if (cc < c) {
+            c = cc;
+            cur = cr;
+            changed = true;
+        }
     }
-    if (H.rs_after >= 0 && c != kEmpty)
-        random_search(V, a, q, gmask, H, A.mirror, H.rs_after, x, y, (uint32_t)i, cur, c, changed);
+    if (do_a) {
+        const int cc = group_sum(pa, gmask);
+        if (cc < c) {
+            c = cc;
+            cur = va;
+            changed = true;
+        }
+    }
+    if (do_b) {
+        const int cc = group_sum(pb, gmask);
+        if (cc < c) {
+            c = cc;
+            cur = vb;
+            changed = true;
+        }
+    }
+    if (H.rs_after >= 0 && c != kEmpty && rs_candidate(H, A.mirror, H.rs_after, (uint32_t)i, cur, cr)) {
+        const int cc = group_sum(group_part(V, a, q, x, y, cr), gmask);
+        if (cc < c) {
+            c = cc;
+            cur = cr;
+            changed = true;
+        }
+    }
     if (changed && q == 0) {
         A.field[i] = pack_vec(cur);
         A.cost[i] = c;
     }
 }
 
-int knn_parts(int gq) {
-    int ctas = (gq + kKnnThreads - 1) / kKnnThreads;
-    int parts = (4 * 152 + ctas - 1) / ctas;
-    parts = parts < 1 ? 1 : (parts > kMaxParts ? kMaxParts : parts);
-    while (parts > 1 && gq / parts < kKnnTile) --parts;
-    return parts;
-}
-
 size_t knn_field_bytes(int w, int h, const sff_params& p) {
     const int n = 1 << (p.num_scales - 1);
     const size_t gq = (size_t)((w + n - 1) / n) * ((h + n - 1) / n);
-    return (size_t)kMaxParts * gq * 8 * sizeof(int2);
+    return gq * 8 * sizeof(int2);
 }
 
 // The stage of Sec. 3.1 for nf = 1 or 2 fields sharing the launches.
@@ -374,12 +396,11 @@ int run_fields(const FieldSpec* spec, int nf, int width, int height, uint64_t se
         }
         if (s == S - 1) {
             const int gq = gw * gh;
-            const int parts = knn_parts(gq);
-            int2* partial = reinterpret_cast<int2*>(workspace);
-            dim3 g1((gq + kKnnThreads - 1) / kKnnThreads, parts, nf);
-            SFF_LAUNCH(k_knn_partial, g1, kKnnThreads, 0, st, F, n, gw, gq, parts, partial);
+            int2* best8 = reinterpret_cast<int2*>(workspace);
+            dim3 g1((gq + kKnnWarps - 1) / kKnnWarps, 1, nf);
+            SFF_LAUNCH(k_knn, g1, kKnnThreads, 0, st, F, n, gw, gq, best8);
             dim3 g2((gq + 7) / 8, 1, nf);
-            SFF_LAUNCH(k_init_select, g2, 256, 0, st, F, n, gw, gq, parts, P.knn_temporal, partial);
+            SFF_LAUNCH(k_init_select, g2, 256, 0, st, F, n, gw, gq, P.knn_temporal, best8);
         } else {
             dim3 g((gw + 127) / 128, gh, nf);
             SFF_LAUNCH(k_inherit, g, 128, 0, st, F, n, gw, gh);
