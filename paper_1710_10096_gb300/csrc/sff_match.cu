@@ -10,7 +10,8 @@
 //
 // k_knn:          temporal K-NN, all-pairs over the coarsest grid, one warp
 //                 per query; candidate tiles staged in shared memory and
-//                 shared by the 16 queries of a CTA; a sorted top-8 of
+//                 shared by the 8 queries of a CTA, the next tile prefetched
+//                 into registers during the current one; a sorted top-8 of
 //                 (distance, grid index) spread over lanes 0-7.
 // k_init_select:  one warp per query: takes the temporal top-K, finds
 //                 the nearest epipolar stereo / cross points and keeps the
@@ -35,7 +36,7 @@
 namespace sff {
 namespace {
 
-constexpr int kKnnThreads = 512;
+constexpr int kKnnThreads = 256;
 constexpr int kKnnWarps = kKnnThreads / 32;
 constexpr int kKnnTile = 256;
 
@@ -95,18 +96,37 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(Fields F, int n, int gw, in
     if (active) load_ref(A.V.ref, pix(w, (qi % gw) * n, (qi / gw) * n), r);
     int ld = 0x7fffffff, li = 0x7fffffff;  // entry `lane` of the sorted top-8 (lanes 0-7)
     int thr_d = 0x7fffffff, thr_i = 0x7fffffff;
-    for (int base = 0; base < gq; base += kKnnTile) {
-        __syncthreads();
-        for (int t = threadIdx.x; t < kKnnTile * 4; t += kKnnThreads) {
+    // software pipeline: the next tile is loaded into registers while the
+    // current one is scored from shared memory
+    constexpr int kPer = kKnnTile * 4 / kKnnThreads;
+    int4 pre[kPer];
+    auto fetch = [&](int base) {
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const int t = threadIdx.x + u * kKnnThreads;
             const int c = base + t / 4, part = t % 4;
+            pre[u] = make_int4(0, 0, 0, 0);
             if (c >= gq) continue;
             const size_t i = pix(w, (c % gw) * n, (c / gw) * n);
             if (part < 3)
-                tile[t / 4][part] = __ldg(reinterpret_cast<const int4*>(A.V.tmp.f + i * kFeat) + part);
+                pre[u] = __ldg(reinterpret_cast<const int4*>(A.V.tmp.f + i * kFeat) + part);
             else
-                tnorm[t / 4] = __ldg(A.V.tmp.nrm + i);
+                pre[u].x = __ldg(A.V.tmp.nrm + i);
+        }
+    };
+    fetch(0);
+    for (int base = 0; base < gq; base += kKnnTile) {
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            const int t = threadIdx.x + u * kKnnThreads;
+            if (t % 4 < 3)
+                tile[t / 4][t % 4] = pre[u];
+            else
+                tnorm[t / 4] = pre[u].x;
         }
         __syncthreads();
+        if (base + kKnnTile < gq) fetch(base + kKnnTile);
         if (!active) continue;
         const int cnt = min(kKnnTile, gq - base);
         for (int b = 0; b < cnt; b += 32) {
