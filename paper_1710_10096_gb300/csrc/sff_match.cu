@@ -40,11 +40,14 @@ constexpr int kKnnThreads = 256;
 constexpr int kKnnWarps = kKnnThreads / 32;
 constexpr int kKnnTile = 256;
 
-// One field: its views at the current scale and its output.
+// One field: its views at the current scale, its state and, for the
+// double-buffered iteration kernel, the buffer it writes.
 struct Field {
     Views V;
-    uint2* field;
+    uint2* field;  // state read (and written in place by the other kernels)
     int* cost;
+    uint2* field_out;  // state written by k_iteration
+    int* cost_out;
     int mirror;
 };
 
@@ -305,42 +308,24 @@ __device__ __forceinline__ bool rs_candidate(const HalfStep& H, int mirror, int 
     return !(cand.u == cur.u && cand.v == cur.v && cand.d0 == cur.d0 && cand.d1 == cur.d1);
 }
 
-// One half-step of one pixel.  The costs of the candidates that do not
-// depend on each other -- the random-search candidate that precedes the
-// propagation (colour 0) and the two predecessors -- are evaluated with all
-// their loads in flight together; the strict-less-than comparisons then run
-// in the order random search, horizontal, vertical, exactly as if evaluated
-// one after the other.  The random search that follows the propagation
-// (colour 1) depends on its result and comes last.
-__global__ void __launch_bounds__(kHalfThreads) k_half_step(Fields F, HalfStep H) {
-    const Field& A = pick(F);
-    const Views& V = A.V;
-    const int q = threadIdx.x & (kLanes - 1);
-    const unsigned gmask = 0xFu << (threadIdx.x & 28);
-    const int gy = blockIdx.y;
-    const int gx = 2 * (blockIdx.x * kHalfPixels + (int)(threadIdx.x >> 2)) + ((H.colour + gy) & 1);
-    if (gx >= H.gw) return;  // the whole group leaves together
-    const int x = gx * H.n, y = gy * H.n;
-    const size_t i = pix(V.w, x, y);
-    // own state, both predecessors' states and the reference quarter at once
-    const int ax = x - H.dx * H.n, by = y - H.dy * H.n;
-    const bool has_a = H.prop && ax >= 0 && ax < V.w;
-    const bool has_b = H.prop && by >= 0 && by < V.h;
-    const size_t ja = has_a ? pix(V.w, ax, y) : i, jb = has_b ? pix(V.w, x, by) : i;
-    int c = A.cost[i];
-    const uint2 wc = A.field[i];
-    const int ca_own = A.cost[ja], cb_own = A.cost[jb];
-    const uint2 wa = A.field[ja], wb = A.field[jb];
-    if (!H.prop && c == kEmpty) return;
-    const int4 a = load_quarter(V.ref, i, q);
-    Vec4 cur = unpack_vec(wc);
+// One half-step of one pixel with own state (cur, c) and predecessor states
+// (va, ca), (vb, cb) (ca/cb = kEmpty when absent).  The costs of the
+// candidates that do not depend on each other -- the random-search candidate
+// that precedes the propagation (colour 0) and the two predecessors -- are
+// evaluated with all their loads in flight together; the
+// strict-less-than comparisons then run in the order random search,
+// horizontal, vertical, exactly as if evaluated one after the other.  The
+// random search that follows the propagation (colour 1) depends on its
+// result and comes last.  rs_before / rs_after < 0: no search.
+__device__ __forceinline__ bool update_pixel(const Views& V, const int4& a, int q, unsigned gmask, int n, int s,
+                                             uint2 key, int mirror, int x, int y, uint32_t pixel, int rs_before,
+                                             int rs_after, const Vec4& va, int ca, const Vec4& vb, int cb, Vec4& cur,
+                                             int& c) {
     bool changed = false;
-
+    const HalfStep H{n, s, 0, 0, 0, 0, 0, 0, 0, key};
     Vec4 cr;
-    const bool do_rs = H.rs_before >= 0 && c != kEmpty && rs_candidate(H, A.mirror, H.rs_before, (uint32_t)i, cur, cr);
-    const bool do_a = has_a && ca_own != kEmpty;
-    const bool do_b = has_b && cb_own != kEmpty;
-    const Vec4 va = unpack_vec(wa), vb = unpack_vec(wb);
+    const bool do_rs = rs_before >= 0 && c != kEmpty && rs_candidate(H, mirror, rs_before, pixel, cur, cr);
+    const bool do_a = ca != kEmpty, do_b = cb != kEmpty;
     const int pr = do_rs ? group_part(V, a, q, x, y, cr) : 0;
     const int pa = do_a ? group_part(V, a, q, x, y, va) : 0;
     const int pb = do_b ? group_part(V, a, q, x, y, vb) : 0;
@@ -368,7 +353,7 @@ __global__ void __launch_bounds__(kHalfThreads) k_half_step(Fields F, HalfStep H
             changed = true;
         }
     }
-    if (H.rs_after >= 0 && c != kEmpty && rs_candidate(H, A.mirror, H.rs_after, (uint32_t)i, cur, cr)) {
+    if (rs_after >= 0 && c != kEmpty && rs_candidate(H, mirror, rs_after, pixel, cur, cr)) {
         const int cc = group_sum(group_part(V, a, q, x, y, cr), gmask);
         if (cc < c) {
             c = cc;
@@ -376,9 +361,134 @@ __global__ void __launch_bounds__(kHalfThreads) k_half_step(Fields F, HalfStep H
             changed = true;
         }
     }
-    if (changed && q == 0) {
+    return changed;
+}
+
+// One colour of the checkerboard over the whole grid, in place.  Used for
+// the random search of colour 0 after the last iteration of a scale.
+__global__ void __launch_bounds__(kHalfThreads) k_half_step(Fields F, HalfStep H) {
+    const Field& A = pick(F);
+    const Views& V = A.V;
+    const int q = threadIdx.x & (kLanes - 1);
+    const unsigned gmask = 0xFu << (threadIdx.x & 28);
+    const int gy = blockIdx.y;
+    const int gx = 2 * (blockIdx.x * kHalfPixels + (int)(threadIdx.x >> 2)) + ((H.colour + gy) & 1);
+    if (gx >= H.gw) return;  // the whole group leaves together
+    const int x = gx * H.n, y = gy * H.n;
+    const size_t i = pix(V.w, x, y);
+    const int ax = x - H.dx * H.n, by = y - H.dy * H.n;
+    const bool has_a = H.prop && ax >= 0 && ax < V.w;
+    const bool has_b = H.prop && by >= 0 && by < V.h;
+    const size_t ja = has_a ? pix(V.w, ax, y) : i, jb = has_b ? pix(V.w, x, by) : i;
+    int c = A.cost[i];
+    const uint2 wc = A.field[i];
+    const int ca = has_a ? A.cost[ja] : kEmpty, cb = has_b ? A.cost[jb] : kEmpty;
+    const uint2 wa = A.field[ja], wb = A.field[jb];
+    if (!H.prop && c == kEmpty) return;
+    const int4 a = load_quarter(V.ref, i, q);
+    Vec4 cur = unpack_vec(wc);
+    if (update_pixel(V, a, q, gmask, H.n, H.s, H.key, A.mirror, x, y, (uint32_t)i, H.rs_before, H.rs_after,
+                     unpack_vec(wa), ca, unpack_vec(wb), cb, cur, c) &&
+        q == 0) {
         A.field[i] = pack_vec(cur);
         A.cost[i] = c;
+    }
+}
+
+// One whole iteration (both colours) over a 32x8 tile of grid pixels.
+// Phase 1 updates the colour-0 pixels of the tile and of a one-pixel halo on
+// the sides the colour-1 pixels read from (the predecessor sides of the
+// sweep), keeping the results in shared memory; phase 2 updates the
+// colour-1 pixels of the tile from them.  The state is read from `field` and
+// written to `field_out` (double buffering), so a CTA never sees another
+// CTA's writes of the same iteration; halo pixels are computed redundantly
+// and only written by the CTA that owns them.  At scale 0 the records of
+// the two colours share cache lines, so the second phase mostly hits L1.
+constexpr int kTileX = 32, kTileY = 8;
+constexpr int kRegX = kTileX + 1, kRegY = kTileY + 1;
+constexpr int kItThreads = 256;
+constexpr int kItGroups = kItThreads / kLanes;
+
+struct IterStep {
+    int n, s, gw, gh, dx, dy, it;
+    uint2 key;
+};
+
+__global__ void __launch_bounds__(kItThreads) k_iteration(Fields F, IterStep H) {
+    __shared__ uint2 s_vec[kRegX * kRegY];
+    __shared__ int s_cost[kRegX * kRegY];
+    const Field& A = pick(F);
+    const Views& V = A.V;
+    const int q = threadIdx.x & (kLanes - 1);
+    const unsigned gmask = 0xFu << (threadIdx.x & 28);
+    const int grp = threadIdx.x >> 2;
+    const int tx0 = blockIdx.x * kTileX, ty0 = blockIdx.y * kTileY;
+    const int rx0 = tx0 - (H.dx > 0 ? 1 : 0), ry0 = ty0 - (H.dy > 0 ? 1 : 0);  // region origin
+    const int n = H.n;
+
+    // phase 1: colour-0 pixels of the region (tile + halo)
+    constexpr int kHalfRow = (kRegX + 1) / 2;
+    for (int k = grp; k < kHalfRow * kRegY; k += kItGroups) {
+        const int ry = k / kHalfRow;
+        const int rx = 2 * (k % kHalfRow) + ((rx0 + ry0 + ry) & 1);
+        const int gx = rx0 + rx, gy = ry0 + ry;
+        if (rx >= kRegX || gx < 0 || gx >= H.gw || gy < 0 || gy >= H.gh) continue;
+        const int x = gx * n, y = gy * n;
+        const size_t i = pix(V.w, x, y);
+        const int ax = x - H.dx * n, by = y - H.dy * n;
+        const bool has_a = ax >= 0 && ax < V.w, has_b = by >= 0 && by < V.h;
+        const size_t ja = has_a ? pix(V.w, ax, y) : i, jb = has_b ? pix(V.w, x, by) : i;
+        int c = A.cost[i];
+        const uint2 wc = A.field[i];
+        const int ca = has_a ? A.cost[ja] : kEmpty, cb = has_b ? A.cost[jb] : kEmpty;
+        const uint2 wa = A.field[ja], wb = A.field[jb];
+        const int4 a = load_quarter(V.ref, i, q);
+        Vec4 cur = unpack_vec(wc);
+        update_pixel(V, a, q, gmask, n, H.s, H.key, A.mirror, x, y, (uint32_t)i, H.it - 1, -1, unpack_vec(wa), ca,
+                     unpack_vec(wb), cb, cur, c);
+        if (q == 0) {
+            const uint2 wv = pack_vec(cur);
+            s_vec[ry * kRegX + rx] = wv;
+            s_cost[ry * kRegX + rx] = c;
+            if (gx >= tx0 && gx < tx0 + kTileX && gy >= ty0 && gy < ty0 + kTileY) {
+                A.field_out[i] = wv;
+                A.cost_out[i] = c;
+            }
+        }
+    }
+    __syncthreads();
+
+    // phase 2: colour-1 pixels of the tile
+    constexpr int kTileHalfRow = kTileX / 2;
+    for (int k = grp; k < kTileHalfRow * kTileY; k += kItGroups) {
+        const int ly = k / kTileHalfRow;
+        const int gy = ty0 + ly;
+        const int gx = tx0 + 2 * (k % kTileHalfRow) + ((tx0 + gy + 1) & 1);
+        if (gx >= H.gw || gy >= H.gh) continue;
+        const int x = gx * n, y = gy * n;
+        const size_t i = pix(V.w, x, y);
+        int c = A.cost[i];
+        Vec4 cur = unpack_vec(A.field[i]);
+        const int4 a = load_quarter(V.ref, i, q);
+        const int agx = gx - H.dx, bgy = gy - H.dy;  // predecessors (colour 0, in the region)
+        int ca = kEmpty, cb = kEmpty;
+        uint2 wa = make_uint2(0u, 0u), wb = make_uint2(0u, 0u);
+        if (agx >= 0 && agx < H.gw) {
+            const int r = (gy - ry0) * kRegX + (agx - rx0);
+            ca = s_cost[r];
+            wa = s_vec[r];
+        }
+        if (bgy >= 0 && bgy < H.gh) {
+            const int r = (bgy - ry0) * kRegX + (gx - rx0);
+            cb = s_cost[r];
+            wb = s_vec[r];
+        }
+        update_pixel(V, a, q, gmask, n, H.s, H.key, A.mirror, x, y, (uint32_t)i, -1, H.it, unpack_vec(wa), ca,
+                     unpack_vec(wb), cb, cur, c);
+        if (q == 0) {
+            A.field_out[i] = pack_vec(cur);
+            A.cost_out[i] = c;
+        }
     }
 }
 
@@ -387,6 +497,9 @@ size_t knn_field_bytes(int w, int h, const sff_params& p) {
     const size_t gq = (size_t)((w + n - 1) / n) * ((h + n - 1) / n);
     return gq * 8 * sizeof(int2);
 }
+
+// Second state buffer (field + cost) of one field for the double-buffered iterations.
+size_t state_bytes(int w, int h) { return align256((size_t)w * h * 8) + align256((size_t)w * h * 4); }
 
 // The stage of Sec. 3.1 for nf = 1 or 2 fields sharing the launches.
 struct FieldSpec {
@@ -402,6 +515,16 @@ int run_fields(const FieldSpec* spec, int nf, int width, int height, uint64_t se
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     static const int kDirs[4][2] = {{1, 1}, {-1, -1}, {1, -1}, {-1, 1}};
     Fields F{};
+    // workspace: [top-8 lists of both fields][state buffers of field 0][of field 1]
+    char* ws = reinterpret_cast<char*>(workspace);
+    char* st_base = ws + align256(2 * knn_field_bytes(width, height, P));
+    int16_t* tmp_field[2];
+    int32_t* tmp_cost[2];
+    for (int k = 0; k < 2; ++k) {
+        char* b = st_base + k * state_bytes(width, height);
+        tmp_field[k] = reinterpret_cast<int16_t*>(b);
+        tmp_cost[k] = reinterpret_cast<int32_t*>(b + align256((size_t)width * height * 8));
+    }
     for (int s = S - 1; s >= 0; --s) {
         const int n = 1 << s;
         const int gw = (width + n - 1) / n, gh = (height + n - 1) / n;
@@ -410,8 +533,8 @@ int run_fields(const FieldSpec* spec, int nf, int width, int height, uint64_t se
             F.f[k].V = Views{plane_of(fs.ref, s, S, width, height), plane_of(fs.tmp, s, S, width, height),
                              plane_of(fs.ste, s, S, width, height), plane_of(fs.crs, s, S, width, height), width,
                              height, fs.mirror ? -1 : 1};
-            F.f[k].field = reinterpret_cast<uint2*>(fs.field);
-            F.f[k].cost = fs.cost;
+            F.f[k].field = F.f[k].field_out = reinterpret_cast<uint2*>(fs.field);
+            F.f[k].cost = F.f[k].cost_out = fs.cost;
             F.f[k].mirror = fs.mirror;
         }
         if (s == S - 1) {
@@ -425,17 +548,35 @@ int run_fields(const FieldSpec* spec, int nf, int width, int height, uint64_t se
             dim3 g((gw + 127) / 128, gh, nf);
             SFF_LAUNCH(k_inherit, g, 128, 0, st, F, n, gw, gh);
         }
-        const int half_w = (gw + 1) / 2;
-        dim3 g((half_w + kHalfPixels - 1) / kHalfPixels, gh, nf);
+        // iterations alternate between the caller's buffers (U) and the
+        // workspace buffers (T); with an odd count U is first copied to T so
+        // that the last iteration writes U
+        if (I & 1)
+            for (int k = 0; k < nf; ++k) {
+                cudaMemcpyAsync(tmp_field[k], spec[k].field, (size_t)width * height * 8, cudaMemcpyDeviceToDevice, st);
+                cudaMemcpyAsync(tmp_cost[k], spec[k].cost, (size_t)width * height * 4, cudaMemcpyDeviceToDevice, st);
+            }
+        dim3 gi((gw + kTileX - 1) / kTileX, (gh + kTileY - 1) / kTileY, nf);
         for (int it = 0; it < I; ++it) {
-            HalfStep H{n, s, gw, 0, kDirs[it % 4][0], kDirs[it % 4][1], 1, it - 1, -1, key};
-            SFF_LAUNCH(k_half_step, g, kHalfThreads, 0, st, F, H);
-            H.colour = 1;
-            H.rs_before = -1;
-            H.rs_after = it;
-            SFF_LAUNCH(k_half_step, g, kHalfThreads, 0, st, F, H);
+            const bool from_user = ((I - it) & 1) == 0;  // the last iteration reads T and writes U
+            for (int k = 0; k < nf; ++k) {
+                uint2* U = reinterpret_cast<uint2*>(spec[k].field);
+                uint2* T = reinterpret_cast<uint2*>(tmp_field[k]);
+                F.f[k].field = from_user ? U : T;
+                F.f[k].cost = from_user ? spec[k].cost : tmp_cost[k];
+                F.f[k].field_out = from_user ? T : U;
+                F.f[k].cost_out = from_user ? tmp_cost[k] : spec[k].cost;
+            }
+            IterStep H{n, s, gw, gh, kDirs[it % 4][0], kDirs[it % 4][1], it, key};
+            SFF_LAUNCH(k_iteration, gi, kItThreads, 0, st, F, H);
+        }
+        for (int k = 0; k < nf; ++k) {
+            F.f[k].field = F.f[k].field_out = reinterpret_cast<uint2*>(spec[k].field);
+            F.f[k].cost = F.f[k].cost_out = spec[k].cost;
         }
         if (I > 0) {
+            const int half_w = (gw + 1) / 2;
+            dim3 g((half_w + kHalfPixels - 1) / kHalfPixels, gh, nf);
             HalfStep H{n, s, gw, 0, 0, 0, 0, I - 1, -1, key};
             SFF_LAUNCH(k_half_step, g, kHalfThreads, 0, st, F, H);
         }
@@ -447,7 +588,11 @@ bool misaligned_pyr(const uint8_t* p) { return ((uintptr_t)p & 15) != 0; }
 
 }  // namespace
 
-size_t match_ws_bytes(int w, int h, const sff_params& p) { return align256(2 * knn_field_bytes(w, h, p)); }
+// Workspace: per field the temporal top-8 lists and a second state buffer
+// (field + cost) for the double-buffered iterations.
+size_t match_ws_bytes(int w, int h, const sff_params& p) {
+    return align256(2 * knn_field_bytes(w, h, p)) + 2 * state_bytes(w, h);
+}
 
 }  // namespace sff
 
