@@ -230,6 +230,11 @@ int sff_profile_enable(int32_t on);
  * clears the record.  Host pointers. */
 int sff_profile_collect(sff_kernel_time* out, int32_t capacity, int32_t* n_out);
 
+/* Number of device-side bounded waits (on the completion of the library's own
+ * asynchronous copies) that gave up since the last reset; nonzero means a
+ * result is invalid.  Synchronises the current device.  Host pointer. */
+int sff_device_timeouts(uint32_t* out, int32_t reset);
+
 /* Human-readable name of a status code (static string). */
 const char* sff_status_string(int status);
 

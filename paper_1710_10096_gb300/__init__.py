@@ -102,6 +102,8 @@ def lib():
         L.sff_profile_enable.restype = i32
         L.sff_profile_collect.argtypes = [ctypes.POINTER(KernelTime), i32, ctypes.POINTER(i32)]
         L.sff_profile_collect.restype = i32
+        L.sff_device_timeouts.argtypes = [ctypes.POINTER(ctypes.c_uint32), i32]
+        L.sff_device_timeouts.restype = i32
         L.sff_status_string.argtypes = [i32]
         L.sff_status_string.restype = ctypes.c_char_p
         _lib = L
@@ -200,6 +202,13 @@ def emit_seeds(fwd, fwd_cost, keep, cerr, seeds, capacity: int, count, workspace
     assert _nbytes(seeds) >= 20 * capacity
     _check(lib().sff_emit_seeds(_ptr(fwd), _ptr(fwd_cost), _ptr(keep), _ptr(cerr), w, h, _ptr(seeds), capacity,
                                 _ptr(count), _ptr(workspace), _nbytes(workspace), _stream(stream)), "sff_emit_seeds")
+
+
+def device_timeouts(reset: bool = False) -> int:
+    """Device-side bounded waits that gave up (0 in any valid run)."""
+    v = ctypes.c_uint32(0)
+    _check(lib().sff_device_timeouts(ctypes.byref(v), 1 if reset else 0), "sff_device_timeouts")
+    return v.value
 
 
 def seed_capacity(width: int, height: int) -> int:

@@ -8,11 +8,13 @@
 // parallelism of the small coarse-scale launches and lets one L2 fill of a
 // scale's features serve both fields.
 //
+// k_gather_grid:  packs the coarsest-grid records of the reference and
+//                 temporal images into contiguous arrays.
 // k_knn:          temporal K-NN, all-pairs over the coarsest grid, one warp
-//                 per query; candidate tiles staged in shared memory and
-//                 shared by the 8 queries of a CTA, the next tile prefetched
-//                 into registers during the current one; a sorted top-8 of
-//                 (distance, grid index) spread over lanes 0-7.
+//                 per query; candidate tiles streamed into shared memory by
+//                 TMA bulk copies on mbarriers (double-buffered) and shared
+//                 by the 8 queries of a CTA; a sorted top-8 of (distance,
+//                 grid index) spread over lanes 0-7.
 // k_init_select:  one warp per query: takes the temporal top-K, finds
 //                 the nearest epipolar stereo / cross points and keeps the
 //                 best combination.  The cost is the sum of the three
@@ -38,7 +40,7 @@ namespace {
 
 constexpr int kKnnThreads = 256;
 constexpr int kKnnWarps = kKnnThreads / 32;
-constexpr int kKnnTile = 256;
+constexpr int kKnnTile = 256;  // candidates per shared-memory tile (12 KB of records)
 
 // One field: its views at the current scale, its state and, for the
 // double-buffered iteration kernel, the buffer it writes.
@@ -82,82 +84,163 @@ __device__ __forceinline__ int dot12(const int (&a)[12], const int4& p0, const i
     return e;
 }
 
-// Temporal K-NN of one query per warp.  Lane l scores candidate l of each
-// batch of 32 (read from a shared-memory tile that all the CTA's queries
-// share); a ballot against the current 8th-best (distance, index) keeps the
-// rare candidates that enter the list, and each of them is inserted into the
-// sorted top-8 held by lanes 0-7 with warp-uniform shuffles.
-__global__ void __launch_bounds__(kKnnThreads) k_knn(Fields F, int n, int gw, int gq, int2* __restrict__ best8) {
-    __shared__ int4 tile[kKnnTile][3];
-    __shared__ int tnorm[kKnnTile];
+// Copies the coarsest-grid records of the reference (role 0) and temporal
+// (role 1) images of each field into contiguous arrays, so that the K-NN
+// search streams them with bulk copies.  Layout: [field][role][gq + pad]
+// records of 48 bytes and int32 norms.
+__global__ void k_gather_grid(Fields F, int n, int gw, int gq, int gq_pad, uint8_t* __restrict__ cf,
+                              int* __restrict__ cn) {
     const Field& A = pick(F);
-    const int w = A.V.w;
+    const int role = blockIdx.y;
+    const Plane& P = role ? A.V.tmp : A.V.ref;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = t >> 2, part = t & 3;
+    if (c >= gq) return;
+    const size_t i = pix(A.V.w, (c % gw) * n, (c / gw) * n);
+    const size_t slot = ((size_t)blockIdx.z * 2 + role) * gq_pad + c;
+    if (part < 3)
+        reinterpret_cast<int4*>(cf + slot * kFeat)[part] = __ldg(reinterpret_cast<const int4*>(P.f + i * kFeat) + part);
+    else
+        cn[slot] = __ldg(P.nrm + i);
+}
+
+// TMA (bulk-copy) helpers: 1-D global -> shared copies completing on an
+// mbarrier.  Addresses and sizes are multiples of 16 bytes.
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after kSpinLimit polls and reports false.
+constexpr int kSpinLimit = 1 << 22;
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+    for (int k = 0; k < kSpinLimit; ++k)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ unsigned int g_wait_timeouts;  // bounded waits that gave up (read by sff_device_timeouts)
+
+// Temporal K-NN of one query per warp.  The candidate records stream through
+// two shared-memory tiles filled by bulk copies (thread 0 issues tile t+1
+// while tile t is scored).  Lane l scores candidate l of each batch of 32; a
+// ballot against the current 8th-best (distance, index) keeps the rare
+// candidates that enter the list, and each of them is inserted into the
+// sorted top-8 held by lanes 0-7 with warp-uniform shuffles.
+__global__ void __launch_bounds__(kKnnThreads) k_knn(int gq, int gq_pad, const uint8_t* __restrict__ cf,
+                                                      const int* __restrict__ cn, int2* __restrict__ best8) {
+    __shared__ __align__(128) int4 tile[2][kKnnTile][3];
+    __shared__ __align__(16) int tnorm[2][kKnnTile];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ int s_fail;
     const int lane = threadIdx.x & 31;
     const int qi = blockIdx.x * kKnnWarps + (threadIdx.x >> 5);
     const bool active = qi < gq;  // warp-uniform
+    const uint8_t* qf = cf + (size_t)(blockIdx.z * 2 + 0) * gq_pad * kFeat;
+    const uint8_t* tf = cf + (size_t)(blockIdx.z * 2 + 1) * gq_pad * kFeat;
+    const int* qn = cn + (size_t)(blockIdx.z * 2 + 0) * gq_pad;
+    const int* tn = cn + (size_t)(blockIdx.z * 2 + 1) * gq_pad;
     RefFeat r;
-    if (active) load_ref(A.V.ref, pix(w, (qi % gw) * n, (qi / gw) * n), r);
+    if (active) {
+        const int4* p = reinterpret_cast<const int4*>(qf + (size_t)qi * kFeat);
+        const int4 q0 = __ldg(p), q1 = __ldg(p + 1), q2 = __ldg(p + 2);
+        r.a[0] = q0.x; r.a[1] = q0.y; r.a[2] = q0.z; r.a[3] = q0.w;
+        r.a[4] = q1.x; r.a[5] = q1.y; r.a[6] = q1.z; r.a[7] = q1.w;
+        r.a[8] = q2.x; r.a[9] = q2.y; r.a[10] = q2.z; r.a[11] = q2.w;
+        r.n = __ldg(qn + qi);
+    }
+    const int ntiles = (gq + kKnnTile - 1) / kKnnTile;
+    // copy sizes: whole records, rounded up to 4 records (16-byte multiples);
+    // the arrays carry that padding
+    auto issue = [&](int t) {
+        const int base = t * kKnnTile;
+        const int cnt4 = (min(kKnnTile, gq - base) + 3) & ~3;
+        const unsigned fb = (unsigned)cnt4 * kFeat, nb = (unsigned)cnt4 * 4;
+        mbar_expect_tx(&bar[t & 1], fb + nb);
+        bulk_copy_g2s(&tile[t & 1][0][0], tf + (size_t)base * kFeat, fb, &bar[t & 1]);
+        bulk_copy_g2s(&tnorm[t & 1][0], tn + base, nb, &bar[t & 1]);
+    };
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+        s_fail = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) issue(0);
     int ld = 0x7fffffff, li = 0x7fffffff;  // entry `lane` of the sorted top-8 (lanes 0-7)
     int thr_d = 0x7fffffff, thr_i = 0x7fffffff;
-    // software pipeline: the next tile is loaded into registers while the
-    // current one is scored from shared memory
-    constexpr int kPer = kKnnTile * 4 / kKnnThreads;
-    int4 pre[kPer];
-    auto fetch = [&](int base) {
-#pragma unroll
-        for (int u = 0; u < kPer; ++u) {
-            const int t = threadIdx.x + u * kKnnThreads;
-            const int c = base + t / 4, part = t % 4;
-            pre[u] = make_int4(0, 0, 0, 0);
-            if (c >= gq) continue;
-            const size_t i = pix(w, (c % gw) * n, (c / gw) * n);
-            if (part < 3)
-                pre[u] = __ldg(reinterpret_cast<const int4*>(A.V.tmp.f + i * kFeat) + part);
-            else
-                pre[u].x = __ldg(A.V.tmp.nrm + i);
+    for (int t = 0; t < ntiles; ++t) {
+        const int buf = t & 1;
+        // the other buffer was released by the __syncthreads that ended tile t-1
+        if (threadIdx.x == 0 && t + 1 < ntiles) issue(t + 1);
+        if (!mbar_wait(&bar[buf], (unsigned)(t >> 1) & 1u)) s_fail = 1;
+        if (__syncthreads_or(s_fail)) {
+            if (threadIdx.x == 0) {
+                atomicAdd(&g_wait_timeouts, 1u);
+                // let the copy issued for the next tile land (bounded) before the CTA exits
+                if (t + 1 < ntiles) mbar_wait(&bar[buf ^ 1], (unsigned)((t + 1) >> 1) & 1u);
+            }
+            return;
         }
-    };
-    fetch(0);
-    for (int base = 0; base < gq; base += kKnnTile) {
-        __syncthreads();
-#pragma unroll
-        for (int u = 0; u < kPer; ++u) {
-            const int t = threadIdx.x + u * kKnnThreads;
-            if (t % 4 < 3)
-                tile[t / 4][t % 4] = pre[u];
-            else
-                tnorm[t / 4] = pre[u].x;
-        }
-        __syncthreads();
-        if (base + kKnnTile < gq) fetch(base + kKnnTile);
-        if (!active) continue;
+        const int base = t * kKnnTile;
         const int cnt = min(kKnnTile, gq - base);
-        for (int b = 0; b < cnt; b += 32) {
-            const int k = b + lane;
-            int d = 0x7fffffff;
-            if (k < cnt) d = r.n + tnorm[k] - 2 * dot12(r.a, tile[k][0], tile[k][1], tile[k][2]);
-            const int idx = base + k;
-            unsigned enter = __ballot_sync(0xffffffffu, k < cnt && less_di(d, idx, thr_d, thr_i));
-            while (enter) {
-                const int src = __ffs(enter) - 1;
-                enter &= enter - 1;
-                const int nd = __shfl_sync(0xffffffffu, d, src), ni = __shfl_sync(0xffffffffu, idx, src);
-                if (!less_di(nd, ni, thr_d, thr_i)) continue;  // the threshold moved meanwhile
-                const int pos = __popc(__ballot_sync(0xffffffffu, lane < 8 && !less_di(nd, ni, ld, li)));
-                const int pd = __shfl_up_sync(0xffffffffu, ld, 1), pi = __shfl_up_sync(0xffffffffu, li, 1);
-                if (lane < 8) {
-                    if (lane > pos) {
-                        ld = pd;
-                        li = pi;
-                    } else if (lane == pos) {
-                        ld = nd;
-                        li = ni;
+        if (active) {
+            for (int b = 0; b < cnt; b += 32) {
+                const int k = b + lane;
+                int d = 0x7fffffff;
+                if (k < cnt)
+                    d = r.n + tnorm[buf][k] - 2 * dot12(r.a, tile[buf][k][0], tile[buf][k][1], tile[buf][k][2]);
+                const int idx = base + k;
+                unsigned enter = __ballot_sync(0xffffffffu, k < cnt && less_di(d, idx, thr_d, thr_i));
+                while (enter) {
+                    const int src = __ffs(enter) - 1;
+                    enter &= enter - 1;
+                    const int nd = __shfl_sync(0xffffffffu, d, src), ni = __shfl_sync(0xffffffffu, idx, src);
+                    if (!less_di(nd, ni, thr_d, thr_i)) continue;  // the threshold moved meanwhile
+                    const int pos = __popc(__ballot_sync(0xffffffffu, lane < 8 && !less_di(nd, ni, ld, li)));
+                    const int pd = __shfl_up_sync(0xffffffffu, ld, 1), pi = __shfl_up_sync(0xffffffffu, li, 1);
+                    if (lane < 8) {
+                        if (lane > pos) {
+                            ld = pd;
+                            li = pi;
+                        } else if (lane == pos) {
+                            ld = nd;
+                            li = ni;
+                        }
                     }
+                    thr_d = __shfl_sync(0xffffffffu, ld, 7);
+                    thr_i = __shfl_sync(0xffffffffu, li, 7);
                 }
-                thr_d = __shfl_sync(0xffffffffu, ld, 7);
-                thr_i = __shfl_sync(0xffffffffu, li, 7);
             }
         }
+        __syncthreads();
     }
     if (active && lane < 8) best8[((size_t)blockIdx.z * gq + qi) * 8 + lane] = make_int2(ld, li);
 }
@@ -308,6 +391,10 @@ __device__ __forceinline__ bool rs_candidate(const HalfStep& H, int mirror, int 
     return !(cand.u == cur.u && cand.v == cur.v && cand.d0 == cur.d0 && cand.d1 == cur.d1);
 }
 
+__device__ __forceinline__ bool same_vec(const Vec4& a, const Vec4& b) {
+    return a.u == b.u && a.v == b.v && a.d0 == b.d0 && a.d1 == b.d1;
+}
+
 // One half-step of one pixel with own state (cur, c) and predecessor states
 // (va, ca), (vb, cb) (ca/cb = kEmpty when absent).  The costs of the
 // candidates that do not depend on each other -- the random-search candidate
@@ -325,7 +412,14 @@ __device__ __forceinline__ bool update_pixel(const Views& V, const int4& a, int 
     const HalfStep H{n, s, 0, 0, 0, 0, 0, 0, 0, key};
     Vec4 cr;
     const bool do_rs = rs_before >= 0 && c != kEmpty && rs_candidate(H, mirror, rs_before, pixel, cur, cr);
-    const bool do_a = ca != kEmpty, do_b = cb != kEmpty;
+    // A predecessor holding the pixel's own vector, or the same vector as the
+    // other predecessor, has exactly that candidate's cost and can never be
+    // strictly lower: it is not evaluated (the result is unchanged).  Vectors
+    // are copied by propagation, so this is the common case once a region
+    // has converged.
+    const bool own_valid = c != kEmpty;
+    const bool do_a = ca != kEmpty && !(own_valid && same_vec(va, cur));
+    const bool do_b = cb != kEmpty && !(own_valid && same_vec(vb, cur)) && !(ca != kEmpty && same_vec(vb, va));
     const int pr = do_rs ? group_part(V, a, q, x, y, cr) : 0;
     const int pa = do_a ? group_part(V, a, q, x, y, va) : 0;
     const int pb = do_b ? group_part(V, a, q, x, y, vb) : 0;
@@ -492,10 +586,21 @@ __global__ void __launch_bounds__(kItThreads) k_iteration(Fields F, IterStep H) 
     }
 }
 
-size_t knn_field_bytes(int w, int h, const sff_params& p) {
+int coarse_gq(int w, int h, const sff_params& p) {
     const int n = 1 << (p.num_scales - 1);
-    const size_t gq = (size_t)((w + n - 1) / n) * ((h + n - 1) / n);
-    return gq * 8 * sizeof(int2);
+    return ((w + n - 1) / n) * ((h + n - 1) / n);
+}
+
+// K-NN scratch of both fields: top-8 lists, then the compacted records and
+// norms of [field][role].  Rows are padded to a multiple of 4 records plus 4,
+// so every bulk copy (whole groups of 4 records) starts and ends on 16 bytes.
+int gq_padded(int gq) { return ((gq + 3) & ~3) + 4; }
+size_t knn_lists_bytes(int gq) { return align256((size_t)2 * gq * 8 * sizeof(int2)); }
+size_t knn_recs_bytes(int gq) { return align256((size_t)4 * gq_padded(gq) * kFeat); }
+size_t knn_norms_bytes(int gq) { return align256((size_t)4 * gq_padded(gq) * sizeof(int)); }
+size_t knn_ws_bytes(int w, int h, const sff_params& p) {
+    const int gq = coarse_gq(w, h, p);
+    return knn_lists_bytes(gq) + knn_recs_bytes(gq) + knn_norms_bytes(gq);
 }
 
 // Second state buffer (field + cost) of one field for the double-buffered iterations.
@@ -517,7 +622,7 @@ int run_fields(const FieldSpec* spec, int nf, int width, int height, uint64_t se
     Fields F{};
     // workspace: [top-8 lists of both fields][state buffers of field 0][of field 1]
     char* ws = reinterpret_cast<char*>(workspace);
-    char* st_base = ws + align256(2 * knn_field_bytes(width, height, P));
+    char* st_base = ws + knn_ws_bytes(width, height, P);
     int16_t* tmp_field[2];
     int32_t* tmp_cost[2];
     for (int k = 0; k < 2; ++k) {
@@ -538,10 +643,14 @@ int run_fields(const FieldSpec* spec, int nf, int width, int height, uint64_t se
             F.f[k].mirror = fs.mirror;
         }
         if (s == S - 1) {
-            const int gq = gw * gh;
-            int2* best8 = reinterpret_cast<int2*>(workspace);
+            const int gq = gw * gh, gq_pad = gq_padded(gq);
+            int2* best8 = reinterpret_cast<int2*>(ws);
+            uint8_t* cf = reinterpret_cast<uint8_t*>(ws + knn_lists_bytes(gq));
+            int* cn = reinterpret_cast<int*>(ws + knn_lists_bytes(gq) + knn_recs_bytes(gq));
+            dim3 g0((gq * 4 + 255) / 256, 2, nf);
+            SFF_LAUNCH(k_gather_grid, g0, 256, 0, st, F, n, gw, gq, gq_pad, cf, cn);
             dim3 g1((gq + kKnnWarps - 1) / kKnnWarps, 1, nf);
-            SFF_LAUNCH(k_knn, g1, kKnnThreads, 0, st, F, n, gw, gq, best8);
+            SFF_LAUNCH(k_knn, g1, kKnnThreads, 0, st, gq, gq_pad, cf, cn, best8);
             dim3 g2((gq + 7) / 8, 1, nf);
             SFF_LAUNCH(k_init_select, g2, 256, 0, st, F, n, gw, gq, P.knn_temporal, best8);
         } else {
@@ -590,9 +699,7 @@ bool misaligned_pyr(const uint8_t* p) { return ((uintptr_t)p & 15) != 0; }
 
 // Workspace: per field the temporal top-8 lists and a second state buffer
 // (field + cost) for the double-buffered iterations.
-size_t match_ws_bytes(int w, int h, const sff_params& p) {
-    return align256(2 * knn_field_bytes(w, h, p)) + 2 * state_bytes(w, h);
-}
+size_t match_ws_bytes(int w, int h, const sff_params& p) { return knn_ws_bytes(w, h, p) + 2 * state_bytes(w, h); }
 
 }  // namespace sff
 
@@ -635,4 +742,16 @@ extern "C" int sff_match_quad(const uint8_t* pyr_l0_dev, const uint8_t* pyr_r0_d
     FieldSpec f[2] = {{pyr_l0_dev, pyr_l1_dev, pyr_r0_dev, pyr_r1_dev, fwd_dev, fwd_cost_dev, 0},
                       {pyr_r1_dev, pyr_r0_dev, pyr_l1_dev, pyr_l0_dev, inv_dev, inv_cost_dev, 1}};
     return run_fields(f, 2, width, height, seed, *params, workspace, (cudaStream_t)stream);
+}
+
+extern "C" int sff_device_timeouts(uint32_t* out, int32_t reset) {
+    if (!out) return SFF_ERR_ARG;
+    unsigned v = 0;
+    if (cudaMemcpyFromSymbol(&v, sff::g_wait_timeouts, sizeof v) != cudaSuccess) return SFF_ERR_CUDA;
+    *out = v;
+    if (reset) {
+        const unsigned z = 0;
+        if (cudaMemcpyToSymbol(sff::g_wait_timeouts, &z, sizeof z) != cudaSuccess) return SFF_ERR_CUDA;
+    }
+    return SFF_OK;
 }

@@ -240,3 +240,9 @@ def test_run_host_matches_device_path(env):
     b = m.run_host(*q.images(), seed=77)
     ref = orc.run_quad(*q.images(), seed=77)
     assert a.tobytes() == ref["seeds"].tobytes() == b.tobytes()
+
+
+def test_no_device_wait_timed_out(env):
+    # every bounded device-side wait of the runs above completed
+    torch, sff, orc = env
+    assert sff.device_timeouts() == 0
