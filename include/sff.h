@@ -72,6 +72,15 @@ typedef struct sff_params {
     int32_t knn_epipolar; /* K_E nearest neighbours per epipolar row; 1..8 (default 2) */
 } sff_params;
 
+/* Work distribution of the propagation kernels (no counterpart in the paper).
+ * Every supported setting gives bit-identical results; only speed differs.
+ * Supported: lanes_per_pixel in {1, 2, 4} x (tile_x, tile_y) in
+ * {(32, 8), (64, 8), (32, 16), (64, 16)} grid pixels. */
+typedef struct sff_tuning {
+    int32_t lanes_per_pixel; /* threads that share one pixel's feature loads */
+    int32_t tile_x, tile_y;  /* grid pixels per CTA of the iteration kernel */
+} sff_tuning;
+
 /* One seed of Sec. 3.2: pixel (x, y) of L0, its vector and its scores. 20 bytes. */
 typedef struct sff_seed {
     int16_t x, y, u, v, d0, d1;
@@ -156,6 +165,20 @@ int sff_match_quad(const uint8_t* pyr_l0_dev, const uint8_t* pyr_r0_dev,
                    int32_t width, int32_t height, uint64_t seed, const sff_params* params,
                    int16_t* fwd_dev, int32_t* fwd_cost_dev, int16_t* inv_dev, int32_t* inv_cost_dev,
                    void* workspace, size_t workspace_bytes, void* stream);
+
+/* sff_match_quad with an explicit work distribution (identical results). */
+int sff_match_quad_tuned(const uint8_t* pyr_l0_dev, const uint8_t* pyr_r0_dev,
+                         const uint8_t* pyr_l1_dev, const uint8_t* pyr_r1_dev,
+                         int32_t width, int32_t height, uint64_t seed, const sff_params* params,
+                         const sff_tuning* tuning,
+                         int16_t* fwd_dev, int32_t* fwd_cost_dev, int16_t* inv_dev, int32_t* inv_cost_dev,
+                         void* workspace, size_t workspace_bytes, void* stream);
+
+/* Fills *out with the default tuning; SFF_ERR_ARG if out is NULL. */
+int sff_default_tuning(sff_tuning* out);
+
+/* 1 if the tuning is one of the supported settings, else 0. */
+int sff_tuning_supported(const sff_tuning* tuning);
 
 /* Consistency check and region filter (Sec. 3.1, "Consistency Check").
  *   For L0 pixel p with forward vector u, q = p + (u - d1, v) in R1 and w the

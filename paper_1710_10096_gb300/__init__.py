@@ -41,6 +41,17 @@ class Params(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class Tuning(ctypes.Structure):
+    """sff_tuning of include/sff.h: work distribution, never changes results."""
+    _fields_ = [("lanes_per_pixel", ctypes.c_int32), ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32)]
+
+    def as_tuple(self):
+        return (self.lanes_per_pixel, self.tile_x, self.tile_y)
+
+
+TUNING_SPACE = [(l, tx, ty) for l in (4, 2, 1) for (tx, ty) in ((32, 8), (64, 8), (32, 16), (64, 16))]
+
+
 class KernelTime(ctypes.Structure):
     """sff_kernel_time of include/sff.h."""
     _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int32), ("total_ms", ctypes.c_double)]
@@ -92,6 +103,13 @@ def lib():
         L.sff_match_views.restype = i32
         L.sff_match_quad.argtypes = [P, P, P, P, i32, i32, ctypes.c_uint64, PP, P, P, P, P, P, sz, P]
         L.sff_match_quad.restype = i32
+        L.sff_match_quad_tuned.argtypes = [P, P, P, P, i32, i32, ctypes.c_uint64, PP, ctypes.POINTER(Tuning), P, P, P,
+                                           P, P, sz, P]
+        L.sff_match_quad_tuned.restype = i32
+        L.sff_default_tuning.argtypes = [ctypes.POINTER(Tuning)]
+        L.sff_default_tuning.restype = i32
+        L.sff_tuning_supported.argtypes = [ctypes.POINTER(Tuning)]
+        L.sff_tuning_supported.restype = i32
         L.sff_consistency_filter.argtypes = [P, P, P, P, i32, i32, PP, P, P, P, sz, P]
         L.sff_consistency_filter.restype = i32
         L.sff_emit_seeds.argtypes = [P, P, P, P, i32, i32, P, i32, P, P, sz, P]
@@ -177,6 +195,29 @@ def match_quad(pyr_l0, pyr_r0, pyr_l1, pyr_r1, width: int, height: int, seed: in
            "sff_match_quad")
 
 
+def default_tuning() -> Tuning:
+    t = Tuning()
+    _check(lib().sff_default_tuning(ctypes.byref(t)), "sff_default_tuning")
+    return t
+
+
+def make_tuning(lanes: int, tile_x: int, tile_y: int) -> Tuning:
+    t = Tuning(lanes, tile_x, tile_y)
+    if not lib().sff_tuning_supported(ctypes.byref(t)):
+        raise SffError(f"unsupported tuning {(lanes, tile_x, tile_y)}")
+    return t
+
+
+def match_quad_tuned(pyr_l0, pyr_r0, pyr_l1, pyr_r1, width: int, height: int, seed: int, tuning: Tuning, fwd,
+                     fwd_cost, inv, inv_cost, workspace, params: Params = None, stream=None) -> None:
+    """sff_match_quad_tuned: match_quad with an explicit work distribution."""
+    params = params or default_params()
+    _check(lib().sff_match_quad_tuned(_ptr(pyr_l0), _ptr(pyr_r0), _ptr(pyr_l1), _ptr(pyr_r1), width, height,
+                                      int(seed) & (2 ** 64 - 1), ctypes.byref(params), ctypes.byref(tuning),
+                                      _ptr(fwd), _ptr(fwd_cost), _ptr(inv), _ptr(inv_cost), _ptr(workspace),
+                                      _nbytes(workspace), _stream(stream)), "sff_match_quad_tuned")
+
+
 def split_pyramid(pyr, width: int, height: int, params: Params = None):
     """(features [S, H, W, 48] int8, norms [S, H, W] int32) views of a pyramid buffer."""
     import torch
@@ -226,10 +267,12 @@ class QuadMatcher:
     arrays, copies them in, runs the stage and copies the seeds back.
     """
 
-    def __init__(self, width: int, height: int, params: Params = None, device="cuda", concurrent: bool = True):
+    def __init__(self, width: int, height: int, params: Params = None, device="cuda", concurrent: bool = True,
+                 tuning: Tuning = None):
         import torch
         self.width, self.height = int(width), int(height)
         self.params = params or default_params()
+        self.tuning = tuning or default_tuning()
         self.device = torch.device(device)
         self.concurrent = concurrent
         w, h = self.width, self.height
@@ -281,8 +324,8 @@ class QuadMatcher:
                 done = torch.cuda.Event()
                 done.record(st)
                 main.wait_event(done)
-            match_quad(pL0, pR0, pL1, pR1, self.width, self.height, seed, self.fwd, self.fwd_cost, self.inv,
-                       self.inv_cost, self.workspace, p, main)
+            match_quad_tuned(pL0, pR0, pL1, pR1, self.width, self.height, seed, self.tuning, self.fwd,
+                             self.fwd_cost, self.inv, self.inv_cost, self.workspace, p, main)
         consistency_filter(self.fwd, self.fwd_cost, self.inv, self.inv_cost, self.keep, self.cerr, self.workspace,
                            p, main)
         emit_seeds(self.fwd, self.fwd_cost, self.keep, self.cerr, self.seeds, self.capacity, self.count,

@@ -340,54 +340,77 @@ struct HalfStep {
     uint2 key;
 };
 
-// k_half_step works with four lanes per pixel.  Lanes 0-2 of a group hold
-// one 16-byte quarter each of the pixel's reference record, lane 3 its norm;
-// every target record is loaded the same way, so one warp-wide 16-byte load
-// fetches eight whole records.  The partial sums of the three views are
-// combined with two shuffles inside the group: SSD = |a|^2 + |b|^2 - 2 a.b.
-constexpr int kLanes = 4;
-constexpr int kHalfThreads = 256;
-constexpr int kHalfPixels = kHalfThreads / kLanes;
+// Pixels are processed by groups of L lanes (L = 1, 2 or 4, a tuning knob
+// that never changes results).  Lane q of a group holds the 16-byte chunks j
+// of a 48-byte record with j % L == q and, on lane 3 % L, the norm; every
+// target record is loaded the same way, so with L = 4 one warp-wide load
+// fetches eight whole records.  Partial sums |a|^2 + |b|^2 - 2 a.b of the
+// three views are combined with log2(L) shuffles inside the group.
+template <int L>
+struct Slice {
+    static constexpr int kChunks = (3 + L - 1) / L;
+    int4 c[kChunks];
+    int nrm;  // the norm on lane 3 % L, 0 on the others
+};
 
-__device__ __forceinline__ int4 load_quarter(const Plane& P, size_t i, int q) {
-    if (q < 3) return __ldg(reinterpret_cast<const int4*>(P.f + i * kFeat) + q);
-    return make_int4(__ldg(P.nrm + i), 0, 0, 0);
+template <int L>
+__device__ __forceinline__ void load_slice(const Plane& P, size_t i, int q, Slice<L>& s) {
+    const int4* p = reinterpret_cast<const int4*>(P.f + i * kFeat);
+#pragma unroll
+    for (int k = 0; k < Slice<L>::kChunks; ++k) {
+        const int j = q + k * L;
+        s.c[k] = j < 3 ? __ldg(p + j) : make_int4(0, 0, 0, 0);
+    }
+    s.nrm = q == 3 % L ? __ldg(P.nrm + i) : 0;
 }
 
-__device__ __forceinline__ int quarter_part(const int4& a, const Plane& P, size_t i, int q) {
-    const int4 t = load_quarter(P, i, q);
-    int d = __dp4a(a.x, t.x, 0);
-    d = __dp4a(a.y, t.y, d);
-    d = __dp4a(a.z, t.z, d);
-    d = __dp4a(a.w, t.w, d);
-    return q < 3 ? -2 * d : a.x + t.x;
+template <int L>
+__device__ __forceinline__ int slice_part(const Slice<L>& a, const Plane& P, size_t i, int q) {
+    Slice<L> t;
+    load_slice<L>(P, i, q, t);
+    int d = 0;
+#pragma unroll
+    for (int k = 0; k < Slice<L>::kChunks; ++k) {
+        d = __dp4a(a.c[k].x, t.c[k].x, d);
+        d = __dp4a(a.c[k].y, t.c[k].y, d);
+        d = __dp4a(a.c[k].z, t.c[k].z, d);
+        d = __dp4a(a.c[k].w, t.c[k].w, d);
+    }
+    return a.nrm + t.nrm - 2 * d;
 }
 
-// Partial (this lane's quarter) of the cost of vector c at (px, py).
-__device__ __forceinline__ int group_part(const Views& V, const int4& a, int q, int px, int py, const Vec4& c) {
+// This lane's part of the cost of vector c at (px, py).
+template <int L>
+__device__ __forceinline__ int group_part(const Views& V, const Slice<L>& a, int q, int px, int py, const Vec4& c) {
     const int tx = clampi(px + c.u, 0, V.w - 1);
     const int ty = clampi(py + c.v, 0, V.h - 1);
     const int sx = clampi(px - V.sigma * c.d0, 0, V.w - 1);
     const int cx = clampi(px + c.u - V.sigma * c.d1, 0, V.w - 1);
-    return quarter_part(a, V.tmp, pix(V.w, tx, ty), q) + quarter_part(a, V.ste, pix(V.w, sx, py), q) +
-           quarter_part(a, V.crs, pix(V.w, cx, ty), q);
+    return slice_part<L>(a, V.tmp, pix(V.w, tx, ty), q) + slice_part<L>(a, V.ste, pix(V.w, sx, py), q) +
+           slice_part<L>(a, V.crs, pix(V.w, cx, ty), q);
 }
 
+template <int L>
 __device__ __forceinline__ int group_sum(int part, unsigned gmask) {
-    part += __shfl_xor_sync(gmask, part, 1);
-    part += __shfl_xor_sync(gmask, part, 2);
+#pragma unroll
+    for (int o = 1; o < L; o <<= 1) part += __shfl_xor_sync(gmask, part, o);
     return part;
+}
+
+template <int L>
+__device__ __forceinline__ unsigned group_mask() {
+    return L == 1 ? (1u << (threadIdx.x & 31)) : (((1u << L) - 1u) << (threadIdx.x & 31 & ~(L - 1)));
 }
 
 // Random-search candidate of iteration `it` around `cur`; false when it
 // equals `cur` (its cost could not be strictly lower).
-__device__ __forceinline__ bool rs_candidate(const HalfStep& H, int mirror, int it, uint32_t pixel, const Vec4& cur,
-                                             Vec4& cand) {
-    const uint4 rnd = philox4x32_10(make_uint4(pixel, (uint32_t)it, (uint32_t)(H.s + 4 * mirror), 0u), H.key);
-    cand.u = (int)(int16_t)(cur.u + rs_offset(rnd.x, H.n));
-    cand.v = (int)(int16_t)(cur.v + rs_offset(rnd.y, H.n));
-    cand.d0 = (int)(int16_t)max(0, cur.d0 + rs_offset(rnd.z, H.n));
-    cand.d1 = (int)(int16_t)max(0, cur.d1 + rs_offset(rnd.w, H.n));
+__device__ __forceinline__ bool rs_candidate(int n, int s, uint2 key, int mirror, int it, uint32_t pixel,
+                                             const Vec4& cur, Vec4& cand) {
+    const uint4 rnd = philox4x32_10(make_uint4(pixel, (uint32_t)it, (uint32_t)(s + 4 * mirror), 0u), key);
+    cand.u = (int)(int16_t)(cur.u + rs_offset(rnd.x, n));
+    cand.v = (int)(int16_t)(cur.v + rs_offset(rnd.y, n));
+    cand.d0 = (int)(int16_t)max(0, cur.d0 + rs_offset(rnd.z, n));
+    cand.d1 = (int)(int16_t)max(0, cur.d1 + rs_offset(rnd.w, n));
     return !(cand.u == cur.u && cand.v == cur.v && cand.d0 == cur.d0 && cand.d1 == cur.d1);
 }
 
@@ -404,27 +427,25 @@ __device__ __forceinline__ bool same_vec(const Vec4& a, const Vec4& b) {
 // horizontal, vertical, exactly as if evaluated one after the other.  The
 // random search that follows the propagation (colour 1) depends on its
 // result and comes last.  rs_before / rs_after < 0: no search.
-__device__ __forceinline__ bool update_pixel(const Views& V, const int4& a, int q, unsigned gmask, int n, int s,
+template <int L>
+__device__ __forceinline__ bool update_pixel(const Views& V, const Slice<L>& a, int q, unsigned gmask, int n, int s,
                                              uint2 key, int mirror, int x, int y, uint32_t pixel, int rs_before,
                                              int rs_after, const Vec4& va, int ca, const Vec4& vb, int cb, Vec4& cur,
                                              int& c) {
     bool changed = false;
-    const HalfStep H{n, s, 0, 0, 0, 0, 0, 0, 0, key};
     Vec4 cr;
-    const bool do_rs = rs_before >= 0 && c != kEmpty && rs_candidate(H, mirror, rs_before, pixel, cur, cr);
+    const bool do_rs = rs_before >= 0 && c != kEmpty && rs_candidate(n, s, key, mirror, rs_before, pixel, cur, cr);
     // A predecessor holding the pixel's own vector, or the same vector as the
     // other predecessor, has exactly that candidate's cost and can never be
-    // strictly lower: it is not evaluated (the result is unchanged).  Vectors
-    // are copied by propagation, so this is the common case once a region
-    // has converged.
+    // strictly lower: it is not evaluated (the result is unchanged).
     const bool own_valid = c != kEmpty;
     const bool do_a = ca != kEmpty && !(own_valid && same_vec(va, cur));
     const bool do_b = cb != kEmpty && !(own_valid && same_vec(vb, cur)) && !(ca != kEmpty && same_vec(vb, va));
-    const int pr = do_rs ? group_part(V, a, q, x, y, cr) : 0;
-    const int pa = do_a ? group_part(V, a, q, x, y, va) : 0;
-    const int pb = do_b ? group_part(V, a, q, x, y, vb) : 0;
+    const int pr = do_rs ? group_part<L>(V, a, q, x, y, cr) : 0;
+    const int pa = do_a ? group_part<L>(V, a, q, x, y, va) : 0;
+    const int pb = do_b ? group_part<L>(V, a, q, x, y, vb) : 0;
     if (do_rs) {
-        const int cc = group_sum(pr, gmask);
+        const int cc = group_sum<L>(pr, gmask);
         if (cc < c) {
             c = cc;
             cur = cr;
@@ -432,7 +453,7 @@ __device__ __forceinline__ bool update_pixel(const Views& V, const int4& a, int 
         }
     }
     if (do_a) {
-        const int cc = group_sum(pa, gmask);
+        const int cc = group_sum<L>(pa, gmask);
         if (cc < c) {
             c = cc;
             cur = va;
@@ -440,15 +461,15 @@ __device__ __forceinline__ bool update_pixel(const Views& V, const int4& a, int 
         }
     }
     if (do_b) {
-        const int cc = group_sum(pb, gmask);
+        const int cc = group_sum<L>(pb, gmask);
         if (cc < c) {
             c = cc;
             cur = vb;
             changed = true;
         }
     }
-    if (rs_after >= 0 && c != kEmpty && rs_candidate(H, mirror, rs_after, pixel, cur, cr)) {
-        const int cc = group_sum(group_part(V, a, q, x, y, cr), gmask);
+    if (rs_after >= 0 && c != kEmpty && rs_candidate(n, s, key, mirror, rs_after, pixel, cur, cr)) {
+        const int cc = group_sum<L>(group_part<L>(V, a, q, x, y, cr), gmask);
         if (cc < c) {
             c = cc;
             cur = cr;
@@ -458,15 +479,20 @@ __device__ __forceinline__ bool update_pixel(const Views& V, const int4& a, int 
     return changed;
 }
 
+constexpr int kHalfLanes = 4;
+constexpr int kHalfThreads = 256;
+constexpr int kHalfPixels = kHalfThreads / kHalfLanes;
+
 // One colour of the checkerboard over the whole grid, in place.  Used for
 // the random search of colour 0 after the last iteration of a scale.
 __global__ void __launch_bounds__(kHalfThreads) k_half_step(Fields F, HalfStep H) {
+    constexpr int L = kHalfLanes;
     const Field& A = pick(F);
     const Views& V = A.V;
-    const int q = threadIdx.x & (kLanes - 1);
-    const unsigned gmask = 0xFu << (threadIdx.x & 28);
+    const int q = threadIdx.x & (L - 1);
+    const unsigned gmask = group_mask<L>();
     const int gy = blockIdx.y;
-    const int gx = 2 * (blockIdx.x * kHalfPixels + (int)(threadIdx.x >> 2)) + ((H.colour + gy) & 1);
+    const int gx = 2 * (blockIdx.x * kHalfPixels + (int)(threadIdx.x / L)) + ((H.colour + gy) & 1);
     if (gx >= H.gw) return;  // the whole group leaves together
     const int x = gx * H.n, y = gy * H.n;
     const size_t i = pix(V.w, x, y);
@@ -479,17 +505,18 @@ __global__ void __launch_bounds__(kHalfThreads) k_half_step(Fields F, HalfStep H
     const int ca = has_a ? A.cost[ja] : kEmpty, cb = has_b ? A.cost[jb] : kEmpty;
     const uint2 wa = A.field[ja], wb = A.field[jb];
     if (!H.prop && c == kEmpty) return;
-    const int4 a = load_quarter(V.ref, i, q);
+    Slice<L> a;
+    load_slice<L>(V.ref, i, q, a);
     Vec4 cur = unpack_vec(wc);
-    if (update_pixel(V, a, q, gmask, H.n, H.s, H.key, A.mirror, x, y, (uint32_t)i, H.rs_before, H.rs_after,
-                     unpack_vec(wa), ca, unpack_vec(wb), cb, cur, c) &&
+    if (update_pixel<L>(V, a, q, gmask, H.n, H.s, H.key, A.mirror, x, y, (uint32_t)i, H.rs_before, H.rs_after,
+                        unpack_vec(wa), ca, unpack_vec(wb), cb, cur, c) &&
         q == 0) {
         A.field[i] = pack_vec(cur);
         A.cost[i] = c;
     }
 }
 
-// One whole iteration (both colours) over a 32x8 tile of grid pixels.
+// One whole iteration (both colours) over a TX x TY tile of grid pixels.
 // Phase 1 updates the colour-0 pixels of the tile and of a one-pixel halo on
 // the sides the colour-1 pixels read from (the predecessor sides of the
 // sweep), keeping the results in shared memory; phase 2 updates the
@@ -498,31 +525,31 @@ __global__ void __launch_bounds__(kHalfThreads) k_half_step(Fields F, HalfStep H
 // CTA's writes of the same iteration; halo pixels are computed redundantly
 // and only written by the CTA that owns them.  At scale 0 the records of
 // the two colours share cache lines, so the second phase mostly hits L1.
-constexpr int kTileX = 32, kTileY = 8;
-constexpr int kRegX = kTileX + 1, kRegY = kTileY + 1;
 constexpr int kItThreads = 256;
-constexpr int kItGroups = kItThreads / kLanes;
 
 struct IterStep {
     int n, s, gw, gh, dx, dy, it;
     uint2 key;
 };
 
+template <int L, int TX, int TY>
 __global__ void __launch_bounds__(kItThreads) k_iteration(Fields F, IterStep H) {
+    constexpr int kRegX = TX + 1, kRegY = TY + 1;
+    constexpr int kGroups = kItThreads / L;
     __shared__ uint2 s_vec[kRegX * kRegY];
     __shared__ int s_cost[kRegX * kRegY];
     const Field& A = pick(F);
     const Views& V = A.V;
-    const int q = threadIdx.x & (kLanes - 1);
-    const unsigned gmask = 0xFu << (threadIdx.x & 28);
-    const int grp = threadIdx.x >> 2;
-    const int tx0 = blockIdx.x * kTileX, ty0 = blockIdx.y * kTileY;
+    const int q = threadIdx.x & (L - 1);
+    const unsigned gmask = group_mask<L>();
+    const int grp = threadIdx.x / L;
+    const int tx0 = blockIdx.x * TX, ty0 = blockIdx.y * TY;
     const int rx0 = tx0 - (H.dx > 0 ? 1 : 0), ry0 = ty0 - (H.dy > 0 ? 1 : 0);  // region origin
     const int n = H.n;
 
     // phase 1: colour-0 pixels of the region (tile + halo)
     constexpr int kHalfRow = (kRegX + 1) / 2;
-    for (int k = grp; k < kHalfRow * kRegY; k += kItGroups) {
+    for (int k = grp; k < kHalfRow * kRegY; k += kGroups) {
         const int ry = k / kHalfRow;
         const int rx = 2 * (k % kHalfRow) + ((rx0 + ry0 + ry) & 1);
         const int gx = rx0 + rx, gy = ry0 + ry;
@@ -536,15 +563,16 @@ __global__ void __launch_bounds__(kItThreads) k_iteration(Fields F, IterStep H) 
         const uint2 wc = A.field[i];
         const int ca = has_a ? A.cost[ja] : kEmpty, cb = has_b ? A.cost[jb] : kEmpty;
         const uint2 wa = A.field[ja], wb = A.field[jb];
-        const int4 a = load_quarter(V.ref, i, q);
+        Slice<L> a;
+        load_slice<L>(V.ref, i, q, a);
         Vec4 cur = unpack_vec(wc);
-        update_pixel(V, a, q, gmask, n, H.s, H.key, A.mirror, x, y, (uint32_t)i, H.it - 1, -1, unpack_vec(wa), ca,
-                     unpack_vec(wb), cb, cur, c);
+        update_pixel<L>(V, a, q, gmask, n, H.s, H.key, A.mirror, x, y, (uint32_t)i, H.it - 1, -1, unpack_vec(wa), ca,
+                        unpack_vec(wb), cb, cur, c);
         if (q == 0) {
             const uint2 wv = pack_vec(cur);
             s_vec[ry * kRegX + rx] = wv;
             s_cost[ry * kRegX + rx] = c;
-            if (gx >= tx0 && gx < tx0 + kTileX && gy >= ty0 && gy < ty0 + kTileY) {
+            if (gx >= tx0 && gx < tx0 + TX && gy >= ty0 && gy < ty0 + TY) {
                 A.field_out[i] = wv;
                 A.cost_out[i] = c;
             }
@@ -553,8 +581,8 @@ __global__ void __launch_bounds__(kItThreads) k_iteration(Fields F, IterStep H) 
     __syncthreads();
 
     // phase 2: colour-1 pixels of the tile
-    constexpr int kTileHalfRow = kTileX / 2;
-    for (int k = grp; k < kTileHalfRow * kTileY; k += kItGroups) {
+    constexpr int kTileHalfRow = TX / 2;
+    for (int k = grp; k < kTileHalfRow * TY; k += kGroups) {
         const int ly = k / kTileHalfRow;
         const int gy = ty0 + ly;
         const int gx = tx0 + 2 * (k % kTileHalfRow) + ((tx0 + gy + 1) & 1);
@@ -563,7 +591,8 @@ __global__ void __launch_bounds__(kItThreads) k_iteration(Fields F, IterStep H) 
         const size_t i = pix(V.w, x, y);
         int c = A.cost[i];
         Vec4 cur = unpack_vec(A.field[i]);
-        const int4 a = load_quarter(V.ref, i, q);
+        Slice<L> a;
+        load_slice<L>(V.ref, i, q, a);
         const int agx = gx - H.dx, bgy = gy - H.dy;  // predecessors (colour 0, in the region)
         int ca = kEmpty, cb = kEmpty;
         uint2 wa = make_uint2(0u, 0u), wb = make_uint2(0u, 0u);
@@ -577,13 +606,33 @@ __global__ void __launch_bounds__(kItThreads) k_iteration(Fields F, IterStep H) 
             cb = s_cost[r];
             wb = s_vec[r];
         }
-        update_pixel(V, a, q, gmask, n, H.s, H.key, A.mirror, x, y, (uint32_t)i, -1, H.it, unpack_vec(wa), ca,
-                     unpack_vec(wb), cb, cur, c);
+        update_pixel<L>(V, a, q, gmask, n, H.s, H.key, A.mirror, x, y, (uint32_t)i, -1, H.it, unpack_vec(wa), ca,
+                        unpack_vec(wb), cb, cur, c);
         if (q == 0) {
             A.field_out[i] = pack_vec(cur);
             A.cost_out[i] = c;
         }
     }
+}
+
+// Instantiated (lanes per pixel, tile) variants; any of them gives identical
+// results.
+using IterKernel = void (*)(Fields, IterStep);
+struct IterVariant {
+    int lanes, tx, ty;
+    IterKernel k;
+};
+const IterVariant kIterVariants[] = {
+    {4, 32, 8, k_iteration<4, 32, 8>},   {4, 64, 8, k_iteration<4, 64, 8>},   {4, 32, 16, k_iteration<4, 32, 16>},
+    {4, 64, 16, k_iteration<4, 64, 16>}, {2, 32, 8, k_iteration<2, 32, 8>},   {2, 64, 8, k_iteration<2, 64, 8>},
+    {2, 32, 16, k_iteration<2, 32, 16>}, {2, 64, 16, k_iteration<2, 64, 16>}, {1, 32, 8, k_iteration<1, 32, 8>},
+    {1, 64, 8, k_iteration<1, 64, 8>},   {1, 32, 16, k_iteration<1, 32, 16>}, {1, 64, 16, k_iteration<1, 64, 16>},
+};
+
+const IterVariant* find_variant(const sff_tuning& t) {
+    for (const auto& v : kIterVariants)
+        if (v.lanes == t.lanes_per_pixel && v.tx == t.tile_x && v.ty == t.tile_y) return &v;
+    return nullptr;
 }
 
 int coarse_gq(int w, int h, const sff_params& p) {
@@ -615,7 +664,9 @@ struct FieldSpec {
 };
 
 int run_fields(const FieldSpec* spec, int nf, int width, int height, uint64_t seed, const sff_params& P,
-               void* workspace, cudaStream_t st) {
+               const sff_tuning& T, void* workspace, cudaStream_t st) {
+    const IterVariant* var = find_variant(T);
+    if (!var) return SFF_ERR_ARG;
     const int S = P.num_scales, I = P.iterations;
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     static const int kDirs[4][2] = {{1, 1}, {-1, -1}, {1, -1}, {-1, 1}};
@@ -665,7 +716,7 @@ int run_fields(const FieldSpec* spec, int nf, int width, int height, uint64_t se
                 cudaMemcpyAsync(tmp_field[k], spec[k].field, (size_t)width * height * 8, cudaMemcpyDeviceToDevice, st);
                 cudaMemcpyAsync(tmp_cost[k], spec[k].cost, (size_t)width * height * 4, cudaMemcpyDeviceToDevice, st);
             }
-        dim3 gi((gw + kTileX - 1) / kTileX, (gh + kTileY - 1) / kTileY, nf);
+        dim3 gi((gw + var->tx - 1) / var->tx, (gh + var->ty - 1) / var->ty, nf);
         for (int it = 0; it < I; ++it) {
             const bool from_user = ((I - it) & 1) == 0;  // the last iteration reads T and writes U
             for (int k = 0; k < nf; ++k) {
@@ -677,7 +728,9 @@ int run_fields(const FieldSpec* spec, int nf, int width, int height, uint64_t se
                 F.f[k].cost_out = from_user ? tmp_cost[k] : spec[k].cost;
             }
             IterStep H{n, s, gw, gh, kDirs[it % 4][0], kDirs[it % 4][1], it, key};
-            SFF_LAUNCH(k_iteration, gi, kItThreads, 0, st, F, H);
+            if (::sff::profiling()) ::sff::profile_mark("k_iteration", st, false);
+            var->k<<<gi, kItThreads, 0, st>>>(F, H);
+            if (::sff::profiling()) ::sff::profile_mark("k_iteration", st, true);
         }
         for (int k = 0; k < nf; ++k) {
             F.f[k].field = F.f[k].field_out = reinterpret_cast<uint2*>(spec[k].field);
@@ -720,15 +773,31 @@ extern "C" int sff_match_views(const uint8_t* pyr_ref_dev, const uint8_t* pyr_te
     if (((uintptr_t)field_dev & 7) || ((uintptr_t)cost_dev & 3) || ((uintptr_t)workspace & 255)) return SFF_ERR_ARG;
     if (workspace_bytes < match_ws_bytes(width, height, *params)) return SFF_ERR_WORKSPACE;
     FieldSpec f{pyr_ref_dev, pyr_temporal_dev, pyr_stereo_dev, pyr_cross_dev, field_dev, cost_dev, mirror};
-    return run_fields(&f, 1, width, height, seed, *params, workspace, (cudaStream_t)stream);
+    sff_tuning t;
+    sff_default_tuning(&t);
+    return run_fields(&f, 1, width, height, seed, *params, t, workspace, (cudaStream_t)stream);
 }
 
-extern "C" int sff_match_quad(const uint8_t* pyr_l0_dev, const uint8_t* pyr_r0_dev, const uint8_t* pyr_l1_dev,
-                              const uint8_t* pyr_r1_dev, int32_t width, int32_t height, uint64_t seed,
-                              const sff_params* params, int16_t* fwd_dev, int32_t* fwd_cost_dev, int16_t* inv_dev,
-                              int32_t* inv_cost_dev, void* workspace, size_t workspace_bytes, void* stream) {
+extern "C" int sff_default_tuning(sff_tuning* out) {
+    if (!out) return SFF_ERR_ARG;
+    out->lanes_per_pixel = 4;
+    out->tile_x = 32;
+    out->tile_y = 8;
+    return SFF_OK;
+}
+
+extern "C" int sff_tuning_supported(const sff_tuning* t) {
+    return t && sff::find_variant(*t) ? 1 : 0;
+}
+
+extern "C" int sff_match_quad_tuned(const uint8_t* pyr_l0_dev, const uint8_t* pyr_r0_dev, const uint8_t* pyr_l1_dev,
+                                    const uint8_t* pyr_r1_dev, int32_t width, int32_t height, uint64_t seed,
+                                    const sff_params* params, const sff_tuning* tuning, int16_t* fwd_dev,
+                                    int32_t* fwd_cost_dev, int16_t* inv_dev, int32_t* inv_cost_dev, void* workspace,
+                                    size_t workspace_bytes, void* stream) {
     using namespace sff;
     if (check_size(width, height) || check_params(params)) return SFF_ERR_ARG;
+    if (!tuning || !find_variant(*tuning)) return SFF_ERR_ARG;
     if (!pyr_l0_dev || !pyr_r0_dev || !pyr_l1_dev || !pyr_r1_dev || !fwd_dev || !fwd_cost_dev || !inv_dev ||
         !inv_cost_dev || !workspace)
         return SFF_ERR_ARG;
@@ -741,7 +810,17 @@ extern "C" int sff_match_quad(const uint8_t* pyr_l0_dev, const uint8_t* pyr_r0_d
     if (workspace_bytes < match_ws_bytes(width, height, *params)) return SFF_ERR_WORKSPACE;
     FieldSpec f[2] = {{pyr_l0_dev, pyr_l1_dev, pyr_r0_dev, pyr_r1_dev, fwd_dev, fwd_cost_dev, 0},
                       {pyr_r1_dev, pyr_r0_dev, pyr_l1_dev, pyr_l0_dev, inv_dev, inv_cost_dev, 1}};
-    return run_fields(f, 2, width, height, seed, *params, workspace, (cudaStream_t)stream);
+    return run_fields(f, 2, width, height, seed, *params, *tuning, workspace, (cudaStream_t)stream);
+}
+
+extern "C" int sff_match_quad(const uint8_t* pyr_l0_dev, const uint8_t* pyr_r0_dev, const uint8_t* pyr_l1_dev,
+                              const uint8_t* pyr_r1_dev, int32_t width, int32_t height, uint64_t seed,
+                              const sff_params* params, int16_t* fwd_dev, int32_t* fwd_cost_dev, int16_t* inv_dev,
+                              int32_t* inv_cost_dev, void* workspace, size_t workspace_bytes, void* stream) {
+    sff_tuning t;
+    sff_default_tuning(&t);
+    return sff_match_quad_tuned(pyr_l0_dev, pyr_r0_dev, pyr_l1_dev, pyr_r1_dev, width, height, seed, params, &t,
+                                fwd_dev, fwd_cost_dev, inv_dev, inv_cost_dev, workspace, workspace_bytes, stream);
 }
 
 extern "C" int sff_device_timeouts(uint32_t* out, int32_t reset) {

@@ -96,3 +96,11 @@ def test_product_path_has_no_oracle_dependency():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in text.replace("oracle-", ""), os.path.join(dirpath, f)
+
+
+def test_tuning_space(sff):
+    assert sff.default_tuning().as_tuple() in sff.TUNING_SPACE
+    for cand in sff.TUNING_SPACE:
+        assert sff.make_tuning(*cand).as_tuple() == cand
+    with pytest.raises(sff.SffError):
+        sff.make_tuning(3, 32, 8)

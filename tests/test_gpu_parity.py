@@ -246,3 +246,27 @@ def test_no_device_wait_timed_out(env):
     # every bounded device-side wait of the runs above completed
     torch, sff, orc = env
     assert sff.device_timeouts() == 0
+
+
+def test_every_tuning_gives_identical_fields(env):
+    # lanes per pixel and tile shape change the work distribution, never the result
+    torch, sff, orc = env
+    q = scenegen.make_named("planes_256x80", 7)
+    w, h = q.width, q.height
+    p = sff.default_params()
+    pyrs = [_gpu_features(torch, sff, im, p)[0] for im in q.images()]
+    ws = torch.empty(sff.workspace_bytes(w, h, p), dtype=torch.uint8, device="cuda")
+    ref = None
+    for cand in sff.TUNING_SPACE:
+        t = sff.make_tuning(*cand)
+        out = [torch.empty((h, w, 4), dtype=torch.int16, device="cuda") for _ in range(2)]
+        cst = [torch.empty((h, w), dtype=torch.int32, device="cuda") for _ in range(2)]
+        sff.match_quad_tuned(*pyrs, w, h, 5, t, out[0], cst[0], out[1], cst[1], ws, p)
+        torch.cuda.synchronize()
+        got = [a.cpu().numpy() for a in out + cst]
+        if ref is None:
+            ref = got
+            o = orc.run_quad(*q.images(), seed=5)
+            assert np.array_equal(got[0], o["fwd"]) and np.array_equal(got[1], o["inv"])
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b), cand
