@@ -42,7 +42,9 @@ FALLBACK_HBM_GBS = 6800.0
 #                 record 48 B + norm 4 B, one 52 B target record per view
 #   k_features    per pixel and scale: packed smoothed pixel 4 B in, 48 B
 #                 record + 4 B norm out
-ALGO_BYTES = {"k_half_step": 24 + 52 + 3 * 52, "k_features": 4 + 52}
+#   k_iteration   per grid pixel and iteration (each pixel is updated once
+#                 per iteration): the same 232 B as one half-step
+ALGO_BYTES = {"k_iteration": 24 + 52 + 3 * 52, "k_half_step": 24 + 52 + 3 * 52, "k_features": 4 + 52}
 
 
 def parse():
@@ -151,8 +153,8 @@ def ncu_traffic(kernel: str):
 def _units(kernel: str, w: int, h: int, params) -> float:
     """Units of work of `kernel` in one step (summed over its launches)."""
     S, I = params.num_scales, params.iterations
-    if kernel == "k_half_step":
-        # 2 fields x per scale: I iterations x 2 colours cover every grid pixel once per iteration
+    if kernel in ("k_iteration", "k_half_step"):
+        # 2 fields x per scale: I iterations, each updating every grid pixel once
         total = 0
         for s in range(S):
             n = 1 << s
@@ -238,7 +240,14 @@ def main():
 
     q = scenegen.make_named(args.workload, SCENE_SEED + rank)
     params = sff.default_params()
-    m = sff.QuadMatcher(q.width, q.height, params, device=dev)
+    # work distribution of the propagation kernels: autotuned once per image
+    # size (any setting gives bit-identical results)
+    from paper_1710_10096_gb300 import tune
+    probe = sff.QuadMatcher(q.width, q.height, params, device=dev)
+    probe.run(*[torch.as_tensor(im).to(dev) for im in q.images()], seed=MATCH_SEED)
+    tuning = tune.autotune(probe.pyr, q.width, q.height, params, reps=3)
+    del probe
+    m = sff.QuadMatcher(q.width, q.height, params, device=dev, tuning=tuning)
     stream = torch.cuda.Stream(device=dev)
     host_in = torch.empty((4, q.height, q.width, 3), dtype=torch.uint8).pin_memory()
     for k, im in enumerate(q.images()):
@@ -333,7 +342,8 @@ def main():
             "config": {"workload": args.workload, "width": q.width, "height": q.height, "quads_per_step": 1,
                        "parallelism": f"replicas{world}", "cuda_graph": True,
                        "l2": "flushed between timed steps (256 MB write outside the step events)",
-                       "params": params.as_dict(), "scene_seed": SCENE_SEED, "match_seed": MATCH_SEED},
+                       "params": params.as_dict(), "scene_seed": SCENE_SEED, "match_seed": MATCH_SEED,
+                       "tuning": {"lanes_per_pixel": tuning.lanes_per_pixel, "tile": [tuning.tile_x, tuning.tile_y]}},
             "roofline": roof, "gpu_launches": int(round(launches_per_step * args.steps)),
             "e2e": e2e, "clocks": clk, "kernels": kernels, "seeds": n_seeds}
     if rank == 0 and not args.no_cpu_baseline:

@@ -49,7 +49,7 @@ class Tuning(ctypes.Structure):
         return (self.lanes_per_pixel, self.tile_x, self.tile_y)
 
 
-TUNING_SPACE = [(l, tx, ty) for l in (4, 2, 1) for (tx, ty) in ((32, 8), (64, 8), (32, 16), (64, 16))]
+TUNING_SPACE = [(l, tx, ty) for l in (1, 2, 4) for (tx, ty) in ((64, 16), (32, 16), (64, 8), (32, 8), (16, 8), (8, 8))]
 
 
 class KernelTime(ctypes.Structure):

@@ -622,12 +622,31 @@ struct IterVariant {
     int lanes, tx, ty;
     IterKernel k;
 };
-const IterVariant kIterVariants[] = {
-    {4, 32, 8, k_iteration<4, 32, 8>},   {4, 64, 8, k_iteration<4, 64, 8>},   {4, 32, 16, k_iteration<4, 32, 16>},
-    {4, 64, 16, k_iteration<4, 64, 16>}, {2, 32, 8, k_iteration<2, 32, 8>},   {2, 64, 8, k_iteration<2, 64, 8>},
-    {2, 32, 16, k_iteration<2, 32, 16>}, {2, 64, 16, k_iteration<2, 64, 16>}, {1, 32, 8, k_iteration<1, 32, 8>},
-    {1, 64, 8, k_iteration<1, 64, 8>},   {1, 32, 16, k_iteration<1, 32, 16>}, {1, 64, 16, k_iteration<1, 64, 16>},
-};
+#define SFF_ITER_VARIANTS(L)                                                                              \
+    {L, 64, 16, k_iteration<L, 64, 16>}, {L, 32, 16, k_iteration<L, 32, 16>}, {L, 64, 8, k_iteration<L, 64, 8>}, \
+        {L, 32, 8, k_iteration<L, 32, 8>}, {L, 16, 8, k_iteration<L, 16, 8>}, {L, 8, 8, k_iteration<L, 8, 8>}
+const IterVariant kIterVariants[] = {SFF_ITER_VARIANTS(1), SFF_ITER_VARIANTS(2), SFF_ITER_VARIANTS(4)};
+#undef SFF_ITER_VARIANTS
+
+// Tile of the iteration kernel at one scale: the tuned tile for grids that
+// fill the GPU, else the largest smaller tile (same lanes per pixel) that
+// still gives at least two CTAs per SM, else the smallest.  Any tile gives
+// the same result.
+const IterVariant* tile_for_grid(const IterVariant* tuned, int gw, int gh, int nf) {
+    constexpr int kWantCtas = 2 * 152;
+    const IterVariant* pick_v = nullptr;
+    for (const auto& v : kIterVariants) {
+        if (v.lanes != tuned->lanes || v.tx * v.ty > tuned->tx * tuned->ty) continue;
+        const long ctas = (long)((gw + v.tx - 1) / v.tx) * ((gh + v.ty - 1) / v.ty) * nf;
+        if (ctas >= kWantCtas) {
+            if (!pick_v || v.tx * v.ty > pick_v->tx * pick_v->ty) pick_v = &v;
+        }
+    }
+    if (pick_v) return (tuned->tx * tuned->ty == pick_v->tx * pick_v->ty) ? tuned : pick_v;
+    for (const auto& v : kIterVariants)  // none fills the GPU: the smallest tile
+        if (v.lanes == tuned->lanes && (!pick_v || v.tx * v.ty < pick_v->tx * pick_v->ty)) pick_v = &v;
+    return pick_v;
+}
 
 const IterVariant* find_variant(const sff_tuning& t) {
     for (const auto& v : kIterVariants)
@@ -716,7 +735,8 @@ int run_fields(const FieldSpec* spec, int nf, int width, int height, uint64_t se
                 cudaMemcpyAsync(tmp_field[k], spec[k].field, (size_t)width * height * 8, cudaMemcpyDeviceToDevice, st);
                 cudaMemcpyAsync(tmp_cost[k], spec[k].cost, (size_t)width * height * 4, cudaMemcpyDeviceToDevice, st);
             }
-        dim3 gi((gw + var->tx - 1) / var->tx, (gh + var->ty - 1) / var->ty, nf);
+        const IterVariant* sv = tile_for_grid(var, gw, gh, nf);
+        dim3 gi((gw + sv->tx - 1) / sv->tx, (gh + sv->ty - 1) / sv->ty, nf);
         for (int it = 0; it < I; ++it) {
             const bool from_user = ((I - it) & 1) == 0;  // the last iteration reads T and writes U
             for (int k = 0; k < nf; ++k) {
@@ -729,7 +749,7 @@ int run_fields(const FieldSpec* spec, int nf, int width, int height, uint64_t se
             }
             IterStep H{n, s, gw, gh, kDirs[it % 4][0], kDirs[it % 4][1], it, key};
             if (::sff::profiling()) ::sff::profile_mark("k_iteration", st, false);
-            var->k<<<gi, kItThreads, 0, st>>>(F, H);
+            sv->k<<<gi, kItThreads, 0, st>>>(F, H);
             if (::sff::profiling()) ::sff::profile_mark("k_iteration", st, true);
         }
         for (int k = 0; k < nf; ++k) {
@@ -780,9 +800,9 @@ extern "C" int sff_match_views(const uint8_t* pyr_ref_dev, const uint8_t* pyr_te
 
 extern "C" int sff_default_tuning(sff_tuning* out) {
     if (!out) return SFF_ERR_ARG;
-    out->lanes_per_pixel = 4;
+    out->lanes_per_pixel = 1;
     out->tile_x = 32;
-    out->tile_y = 8;
+    out->tile_y = 16;
     return SFF_OK;
 }
 
