@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sff", choices=["sff", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tuning", default="auto",
+                    help="work distribution of the propagation kernels: 'auto' (autotune) or L,TX,TY")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(scenegen.CONFIG_SIZES),
                     help="scene (profiling uses the small planes_256x80 case)")
     return ap.parse_args()
@@ -243,10 +245,13 @@ def main():
     # work distribution of the propagation kernels: autotuned once per image
     # size (any setting gives bit-identical results)
     from paper_1710_10096_gb300 import tune
-    probe = sff.QuadMatcher(q.width, q.height, params, device=dev)
-    probe.run(*[torch.as_tensor(im).to(dev) for im in q.images()], seed=MATCH_SEED)
-    tuning = tune.autotune(probe.pyr, q.width, q.height, params, reps=3)
-    del probe
+    if args.tuning == "auto":
+        probe = sff.QuadMatcher(q.width, q.height, params, device=dev)
+        probe.run(*[torch.as_tensor(im).to(dev) for im in q.images()], seed=MATCH_SEED)
+        tuning = tune.autotune(probe.pyr, q.width, q.height, params, reps=3)
+        del probe
+    else:
+        tuning = sff.make_tuning(*(int(v) for v in args.tuning.split(",")))
     m = sff.QuadMatcher(q.width, q.height, params, device=dev, tuning=tuning)
     stream = torch.cuda.Stream(device=dev)
     host_in = torch.empty((4, q.height, q.width, 3), dtype=torch.uint8).pin_memory()

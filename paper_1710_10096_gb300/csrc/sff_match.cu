@@ -525,7 +525,13 @@ __global__ void __launch_bounds__(kHalfThreads) k_half_step(Fields F, HalfStep H
 // CTA's writes of the same iteration; halo pixels are computed redundantly
 // and only written by the CTA that owns them.  At scale 0 the records of
 // the two colours share cache lines, so the second phase mostly hits L1.
-constexpr int kItThreads = 256;
+// Threads of the iteration kernel: enough L-lane groups for one colour-0
+// cell of the region (tile + halo) each, so that both phases finish in one
+// round and no thread waits at the barrier for a second pixel of another.
+template <int L, int TX, int TY>
+__host__ __device__ constexpr int iter_threads() {
+    return ((L * (((TX + 1) * (TY + 1) + 1) / 2)) + 31) / 32 * 32;
+}
 
 struct IterStep {
     int n, s, gw, gh, dx, dy, it;
@@ -533,9 +539,9 @@ struct IterStep {
 };
 
 template <int L, int TX, int TY>
-__global__ void __launch_bounds__(kItThreads) k_iteration(Fields F, IterStep H) {
+__global__ void __launch_bounds__(iter_threads<L, TX, TY>()) k_iteration(Fields F, IterStep H) {
     constexpr int kRegX = TX + 1, kRegY = TY + 1;
-    constexpr int kGroups = kItThreads / L;
+    constexpr int kGroups = iter_threads<L, TX, TY>() / L;
     __shared__ uint2 s_vec[kRegX * kRegY];
     __shared__ int s_cost[kRegX * kRegY];
     const Field& A = pick(F);
@@ -621,12 +627,15 @@ using IterKernel = void (*)(Fields, IterStep);
 struct IterVariant {
     int lanes, tx, ty;
     IterKernel k;
+    int threads;
 };
-#define SFF_ITER_VARIANTS(L)                                                                              \
-    {L, 64, 16, k_iteration<L, 64, 16>}, {L, 32, 16, k_iteration<L, 32, 16>}, {L, 64, 8, k_iteration<L, 64, 8>}, \
-        {L, 32, 8, k_iteration<L, 32, 8>}, {L, 16, 8, k_iteration<L, 16, 8>}, {L, 8, 8, k_iteration<L, 8, 8>}
+#define SFF_ITER_V(L, X, Y) {L, X, Y, k_iteration<L, X, Y>, iter_threads<L, X, Y>()}
+#define SFF_ITER_VARIANTS(L)                                                                        \
+    SFF_ITER_V(L, 64, 16), SFF_ITER_V(L, 32, 16), SFF_ITER_V(L, 64, 8), SFF_ITER_V(L, 32, 8), \
+        SFF_ITER_V(L, 16, 8), SFF_ITER_V(L, 8, 8)
 const IterVariant kIterVariants[] = {SFF_ITER_VARIANTS(1), SFF_ITER_VARIANTS(2), SFF_ITER_VARIANTS(4)};
 #undef SFF_ITER_VARIANTS
+#undef SFF_ITER_V
 
 // Tile of the iteration kernel at one scale: the tuned tile for grids that
 // fill the GPU, else the largest smaller tile (same lanes per pixel) that
@@ -749,7 +758,7 @@ int run_fields(const FieldSpec* spec, int nf, int width, int height, uint64_t se
             }
             IterStep H{n, s, gw, gh, kDirs[it % 4][0], kDirs[it % 4][1], it, key};
             if (::sff::profiling()) ::sff::profile_mark("k_iteration", st, false);
-            sv->k<<<gi, kItThreads, 0, st>>>(F, H);
+            sv->k<<<gi, sv->threads, 0, st>>>(F, H);
             if (::sff::profiling()) ::sff::profile_mark("k_iteration", st, true);
         }
         for (int k = 0; k < nf; ++k) {
