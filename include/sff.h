@@ -76,8 +76,8 @@ typedef struct sff_params {
  * Every supported setting gives bit-identical results; only speed differs.
  * Supported: lanes_per_pixel in {1, 2, 4} x (tile_x, tile_y) in
  * {(64, 16), (32, 16), (64, 8), (32, 8), (16, 8), (8, 8)} grid pixels.  The
- * tile applies to grids that fill the GPU; coarser scales use the largest
- * smaller tile that still gives two CTAs per SM. */
+ * tile is used at scale 0 (and at coarser scales whose grid it splits into
+ * at least two CTAs per SM; otherwise the largest smaller tile that does). */
 typedef struct sff_tuning {
     int32_t lanes_per_pixel; /* threads that share one pixel's feature loads */
     int32_t tile_x, tile_y;  /* grid pixels per CTA of the iteration kernel */

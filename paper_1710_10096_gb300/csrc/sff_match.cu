@@ -527,10 +527,13 @@ __global__ void __launch_bounds__(kHalfThreads) k_half_step(Fields F, HalfStep H
 // the two colours share cache lines, so the second phase mostly hits L1.
 // Threads of the iteration kernel: enough L-lane groups for one colour-0
 // cell of the region (tile + halo) each, so that both phases finish in one
-// round and no thread waits at the barrier for a second pixel of another.
+// round and no thread waits at the barrier for a second pixel of another;
+// at most 1024 (larger settings take more rounds).
 template <int L, int TX, int TY>
 __host__ __device__ constexpr int iter_threads() {
-    return ((L * (((TX + 1) * (TY + 1) + 1) / 2)) + 31) / 32 * 32;
+    return ((L * (((TX + 1) * (TY + 1) + 1) / 2)) + 31) / 32 * 32 > 1024
+               ? 1024
+               : ((L * (((TX + 1) * (TY + 1) + 1) / 2)) + 31) / 32 * 32;
 }
 
 struct IterStep {
@@ -637,11 +640,12 @@ const IterVariant kIterVariants[] = {SFF_ITER_VARIANTS(1), SFF_ITER_VARIANTS(2),
 #undef SFF_ITER_VARIANTS
 #undef SFF_ITER_V
 
-// Tile of the iteration kernel at one scale: the tuned tile for grids that
-// fill the GPU, else the largest smaller tile (same lanes per pixel) that
-// still gives at least two CTAs per SM, else the smallest.  Any tile gives
-// the same result.
-const IterVariant* tile_for_grid(const IterVariant* tuned, int gw, int gh, int nf) {
+// Tile of the iteration kernel at one scale: the tuned tile at scale 0; at
+// coarser scales the tuned tile if its grid fills the GPU, else the largest
+// smaller tile (same lanes per pixel) that still gives at least two CTAs per
+// SM, else the smallest.  Any tile gives the same result.
+const IterVariant* tile_for_grid(const IterVariant* tuned, int s, int gw, int gh, int nf) {
+    if (s == 0) return tuned;
     constexpr int kWantCtas = 2 * 152;
     const IterVariant* pick_v = nullptr;
     for (const auto& v : kIterVariants) {
@@ -744,7 +748,7 @@ int run_fields(const FieldSpec* spec, int nf, int width, int height, uint64_t se
                 cudaMemcpyAsync(tmp_field[k], spec[k].field, (size_t)width * height * 8, cudaMemcpyDeviceToDevice, st);
                 cudaMemcpyAsync(tmp_cost[k], spec[k].cost, (size_t)width * height * 4, cudaMemcpyDeviceToDevice, st);
             }
-        const IterVariant* sv = tile_for_grid(var, gw, gh, nf);
+        const IterVariant* sv = tile_for_grid(var, s, gw, gh, nf);
         dim3 gi((gw + sv->tx - 1) / sv->tx, (gh + sv->ty - 1) / sv->ty, nf);
         for (int it = 0; it < I; ++it) {
             const bool from_user = ((I - it) & 1) == 0;  // the last iteration reads T and writes U
