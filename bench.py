@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sff", choices=["sff", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 32-quad batched measurement")
     ap.add_argument("--tuning", default="auto",
                     help="work distribution of the propagation kernels: 'auto' (autotune) or L,TX,TY")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(scenegen.CONFIG_SIZES),
@@ -186,6 +187,79 @@ def cpu_baseline(q, seed, target_s=12.0):
                       f"{cores} OpenMP threads, {statistics.mean(times):.2f} s each"}, ref
 
 
+# The batched workload: 32 quads of uneven sizes, 8 each, scene seeds 100..131
+BATCH_SIZES = [("driving", 1242, 375), ("driving", 1024, 436), ("planes", 640, 192), ("planes", 512, 160)]
+BATCH_PER_SIZE = 8
+
+
+def _gen_batch_quad(args):
+    fam, w, h, seed = args
+    q = scenegen.make_quad(fam, w, h, seed, supersample=1, with_gt=False)
+    return q.L0, q.R0, q.L1, q.R1
+
+
+def make_batch_quads():
+    """The 32 quads, rendered in a spawn process pool (before any GPU work)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    jobs = [(fam, w, h, 100 + k * BATCH_PER_SIZE + j) for k, (fam, w, h) in enumerate(BATCH_SIZES)
+            for j in range(BATCH_PER_SIZE)]
+    with cf.ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1), mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_gen_batch_quad, jobs)), [j[3] for j in jobs]
+
+
+def bench_batched(sff, torch, dev, quads, seeds, params, tuning, steps, warmup):
+    """Matched px/s of the 32-quad batch: one CUDA graph of shared launches
+    (sff_run_batch) vs the plain per-quad form (one graph per quad, replayed
+    one after the other); outputs compared for identity."""
+    sizes = [(im[0].shape[1], im[0].shape[0]) for im in quads]
+    px = sum(w * h for w, h in sizes)
+    bm = sff.BatchMatcher(sizes, params, device=dev, tuning=tuning)
+    for k, im in enumerate(quads):
+        bm.load(k, *im)
+    g_batch = bm.capture(seeds)
+    # plain: one matcher + graph per quad
+    plain = []
+    for k, im in enumerate(quads):
+        m = sff.QuadMatcher(sizes[k][0], sizes[k][1], params, device=dev, tuning=tuning)
+        for j in range(4):
+            m.dev_in[j].copy_(torch.as_tensor(im[j]))
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream(device=dev)
+        with torch.cuda.stream(s):
+            m.run(*m.dev_in.unbind(0), seed=seeds[k], stream=s)
+            s.synchronize()
+            with torch.cuda.graph(g, stream=s):
+                m.run(*m.dev_in.unbind(0), seed=seeds[k], stream=torch.cuda.current_stream(dev))
+        plain.append((m, g))
+    torch.cuda.synchronize(dev)
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            fn()
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b) / steps / 1e3
+
+    t_batch = timed(g_batch.replay)
+    t_plain = timed(lambda: [g.replay() for _, g in plain])
+    same = all(bq.seeds_numpy().tobytes() == m.buf.seeds_numpy().tobytes()
+               and torch.equal(bq.fwd, m.fwd) and torch.equal(bq.inv, m.inv) for bq, (m, _) in zip(bm.quads, plain))
+    out = {"workload": "32 quads: 8 x 1242x375 + 8 x 1024x436 (driving scenes), 8 x 640x192 + 8 x 512x160 "
+                       "(planes scenes), scene seeds 100..131",
+           "px_per_step": px, "value": px / t_batch, "unit": "px/s", "ms_per_step": 1e3 * t_batch,
+           "plain_value": px / t_plain, "plain_ms_per_step": 1e3 * t_plain, "speedup_vs_plain": t_plain / t_batch,
+           "identical_to_plain": bool(same), "cuda_graph": True}
+    del bm, plain, g_batch
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
@@ -233,6 +307,7 @@ def main():
     import paper_1710_10096_gb300 as sff
 
     rank, world, local = dist_info()
+    batch = None if args.no_batch else make_batch_quads()  # CPU work before any GPU call
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
@@ -351,6 +426,9 @@ def main():
                        "tuning": {"lanes_per_pixel": tuning.lanes_per_pixel, "tile": [tuning.tile_x, tuning.tile_y]}},
             "roofline": roof, "gpu_launches": int(round(launches_per_step * args.steps)),
             "e2e": e2e, "clocks": clk, "kernels": kernels, "seeds": n_seeds}
+    if batch is not None:
+        line["batched"] = bench_batched(sff, torch, dev, batch[0], batch[1], params, tuning, min(args.steps, 20),
+                                        max(1, args.warmup))
     if rank == 0 and not args.no_cpu_baseline:
         cb, ref = cpu_baseline(q, MATCH_SEED)
         line["cpu_baseline"] = cb

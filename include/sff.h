@@ -237,6 +237,41 @@ int sff_emit_seeds_noalloc(const int16_t* fwd_dev, const int32_t* fwd_cost_dev,
                            int32_t width, int32_t height, sff_seed* seeds_dev, int32_t capacity,
                            int32_t* count_dev, void* stream);
 
+/* One quad of a batch: its images, outputs and scratch (device pointers).
+ * The four images share one pitch; seeds are written as by sff_emit_seeds. */
+#define SFF_MAX_BATCH 32
+typedef struct sff_quad {
+    const uint8_t* rgb[4];     /* L0, R0, L1, R1: H x W x 3 uint8 */
+    int32_t pitch_bytes;       /* row pitch of the four images (>= 3 W) */
+    int32_t width, height;
+    uint64_t seed;             /* random-search seed of this quad */
+    uint8_t* pyramid[4];       /* sff_pyramid_bytes() each, 16-byte aligned */
+    int16_t* fwd;              /* [H][W][4] forward field of L0 */
+    int32_t* fwd_cost;
+    int16_t* inv;              /* [H][W][4] inverse field of R1 */
+    int32_t* inv_cost;
+    uint8_t* keep;             /* [H][W] filter result */
+    uint8_t* cerr;             /* [H][W] consistency error */
+    sff_seed* seeds;           /* room for `capacity` seeds */
+    int32_t capacity;
+    int32_t* count;            /* device int32: number of seeds */
+    void* workspace;           /* sff_quad_workspace_bytes(), 256-byte aligned */
+    size_t workspace_bytes;
+} sff_quad;
+
+/* Scratch one quad of sff_run_batch needs; 0 for invalid arguments. */
+size_t sff_quad_workspace_bytes(int32_t width, int32_t height, const sff_params* params);
+
+/* The whole stage (Sec. 3.1-3.2: sff_features on the four images,
+ * sff_match_quad, sff_consistency_filter, sff_emit_seeds) for n <= 32 quads
+ * of any sizes, each phase in shared kernel launches.  Every quad's outputs
+ * are identical to running those calls on it alone with its own seed.
+ * `quads` is a host array read during the call; tuning NULL = default.
+ * The enqueued work has no host synchronisation and can be captured into a
+ * CUDA graph. */
+int sff_run_batch(const sff_quad* quads, int32_t n, const sff_params* params, const sff_tuning* tuning,
+                  void* stream);
+
 /* Per-kernel timing (no counterpart in the paper: measurement support).
  * While enabled, every kernel launch of the library is bracketed by two
  * CUDA events recorded on the launch's stream.  Enabling or disabling

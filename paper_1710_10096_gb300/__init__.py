@@ -17,8 +17,10 @@ import os
 
 import numpy as np
 
-__all__ = ["Params", "SffError", "default_params", "pyramid_bytes", "workspace_bytes", "features", "match_views",
-           "consistency_filter", "emit_seeds", "QuadMatcher", "SEED_DTYPE", "lib", "build"]
+__all__ = ["Params", "Tuning", "SffError", "default_params", "default_tuning", "make_tuning", "pyramid_bytes",
+           "workspace_bytes", "quad_workspace_bytes", "features", "match_views", "match_quad", "match_quad_tuned",
+           "consistency_filter", "emit_seeds", "run_batch", "QuadBuffers", "BatchMatcher", "QuadMatcher",
+           "SEED_DTYPE", "lib", "build"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsff.so")
@@ -50,6 +52,19 @@ class Tuning(ctypes.Structure):
 
 
 TUNING_SPACE = [(l, tx, ty) for l in (1, 2, 4) for (tx, ty) in ((64, 16), (32, 16), (64, 8), (32, 8), (16, 8), (8, 8))]
+
+
+class QuadDesc(ctypes.Structure):
+    """sff_quad of include/sff.h."""
+    _fields_ = [("rgb", ctypes.c_void_p * 4), ("pitch_bytes", ctypes.c_int32), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("seed", ctypes.c_uint64), ("pyramid", ctypes.c_void_p * 4),
+                ("fwd", ctypes.c_void_p), ("fwd_cost", ctypes.c_void_p), ("inv", ctypes.c_void_p),
+                ("inv_cost", ctypes.c_void_p), ("keep", ctypes.c_void_p), ("cerr", ctypes.c_void_p),
+                ("seeds", ctypes.c_void_p), ("capacity", ctypes.c_int32), ("count", ctypes.c_void_p),
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
+
+
+MAX_BATCH = 32
 
 
 class KernelTime(ctypes.Structure):
@@ -110,6 +125,10 @@ def lib():
         L.sff_default_tuning.restype = i32
         L.sff_tuning_supported.argtypes = [ctypes.POINTER(Tuning)]
         L.sff_tuning_supported.restype = i32
+        L.sff_quad_workspace_bytes.argtypes = [i32, i32, PP]
+        L.sff_quad_workspace_bytes.restype = sz
+        L.sff_run_batch.argtypes = [ctypes.POINTER(QuadDesc), i32, PP, ctypes.POINTER(Tuning), P]
+        L.sff_run_batch.restype = i32
         L.sff_consistency_filter.argtypes = [P, P, P, P, i32, i32, PP, P, P, P, sz, P]
         L.sff_consistency_filter.restype = i32
         L.sff_emit_seeds.argtypes = [P, P, P, P, i32, i32, P, i32, P, P, sz, P]
@@ -260,76 +279,146 @@ def seeds_to_numpy(seeds_bytes: np.ndarray, count: int) -> np.ndarray:
     return np.frombuffer(np.ascontiguousarray(seeds_bytes).tobytes(), SEED_DTYPE)[:count].copy()
 
 
-class QuadMatcher:
-    """Device buffers for W x H quads and the four calls of the stage in order.
+def quad_workspace_bytes(width: int, height: int, params: Params = None) -> int:
+    params = params or default_params()
+    return lib().sff_quad_workspace_bytes(width, height, ctypes.byref(params))
 
-    run() works on CUDA tensors already on the device; run_host() takes host
-    arrays, copies them in, runs the stage and copies the seeds back.
-    """
 
-    def __init__(self, width: int, height: int, params: Params = None, device="cuda", concurrent: bool = True,
-                 tuning: Tuning = None):
+class QuadBuffers:
+    """Device buffers of one W x H quad: input images, pyramids, fields,
+    filter masks, seeds and scratch."""
+
+    def __init__(self, width: int, height: int, params: Params, device, per_call_workspaces: int = 0):
         import torch
         self.width, self.height = int(width), int(height)
-        self.params = params or default_params()
-        self.tuning = tuning or default_tuning()
-        self.device = torch.device(device)
-        self.concurrent = concurrent
         w, h = self.width, self.height
-        pb = pyramid_bytes(w, h, self.params)
-        wb = workspace_bytes(w, h, self.params)
-        if pb == 0 or wb == 0:
+        pb = pyramid_bytes(w, h, params)
+        qb = quad_workspace_bytes(w, h, params)
+        if pb == 0 or qb == 0:
             raise SffError(f"invalid size {w}x{h} or parameters")
-        u8 = dict(dtype=torch.uint8, device=self.device)
-        self.pyr = [torch.empty(pb, **u8) for _ in range(4)]  # L0, R0, L1, R1
-        # one workspace per concurrent stream: the features of the four images
-        # run on four streams; both fields then share the launches of
-        # sff_match_quad
-        self.workspaces = [torch.empty(wb, **u8) for _ in range(4 if concurrent else 1)]
-        self.workspace = self.workspaces[0]
-        self._side = [torch.cuda.Stream(device=self.device) for _ in range(3)] if concurrent else []
-        self.fwd = torch.empty((h, w, 4), dtype=torch.int16, device=self.device)
-        self.inv = torch.empty((h, w, 4), dtype=torch.int16, device=self.device)
-        self.fwd_cost = torch.empty((h, w), dtype=torch.int32, device=self.device)
-        self.inv_cost = torch.empty((h, w), dtype=torch.int32, device=self.device)
+        u8 = dict(dtype=torch.uint8, device=device)
+        self.dev_in = torch.empty((4, h, w, 3), **u8)  # L0, R0, L1, R1
+        self.pyr = [torch.empty(pb, **u8) for _ in range(4)]
+        self.workspace = torch.empty(qb, **u8)
+        self.fwd = torch.empty((h, w, 4), dtype=torch.int16, device=device)
+        self.inv = torch.empty((h, w, 4), dtype=torch.int16, device=device)
+        self.fwd_cost = torch.empty((h, w), dtype=torch.int32, device=device)
+        self.inv_cost = torch.empty((h, w), dtype=torch.int32, device=device)
         self.keep = torch.empty((h, w), **u8)
         self.cerr = torch.empty((h, w), **u8)
         self.capacity = seed_capacity(w, h)
         self.seeds = torch.empty(20 * self.capacity, **u8)
-        self.count = torch.zeros(1, dtype=torch.int32, device=self.device)
+        self.count = torch.zeros(1, dtype=torch.int32, device=device)
+
+    def desc(self, images, seed: int) -> QuadDesc:
+        imgs = list(images) if images is not None else list(self.dev_in.unbind(0))
+        pitch = imgs[0].stride(0)
+        for im in imgs:
+            assert im.is_cuda and im.stride(0) == pitch and im.stride(1) == 3 and im.stride(2) == 1
+            assert tuple(im.shape) == (self.height, self.width, 3)
+        d = QuadDesc()
+        for k in range(4):
+            d.rgb[k] = imgs[k].data_ptr()
+            d.pyramid[k] = self.pyr[k].data_ptr()
+        d.pitch_bytes, d.width, d.height, d.seed = pitch, self.width, self.height, int(seed) & (2 ** 64 - 1)
+        d.fwd, d.fwd_cost = self.fwd.data_ptr(), self.fwd_cost.data_ptr()
+        d.inv, d.inv_cost = self.inv.data_ptr(), self.inv_cost.data_ptr()
+        d.keep, d.cerr = self.keep.data_ptr(), self.cerr.data_ptr()
+        d.seeds, d.capacity, d.count = self.seeds.data_ptr(), self.capacity, self.count.data_ptr()
+        d.workspace, d.workspace_bytes = self.workspace.data_ptr(), _nbytes(self.workspace)
+        return d
+
+    def seeds_numpy(self) -> np.ndarray:
+        n = int(self.count.item())
+        return seeds_to_numpy(self.seeds.cpu().numpy(), min(n, self.capacity))
+
+
+def run_batch(descs, params: Params = None, tuning: Tuning = None, stream=None) -> None:
+    """sff_run_batch on a list of QuadDesc (at most MAX_BATCH)."""
+    params = params or default_params()
+    arr = (QuadDesc * len(descs))(*descs)
+    _check(lib().sff_run_batch(arr, len(descs), ctypes.byref(params), ctypes.byref(tuning) if tuning else None,
+                               _stream(stream)), "sff_run_batch")
+
+
+class BatchMatcher:
+    """Buffers for a fixed list of quad sizes; run() matches all of them in
+    shared launches (sff_run_batch), capture() records that into a CUDA graph."""
+
+    def __init__(self, sizes, params: Params = None, device="cuda", tuning: Tuning = None):
+        import torch
+        if not 1 <= len(sizes) <= MAX_BATCH:
+            raise SffError(f"a batch holds 1..{MAX_BATCH} quads")
+        self.params = params or default_params()
+        self.tuning = tuning or default_tuning()
+        self.device = torch.device(device)
+        self.quads = [QuadBuffers(w, h, self.params, self.device) for (w, h) in sizes]
+
+    def load(self, k: int, L0, R0, L1, R1) -> None:
+        """Copy host (or device) images of quad k into its device input buffer."""
+        import torch
+        for j, im in enumerate((L0, R0, L1, R1)):
+            self.quads[k].dev_in[j].copy_(torch.as_tensor(np.ascontiguousarray(im)) if isinstance(im, np.ndarray) else im,
+                                          non_blocking=True)
+
+    def run(self, seeds, stream=None) -> None:
+        descs = [q.desc(None, sd) for q, sd in zip(self.quads, seeds)]
+        run_batch(descs, self.params, self.tuning, stream)
+
+    def capture(self, seeds):
+        """A CUDA graph replaying run(seeds) on the current input buffers."""
+        import torch
+        s = torch.cuda.Stream(device=self.device)
+        s.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(s):
+            self.run(seeds, s)  # warm-up outside the capture
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            self.run(seeds, torch.cuda.current_stream(self.device))
+        return g
+
+
+class QuadMatcher:
+    """One W x H quad.  run() works on CUDA images already on the device;
+    run_host() takes host arrays, copies them in, runs the stage and copies
+    the seeds back.
+
+    mode "batch" runs the whole stage with sff_run_batch (one quad); mode
+    "calls" runs the four calls sff_features x4, sff_match_quad,
+    sff_consistency_filter and sff_emit_seeds.  Both give identical results.
+    """
+
+    def __init__(self, width: int, height: int, params: Params = None, device="cuda", tuning: Tuning = None,
+                 mode: str = "batch"):
+        import torch
+        self.params = params or default_params()
+        self.tuning = tuning or default_tuning()
+        self.device = torch.device(device)
+        self.mode = mode
+        self.buf = QuadBuffers(width, height, self.params, self.device)
+        b = self.buf
+        self.width, self.height = b.width, b.height
+        self.pyr, self.fwd, self.inv, self.fwd_cost, self.inv_cost = b.pyr, b.fwd, b.inv, b.fwd_cost, b.inv_cost
+        self.keep, self.cerr, self.seeds, self.count, self.capacity = b.keep, b.cerr, b.seeds, b.count, b.capacity
+        self.workspace = b.workspace
         self._host_in = None
 
     def run(self, L0, R0, L1, R1, seed: int, stream=None):
         """All four calls on device images; returns (seeds bytes tensor, count tensor)."""
-        import torch
         p = self.params
-        main = stream if stream is not None else torch.cuda.current_stream(self.device)
+        if self.mode == "batch":
+            run_batch([self.buf.desc((L0, R0, L1, R1), seed)], p, self.tuning, stream)
+            return self.seeds, self.count
+        ws = workspace_bytes(self.width, self.height, p)
+        w = self.workspace[:ws]
+        for img, pyr in zip((L0, R0, L1, R1), self.pyr):
+            features(img, pyr, w, p, stream)
         pL0, pR0, pL1, pR1 = self.pyr
-        if not self.concurrent:
-            for img, pyr in zip((L0, R0, L1, R1), self.pyr):
-                features(img, pyr, self.workspace, p, main)
-            match_views(pL0, pL1, pR0, pR1, self.width, self.height, 0, seed, self.fwd, self.fwd_cost,
-                        self.workspace, p, main)
-            match_views(pR1, pR0, pL1, pL0, self.width, self.height, 1, seed, self.inv, self.inv_cost,
-                        self.workspace, p, main)
-        else:
-            streams = [main] + self._side
-            fork = torch.cuda.Event()
-            fork.record(main)
-            for st in self._side:
-                st.wait_event(fork)
-            for img, pyr, ws, st in zip((L0, R0, L1, R1), self.pyr, self.workspaces, streams):
-                features(img, pyr, ws, p, st)
-            for st in self._side:
-                done = torch.cuda.Event()
-                done.record(st)
-                main.wait_event(done)
-            match_quad_tuned(pL0, pR0, pL1, pR1, self.width, self.height, seed, self.tuning, self.fwd,
-                             self.fwd_cost, self.inv, self.inv_cost, self.workspace, p, main)
-        consistency_filter(self.fwd, self.fwd_cost, self.inv, self.inv_cost, self.keep, self.cerr, self.workspace,
-                           p, main)
-        emit_seeds(self.fwd, self.fwd_cost, self.keep, self.cerr, self.seeds, self.capacity, self.count,
-                   self.workspace, main)
+        match_quad_tuned(pL0, pR0, pL1, pR1, self.width, self.height, seed, self.tuning, self.fwd, self.fwd_cost,
+                         self.inv, self.inv_cost, w, p, stream)
+        consistency_filter(self.fwd, self.fwd_cost, self.inv, self.inv_cost, self.keep, self.cerr, w, p, stream)
+        emit_seeds(self.fwd, self.fwd_cost, self.keep, self.cerr, self.seeds, self.capacity, self.count, w, stream)
         return self.seeds, self.count
 
     def run_host(self, L0, R0, L1, R1, seed: int, stream=None) -> np.ndarray:
@@ -338,20 +427,23 @@ class QuadMatcher:
         h, w = self.height, self.width
         if self._host_in is None:
             self._host_in = torch.empty((4, h, w, 3), dtype=torch.uint8).pin_memory()
-            self._dev_in = torch.empty((4, h, w, 3), dtype=torch.uint8, device=self.device)
             self._host_seeds = torch.empty(20 * self.capacity, dtype=torch.uint8).pin_memory()
             self._host_count = torch.empty(1, dtype=torch.int32).pin_memory()
         for k, img in enumerate((L0, R0, L1, R1)):
             self._host_in[k].copy_(torch.as_tensor(np.ascontiguousarray(img)))
-        s = stream if stream is not None else torch.cuda.current_stream()
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
         with torch.cuda.stream(s):
-            self._dev_in.copy_(self._host_in, non_blocking=True)
-            self.run(*self._dev_in.unbind(0), seed=seed, stream=s)
+            self.buf.dev_in.copy_(self._host_in, non_blocking=True)
+            self.run(*self.buf.dev_in.unbind(0), seed=seed, stream=s)
             self._host_count.copy_(self.count, non_blocking=True)
             self._host_seeds.copy_(self.seeds, non_blocking=True)
         s.synchronize()
         n = int(self._host_count.item())
         return seeds_to_numpy(self._host_seeds[:20 * min(n, self.capacity)].numpy(), n)
+
+    @property
+    def dev_in(self):
+        return self.buf.dev_in
 
     @property
     def h2d_bytes(self) -> int:

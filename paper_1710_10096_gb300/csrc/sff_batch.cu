@@ -1,0 +1,101 @@
+// The whole stage for a batch of quads of any sizes (up to 32): features of
+// all 4n images, both fields of all n quads, the filter and the seeds, each
+// phase in shared launches (blockIdx.z selects the image / field / quad), so
+// small quads and coarse scales fill the GPU together and one CUDA graph can
+// hold the whole batch.  Every quad's outputs are identical to running the
+// four calls on it alone.
+#include <algorithm>
+
+#include "sff_internal.cuh"
+
+namespace sff {
+
+// Per-quad scratch: the phases run one after the other, so they share it.
+size_t quad_ws_bytes(int w, int h, const sff_params& p) {
+    size_t b = 4 * features_ws_bytes(w, h, p);  // the four images are smoothed in one launch
+    b = std::max(b, 2 * field_ws_bytes(w, h, p));
+    b = std::max(b, filter_ws_bytes(w, h));
+    b = std::max(b, seeds_ws_bytes(w, h));
+    return b;
+}
+
+}  // namespace sff
+
+extern "C" size_t sff_quad_workspace_bytes(int32_t width, int32_t height, const sff_params* params) {
+    if (sff::check_size(width, height) || sff::check_params(params)) return 0;
+    return sff::quad_ws_bytes(width, height, *params);
+}
+
+extern "C" int sff_run_batch(const sff_quad* quads, int32_t n, const sff_params* params, const sff_tuning* tuning,
+                             void* stream) {
+    using namespace sff;
+    if (!quads || n < 1 || n > SFF_MAX_BATCH || check_params(params)) return SFF_ERR_ARG;
+    sff_tuning t;
+    if (tuning) {
+        t = *tuning;
+    } else {
+        sff_default_tuning(&t);
+    }
+    if (!sff_tuning_supported(&t)) return SFF_ERR_ARG;
+    const sff_params& P = *params;
+    for (int k = 0; k < n; ++k) {
+        const sff_quad& q = quads[k];
+        if (check_size(q.width, q.height) || q.pitch_bytes < 3 * q.width || !q.workspace || q.capacity < 0)
+            return SFF_ERR_ARG;
+        for (int j = 0; j < 4; ++j)
+            if (!q.rgb[j] || !q.pyramid[j] || ((uintptr_t)q.pyramid[j] & 15)) return SFF_ERR_ARG;
+        if (!q.fwd || !q.inv || !q.fwd_cost || !q.inv_cost || !q.keep || !q.cerr || !q.count ||
+            (q.capacity > 0 && !q.seeds))
+            return SFF_ERR_ARG;
+        if (((uintptr_t)q.fwd & 7) || ((uintptr_t)q.inv & 7) || ((uintptr_t)q.fwd_cost & 3) ||
+            ((uintptr_t)q.inv_cost & 3) || ((uintptr_t)q.workspace & 255) || ((uintptr_t)q.seeds & 3))
+            return SFF_ERR_ARG;
+        if (q.workspace_bytes < quad_ws_bytes(q.width, q.height, P)) return SFF_ERR_WORKSPACE;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+
+    // features of all images
+    ImageJob img[kMaxImages];
+    for (int k = 0; k < n; ++k) {
+        const sff_quad& q = quads[k];
+        const size_t fw = features_ws_bytes(q.width, q.height, P);
+        for (int j = 0; j < 4; ++j)
+            img[4 * k + j] = ImageJob{q.rgb[j], q.pitch_bytes, q.width, q.height,
+                                      reinterpret_cast<uint32_t*>((char*)q.workspace + j * fw), q.pyramid[j]};
+    }
+    int status = run_features(img, 4 * n, P, st);
+    if (status) return status;
+
+    // both fields of every quad (pyramids in the order L0, R0, L1, R1)
+    FieldSpec fs[kMaxBatchFields];
+    for (int k = 0; k < n; ++k) {
+        const sff_quad& q = quads[k];
+        char* ws = reinterpret_cast<char*>(q.workspace);
+        const size_t half = field_ws_bytes(q.width, q.height, P);
+        fs[2 * k] = FieldSpec{q.pyramid[0], q.pyramid[2], q.pyramid[1], q.pyramid[3], q.fwd, q.fwd_cost, 0,
+                              q.width,      q.height,     q.seed,       ws};
+        fs[2 * k + 1] = FieldSpec{q.pyramid[3], q.pyramid[1], q.pyramid[2], q.pyramid[0], q.inv, q.inv_cost, 1,
+                                  q.width,      q.height,     q.seed,       ws + half};
+    }
+    status = run_fields(fs, 2 * n, P, t, st);
+    if (status) return status;
+
+    // consistency + region filter, then seeds
+    FilterJob fj[kMaxQuads];
+    SeedJob sj[kMaxQuads];
+    for (int k = 0; k < n; ++k) {
+        const sff_quad& q = quads[k];
+        fj[k] = FilterJob{reinterpret_cast<const uint2*>(q.fwd), q.fwd_cost, reinterpret_cast<const uint2*>(q.inv),
+                          q.inv_cost, q.width, q.height, q.keep, q.cerr, nullptr, nullptr, nullptr};
+        filter_carve(q.workspace, q.width, q.height, &fj[k].parent, &fj[k].size, &fj[k].joinable);
+    }
+    status = run_filter(fj, n, P, st);
+    if (status) return status;
+    for (int k = 0; k < n; ++k) {
+        const sff_quad& q = quads[k];
+        sj[k] = SeedJob{reinterpret_cast<const uint2*>(q.fwd), q.fwd_cost, q.keep, q.cerr, q.width, q.height,
+                        nullptr, nullptr, q.seeds, q.capacity, q.count};
+        seeds_carve(q.workspace, q.width, q.height, &sj[k].best, &sj[k].chunk);
+    }
+    return run_seeds(sj, n, st);
+}

@@ -10,6 +10,8 @@
 //             so packed adds and subtracts are exact).  The 16 kept
 //             coefficients are read out through the sequency->natural index
 //             map, quantised and written as one 48-byte record plus its norm.
+#include <mutex>
+
 #include "sff_internal.cuh"
 
 namespace sff {
@@ -29,11 +31,14 @@ static_assert(seq_to_nat(1) == 4 && seq_to_nat(2) == 6 && seq_to_nat(5) == 7 && 
 static_assert(order_ky(0) == 0 && order_kx(0) == 1 && order_ky(4) == 2 && order_kx(4) == 0, "order");
 static_assert(order_ky(13) == 4 && order_kx(13) == 0 && order_ky(15) == 1 && order_kx(15) == 4, "order");
 
-__global__ void k_smooth(const uint8_t* __restrict__ rgb, int pitch, int w, int h, int S,
-                         uint32_t* __restrict__ out) {
+__global__ void k_smooth(const __grid_constant__ ImageJobs J, int S) {
+    const ImageJob& job = J.im[blockIdx.z];
+    const uint8_t* __restrict__ rgb = job.rgb;
+    const int pitch = job.pitch, w = job.w, h = job.h;
+    uint32_t* __restrict__ out = job.sm;
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y;
-    if (x >= w) return;
+    if (x >= w || y >= h) return;
     {
         const uint8_t* p = rgb + (size_t)y * pitch + 3 * x;
         out[(size_t)y * w + x] = (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16);
@@ -70,11 +75,16 @@ __device__ __forceinline__ void fwht8(int (&a)[8]) {
 
 __device__ __forceinline__ int lo16(int x) { return (x << 16) >> 16; }
 
-__global__ void k_features(const uint32_t* __restrict__ sm, int w, int h, int s, int qshift,
-                           uint8_t* __restrict__ out, int* __restrict__ norm_out) {
+__global__ void k_features(const __grid_constant__ ImageJobs J, int s, int S, int qshift) {
+    const ImageJob& job = J.im[blockIdx.z];
+    const int w = job.w, h = job.h;
+    const size_t np = (size_t)w * h;
+    const uint32_t* __restrict__ sm = job.sm + s * np;
+    uint8_t* __restrict__ out = job.pyr + s * np * kFeat;
+    int* __restrict__ norm_out = reinterpret_cast<int*>(job.pyr + (size_t)S * np * kFeat) + s * np;
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     int y = blockIdx.y;
-    if (x >= w) return;
+    if (x >= w || y >= h) return;
     const int n = 1 << s;
     int xs[8];
 #pragma unroll
@@ -153,6 +163,23 @@ size_t features_ws_bytes(int w, int h, const sff_params& p) {
     return align256((size_t)p.num_scales * w * h * sizeof(uint32_t));
 }
 
+int run_features(const ImageJob* jobs, int n, const sff_params& P, cudaStream_t st) {
+    if (n < 1 || n > kMaxImages) return SFF_ERR_ARG;
+    static ImageJobs J;  // host staging of the kernel parameter (copied at each launch)
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    int mw = 0, mh = 0;
+    for (int k = 0; k < n; ++k) {
+        J.im[k] = jobs[k];
+        mw = mw > jobs[k].w ? mw : jobs[k].w;
+        mh = mh > jobs[k].h ? mh : jobs[k].h;
+    }
+    dim3 blk(128), grd((mw + 127) / 128, mh, n);
+    SFF_LAUNCH(k_smooth, grd, blk, 0, st, J, P.num_scales);
+    for (int s = 0; s < P.num_scales; ++s) SFF_LAUNCH(k_features, grd, blk, 0, st, J, s, P.num_scales, P.quant_shift);
+    return launch_status();
+}
+
 }  // namespace sff
 
 extern "C" int sff_features(const uint8_t* rgb_dev, int32_t width, int32_t height, int32_t pitch_bytes,
@@ -163,14 +190,6 @@ extern "C" int sff_features(const uint8_t* rgb_dev, int32_t width, int32_t heigh
     if (!rgb_dev || !pyramid_dev || !workspace || pitch_bytes < 3 * width) return SFF_ERR_ARG;
     if (((uintptr_t)pyramid_dev & 15) || ((uintptr_t)workspace & 255)) return SFF_ERR_ARG;
     if (workspace_bytes < features_ws_bytes(width, height, *params)) return SFF_ERR_WORKSPACE;
-    cudaStream_t st = (cudaStream_t)stream;
-    uint32_t* sm = (uint32_t*)workspace;
-    dim3 blk(128), grd((width + 127) / 128, height);
-    SFF_LAUNCH(k_smooth, grd, blk, 0, st, rgb_dev, pitch_bytes, width, height, params->num_scales, sm);
-    const size_t np = (size_t)width * height;
-    int* norms = reinterpret_cast<int*>(pyramid_dev + (size_t)params->num_scales * np * kFeat);
-    for (int s = 0; s < params->num_scales; ++s)
-        SFF_LAUNCH(k_features, grd, blk, 0, st, sm + s * np, width, height, s, params->quant_shift,
-                   pyramid_dev + s * np * kFeat, norms + s * np);
-    return launch_status();
+    ImageJob job{rgb_dev, pitch_bytes, width, height, (uint32_t*)workspace, pyramid_dev};
+    return run_features(&job, 1, *params, (cudaStream_t)stream);
 }

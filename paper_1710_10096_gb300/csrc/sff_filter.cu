@@ -14,25 +14,31 @@
 //                accumulated on the root (k_cc_stats), and small joinable
 //                components are removed (k_cc_remove).
 // Scratch (workspace): parent[H*W], size[H*W], joinable[H*W] int32.
+#include <mutex>
+
 #include "sff_internal.cuh"
 
 namespace sff {
 namespace {
 
-__global__ void k_consistency(const uint2* __restrict__ fwd, const int* __restrict__ fcost,
-                              const uint2* __restrict__ inv, const int* __restrict__ icost, int w, int h, int tau_c,
-                              uint8_t* __restrict__ keep, uint8_t* __restrict__ cerr) {
+struct FilterJobs {
+    FilterJob q[kMaxQuads];
+};
+
+__global__ void k_consistency(const __grid_constant__ FilterJobs J, int tau_c) {
+    const FilterJob& Q = J.q[blockIdx.z];
+    const int w = Q.w, h = Q.h;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    if (x >= w) return;
+    if (x >= w || y >= h) return;
     const size_t i = (size_t)y * w + x;
     uint8_t k = 0, e = 255;
-    if (fcost[i] != kEmpty) {
-        const Vec4 a = unpack_vec(fwd[i]);
+    if (Q.fcost[i] != kEmpty) {
+        const Vec4 a = unpack_vec(Q.fwd[i]);
         const int qx = x + a.u - a.d1, qy = y + a.v;
         if (qx >= 0 && qx < w && qy >= 0 && qy < h) {
             const size_t j = (size_t)qy * w + qx;
-            if (icost[j] != kEmpty) {
-                const Vec4 b = unpack_vec(inv[j]);
+            if (Q.icost[j] != kEmpty) {
+                const Vec4 b = unpack_vec(Q.inv[j]);
                 const int d0 = abs(b.u + a.u - a.d1 + a.d0), d1 = abs(b.v + a.v);
                 const int d2 = abs(b.d0 - a.d1), d3 = abs(b.d1 - a.d0);
                 const int mx = max(max(d0, d1), max(d2, d3)), sum = d0 + d1 + d2 + d3;
@@ -41,8 +47,8 @@ __global__ void k_consistency(const uint2* __restrict__ fwd, const int* __restri
             }
         }
     }
-    keep[i] = k;
-    cerr[i] = e;
+    Q.keep[i] = k;
+    Q.cerr[i] = e;
 }
 
 __device__ __forceinline__ bool close_vec(uint2 a, uint2 b, int tau) {
@@ -108,24 +114,25 @@ __device__ void unite_local(int* lp, int a, int b) {
 // order, so a local root is the minimum raster index of its local component;
 // every kept pixel's parent becomes its local root.  Also clears size and
 // joinable for the tile's pixels.
-__global__ void __launch_bounds__(256) k_cc_local(const uint2* __restrict__ fwd, const uint8_t* __restrict__ keep,
-                                                  int w, int h, int tau_r, int* __restrict__ parent,
-                                                  int* __restrict__ size, int* __restrict__ joinable) {
+__global__ void __launch_bounds__(256) k_cc_local(const __grid_constant__ FilterJobs J, int tau_r) {
     __shared__ int lp[kTile * kTile];
     __shared__ uint2 lf[kTile * kTile];
     __shared__ uint8_t lk[kTile * kTile];
+    const FilterJob& Q = J.q[blockIdx.z];
+    const int w = Q.w, h = Q.h;
     const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
+    if (x0 >= w || y0 >= h) return;  // whole CTA beyond this quad
     for (int k = threadIdx.x; k < kTile * kTile; k += blockDim.x) {
         const int x = x0 + (k % kTile), y = y0 + (k / kTile);
         const bool inside = x < w && y < h;
         const size_t i = (size_t)y * w + x;
-        const bool kk = inside && keep[i];
+        const bool kk = inside && Q.keep[i];
         lk[k] = kk;
-        lf[k] = kk ? fwd[i] : make_uint2(0u, 0u);
+        lf[k] = kk ? Q.fwd[i] : make_uint2(0u, 0u);
         lp[k] = kk ? k : -1;
         if (inside) {
-            size[i] = 0;
-            joinable[i] = 0;
+            Q.size[i] = 0;
+            Q.joinable[i] = 0;
         }
     }
     __syncthreads();
@@ -139,40 +146,44 @@ __global__ void __launch_bounds__(256) k_cc_local(const uint2* __restrict__ fwd,
     for (int k = threadIdx.x; k < kTile * kTile; k += blockDim.x) {
         if (!lk[k]) continue;
         const int r = find_local(lp, k);
-        parent[(size_t)(y0 + k / kTile) * w + x0 + k % kTile] = (y0 + r / kTile) * w + x0 + r % kTile;
+        Q.parent[(size_t)(y0 + k / kTile) * w + x0 + k % kTile] = (y0 + r / kTile) * w + x0 + r % kTile;
     }
 }
 
 // Unions across tile borders only (right column and bottom row of each tile).
-__global__ void k_cc_border(const uint2* __restrict__ fwd, const uint8_t* __restrict__ keep, int w, int h,
-                            int tau_r, int* parent) {
+__global__ void k_cc_border(const __grid_constant__ FilterJobs J, int tau_r) {
+    const FilterJob& Q = J.q[blockIdx.z];
+    const int w = Q.w, h = Q.h;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    if (x >= w) return;
+    if (x >= w || y >= h) return;
     const bool right = (x % kTile) == kTile - 1 && x + 1 < w;
     const bool down = (y % kTile) == kTile - 1 && y + 1 < h;
     if (!right && !down) return;
     const int i = y * w + x;
-    if (!keep[i]) return;
-    const uint2 a = fwd[i];
-    if (right && keep[i + 1] && close_vec(a, fwd[i + 1], tau_r)) unite(parent, i, i + 1);
-    if (down && keep[i + w] && close_vec(a, fwd[i + w], tau_r)) unite(parent, i, i + w);
+    if (!Q.keep[i]) return;
+    const uint2 a = Q.fwd[i];
+    if (right && Q.keep[i + 1] && close_vec(a, Q.fwd[i + 1], tau_r)) unite(Q.parent, i, i + 1);
+    if (down && Q.keep[i + w] && close_vec(a, Q.fwd[i + w], tau_r)) unite(Q.parent, i, i + w);
 }
 
 // Root of every kept pixel (written back to parent), component sizes with
 // one atomic per distinct root per warp, and the "a rejected neighbour
 // could join" flag.
-__global__ void k_cc_stats(const uint2* __restrict__ fwd, const int* __restrict__ fcost,
-                           const uint8_t* __restrict__ keep, int w, int h, int tau_r, int* parent, int* size,
-                           int* joinable) {
+__global__ void k_cc_stats(const __grid_constant__ FilterJobs J, int tau_r) {
+    const FilterJob& Q = J.q[blockIdx.z];
+    const int w = Q.w, h = Q.h;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     const int i = y * w + x;
-    const bool kept = x < w && keep[i];
+    const bool kept = x < w && y < h && Q.keep[i];
     int root = -1;
     bool join = false;
     if (kept) {
-        root = find_root(parent, i);
-        parent[i] = root;
-        const uint2 a = fwd[i];
+        root = find_root(Q.parent, i);
+        Q.parent[i] = root;
+        const uint2 a = Q.fwd[i];
+        const uint8_t* keep = Q.keep;
+        const int* fcost = Q.fcost;
+        const uint2* fwd = Q.fwd;
         if (x + 1 < w && !keep[i + 1] && fcost[i + 1] != kEmpty && close_vec(a, fwd[i + 1], tau_r)) join = true;
         if (x > 0 && !keep[i - 1] && fcost[i - 1] != kEmpty && close_vec(a, fwd[i - 1], tau_r)) join = true;
         if (y + 1 < h && !keep[i + w] && fcost[i + w] != kEmpty && close_vec(a, fwd[i + w], tau_r)) join = true;
@@ -180,21 +191,51 @@ __global__ void k_cc_stats(const uint2* __restrict__ fwd, const int* __restrict_
     }
     const unsigned peers = __match_any_sync(0xffffffffu, root);
     const int lane = threadIdx.x & 31;
-    if (kept && lane == __ffs(peers) - 1) atomicAdd(size + root, __popc(peers));
-    if (join) atomicOr(joinable + root, 1);
+    if (kept && lane == __ffs(peers) - 1) atomicAdd(Q.size + root, __popc(peers));
+    if (join) atomicOr(Q.joinable + root, 1);
 }
 
-__global__ void k_cc_remove(uint8_t* __restrict__ keep, int np, const int* __restrict__ parent,
-                            const int* __restrict__ size, const int* __restrict__ joinable, int region_min) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= np || !keep[i]) return;
-    const int root = parent[i];
-    if (joinable[root] && size[root] < region_min) keep[i] = 0;
+__global__ void k_cc_remove(const __grid_constant__ FilterJobs J, int region_min) {
+    const FilterJob& Q = J.q[blockIdx.z];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= Q.w || y >= Q.h) return;
+    const int i = y * Q.w + x;
+    if (!Q.keep[i]) return;
+    const int root = Q.parent[i];
+    if (Q.joinable[root] && Q.size[root] < region_min) Q.keep[i] = 0;
 }
 
 }  // namespace
 
 size_t filter_ws_bytes(int w, int h) { return 3 * align256((size_t)w * h * sizeof(int)); }
+
+void filter_carve(void* workspace, int w, int h, int** parent, int** size, int** joinable) {
+    const size_t slab = align256((size_t)w * h * sizeof(int));
+    *parent = reinterpret_cast<int*>(workspace);
+    *size = reinterpret_cast<int*>((char*)workspace + slab);
+    *joinable = reinterpret_cast<int*>((char*)workspace + 2 * slab);
+}
+
+int run_filter(const FilterJob* jobs, int n, const sff_params& P, cudaStream_t st) {
+    if (n < 1 || n > kMaxQuads) return SFF_ERR_ARG;
+    static FilterJobs J;  // host staging of the kernel parameter (copied at each launch)
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    int mw = 0, mh = 0;
+    for (int k = 0; k < n; ++k) {
+        J.q[k] = jobs[k];
+        mw = mw > jobs[k].w ? mw : jobs[k].w;
+        mh = mh > jobs[k].h ? mh : jobs[k].h;
+    }
+    dim3 b2(128), g2((mw + 127) / 128, mh, n);
+    dim3 gt((mw + kTile - 1) / kTile, (mh + kTile - 1) / kTile, n);
+    SFF_LAUNCH(k_consistency, g2, b2, 0, st, J, P.tau_c);
+    SFF_LAUNCH(k_cc_local, gt, 256, 0, st, J, P.tau_r);
+    SFF_LAUNCH(k_cc_border, g2, b2, 0, st, J, P.tau_r);
+    SFF_LAUNCH(k_cc_stats, g2, b2, 0, st, J, P.tau_r);
+    SFF_LAUNCH(k_cc_remove, g2, b2, 0, st, J, P.region_min);
+    return launch_status();
+}
 
 }  // namespace sff
 
@@ -210,23 +251,8 @@ extern "C" int sff_consistency_filter(const int16_t* fwd_dev, const int32_t* fwd
         ((uintptr_t)inv_cost_dev & 3) || ((uintptr_t)workspace & 255))
         return SFF_ERR_ARG;
     if (workspace_bytes < filter_ws_bytes(width, height)) return SFF_ERR_WORKSPACE;
-    cudaStream_t st = (cudaStream_t)stream;
-    const uint2* fwd = reinterpret_cast<const uint2*>(fwd_dev);
-    const uint2* inv = reinterpret_cast<const uint2*>(inv_dev);
-    const int np = width * height;
-    const size_t slab = align256((size_t)np * sizeof(int));
-    int* parent = reinterpret_cast<int*>(workspace);
-    int* size = reinterpret_cast<int*>((char*)workspace + slab);
-    int* joinable = reinterpret_cast<int*>((char*)workspace + 2 * slab);
-    dim3 b2(128), g2((width + 127) / 128, height);
-    const int g1 = (np + 255) / 256;
-    SFF_LAUNCH(k_consistency, g2, b2, 0, st, fwd, fwd_cost_dev, inv, inv_cost_dev, width, height, params->tau_c, keep_dev,
-                                     cerr_dev);
-    dim3 gt((width + kTile - 1) / kTile, (height + kTile - 1) / kTile);
-    SFF_LAUNCH(k_cc_local, gt, 256, 0, st, fwd, keep_dev, width, height, params->tau_r, parent, size, joinable);
-    SFF_LAUNCH(k_cc_border, g2, b2, 0, st, fwd, keep_dev, width, height, params->tau_r, parent);
-    SFF_LAUNCH(k_cc_stats, g2, b2, 0, st, fwd, fwd_cost_dev, keep_dev, width, height, params->tau_r, parent, size,
-                                  joinable);
-    SFF_LAUNCH(k_cc_remove, g1, 256, 0, st, keep_dev, np, parent, size, joinable, params->region_min);
-    return launch_status();
+    FilterJob job{reinterpret_cast<const uint2*>(fwd_dev), fwd_cost_dev, reinterpret_cast<const uint2*>(inv_dev),
+                  inv_cost_dev, width, height, keep_dev, cerr_dev, nullptr, nullptr, nullptr};
+    filter_carve(workspace, width, height, &job.parent, &job.size, &job.joinable);
+    return run_filter(&job, 1, *params, (cudaStream_t)stream);
 }

@@ -136,6 +136,67 @@ __device__ __forceinline__ int rs_offset(uint32_t r, int n) {
 // ---------------------------------------------------------------------------
 // host-side helpers
 
+// One field to match (Sec. 3.1): its four views' pyramids, its output and
+// its scratch (field_ws_bytes).  Fields of any sizes and seeds can share a
+// run_fields call.
+struct FieldSpec {
+    const uint8_t *ref, *tmp, *ste, *crs;
+    int16_t* field;
+    int32_t* cost;
+    int mirror;
+    int width, height;
+    uint64_t seed;
+    void* workspace;
+};
+constexpr int kMaxBatchFields = 64;
+
+// One image of a features launch: input, smoothed scale space (workspace,
+// features_ws_bytes) and pyramid.  Up to kMaxImages share a launch.
+struct ImageJob {
+    const uint8_t* rgb;
+    int pitch, w, h;
+    uint32_t* sm;
+    uint8_t* pyr;
+};
+constexpr int kMaxImages = 128;
+struct ImageJobs {
+    ImageJob im[kMaxImages];
+};
+int run_features(const ImageJob* jobs, int n, const sff_params& P, cudaStream_t st);
+
+// One quad of a consistency-filter / seeds launch (up to kMaxQuads).
+struct FilterJob {
+    const uint2* fwd;
+    const int* fcost;
+    const uint2* inv;
+    const int* icost;
+    int w, h;
+    uint8_t* keep;
+    uint8_t* cerr;
+    int* parent;
+    int* size;
+    int* joinable;
+};
+struct SeedJob {
+    const uint2* fwd;
+    const int* fcost;
+    const uint8_t* keep;
+    const uint8_t* cerr;
+    int w, h;
+    int* best;
+    int* chunk;
+    sff_seed* out;
+    int capacity;
+    int* count;
+};
+constexpr int kMaxQuads = 32;
+int run_filter(const FilterJob* jobs, int n, const sff_params& P, cudaStream_t st);
+int run_seeds(const SeedJob* jobs, int n, cudaStream_t st);
+void filter_carve(void* workspace, int w, int h, int** parent, int** size, int** joinable);
+void seeds_carve(void* workspace, int w, int h, int** best, int** chunk);
+size_t field_ws_bytes(int w, int h, const sff_params& p);
+int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tuning& T, cudaStream_t st);
+
 // Optional per-kernel event timing (sff_profile_enable).  SFF_LAUNCH wraps
 // every kernel launch of the library.
 bool profiling();

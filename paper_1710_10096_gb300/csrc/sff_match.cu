@@ -33,17 +33,24 @@
 //                 "half-step 0, half-step 1, random search", because a
 //                 half-step only reads the other colour and the search only
 //                 reads the pixel itself.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
 #include "sff_internal.cuh"
 
 namespace sff {
 namespace {
 
+std::mutex g_fields_mu;  // guards the host staging of the Fields parameter
+
 constexpr int kKnnThreads = 256;
 constexpr int kKnnWarps = kKnnThreads / 32;
 constexpr int kKnnTile = 256;  // candidates per shared-memory tile (12 KB of records)
 
-// One field: its views at the current scale, its state and, for the
-// double-buffered iteration kernel, the buffer it writes.
+// One field: its views and grid at the current scale, its state and, for
+// the double-buffered iteration kernel, the buffer it writes; plus its
+// coarsest-scale K-NN scratch.
 struct Field {
     Views V;
     uint2* field;  // state read (and written in place by the other kernels)
@@ -51,13 +58,22 @@ struct Field {
     uint2* field_out;  // state written by k_iteration
     int* cost_out;
     int mirror;
+    int gw, gh;  // grid of the current scale
+    int gq, gq_pad;  // coarsest grid points and padded row count of the compact arrays
+    int2* best8;  // [gq][8] temporal top-8 (distance, grid index)
+    uint8_t* cf;  // [2 roles][gq_pad] 48-byte records: reference, temporal
+    int* cn;  // [2 roles][gq_pad] norms
+    uint2 key;  // Philox key: the seed of the field's quad
 };
 
+// Up to kMaxFields fields of any sizes share every launch (blockIdx.z picks
+// the field); passed by value as a __grid_constant__ kernel parameter.
+constexpr int kMaxFields = kMaxBatchFields;
 struct Fields {
-    Field f[2];
+    Field f[kMaxFields];
 };
 
-__device__ __forceinline__ const Field& pick(const Fields& F) { return blockIdx.z ? F.f[1] : F.f[0]; }
+__device__ __forceinline__ const Field& pick(const Fields& F) { return F.f[blockIdx.z]; }
 
 __device__ __forceinline__ bool less_di(int d, int i, int d2, int i2) { return d < d2 || (d == d2 && i < i2); }
 
@@ -88,20 +104,20 @@ __device__ __forceinline__ int dot12(const int (&a)[12], const int4& p0, const i
 // (role 1) images of each field into contiguous arrays, so that the K-NN
 // search streams them with bulk copies.  Layout: [field][role][gq + pad]
 // records of 48 bytes and int32 norms.
-__global__ void k_gather_grid(Fields F, int n, int gw, int gq, int gq_pad, uint8_t* __restrict__ cf,
-                              int* __restrict__ cn) {
+__global__ void k_gather_grid(const __grid_constant__ Fields F, int n) {
     const Field& A = pick(F);
     const int role = blockIdx.y;
     const Plane& P = role ? A.V.tmp : A.V.ref;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int c = t >> 2, part = t & 3;
-    if (c >= gq) return;
-    const size_t i = pix(A.V.w, (c % gw) * n, (c / gw) * n);
-    const size_t slot = ((size_t)blockIdx.z * 2 + role) * gq_pad + c;
+    if (c >= A.gq) return;
+    const size_t i = pix(A.V.w, (c % A.gw) * n, (c / A.gw) * n);
+    const size_t slot = (size_t)role * A.gq_pad + c;
     if (part < 3)
-        reinterpret_cast<int4*>(cf + slot * kFeat)[part] = __ldg(reinterpret_cast<const int4*>(P.f + i * kFeat) + part);
+        reinterpret_cast<int4*>(A.cf + slot * kFeat)[part] =
+            __ldg(reinterpret_cast<const int4*>(P.f + i * kFeat) + part);
     else
-        cn[slot] = __ldg(P.nrm + i);
+        A.cn[slot] = __ldg(P.nrm + i);
 }
 
 // TMA (bulk-copy) helpers: 1-D global -> shared copies completing on an
@@ -153,19 +169,21 @@ __device__ unsigned int g_wait_timeouts;  // bounded waits that gave up (read by
 // ballot against the current 8th-best (distance, index) keeps the rare
 // candidates that enter the list, and each of them is inserted into the
 // sorted top-8 held by lanes 0-7 with warp-uniform shuffles.
-__global__ void __launch_bounds__(kKnnThreads) k_knn(int gq, int gq_pad, const uint8_t* __restrict__ cf,
-                                                      const int* __restrict__ cn, int2* __restrict__ best8) {
+__global__ void __launch_bounds__(kKnnThreads) k_knn(const __grid_constant__ Fields F) {
     __shared__ __align__(128) int4 tile[2][kKnnTile][3];
     __shared__ __align__(16) int tnorm[2][kKnnTile];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ int s_fail;
+    const Field& A = pick(F);
+    const int gq = A.gq;
+    if ((int)blockIdx.x * kKnnWarps >= gq) return;  // CTA beyond this field's queries
     const int lane = threadIdx.x & 31;
     const int qi = blockIdx.x * kKnnWarps + (threadIdx.x >> 5);
     const bool active = qi < gq;  // warp-uniform
-    const uint8_t* qf = cf + (size_t)(blockIdx.z * 2 + 0) * gq_pad * kFeat;
-    const uint8_t* tf = cf + (size_t)(blockIdx.z * 2 + 1) * gq_pad * kFeat;
-    const int* qn = cn + (size_t)(blockIdx.z * 2 + 0) * gq_pad;
-    const int* tn = cn + (size_t)(blockIdx.z * 2 + 1) * gq_pad;
+    const uint8_t* qf = A.cf;
+    const uint8_t* tf = A.cf + (size_t)A.gq_pad * kFeat;
+    const int* qn = A.cn;
+    const int* tn = A.cn + A.gq_pad;
     RefFeat r;
     if (active) {
         const int4* p = reinterpret_cast<const int4*>(qf + (size_t)qi * kFeat);
@@ -242,7 +260,7 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(int gq, int gq_pad, const u
         }
         __syncthreads();
     }
-    if (active && lane < 8) best8[((size_t)blockIdx.z * gq + qi) * 8 + lane] = make_int2(ld, li);
+    if (active && lane < 8) A.best8[(size_t)qi * 8 + lane] = make_int2(ld, li);
 }
 
 // Nearest grid point of row y by (distance, x), constrained by sigma, found by
@@ -271,18 +289,19 @@ __device__ __forceinline__ void warp_row_nearest(const RefFeat& r, const Plane& 
     best_x = bx;
 }
 
-__global__ void k_init_select(Fields F, int n, int gw, int gq, int knn, const int2* __restrict__ best8) {
+__global__ void k_init_select(const __grid_constant__ Fields F, int n, int knn) {
     const Field& A = pick(F);
     const Views& V = A.V;
+    const int gw = A.gw;
     const int qi = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
-    if (qi >= gq) return;  // warp-uniform
+    if (qi >= A.gq) return;  // warp-uniform
     const int px = (qi % gw) * n, py = (qi / gw) * n;
     RefFeat r;
     load_ref(V.ref, pix(V.w, px, py), r);
     // the query's temporal top-8 (every lane the same, reads broadcast)
     int bd[8], bi[8];
-    const int2* src = best8 + ((size_t)blockIdx.z * gq + qi) * 8;
+    const int2* src = A.best8 + (size_t)qi * 8;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         const int2 e = src[k];
@@ -315,11 +334,11 @@ __global__ void k_init_select(Fields F, int n, int gw, int gq, int knn, const in
     }
 }
 
-__global__ void k_inherit(Fields F, int n, int gw, int gh) {
+__global__ void k_inherit(const __grid_constant__ Fields F, int n) {
     const Field& A = pick(F);
     const Views& V = A.V;
     const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y;
-    if (gx >= gw || gy >= gh) return;
+    if (gx >= A.gw || gy >= A.gh) return;
     const int x = gx * n, y = gy * n;
     const size_t i = pix(V.w, x, y);
     const bool coarse = ((gx | gy) & 1) == 0;
@@ -336,8 +355,7 @@ __global__ void k_inherit(Fields F, int n, int gw, int gh) {
 }
 
 struct HalfStep {
-    int n, s, gw, colour, dx, dy, prop, rs_before, rs_after;
-    uint2 key;
+    int n, s, colour, dx, dy, prop, rs_before, rs_after;
 };
 
 // Pixels are processed by groups of L lanes (L = 1, 2 or 4, a tuning knob
@@ -485,7 +503,7 @@ constexpr int kHalfPixels = kHalfThreads / kHalfLanes;
 
 // One colour of the checkerboard over the whole grid, in place.  Used for
 // the random search of colour 0 after the last iteration of a scale.
-__global__ void __launch_bounds__(kHalfThreads) k_half_step(Fields F, HalfStep H) {
+__global__ void __launch_bounds__(kHalfThreads) k_half_step(const __grid_constant__ Fields F, HalfStep H) {
     constexpr int L = kHalfLanes;
     const Field& A = pick(F);
     const Views& V = A.V;
@@ -493,7 +511,7 @@ __global__ void __launch_bounds__(kHalfThreads) k_half_step(Fields F, HalfStep H
     const unsigned gmask = group_mask<L>();
     const int gy = blockIdx.y;
     const int gx = 2 * (blockIdx.x * kHalfPixels + (int)(threadIdx.x / L)) + ((H.colour + gy) & 1);
-    if (gx >= H.gw) return;  // the whole group leaves together
+    if (gx >= A.gw || gy >= A.gh) return;  // the whole group leaves together
     const int x = gx * H.n, y = gy * H.n;
     const size_t i = pix(V.w, x, y);
     const int ax = x - H.dx * H.n, by = y - H.dy * H.n;
@@ -508,7 +526,7 @@ __global__ void __launch_bounds__(kHalfThreads) k_half_step(Fields F, HalfStep H
     Slice<L> a;
     load_slice<L>(V.ref, i, q, a);
     Vec4 cur = unpack_vec(wc);
-    if (update_pixel<L>(V, a, q, gmask, H.n, H.s, H.key, A.mirror, x, y, (uint32_t)i, H.rs_before, H.rs_after,
+    if (update_pixel<L>(V, a, q, gmask, H.n, H.s, A.key, A.mirror, x, y, (uint32_t)i, H.rs_before, H.rs_after,
                         unpack_vec(wa), ca, unpack_vec(wb), cb, cur, c) &&
         q == 0) {
         A.field[i] = pack_vec(cur);
@@ -537,12 +555,11 @@ __host__ __device__ constexpr int iter_threads() {
 }
 
 struct IterStep {
-    int n, s, gw, gh, dx, dy, it;
-    uint2 key;
+    int n, s, dx, dy, it;
 };
 
 template <int L, int TX, int TY>
-__global__ void __launch_bounds__(iter_threads<L, TX, TY>()) k_iteration(Fields F, IterStep H) {
+__global__ void __launch_bounds__(iter_threads<L, TX, TY>()) k_iteration(const __grid_constant__ Fields F, IterStep H) {
     constexpr int kRegX = TX + 1, kRegY = TY + 1;
     constexpr int kGroups = iter_threads<L, TX, TY>() / L;
     __shared__ uint2 s_vec[kRegX * kRegY];
@@ -553,6 +570,8 @@ __global__ void __launch_bounds__(iter_threads<L, TX, TY>()) k_iteration(Fields 
     const unsigned gmask = group_mask<L>();
     const int grp = threadIdx.x / L;
     const int tx0 = blockIdx.x * TX, ty0 = blockIdx.y * TY;
+    const int gw = A.gw, gh = A.gh;
+    if (tx0 >= gw || ty0 >= gh) return;  // tile beyond this field's grid (whole CTA)
     const int rx0 = tx0 - (H.dx > 0 ? 1 : 0), ry0 = ty0 - (H.dy > 0 ? 1 : 0);  // region origin
     const int n = H.n;
 
@@ -562,7 +581,7 @@ __global__ void __launch_bounds__(iter_threads<L, TX, TY>()) k_iteration(Fields 
         const int ry = k / kHalfRow;
         const int rx = 2 * (k % kHalfRow) + ((rx0 + ry0 + ry) & 1);
         const int gx = rx0 + rx, gy = ry0 + ry;
-        if (rx >= kRegX || gx < 0 || gx >= H.gw || gy < 0 || gy >= H.gh) continue;
+        if (rx >= kRegX || gx < 0 || gx >= gw || gy < 0 || gy >= gh) continue;
         const int x = gx * n, y = gy * n;
         const size_t i = pix(V.w, x, y);
         const int ax = x - H.dx * n, by = y - H.dy * n;
@@ -575,7 +594,7 @@ __global__ void __launch_bounds__(iter_threads<L, TX, TY>()) k_iteration(Fields 
         Slice<L> a;
         load_slice<L>(V.ref, i, q, a);
         Vec4 cur = unpack_vec(wc);
-        update_pixel<L>(V, a, q, gmask, n, H.s, H.key, A.mirror, x, y, (uint32_t)i, H.it - 1, -1, unpack_vec(wa), ca,
+        update_pixel<L>(V, a, q, gmask, n, H.s, A.key, A.mirror, x, y, (uint32_t)i, H.it - 1, -1, unpack_vec(wa), ca,
                         unpack_vec(wb), cb, cur, c);
         if (q == 0) {
             const uint2 wv = pack_vec(cur);
@@ -595,7 +614,7 @@ __global__ void __launch_bounds__(iter_threads<L, TX, TY>()) k_iteration(Fields 
         const int ly = k / kTileHalfRow;
         const int gy = ty0 + ly;
         const int gx = tx0 + 2 * (k % kTileHalfRow) + ((tx0 + gy + 1) & 1);
-        if (gx >= H.gw || gy >= H.gh) continue;
+        if (gx >= gw || gy >= gh) continue;
         const int x = gx * n, y = gy * n;
         const size_t i = pix(V.w, x, y);
         int c = A.cost[i];
@@ -605,17 +624,17 @@ __global__ void __launch_bounds__(iter_threads<L, TX, TY>()) k_iteration(Fields 
         const int agx = gx - H.dx, bgy = gy - H.dy;  // predecessors (colour 0, in the region)
         int ca = kEmpty, cb = kEmpty;
         uint2 wa = make_uint2(0u, 0u), wb = make_uint2(0u, 0u);
-        if (agx >= 0 && agx < H.gw) {
+        if (agx >= 0 && agx < gw) {
             const int r = (gy - ry0) * kRegX + (agx - rx0);
             ca = s_cost[r];
             wa = s_vec[r];
         }
-        if (bgy >= 0 && bgy < H.gh) {
+        if (bgy >= 0 && bgy < gh) {
             const int r = (bgy - ry0) * kRegX + (gx - rx0);
             cb = s_cost[r];
             wb = s_vec[r];
         }
-        update_pixel<L>(V, a, q, gmask, n, H.s, H.key, A.mirror, x, y, (uint32_t)i, -1, H.it, unpack_vec(wa), ca,
+        update_pixel<L>(V, a, q, gmask, n, H.s, A.key, A.mirror, x, y, (uint32_t)i, -1, H.it, unpack_vec(wa), ca,
                         unpack_vec(wb), cb, cur, c);
         if (q == 0) {
             A.field_out[i] = pack_vec(cur);
@@ -640,20 +659,29 @@ const IterVariant kIterVariants[] = {SFF_ITER_VARIANTS(1), SFF_ITER_VARIANTS(2),
 #undef SFF_ITER_VARIANTS
 #undef SFF_ITER_V
 
+const IterVariant* find_variant(const sff_tuning& t) {
+    for (const auto& v : kIterVariants)
+        if (v.lanes == t.lanes_per_pixel && v.tx == t.tile_x && v.ty == t.tile_y) return &v;
+    return nullptr;
+}
+
 // Tile of the iteration kernel at one scale: the tuned tile at scale 0; at
-// coarser scales the tuned tile if its grid fills the GPU, else the largest
-// smaller tile (same lanes per pixel) that still gives at least two CTAs per
-// SM, else the smallest.  Any tile gives the same result.
-const IterVariant* tile_for_grid(const IterVariant* tuned, int s, int gw, int gh, int nf) {
+// coarser scales the tuned tile if it gives at least two CTAs per SM over
+// all fields, else the largest smaller tile (same lanes per pixel) that
+// does, else the smallest.  Any tile gives the same result.
+long ctas_for(const IterVariant& v, const int* gw, const int* gh, int nf) {
+    long c = 0;
+    for (int k = 0; k < nf; ++k) c += (long)((gw[k] + v.tx - 1) / v.tx) * ((gh[k] + v.ty - 1) / v.ty);
+    return c;
+}
+
+const IterVariant* tile_for_grid(const IterVariant* tuned, int s, const int* gw, const int* gh, int nf) {
     if (s == 0) return tuned;
-    constexpr int kWantCtas = 2 * 152;
+    constexpr long kWantCtas = 2 * 152;
     const IterVariant* pick_v = nullptr;
     for (const auto& v : kIterVariants) {
         if (v.lanes != tuned->lanes || v.tx * v.ty > tuned->tx * tuned->ty) continue;
-        const long ctas = (long)((gw + v.tx - 1) / v.tx) * ((gh + v.ty - 1) / v.ty) * nf;
-        if (ctas >= kWantCtas) {
-            if (!pick_v || v.tx * v.ty > pick_v->tx * pick_v->ty) pick_v = &v;
-        }
+        if (ctas_for(v, gw, gh, nf) >= kWantCtas && (!pick_v || v.tx * v.ty > pick_v->tx * pick_v->ty)) pick_v = &v;
     }
     if (pick_v) return (tuned->tx * tuned->ty == pick_v->tx * pick_v->ty) ? tuned : pick_v;
     for (const auto& v : kIterVariants)  // none fills the GPU: the smallest tile
@@ -661,131 +689,139 @@ const IterVariant* tile_for_grid(const IterVariant* tuned, int s, int gw, int gh
     return pick_v;
 }
 
-const IterVariant* find_variant(const sff_tuning& t) {
-    for (const auto& v : kIterVariants)
-        if (v.lanes == t.lanes_per_pixel && v.tx == t.tile_x && v.ty == t.tile_y) return &v;
-    return nullptr;
-}
-
 int coarse_gq(int w, int h, const sff_params& p) {
     const int n = 1 << (p.num_scales - 1);
     return ((w + n - 1) / n) * ((h + n - 1) / n);
 }
 
-// K-NN scratch of both fields: top-8 lists, then the compacted records and
-// norms of [field][role].  Rows are padded to a multiple of 4 records plus 4,
-// so every bulk copy (whole groups of 4 records) starts and ends on 16 bytes.
+// Scratch of one field: K-NN lists and compact coarsest-grid records, then a
+// second state buffer (field + cost) for the double-buffered iterations.
+// Compact rows are padded to a multiple of 4 records plus 4, so every bulk
+// copy (whole groups of 4 records) starts and ends on 16 bytes.
 int gq_padded(int gq) { return ((gq + 3) & ~3) + 4; }
-size_t knn_lists_bytes(int gq) { return align256((size_t)2 * gq * 8 * sizeof(int2)); }
-size_t knn_recs_bytes(int gq) { return align256((size_t)4 * gq_padded(gq) * kFeat); }
-size_t knn_norms_bytes(int gq) { return align256((size_t)4 * gq_padded(gq) * sizeof(int)); }
-size_t knn_ws_bytes(int w, int h, const sff_params& p) {
-    const int gq = coarse_gq(w, h, p);
-    return knn_lists_bytes(gq) + knn_recs_bytes(gq) + knn_norms_bytes(gq);
+struct FieldScratch {
+    size_t best8, cf, cn, field, cost, total;
+};
+FieldScratch field_scratch(int w, int h, const sff_params& p) {
+    const int gq = coarse_gq(w, h, p), gp = gq_padded(gq);
+    FieldScratch f;
+    f.best8 = 0;
+    f.cf = f.best8 + align256((size_t)gq * 8 * sizeof(int2));
+    f.cn = f.cf + align256((size_t)2 * gp * kFeat);
+    f.field = f.cn + align256((size_t)2 * gp * sizeof(int));
+    f.cost = f.field + align256((size_t)w * h * 8);
+    f.total = f.cost + align256((size_t)w * h * 4);
+    return f;
 }
 
-// Second state buffer (field + cost) of one field for the double-buffered iterations.
-size_t state_bytes(int w, int h) { return align256((size_t)w * h * 8) + align256((size_t)w * h * 4); }
+}  // namespace
 
-// The stage of Sec. 3.1 for nf = 1 or 2 fields sharing the launches.
-struct FieldSpec {
-    const uint8_t *ref, *tmp, *ste, *crs;
-    int16_t* field;
-    int32_t* cost;
-    int mirror;
-};
+size_t field_ws_bytes(int w, int h, const sff_params& p) { return field_scratch(w, h, p).total; }
 
-int run_fields(const FieldSpec* spec, int nf, int width, int height, uint64_t seed, const sff_params& P,
-               const sff_tuning& T, void* workspace, cudaStream_t st) {
+// Workspace of sff_match_views / sff_match_quad: the scratch of two fields.
+size_t match_ws_bytes(int w, int h, const sff_params& p) { return 2 * field_ws_bytes(w, h, p); }
+
+// The stage of Sec. 3.1 for nf <= kMaxFields fields (any sizes) sharing the
+// launches.  spec[k].workspace holds field_ws_bytes() of scratch.
+int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tuning& T, cudaStream_t st) {
     const IterVariant* var = find_variant(T);
-    if (!var) return SFF_ERR_ARG;
+    if (!var || nf < 1 || nf > kMaxFields) return SFF_ERR_ARG;
     const int S = P.num_scales, I = P.iterations;
-    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     static const int kDirs[4][2] = {{1, 1}, {-1, -1}, {1, -1}, {-1, 1}};
-    Fields F{};
-    // workspace: [top-8 lists of both fields][state buffers of field 0][of field 1]
-    char* ws = reinterpret_cast<char*>(workspace);
-    char* st_base = ws + knn_ws_bytes(width, height, P);
-    int16_t* tmp_field[2];
-    int32_t* tmp_cost[2];
-    for (int k = 0; k < 2; ++k) {
-        char* b = st_base + k * state_bytes(width, height);
-        tmp_field[k] = reinterpret_cast<int16_t*>(b);
-        tmp_cost[k] = reinterpret_cast<int32_t*>(b + align256((size_t)width * height * 8));
+    static Fields F;  // host staging of the kernel parameter (copied at each launch)
+    std::lock_guard<std::mutex> lk(g_fields_mu);
+    memset(&F, 0, sizeof F);
+    uint2* U[kMaxFields];
+    int* Uc[kMaxFields];
+    uint2* Tf[kMaxFields];
+    int* Tc[kMaxFields];
+    int gw[kMaxFields], gh[kMaxFields];
+    for (int k = 0; k < nf; ++k) {
+        const FieldSpec& fs = spec[k];
+        const FieldScratch sc = field_scratch(fs.width, fs.height, P);
+        char* ws = reinterpret_cast<char*>(fs.workspace);
+        F.f[k].best8 = reinterpret_cast<int2*>(ws + sc.best8);
+        F.f[k].cf = reinterpret_cast<uint8_t*>(ws + sc.cf);
+        F.f[k].cn = reinterpret_cast<int*>(ws + sc.cn);
+        F.f[k].gq = coarse_gq(fs.width, fs.height, P);
+        F.f[k].gq_pad = gq_padded(F.f[k].gq);
+        F.f[k].mirror = fs.mirror;
+        F.f[k].key = make_uint2((uint32_t)fs.seed, (uint32_t)(fs.seed >> 32));
+        U[k] = reinterpret_cast<uint2*>(fs.field);
+        Uc[k] = fs.cost;
+        Tf[k] = reinterpret_cast<uint2*>(ws + sc.field);
+        Tc[k] = reinterpret_cast<int*>(ws + sc.cost);
     }
     for (int s = S - 1; s >= 0; --s) {
         const int n = 1 << s;
-        const int gw = (width + n - 1) / n, gh = (height + n - 1) / n;
+        int mgw = 0, mgh = 0, mgq = 0;
         for (int k = 0; k < nf; ++k) {
             const FieldSpec& fs = spec[k];
-            F.f[k].V = Views{plane_of(fs.ref, s, S, width, height), plane_of(fs.tmp, s, S, width, height),
-                             plane_of(fs.ste, s, S, width, height), plane_of(fs.crs, s, S, width, height), width,
-                             height, fs.mirror ? -1 : 1};
-            F.f[k].field = F.f[k].field_out = reinterpret_cast<uint2*>(fs.field);
-            F.f[k].cost = F.f[k].cost_out = fs.cost;
-            F.f[k].mirror = fs.mirror;
+            const int w = fs.width, h = fs.height;
+            F.f[k].V = Views{plane_of(fs.ref, s, S, w, h), plane_of(fs.tmp, s, S, w, h), plane_of(fs.ste, s, S, w, h),
+                             plane_of(fs.crs, s, S, w, h), w, h, fs.mirror ? -1 : 1};
+            F.f[k].field = F.f[k].field_out = U[k];
+            F.f[k].cost = F.f[k].cost_out = Uc[k];
+            gw[k] = F.f[k].gw = (w + n - 1) / n;
+            gh[k] = F.f[k].gh = (h + n - 1) / n;
+            mgw = std::max(mgw, gw[k]);
+            mgh = std::max(mgh, gh[k]);
+            mgq = std::max(mgq, F.f[k].gq);
         }
         if (s == S - 1) {
-            const int gq = gw * gh, gq_pad = gq_padded(gq);
-            int2* best8 = reinterpret_cast<int2*>(ws);
-            uint8_t* cf = reinterpret_cast<uint8_t*>(ws + knn_lists_bytes(gq));
-            int* cn = reinterpret_cast<int*>(ws + knn_lists_bytes(gq) + knn_recs_bytes(gq));
-            dim3 g0((gq * 4 + 255) / 256, 2, nf);
-            SFF_LAUNCH(k_gather_grid, g0, 256, 0, st, F, n, gw, gq, gq_pad, cf, cn);
-            dim3 g1((gq + kKnnWarps - 1) / kKnnWarps, 1, nf);
-            SFF_LAUNCH(k_knn, g1, kKnnThreads, 0, st, gq, gq_pad, cf, cn, best8);
-            dim3 g2((gq + 7) / 8, 1, nf);
-            SFF_LAUNCH(k_init_select, g2, 256, 0, st, F, n, gw, gq, P.knn_temporal, best8);
+            dim3 g0((mgq * 4 + 255) / 256, 2, nf);
+            SFF_LAUNCH(k_gather_grid, g0, 256, 0, st, F, n);
+            dim3 g1((mgq + kKnnWarps - 1) / kKnnWarps, 1, nf);
+            SFF_LAUNCH(k_knn, g1, kKnnThreads, 0, st, F);
+            dim3 g2((mgq + 7) / 8, 1, nf);
+            SFF_LAUNCH(k_init_select, g2, 256, 0, st, F, n, P.knn_temporal);
         } else {
-            dim3 g((gw + 127) / 128, gh, nf);
-            SFF_LAUNCH(k_inherit, g, 128, 0, st, F, n, gw, gh);
+            dim3 g((mgw + 127) / 128, mgh, nf);
+            SFF_LAUNCH(k_inherit, g, 128, 0, st, F, n);
         }
         // iterations alternate between the caller's buffers (U) and the
         // workspace buffers (T); with an odd count U is first copied to T so
         // that the last iteration writes U
         if (I & 1)
             for (int k = 0; k < nf; ++k) {
-                cudaMemcpyAsync(tmp_field[k], spec[k].field, (size_t)width * height * 8, cudaMemcpyDeviceToDevice, st);
-                cudaMemcpyAsync(tmp_cost[k], spec[k].cost, (size_t)width * height * 4, cudaMemcpyDeviceToDevice, st);
+                const size_t np = (size_t)spec[k].width * spec[k].height;
+                cudaMemcpyAsync(Tf[k], U[k], np * 8, cudaMemcpyDeviceToDevice, st);
+                cudaMemcpyAsync(Tc[k], Uc[k], np * 4, cudaMemcpyDeviceToDevice, st);
             }
         const IterVariant* sv = tile_for_grid(var, s, gw, gh, nf);
-        dim3 gi((gw + sv->tx - 1) / sv->tx, (gh + sv->ty - 1) / sv->ty, nf);
+        dim3 gi((mgw + sv->tx - 1) / sv->tx, (mgh + sv->ty - 1) / sv->ty, nf);
         for (int it = 0; it < I; ++it) {
             const bool from_user = ((I - it) & 1) == 0;  // the last iteration reads T and writes U
             for (int k = 0; k < nf; ++k) {
-                uint2* U = reinterpret_cast<uint2*>(spec[k].field);
-                uint2* T = reinterpret_cast<uint2*>(tmp_field[k]);
-                F.f[k].field = from_user ? U : T;
-                F.f[k].cost = from_user ? spec[k].cost : tmp_cost[k];
-                F.f[k].field_out = from_user ? T : U;
-                F.f[k].cost_out = from_user ? tmp_cost[k] : spec[k].cost;
+                F.f[k].field = from_user ? U[k] : Tf[k];
+                F.f[k].cost = from_user ? Uc[k] : Tc[k];
+                F.f[k].field_out = from_user ? Tf[k] : U[k];
+                F.f[k].cost_out = from_user ? Tc[k] : Uc[k];
             }
-            IterStep H{n, s, gw, gh, kDirs[it % 4][0], kDirs[it % 4][1], it, key};
+            IterStep H{n, s, kDirs[it % 4][0], kDirs[it % 4][1], it};
             if (::sff::profiling()) ::sff::profile_mark("k_iteration", st, false);
             sv->k<<<gi, sv->threads, 0, st>>>(F, H);
             if (::sff::profiling()) ::sff::profile_mark("k_iteration", st, true);
         }
         for (int k = 0; k < nf; ++k) {
-            F.f[k].field = F.f[k].field_out = reinterpret_cast<uint2*>(spec[k].field);
-            F.f[k].cost = F.f[k].cost_out = spec[k].cost;
+            F.f[k].field = F.f[k].field_out = U[k];
+            F.f[k].cost = F.f[k].cost_out = Uc[k];
         }
         if (I > 0) {
-            const int half_w = (gw + 1) / 2;
-            dim3 g((half_w + kHalfPixels - 1) / kHalfPixels, gh, nf);
-            HalfStep H{n, s, gw, 0, 0, 0, 0, I - 1, -1, key};
+            const int half_w = (mgw + 1) / 2;
+            dim3 g((half_w + kHalfPixels - 1) / kHalfPixels, mgh, nf);
+            HalfStep H{n, s, 0, 0, 0, 0, I - 1, -1};
             SFF_LAUNCH(k_half_step, g, kHalfThreads, 0, st, F, H);
         }
     }
     return launch_status();
 }
 
+namespace {
+
 bool misaligned_pyr(const uint8_t* p) { return ((uintptr_t)p & 15) != 0; }
 
 }  // namespace
-
-// Workspace: per field the temporal top-8 lists and a second state buffer
-// (field + cost) for the double-buffered iterations.
-size_t match_ws_bytes(int w, int h, const sff_params& p) { return knn_ws_bytes(w, h, p) + 2 * state_bytes(w, h); }
 
 }  // namespace sff
 
@@ -805,10 +841,11 @@ extern "C" int sff_match_views(const uint8_t* pyr_ref_dev, const uint8_t* pyr_te
         return SFF_ERR_ARG;
     if (((uintptr_t)field_dev & 7) || ((uintptr_t)cost_dev & 3) || ((uintptr_t)workspace & 255)) return SFF_ERR_ARG;
     if (workspace_bytes < match_ws_bytes(width, height, *params)) return SFF_ERR_WORKSPACE;
-    FieldSpec f{pyr_ref_dev, pyr_temporal_dev, pyr_stereo_dev, pyr_cross_dev, field_dev, cost_dev, mirror};
+    FieldSpec f{pyr_ref_dev, pyr_temporal_dev, pyr_stereo_dev, pyr_cross_dev, field_dev, cost_dev, mirror,
+                width, height, seed, workspace};
     sff_tuning t;
     sff_default_tuning(&t);
-    return run_fields(&f, 1, width, height, seed, *params, t, workspace, (cudaStream_t)stream);
+    return run_fields(&f, 1, *params, t, (cudaStream_t)stream);
 }
 
 extern "C" int sff_default_tuning(sff_tuning* out) {
@@ -841,9 +878,13 @@ extern "C" int sff_match_quad_tuned(const uint8_t* pyr_l0_dev, const uint8_t* py
         ((uintptr_t)inv_cost_dev & 3) || ((uintptr_t)workspace & 255))
         return SFF_ERR_ARG;
     if (workspace_bytes < match_ws_bytes(width, height, *params)) return SFF_ERR_WORKSPACE;
-    FieldSpec f[2] = {{pyr_l0_dev, pyr_l1_dev, pyr_r0_dev, pyr_r1_dev, fwd_dev, fwd_cost_dev, 0},
-                      {pyr_r1_dev, pyr_r0_dev, pyr_l1_dev, pyr_l0_dev, inv_dev, inv_cost_dev, 1}};
-    return run_fields(f, 2, width, height, seed, *params, *tuning, workspace, (cudaStream_t)stream);
+    char* ws = reinterpret_cast<char*>(workspace);
+    const size_t half = field_ws_bytes(width, height, *params);
+    FieldSpec f[2] = {{pyr_l0_dev, pyr_l1_dev, pyr_r0_dev, pyr_r1_dev, fwd_dev, fwd_cost_dev, 0, width, height, seed,
+                       ws},
+                      {pyr_r1_dev, pyr_r0_dev, pyr_l1_dev, pyr_l0_dev, inv_dev, inv_cost_dev, 1, width, height, seed,
+                       ws + half}};
+    return run_fields(f, 2, *params, *tuning, (cudaStream_t)stream);
 }
 
 extern "C" int sff_match_quad(const uint8_t* pyr_l0_dev, const uint8_t* pyr_r0_dev, const uint8_t* pyr_l1_dev,

@@ -27,11 +27,16 @@ constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 int* g_noalloc_ptr[kMaxDevices] = {};
 
+struct SeedJobs {
+    SeedJob q[kMaxQuads];
+};
+
 // One thread per block: raster index of its best kept pixel or -1; one count
 // of found seeds per CTA.
-__global__ void __launch_bounds__(kChunk) k_block_best(const int* __restrict__ fcost, const uint8_t* __restrict__ keep,
-                                                       const uint8_t* __restrict__ cerr, int w, int h, int bw, int nb,
-                                                       int* __restrict__ best, int* __restrict__ chunk_count) {
+__global__ void __launch_bounds__(kChunk) k_block_best(const __grid_constant__ SeedJobs J) {
+    const SeedJob& Q = J.q[blockIdx.z];
+    const int w = Q.w, h = Q.h, bw = (w + 2) / 3, nb = bw * ((h + 2) / 3);
+    if ((int)blockIdx.x * kChunk >= nb) return;  // whole CTA beyond this quad's blocks
     const int b = blockIdx.x * kChunk + threadIdx.x;
     int bi = -1;
     if (b < nb) {
@@ -40,24 +45,28 @@ __global__ void __launch_bounds__(kChunk) k_block_best(const int* __restrict__ f
         for (int y = by; y < min(by + 3, h); ++y)
             for (int x = bx; x < min(bx + 3, w); ++x) {
                 const int i = y * w + x;
-                if (!keep[i]) continue;
-                const int e = cerr[i], c = fcost[i];
+                if (!Q.keep[i]) continue;
+                const int e = Q.cerr[i], c = Q.fcost[i];
                 if (bi < 0 || e < be || (e == be && c < bc)) {  // raster order: ties keep the earlier pixel
                     bi = i;
                     be = e;
                     bc = c;
                 }
             }
-        best[b] = bi;
+        Q.best[b] = bi;
     }
     const int n = __syncthreads_count(bi >= 0);
-    if (threadIdx.x == 0) chunk_count[blockIdx.x] = n;
+    if (threadIdx.x == 0) Q.chunk[blockIdx.x] = n;
 }
 
-// One CTA: exclusive scan of the chunk counts in place; the total to *count.
-__global__ void __launch_bounds__(kScanThreads) k_scan_chunks(int* __restrict__ chunk, int nchunks,
-                                                             int* __restrict__ count) {
+// One CTA per quad: exclusive scan of the chunk counts in place; the total
+// to *count.
+__global__ void __launch_bounds__(kScanThreads) k_scan_chunks(const __grid_constant__ SeedJobs J) {
     __shared__ int warp_sums[kScanThreads / 32];
+    const SeedJob& Q = J.q[blockIdx.z];
+    const int nb = ((Q.w + 2) / 3) * ((Q.h + 2) / 3);
+    const int nchunks = (nb + kChunk - 1) / kChunk;
+    int* chunk = Q.chunk;
     const int t = threadIdx.x;
     const int per = (nchunks + kScanThreads - 1) / kScanThreads;
     const int c0 = min(nchunks, t * per), c1 = min(nchunks, c0 + per);
@@ -87,19 +96,18 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_chunks(int* __restrict__ 
         chunk[c] = pos;
         pos += k;
     }
-    if (t == kScanThreads - 1) *count = pos;
+    if (t == kScanThreads - 1) *Q.count = pos;
 }
 
 // Same grid as k_block_best: rank of each found seed inside its CTA (warp
 // ballots + warp offsets) plus the chunk offset gives its output slot.
-__global__ void __launch_bounds__(kChunk) k_write_seeds(const int* __restrict__ best, int nb,
-                                                        const int* __restrict__ chunk_off,
-                                                        const uint2* __restrict__ fwd, const int* __restrict__ fcost,
-                                                        const uint8_t* __restrict__ cerr, int w,
-                                                        sff_seed* __restrict__ out, int capacity) {
+__global__ void __launch_bounds__(kChunk) k_write_seeds(const __grid_constant__ SeedJobs J) {
     __shared__ int warp_base[kChunk / 32];
+    const SeedJob& Q = J.q[blockIdx.z];
+    const int w = Q.w, nb = ((Q.w + 2) / 3) * ((Q.h + 2) / 3);
+    if ((int)blockIdx.x * kChunk >= nb) return;  // whole CTA beyond this quad's blocks
     const int b = blockIdx.x * kChunk + threadIdx.x;
-    const int i = b < nb ? best[b] : -1;
+    const int i = b < nb ? Q.best[b] : -1;
     const unsigned ballot = __ballot_sync(0xffffffffu, i >= 0);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) warp_base[wid] = __popc(ballot);
@@ -114,9 +122,9 @@ __global__ void __launch_bounds__(kChunk) k_write_seeds(const int* __restrict__ 
     }
     __syncthreads();
     if (i < 0) return;
-    const int pos = chunk_off[blockIdx.x] + warp_base[wid] + __popc(ballot & ((1u << lane) - 1u));
-    if (pos >= capacity) return;
-    const Vec4 a = unpack_vec(fwd[i]);
+    const int pos = Q.chunk[blockIdx.x] + warp_base[wid] + __popc(ballot & ((1u << lane) - 1u));
+    if (pos >= Q.capacity) return;
+    const Vec4 a = unpack_vec(Q.fwd[i]);
     sff_seed sd;
     sd.x = (int16_t)(i % w);
     sd.y = (int16_t)(i / w);
@@ -124,23 +132,10 @@ __global__ void __launch_bounds__(kChunk) k_write_seeds(const int* __restrict__ 
     sd.v = (int16_t)a.v;
     sd.d0 = (int16_t)a.d0;
     sd.d1 = (int16_t)a.d1;
-    sd.cost = fcost[i];
-    sd.cerr = cerr[i];
+    sd.cost = Q.fcost[i];
+    sd.cerr = Q.cerr[i];
     sd.pad[0] = sd.pad[1] = sd.pad[2] = 0;
-    out[pos] = sd;
-}
-
-int launch_seeds(const int16_t* fwd_dev, const int32_t* fwd_cost_dev, const uint8_t* keep_dev,
-                 const uint8_t* cerr_dev, int width, int height, sff_seed* seeds_dev, int capacity, int* count_dev,
-                 int* best, int* chunk, cudaStream_t st) {
-    const int bw = (width + 2) / 3, nb = bw * ((height + 2) / 3);
-    const int nchunks = (nb + kChunk - 1) / kChunk;
-    SFF_LAUNCH(k_block_best, nchunks, kChunk, 0, st, fwd_cost_dev, keep_dev, cerr_dev, width, height, bw, nb, best,
-               chunk);
-    SFF_LAUNCH(k_scan_chunks, 1, kScanThreads, 0, st, chunk, nchunks, count_dev);
-    SFF_LAUNCH(k_write_seeds, nchunks, kChunk, 0, st, best, nb, chunk, reinterpret_cast<const uint2*>(fwd_dev),
-               fwd_cost_dev, cerr_dev, width, seeds_dev, capacity);
-    return launch_status();
+    Q.out[pos] = sd;
 }
 
 }  // namespace
@@ -148,6 +143,29 @@ int launch_seeds(const int16_t* fwd_dev, const int32_t* fwd_cost_dev, const uint
 size_t seeds_ws_bytes(int w, int h) {
     const size_t nb = (size_t)((w + 2) / 3) * ((h + 2) / 3);
     return align256(nb * sizeof(int)) + align256((nb + kChunk - 1) / kChunk * sizeof(int));
+}
+
+void seeds_carve(void* workspace, int w, int h, int** best, int** chunk) {
+    const size_t nb = (size_t)((w + 2) / 3) * ((h + 2) / 3);
+    *best = reinterpret_cast<int*>(workspace);
+    *chunk = reinterpret_cast<int*>((char*)workspace + align256(nb * sizeof(int)));
+}
+
+int run_seeds(const SeedJob* jobs, int n, cudaStream_t st) {
+    if (n < 1 || n > kMaxQuads) return SFF_ERR_ARG;
+    static SeedJobs J;  // host staging of the kernel parameter (copied at each launch)
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    int mchunks = 0;
+    for (int k = 0; k < n; ++k) {
+        J.q[k] = jobs[k];
+        const int nb = ((jobs[k].w + 2) / 3) * ((jobs[k].h + 2) / 3);
+        mchunks = mchunks > (nb + kChunk - 1) / kChunk ? mchunks : (nb + kChunk - 1) / kChunk;
+    }
+    SFF_LAUNCH(k_block_best, dim3(mchunks, 1, n), kChunk, 0, st, J);
+    SFF_LAUNCH(k_scan_chunks, dim3(1, 1, n), kScanThreads, 0, st, J);
+    SFF_LAUNCH(k_write_seeds, dim3(mchunks, 1, n), kChunk, 0, st, J);
+    return launch_status();
 }
 
 }  // namespace sff
@@ -163,11 +181,10 @@ extern "C" int sff_emit_seeds(const int16_t* fwd_dev, const int32_t* fwd_cost_de
     if (capacity > 0 && !seeds_dev) return SFF_ERR_ARG;
     if (((uintptr_t)fwd_dev & 7) || ((uintptr_t)seeds_dev & 3) || ((uintptr_t)workspace & 255)) return SFF_ERR_ARG;
     if (workspace_bytes < seeds_ws_bytes(width, height)) return SFF_ERR_WORKSPACE;
-    const size_t nb = (size_t)((width + 2) / 3) * ((height + 2) / 3);
-    int* best = reinterpret_cast<int*>(workspace);
-    int* chunk = reinterpret_cast<int*>((char*)workspace + align256(nb * sizeof(int)));
-    return launch_seeds(fwd_dev, fwd_cost_dev, keep_dev, cerr_dev, width, height, seeds_dev, capacity, count_dev,
-                        best, chunk, (cudaStream_t)stream);
+    SeedJob job{reinterpret_cast<const uint2*>(fwd_dev), fwd_cost_dev, keep_dev, cerr_dev, width, height, nullptr,
+                nullptr, seeds_dev, capacity, count_dev};
+    seeds_carve(workspace, width, height, &job.best, &job.chunk);
+    return run_seeds(&job, 1, (cudaStream_t)stream);
 }
 
 extern "C" int sff_emit_seeds_noalloc(const int16_t* fwd_dev, const int32_t* fwd_cost_dev, const uint8_t* keep_dev,
@@ -197,6 +214,7 @@ extern "C" int sff_emit_seeds_noalloc(const int16_t* fwd_dev, const int32_t* fwd
     }
     // Every scratch entry a call reads is written earlier in the same call
     // (block bests and chunk counts by k_block_best), so nothing is cleared.
-    return launch_seeds(fwd_dev, fwd_cost_dev, keep_dev, cerr_dev, width, height, seeds_dev, capacity, count_dev,
-                        scratch, scratch + kNoAllocMaxBlocks, (cudaStream_t)stream);
+    SeedJob job{reinterpret_cast<const uint2*>(fwd_dev), fwd_cost_dev, keep_dev, cerr_dev, width, height, scratch,
+                scratch + kNoAllocMaxBlocks, seeds_dev, capacity, count_dev};
+    return run_seeds(&job, 1, (cudaStream_t)stream);
 }

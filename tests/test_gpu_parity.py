@@ -124,8 +124,8 @@ def test_match_views_planes_scene(env, seed):
         assert np.array_equal(gf, of)
 
 
-def _run_gpu_quad(torch, sff, q, seed, p=None, concurrent=True):
-    m = sff.QuadMatcher(q.width, q.height, p, concurrent=concurrent)
+def _run_gpu_quad(torch, sff, q, seed, p=None, mode="batch"):
+    m = sff.QuadMatcher(q.width, q.height, p, mode=mode)
     dev = [torch.as_tensor(im).cuda() for im in q.images()]
     seeds, count = m.run(*dev, seed=seed)
     torch.cuda.synchronize()
@@ -144,12 +144,12 @@ def _assert_quad_equal(m, got_seeds, n, ref):
     assert got_seeds.tobytes() == ref["seeds"].tobytes()
 
 
-@pytest.mark.parametrize("name,seed,concurrent", [("planes_256x80", 1, True), ("planes_256x80", 5, True),
-                                                  ("planes_256x80", 5, False)])
-def test_full_stage_small(env, name, seed, concurrent):
+@pytest.mark.parametrize("name,seed,mode", [("planes_256x80", 1, "batch"), ("planes_256x80", 5, "batch"),
+                                            ("planes_256x80", 5, "calls")])
+def test_full_stage_small(env, name, seed, mode):
     torch, sff, orc = env
     q = scenegen.make_named(name, seed)
-    m, got, n = _run_gpu_quad(torch, sff, q, seed=seed, concurrent=concurrent)
+    m, got, n = _run_gpu_quad(torch, sff, q, seed=seed, mode=mode)
     ref = orc.run_quad(*q.images(), seed=seed)
     _assert_quad_equal(m, got, n, ref)
 
@@ -270,3 +270,46 @@ def test_every_tuning_gives_identical_fields(env):
             assert np.array_equal(got[0], o["fwd"]) and np.array_equal(got[1], o["inv"])
         for a, b in zip(got, ref):
             assert np.array_equal(a, b), cand
+
+
+def test_batch_of_uneven_quads_equals_each_alone(env):
+    # quads of different sizes and seeds in shared launches (sff_run_batch):
+    # every quad's fields, masks and seeds equal the oracle's run on it alone
+    torch, sff, orc = env
+    specs = [("planes", 256, 80, 1, 11), ("planes", 96, 40, 2, 12), ("planes", 130, 70, 3, 13),
+             ("planes", 64, 48, 4, 14), ("shift", 160, 96, 5, 15)]
+    quads = []
+    for fam, w, h, sd, ms in specs:
+        q = (scenegen.make_shift_quad(w, h, sd, u=-3, v=2, d0=4, d1=6) if fam == "shift"
+             else scenegen.make_quad(fam, w, h, sd))
+        quads.append((q, ms))
+    bm = sff.BatchMatcher([(q.width, q.height) for q, _ in quads])
+    for k, (q, _) in enumerate(quads):
+        bm.load(k, *q.images())
+    bm.run([ms for _, ms in quads])
+    torch.cuda.synchronize()
+    for (q, ms), b in zip(quads, bm.quads):
+        ref = orc.run_quad(*q.images(), seed=ms)
+        assert np.array_equal(b.fwd.cpu().numpy(), ref["fwd"])
+        assert np.array_equal(b.inv.cpu().numpy(), ref["inv"])
+        assert np.array_equal(b.fwd_cost.cpu().numpy(), ref["fwd_cost"])
+        assert np.array_equal(b.keep.cpu().numpy(), ref["keep"])
+        assert np.array_equal(b.cerr.cpu().numpy(), ref["cerr"])
+        assert b.seeds_numpy().tobytes() == ref["seeds"].tobytes()
+
+
+def test_batch_graph_replay_is_deterministic(env):
+    torch, sff, orc = env
+    qs = [scenegen.make_quad("planes", 128, 64, s) for s in (21, 22, 23)]
+    bm = sff.BatchMatcher([(128, 64)] * 3)
+    for k, q in enumerate(qs):
+        bm.load(k, *q.images())
+    g = bm.capture([1, 2, 3])
+    g.replay()
+    torch.cuda.synchronize()
+    first = [b.seeds_numpy().tobytes() for b in bm.quads]
+    g.replay()
+    torch.cuda.synchronize()
+    assert first == [b.seeds_numpy().tobytes() for b in bm.quads]
+    ref = orc.run_quad(*qs[1].images(), seed=2)
+    assert first[1] == ref["seeds"].tobytes()
