@@ -54,7 +54,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sff", choices=["sff", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-batch", action="store_true", help="skip the 32-quad batched measurement")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 32-quad batched and the serving measurements")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--tuning", default="auto",
                     help="work distribution of the propagation kernels: 'auto' (autotune) or L,TX,TY")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(scenegen.CONFIG_SIZES),
@@ -260,6 +261,31 @@ def bench_batched(sff, torch, dev, quads, seeds, params, tuning, steps, warmup):
     return out
 
 
+SERVING_RATES = (50.0, 200.0, 400.0)  # aggregate quads/s over 8 camera streams
+
+
+def bench_serving(sff, torch, dev, quads, params, tuning, n_requests=240):
+    """p50/p99 latency and sustained px/s of the continuous-batching server
+    vs the plain per-request server, on Poisson arrivals from 8 streams over
+    a pool of 24 quads (8 each of 1242x375, 1024x436, 640x192)."""
+    from paper_1710_10096_gb300.serve import PlainServer, Server, poisson_arrivals, simulate, summarize
+    pool = [tuple(im) for im in quads if im[0].shape[1] in (1242, 1024, 640)]
+    out = {"pool": f"{len(pool)} quads: 8 x 1242x375, 8 x 1024x436, 8 x 640x192", "streams": 8,
+           "requests_per_rate": n_requests}
+    srv = Server(params, tuning, device=dev, max_batch=32)
+    plain = PlainServer(params, tuning, device=dev)
+    simulate(srv, poisson_arrivals(400.0, 24, 8, len(pool), seed=1), pool)  # warm-up: slots allocated
+    simulate(plain, poisson_arrivals(400.0, 24, 8, len(pool), seed=1), pool)
+    for rate in SERVING_RATES:
+        arr = poisson_arrivals(rate, n_requests, 8, len(pool), seed=7)
+        r1, w1 = simulate(srv, arr, pool)
+        r2, w2 = simulate(plain, arr, pool)
+        a, b = summarize(r1, w1), summarize(r2, w2)
+        same = all(x.seeds.tobytes() == y.seeds.tobytes() for x, y in zip(r1, r2))
+        out[f"rate_{int(rate)}"] = {"continuous": a, "plain": b, "identical_results": bool(same)}
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
@@ -429,6 +455,8 @@ def main():
     if batch is not None:
         line["batched"] = bench_batched(sff, torch, dev, batch[0], batch[1], params, tuning, min(args.steps, 20),
                                         max(1, args.warmup))
+        if not args.no_serving:
+            line["serving"] = bench_serving(sff, torch, dev, batch[0], params, tuning)
     if rank == 0 and not args.no_cpu_baseline:
         cb, ref = cpu_baseline(q, MATCH_SEED)
         line["cpu_baseline"] = cb
