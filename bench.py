@@ -261,22 +261,25 @@ def bench_batched(sff, torch, dev, quads, seeds, params, tuning, steps, warmup):
     return out
 
 
-SERVING_RATES = (50.0, 200.0, 400.0)  # aggregate quads/s over 8 camera streams
+SERVING_RATES = (10.0, 50.0, 200.0, 400.0)  # aggregate quads/s over 8 camera streams
 
 
-def bench_serving(sff, torch, dev, quads, params, tuning, n_requests=240):
+def bench_serving(sff, torch, dev, quads, params, tuning, max_requests=240):
     """p50/p99 latency and sustained px/s of the continuous-batching server
     vs the plain per-request server, on Poisson arrivals from 8 streams over
     a pool of 24 quads (8 each of 1242x375, 1024x436, 640x192)."""
     from paper_1710_10096_gb300.serve import PlainServer, Server, poisson_arrivals, simulate, summarize
     pool = [tuple(im) for im in quads if im[0].shape[1] in (1242, 1024, 640)]
     out = {"pool": f"{len(pool)} quads: 8 x 1242x375, 8 x 1024x436, 8 x 640x192", "streams": 8,
-           "requests_per_rate": n_requests}
+           "requests": "min(240, 3 s of arrivals), at least 40 per rate"}
     srv = Server(params, tuning, device=dev, max_batch=32)
+    for size in {(im[0].shape[1], im[0].shape[0]) for im in pool}:
+        srv.reserve(size, 8)  # resident slots: no allocation while requests wait
     plain = PlainServer(params, tuning, device=dev)
     simulate(srv, poisson_arrivals(400.0, 24, 8, len(pool), seed=1), pool)  # warm-up: slots allocated
     simulate(plain, poisson_arrivals(400.0, 24, 8, len(pool), seed=1), pool)
     for rate in SERVING_RATES:
+        n_requests = max(40, min(max_requests, int(3 * rate)))
         arr = poisson_arrivals(rate, n_requests, 8, len(pool), seed=7)
         r1, w1 = simulate(srv, arr, pool)
         r2, w2 = simulate(plain, arr, pool)

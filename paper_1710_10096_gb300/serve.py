@@ -93,6 +93,22 @@ class Server:
         with self._lock:
             self.pending.append(req)
 
+    def reserve(self, size, count: int) -> int:
+        """Pre-allocate up to `count` idle slots of `size` within the budget
+        (allocation is slow: it should not happen while requests wait)."""
+        made = 0
+        with self._lock:
+            while len(self.slots[size]) < count:
+                need = self._slot_bytes(size)
+                if self.bytes_used + need > self.hbm_budget:
+                    break
+                slot = _Slot(size[0], size[1], self.params, self.device)
+                self.bytes_used += need
+                self.slots[size].append(slot)
+                self.free[size].append(slot)
+                made += 1
+        return made
+
     # --- admission: a free slot of the request's size, or a new one within budget
     def _admit(self):
         while self.pending:
