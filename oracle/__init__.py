@@ -22,18 +22,20 @@ _lib = None
 
 NF = 48
 EMPTY = np.iinfo(np.int32).max
+# order_mode bits: readings switched back towards the paper's own procedure
+SEQUENTIAL_SCAN, KDTREE_INIT, SEQUENTIAL_RNG = 1, 2, 4
 
 
 class Params(ctypes.Structure):
     """Method parameters (Sec. 5 values plus the stated readings)."""
     _fields_ = [("num_scales", ctypes.c_int32), ("iterations", ctypes.c_int32), ("tau_c", ctypes.c_int32),
                 ("region_min", ctypes.c_int32), ("tau_r", ctypes.c_int32), ("quant_shift", ctypes.c_int32),
-                ("knn_temporal", ctypes.c_int32), ("knn_epipolar", ctypes.c_int32)]
+                ("knn_temporal", ctypes.c_int32), ("knn_epipolar", ctypes.c_int32), ("order_mode", ctypes.c_int32)]
 
 
 def default_params(**over) -> Params:
     p = dict(num_scales=4, iterations=12, tau_c=1, region_min=150, tau_r=1, quant_shift=4,
-             knn_temporal=4, knn_epipolar=2)
+             knn_temporal=4, knn_epipolar=2, order_mode=0)
     p.update(over)
     return Params(**p)
 

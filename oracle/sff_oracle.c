@@ -76,7 +76,16 @@ typedef struct {
     int32_t quant_shift;   /* feature quantisation shift */
     int32_t knn_temporal;  /* K_T leaves of the temporal tree */
     int32_t knn_epipolar;  /* K_E leaves of each epipolar tree */
+    int32_t order_mode;    /* 0: the readings above (what the CUDA path computes); bits switch
+                              readings back towards the paper's own procedure, for the
+                              quality comparison only: 1 = in-place sequential scans (D4),
+                              2 = approximate kD-tree leaves (D3), 4 = sequential random
+                              stream (D5) */
 } sffo_params;
+
+#define SFFO_SEQUENTIAL_SCAN 1
+#define SFFO_KDTREE_INIT 2
+#define SFFO_SEQUENTIAL_RNG 4
 
 typedef struct {
     int16_t x, y, u, v, d0, d1;
@@ -359,6 +368,141 @@ static void init_coarsest(const views_t* V, int s, const sffo_params* prm, int16
 }
 
 /* ---------------------------------------------------------------------------
+ * The paper's approximate initialisation (Sec. 3.1 "Initialization"), for the
+ * quality comparison of reading D3: kD-trees over the coarsest-grid features
+ * of the temporal image and, per grid row, of the stereo and cross images
+ * ("epipolar" trees); a query descends to one leaf and all combinations of
+ * the leaves' points are scored with the full cost.  Trees: median split on
+ * the dimension of largest spread, leaves of at most 8 points, single
+ * descent without backtracking.
+ */
+typedef struct { int dim, split, left, right, start, count; } kdnode;
+
+typedef struct {
+    kdnode* nodes; int nn, cap;
+    int* idx;          /* raster indices, permuted so that leaves are contiguous */
+    const int8_t* f;   /* feature plane [H][W][48] */
+} kdtree;
+
+static const int8_t* g_sort_f;
+static int g_sort_dim;
+static int cmp_dim(const void* a, const void* b) {
+    int ia = *(const int*)a, ib = *(const int*)b;
+    int va = g_sort_f[(size_t)ia * NF + g_sort_dim], vb = g_sort_f[(size_t)ib * NF + g_sort_dim];
+    if (va != vb) return va < vb ? -1 : 1;
+    return ia < ib ? -1 : (ia > ib);
+}
+
+static int kd_build(kdtree* T, int start, int count) {
+    if (T->nn == T->cap) { T->cap = T->cap ? 2 * T->cap : 64; T->nodes = (kdnode*)realloc(T->nodes, T->cap * sizeof(kdnode)); }
+    int id = T->nn++;
+    kdnode nd = {0, 0, -1, -1, start, count};
+    if (count > 8) {
+        int best_dim = 0, best_spread = -1;
+        for (int d = 0; d < NF; d++) {
+            int lo = 127, hi = -128;
+            for (int k = 0; k < count; k++) {
+                int v = T->f[(size_t)T->idx[start + k] * NF + d];
+                if (v < lo) lo = v;
+                if (v > hi) hi = v;
+            }
+            if (hi - lo > best_spread) { best_spread = hi - lo; best_dim = d; }
+        }
+        g_sort_f = T->f; g_sort_dim = best_dim;
+        qsort(T->idx + start, count, sizeof(int), cmp_dim);
+        int m = count / 2;
+        nd.dim = best_dim;
+        nd.split = T->f[(size_t)T->idx[start + m] * NF + best_dim];
+        int l = kd_build(T, start, m);
+        int r = kd_build(T, start + m, count - m);
+        nd.left = l; nd.right = r;
+    }
+    T->nodes[id] = nd;
+    return id;
+}
+
+static void kd_init(kdtree* T, const int8_t* f, const int* pts, int n) {
+    T->nodes = NULL; T->nn = T->cap = 0; T->f = f;
+    T->idx = (int*)malloc((n > 0 ? n : 1) * sizeof(int));
+    memcpy(T->idx, pts, n * sizeof(int));
+    if (n > 0) kd_build(T, 0, n);
+}
+
+static void kd_free(kdtree* T) { free(T->nodes); free(T->idx); }
+
+/* the leaf a query descends to: its points T->idx[*start .. *start + *count) */
+static void kd_leaf(const kdtree* T, const int8_t* q, int* start, int* count) {
+    int node = 0;
+    while (T->nodes[node].left >= 0) node = q[T->nodes[node].dim] < T->nodes[node].split ? T->nodes[node].left : T->nodes[node].right;
+    *start = T->nodes[node].start; *count = T->nodes[node].count;
+}
+
+static void init_kdtree(const views_t* V, int s, const sffo_params* prm, int16_t* field, int32_t* cost) {
+    int w = V->w, h = V->h, n = 1 << s;
+    int gw = (w + n - 1) / n, gh = (h + n - 1) / n;
+    int* pts = (int*)malloc((size_t)gw * gh * sizeof(int));
+    int np = 0;
+    for (int y = 0; y < h; y += n) for (int x = 0; x < w; x += n) pts[np++] = y * w + x;
+    kdtree tt; kd_init(&tt, V->tmp, pts, np);
+    kdtree* st = (kdtree*)malloc(gh * sizeof(kdtree));
+    kdtree* xt = (kdtree*)malloc(gh * sizeof(kdtree));
+    for (int r = 0; r < gh; r++) { kd_init(&st[r], V->ste, pts + r * gw, gw); kd_init(&xt[r], V->crs, pts + r * gw, gw); }
+    int KT = prm->knn_temporal, KE = prm->knn_epipolar;
+    #pragma omp parallel for num_threads(g_threads) schedule(dynamic, 1)
+    for (int py = 0; py < h; py += n) {
+        cand_t tl[64], sl[64], xl[64];
+        for (int px = 0; px < w; px += n) {
+            const int8_t* a = V->ref + ((size_t)py * w + px) * NF;
+            int ls, lc, nt = 0, ns = 0;
+            kd_leaf(&tt, a, &ls, &lc);
+            for (int k = 0; k < lc; k++) { int q = tt.idx[ls + k]; knn_insert(tl, &nt, KT, ssd(a, V->tmp + (size_t)q * NF), q); }
+            const kdtree* S = &st[py / n];
+            kd_leaf(S, a, &ls, &lc);
+            for (int k = 0; k < lc; k++) {
+                int q = S->idx[ls + k];
+                if (V->sigma * (px - q % w) >= 0) knn_insert(sl, &ns, KE, ssd(a, V->ste + (size_t)q * NF), q);
+            }
+            if (ns == 0) /* no leaf point satisfies d0 >= 0: the pixel's own column is always valid */
+                knn_insert(sl, &ns, KE, ssd(a, V->ste + ((size_t)py * w + px) * NF), py * w + px);
+            int32_t best_c = EMPTY_COST;
+            int16_t best_u[4] = {0, 0, 0, 0};
+            for (int it = 0; it < nt; it++) {
+                int tx = tl[it].idx % w, ty = tl[it].idx / w, nx = 0;
+                const kdtree* X = &xt[ty / n];
+                kd_leaf(X, a, &ls, &lc);
+                for (int k = 0; k < lc; k++) {
+                    int q = X->idx[ls + k];
+                    if (V->sigma * (tx - q % w) >= 0) knn_insert(xl, &nx, KE, ssd(a, V->crs + (size_t)q * NF), q);
+                }
+                if (nx == 0) knn_insert(xl, &nx, KE, ssd(a, V->crs + ((size_t)ty * w + tx) * NF), ty * w + tx);
+                for (int is = 0; is < ns; is++)
+                    for (int ix = 0; ix < nx; ix++) {
+                        int sx = sl[is].idx % w, cx = xl[ix].idx % w;
+                        int16_t u[4] = {(int16_t)(tx - px), (int16_t)(ty - py), (int16_t)(V->sigma * (px - sx)),
+                                        (int16_t)(V->sigma * (tx - cx))};
+                        int32_t c = cost_at(V, px, py, u);
+                        if (c < best_c) { best_c = c; memcpy(best_u, u, sizeof best_u); }
+                    }
+            }
+            memcpy(field + ((size_t)py * w + px) * 4, best_u, sizeof best_u);
+            cost[(size_t)py * w + px] = best_c;
+        }
+    }
+    kd_free(&tt);
+    for (int r = 0; r < gh; r++) { kd_free(&st[r]); kd_free(&xt[r]); }
+    free(st); free(xt); free(pts);
+}
+
+/* Sequential random stream for reading D5's comparison: splitmix64 (Steele,
+ * Lea, Flood, "Fast splittable pseudorandom number generators", OOPSLA'14). */
+static uint64_t splitmix64(uint64_t* st) {
+    uint64_t z = (*st += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* ---------------------------------------------------------------------------
  * Field estimation for one reference view (forward: mirror = 0, reference L0,
  * temporal L1, stereo R0, cross R1; inverse: mirror = 1, reference R1,
  * temporal R0, stereo L1, cross L0).  feat_*: [S][H][W][48] from sffo_features.
@@ -383,7 +527,8 @@ void sffo_match_views(const int8_t* f_ref, const int8_t* f_tmp, const int8_t* f_
 
         if (s == S - 1) {
             /* initialisation on the coarsest scale only (Sec. 3.1) */
-            init_coarsest(&V, s, prm, field, cost);
+            if (prm->order_mode & SFFO_KDTREE_INIT) init_kdtree(&V, s, prm, field, cost);
+            else init_coarsest(&V, s, prm, field, cost);
         } else {
             /* points of the coarser grid keep their vector, re-scored at this
                scale; all other points of this grid start empty */
@@ -403,6 +548,25 @@ void sffo_match_views(const int8_t* f_ref, const int8_t* f_tmp, const int8_t* f_
 
         for (int it = 0; it < prm->iterations; it++) {
             int dx = DIRS[it % 4][0], dy = DIRS[it % 4][1];
+            if (prm->order_mode & SFFO_SEQUENTIAL_SCAN) {
+                /* the paper's order: one in-place raster sweep in the
+                   iteration's direction; each pixel sees its predecessors'
+                   values of this sweep */
+                int gw = (w + n - 1) / n, gh = (h + n - 1) / n;
+                for (int gyk = 0; gyk < gh; gyk++)
+                    for (int gxk = 0; gxk < gw; gxk++) {
+                        int x = (dx > 0 ? gxk : gw - 1 - gxk) * n, y = (dy > 0 ? gyk : gh - 1 - gyk) * n;
+                        size_t i = (size_t)y * w + x;
+                        int qx[2] = {x - dx * n, x}, qy[2] = {y, y - dy * n};
+                        for (int k = 0; k < 2; k++) {
+                            if (qx[k] < 0 || qx[k] >= w || qy[k] < 0 || qy[k] >= h) continue;
+                            size_t j = (size_t)qy[k] * w + qx[k];
+                            if (cost[j] == EMPTY_COST) continue;
+                            int32_t c = cost_at(&V, x, y, field + 4 * j);
+                            if (c < cost[i]) { cost[i] = c; memcpy(field + 4 * i, field + 4 * j, 4 * sizeof(int16_t)); }
+                        }
+                    }
+            } else
             /* propagation: two synchronous half-steps over the grid colours */
             for (int colour = 0; colour < 2; colour++) {
                 memcpy(snap_f, field, np * 4 * sizeof(int16_t));
@@ -428,6 +592,25 @@ void sffo_match_views(const int8_t* f_ref, const int8_t* f_tmp, const int8_t* f_
                     }
             }
             /* random search after the iteration: every non-empty grid pixel */
+            if (prm->order_mode & SFFO_SEQUENTIAL_RNG) {
+                /* one sequential stream in raster order */
+                uint64_t st = seed ^ ((uint64_t)(s + 4 * mirror) << 40) ^ ((uint64_t)it << 48);
+                for (int y = 0; y < h; y += n)
+                    for (int x = 0; x < w; x += n) {
+                        size_t i = (size_t)y * w + x;
+                        if (cost[i] == EMPTY_COST) continue;
+                        uint64_t r0 = splitmix64(&st), r1 = splitmix64(&st);
+                        uint32_t r[4] = {(uint32_t)r0, (uint32_t)(r0 >> 32), (uint32_t)r1, (uint32_t)(r1 >> 32)};
+                        int32_t cu[4];
+                        for (int k = 0; k < 4; k++) cu[k] = field[4 * i + k] + sffo_rs_offset(r[k], n);
+                        if (cu[2] < 0) cu[2] = 0;
+                        if (cu[3] < 0) cu[3] = 0;
+                        int16_t cand[4] = {(int16_t)cu[0], (int16_t)cu[1], (int16_t)cu[2], (int16_t)cu[3]};
+                        int32_t c = cost_at(&V, x, y, cand);
+                        if (c < cost[i]) { cost[i] = c; memcpy(field + 4 * i, cand, sizeof cand); }
+                    }
+                continue;
+            }
             #pragma omp parallel for num_threads(g_threads) schedule(static)
             for (int y = 0; y < h; y += n)
                 for (int x = 0; x < w; x += n) {
