@@ -289,6 +289,22 @@ def bench_serving(sff, torch, dev, quads, params, tuning, max_requests=240):
     return out
 
 
+def combine_ranks(t_step: float, px_per_rank: int, world: int, device=None):
+    """Whole-job throughput of `world` replicas: every rank matched its own
+    quad; the job time is the slowest rank's (max over ranks), the pixels are
+    summed.  Returns (max step time, px/s)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([t_step, float(px_per_rank)], dtype=torch.float64, device=device)
+        tmax = t[:1].clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        px = t[1:].clone()
+        dist.all_reduce(px, op=dist.ReduceOp.SUM)
+        return float(tmax.item()), float(px.item()) / float(tmax.item())
+    return t_step, px_per_rank / t_step
+
+
 def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
@@ -403,13 +419,8 @@ def main():
     torch.cuda.synchronize(dev)
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_step = statistics.mean(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([t_step], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_step = float(t.item())
     px = q.width * q.height
-    value = px * world / t_step
+    t_step, value = combine_ranks(statistics.mean(step_ms) / 1e3, px, world, dev)
 
     # end to end through the public host API: pinned host images in, seeds out
     e2e_times = []
@@ -424,7 +435,7 @@ def main():
             if k >= args.warmup:
                 e2e_times.append(time.perf_counter() - t0)
     n_seeds = int(host_count.item())
-    e2e = {"value": px * world / statistics.mean(e2e_times), "unit": "px/s",
+    e2e = {"value": combine_ranks(statistics.mean(e2e_times), px, world, dev)[1], "unit": "px/s",
            "h2d_bytes_per_step": int(host_in.numel()), "d2h_bytes_per_step": int(m.seeds.numel() + 4)}
 
     # roofline of the dominant kernel (largest share of profiled time)
