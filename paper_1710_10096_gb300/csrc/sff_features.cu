@@ -1,15 +1,22 @@
 // Walsh-Hadamard patch features on the box-smoothed scale space
 // (Sec. 3.1, "Initialization" and "Multi-Scale Propagation").
 //
-// k_smooth:   S_s for every scale, one thread per pixel, RGB packed in one
-//             uint32 per pixel (workspace [S][H][W]).
-// k_features: one thread per pixel and scale; the 8x8 patch of each channel
-//             is transformed separably with 8-point fast Walsh-Hadamard
-//             butterflies (natural order), R and G packed into one int32 as
-//             R + 65536 G (every intermediate stays below 2^31 in magnitude,
-//             so packed adds and subtracts are exact).  The 16 kept
-//             coefficients are read out through the sequency->natural index
-//             map, quantised and written as one 48-byte record plus its norm.
+// k_smooth:   a 64x16 tile of output pixels per CTA; the tile's input region
+//             (with the largest box's margin, edges replicated) is turned
+//             into a summed-area table in shared memory, so every box sum of
+//             every scale costs four lookups per channel.  Output per scale:
+//             R and G packed as R + 65536 G (one int32 plane) and B (a
+//             second plane), the form the transform consumes.
+// k_features: one thread per pair of pixels (x, y), (x, y + n) of scale s:
+//             their 8x8 patches share 7 of 8 rows, so 9 row transforms (fast
+//             8-point Walsh-Hadamard butterflies, R and G packed in one
+//             int32; every intermediate stays below 2^31 in magnitude, so
+//             packed adds and subtracts are exact) serve both.  Each row
+//             transform is folded into the 16 kept coefficients of both
+//             pixels with compile-time signs of the sequency-ordered Walsh
+//             rows.  The coefficients are quantised, packed and written as
+//             one 48-byte record per pixel; the norm is a dp4a of the packed
+//             bytes with themselves.
 #include <mutex>
 
 #include "sff_internal.cuh"
@@ -27,37 +34,81 @@ __host__ __device__ constexpr int seq_to_nat(int k) {
 __host__ __device__ constexpr int diag_of(int m) { return m < 2 ? 1 : m < 5 ? 2 : m < 9 ? 3 : m < 14 ? 4 : 5; }
 __host__ __device__ constexpr int order_ky(int m) { return m - (diag_of(m) * (diag_of(m) + 1) / 2 - 1); }
 __host__ __device__ constexpr int order_kx(int m) { return diag_of(m) - order_ky(m); }
+// Entry (k, i) of the sequency-ordered Walsh matrix: natural Hadamard row
+// seq_to_nat(k), i.e. (-1)^popcount(seq_to_nat(k) & i).
+__host__ __device__ constexpr int walsh(int k, int i) {
+    return (((seq_to_nat(k) & i) & 1) ^ (((seq_to_nat(k) & i) >> 1) & 1) ^ (((seq_to_nat(k) & i) >> 2) & 1)) ? -1 : 1;
+}
 static_assert(seq_to_nat(1) == 4 && seq_to_nat(2) == 6 && seq_to_nat(5) == 7 && seq_to_nat(7) == 1, "walsh map");
 static_assert(order_ky(0) == 0 && order_kx(0) == 1 && order_ky(4) == 2 && order_kx(4) == 0, "order");
 static_assert(order_ky(13) == 4 && order_kx(13) == 0 && order_ky(15) == 1 && order_kx(15) == 4, "order");
+static_assert(walsh(1, 0) == 1 && walsh(1, 4) == -1 && walsh(2, 2) == -1 && walsh(2, 6) == 1, "walsh rows");
 
-__global__ void k_smooth(const __grid_constant__ ImageJobs J, int S) {
+constexpr int kSmX = 64, kSmY = 16;  // output tile of k_smooth
+constexpr int kMargin = 4;           // half of the largest box (n = 8)
+constexpr int kRegX = kSmX + 2 * kMargin, kRegY = kSmY + 2 * kMargin;
+
+__global__ void __launch_bounds__(256) k_smooth(const __grid_constant__ ImageJobs J, int S) {
+    __shared__ int sat[3][kRegY + 1][kRegX + 1];  // summed-area table per channel, zero first row/column
     const ImageJob& job = J.im[blockIdx.z];
-    const uint8_t* __restrict__ rgb = job.rgb;
-    const int pitch = job.pitch, w = job.w, h = job.h;
-    uint32_t* __restrict__ out = job.sm;
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y;
-    if (x >= w || y >= h) return;
-    {
-        const uint8_t* p = rgb + (size_t)y * pitch + 3 * x;
-        out[(size_t)y * w + x] = (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16);
-    }
-    for (int s = 1; s < S; ++s) {
-        int n = 1 << s;
-        uint32_t sr = 0, sg = 0, sb = 0;
-        for (int j = -n / 2; j < n / 2; ++j) {
-            const uint8_t* row = rgb + (size_t)clampi(y + j, 0, h - 1) * pitch;
-            for (int i = -n / 2; i < n / 2; ++i) {
-                const uint8_t* p = row + 3 * clampi(x + i, 0, w - 1);
-                sr += p[0];
-                sg += p[1];
-                sb += p[2];
-            }
+    const int w = job.w, h = job.h, pitch = job.pitch;
+    const int x0 = blockIdx.x * kSmX, y0 = blockIdx.y * kSmY;
+    if (x0 >= w || y0 >= h) return;
+    for (int k = threadIdx.x; k < (kRegY + 1) * (kRegX + 1); k += blockDim.x) {
+        const int ry = k / (kRegX + 1), rx = k % (kRegX + 1);
+        if (ry == 0 || rx == 0) {
+            sat[0][ry][rx] = sat[1][ry][rx] = sat[2][ry][rx] = 0;
+            continue;
         }
-        uint32_t half = (uint32_t)(n * n / 2);
-        uint32_t r = (sr + half) >> (2 * s), g = (sg + half) >> (2 * s), b = (sb + half) >> (2 * s);
-        out[((size_t)s * h + y) * w + x] = r | (g << 8) | (b << 16);
+        const int x = clampi(x0 - kMargin + rx - 1, 0, w - 1), y = clampi(y0 - kMargin + ry - 1, 0, h - 1);
+        const uint8_t* p = job.rgb + (size_t)y * pitch + 3 * x;
+        sat[0][ry][rx] = p[0];
+        sat[1][ry][rx] = p[1];
+        sat[2][ry][rx] = p[2];
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 3 * kRegY; k += blockDim.x) {  // prefix along rows
+        int* row = &sat[k / kRegY][1 + k % kRegY][0];
+        for (int x = 1; x <= kRegX; ++x) row[x] += row[x - 1];
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 3 * kRegX; k += blockDim.x) {  // prefix along columns
+        const int c = k / kRegX, x = 1 + k % kRegX;
+        for (int y = 1; y <= kRegY; ++y) sat[c][y][x] += sat[c][y - 1][x];
+    }
+    __syncthreads();
+    const size_t np = (size_t)w * h;
+    int* rg_out = reinterpret_cast<int*>(job.sm);
+    int* b_out = rg_out + (size_t)S * np;
+    for (int k = threadIdx.x; k < kSmX * kSmY; k += blockDim.x) {
+        const int lx = k % kSmX, ly = k / kSmX;
+        const int x = x0 + lx, y = y0 + ly;
+        if (x >= w || y >= h) continue;
+        const size_t i = (size_t)y * w + x;
+        // scale 0: the pixel itself (region cell (ly + margin, lx + margin))
+        {
+            const int cy = ly + kMargin + 1, cx = lx + kMargin + 1;
+            int v[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                v[c] = sat[c][cy][cx] - sat[c][cy - 1][cx] - sat[c][cy][cx - 1] + sat[c][cy - 1][cx - 1];
+            rg_out[i] = v[0] + 65536 * v[1];
+            b_out[i] = v[2];
+        }
+        for (int s = 1; s < S; ++s) {
+            const int n = 1 << s;
+            // box rows/columns -n/2 .. n/2-1 around the pixel, in region cells (+1 for the zero border)
+            const int ya = ly + kMargin - n / 2, yb = ly + kMargin + n / 2;  // rows [ya, yb) of the region
+            const int xa = lx + kMargin - n / 2, xb = lx + kMargin + n / 2;
+            int v[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int sum = sat[c][yb][xb] - sat[c][ya][xb] - sat[c][yb][xa] + sat[c][ya][xa];
+                v[c] = (sum + n * n / 2) >> (2 * s);
+            }
+            rg_out[(size_t)s * np + i] = v[0] + 65536 * v[1];
+            b_out[(size_t)s * np + i] = v[2];
+        }
     }
 }
 
@@ -75,92 +126,118 @@ __device__ __forceinline__ void fwht8(int (&a)[8]) {
 
 __device__ __forceinline__ int lo16(int x) { return (x << 16) >> 16; }
 
-__global__ void k_features(const __grid_constant__ ImageJobs J, int s, int S, int qshift) {
-    const ImageJob& job = J.im[blockIdx.z];
-    const int w = job.w, h = job.h;
-    const size_t np = (size_t)w * h;
-    const uint32_t* __restrict__ sm = job.sm + s * np;
-    uint8_t* __restrict__ out = job.pyr + s * np * kFeat;
-    int* __restrict__ norm_out = reinterpret_cast<int*>(job.pyr + (size_t)S * np * kFeat) + s * np;
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y;
-    if (x >= w || y >= h) return;
-    const int n = 1 << s;
-    int xs[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) xs[j] = clampi(x + n * (j - 3), 0, w - 1);
+__device__ __forceinline__ int sat8(int v) { return v < -128 ? -128 : (v > 127 ? 127 : v); }
 
-    // row transforms: keep the natural columns of sequency kx = 0..5
-    int rg[8][6], bb[8][6];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const uint32_t* row = sm + (size_t)clampi(y + n * (i - 3), 0, h - 1) * w;
-        int a[8], b[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            uint32_t px = __ldg(row + xs[j]);
-            a[j] = (int)(px & 0xffu) + 65536 * (int)((px >> 8) & 0xffu);
-            b[j] = (int)((px >> 16) & 0xffu);
-        }
-        fwht8(a);
-        fwht8(b);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-            rg[i][k] = a[seq_to_nat(k)];
-            bb[i][k] = b[seq_to_nat(k)];
-        }
-    }
-    // column transforms
-    int crg[8][6], cb[8][6];
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-        int a[8], b[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            a[i] = rg[i][k];
-            b[i] = bb[i][k];
-        }
-        fwht8(a);
-        fwht8(b);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            crg[i][k] = a[i];
-            cb[i][k] = b[i];
-        }
-    }
-    // read out, quantise, pack
-    int8_t f[48];
-    int norm = 0;
+__device__ __forceinline__ int pack4(int a, int b, int c, int d) {
+    return (int)((uint32_t)(a & 0xff) | ((uint32_t)(b & 0xff) << 8) | ((uint32_t)(c & 0xff) << 16) |
+                 ((uint32_t)(d & 0xff) << 24));
+}
+
+// Accumulate row transform (rg[kx], b[kx], kx = 0..5 in sequency order) of
+// patch row i into the 16 kept coefficients.
+template <int I>
+__device__ __forceinline__ void fold_row(const int (&rg)[6], const int (&bb)[6], int (&arg)[16], int (&ab)[16]) {
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
-        int X = crg[seq_to_nat(order_ky(m))][order_kx(m)];
-        int r = lo16(X);
-        int g = (X - r) >> 16;
-        int b = cb[seq_to_nat(order_ky(m))][order_kx(m)];
-        int q[3] = {r, g, b};
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            int v = clampi(q[c] >> qshift, -128, 127);
-            f[c * 16 + m] = (int8_t)v;
-            norm += v * v;
+        if (walsh(order_ky(m), I) > 0) {
+            arg[m] += rg[order_kx(m)];
+            ab[m] += bb[order_kx(m)];
+        } else {
+            arg[m] -= rg[order_kx(m)];
+            ab[m] -= bb[order_kx(m)];
         }
+    }
+}
+
+__device__ __forceinline__ void write_record(const int (&arg)[16], const int (&ab)[16], int qshift, uint8_t* rec,
+                                             int* norm) {
+    int q[3][16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) {
+        const int r = lo16(arg[m]);
+        const int g = (arg[m] - r) >> 16;
+        q[0][m] = sat8(r >> qshift);
+        q[1][m] = sat8(g >> qshift);
+        q[2][m] = sat8(ab[m] >> qshift);
     }
     int words[12];
 #pragma unroll
-    for (int k = 0; k < 12; ++k)
-        words[k] = (int)((uint32_t)(uint8_t)f[4 * k] | ((uint32_t)(uint8_t)f[4 * k + 1] << 8) |
-                         ((uint32_t)(uint8_t)f[4 * k + 2] << 16) | ((uint32_t)(uint8_t)f[4 * k + 3] << 24));
-    const size_t i = (size_t)y * w + x;
-    int4* dst = reinterpret_cast<int4*>(out + i * kFeat);
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) words[4 * c + k] = pack4(q[c][4 * k], q[c][4 * k + 1], q[c][4 * k + 2], q[c][4 * k + 3]);
+    int nn = 0;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) nn = __dp4a(words[k], words[k], nn);
+    int4* dst = reinterpret_cast<int4*>(rec);
 #pragma unroll
     for (int k = 0; k < 3; ++k) dst[k] = make_int4(words[4 * k], words[4 * k + 1], words[4 * k + 2], words[4 * k + 3]);
-    norm_out[i] = norm;
+    *norm = nn;
+}
+
+__global__ void __launch_bounds__(128) k_features(const __grid_constant__ ImageJobs J, int s, int S, int qshift) {
+    const ImageJob& job = J.im[blockIdx.z];
+    const int w = job.w, h = job.h;
+    const int n = 1 << s;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    // pair row p covers (y, y + n) with y = (p / n) * 2n + p % n
+    const int p = blockIdx.y;
+    const int y = (p / n) * 2 * n + p % n;
+    if (x >= w || y >= h) return;
+    const bool second = y + n < h;
+    const size_t np = (size_t)w * h;
+    const int* rgp = reinterpret_cast<const int*>(job.sm) + (size_t)s * np;
+    const int* bp = reinterpret_cast<const int*>(job.sm) + (size_t)S * np + (size_t)s * np;
+    int xs[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) xs[j] = clampi(x + n * (j - 3), 0, w - 1);
+    int a_rg[16], a_b[16], b_rg[16], b_b[16];
+#pragma unroll
+    for (int m = 0; m < 16; ++m) a_rg[m] = a_b[m] = b_rg[m] = b_b[m] = 0;
+    // rows y + n (k - 3), k = 0..8: pixel (x, y) uses k = 0..7 as patch row k,
+    // pixel (x, y + n) uses k = 1..8 as patch row k - 1
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const size_t row = (size_t)clampi(y + n * (k - 3), 0, h - 1) * w;
+        int a[8], b[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            a[j] = __ldg(rgp + row + xs[j]);
+            b[j] = __ldg(bp + row + xs[j]);
+        }
+        fwht8(a);
+        fwht8(b);
+        int rg[6], bb[6];
+#pragma unroll
+        for (int kx = 0; kx < 6; ++kx) {
+            rg[kx] = a[seq_to_nat(kx)];
+            bb[kx] = b[seq_to_nat(kx)];
+        }
+        // compile-time patch row of each pixel
+        switch (k) {
+            case 0: fold_row<0>(rg, bb, a_rg, a_b); break;
+            case 1: fold_row<1>(rg, bb, a_rg, a_b); fold_row<0>(rg, bb, b_rg, b_b); break;
+            case 2: fold_row<2>(rg, bb, a_rg, a_b); fold_row<1>(rg, bb, b_rg, b_b); break;
+            case 3: fold_row<3>(rg, bb, a_rg, a_b); fold_row<2>(rg, bb, b_rg, b_b); break;
+            case 4: fold_row<4>(rg, bb, a_rg, a_b); fold_row<3>(rg, bb, b_rg, b_b); break;
+            case 5: fold_row<5>(rg, bb, a_rg, a_b); fold_row<4>(rg, bb, b_rg, b_b); break;
+            case 6: fold_row<6>(rg, bb, a_rg, a_b); fold_row<5>(rg, bb, b_rg, b_b); break;
+            case 7: fold_row<7>(rg, bb, a_rg, a_b); fold_row<6>(rg, bb, b_rg, b_b); break;
+            default: fold_row<7>(rg, bb, b_rg, b_b); break;
+        }
+    }
+    uint8_t* feat = job.pyr + (size_t)s * np * kFeat;
+    int* norms = reinterpret_cast<int*>(job.pyr + (size_t)S * np * kFeat) + (size_t)s * np;
+    const size_t i = (size_t)y * w + x;
+    write_record(a_rg, a_b, qshift, feat + i * kFeat, norms + i);
+    if (second) write_record(b_rg, b_b, qshift, feat + (i + (size_t)n * w) * kFeat, norms + i + (size_t)n * w);
 }
 
 }  // namespace
 
+// Scratch of one image: the smoothed scale space as two int32 planes per
+// scale (R + 65536 G, and B).
 size_t features_ws_bytes(int w, int h, const sff_params& p) {
-    return align256((size_t)p.num_scales * w * h * sizeof(uint32_t));
+    return align256((size_t)2 * p.num_scales * w * h * sizeof(int));
 }
 
 int run_features(const ImageJob* jobs, int n, const sff_params& P, cudaStream_t st) {
@@ -174,9 +251,14 @@ int run_features(const ImageJob* jobs, int n, const sff_params& P, cudaStream_t 
         mw = mw > jobs[k].w ? mw : jobs[k].w;
         mh = mh > jobs[k].h ? mh : jobs[k].h;
     }
-    dim3 blk(128), grd((mw + 127) / 128, mh, n);
-    SFF_LAUNCH(k_smooth, grd, blk, 0, st, J, P.num_scales);
-    for (int s = 0; s < P.num_scales; ++s) SFF_LAUNCH(k_features, grd, blk, 0, st, J, s, P.num_scales, P.quant_shift);
+    dim3 gs((mw + kSmX - 1) / kSmX, (mh + kSmY - 1) / kSmY, n);
+    SFF_LAUNCH(k_smooth, gs, 256, 0, st, J, P.num_scales);
+    for (int s = 0; s < P.num_scales; ++s) {
+        const int nn = 1 << s;
+        // pair rows: ceil(H / 2n) pairs per residue class of rows mod n
+        dim3 gf((mw + 127) / 128, ((mh + 2 * nn - 1) / (2 * nn)) * nn, n);
+        SFF_LAUNCH(k_features, gf, 128, 0, st, J, s, P.num_scales, P.quant_shift);
+    }
     return launch_status();
 }
 
