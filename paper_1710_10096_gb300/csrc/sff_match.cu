@@ -10,11 +10,11 @@
 //
 // k_gather_grid:  packs the coarsest-grid records of the reference and
 //                 temporal images into contiguous arrays.
-// k_knn:          temporal K-NN, all-pairs over the coarsest grid, one warp
-//                 per query; candidate tiles streamed into shared memory by
-//                 TMA bulk copies on mbarriers (double-buffered) and shared
-//                 by the 8 queries of a CTA; a sorted top-8 of (distance,
-//                 grid index) spread over lanes 0-7.
+// k_knn:          temporal K-NN, all-pairs over the coarsest grid on the
+//                 tensor cores (mma.sync bf16, exact for int8 features);
+//                 candidate tiles streamed into shared memory by TMA bulk
+//                 copies on mbarriers (double-buffered); per-thread sorted
+//                 top-8 lists merged per query at the end.
 // k_init_select:  one warp per query: takes the temporal top-K, finds
 //                 the nearest epipolar stereo / cross points and keeps the
 //                 best combination.  The cost is the sum of the three
@@ -44,9 +44,11 @@ namespace {
 
 std::mutex g_fields_mu;  // guards the host staging of the Fields parameter
 
-constexpr int kKnnThreads = 256;
+constexpr int kKnnThreads = 128;
 constexpr int kKnnWarps = kKnnThreads / 32;
-constexpr int kKnnTile = 256;  // candidates per shared-memory tile (12 KB of records)
+constexpr int kKnnQueries = 16 * kKnnWarps;  // 16 queries per warp (one mma row block)
+constexpr int kKnnTile = 128;                // candidates per shared-memory tile (12 KB of bf16 records)
+constexpr int kRecBf16 = 96;                 // bytes of a compacted record: 48 bf16
 
 // One field: its views and grid at the current scale, its state and, for
 // the double-buffered iteration kernel, the buffer it writes; plus its
@@ -101,9 +103,10 @@ __device__ __forceinline__ int dot12(const int (&a)[12], const int4& p0, const i
 }
 
 // Copies the coarsest-grid records of the reference (role 0) and temporal
-// (role 1) images of each field into contiguous arrays, so that the K-NN
-// search streams them with bulk copies.  Layout: [field][role][gq + pad]
-// records of 48 bytes and int32 norms.
+// (role 1) images of each field into contiguous arrays for the tensor-core
+// K-NN search: 48 features as bf16 (int8 values are exact in bf16, so are
+// their products and the 48-term sums in fp32) and the int32 norms.
+// Layout per field: [2 roles][gq_pad] records of 96 bytes / norms.
 __global__ void k_gather_grid(const __grid_constant__ Fields F, int n) {
     const Field& A = pick(F);
     const int role = blockIdx.y;
@@ -113,11 +116,23 @@ __global__ void k_gather_grid(const __grid_constant__ Fields F, int n) {
     if (c >= A.gq) return;
     const size_t i = pix(A.V.w, (c % A.gw) * n, (c / A.gw) * n);
     const size_t slot = (size_t)role * A.gq_pad + c;
-    if (part < 3)
-        reinterpret_cast<int4*>(A.cf + slot * kFeat)[part] =
-            __ldg(reinterpret_cast<const int4*>(P.f + i * kFeat) + part);
-    else
+    if (part < 3) {
+        const int4 v = __ldg(reinterpret_cast<const int4*>(P.f + i * kFeat) + part);
+        const int words[4] = {v.x, v.y, v.z, v.w};
+        uint32_t out[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {  // two int8 -> two bf16 per 32-bit word
+            const int w = words[k / 2];
+            const int lo = (int)(int8_t)((w >> (16 * (k & 1))) & 0xff);
+            const int hi = (int)(int8_t)((w >> (16 * (k & 1) + 8)) & 0xff);
+            out[k] = (__float_as_uint((float)lo) >> 16) | (__float_as_uint((float)hi) & 0xffff0000u);
+        }
+        uint4* dst = reinterpret_cast<uint4*>(A.cf + slot * kRecBf16) + 2 * part;
+        dst[0] = make_uint4(out[0], out[1], out[2], out[3]);
+        dst[1] = make_uint4(out[4], out[5], out[6], out[7]);
+    } else {
         A.cn[slot] = __ldg(P.nrm + i);
+    }
 }
 
 // TMA (bulk-copy) helpers: 1-D global -> shared copies completing on an
@@ -163,46 +178,88 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
 
 __device__ unsigned int g_wait_timeouts;  // bounded waits that gave up (read by sff_device_timeouts)
 
-// Temporal K-NN of one query per warp.  The candidate records stream through
-// two shared-memory tiles filled by bulk copies (thread 0 issues tile t+1
-// while tile t is scored).  Lane l scores candidate l of each batch of 32; a
-// ballot against the current 8th-best (distance, index) keeps the rare
-// candidates that enter the list, and each of them is inserted into the
-// sorted top-8 held by lanes 0-7 with warp-uniform shuffles.
+__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Sorted insertion of (nd, ni) into an 8-entry list (d ascending, index
+// ascending on ties) that is known to take it.
+__device__ __forceinline__ void list8_insert(int (&d)[8], int (&id)[8], int nd, int ni) {
+#pragma unroll
+    for (int k = 7; k >= 0; --k) {
+        const bool lt_prev = k > 0 && less_di(nd, ni, d[k > 0 ? k - 1 : 0], id[k > 0 ? k - 1 : 0]);
+        if (lt_prev) {
+            d[k] = d[k - 1];
+            id[k] = id[k - 1];
+        } else if (less_di(nd, ni, d[k], id[k])) {
+            d[k] = nd;
+            id[k] = ni;
+        }
+    }
+}
+
+// Temporal K-NN on the tensor cores.  A warp takes 16 queries; the
+// candidate records stream through two shared-memory tiles filled by bulk
+// copies (thread 0 issues tile t+1 while tile t is scored).  For every group
+// of 8 candidates three mma.sync m16n8k16 (bf16 in, fp32 accumulate: exact
+// for these integers) give the 16 x 8 dot products; each thread turns its 4
+// into distances |q|^2 + |c|^2 - 2 q.c and keeps, for each of its 2 query
+// rows, a sorted top-8 of the candidates it sees (every 4th pair of
+// columns).  Candidates are visited in increasing index, so a strictly
+// smaller distance is the only way in, exactly as in the (distance, index)
+// order.  At the end the 4 partial lists of a query are merged through
+// shared memory.
 __global__ void __launch_bounds__(kKnnThreads) k_knn(const __grid_constant__ Fields F) {
-    __shared__ __align__(128) int4 tile[2][kKnnTile][3];
+    __shared__ __align__(128) uint4 tile[2][kKnnTile * kRecBf16 / 16];
     __shared__ __align__(16) int tnorm[2][kKnnTile];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ int s_fail;
+    __shared__ int2 merge[kKnnWarps * 16][4][8];
     const Field& A = pick(F);
     const int gq = A.gq;
-    if ((int)blockIdx.x * kKnnWarps >= gq) return;  // CTA beyond this field's queries
-    const int lane = threadIdx.x & 31;
-    const int qi = blockIdx.x * kKnnWarps + (threadIdx.x >> 5);
-    const bool active = qi < gq;  // warp-uniform
-    const uint8_t* qf = A.cf;
-    const uint8_t* tf = A.cf + (size_t)A.gq_pad * kFeat;
+    const int q0 = blockIdx.x * kKnnQueries;
+    if (q0 >= gq) return;  // CTA beyond this field's queries
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, c = lane & 3;
+    const uint8_t* qrec = A.cf;                                   // role 0: queries
+    const uint8_t* crec = A.cf + (size_t)A.gq_pad * kRecBf16;     // role 1: candidates
     const int* qn = A.cn;
-    const int* tn = A.cn + A.gq_pad;
-    RefFeat r;
-    if (active) {
-        const int4* p = reinterpret_cast<const int4*>(qf + (size_t)qi * kFeat);
-        const int4 q0 = __ldg(p), q1 = __ldg(p + 1), q2 = __ldg(p + 2);
-        r.a[0] = q0.x; r.a[1] = q0.y; r.a[2] = q0.z; r.a[3] = q0.w;
-        r.a[4] = q1.x; r.a[5] = q1.y; r.a[6] = q1.z; r.a[7] = q1.w;
-        r.a[8] = q2.x; r.a[9] = q2.y; r.a[10] = q2.z; r.a[11] = q2.w;
-        r.n = __ldg(qn + qi);
+    const int* cnm = A.cn + A.gq_pad;
+    // A fragments of this warp's 16 queries (rows g and g + 8), 3 k-steps
+    const int qa = min(q0 + warp * 16 + g, gq - 1), qb = min(q0 + warp * 16 + g + 8, gq - 1);
+    uint32_t af[3][4];
+#pragma unroll
+    for (int ks = 0; ks < 3; ++ks) {
+        const uint32_t* ra = reinterpret_cast<const uint32_t*>(qrec + (size_t)qa * kRecBf16) + ks * 8;
+        const uint32_t* rb = reinterpret_cast<const uint32_t*>(qrec + (size_t)qb * kRecBf16) + ks * 8;
+        af[ks][0] = __ldg(ra + c);
+        af[ks][1] = __ldg(rb + c);
+        af[ks][2] = __ldg(ra + c + 4);
+        af[ks][3] = __ldg(rb + c + 4);
     }
+    const int na = __ldg(qn + qa), nb = __ldg(qn + qb);
+    int ld[2][8], li[2][8];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            ld[r][k] = 0x7fffffff;
+            li[r][k] = 0x7fffffff;
+        }
     const int ntiles = (gq + kKnnTile - 1) / kKnnTile;
-    // copy sizes: whole records, rounded up to 4 records (16-byte multiples);
-    // the arrays carry that padding
+    // copy sizes: whole records, rounded up to 4 records (16-byte multiples of
+    // the norms); the arrays carry that padding
     auto issue = [&](int t) {
         const int base = t * kKnnTile;
         const int cnt4 = (min(kKnnTile, gq - base) + 3) & ~3;
-        const unsigned fb = (unsigned)cnt4 * kFeat, nb = (unsigned)cnt4 * 4;
-        mbar_expect_tx(&bar[t & 1], fb + nb);
-        bulk_copy_g2s(&tile[t & 1][0][0], tf + (size_t)base * kFeat, fb, &bar[t & 1]);
-        bulk_copy_g2s(&tnorm[t & 1][0], tn + base, nb, &bar[t & 1]);
+        const unsigned fb = (unsigned)cnt4 * kRecBf16, nbytes = (unsigned)cnt4 * 4;
+        mbar_expect_tx(&bar[t & 1], fb + nbytes);
+        bulk_copy_g2s(&tile[t & 1][0], crec + (size_t)base * kRecBf16, fb, &bar[t & 1]);
+        bulk_copy_g2s(&tnorm[t & 1][0], cnm + base, nbytes, &bar[t & 1]);
     };
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
@@ -212,8 +269,6 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(const __grid_constant__ Fie
     }
     __syncthreads();
     if (threadIdx.x == 0) issue(0);
-    int ld = 0x7fffffff, li = 0x7fffffff;  // entry `lane` of the sorted top-8 (lanes 0-7)
-    int thr_d = 0x7fffffff, thr_i = 0x7fffffff;
     for (int t = 0; t < ntiles; ++t) {
         const int buf = t & 1;
         // the other buffer was released by the __syncthreads that ended tile t-1
@@ -229,38 +284,52 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(const __grid_constant__ Fie
         }
         const int base = t * kKnnTile;
         const int cnt = min(kKnnTile, gq - base);
-        if (active) {
-            for (int b = 0; b < cnt; b += 32) {
-                const int k = b + lane;
-                int d = 0x7fffffff;
-                if (k < cnt)
-                    d = r.n + tnorm[buf][k] - 2 * dot12(r.a, tile[buf][k][0], tile[buf][k][1], tile[buf][k][2]);
-                const int idx = base + k;
-                unsigned enter = __ballot_sync(0xffffffffu, k < cnt && less_di(d, idx, thr_d, thr_i));
-                while (enter) {
-                    const int src = __ffs(enter) - 1;
-                    enter &= enter - 1;
-                    const int nd = __shfl_sync(0xffffffffu, d, src), ni = __shfl_sync(0xffffffffu, idx, src);
-                    if (!less_di(nd, ni, thr_d, thr_i)) continue;  // the threshold moved meanwhile
-                    const int pos = __popc(__ballot_sync(0xffffffffu, lane < 8 && !less_di(nd, ni, ld, li)));
-                    const int pd = __shfl_up_sync(0xffffffffu, ld, 1), pi = __shfl_up_sync(0xffffffffu, li, 1);
-                    if (lane < 8) {
-                        if (lane > pos) {
-                            ld = pd;
-                            li = pi;
-                        } else if (lane == pos) {
-                            ld = nd;
-                            li = ni;
-                        }
-                    }
-                    thr_d = __shfl_sync(0xffffffffu, ld, 7);
-                    thr_i = __shfl_sync(0xffffffffu, li, 7);
-                }
+        const uint32_t* tw = reinterpret_cast<const uint32_t*>(&tile[buf][0]);
+        for (int grp8 = 0; grp8 < cnt; grp8 += 8) {
+            // B fragment: candidate grp8 + g, k pairs (2c, 2c+1) and (2c+8, 2c+9)
+            const uint32_t* cb = tw + (size_t)(grp8 + g) * (kRecBf16 / 4);
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int ks = 0; ks < 3; ++ks) mma_bf16_16816(acc, af[ks], cb[ks * 8 + c], cb[ks * 8 + c + 4]);
+            // this thread's entries: rows g, g+8; candidates grp8 + 2c, grp8 + 2c + 1
+            const int j0 = grp8 + 2 * c, j1 = j0 + 1;
+            const int n0 = tnorm[buf][j0], n1 = tnorm[buf][j1];
+            const int dv[4] = {na + n0 - 2 * __float2int_rn(acc[0]), na + n1 - 2 * __float2int_rn(acc[1]),
+                               nb + n0 - 2 * __float2int_rn(acc[2]), nb + n1 - 2 * __float2int_rn(acc[3])};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int j = e & 1 ? j1 : j0;
+                const int r = e >> 1;
+                if (j < cnt && dv[e] < ld[r][7]) list8_insert(ld[r], li[r], dv[e], base + j);
             }
         }
         __syncthreads();
     }
-    if (active && lane < 8) A.best8[(size_t)qi * 8 + lane] = make_int2(ld, li);
+    // merge the 4 partial lists of each query (threads c = 0..3 of its row)
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) merge[warp * 16 + g + 8 * r][c][k] = make_int2(ld[r][k], li[r][k]);
+    __syncthreads();
+    if (threadIdx.x < kKnnQueries) {
+        const int qi = q0 + threadIdx.x;
+        if (qi < gq) {
+            int md[8], mi[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                md[k] = 0x7fffffff;
+                mi[k] = 0x7fffffff;
+            }
+            for (int cc = 0; cc < 4; ++cc)
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int2 e = merge[threadIdx.x][cc][k];
+                    if (less_di(e.x, e.y, md[7], mi[7])) list8_insert(md, mi, e.x, e.y);
+                }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) A.best8[(size_t)qi * 8 + k] = make_int2(md[k], mi[k]);
+        }
+    }
 }
 
 // Nearest grid point of row y by (distance, x), constrained by sigma, found by
@@ -707,7 +776,7 @@ FieldScratch field_scratch(int w, int h, const sff_params& p) {
     FieldScratch f;
     f.best8 = 0;
     f.cf = f.best8 + align256((size_t)gq * 8 * sizeof(int2));
-    f.cn = f.cf + align256((size_t)2 * gp * kFeat);
+    f.cn = f.cf + align256((size_t)2 * gp * kRecBf16);
     f.field = f.cn + align256((size_t)2 * gp * sizeof(int));
     f.cost = f.field + align256((size_t)w * h * 8);
     f.total = f.cost + align256((size_t)w * h * 4);
@@ -771,7 +840,7 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
         if (s == S - 1) {
             dim3 g0((mgq * 4 + 255) / 256, 2, nf);
             SFF_LAUNCH(k_gather_grid, g0, 256, 0, st, F, n);
-            dim3 g1((mgq + kKnnWarps - 1) / kKnnWarps, 1, nf);
+            dim3 g1((mgq + kKnnQueries - 1) / kKnnQueries, 1, nf);
             SFF_LAUNCH(k_knn, g1, kKnnThreads, 0, st, F);
             dim3 g2((mgq + 7) / 8, 1, nf);
             SFF_LAUNCH(k_init_select, g2, 256, 0, st, F, n, P.knn_temporal);
