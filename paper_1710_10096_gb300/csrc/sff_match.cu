@@ -47,8 +47,9 @@ std::mutex g_fields_mu;  // guards the host staging of the Fields parameter
 constexpr int kKnnThreads = 128;
 constexpr int kKnnWarps = kKnnThreads / 32;
 constexpr int kKnnQueries = 16 * kKnnWarps;  // 16 queries per warp (one mma row block)
-constexpr int kKnnTile = 128;                // candidates per shared-memory tile (12 KB of bf16 records)
+constexpr int kKnnTile = 64;                 // candidates per shared-memory tile (6 KB of bf16 records)
 constexpr int kRecBf16 = 96;                 // bytes of a compacted record: 48 bf16
+constexpr int kKnnSplits = 8;                // candidate ranges per query block (merged by k_init_select)
 
 // One field: its views and grid at the current scale, its state and, for
 // the double-buffered iteration kernel, the buffer it writes; plus its
@@ -202,31 +203,35 @@ __device__ __forceinline__ void list8_insert(int (&d)[8], int (&id)[8], int nd, 
     }
 }
 
-// Temporal K-NN on the tensor cores.  A warp takes 16 queries; the
-// candidate records stream through two shared-memory tiles filled by bulk
-// copies (thread 0 issues tile t+1 while tile t is scored).  For every group
-// of 8 candidates three mma.sync m16n8k16 (bf16 in, fp32 accumulate: exact
-// for these integers) give the 16 x 8 dot products; each thread turns its 4
-// into distances |q|^2 + |c|^2 - 2 q.c and keeps, for each of its 2 query
-// rows, a sorted top-8 of the candidates it sees (every 4th pair of
-// columns).  Candidates are visited in increasing index, so a strictly
-// smaller distance is the only way in, exactly as in the (distance, index)
-// order.  At the end the 4 partial lists of a query are merged through
-// shared memory.
+// Temporal K-NN: tensor-core distances, warp-uniform selection.
+// A CTA takes 64 queries (16 per warp) and one of kKnnSplits ranges of the
+// candidates (blockIdx.y).  Candidate records stream through two
+// shared-memory tiles filled by bulk copies (thread 0 issues tile t+1 while
+// tile t is scored).  Per tile each warp computes its 16 x 128 dot products
+// with mma.sync m16n8k16 (bf16 in, fp32 accumulate: exact for these
+// integers) into a shared-memory block of distances |q|^2 + |c|^2 - 2 q.c.
+// Selection then reads that block one query at a time: four ballots against
+// the query's current 8th-best distance; the rare candidates that enter are
+// inserted into the query's sorted top-8, held by lanes 8(q%4)..8(q%4)+7 in
+// register slot q/4.  Candidates are visited in increasing index, so a
+// strictly smaller distance is the only way in, exactly as in the (distance,
+// index) order.  The partial top-8 of each range is merged by k_init_select.
 __global__ void __launch_bounds__(kKnnThreads) k_knn(const __grid_constant__ Fields F) {
     __shared__ __align__(128) uint4 tile[2][kKnnTile * kRecBf16 / 16];
     __shared__ __align__(16) int tnorm[2][kKnnTile];
+    __shared__ __align__(16) int sdist[kKnnWarps][16][kKnnTile + 4];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ int s_fail;
-    __shared__ int2 merge[kKnnWarps * 16][4][8];
     const Field& A = pick(F);
     const int gq = A.gq;
     const int q0 = blockIdx.x * kKnnQueries;
+    const int per = (((gq + kKnnSplits - 1) / kKnnSplits) + 3) & ~3;  // multiple of 4: aligned bulk copies
+    const int c0 = blockIdx.y * per, c1 = min(gq, c0 + per);
     if (q0 >= gq) return;  // CTA beyond this field's queries
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, c = lane & 3;
-    const uint8_t* qrec = A.cf;                                   // role 0: queries
-    const uint8_t* crec = A.cf + (size_t)A.gq_pad * kRecBf16;     // role 1: candidates
+    const uint8_t* qrec = A.cf;                                // role 0: queries
+    const uint8_t* crec = A.cf + (size_t)A.gq_pad * kRecBf16;  // role 1: candidates
     const int* qn = A.cn;
     const int* cnm = A.cn + A.gq_pad;
     // A fragments of this warp's 16 queries (rows g and g + 8), 3 k-steps
@@ -242,20 +247,19 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(const __grid_constant__ Fie
         af[ks][3] = __ldg(rb + c + 4);
     }
     const int na = __ldg(qn + qa), nb = __ldg(qn + qb);
-    int ld[2][8], li[2][8];
+    // top-8 of query 4k + lane/8 in slot k (entry lane % 8)
+    int ed[4], ei[4];
 #pragma unroll
-    for (int r = 0; r < 2; ++r)
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            ld[r][k] = 0x7fffffff;
-            li[r][k] = 0x7fffffff;
-        }
-    const int ntiles = (gq + kKnnTile - 1) / kKnnTile;
+    for (int k = 0; k < 4; ++k) {
+        ed[k] = 0x7fffffff;
+        ei[k] = 0x7fffffff;
+    }
+    const int ntiles = c1 > c0 ? (c1 - c0 + kKnnTile - 1) / kKnnTile : 0;
     // copy sizes: whole records, rounded up to 4 records (16-byte multiples of
-    // the norms); the arrays carry that padding
+    // the norms); the arrays carry that padding, and c0 is a multiple of 4
     auto issue = [&](int t) {
-        const int base = t * kKnnTile;
-        const int cnt4 = (min(kKnnTile, gq - base) + 3) & ~3;
+        const int base = c0 + t * kKnnTile;
+        const int cnt4 = (min(kKnnTile, c1 - base) + 3) & ~3;
         const unsigned fb = (unsigned)cnt4 * kRecBf16, nbytes = (unsigned)cnt4 * 4;
         mbar_expect_tx(&bar[t & 1], fb + nbytes);
         bulk_copy_g2s(&tile[t & 1][0], crec + (size_t)base * kRecBf16, fb, &bar[t & 1]);
@@ -268,7 +272,7 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(const __grid_constant__ Fie
         s_fail = 0;
     }
     __syncthreads();
-    if (threadIdx.x == 0) issue(0);
+    if (threadIdx.x == 0 && ntiles > 0) issue(0);
     for (int t = 0; t < ntiles; ++t) {
         const int buf = t & 1;
         // the other buffer was released by the __syncthreads that ended tile t-1
@@ -282,53 +286,64 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(const __grid_constant__ Fie
             }
             return;
         }
-        const int base = t * kKnnTile;
-        const int cnt = min(kKnnTile, gq - base);
+        const int base = c0 + t * kKnnTile;
+        const int cnt = min(kKnnTile, c1 - base);
         const uint32_t* tw = reinterpret_cast<const uint32_t*>(&tile[buf][0]);
+        // distances of the warp's 16 queries x this tile's candidates
         for (int grp8 = 0; grp8 < cnt; grp8 += 8) {
-            // B fragment: candidate grp8 + g, k pairs (2c, 2c+1) and (2c+8, 2c+9)
             const uint32_t* cb = tw + (size_t)(grp8 + g) * (kRecBf16 / 4);
             float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int ks = 0; ks < 3; ++ks) mma_bf16_16816(acc, af[ks], cb[ks * 8 + c], cb[ks * 8 + c + 4]);
-            // this thread's entries: rows g, g+8; candidates grp8 + 2c, grp8 + 2c + 1
-            const int j0 = grp8 + 2 * c, j1 = j0 + 1;
-            const int n0 = tnorm[buf][j0], n1 = tnorm[buf][j1];
-            const int dv[4] = {na + n0 - 2 * __float2int_rn(acc[0]), na + n1 - 2 * __float2int_rn(acc[1]),
-                               nb + n0 - 2 * __float2int_rn(acc[2]), nb + n1 - 2 * __float2int_rn(acc[3])};
+            const int j0 = grp8 + 2 * c;
+            const int n0 = tnorm[buf][j0], n1 = tnorm[buf][j0 + 1];
+            *reinterpret_cast<int2*>(&sdist[warp][g][j0]) =
+                make_int2(na + n0 - 2 * __float2int_rn(acc[0]), na + n1 - 2 * __float2int_rn(acc[1]));
+            *reinterpret_cast<int2*>(&sdist[warp][g + 8][j0]) =
+                make_int2(nb + n0 - 2 * __float2int_rn(acc[2]), nb + n1 - 2 * __float2int_rn(acc[3]));
+        }
+        __syncwarp();
+        // warp-uniform selection, one query at a time
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int j = e & 1 ? j1 : j0;
-                const int r = e >> 1;
-                if (j < cnt && dv[e] < ld[r][7]) list8_insert(ld[r], li[r], dv[e], base + j);
+        for (int qq = 0; qq < 16; ++qq) {
+            const int slot = qq >> 2, grp = qq & 3;
+            int thr = __shfl_sync(0xffffffffu, ed[slot], 8 * grp + 7);
+#pragma unroll
+            for (int r = 0; r < kKnnTile / 32; ++r) {
+                const int j = r * 32 + lane;
+                const int dj = j < cnt ? sdist[warp][qq][j] : 0x7fffffff;
+                unsigned enter = __ballot_sync(0xffffffffu, dj < thr);
+                while (enter) {
+                    const int src = __ffs(enter) - 1;
+                    enter &= enter - 1;
+                    const int nd = __shfl_sync(0xffffffffu, dj, src);
+                    if (nd >= thr) continue;  // the threshold moved meanwhile
+                    const int ni = base + r * 32 + src;
+                    const bool mine = (lane >> 3) == grp;
+                    const int pos = __popc(__ballot_sync(0xffffffffu, mine && !less_di(nd, ni, ed[slot], ei[slot])) );
+                    const int pd = __shfl_up_sync(0xffffffffu, ed[slot], 1), pi = __shfl_up_sync(0xffffffffu, ei[slot], 1);
+                    const int e = lane & 7;
+                    if (mine) {
+                        if (e > pos) {
+                            ed[slot] = pd;
+                            ei[slot] = pi;
+                        } else if (e == pos) {
+                            ed[slot] = nd;
+                            ei[slot] = ni;
+                        }
+                    }
+                    thr = __shfl_sync(0xffffffffu, ed[slot], 8 * grp + 7);
+                }
             }
         }
         __syncthreads();
     }
-    // merge the 4 partial lists of each query (threads c = 0..3 of its row)
+    // partial top-8 of this candidate range
 #pragma unroll
-    for (int r = 0; r < 2; ++r)
-#pragma unroll
-        for (int k = 0; k < 8; ++k) merge[warp * 16 + g + 8 * r][c][k] = make_int2(ld[r][k], li[r][k]);
-    __syncthreads();
-    if (threadIdx.x < kKnnQueries) {
-        const int qi = q0 + threadIdx.x;
-        if (qi < gq) {
-            int md[8], mi[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                md[k] = 0x7fffffff;
-                mi[k] = 0x7fffffff;
-            }
-            for (int cc = 0; cc < 4; ++cc)
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const int2 e = merge[threadIdx.x][cc][k];
-                    if (less_di(e.x, e.y, md[7], mi[7])) list8_insert(md, mi, e.x, e.y);
-                }
-#pragma unroll
-            for (int k = 0; k < 8; ++k) A.best8[(size_t)qi * 8 + k] = make_int2(md[k], mi[k]);
-        }
+    for (int k = 0; k < 4; ++k) {
+        const int qi = q0 + warp * 16 + 4 * k + (lane >> 3);
+        if (qi < gq)
+            A.best8[(((size_t)blockIdx.y * gq) + qi) * 8 + (lane & 7)] = make_int2(ed[k], ei[k]);
     }
 }
 
@@ -368,14 +383,21 @@ __global__ void k_init_select(const __grid_constant__ Fields F, int n, int knn) 
     const int px = (qi % gw) * n, py = (qi / gw) * n;
     RefFeat r;
     load_ref(V.ref, pix(V.w, px, py), r);
-    // the query's temporal top-8 (every lane the same, reads broadcast)
+    // merge the partial top-8 lists of the candidate ranges (every lane the
+    // same, reads broadcast)
     int bd[8], bi[8];
-    const int2* src = A.best8 + (size_t)qi * 8;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        const int2 e = src[k];
-        bd[k] = e.x;
-        bi[k] = e.y;
+        bd[k] = 0x7fffffff;
+        bi[k] = 0x7fffffff;
+    }
+    for (int p = 0; p < kKnnSplits; ++p) {
+        const int2* src = A.best8 + ((size_t)p * A.gq + qi) * 8;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int2 e = src[k];
+            if (less_di(e.x, e.y, bd[7], bi[7])) top8_insert(bd, bi, e.x, e.y);
+        }
     }
     int ds, sx;
     warp_row_nearest(r, V.ste, V.w, n, gw, py, px, V.sigma, lane, ds, sx);
@@ -775,7 +797,7 @@ FieldScratch field_scratch(int w, int h, const sff_params& p) {
     const int gq = coarse_gq(w, h, p), gp = gq_padded(gq);
     FieldScratch f;
     f.best8 = 0;
-    f.cf = f.best8 + align256((size_t)gq * 8 * sizeof(int2));
+    f.cf = f.best8 + align256((size_t)kKnnSplits * gq * 8 * sizeof(int2));
     f.cn = f.cf + align256((size_t)2 * gp * kRecBf16);
     f.field = f.cn + align256((size_t)2 * gp * sizeof(int));
     f.cost = f.field + align256((size_t)w * h * 8);
@@ -840,7 +862,7 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
         if (s == S - 1) {
             dim3 g0((mgq * 4 + 255) / 256, 2, nf);
             SFF_LAUNCH(k_gather_grid, g0, 256, 0, st, F, n);
-            dim3 g1((mgq + kKnnQueries - 1) / kKnnQueries, 1, nf);
+            dim3 g1((mgq + kKnnQueries - 1) / kKnnQueries, kKnnSplits, nf);
             SFF_LAUNCH(k_knn, g1, kKnnThreads, 0, st, F);
             dim3 g2((mgq + 7) / 8, 1, nf);
             SFF_LAUNCH(k_init_select, g2, 256, 0, st, F, n, P.knn_temporal);
