@@ -66,6 +66,7 @@ struct Field {
     int2* best8;  // [gq][8] temporal top-8 (distance, grid index)
     uint8_t* cf;  // [2 roles][gq_pad] 48-byte records: reference, temporal
     int* cn;  // [2 roles][gq_pad] norms
+    int* bound;  // [gq] upper bound of each query's 8th-nearest temporal distance
     uint2 key;  // Philox key: the seed of the field's quad
 };
 
@@ -203,6 +204,39 @@ __device__ __forceinline__ void list8_insert(int (&d)[8], int (&id)[8], int nd, 
     }
 }
 
+// Upper bound of each query's 8th-nearest temporal distance: the 8th
+// smallest distance among 25 distinct coarsest-grid points around the
+// query's own position (a 5x5 window shifted inside the grid).  Eight real
+// candidates lie at or below it, so the true 8th-nearest distance does too
+// and k_knn can skip every candidate above it.  INT32_MAX (no bound) when
+// the grid has fewer than 8 points in the window.  One warp per query.
+__global__ void k_knn_bound(const __grid_constant__ Fields F, int n) {
+    const Field& A = pick(F);
+    const int qi = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (qi >= A.gq) return;  // warp-uniform
+    const int gw = A.gw, gh = A.gh;
+    const int gx = qi % gw, gy = qi / gw;
+    const int ww = min(5, gw), wh = min(5, gh);
+    const int ox = clampi(gx - 2, 0, gw - ww), oy = clampi(gy - 2, 0, gh - wh);
+    RefFeat r;
+    load_ref(A.V.ref, pix(A.V.w, gx * n, gy * n), r);
+    int d = 0x7fffffff;
+    if (lane < ww * wh) d = ssd_at(r, A.V.tmp, pix(A.V.w, (ox + lane % ww) * n, (oy + lane / ww) * n));
+    int t = 0x7fffffff;
+    if (ww * wh >= 8) {
+#pragma unroll 1
+        for (int k = 0; k < 8; ++k) {  // remove the smallest 7 times; the 8th minimum is the bound
+            int m = d;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
+            t = m;
+            const unsigned who = __ballot_sync(0xffffffffu, d == m);
+            if (lane == __ffs(who) - 1) d = 0x7fffffff;
+        }
+    }
+    if (lane == 0) A.bound[qi] = t;
+}
+
 // Temporal K-NN: tensor-core distances, warp-uniform selection.
 // A CTA takes 64 queries (16 per warp) and one of kKnnSplits ranges of the
 // candidates (blockIdx.y).  Candidate records stream through two
@@ -210,8 +244,10 @@ __device__ __forceinline__ void list8_insert(int (&d)[8], int (&id)[8], int nd, 
 // tile t is scored).  Per tile each warp computes its 16 x 128 dot products
 // with mma.sync m16n8k16 (bf16 in, fp32 accumulate: exact for these
 // integers) into a shared-memory block of distances |q|^2 + |c|^2 - 2 q.c.
-// Selection then reads that block one query at a time: four ballots against
-// the query's current 8th-best distance; the rare candidates that enter are
+// Selection then reads that block one query at a time: ballots against the
+// query's current 8th-best distance, capped by the bound of k_knn_bound (a
+// candidate above it cannot be among the 8 nearest, so the union of the
+// ranges' lists still holds the exact top-8); the rare candidates that enter are
 // inserted into the query's sorted top-8, held by lanes 8(q%4)..8(q%4)+7 in
 // register slot q/4.  Candidates are visited in increasing index, so a
 // strictly smaller distance is the only way in, exactly as in the (distance,
@@ -222,6 +258,7 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(const __grid_constant__ Fie
     __shared__ __align__(16) int sdist[kKnnWarps][16][kKnnTile + 4];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ int s_fail;
+    __shared__ int s_lim[kKnnQueries];  // entry limit per query: bound + 1 (distances <= bound may enter)
     const Field& A = pick(F);
     const int gq = A.gq;
     const int q0 = blockIdx.x * kKnnQueries;
@@ -271,6 +308,10 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(const __grid_constant__ Fie
         mbar_fence_init();
         s_fail = 0;
     }
+    for (int k = threadIdx.x; k < kKnnQueries; k += kKnnThreads) {
+        const int b = q0 + k < gq ? A.bound[q0 + k] : 0x7fffffff;
+        s_lim[k] = b == 0x7fffffff ? b : b + 1;
+    }
     __syncthreads();
     if (threadIdx.x == 0 && ntiles > 0) issue(0);
     for (int t = 0; t < ntiles; ++t) {
@@ -307,7 +348,8 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(const __grid_constant__ Fie
 #pragma unroll
         for (int qq = 0; qq < 16; ++qq) {
             const int slot = qq >> 2, grp = qq & 3;
-            int thr = __shfl_sync(0xffffffffu, ed[slot], 8 * grp + 7);
+            const int lim = s_lim[warp * 16 + qq];
+            int thr = min(lim, __shfl_sync(0xffffffffu, ed[slot], 8 * grp + 7));
 #pragma unroll
             for (int r = 0; r < kKnnTile / 32; ++r) {
                 const int j = r * 32 + lane;
@@ -332,7 +374,7 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(const __grid_constant__ Fie
                             ei[slot] = ni;
                         }
                     }
-                    thr = __shfl_sync(0xffffffffu, ed[slot], 8 * grp + 7);
+                    thr = min(lim, __shfl_sync(0xffffffffu, ed[slot], 8 * grp + 7));
                 }
             }
         }
@@ -791,7 +833,7 @@ int coarse_gq(int w, int h, const sff_params& p) {
 // copy (whole groups of 4 records) starts and ends on 16 bytes.
 int gq_padded(int gq) { return ((gq + 3) & ~3) + 4; }
 struct FieldScratch {
-    size_t best8, cf, cn, field, cost, total;
+    size_t best8, cf, cn, bound, field, cost, total;
 };
 FieldScratch field_scratch(int w, int h, const sff_params& p) {
     const int gq = coarse_gq(w, h, p), gp = gq_padded(gq);
@@ -799,7 +841,8 @@ FieldScratch field_scratch(int w, int h, const sff_params& p) {
     f.best8 = 0;
     f.cf = f.best8 + align256((size_t)kKnnSplits * gq * 8 * sizeof(int2));
     f.cn = f.cf + align256((size_t)2 * gp * kRecBf16);
-    f.field = f.cn + align256((size_t)2 * gp * sizeof(int));
+    f.bound = f.cn + align256((size_t)2 * gp * sizeof(int));
+    f.field = f.bound + align256((size_t)gq * sizeof(int));
     f.cost = f.field + align256((size_t)w * h * 8);
     f.total = f.cost + align256((size_t)w * h * 4);
     return f;
@@ -834,6 +877,7 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
         F.f[k].best8 = reinterpret_cast<int2*>(ws + sc.best8);
         F.f[k].cf = reinterpret_cast<uint8_t*>(ws + sc.cf);
         F.f[k].cn = reinterpret_cast<int*>(ws + sc.cn);
+        F.f[k].bound = reinterpret_cast<int*>(ws + sc.bound);
         F.f[k].gq = coarse_gq(fs.width, fs.height, P);
         F.f[k].gq_pad = gq_padded(F.f[k].gq);
         F.f[k].mirror = fs.mirror;
@@ -862,6 +906,8 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
         if (s == S - 1) {
             dim3 g0((mgq * 4 + 255) / 256, 2, nf);
             SFF_LAUNCH(k_gather_grid, g0, 256, 0, st, F, n);
+            dim3 gb((mgq + 7) / 8, 1, nf);
+            SFF_LAUNCH(k_knn_bound, gb, 256, 0, st, F, n);
             dim3 g1((mgq + kKnnQueries - 1) / kKnnQueries, kKnnSplits, nf);
             SFF_LAUNCH(k_knn, g1, kKnnThreads, 0, st, F);
             dim3 g2((mgq + 7) / 8, 1, nf);
