@@ -10,11 +10,12 @@
 //
 // k_gather_grid:  packs the coarsest-grid records of the reference and
 //                 temporal images into contiguous arrays.
-// k_knn:          temporal K-NN, all-pairs over the coarsest grid on the
-//                 tensor cores (mma.sync bf16, exact for int8 features);
-//                 candidate tiles streamed into shared memory by TMA bulk
-//                 copies on mbarriers (double-buffered); per-thread sorted
-//                 top-8 lists merged per query at the end.
+// k_knn_bound:    an exact upper bound of each query's 8th-nearest distance
+//                 from a 5x5 window of coarsest-grid points around it.
+// k_knn:          temporal K-NN, all-pairs over the coarsest grid, one warp
+//                 per query; candidate tiles streamed into shared memory by
+//                 TMA bulk copies on mbarriers (double-buffered); a sorted
+//                 top-8 spread over lanes 0-7, entry capped by the bound.
 // k_init_select:  one warp per query: takes the temporal top-K, finds
 //                 the nearest epipolar stereo / cross points and keeps the
 //                 best combination.  The cost is the sum of the three
@@ -44,12 +45,9 @@ namespace {
 
 std::mutex g_fields_mu;  // guards the host staging of the Fields parameter
 
-constexpr int kKnnThreads = 128;
-constexpr int kKnnWarps = kKnnThreads / 32;
-constexpr int kKnnQueries = 16 * kKnnWarps;  // 16 queries per warp (one mma row block)
-constexpr int kKnnTile = 64;                 // candidates per shared-memory tile (6 KB of bf16 records)
-constexpr int kRecBf16 = 96;                 // bytes of a compacted record: 48 bf16
-constexpr int kKnnSplits = 8;                // candidate ranges per query block (merged by k_init_select)
+constexpr int kKnnThreads = 256;
+constexpr int kKnnWarps = kKnnThreads / 32;  // one query per warp
+constexpr int kKnnTile = 256;                // candidates per shared-memory tile (12 KB of records)
 
 // One field: its views and grid at the current scale, its state and, for
 // the double-buffered iteration kernel, the buffer it writes; plus its
@@ -105,10 +103,9 @@ __device__ __forceinline__ int dot12(const int (&a)[12], const int4& p0, const i
 }
 
 // Copies the coarsest-grid records of the reference (role 0) and temporal
-// (role 1) images of each field into contiguous arrays for the tensor-core
-// K-NN search: 48 features as bf16 (int8 values are exact in bf16, so are
-// their products and the 48-term sums in fp32) and the int32 norms.
-// Layout per field: [2 roles][gq_pad] records of 96 bytes / norms.
+// (role 1) images of each field into contiguous arrays, so that the K-NN
+// search streams them with bulk copies.  Layout per field: [2 roles][gq_pad]
+// 48-byte records and int32 norms.
 __global__ void k_gather_grid(const __grid_constant__ Fields F, int n) {
     const Field& A = pick(F);
     const int role = blockIdx.y;
@@ -118,23 +115,11 @@ __global__ void k_gather_grid(const __grid_constant__ Fields F, int n) {
     if (c >= A.gq) return;
     const size_t i = pix(A.V.w, (c % A.gw) * n, (c / A.gw) * n);
     const size_t slot = (size_t)role * A.gq_pad + c;
-    if (part < 3) {
-        const int4 v = __ldg(reinterpret_cast<const int4*>(P.f + i * kFeat) + part);
-        const int words[4] = {v.x, v.y, v.z, v.w};
-        uint32_t out[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {  // two int8 -> two bf16 per 32-bit word
-            const int w = words[k / 2];
-            const int lo = (int)(int8_t)((w >> (16 * (k & 1))) & 0xff);
-            const int hi = (int)(int8_t)((w >> (16 * (k & 1) + 8)) & 0xff);
-            out[k] = (__float_as_uint((float)lo) >> 16) | (__float_as_uint((float)hi) & 0xffff0000u);
-        }
-        uint4* dst = reinterpret_cast<uint4*>(A.cf + slot * kRecBf16) + 2 * part;
-        dst[0] = make_uint4(out[0], out[1], out[2], out[3]);
-        dst[1] = make_uint4(out[4], out[5], out[6], out[7]);
-    } else {
+    if (part < 3)
+        reinterpret_cast<int4*>(A.cf + slot * kFeat)[part] =
+            __ldg(reinterpret_cast<const int4*>(P.f + i * kFeat) + part);
+    else
         A.cn[slot] = __ldg(P.nrm + i);
-    }
 }
 
 // TMA (bulk-copy) helpers: 1-D global -> shared copies completing on an
@@ -180,30 +165,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
 
 __device__ unsigned int g_wait_timeouts;  // bounded waits that gave up (read by sff_device_timeouts)
 
-__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-// Sorted insertion of (nd, ni) into an 8-entry list (d ascending, index
-// ascending on ties) that is known to take it.
-__device__ __forceinline__ void list8_insert(int (&d)[8], int (&id)[8], int nd, int ni) {
-#pragma unroll
-    for (int k = 7; k >= 0; --k) {
-        const bool lt_prev = k > 0 && less_di(nd, ni, d[k > 0 ? k - 1 : 0], id[k > 0 ? k - 1 : 0]);
-        if (lt_prev) {
-            d[k] = d[k - 1];
-            id[k] = id[k - 1];
-        } else if (less_di(nd, ni, d[k], id[k])) {
-            d[k] = nd;
-            id[k] = ni;
-        }
-    }
-}
-
 // Upper bound of each query's 8th-nearest temporal distance: the 8th
 // smallest distance among 25 distinct coarsest-grid points around the
 // query's own position (a 5x5 window shifted inside the grid).  Eight real
@@ -237,70 +198,51 @@ __global__ void k_knn_bound(const __grid_constant__ Fields F, int n) {
     if (lane == 0) A.bound[qi] = t;
 }
 
-// Temporal K-NN: tensor-core distances, warp-uniform selection.
-// A CTA takes 64 queries (16 per warp) and one of kKnnSplits ranges of the
-// candidates (blockIdx.y).  Candidate records stream through two
-// shared-memory tiles filled by bulk copies (thread 0 issues tile t+1 while
-// tile t is scored).  Per tile each warp computes its 16 x 128 dot products
-// with mma.sync m16n8k16 (bf16 in, fp32 accumulate: exact for these
-// integers) into a shared-memory block of distances |q|^2 + |c|^2 - 2 q.c.
-// Selection then reads that block one query at a time: ballots against the
-// query's current 8th-best distance, capped by the bound of k_knn_bound (a
-// candidate above it cannot be among the 8 nearest, so the union of the
-// ranges' lists still holds the exact top-8); the rare candidates that enter are
-// inserted into the query's sorted top-8, held by lanes 8(q%4)..8(q%4)+7 in
-// register slot q/4.  Candidates are visited in increasing index, so a
-// strictly smaller distance is the only way in, exactly as in the (distance,
-// index) order.  The partial top-8 of each range is merged by k_init_select.
+// Temporal K-NN of one query per warp over all candidates.  The candidate
+// records stream through two shared-memory tiles filled by bulk copies
+// (thread 0 issues tile t+1 while tile t is scored); the 8 queries of a CTA
+// share them.  Lane l scores candidate l of each batch of 32 (12 dp4a); a
+// ballot against the query's current 8th-best distance, capped from the
+// start by the bound of k_knn_bound, keeps the rare candidates that enter;
+// each is inserted into the sorted top-8 held by lanes 0-7 with warp-uniform
+// shuffles.  Candidates are visited in increasing index, so a strictly
+// smaller distance is the only way in, exactly as in the (distance, index)
+// order, and every candidate above the bound is provably not among the 8.
 __global__ void __launch_bounds__(kKnnThreads) k_knn(const __grid_constant__ Fields F) {
-    __shared__ __align__(128) uint4 tile[2][kKnnTile * kRecBf16 / 16];
+    __shared__ __align__(128) int4 tile[2][kKnnTile][3];
     __shared__ __align__(16) int tnorm[2][kKnnTile];
-    __shared__ __align__(16) int sdist[kKnnWarps][16][kKnnTile + 4];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ int s_fail;
-    __shared__ int s_lim[kKnnQueries];  // entry limit per query: bound + 1 (distances <= bound may enter)
     const Field& A = pick(F);
     const int gq = A.gq;
-    const int q0 = blockIdx.x * kKnnQueries;
-    const int per = (((gq + kKnnSplits - 1) / kKnnSplits) + 3) & ~3;  // multiple of 4: aligned bulk copies
-    const int c0 = blockIdx.y * per, c1 = min(gq, c0 + per);
-    if (q0 >= gq) return;  // CTA beyond this field's queries
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane >> 2, c = lane & 3;
-    const uint8_t* qrec = A.cf;                                // role 0: queries
-    const uint8_t* crec = A.cf + (size_t)A.gq_pad * kRecBf16;  // role 1: candidates
-    const int* qn = A.cn;
-    const int* cnm = A.cn + A.gq_pad;
-    // A fragments of this warp's 16 queries (rows g and g + 8), 3 k-steps
-    const int qa = min(q0 + warp * 16 + g, gq - 1), qb = min(q0 + warp * 16 + g + 8, gq - 1);
-    uint32_t af[3][4];
-#pragma unroll
-    for (int ks = 0; ks < 3; ++ks) {
-        const uint32_t* ra = reinterpret_cast<const uint32_t*>(qrec + (size_t)qa * kRecBf16) + ks * 8;
-        const uint32_t* rb = reinterpret_cast<const uint32_t*>(qrec + (size_t)qb * kRecBf16) + ks * 8;
-        af[ks][0] = __ldg(ra + c);
-        af[ks][1] = __ldg(rb + c);
-        af[ks][2] = __ldg(ra + c + 4);
-        af[ks][3] = __ldg(rb + c + 4);
+    if ((int)blockIdx.x * kKnnWarps >= gq) return;  // CTA beyond this field's queries
+    const int lane = threadIdx.x & 31;
+    const int qi = blockIdx.x * kKnnWarps + (threadIdx.x >> 5);
+    const bool active = qi < gq;  // warp-uniform
+    const uint8_t* tf = A.cf + (size_t)A.gq_pad * kFeat;  // role 1: candidates
+    const int* tn = A.cn + A.gq_pad;
+    RefFeat r;
+    int lim = 0x7fffffff;
+    if (active) {
+        const int4* p = reinterpret_cast<const int4*>(A.cf + (size_t)qi * kFeat);  // role 0: queries
+        const int4 q0 = __ldg(p), q1 = __ldg(p + 1), q2 = __ldg(p + 2);
+        r.a[0] = q0.x; r.a[1] = q0.y; r.a[2] = q0.z; r.a[3] = q0.w;
+        r.a[4] = q1.x; r.a[5] = q1.y; r.a[6] = q1.z; r.a[7] = q1.w;
+        r.a[8] = q2.x; r.a[9] = q2.y; r.a[10] = q2.z; r.a[11] = q2.w;
+        r.n = __ldg(A.cn + qi);
+        const int b = A.bound[qi];
+        lim = b == 0x7fffffff ? b : b + 1;  // distances <= bound may enter
     }
-    const int na = __ldg(qn + qa), nb = __ldg(qn + qb);
-    // top-8 of query 4k + lane/8 in slot k (entry lane % 8)
-    int ed[4], ei[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        ed[k] = 0x7fffffff;
-        ei[k] = 0x7fffffff;
-    }
-    const int ntiles = c1 > c0 ? (c1 - c0 + kKnnTile - 1) / kKnnTile : 0;
-    // copy sizes: whole records, rounded up to 4 records (16-byte multiples of
-    // the norms); the arrays carry that padding, and c0 is a multiple of 4
+    const int ntiles = (gq + kKnnTile - 1) / kKnnTile;
+    // copy sizes: whole records, rounded up to 4 records (16-byte multiples);
+    // the arrays carry that padding
     auto issue = [&](int t) {
-        const int base = c0 + t * kKnnTile;
-        const int cnt4 = (min(kKnnTile, c1 - base) + 3) & ~3;
-        const unsigned fb = (unsigned)cnt4 * kRecBf16, nbytes = (unsigned)cnt4 * 4;
+        const int base = t * kKnnTile;
+        const int cnt4 = (min(kKnnTile, gq - base) + 3) & ~3;
+        const unsigned fb = (unsigned)cnt4 * kFeat, nbytes = (unsigned)cnt4 * 4;
         mbar_expect_tx(&bar[t & 1], fb + nbytes);
-        bulk_copy_g2s(&tile[t & 1][0], crec + (size_t)base * kRecBf16, fb, &bar[t & 1]);
-        bulk_copy_g2s(&tnorm[t & 1][0], cnm + base, nbytes, &bar[t & 1]);
+        bulk_copy_g2s(&tile[t & 1][0][0], tf + (size_t)base * kFeat, fb, &bar[t & 1]);
+        bulk_copy_g2s(&tnorm[t & 1][0], tn + base, nbytes, &bar[t & 1]);
     };
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
@@ -308,12 +250,10 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(const __grid_constant__ Fie
         mbar_fence_init();
         s_fail = 0;
     }
-    for (int k = threadIdx.x; k < kKnnQueries; k += kKnnThreads) {
-        const int b = q0 + k < gq ? A.bound[q0 + k] : 0x7fffffff;
-        s_lim[k] = b == 0x7fffffff ? b : b + 1;
-    }
     __syncthreads();
-    if (threadIdx.x == 0 && ntiles > 0) issue(0);
+    if (threadIdx.x == 0) issue(0);
+    int ld = 0x7fffffff, li = 0x7fffffff;  // entry `lane` of the sorted top-8 (lanes 0-7)
+    int thr = lim;
     for (int t = 0; t < ntiles; ++t) {
         const int buf = t & 1;
         // the other buffer was released by the __syncthreads that ended tile t-1
@@ -327,66 +267,41 @@ __global__ void __launch_bounds__(kKnnThreads) k_knn(const __grid_constant__ Fie
             }
             return;
         }
-        const int base = c0 + t * kKnnTile;
-        const int cnt = min(kKnnTile, c1 - base);
-        const uint32_t* tw = reinterpret_cast<const uint32_t*>(&tile[buf][0]);
-        // distances of the warp's 16 queries x this tile's candidates
-        for (int grp8 = 0; grp8 < cnt; grp8 += 8) {
-            const uint32_t* cb = tw + (size_t)(grp8 + g) * (kRecBf16 / 4);
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int ks = 0; ks < 3; ++ks) mma_bf16_16816(acc, af[ks], cb[ks * 8 + c], cb[ks * 8 + c + 4]);
-            const int j0 = grp8 + 2 * c;
-            const int n0 = tnorm[buf][j0], n1 = tnorm[buf][j0 + 1];
-            *reinterpret_cast<int2*>(&sdist[warp][g][j0]) =
-                make_int2(na + n0 - 2 * __float2int_rn(acc[0]), na + n1 - 2 * __float2int_rn(acc[1]));
-            *reinterpret_cast<int2*>(&sdist[warp][g + 8][j0]) =
-                make_int2(nb + n0 - 2 * __float2int_rn(acc[2]), nb + n1 - 2 * __float2int_rn(acc[3]));
-        }
-        __syncwarp();
-        // warp-uniform selection, one query at a time
-#pragma unroll
-        for (int qq = 0; qq < 16; ++qq) {
-            const int slot = qq >> 2, grp = qq & 3;
-            const int lim = s_lim[warp * 16 + qq];
-            int thr = min(lim, __shfl_sync(0xffffffffu, ed[slot], 8 * grp + 7));
-#pragma unroll
-            for (int r = 0; r < kKnnTile / 32; ++r) {
-                const int j = r * 32 + lane;
-                const int dj = j < cnt ? sdist[warp][qq][j] : 0x7fffffff;
-                unsigned enter = __ballot_sync(0xffffffffu, dj < thr);
+        const int base = t * kKnnTile;
+        const int cnt = min(kKnnTile, gq - base);
+        if (active) {
+            const int4(*tl)[3] = tile[buf];
+            const int* tnm = tnorm[buf];
+#pragma unroll 2
+            for (int b = 0; b < cnt; b += 32) {
+                const int k = b + lane;
+                const int d = k < cnt ? r.n + tnm[k] - 2 * dot12(r.a, tl[k][0], tl[k][1], tl[k][2]) : 0x7fffffff;
+                unsigned enter = __ballot_sync(0xffffffffu, d < thr);
                 while (enter) {
                     const int src = __ffs(enter) - 1;
                     enter &= enter - 1;
-                    const int nd = __shfl_sync(0xffffffffu, dj, src);
+                    const int nd = __shfl_sync(0xffffffffu, d, src);
                     if (nd >= thr) continue;  // the threshold moved meanwhile
-                    const int ni = base + r * 32 + src;
-                    const bool mine = (lane >> 3) == grp;
-                    const int pos = __popc(__ballot_sync(0xffffffffu, mine && !less_di(nd, ni, ed[slot], ei[slot])) );
-                    const int pd = __shfl_up_sync(0xffffffffu, ed[slot], 1), pi = __shfl_up_sync(0xffffffffu, ei[slot], 1);
-                    const int e = lane & 7;
-                    if (mine) {
-                        if (e > pos) {
-                            ed[slot] = pd;
-                            ei[slot] = pi;
-                        } else if (e == pos) {
-                            ed[slot] = nd;
-                            ei[slot] = ni;
+                    const int ni = base + b + src;
+                    // entries are earlier candidates: (d, index) order is d order with ties kept
+                    const int pos = __popc(__ballot_sync(0xffffffffu, lane < 8 && ld <= nd));
+                    const int pd = __shfl_up_sync(0xffffffffu, ld, 1), pi = __shfl_up_sync(0xffffffffu, li, 1);
+                    if (lane < 8) {
+                        if (lane > pos) {
+                            ld = pd;
+                            li = pi;
+                        } else if (lane == pos) {
+                            ld = nd;
+                            li = ni;
                         }
                     }
-                    thr = min(lim, __shfl_sync(0xffffffffu, ed[slot], 8 * grp + 7));
+                    thr = min(lim, __shfl_sync(0xffffffffu, ld, 7));
                 }
             }
         }
         __syncthreads();
     }
-    // partial top-8 of this candidate range
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int qi = q0 + warp * 16 + 4 * k + (lane >> 3);
-        if (qi < gq)
-            A.best8[(((size_t)blockIdx.y * gq) + qi) * 8 + (lane & 7)] = make_int2(ed[k], ei[k]);
-    }
+    if (active && lane < 8) A.best8[(size_t)qi * 8 + lane] = make_int2(ld, li);
 }
 
 // Nearest grid point of row y by (distance, x), constrained by sigma, found by
@@ -425,21 +340,14 @@ __global__ void k_init_select(const __grid_constant__ Fields F, int n, int knn) 
     const int px = (qi % gw) * n, py = (qi / gw) * n;
     RefFeat r;
     load_ref(V.ref, pix(V.w, px, py), r);
-    // merge the partial top-8 lists of the candidate ranges (every lane the
-    // same, reads broadcast)
+    // the query's temporal top-8 (every lane the same, reads broadcast)
     int bd[8], bi[8];
+    const int2* src = A.best8 + (size_t)qi * 8;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        bd[k] = 0x7fffffff;
-        bi[k] = 0x7fffffff;
-    }
-    for (int p = 0; p < kKnnSplits; ++p) {
-        const int2* src = A.best8 + ((size_t)p * A.gq + qi) * 8;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int2 e = src[k];
-            if (less_di(e.x, e.y, bd[7], bi[7])) top8_insert(bd, bi, e.x, e.y);
-        }
+        const int2 e = src[k];
+        bd[k] = e.x;
+        bi[k] = e.y;
     }
     int ds, sx;
     warp_row_nearest(r, V.ste, V.w, n, gw, py, px, V.sigma, lane, ds, sx);
@@ -839,8 +747,8 @@ FieldScratch field_scratch(int w, int h, const sff_params& p) {
     const int gq = coarse_gq(w, h, p), gp = gq_padded(gq);
     FieldScratch f;
     f.best8 = 0;
-    f.cf = f.best8 + align256((size_t)kKnnSplits * gq * 8 * sizeof(int2));
-    f.cn = f.cf + align256((size_t)2 * gp * kRecBf16);
+    f.cf = f.best8 + align256((size_t)gq * 8 * sizeof(int2));
+    f.cn = f.cf + align256((size_t)2 * gp * kFeat);
     f.bound = f.cn + align256((size_t)2 * gp * sizeof(int));
     f.field = f.bound + align256((size_t)gq * sizeof(int));
     f.cost = f.field + align256((size_t)w * h * 8);
@@ -908,7 +816,7 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
             SFF_LAUNCH(k_gather_grid, g0, 256, 0, st, F, n);
             dim3 gb((mgq + 7) / 8, 1, nf);
             SFF_LAUNCH(k_knn_bound, gb, 256, 0, st, F, n);
-            dim3 g1((mgq + kKnnQueries - 1) / kKnnQueries, kKnnSplits, nf);
+            dim3 g1((mgq + kKnnWarps - 1) / kKnnWarps, 1, nf);
             SFF_LAUNCH(k_knn, g1, kKnnThreads, 0, st, F);
             dim3 g2((mgq + 7) / 8, 1, nf);
             SFF_LAUNCH(k_init_select, g2, 256, 0, st, F, n, P.knn_temporal);
