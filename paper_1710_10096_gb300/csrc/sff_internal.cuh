@@ -9,6 +9,7 @@
 //   cost     [y][x] int32, SFF_EMPTY_COST where no vector is held yet.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 

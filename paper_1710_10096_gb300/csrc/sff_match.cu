@@ -8,14 +8,15 @@
 // parallelism of the small coarse-scale launches and lets one L2 fill of a
 // scale's features serve both fields.
 //
-// k_gather_grid:  packs the coarsest-grid records of the reference and
-//                 temporal images into contiguous arrays.
-// k_knn_bound:    an exact upper bound of each query's 8th-nearest distance
-//                 from a 5x5 window of coarsest-grid points around it.
-// k_knn:          temporal K-NN, all-pairs over the coarsest grid, one warp
-//                 per query; candidate tiles streamed into shared memory by
-//                 TMA bulk copies on mbarriers (double-buffered); a sorted
-//                 top-8 spread over lanes 0-7, entry capped by the bound.
+// k_gather_grid:  writes the coarsest-grid points of the reference and
+//                 temporal images as augmented bf16 rows whose products are
+//                 the squared feature distances, in the tensor-core tile
+//                 layout.
+// k_knn_tc:       temporal K-NN, all-pairs over the coarsest grid: the
+//                 distance matrix on the tensor cores (tcgen05.mma into
+//                 tensor memory, operands streamed by TMA bulk copies),
+//                 two scans of it -- a bound from 128 bucket minima, then
+//                 exact top-8 lists under that bound.
 // k_init_select:  one warp per query: takes the temporal top-K, finds
 //                 the nearest epipolar stereo / cross points and keeps the
 //                 best combination.  The cost is the sum of the three
@@ -45,9 +46,6 @@ namespace {
 
 std::mutex g_fields_mu;  // guards the host staging of the Fields parameter
 
-constexpr int kKnnThreads = 256;
-constexpr int kKnnWarps = kKnnThreads / 32;  // one query per warp
-constexpr int kKnnTile = 256;                // candidates per shared-memory tile (12 KB of records)
 
 // One field: its views and grid at the current scale, its state and, for
 // the double-buffered iteration kernel, the buffer it writes; plus its
@@ -60,11 +58,9 @@ struct Field {
     int* cost_out;
     int mirror;
     int gw, gh;  // grid of the current scale
-    int gq, gq_pad;  // coarsest grid points and padded row count of the compact arrays
+    int gq;  // coarsest grid points
     int2* best8;  // [gq][8] temporal top-8 (distance, grid index)
-    uint8_t* cf;  // [2 roles][gq_pad] 48-byte records: reference, temporal
-    int* cn;  // [2 roles][gq_pad] norms
-    int* bound;  // [gq] upper bound of each query's 8th-nearest temporal distance
+    uint8_t* tk;  // [2 roles][rows] augmented bf16 rows in MMA tile layout: queries, candidates
     uint2 key;  // Philox key: the seed of the field's quad
 };
 
@@ -77,53 +73,105 @@ struct Fields {
 
 __device__ __forceinline__ const Field& pick(const Fields& F) { return F.f[blockIdx.z]; }
 
-__device__ __forceinline__ bool less_di(int d, int i, int d2, int i2) { return d < d2 || (d == d2 && i < i2); }
 
-__device__ __forceinline__ void top8_insert(int (&d)[8], int (&id)[8], int nd, int ni) {
-    if (!less_di(nd, ni, d[7], id[7])) return;
-#pragma unroll
-    for (int k = 7; k >= 0; --k) {
-        bool lt_prev = (k > 0) && less_di(nd, ni, d[k > 0 ? k - 1 : 0], id[k > 0 ? k - 1 : 0]);
-        if (lt_prev) {
-            d[k] = d[k - 1];
-            id[k] = id[k - 1];
-        } else if (less_di(nd, ni, d[k], id[k])) {
-            d[k] = nd;
-            id[k] = ni;
-        }
-    }
-}
 
-__device__ __forceinline__ int dot12(const int (&a)[12], const int4& p0, const int4& p1, const int4& p2) {
-    int e = 0;
-    e = __dp4a(a[0], p0.x, e); e = __dp4a(a[1], p0.y, e); e = __dp4a(a[2], p0.z, e); e = __dp4a(a[3], p0.w, e);
-    e = __dp4a(a[4], p1.x, e); e = __dp4a(a[5], p1.y, e); e = __dp4a(a[6], p1.z, e); e = __dp4a(a[7], p1.w, e);
-    e = __dp4a(a[8], p2.x, e); e = __dp4a(a[9], p2.y, e); e = __dp4a(a[10], p2.z, e); e = __dp4a(a[11], p2.w, e);
-    return e;
-}
 
-// Copies the coarsest-grid records of the reference (role 0) and temporal
-// (role 1) images of each field into contiguous arrays, so that the K-NN
-// search streams them with bulk copies.  Layout per field: [2 roles][gq_pad]
-// 48-byte records and int32 norms.
+// ---------------------------------------------------------------------------
+// Temporal K-NN on the tensor cores.
+//
+// The squared distance |q - c|^2 = |q|^2 + |c|^2 - 2 q.c of every
+// (query, candidate) pair of the coarsest grid is one entry of a matrix
+// product D = C Q^T with augmented rows
+//     candidate c:  [ c_0..c_47,  P(|c|^2),  1, 1, 1,  0 ... ]
+//     query q:      [ -2q_0..-2q_47,  1, 1, 1,  P(|q|^2),  0 ... ]
+// where P(n) = (n & 0xff0000, n & 0xff00, n & 0xff) splits a norm
+// (< 2^20) into three parts of at most 8 significant bits.  Every entry is
+// an integer that bf16 holds exactly, every product and partial sum is an
+// integer below 2^22 in magnitude, so the fp32 accumulation gives the exact
+// distance whatever the order of its sums.  K = 54 is padded to 64.
+//
+// Operands sit in global memory already in the tcgen05 "no swizzle,
+// K-major" shared-memory layout, 128 rows per 16 KB tile: core matrix
+// (row group m, K group k) of 8 rows x 8 bf16 at byte
+//     k * kTcKGroupStride + m * 128 + (row % 8) * 16 + (col % 8) * 2,
+// so one bulk copy moves a tile.
+constexpr int kTcRows = 128;                        // candidates per tile (M) = queries per CTA (N)
+constexpr int kTcK = 64;                            // augmented row length (bf16)
+constexpr int kTcTileBytes = kTcRows * kTcK * 2;    // 16 KB
+constexpr int kTcKGroupStride = kTcRows * 16;       // bytes between K groups of 8 columns
+constexpr int kTcStages = 6;                        // candidate tiles in shared memory
+constexpr int kTcAcc = 4;                           // fp32 accumulators in tensor memory
+constexpr int kTcScanWarps = 16;                    // warps reading the accumulators
+constexpr int kTcScanCols = kTcRows * 4 / kTcScanWarps;  // query columns per scanning warp (32)
+constexpr int kTcMmaWarp = kTcScanWarps;            // issues the MMAs
+constexpr int kTcTmaWarp = kTcScanWarps + 1;        // issues the bulk copies
+constexpr int kTcThreads = (kTcScanWarps + 2) * 32;
+static_assert(kTcScanCols == 32, "one 32-column TMEM load per warp and step");
+constexpr int kTcCols = kTcAcc * kTcRows;           // TMEM columns (all 512)
+// instruction descriptor, kind::f16: fp32 D (bits 4-5 = 1), bf16 A (7-9 = 1)
+// and B (10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kTcRows >> 3) << 17) |
+                              ((uint32_t)(kTcRows >> 4) << 24);
+// shared memory: queries | candidate stages | scratch (bucket minima, then
+// the per-lane-group candidate buffers) | limits | counts | barriers
+constexpr int kTcOffQ = 0;
+constexpr int kTcOffA = kTcOffQ + kTcTileBytes;
+constexpr int kTcOffScratch = kTcOffA + kTcStages * kTcTileBytes;
+constexpr int kTcMinStride = kTcRows + 1;                         // padded row: conflict-free both ways
+constexpr int kTcScratchBytes = kTcRows * kTcMinStride * 4;      // [query][bucket] minima
+constexpr int kTcCap = 16;                                       // buffered candidates per (lane group, query)
+constexpr int kTcOffLim = kTcOffScratch + kTcScratchBytes;
+constexpr int kTcOffCnt = kTcOffLim + 4 * kTcRows * 4;
+constexpr int kTcOffBar = kTcOffCnt + 4 * kTcRows * 4;
+constexpr int kTcSmemBytes = kTcOffBar + 256 + 1024;            // + alignment slack
+static_assert(4 * kTcRows * kTcCap * 8 <= kTcScratchBytes, "candidate buffers fit the scratch");
+constexpr unsigned kInfBits = 0x7f800000u;   // +inf
+constexpr int kMaxFiniteBits = 0x7f7fffff;   // largest finite float
+
+__host__ __device__ __forceinline__ int tc_rows(int gq) { return (gq + kTcRows - 1) / kTcRows * kTcRows; }
+
+// Writes the augmented bf16 rows of the reference (role 0: queries) and
+// temporal (role 1: candidates) coarsest-grid points; rows past gq are zero.
+// One thread per 8-column group of a row.
 __global__ void k_gather_grid(const __grid_constant__ Fields F, int n) {
     const Field& A = pick(F);
     const int role = blockIdx.y;
-    const Plane& P = role ? A.V.tmp : A.V.ref;
+    const int rows = tc_rows(A.gq);
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int c = t >> 2, part = t & 3;
-    if (c >= A.gq) return;
-    const size_t i = pix(A.V.w, (c % A.gw) * n, (c / A.gw) * n);
-    const size_t slot = (size_t)role * A.gq_pad + c;
-    if (part < 3)
-        reinterpret_cast<int4*>(A.cf + slot * kFeat)[part] =
-            __ldg(reinterpret_cast<const int4*>(P.f + i * kFeat) + part);
-    else
-        A.cn[slot] = __ldg(P.nrm + i);
+    const int r = t >> 3, kg = t & 7;
+    if (r >= rows) return;
+    float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (r < A.gq) {
+        const Plane& P = role ? A.V.tmp : A.V.ref;
+        const size_t i = pix(A.V.w, (r % A.gw) * n, (r / A.gw) * n);
+        if (kg < 6) {
+            const int2 f = __ldg(reinterpret_cast<const int2*>(P.f + i * kFeat) + kg);
+            const int8_t* b = reinterpret_cast<const int8_t*>(&f);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = role ? (float)b[k] : (float)(-2 * b[k]);
+        } else if (kg == 6) {
+            const int nr = __ldg(P.nrm + i);
+            const float p2 = (float)(nr & 0xff0000), p1 = (float)(nr & 0xff00), p0 = (float)(nr & 0xff);
+            const int norm_at = role ? 0 : 3;  // candidates: norm then ones; queries: ones then norm
+            v[norm_at] = p2;
+            v[norm_at + 1] = p1;
+            v[norm_at + 2] = p0;
+            v[3 - norm_at] = v[4 - norm_at] = v[5 - norm_at] = 1.f;
+        }
+    }
+    uint32_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+        w[k] = *reinterpret_cast<const uint32_t*>(&h);
+    }
+    uint8_t* base = A.tk + (size_t)role * rows * (kTcK * 2);
+    const size_t off = (size_t)(r / kTcRows) * kTcTileBytes + (size_t)kg * kTcKGroupStride + ((r % kTcRows) >> 3) * 128 +
+                       (r & 7) * 16;
+    *reinterpret_cast<uint4*>(base + off) = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-// TMA (bulk-copy) helpers: 1-D global -> shared copies completing on an
-// mbarrier.  Addresses and sizes are multiples of 16 bytes.
+// mbarrier and bulk-copy helpers.  Addresses and sizes are multiples of 16 bytes.
 __device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
@@ -135,6 +183,10 @@ __device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                  : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
@@ -165,143 +217,405 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
 
 __device__ unsigned int g_wait_timeouts;  // bounded waits that gave up (read by sff_device_timeouts)
 
-// Upper bound of each query's 8th-nearest temporal distance: the 8th
-// smallest distance among 25 distinct coarsest-grid points around the
-// query's own position (a 5x5 window shifted inside the grid).  Eight real
-// candidates lie at or below it, so the true 8th-nearest distance does too
-// and k_knn can skip every candidate above it.  INT32_MAX (no bound) when
-// the grid has fewer than 8 points in the window.  One warp per query.
-__global__ void k_knn_bound(const __grid_constant__ Fields F, int n) {
-    const Field& A = pick(F);
-    const int qi = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
-    if (qi >= A.gq) return;  // warp-uniform
-    const int gw = A.gw, gh = A.gh;
-    const int gx = qi % gw, gy = qi / gw;
-    const int ww = min(5, gw), wh = min(5, gh);
-    const int ox = clampi(gx - 2, 0, gw - ww), oy = clampi(gy - 2, 0, gh - wh);
-    RefFeat r;
-    load_ref(A.V.ref, pix(A.V.w, gx * n, gy * n), r);
-    int d = 0x7fffffff;
-    if (lane < ww * wh) d = ssd_at(r, A.V.tmp, pix(A.V.w, (ox + lane % ww) * n, (oy + lane / ww) * n));
-    int t = 0x7fffffff;
-    if (ww * wh >= 8) {
-#pragma unroll 1
-        for (int k = 0; k < 8; ++k) {  // remove the smallest 7 times; the 8th minimum is the bound
-            int m = d;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
-            t = m;
-            const unsigned who = __ballot_sync(0xffffffffu, d == m);
-            if (lane == __ffs(who) - 1) d = 0x7fffffff;
-        }
-    }
-    if (lane == 0) A.bound[qi] = t;
+// tcgen05 helpers (tensor memory, MMA, commit, loads).
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
 }
 
-// Temporal K-NN of one query per warp over all candidates.  The candidate
-// records stream through two shared-memory tiles filled by bulk copies
-// (thread 0 issues tile t+1 while tile t is scored); the 8 queries of a CTA
-// share them.  Lane l scores candidate l of each batch of 32 (12 dp4a); a
-// ballot against the query's current 8th-best distance, capped from the
-// start by the bound of k_knn_bound, keeps the rare candidates that enter;
-// each is inserted into the sorted top-8 held by lanes 0-7 with warp-uniform
-// shuffles.  Candidates are visited in increasing index, so a strictly
-// smaller distance is the only way in, exactly as in the (distance, index)
-// order, and every candidate above the bound is provably not among the 8.
-__global__ void __launch_bounds__(kKnnThreads) k_knn(const __grid_constant__ Fields F) {
-    __shared__ __align__(128) int4 tile[2][kKnnTile][3];
-    __shared__ __align__(16) int tnorm[2][kKnnTile];
-    __shared__ __align__(8) uint64_t bar[2];
-    __shared__ int s_fail;
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// shared-memory matrix descriptor: start, leading (K-direction) and stride
+// (row-group) byte offsets, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+
+// 32 lanes x 32 consecutive columns: thread t gets lane (base + t).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32], int o) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+        "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr + (uint32_t)o));
+}
+
+// Waits for the warp's tensor-memory loads; the registers are operands so
+// that no use of them moves above the wait.
+__device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+                 :
+                 : "memory");
+}
+
+// Reduces a buffer of `cnt` (<= kTcCap) candidates of one (lane group,
+// query) to its 8 best in (distance, index) order, at the front in order;
+// returns the limit they imply: the float bits just below the 8th distance
+// (a candidate that comes later has a larger index, so it needs a strictly
+// smaller distance).  The whole warp calls it.
+__device__ __forceinline__ int tc_compact(int2* buf, int cnt, int lane) {
+    const int2 x = lane < cnt ? buf[lane] : make_int2(0x7fffffff, 0x7fffffff);
+    int rank = 0;
+#pragma unroll
+    for (int m = 0; m < kTcCap; ++m) {
+        const int od = __shfl_sync(0xffffffffu, x.x, m), oi = __shfl_sync(0xffffffffu, x.y, m);
+        rank += m < cnt && (od < x.x || (od == x.x && oi < x.y));
+    }
+    __syncwarp();
+    if (lane < cnt && rank < 8) buf[rank] = x;
+    const unsigned at7 = __ballot_sync(0xffffffffu, lane < cnt && rank == 7);
+    const int d7 = __shfl_sync(0xffffffffu, x.x, at7 ? __ffs(at7) - 1 : 0);
+    __syncwarp();
+    return at7 ? __float_as_int((float)d7) - 1 : 0x7fffffff;
+}
+
+// Appends the lanes of `enter` (lane order = increasing candidate index) to
+// a full-enough buffer, compacting it to its 8 best whenever it fills;
+// every compaction lowers the limit, which drops the lanes no longer
+// within it.  Rare: only when a column brings more candidates than the
+// buffer holds (ties at the bound).
+__device__ __noinline__ void tc_append_slow(unsigned enter, int mine, int idx, int cnt, int2* buf, int* cntp, int* limp,
+                                            int lane) {
+    const unsigned lt = (1u << lane) - 1u;
+    while (enter) {
+        const int room = kTcCap - cnt;
+        const bool mine_in = (enter >> lane) & 1u;
+        const int rank = __popc(enter & lt);
+        if (mine_in && rank < room) buf[cnt + rank] = make_int2((int)__int_as_float(mine), idx);
+        const int took = min(room, __popc(enter));
+        enter = __ballot_sync(0xffffffffu, mine_in && rank >= room);
+        cnt += took;
+        __syncwarp();
+        if (cnt == kTcCap) {
+            const int nl = tc_compact(buf, cnt, lane);
+            cnt = 8;
+            const int l = min(*limp, nl);
+            __syncwarp();
+            if (lane == 0) *limp = l;
+            enter &= __ballot_sync(0xffffffffu, mine <= l);
+        }
+    }
+    __syncwarp();
+    if (lane == 0) *cntp = cnt;
+    __syncwarp();
+}
+
+// Bounded wait on an accumulator for a whole warp (lane 0 polls); false
+// (and the CTA's failure flag raised) on a timeout or when another warp
+// already failed.
+__device__ __forceinline__ bool scan_wait(uint64_t* bar, unsigned parity, volatile int* fail, int lane) {
+    bool ok = true;
+    if (lane == 0) ok = mbar_wait(bar, parity) && *fail == 0;
+    const bool failed = __shfl_sync(0xffffffffu, (int)ok, 0) == 0;
+    if (failed && lane == 0) {
+        *fail = 1;
+        atomicAdd(&g_wait_timeouts, 1u);
+    }
+    return !failed;
+}
+
+// Reads the warp's 32 candidates x 32 queries of accumulator b and releases it.
+__device__ __forceinline__ void scan_load(uint32_t trow, int b, uint32_t (&v)[32], uint64_t* bar_free, int lane) {
+    tc_fence_after();
+    tmem_ld32(trow + (uint32_t)(b * kTcRows), v, 0);
+    tmem_ld_wait(v);
+    tc_fence_before();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&bar_free[b]);
+}
+
+// Temporal K-NN of the kTcRows queries of one CTA over every candidate of
+// the field, exact in (distance, candidate index) order.
+//
+// Warp 17 streams candidate tiles into kTcStages shared-memory stages with
+// bulk copies; warp 16 issues, per tile, four M128 N128 K16 MMAs into one of
+// kTcAcc TMEM accumulators (rows = candidates, columns = queries) and
+// commits them to the accumulator's and the stage's barriers.  Warps 0-15
+// read an accumulator (warp w: lanes 32 (w % 4).., query columns
+// 32 (w / 4)..), release it and scan it while the MMAs of the next tiles
+// run.  Every tile is visited twice:
+//   pass 1: each lane keeps, per query, the minimum over its candidates
+//           ("bucket" = candidate index mod 128); the 8th smallest of the
+//           128 bucket minima is reached by 8 distinct candidates, so it
+//           bounds the query's 8th-nearest distance from above -- exactly
+//           it, unless two of the 8 nearest share a bucket;
+//   pass 2: candidates within the bound are appended to a buffer per lane
+//           group and query (compacted to its 8 best if it fills, which
+//           lowers the limit); the four buffers of a query are merged at
+//           the end.
+// Every wait is bounded; a timeout raises the CTA's failure flag, after
+// which the warps skip their work but still reach every barrier, and the
+// copy and MMA threads let their work in flight land before the tensor
+// memory is released.
+__global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const __grid_constant__ Fields F) {
+    extern __shared__ uint8_t smem_raw[];
     const Field& A = pick(F);
     const int gq = A.gq;
-    if ((int)blockIdx.x * kKnnWarps >= gq) return;  // CTA beyond this field's queries
-    const int lane = threadIdx.x & 31;
-    const int qi = blockIdx.x * kKnnWarps + (threadIdx.x >> 5);
-    const bool active = qi < gq;  // warp-uniform
-    const uint8_t* tf = A.cf + (size_t)A.gq_pad * kFeat;  // role 1: candidates
-    const int* tn = A.cn + A.gq_pad;
-    RefFeat r;
-    int lim = 0x7fffffff;
-    if (active) {
-        const int4* p = reinterpret_cast<const int4*>(A.cf + (size_t)qi * kFeat);  // role 0: queries
-        const int4 q0 = __ldg(p), q1 = __ldg(p + 1), q2 = __ldg(p + 2);
-        r.a[0] = q0.x; r.a[1] = q0.y; r.a[2] = q0.z; r.a[3] = q0.w;
-        r.a[4] = q1.x; r.a[5] = q1.y; r.a[6] = q1.z; r.a[7] = q1.w;
-        r.a[8] = q2.x; r.a[9] = q2.y; r.a[10] = q2.z; r.a[11] = q2.w;
-        r.n = __ldg(A.cn + qi);
-        const int b = A.bound[qi];
-        lim = b == 0x7fffffff ? b : b + 1;  // distances <= bound may enter
-    }
-    const int ntiles = (gq + kKnnTile - 1) / kKnnTile;
-    // copy sizes: whole records, rounded up to 4 records (16-byte multiples);
-    // the arrays carry that padding
-    auto issue = [&](int t) {
-        const int base = t * kKnnTile;
-        const int cnt4 = (min(kKnnTile, gq - base) + 3) & ~3;
-        const unsigned fb = (unsigned)cnt4 * kFeat, nbytes = (unsigned)cnt4 * 4;
-        mbar_expect_tx(&bar[t & 1], fb + nbytes);
-        bulk_copy_g2s(&tile[t & 1][0][0], tf + (size_t)base * kFeat, fb, &bar[t & 1]);
-        bulk_copy_g2s(&tnorm[t & 1][0], tn + base, nbytes, &bar[t & 1]);
-    };
+    const int q0 = blockIdx.x * kTcRows;
+    if (q0 >= gq) return;  // CTA-uniform, before any barrier or allocation
+    uint8_t* sm = smem_raw + ((1024 - (smem_addr(smem_raw) & 1023)) & 1023);
+    uint8_t* sQ = sm + kTcOffQ;
+    uint8_t* sA = sm + kTcOffA;
+    int* scratch = reinterpret_cast<int*>(sm + kTcOffScratch);
+    int* lim = reinterpret_cast<int*>(sm + kTcOffLim);  // [4 lane groups][kTcRows queries]
+    int* count = reinterpret_cast<int*>(sm + kTcOffCnt);  // [4 lane groups][kTcRows queries]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kTcOffBar);
+    uint64_t* bar_q = bars;
+    uint64_t* bar_a = bars + 1;                                  // [kTcStages] tile landed
+    uint64_t* bar_empty = bars + 1 + kTcStages;                  // [kTcStages] tile read by its MMAs
+    uint64_t* bar_mma = bars + 1 + 2 * kTcStages;                // [kTcAcc] accumulator written
+    uint64_t* bar_free = bars + 1 + 2 * kTcStages + kTcAcc;      // [kTcAcc] accumulator read
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 1 + 2 * kTcStages + 2 * kTcAcc);
+    volatile int* fail = reinterpret_cast<volatile int*>(bars + 2 + 2 * kTcStages + 2 * kTcAcc);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nt = (gq + kTcRows - 1) / kTcRows;  // candidate tiles
+    const int steps = 2 * nt;                      // two passes
+    const int rows = nt * kTcRows;
+    const uint8_t* gQ = A.tk + (size_t)q0 * (kTcK * 2);
+    const uint8_t* gC = A.tk + (size_t)rows * (kTcK * 2);
+
     if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
-        mbar_fence_init();
-        s_fail = 0;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) issue(0);
-    int ld = 0x7fffffff, li = 0x7fffffff;  // entry `lane` of the sorted top-8 (lanes 0-7)
-    int thr = lim;
-    for (int t = 0; t < ntiles; ++t) {
-        const int buf = t & 1;
-        // the other buffer was released by the __syncthreads that ended tile t-1
-        if (threadIdx.x == 0 && t + 1 < ntiles) issue(t + 1);
-        if (!mbar_wait(&bar[buf], (unsigned)(t >> 1) & 1u)) s_fail = 1;
-        if (__syncthreads_or(s_fail)) {
-            if (threadIdx.x == 0) {
-                atomicAdd(&g_wait_timeouts, 1u);
-                // let the copy issued for the next tile land (bounded) before the CTA exits
-                if (t + 1 < ntiles) mbar_wait(&bar[buf ^ 1], (unsigned)((t + 1) >> 1) & 1u);
-            }
-            return;
+        mbar_init(bar_q, 1);
+        for (int s = 0; s < kTcStages; ++s) {
+            mbar_init(&bar_a[s], 1);
+            mbar_init(&bar_empty[s], 1);
         }
-        const int base = t * kKnnTile;
-        const int cnt = min(kKnnTile, gq - base);
-        if (active) {
-            const int4(*tl)[3] = tile[buf];
-            const int* tnm = tnorm[buf];
-#pragma unroll 2
-            for (int b = 0; b < cnt; b += 32) {
-                const int k = b + lane;
-                const int d = k < cnt ? r.n + tnm[k] - 2 * dot12(r.a, tl[k][0], tl[k][1], tl[k][2]) : 0x7fffffff;
-                unsigned enter = __ballot_sync(0xffffffffu, d < thr);
-                while (enter) {
-                    const int src = __ffs(enter) - 1;
-                    enter &= enter - 1;
-                    const int nd = __shfl_sync(0xffffffffu, d, src);
-                    if (nd >= thr) continue;  // the threshold moved meanwhile
-                    const int ni = base + b + src;
-                    // entries are earlier candidates: (d, index) order is d order with ties kept
-                    const int pos = __popc(__ballot_sync(0xffffffffu, lane < 8 && ld <= nd));
-                    const int pd = __shfl_up_sync(0xffffffffu, ld, 1), pi = __shfl_up_sync(0xffffffffu, li, 1);
-                    if (lane < 8) {
-                        if (lane > pos) {
-                            ld = pd;
-                            li = pi;
-                        } else if (lane == pos) {
-                            ld = nd;
-                            li = ni;
-                        }
-                    }
-                    thr = min(lim, __shfl_sync(0xffffffffu, ld, 7));
+        for (int b = 0; b < kTcAcc; ++b) {
+            mbar_init(&bar_mma[b], 1);
+            mbar_init(&bar_free[b], kTcScanWarps);
+        }
+        *fail = 0;
+        mbar_fence_init();
+    }
+    if (warp == kTcMmaWarp) tmem_alloc(tmem_slot, kTcCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == kTcTmaWarp) {
+        // ---- bulk copies (one thread): the queries once, then the
+        // candidate tiles of both passes through the stages
+        if (lane == 0) {
+            mbar_expect_tx(bar_q, kTcTileBytes);
+            bulk_copy_g2s(sQ, gQ, kTcTileBytes, bar_q);
+            int issued = 0;
+            bool ok = true;
+            for (; issued < steps; ++issued) {
+                const int u = issued, s = u % kTcStages;
+                if (u >= kTcStages &&
+                    (*fail || !(ok = mbar_wait(&bar_empty[s], (unsigned)((u - kTcStages) / kTcStages) & 1u))))
+                    break;
+                mbar_expect_tx(&bar_a[s], kTcTileBytes);
+                bulk_copy_g2s(sA + s * kTcTileBytes, gC + (size_t)(u % nt) * kTcTileBytes, kTcTileBytes, &bar_a[s]);
+            }
+            if (!ok) {
+                *fail = 1;
+                atomicAdd(&g_wait_timeouts, 1u);
+            }
+            // let the copies in flight land before the CTA releases its memory
+            mbar_wait(bar_q, 0);
+            for (int u = max(0, issued - kTcStages); u < issued; ++u)
+                mbar_wait(&bar_a[u % kTcStages], (unsigned)(u / kTcStages) & 1u);
+        }
+        __syncwarp();
+    } else if (warp == kTcMmaWarp) {
+        // ---- MMAs (one thread)
+        if (lane == 0) {
+            int committed = 0;
+            bool ok = mbar_wait(bar_q, 0);
+            const uint32_t qaddr = smem_addr(sQ);
+            for (int u = 0; ok && u < steps; ++u) {
+                if (*fail) {
+                    ok = false;
+                    break;
+                }
+                const int s = u % kTcStages, b = u % kTcAcc;
+                if (!(ok = mbar_wait(&bar_a[s], (unsigned)(u / kTcStages) & 1u))) break;
+                if (u >= kTcAcc && !(ok = mbar_wait(&bar_free[b], (unsigned)((u - kTcAcc) / kTcAcc) & 1u))) break;
+                tc_fence_after();
+                const uint32_t aaddr = smem_addr(sA + s * kTcTileBytes);
+#pragma unroll
+                for (int kk = 0; kk < kTcK / 16; ++kk)
+                    tc_mma(tmem + (uint32_t)(b * kTcRows), smem_desc(aaddr + kk * 2 * kTcKGroupStride, kTcKGroupStride, 128),
+                           smem_desc(qaddr + kk * 2 * kTcKGroupStride, kTcKGroupStride, 128), kTcIdesc, kk > 0);
+                tc_commit(&bar_mma[b]);
+                tc_commit(&bar_empty[s]);
+                committed = u + 1;
+            }
+            if (!ok) {
+                *fail = 1;
+                atomicAdd(&g_wait_timeouts, 1u);
+            }
+            // the MMAs in flight finish before the tensor memory is released
+            if (committed > 0)
+                mbar_wait(&bar_mma[(committed - 1) % kTcAcc], (unsigned)((committed - 1) / kTcAcc) & 1u);
+        }
+        __syncwarp();
+    } else {
+        // ---- scanners: warp w reads TMEM lanes 32 (w % 4).. (its candidates)
+        // and query columns 32 (w / 4)..
+        const int g = warp & 3, h = warp >> 2;
+        const uint32_t trow = tmem + ((uint32_t)(32 * g) << 16) + (uint32_t)(kTcScanCols * h);
+        const int qc = kTcScanCols * h;  // first query column of the warp
+        int* mylim = lim + g * kTcRows + qc;
+        int* mycnt = count + g * kTcRows + qc;
+        int2* bufs = reinterpret_cast<int2*>(scratch);  // [4][kTcRows][kTcCap] in pass 2
+        int2* mybuf = bufs + ((size_t)g * kTcRows + qc) * kTcCap;
+        bool live = true;
+        {
+            // pass 1: bucket minima
+            uint32_t mins[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) mins[j] = kInfBits;
+            for (int u = 0; u < nt && live; ++u) {
+                if (!(live = scan_wait(&bar_mma[u % kTcAcc], (unsigned)(u / kTcAcc) & 1u, fail, lane))) break;
+                uint32_t v[32];
+                scan_load(trow, u % kTcAcc, v, bar_free, lane);
+                if (u * kTcRows + 32 * g + lane < gq) {  // not a padding row of the last tile
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) mins[j] = min(mins[j], v[j]);  // unsigned: a -0 never lowers a bound
                 }
             }
+#pragma unroll
+            for (int j = 0; j < 32; ++j) scratch[(qc + j) * kTcMinStride + 32 * g + lane] = (int)mins[j];
         }
-        __syncthreads();
+        asm volatile("bar.sync 1, %0;" ::"r"(kTcScanWarps * 32) : "memory");
+        {
+            // bounds: four threads per query, each the 8 smallest of 32 bucket
+            // minima (branch-free sorted insertion), then two merges; the 8th
+            // smallest of the 128 is the inclusive bound
+            const int q = threadIdx.x >> 2, part = threadIdx.x & 3;
+            uint32_t a[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) a[k] = 0xffffffffu;
+            const int* row = scratch + q * kTcMinStride + 32 * part;
+#pragma unroll 8
+            for (int i = 0; i < 32; ++i) {
+                uint32_t x = (uint32_t)row[i];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const uint32_t lo = min(a[k], x);
+                    x = max(a[k], x);
+                    a[k] = lo;
+                }
+            }
+#pragma unroll
+            for (int o = 1; o <= 2; o <<= 1) {
+                uint32_t b8[8];
+#pragma unroll
+                for (int k = 0; k < 8; ++k) b8[k] = __shfl_xor_sync(0xffffffffu, a[k], o);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    uint32_t x = b8[i];
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const uint32_t lo = min(a[k], x);
+                        x = max(a[k], x);
+                        a[k] = lo;
+                    }
+                }
+            }
+            // capped below +inf so that padding never enters
+            lim[part * kTcRows + q] = (int)min(a[7], (uint32_t)kMaxFiniteBits);
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(kTcScanWarps * 32) : "memory");
+        for (int e = threadIdx.x; e < 4 * kTcRows * kTcCap; e += kTcScanWarps * 32)
+            bufs[e] = make_int2(0x7fffffff, 0x7fffffff);
+        for (int e = threadIdx.x; e < 4 * kTcRows; e += kTcScanWarps * 32) count[e] = 0;
+        asm volatile("bar.sync 1, %0;" ::"r"(kTcScanWarps * 32) : "memory");
+        // pass 2: every candidate within its query's limit goes to the
+        // buffer of (lane group, query), in increasing index order
+        const unsigned lt = (1u << lane) - 1u;
+        for (int u = nt; u < steps && live; ++u) {
+            if (!(live = scan_wait(&bar_mma[u % kTcAcc], (unsigned)(u / kTcAcc) & 1u, fail, lane))) break;
+            uint32_t v[32];
+            scan_load(trow, u % kTcAcc, v, bar_free, lane);
+            const int idx = (u - nt) * kTcRows + 32 * g + lane;
+            unsigned m = 0;  // columns where this lane's candidate is within the limit
+            if (idx < gq) {  // not a padding row of the last tile
+#pragma unroll
+                for (int j = 0; j < 32; j += 4) {
+                    const int4 l4 = *reinterpret_cast<const int4*>(mylim + j);
+                    m |= (unsigned)((int)v[j] <= l4.x) << j | (unsigned)((int)v[j + 1] <= l4.y) << (j + 1) |
+                         (unsigned)((int)v[j + 2] <= l4.z) << (j + 2) | (unsigned)((int)v[j + 3] <= l4.w) << (j + 3);
+                }
+            }
+            unsigned cols = __reduce_or_sync(0xffffffffu, m);
+            while (cols) {
+                const int j = __ffs(cols) - 1;
+                cols &= cols - 1;
+                int mine = (int)v[0];
+#pragma unroll
+                for (int k = 1; k < 32; ++k) mine = j == k ? (int)v[k] : mine;
+                const unsigned ent = __ballot_sync(0xffffffffu, (m >> j) & 1u);
+                const int c = mycnt[j];
+                if (c + __popc(ent) <= kTcCap) {
+                    if ((m >> j) & 1u) mybuf[j * kTcCap + c + __popc(ent & lt)] = make_int2((int)__int_as_float(mine), idx);
+                    if (lane == 0) mycnt[j] = c + __popc(ent);
+                } else {
+                    tc_append_slow(ent, mine, idx, c, mybuf + j * kTcCap, mycnt + j, mylim + j, lane);
+                }
+            }
+            __syncwarp();
+        }
+        // each buffer holding more than 8 candidates down to its 8 best
+        for (int j = 0; j < kTcScanCols; ++j) {
+            const int c = mycnt[j];
+            if (c > 8) tc_compact(mybuf + j * kTcCap, c, lane);
+        }
+        // ---- merge the four lane-group buffers (8 best each, in any order)
+        // of each query (warp w: kTcRows / kTcScanWarps queries)
+        asm volatile("bar.sync 1, %0;" ::"r"(kTcScanWarps * 32) : "memory");
+        if (live) {
+            for (int qq = 0; qq < kTcRows / kTcScanWarps; ++qq) {
+                const int q = warp * (kTcRows / kTcScanWarps) + qq;
+                if (q0 + q >= gq) break;
+                const int2 e = bufs[((size_t)(lane >> 3) * kTcRows + q) * kTcCap + (lane & 7)];
+                int rank = 0;
+#pragma unroll
+                for (int o = 0; o < 32; ++o) {
+                    const int od = __shfl_sync(0xffffffffu, e.x, o), oi = __shfl_sync(0xffffffffu, e.y, o);
+                    rank += (od < e.x) || (od == e.x && (oi < e.y || (oi == e.y && o < lane)));
+                }
+                if (rank < 8) A.best8[(size_t)(q0 + q) * 8 + rank] = e;
+            }
+        }
     }
-    if (active && lane < 8) A.best8[(size_t)qi * 8 + lane] = make_int2(ld, li);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == kTcMmaWarp) tmem_dealloc(tmem, kTcCols);
 }
 
 // Nearest grid point of row y by (distance, x), constrained by sigma, found by
@@ -735,22 +1049,18 @@ int coarse_gq(int w, int h, const sff_params& p) {
     return ((w + n - 1) / n) * ((h + n - 1) / n);
 }
 
-// Scratch of one field: K-NN lists and compact coarsest-grid records, then a
-// second state buffer (field + cost) for the double-buffered iterations.
-// Compact rows are padded to a multiple of 4 records plus 4, so every bulk
-// copy (whole groups of 4 records) starts and ends on 16 bytes.
-int gq_padded(int gq) { return ((gq + 3) & ~3) + 4; }
+// Scratch of one field: K-NN lists and the augmented coarsest-grid rows
+// (whole 16 KB tiles, so every bulk copy starts and ends on 16 bytes), then
+// a second state buffer (field + cost) for the double-buffered iterations.
 struct FieldScratch {
-    size_t best8, cf, cn, bound, field, cost, total;
+    size_t best8, tk, field, cost, total;
 };
 FieldScratch field_scratch(int w, int h, const sff_params& p) {
-    const int gq = coarse_gq(w, h, p), gp = gq_padded(gq);
+    const int gq = coarse_gq(w, h, p);
     FieldScratch f;
     f.best8 = 0;
-    f.cf = f.best8 + align256((size_t)gq * 8 * sizeof(int2));
-    f.cn = f.cf + align256((size_t)2 * gp * kFeat);
-    f.bound = f.cn + align256((size_t)2 * gp * sizeof(int));
-    f.field = f.bound + align256((size_t)gq * sizeof(int));
+    f.tk = f.best8 + align256((size_t)gq * 8 * sizeof(int2));
+    f.field = f.tk + align256((size_t)2 * tc_rows(gq) * kTcK * 2);
     f.cost = f.field + align256((size_t)w * h * 8);
     f.total = f.cost + align256((size_t)w * h * 4);
     return f;
@@ -762,6 +1072,21 @@ size_t field_ws_bytes(int w, int h, const sff_params& p) { return field_scratch(
 
 // Workspace of sff_match_views / sff_match_quad: the scratch of two fields.
 size_t match_ws_bytes(int w, int h, const sff_params& p) { return 2 * field_ws_bytes(w, h, p); }
+
+// Opts k_knn_tc into its dynamic shared memory, once per device.
+bool knn_smem_ready() {
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done[dev]) {
+        if (cudaFuncSetAttribute(k_knn_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemBytes) != cudaSuccess)
+            return false;
+        done[dev] = true;
+    }
+    return true;
+}
 
 // The stage of Sec. 3.1 for nf <= kMaxFields fields (any sizes) sharing the
 // launches.  spec[k].workspace holds field_ws_bytes() of scratch.
@@ -783,11 +1108,8 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
         const FieldScratch sc = field_scratch(fs.width, fs.height, P);
         char* ws = reinterpret_cast<char*>(fs.workspace);
         F.f[k].best8 = reinterpret_cast<int2*>(ws + sc.best8);
-        F.f[k].cf = reinterpret_cast<uint8_t*>(ws + sc.cf);
-        F.f[k].cn = reinterpret_cast<int*>(ws + sc.cn);
-        F.f[k].bound = reinterpret_cast<int*>(ws + sc.bound);
+        F.f[k].tk = reinterpret_cast<uint8_t*>(ws + sc.tk);
         F.f[k].gq = coarse_gq(fs.width, fs.height, P);
-        F.f[k].gq_pad = gq_padded(F.f[k].gq);
         F.f[k].mirror = fs.mirror;
         F.f[k].key = make_uint2((uint32_t)fs.seed, (uint32_t)(fs.seed >> 32));
         U[k] = reinterpret_cast<uint2*>(fs.field);
@@ -812,12 +1134,11 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
             mgq = std::max(mgq, F.f[k].gq);
         }
         if (s == S - 1) {
-            dim3 g0((mgq * 4 + 255) / 256, 2, nf);
+            dim3 g0((tc_rows(mgq) * 8 + 255) / 256, 2, nf);
             SFF_LAUNCH(k_gather_grid, g0, 256, 0, st, F, n);
-            dim3 gb((mgq + 7) / 8, 1, nf);
-            SFF_LAUNCH(k_knn_bound, gb, 256, 0, st, F, n);
-            dim3 g1((mgq + kKnnWarps - 1) / kKnnWarps, 1, nf);
-            SFF_LAUNCH(k_knn, g1, kKnnThreads, 0, st, F);
+            if (!knn_smem_ready()) return SFF_ERR_CUDA;
+            dim3 g1((mgq + kTcRows - 1) / kTcRows, 1, nf);
+            SFF_LAUNCH(k_knn_tc, g1, kTcThreads, kTcSmemBytes, st, F);
             dim3 g2((mgq + 7) / 8, 1, nf);
             SFF_LAUNCH(k_init_select, g2, 256, 0, st, F, n, P.knn_temporal);
         } else {
