@@ -61,6 +61,8 @@ struct Field {
     int gq;  // coarsest grid points
     int2* best8;  // [gq][8] temporal top-8 (distance, grid index)
     uint8_t* tk;  // [2 roles][rows] augmented bf16 rows in MMA tile layout: queries, candidates
+    int4* rec;    // [2][gq][3] int8 records of the stereo and cross images' coarsest grid
+    int* rec_n;   // [2][gq] their norms
     uint2 key;  // Philox key: the seed of the field's quad
 };
 
@@ -132,12 +134,27 @@ __host__ __device__ __forceinline__ int tc_rows(int gq) { return (gq + kTcRows -
 
 // Writes the augmented bf16 rows of the reference (role 0: queries) and
 // temporal (role 1: candidates) coarsest-grid points; rows past gq are zero.
-// One thread per 8-column group of a row.
+// One thread per 8-column group of a row.  Roles 2 and 3 copy the stereo
+// and cross images' grid records into compact rows.
 __global__ void k_gather_grid(const __grid_constant__ Fields F, int n) {
     const Field& A = pick(F);
     const int role = blockIdx.y;
     const int rows = tc_rows(A.gq);
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (role >= 2) {
+        // roles 2, 3: compact int8 records of the stereo and cross images
+        // (row-major grid), scanned row by row by k_init_select
+        const int c = t >> 2, part = t & 3;
+        if (c >= A.gq) return;
+        const Plane& P = role == 2 ? A.V.ste : A.V.crs;
+        const size_t i = pix(A.V.w, (c % A.gw) * n, (c / A.gw) * n);
+        const size_t slot = (size_t)(role - 2) * A.gq + c;
+        if (part < 3)
+            A.rec[slot * 3 + part] = __ldg(reinterpret_cast<const int4*>(P.f + i * kFeat) + part);
+        else
+            A.rec_n[slot] = __ldg(P.nrm + i);
+        return;
+    }
     const int r = t >> 3, kg = t & 7;
     if (r >= rows) return;
     float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -618,15 +635,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const __grid_constant_
     if (warp == kTcMmaWarp) tmem_dealloc(tmem, kTcCols);
 }
 
-// Nearest grid point of row y by (distance, x), constrained by sigma, found by
-// one warp: lane l scans grid columns l, l+32, ...; then a warp argmin.
-__device__ __forceinline__ void warp_row_nearest(const RefFeat& r, const Plane& img, int w, int n, int gw, int y,
-                                                 int xlim, int sigma, int lane, int& best_d, int& best_x) {
+// Nearest grid point of grid row gy by (distance, x), constrained by sigma,
+// found by one warp over the compact row (records rec[gy * gw ..]): lane l
+// scans grid columns l, l+32, ...; then a warp argmin.
+__device__ __forceinline__ void warp_row_nearest(const RefFeat& r, const int4* rec, const int* rec_n, int n, int gw,
+                                                 int gy, int xlim, int sigma, int lane, int& best_d, int& best_x) {
     int bd = 0x7fffffff, bx = 0x7fffffff;
+    const int4* row = rec + (size_t)gy * gw * 3;
+    const int* row_n = rec_n + (size_t)gy * gw;
     for (int g = lane; g < gw; g += 32) {
         const int x = g * n;
         if (sigma * (xlim - x) < 0) continue;
-        const int d = ssd_at(r, img, pix(w, x, y));
+        const int4 q0 = __ldg(row + 3 * g), q1 = __ldg(row + 3 * g + 1), q2 = __ldg(row + 3 * g + 2);
+        int dot = 0;
+        dot = __dp4a(r.a[0], q0.x, dot); dot = __dp4a(r.a[1], q0.y, dot);
+        dot = __dp4a(r.a[2], q0.z, dot); dot = __dp4a(r.a[3], q0.w, dot);
+        dot = __dp4a(r.a[4], q1.x, dot); dot = __dp4a(r.a[5], q1.y, dot);
+        dot = __dp4a(r.a[6], q1.z, dot); dot = __dp4a(r.a[7], q1.w, dot);
+        dot = __dp4a(r.a[8], q2.x, dot); dot = __dp4a(r.a[9], q2.y, dot);
+        dot = __dp4a(r.a[10], q2.z, dot); dot = __dp4a(r.a[11], q2.w, dot);
+        const int d = r.n + __ldg(row_n + g) - 2 * dot;
         if (d < bd) {  // ascending x within the lane: ties keep the lower x
             bd = d;
             bx = x;
@@ -664,7 +692,7 @@ __global__ void k_init_select(const __grid_constant__ Fields F, int n, int knn) 
         bi[k] = e.y;
     }
     int ds, sx;
-    warp_row_nearest(r, V.ste, V.w, n, gw, py, px, V.sigma, lane, ds, sx);
+    warp_row_nearest(r, A.rec, A.rec_n, n, gw, qi / gw, px, V.sigma, lane, ds, sx);
     int best_c = 0x7fffffff;
     Vec4 best = {0, 0, 0, 0};
 #pragma unroll
@@ -672,7 +700,7 @@ __global__ void k_init_select(const __grid_constant__ Fields F, int n, int knn) 
         if (k >= knn || bd[k] == 0x7fffffff) break;
         const int tx = (bi[k] % gw) * n, ty = (bi[k] / gw) * n;
         int dxc, cx;
-        warp_row_nearest(r, V.crs, V.w, n, gw, ty, tx, V.sigma, lane, dxc, cx);
+        warp_row_nearest(r, A.rec + (size_t)A.gq * 3, A.rec_n + A.gq, n, gw, bi[k] / gw, tx, V.sigma, lane, dxc, cx);
         const int c = bd[k] + ds + dxc;
         if (c < best_c) {
             best_c = c;
@@ -1020,10 +1048,18 @@ const IterVariant* find_variant(const sff_tuning& t) {
     return nullptr;
 }
 
-// Tile of the iteration kernel at one scale: the tuned tile at scale 0; at
-// coarser scales the tuned tile if it gives at least two CTAs per SM over
-// all fields, else the largest smaller tile (same lanes per pixel) that
-// does, else the smallest.  Any tile gives the same result.
+// Variant of the iteration kernel at one scale.  Scale 0 takes the tuned
+// variant.  A coarser scale is latency-bound: few grid pixels per SM, each a
+// chain of dependent feature loads.  More lanes per pixel put more warps in
+// flight and shorten each lane's chain, so it takes at least 2 lanes below
+// kPixPerSmL1 grid pixels per SM and 4 below kPixPerSmL2 (measured on the
+// 1242x375 driving quad: scale 2 with 385 pixels per SM is fastest with 2
+// lanes, scale 3 with 96 with 4).  The tile is then the tuned tile if it
+// gives at least two CTAs per SM over all fields, else the largest smaller
+// tile that does, else the smallest.  Every variant gives the same result.
+constexpr int kSmCount = 152;
+constexpr long kPixPerSmL1 = 1000, kPixPerSmL2 = 200;
+
 long ctas_for(const IterVariant& v, const int* gw, const int* gh, int nf) {
     long c = 0;
     for (int k = 0; k < nf; ++k) c += (long)((gw[k] + v.tx - 1) / v.tx) * ((gh[k] + v.ty - 1) / v.ty);
@@ -1032,15 +1068,19 @@ long ctas_for(const IterVariant& v, const int* gw, const int* gh, int nf) {
 
 const IterVariant* tile_for_grid(const IterVariant* tuned, int s, const int* gw, const int* gh, int nf) {
     if (s == 0) return tuned;
-    constexpr long kWantCtas = 2 * 152;
+    long px = 0;
+    for (int k = 0; k < nf; ++k) px += (long)gw[k] * gh[k];
+    const long per_sm = px / kSmCount;
+    const int lanes = std::max(tuned->lanes, per_sm >= kPixPerSmL1 ? 1 : per_sm >= kPixPerSmL2 ? 2 : 4);
+    constexpr long kWantCtas = 2 * kSmCount;
     const IterVariant* pick_v = nullptr;
     for (const auto& v : kIterVariants) {
-        if (v.lanes != tuned->lanes || v.tx * v.ty > tuned->tx * tuned->ty) continue;
+        if (v.lanes != lanes || v.tx * v.ty > tuned->tx * tuned->ty) continue;
         if (ctas_for(v, gw, gh, nf) >= kWantCtas && (!pick_v || v.tx * v.ty > pick_v->tx * pick_v->ty)) pick_v = &v;
     }
-    if (pick_v) return (tuned->tx * tuned->ty == pick_v->tx * pick_v->ty) ? tuned : pick_v;
+    if (pick_v) return pick_v;
     for (const auto& v : kIterVariants)  // none fills the GPU: the smallest tile
-        if (v.lanes == tuned->lanes && (!pick_v || v.tx * v.ty < pick_v->tx * pick_v->ty)) pick_v = &v;
+        if (v.lanes == lanes && (!pick_v || v.tx * v.ty < pick_v->tx * pick_v->ty)) pick_v = &v;
     return pick_v;
 }
 
@@ -1053,14 +1093,16 @@ int coarse_gq(int w, int h, const sff_params& p) {
 // (whole 16 KB tiles, so every bulk copy starts and ends on 16 bytes), then
 // a second state buffer (field + cost) for the double-buffered iterations.
 struct FieldScratch {
-    size_t best8, tk, field, cost, total;
+    size_t best8, tk, rec, rec_n, field, cost, total;
 };
 FieldScratch field_scratch(int w, int h, const sff_params& p) {
     const int gq = coarse_gq(w, h, p);
     FieldScratch f;
     f.best8 = 0;
     f.tk = f.best8 + align256((size_t)gq * 8 * sizeof(int2));
-    f.field = f.tk + align256((size_t)2 * tc_rows(gq) * kTcK * 2);
+    f.rec = f.tk + align256((size_t)2 * tc_rows(gq) * kTcK * 2);
+    f.rec_n = f.rec + align256((size_t)2 * gq * kFeat);
+    f.field = f.rec_n + align256((size_t)2 * gq * sizeof(int));
     f.cost = f.field + align256((size_t)w * h * 8);
     f.total = f.cost + align256((size_t)w * h * 4);
     return f;
@@ -1109,6 +1151,8 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
         char* ws = reinterpret_cast<char*>(fs.workspace);
         F.f[k].best8 = reinterpret_cast<int2*>(ws + sc.best8);
         F.f[k].tk = reinterpret_cast<uint8_t*>(ws + sc.tk);
+        F.f[k].rec = reinterpret_cast<int4*>(ws + sc.rec);
+        F.f[k].rec_n = reinterpret_cast<int*>(ws + sc.rec_n);
         F.f[k].gq = coarse_gq(fs.width, fs.height, P);
         F.f[k].mirror = fs.mirror;
         F.f[k].key = make_uint2((uint32_t)fs.seed, (uint32_t)(fs.seed >> 32));
@@ -1134,7 +1178,7 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
             mgq = std::max(mgq, F.f[k].gq);
         }
         if (s == S - 1) {
-            dim3 g0((tc_rows(mgq) * 8 + 255) / 256, 2, nf);
+            dim3 g0((tc_rows(mgq) * 8 + 255) / 256, 4, nf);
             SFF_LAUNCH(k_gather_grid, g0, 256, 0, st, F, n);
             if (!knn_smem_ready()) return SFF_ERR_CUDA;
             dim3 g1((mgq + kTcRows - 1) / kTcRows, 1, nf);
