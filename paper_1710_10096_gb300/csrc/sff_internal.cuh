@@ -57,9 +57,13 @@ __device__ __forceinline__ void load_ref(const Plane& P, size_t i, RefFeat& r) {
 // |a|^2 + |b|^2 - 2 a.b with the dot product on dp4a (exact in int32).
 __device__ __forceinline__ int ssd_at(const RefFeat& r, const Plane& P, size_t i) {
     const int4* p = reinterpret_cast<const int4*>(P.f + i * kFeat);
-    int4 q0 = __ldg(p), q1 = __ldg(p + 1), q2 = __ldg(p + 2);
-    int nb = __ldg(P.nrm + i);
-    int d = 0;
+    const int4 q0 = __ldg(p), q1 = __ldg(p + 1), q2 = __ldg(p + 2);
+    // |b|^2 from the record itself (dp4a, exact): one sector less than
+    // loading it from the norm plane
+    int nb = 0, d = 0;
+    nb = __dp4a(q0.x, q0.x, nb); nb = __dp4a(q0.y, q0.y, nb); nb = __dp4a(q0.z, q0.z, nb); nb = __dp4a(q0.w, q0.w, nb);
+    nb = __dp4a(q1.x, q1.x, nb); nb = __dp4a(q1.y, q1.y, nb); nb = __dp4a(q1.z, q1.z, nb); nb = __dp4a(q1.w, q1.w, nb);
+    nb = __dp4a(q2.x, q2.x, nb); nb = __dp4a(q2.y, q2.y, nb); nb = __dp4a(q2.z, q2.z, nb); nb = __dp4a(q2.w, q2.w, nb);
     d = __dp4a(r.a[0], q0.x, d); d = __dp4a(r.a[1], q0.y, d);
     d = __dp4a(r.a[2], q0.z, d); d = __dp4a(r.a[3], q0.w, d);
     d = __dp4a(r.a[4], q1.x, d); d = __dp4a(r.a[5], q1.y, d);

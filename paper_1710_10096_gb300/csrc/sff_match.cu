@@ -743,26 +743,37 @@ struct HalfStep {
 
 // Pixels are processed by groups of L lanes (L = 1, 2 or 4, a tuning knob
 // that never changes results).  Lane q of a group holds the 16-byte chunks j
-// of a 48-byte record with j % L == q and, on lane 3 % L, the norm; every
-// target record is loaded the same way, so with L = 4 one warp-wide load
-// fetches eight whole records.  Partial sums |a|^2 + |b|^2 - 2 a.b of the
-// three views are combined with log2(L) shuffles inside the group.
+// of a 48-byte record with j % L == q; every target record is loaded the
+// same way, so with L = 4 one warp-wide load fetches eight whole records.
+// The norms are not loaded: each lane computes its chunks' part of |b|^2
+// with dp4a (exact), which saves the norm plane's sector per record -- the
+// iteration kernels are bound by L1 sector traffic, not by issue.  Partial
+// sums |a|^2 + |b|^2 - 2 a.b of the three views are combined with log2(L)
+// shuffles inside the group.
 template <int L>
 struct Slice {
     static constexpr int kChunks = (3 + L - 1) / L;
     int4 c[kChunks];
-    int nrm;  // the norm on lane 3 % L, 0 on the others
+    int nrm;  // this lane's part of the record's squared norm
 };
+
+__device__ __forceinline__ int dot4(const int4& a, const int4& b, int d) {
+    d = __dp4a(a.x, b.x, d);
+    d = __dp4a(a.y, b.y, d);
+    d = __dp4a(a.z, b.z, d);
+    return __dp4a(a.w, b.w, d);
+}
 
 template <int L>
 __device__ __forceinline__ void load_slice(const Plane& P, size_t i, int q, Slice<L>& s) {
     const int4* p = reinterpret_cast<const int4*>(P.f + i * kFeat);
+    s.nrm = 0;
 #pragma unroll
     for (int k = 0; k < Slice<L>::kChunks; ++k) {
         const int j = q + k * L;
         s.c[k] = j < 3 ? __ldg(p + j) : make_int4(0, 0, 0, 0);
+        s.nrm = dot4(s.c[k], s.c[k], s.nrm);
     }
-    s.nrm = q == 3 % L ? __ldg(P.nrm + i) : 0;
 }
 
 template <int L>
@@ -771,12 +782,7 @@ __device__ __forceinline__ int slice_part(const Slice<L>& a, const Plane& P, siz
     load_slice<L>(P, i, q, t);
     int d = 0;
 #pragma unroll
-    for (int k = 0; k < Slice<L>::kChunks; ++k) {
-        d = __dp4a(a.c[k].x, t.c[k].x, d);
-        d = __dp4a(a.c[k].y, t.c[k].y, d);
-        d = __dp4a(a.c[k].z, t.c[k].z, d);
-        d = __dp4a(a.c[k].w, t.c[k].w, d);
-    }
+    for (int k = 0; k < Slice<L>::kChunks; ++k) d = dot4(a.c[k], t.c[k], d);
     return a.nrm + t.nrm - 2 * d;
 }
 
