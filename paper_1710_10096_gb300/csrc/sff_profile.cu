@@ -1,5 +1,9 @@
 // Opt-in per-kernel timing: CUDA events recorded on the launch stream
 // before and after each kernel launch, summed per kernel name on collect.
+// On a stream that is being captured into a CUDA graph the events become
+// event-record nodes of the graph (cudaEventRecordExternal), so a replay
+// times the kernels as the graph runs them, without the host's launch gaps
+// that separate plain launches of short kernels.
 #include <mutex>
 #include <string>
 #include <vector>
@@ -45,14 +49,23 @@ void release_all() {
 
 bool profiling() { return g_on; }
 
+static void record_mark(cudaEvent_t e, cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    if (cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else
+        cudaEventRecord(e, st);
+}
+
 void profile_mark(const char* name, cudaStream_t st, bool after) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (!after) {
         g_pending = take_event();
-        cudaEventRecord(g_pending, st);
+        record_mark(g_pending, st);
     } else {
         cudaEvent_t stop = take_event();
-        cudaEventRecord(stop, st);
+        record_mark(stop, st);
         g_marks.push_back(Mark{name, g_pending, stop});
         g_pending = nullptr;
     }
