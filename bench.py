@@ -38,13 +38,12 @@ L2_FLUSH_BYTES = 256 << 20
 FALLBACK_HBM_GBS = 6800.0
 
 # Algorithmic bytes per unit of work of each kernel (units in `_units`):
-#   k_half_step   per active grid pixel: own + written state 24 B, reference
-#                 record 48 B + norm 4 B, one 52 B target record per view
+#   k_iteration   per grid pixel and iteration (each pixel is updated once
+#                 per iteration): own + written state 24 B, reference record
+#                 48 B + norm 4 B, one 52 B target record per view = 232 B
 #   k_features    per pixel and scale: packed smoothed pixel 4 B in, 48 B
 #                 record + 4 B norm out
-#   k_iteration   per grid pixel and iteration (each pixel is updated once
-#                 per iteration): the same 232 B as one half-step
-ALGO_BYTES = {"k_iteration": 24 + 52 + 3 * 52, "k_half_step": 24 + 52 + 3 * 52, "k_features": 4 + 52}
+ALGO_BYTES = {"k_iteration": 24 + 52 + 3 * 52, "k_features": 4 + 52}
 
 
 def parse():
@@ -157,7 +156,7 @@ def ncu_traffic(kernel: str):
 def _units(kernel: str, w: int, h: int, params) -> float:
     """Units of work of `kernel` in one step (summed over its launches)."""
     S, I = params.num_scales, params.iterations
-    if kernel in ("k_iteration", "k_half_step"):
+    if kernel == "k_iteration":
         # 2 fields x per scale: I iterations, each updating every grid pixel once
         total = 0
         for s in range(S):

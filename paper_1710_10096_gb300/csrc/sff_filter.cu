@@ -85,13 +85,19 @@ __device__ void unite(int* parent, int a, int b) {
 
 constexpr int kTile = 32;  // union-find tile: 32 x 32 pixels, 256 threads
 
+// Root of k with path halving: every visited node is re-pointed to its
+// grandparent.  Parents only ever point to smaller indices of the same
+// component, so a concurrent halving write or link leaves every pointer on an
+// ancestor: the races are benign and pointers only decrease.
 __device__ __forceinline__ int find_local(volatile int* lp, int k) {
-    int p = lp[k];
-    while (p != k) {
-        k = p;
-        p = lp[k];
+    while (true) {
+        const int p = lp[k];
+        if (p == k) return k;
+        const int gp = lp[p];
+        if (gp == p) return p;
+        lp[k] = gp;
+        k = gp;
     }
-    return k;
 }
 
 __device__ void unite_local(int* lp, int a, int b) {
@@ -111,10 +117,17 @@ __device__ void unite_local(int* lp, int a, int b) {
 }
 
 // Components inside one tile in shared memory.  Local indices follow raster
-// order, so a local root is the minimum raster index of its local component;
-// every kept pixel's parent becomes its local root.  Also clears size and
-// joinable for the tile's pixels.
-__global__ void __launch_bounds__(256) k_cc_local(const __grid_constant__ FilterJobs J, int tau_r) {
+// order.  Each kept pixel starts linked to its connected upper neighbour, else
+// its connected left one (both smaller indices), else to itself; a pixel
+// connected both ways then unites the two; finds halve paths.  The minimum
+// raster index of a local component has no connected upper or left
+// neighbour, starts as a root and stays one, since links always go to the
+// smaller root: every kept pixel's parent becomes that minimum.  Also clears
+// size and joinable for the tile's pixels.
+constexpr int kLocalThreads = 256;
+constexpr int kPerThread = kTile * kTile / kLocalThreads;
+
+__global__ void __launch_bounds__(kLocalThreads) k_cc_local(const __grid_constant__ FilterJobs J, int tau_r) {
     __shared__ int lp[kTile * kTile];
     __shared__ uint2 lf[kTile * kTile];
     __shared__ uint8_t lk[kTile * kTile];
@@ -122,31 +135,50 @@ __global__ void __launch_bounds__(256) k_cc_local(const __grid_constant__ Filter
     const int w = Q.w, h = Q.h;
     const int x0 = blockIdx.x * kTile, y0 = blockIdx.y * kTile;
     if (x0 >= w || y0 >= h) return;  // whole CTA beyond this quad
-    for (int k = threadIdx.x; k < kTile * kTile; k += blockDim.x) {
+#pragma unroll
+    for (int j = 0; j < kPerThread; ++j) {
+        const int k = threadIdx.x + j * kLocalThreads;
         const int x = x0 + (k % kTile), y = y0 + (k / kTile);
         const bool inside = x < w && y < h;
         const size_t i = (size_t)y * w + x;
         const bool kk = inside && Q.keep[i];
         lk[k] = kk;
         lf[k] = kk ? Q.fwd[i] : make_uint2(0u, 0u);
-        lp[k] = kk ? k : -1;
         if (inside) {
             Q.size[i] = 0;
             Q.joinable[i] = 0;
         }
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < kTile * kTile; k += blockDim.x) {
-        if (!lk[k]) continue;
+    bool both[kPerThread];
+#pragma unroll
+    for (int j = 0; j < kPerThread; ++j) {
+        const int k = threadIdx.x + j * kLocalThreads;
         const int lx = k % kTile, ly = k / kTile;
-        if (lx + 1 < kTile && lk[k + 1] && close_vec(lf[k], lf[k + 1], tau_r)) unite_local(lp, k, k + 1);
-        if (ly + 1 < kTile && lk[k + kTile] && close_vec(lf[k], lf[k + kTile], tau_r)) unite_local(lp, k, k + kTile);
+        both[j] = false;
+        if (!lk[k]) {
+            lp[k] = -1;
+            continue;
+        }
+        const bool up = ly > 0 && lk[k - kTile] && close_vec(lf[k], lf[k - kTile], tau_r);
+        const bool left = lx > 0 && lk[k - 1] && close_vec(lf[k], lf[k - 1], tau_r);
+        lp[k] = up ? k - kTile : left ? k - 1 : k;
+        both[j] = up && left;
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < kTile * kTile; k += blockDim.x) {
+#pragma unroll
+    for (int j = 0; j < kPerThread; ++j) {
+        const int k = threadIdx.x + j * kLocalThreads;
+        if (both[j]) unite_local(lp, k - 1, k);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kPerThread; ++j) {
+        const int k = threadIdx.x + j * kLocalThreads;
         if (!lk[k]) continue;
         const int r = find_local(lp, k);
-        Q.parent[(size_t)(y0 + k / kTile) * w + x0 + k % kTile] = (y0 + r / kTile) * w + x0 + r % kTile;
+        const int x = x0 + k % kTile, y = y0 + k / kTile;
+        if (x < w && y < h) Q.parent[(size_t)y * w + x] = (y0 + r / kTile) * w + x0 + r % kTile;
     }
 }
 

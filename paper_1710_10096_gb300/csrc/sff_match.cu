@@ -26,15 +26,16 @@
 //                 combinations in order.
 // k_inherit:      grid points of the coarser scale keep their vector and are
 //                 re-scored at this scale; the others start empty.
-// k_half_step:    one colour of the checkerboard, four lanes per pixel.
-//                 Fused with the random search of that colour: the search
-//                 after iteration i of colour 1 runs at the end of its
-//                 half-step of iteration i, the search of colour 0 at the
-//                 start of its half-step of iteration i+1 (or in a final
-//                 pass).  Both orders read the same values as the plain order
-//                 "half-step 0, half-step 1, random search", because a
-//                 half-step only reads the other colour and the search only
-//                 reads the pixel itself.
+// k_iteration:    one whole iteration (both colours of the checkerboard)
+//                 over a tile, L lanes per pixel.  Fused with the random
+//                 search: the search after iteration i of colour 1 runs at
+//                 the end of its half-step of iteration i, the search of
+//                 colour 0 at the start of its half-step of iteration i+1
+//                 (or, after a scale's last iteration, in a third phase of
+//                 that launch).  Both orders read the same values as the
+//                 plain order "half-step 0, half-step 1, random search",
+//                 because a half-step only reads the other colour and the
+//                 search only reads the pixel itself.
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -737,9 +738,6 @@ __global__ void k_inherit(const __grid_constant__ Fields F, int n) {
     }
 }
 
-struct HalfStep {
-    int n, s, colour, dx, dy, prop, rs_before, rs_after;
-};
 
 // Pixels are processed by groups of L lanes (L = 1, 2 or 4, a tuning knob
 // that never changes results).  Lane q of a group holds the 16-byte chunks j
@@ -886,43 +884,6 @@ __device__ __forceinline__ bool update_pixel(const Views& V, const Slice<L>& a, 
     return changed;
 }
 
-constexpr int kHalfLanes = 4;
-constexpr int kHalfThreads = 256;
-constexpr int kHalfPixels = kHalfThreads / kHalfLanes;
-
-// One colour of the checkerboard over the whole grid, in place.  Used for
-// the random search of colour 0 after the last iteration of a scale.
-__global__ void __launch_bounds__(kHalfThreads) k_half_step(const __grid_constant__ Fields F, HalfStep H) {
-    constexpr int L = kHalfLanes;
-    const Field& A = pick(F);
-    const Views& V = A.V;
-    const int q = threadIdx.x & (L - 1);
-    const unsigned gmask = group_mask<L>();
-    const int gy = blockIdx.y;
-    const int gx = 2 * (blockIdx.x * kHalfPixels + (int)(threadIdx.x / L)) + ((H.colour + gy) & 1);
-    if (gx >= A.gw || gy >= A.gh) return;  // the whole group leaves together
-    const int x = gx * H.n, y = gy * H.n;
-    const size_t i = pix(V.w, x, y);
-    const int ax = x - H.dx * H.n, by = y - H.dy * H.n;
-    const bool has_a = H.prop && ax >= 0 && ax < V.w;
-    const bool has_b = H.prop && by >= 0 && by < V.h;
-    const size_t ja = has_a ? pix(V.w, ax, y) : i, jb = has_b ? pix(V.w, x, by) : i;
-    int c = A.cost[i];
-    const uint2 wc = A.field[i];
-    const int ca = has_a ? A.cost[ja] : kEmpty, cb = has_b ? A.cost[jb] : kEmpty;
-    const uint2 wa = A.field[ja], wb = A.field[jb];
-    if (!H.prop && c == kEmpty) return;
-    Slice<L> a;
-    load_slice<L>(V.ref, i, q, a);
-    Vec4 cur = unpack_vec(wc);
-    if (update_pixel<L>(V, a, q, gmask, H.n, H.s, A.key, A.mirror, x, y, (uint32_t)i, H.rs_before, H.rs_after,
-                        unpack_vec(wa), ca, unpack_vec(wb), cb, cur, c) &&
-        q == 0) {
-        A.field[i] = pack_vec(cur);
-        A.cost[i] = c;
-    }
-}
-
 // One whole iteration (both colours) over a TX x TY tile of grid pixels.
 // Phase 1 updates the colour-0 pixels of the tile and of a one-pixel halo on
 // the sides the colour-1 pixels read from (the predecessor sides of the
@@ -945,6 +906,7 @@ __host__ __device__ constexpr int iter_threads() {
 
 struct IterStep {
     int n, s, dx, dy, it;
+    int last;  // the scale's last iteration: also the colour-0 search of this iteration (phase 3)
 };
 
 template <int L, int TX, int TY>
@@ -1026,6 +988,32 @@ __global__ void __launch_bounds__(iter_threads<L, TX, TY>()) k_iteration(const _
         update_pixel<L>(V, a, q, gmask, n, H.s, A.key, A.mirror, x, y, (uint32_t)i, -1, H.it, unpack_vec(wa), ca,
                         unpack_vec(wb), cb, cur, c);
         if (q == 0) {
+            A.field_out[i] = pack_vec(cur);
+            A.cost_out[i] = c;
+        }
+    }
+    if (!H.last) return;
+
+    // phase 3 (last iteration of the scale): the random search of this
+    // iteration for the tile's colour-0 pixels, from their phase-1 results in
+    // shared memory.  It reads only the pixel itself, so it may follow the
+    // colour-1 half-step, which read the colour-0 values before the search.
+    for (int k = grp; k < kTileHalfRow * TY; k += kGroups) {
+        const int ly = k / kTileHalfRow;
+        const int gy = ty0 + ly;
+        const int gx = tx0 + 2 * (k % kTileHalfRow) + ((tx0 + gy) & 1);
+        if (gx >= gw || gy >= gh) continue;
+        const int r = (gy - ry0) * kRegX + (gx - rx0);
+        int c = s_cost[r];
+        if (c == kEmpty) continue;  // the whole group
+        const int x = gx * n, y = gy * n;
+        const size_t i = pix(V.w, x, y);
+        Vec4 cur = unpack_vec(s_vec[r]);
+        Slice<L> a;
+        load_slice<L>(V.ref, i, q, a);
+        if (update_pixel<L>(V, a, q, gmask, n, H.s, A.key, A.mirror, x, y, (uint32_t)i, H.it, -1, cur, kEmpty, cur,
+                            kEmpty, cur, c) &&
+            q == 0) {
             A.field_out[i] = pack_vec(cur);
             A.cost_out[i] = c;
         }
@@ -1214,7 +1202,7 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
                 F.f[k].field_out = from_user ? Tf[k] : U[k];
                 F.f[k].cost_out = from_user ? Tc[k] : Uc[k];
             }
-            IterStep H{n, s, kDirs[it % 4][0], kDirs[it % 4][1], it};
+            IterStep H{n, s, kDirs[it % 4][0], kDirs[it % 4][1], it, it == I - 1};
             if (::sff::profiling()) ::sff::profile_mark("k_iteration", st, false);
             sv->k<<<gi, sv->threads, 0, st>>>(F, H);
             if (::sff::profiling()) ::sff::profile_mark("k_iteration", st, true);
@@ -1222,12 +1210,6 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
         for (int k = 0; k < nf; ++k) {
             F.f[k].field = F.f[k].field_out = U[k];
             F.f[k].cost = F.f[k].cost_out = Uc[k];
-        }
-        if (I > 0) {
-            const int half_w = (mgw + 1) / 2;
-            dim3 g((half_w + kHalfPixels - 1) / kHalfPixels, mgh, nf);
-            HalfStep H{n, s, 0, 0, 0, 0, I - 1, -1};
-            SFF_LAUNCH(k_half_step, g, kHalfThreads, 0, st, F, H);
         }
     }
     return launch_status();
