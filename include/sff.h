@@ -95,8 +95,10 @@ typedef struct sff_seed {
 int sff_default_params(sff_params* out);
 
 /* Bytes of one image's feature pyramid: num_scales * H * W * 52.
- * Layout: [scale][y][x] 48-byte records of int8 features (channel-major, 16
- * coefficients per channel in the order of sff_features), followed by
+ * Layout: per scale s, H * W 48-byte int8 feature records (16 coefficients
+ * per channel, channel-major, in the order of sff_features): for scale 0 as
+ * three planes of 16-byte chunks ([chunk][y][x], chunk = channel), for the
+ * coarser scales as whole records ([y][x][48]); then
  * [scale][y][x] int32 norms (the sum of squared features of each record).
  * Returns 0 for invalid arguments. */
 size_t sff_pyramid_bytes(int32_t width, int32_t height, const sff_params* params);

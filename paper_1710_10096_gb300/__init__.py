@@ -26,6 +26,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsff.so")
 EMPTY_COST = 2147483647
 FEATURE_BYTES = 48
+WHOLE_RECORD_STRIDE = 2  # scales with a coarser grid keep whole records (see split_pyramid)
 _lib = None
 
 
@@ -238,11 +239,22 @@ def match_quad_tuned(pyr_l0, pyr_r0, pyr_l1, pyr_r1, width: int, height: int, se
 
 
 def split_pyramid(pyr, width: int, height: int, params: Params = None):
-    """(features [S, H, W, 48] int8, norms [S, H, W] int32) views of a pyramid buffer."""
+    """(features [S, H, W, 48] int8, norms [S, H, W] int32) of a pyramid buffer.
+    Scales with grid stride 2^s < WHOLE_RECORD_STRIDE hold their 48-byte
+    records as three planes of 16-byte chunks ([chunk][y][x]), coarser scales
+    as whole records ([y][x][48]); the features are returned as records (a copy)."""
     import torch
     params = params or default_params()
     S, np_ = params.num_scales, width * height
-    feat = pyr[:S * np_ * FEATURE_BYTES].view(torch.int8).view(S, height, width, FEATURE_BYTES)
+    blocks = pyr[:S * np_ * FEATURE_BYTES].view(torch.int8).view(S, np_ * FEATURE_BYTES)
+    scales = []
+    for s in range(S):
+        if (1 << s) < WHOLE_RECORD_STRIDE:
+            scales.append(blocks[s].view(3, height, width, FEATURE_BYTES // 3).permute(1, 2, 0, 3)
+                          .reshape(height, width, FEATURE_BYTES))
+        else:
+            scales.append(blocks[s].view(height, width, FEATURE_BYTES))
+    feat = torch.stack(scales)
     norm = pyr[S * np_ * FEATURE_BYTES:S * np_ * (FEATURE_BYTES + 4)].view(torch.int32).view(S, height, width)
     return feat, norm
 

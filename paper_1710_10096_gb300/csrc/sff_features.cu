@@ -149,8 +149,9 @@ __device__ __forceinline__ void fold_row(const int (&rg)[6], const int (&bb)[6],
     }
 }
 
-__device__ __forceinline__ void write_record(const int (&arg)[16], const int (&ab)[16], int qshift, uint8_t* rec,
-                                             int* norm) {
+// Quantised record of one pixel: chunk k (channel k) at planes[k * cs + i * rs].
+__device__ __forceinline__ void write_record(const int (&arg)[16], const int (&ab)[16], int qshift, int4* planes,
+                                             size_t cs, size_t rs, size_t i, int* norm) {
     int q[3][16];
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
@@ -168,9 +169,9 @@ __device__ __forceinline__ void write_record(const int (&arg)[16], const int (&a
     int nn = 0;
 #pragma unroll
     for (int k = 0; k < 12; ++k) nn = __dp4a(words[k], words[k], nn);
-    int4* dst = reinterpret_cast<int4*>(rec);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) dst[k] = make_int4(words[4 * k], words[4 * k + 1], words[4 * k + 2], words[4 * k + 3]);
+    for (int k = 0; k < 3; ++k)
+        planes[k * cs + i * rs] = make_int4(words[4 * k], words[4 * k + 1], words[4 * k + 2], words[4 * k + 3]);
     *norm = nn;
 }
 
@@ -225,11 +226,12 @@ __global__ void __launch_bounds__(128) k_features(const __grid_constant__ ImageJ
             default: fold_row<7>(rg, bb, b_rg, b_b); break;
         }
     }
-    uint8_t* feat = job.pyr + (size_t)s * np * kFeat;
+    int4* feat = reinterpret_cast<int4*>(job.pyr + (size_t)s * np * kFeat);
     int* norms = reinterpret_cast<int*>(job.pyr + (size_t)S * np * kFeat) + (size_t)s * np;
     const size_t i = (size_t)y * w + x;
-    write_record(a_rg, a_b, qshift, feat + i * kFeat, norms + i);
-    if (second) write_record(b_rg, b_b, qshift, feat + (i + (size_t)n * w) * kFeat, norms + i + (size_t)n * w);
+    const size_t cs = chunk_planes(s) ? np : 1, rs = chunk_planes(s) ? 1 : 3;
+    write_record(a_rg, a_b, qshift, feat, cs, rs, i, norms + i);
+    if (second) write_record(b_rg, b_b, qshift, feat, cs, rs, i + (size_t)n * w, norms + i + (size_t)n * w);
 }
 
 }  // namespace

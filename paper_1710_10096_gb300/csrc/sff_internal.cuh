@@ -25,18 +25,40 @@ __host__ __device__ __forceinline__ int clampi(int a, int lo, int hi) { return a
 __host__ __device__ __forceinline__ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // One image at one scale: its feature records and norms.
+// One scale of one image's pyramid: the 48-byte record of pixel i as three
+// 16-byte chunks, chunk j at f[j * cs + i * rs].  Scale 0 (grid stride 1)
+// keeps three chunk planes (cs = W*H, rs = 1): a warp loading one chunk of 32
+// nearby pixels' records touches a third of the cache lines, and the other
+// colour of the checkerboard uses the rest of every sector.  Coarser scales
+// keep whole records side by side (cs = 1, rs = 3): their grid pixels are
+// n apart, so half or more of a chunk-plane sector would be a non-grid
+// pixel's, and a whole record costs two sectors instead of three.  Measured
+// on the 1242x375 quad / the 32-quad batch (M px/s): planes at stride 1 only
+// 288.7 / 350.9, at strides 1-2 290.1 / 338.8, at 1-4 288.9 / 316.7, whole
+// records everywhere 276.7 / 345.
+constexpr int kWholeRecordStride = 2;
+
+__host__ __device__ __forceinline__ bool chunk_planes(int s) { return (1 << s) < kWholeRecordStride; }
+
 struct Plane {
-    const uint8_t* f;
+    const int4* f;
     const int* nrm;
+    size_t cs;    // chunk stride (int4)
+    uint32_t rs;  // record stride (int4)
 };
 
 __host__ __device__ __forceinline__ Plane plane_of(const uint8_t* pyr, int s, int S, int w, int h) {
     const size_t np = (size_t)w * h;
     Plane P;
-    P.f = pyr + (size_t)s * np * kFeat;
+    P.f = reinterpret_cast<const int4*>(pyr + (size_t)s * np * kFeat);
     P.nrm = reinterpret_cast<const int*>(pyr + (size_t)S * np * kFeat) + (size_t)s * np;
+    P.cs = chunk_planes(s) ? np : 1;
+    P.rs = chunk_planes(s) ? 1 : 3;
     return P;
 }
+
+__device__ __forceinline__ const int4* chunk_ptr(const Plane& P, size_t i, int j) { return P.f + j * P.cs + i * P.rs; }
+__device__ __forceinline__ int4 chunk_of(const Plane& P, size_t i, int j) { return __ldg(chunk_ptr(P, i, j)); }
 
 // Reference feature held in registers: 12 packed int8x4 words and the norm.
 struct RefFeat {
@@ -45,8 +67,7 @@ struct RefFeat {
 };
 
 __device__ __forceinline__ void load_ref(const Plane& P, size_t i, RefFeat& r) {
-    const int4* p = reinterpret_cast<const int4*>(P.f + i * kFeat);
-    int4 q0 = __ldg(p), q1 = __ldg(p + 1), q2 = __ldg(p + 2);
+    const int4 q0 = chunk_of(P, i, 0), q1 = chunk_of(P, i, 1), q2 = chunk_of(P, i, 2);
     r.a[0] = q0.x; r.a[1] = q0.y; r.a[2] = q0.z; r.a[3] = q0.w;
     r.a[4] = q1.x; r.a[5] = q1.y; r.a[6] = q1.z; r.a[7] = q1.w;
     r.a[8] = q2.x; r.a[9] = q2.y; r.a[10] = q2.z; r.a[11] = q2.w;
@@ -56,8 +77,7 @@ __device__ __forceinline__ void load_ref(const Plane& P, size_t i, RefFeat& r) {
 // Sum of squared differences of two int8 feature vectors, as
 // |a|^2 + |b|^2 - 2 a.b with the dot product on dp4a (exact in int32).
 __device__ __forceinline__ int ssd_at(const RefFeat& r, const Plane& P, size_t i) {
-    const int4* p = reinterpret_cast<const int4*>(P.f + i * kFeat);
-    const int4 q0 = __ldg(p), q1 = __ldg(p + 1), q2 = __ldg(p + 2);
+    const int4 q0 = chunk_of(P, i, 0), q1 = chunk_of(P, i, 1), q2 = chunk_of(P, i, 2);
     // |b|^2 from the record itself (dp4a, exact): one sector less than
     // loading it from the norm plane
     int nb = 0, d = 0;

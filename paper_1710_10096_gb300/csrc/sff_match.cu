@@ -151,7 +151,7 @@ __global__ void k_gather_grid(const __grid_constant__ Fields F, int n) {
         const size_t i = pix(A.V.w, (c % A.gw) * n, (c / A.gw) * n);
         const size_t slot = (size_t)(role - 2) * A.gq + c;
         if (part < 3)
-            A.rec[slot * 3 + part] = __ldg(reinterpret_cast<const int4*>(P.f + i * kFeat) + part);
+            A.rec[slot * 3 + part] = chunk_of(P, i, part);
         else
             A.rec_n[slot] = __ldg(P.nrm + i);
         return;
@@ -163,7 +163,7 @@ __global__ void k_gather_grid(const __grid_constant__ Fields F, int n) {
         const Plane& P = role ? A.V.tmp : A.V.ref;
         const size_t i = pix(A.V.w, (r % A.gw) * n, (r / A.gw) * n);
         if (kg < 6) {
-            const int2 f = __ldg(reinterpret_cast<const int2*>(P.f + i * kFeat) + kg);
+            const int2 f = __ldg(reinterpret_cast<const int2*>(chunk_ptr(P, i, kg >> 1)) + (kg & 1));
             const int8_t* b = reinterpret_cast<const int8_t*>(&f);
 #pragma unroll
             for (int k = 0; k < 8; ++k) v[k] = role ? (float)b[k] : (float)(-2 * b[k]);
@@ -764,12 +764,11 @@ __device__ __forceinline__ int dot4(const int4& a, const int4& b, int d) {
 
 template <int L>
 __device__ __forceinline__ void load_slice(const Plane& P, size_t i, int q, Slice<L>& s) {
-    const int4* p = reinterpret_cast<const int4*>(P.f + i * kFeat);
     s.nrm = 0;
 #pragma unroll
     for (int k = 0; k < Slice<L>::kChunks; ++k) {
         const int j = q + k * L;
-        s.c[k] = j < 3 ? __ldg(p + j) : make_int4(0, 0, 0, 0);
+        s.c[k] = j < 3 ? chunk_of(P, i, j) : make_int4(0, 0, 0, 0);
         s.nrm = dot4(s.c[k], s.c[k], s.nrm);
     }
 }
