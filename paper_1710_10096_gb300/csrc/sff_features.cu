@@ -124,13 +124,14 @@ __device__ __forceinline__ void fwht8(int (&a)[8]) {
             }
 }
 
-__device__ __forceinline__ int lo16(int x) { return (x << 16) >> 16; }
-
-__device__ __forceinline__ int sat8(int v) { return v < -128 ? -128 : (v > 127 ? 127 : v); }
-
-__device__ __forceinline__ int pack4(int a, int b, int c, int d) {
-    return (int)((uint32_t)(a & 0xff) | ((uint32_t)(b & 0xff) << 8) | ((uint32_t)(c & 0xff) << 16) |
-                 ((uint32_t)(d & 0xff) << 24));
+// Four int32 values saturated to int8 and packed, v0 in the lowest byte:
+// cvt.pack.sat converts a and b and packs them as (a << 8) | b above the
+// low bits of c.
+__device__ __forceinline__ int pack4_sat(int v0, int v1, int v2, int v3) {
+    unsigned hi, d;
+    asm("cvt.pack.sat.s8.s32.b32 %0, %1, %2, 0;" : "=r"(hi) : "r"(v3), "r"(v2));
+    asm("cvt.pack.sat.s8.s32.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(v1), "r"(v0), "r"(hi));
+    return (int)d;
 }
 
 // Accumulate row transform (rg[kx], b[kx], kx = 0..5 in sequency order) of
@@ -152,20 +153,22 @@ __device__ __forceinline__ void fold_row(const int (&rg)[6], const int (&bb)[6],
 // Quantised record of one pixel: chunk k (channel k) at planes[k * cs + i * rs].
 __device__ __forceinline__ void write_record(const int (&arg)[16], const int (&ab)[16], int qshift, int4* planes,
                                              size_t cs, size_t rs, size_t i, int* norm) {
+    // R = low 16 bits (signed), G = the rest; arithmetic shifts floor, as the
+    // quantisation does
     int q[3][16];
 #pragma unroll
     for (int m = 0; m < 16; ++m) {
-        const int r = lo16(arg[m]);
-        const int g = (arg[m] - r) >> 16;
-        q[0][m] = sat8(r >> qshift);
-        q[1][m] = sat8(g >> qshift);
-        q[2][m] = sat8(ab[m] >> qshift);
+        const int lo = arg[m] << 16;
+        q[0][m] = lo >> (16 + qshift);
+        q[1][m] = (arg[m] - (lo >> 16)) >> (16 + qshift);
+        q[2][m] = ab[m] >> qshift;
     }
     int words[12];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) words[4 * c + k] = pack4(q[c][4 * k], q[c][4 * k + 1], q[c][4 * k + 2], q[c][4 * k + 3]);
+        for (int k = 0; k < 4; ++k)
+            words[4 * c + k] = pack4_sat(q[c][4 * k], q[c][4 * k + 1], q[c][4 * k + 2], q[c][4 * k + 3]);
     int nn = 0;
 #pragma unroll
     for (int k = 0; k < 12; ++k) nn = __dp4a(words[k], words[k], nn);
