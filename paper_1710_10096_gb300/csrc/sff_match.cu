@@ -712,9 +712,8 @@ __global__ void k_init_select(const __grid_constant__ Fields F, int n, int knn) 
         }
     }
     if (lane == 0) {
-        const size_t i = pix(V.w, px, py);
-        A.field[i] = pack_vec(best);
-        A.cost[i] = best_c;
+        A.field[qi] = pack_vec(best);  // compact: grid row-major
+        A.cost[qi] = best_c;
     }
 }
 
@@ -724,17 +723,20 @@ __global__ void k_inherit(const __grid_constant__ Fields F, int n) {
     const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y;
     if (gx >= A.gw || gy >= A.gh) return;
     const int x = gx * n, y = gy * n;
-    const size_t i = pix(V.w, x, y);
     const bool coarse = ((gx | gy) & 1) == 0;
-    const int c = coarse ? A.cost[i] : kEmpty;
+    const size_t ic = (size_t)(gy >> 1) * ((A.gw + 1) >> 1) + (gx >> 1);  // coarser scale's compact state
+    const size_t io = (size_t)gy * A.gw + gx;                              // this scale's
+    const int c = coarse ? A.cost[ic] : kEmpty;
     if (c != kEmpty) {
         RefFeat r;
-        load_ref(V.ref, i, r);
-        const Vec4 a = unpack_vec(A.field[i]);
-        A.cost[i] = cost_of(V, r, x, y, a.u, a.v, a.d0, a.d1);
+        load_ref(V.ref, pix(V.w, x, y), r);
+        const uint2 w = A.field[ic];
+        const Vec4 a = unpack_vec(w);
+        A.field_out[io] = w;
+        A.cost_out[io] = cost_of(V, r, x, y, a.u, a.v, a.d0, a.d1);
     } else {
-        A.cost[i] = kEmpty;
-        A.field[i] = make_uint2(0u, 0u);
+        A.cost_out[io] = kEmpty;
+        A.field_out[io] = make_uint2(0u, 0u);
     }
 }
 
@@ -933,12 +935,13 @@ __global__ void __launch_bounds__(iter_threads<L, TX, TY>()) k_iteration(const _
         const int gx = rx0 + rx, gy = ry0 + ry;
         if (rx >= kRegX || gx < 0 || gx >= gw || gy < 0 || gy >= gh) continue;
         const int x = gx * n, y = gy * n;
-        const size_t i = pix(V.w, x, y);
+        const size_t i = pix(V.w, x, y);            // image pixel: records, random stream
+        const size_t si = (size_t)gy * gw + gx;      // compact state of the scale's grid
         const int ax = x - H.dx * n, by = y - H.dy * n;
         const bool has_a = ax >= 0 && ax < V.w, has_b = by >= 0 && by < V.h;
-        const size_t ja = has_a ? pix(V.w, ax, y) : i, jb = has_b ? pix(V.w, x, by) : i;
-        int c = A.cost[i];
-        const uint2 wc = A.field[i];
+        const size_t ja = has_a ? si - H.dx : si, jb = has_b ? si - (size_t)(H.dy * gw) : si;
+        int c = A.cost[si];
+        const uint2 wc = A.field[si];
         const int ca = has_a ? A.cost[ja] : kEmpty, cb = has_b ? A.cost[jb] : kEmpty;
         const uint2 wa = A.field[ja], wb = A.field[jb];
         Slice<L> a;
@@ -951,8 +954,8 @@ __global__ void __launch_bounds__(iter_threads<L, TX, TY>()) k_iteration(const _
             s_vec[ry * kRegX + rx] = wv;
             s_cost[ry * kRegX + rx] = c;
             if (gx >= tx0 && gx < tx0 + TX && gy >= ty0 && gy < ty0 + TY) {
-                A.field_out[i] = wv;
-                A.cost_out[i] = c;
+                A.field_out[si] = wv;
+                A.cost_out[si] = c;
             }
         }
     }
@@ -967,8 +970,9 @@ __global__ void __launch_bounds__(iter_threads<L, TX, TY>()) k_iteration(const _
         if (gx >= gw || gy >= gh) continue;
         const int x = gx * n, y = gy * n;
         const size_t i = pix(V.w, x, y);
-        int c = A.cost[i];
-        Vec4 cur = unpack_vec(A.field[i]);
+        const size_t si = (size_t)gy * gw + gx;
+        int c = A.cost[si];
+        Vec4 cur = unpack_vec(A.field[si]);
         Slice<L> a;
         load_slice<L>(V.ref, i, q, a);
         const int agx = gx - H.dx, bgy = gy - H.dy;  // predecessors (colour 0, in the region)
@@ -987,8 +991,8 @@ __global__ void __launch_bounds__(iter_threads<L, TX, TY>()) k_iteration(const _
         update_pixel<L>(V, a, q, gmask, n, H.s, A.key, A.mirror, x, y, (uint32_t)i, -1, H.it, unpack_vec(wa), ca,
                         unpack_vec(wb), cb, cur, c);
         if (q == 0) {
-            A.field_out[i] = pack_vec(cur);
-            A.cost_out[i] = c;
+            A.field_out[si] = pack_vec(cur);
+            A.cost_out[si] = c;
         }
     }
     if (!H.last) return;
@@ -1013,8 +1017,9 @@ __global__ void __launch_bounds__(iter_threads<L, TX, TY>()) k_iteration(const _
         if (update_pixel<L>(V, a, q, gmask, n, H.s, A.key, A.mirror, x, y, (uint32_t)i, H.it, -1, cur, kEmpty, cur,
                             kEmpty, cur, c) &&
             q == 0) {
-            A.field_out[i] = pack_vec(cur);
-            A.cost_out[i] = c;
+            const size_t si = (size_t)gy * gw + gx;
+            A.field_out[si] = pack_vec(cur);
+            A.cost_out[si] = c;
         }
     }
 }
@@ -1154,16 +1159,46 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
         Tf[k] = reinterpret_cast<uint2*>(ws + sc.field);
         Tc[k] = reinterpret_cast<int*>(ws + sc.cost);
     }
+    // State buffers: 0 = the caller's (U), 1 = the workspace's (T).  Each
+    // scale keeps its state compact (grid row-major; at scale 0 that is the
+    // image).  The initialisation or inheritance writes buffer `cur`, the
+    // iterations alternate from it, and the next finer scale inherits from
+    // the final one into the other buffer; the start is chosen so that scale
+    // 0 ends in U.
+    uint2* Bf[2][kMaxFields];
+    int* Bc[2][kMaxFields];
+    for (int k = 0; k < nf; ++k) {
+        Bf[0][k] = U[k];
+        Bc[0][k] = Uc[k];
+        Bf[1][k] = Tf[k];
+        Bc[1][k] = Tc[k];
+    }
+    auto final_of_scale0 = [&](int b) {
+        for (int s = S - 1; s >= 0; --s) {
+            if (s < S - 1) b ^= 1;  // inherit into the other buffer
+            b ^= I & 1;             // after the iterations
+        }
+        return b;
+    };
+    int cur = final_of_scale0(0) == 0 ? 0 : 1, prev = 0;
     for (int s = S - 1; s >= 0; --s) {
         const int n = 1 << s;
         int mgw = 0, mgh = 0, mgq = 0;
+        if (s < S - 1) cur = prev ^ 1;
         for (int k = 0; k < nf; ++k) {
             const FieldSpec& fs = spec[k];
             const int w = fs.width, h = fs.height;
             F.f[k].V = Views{plane_of(fs.ref, s, S, w, h), plane_of(fs.tmp, s, S, w, h), plane_of(fs.ste, s, S, w, h),
                              plane_of(fs.crs, s, S, w, h), w, h, fs.mirror ? -1 : 1};
-            F.f[k].field = F.f[k].field_out = U[k];
-            F.f[k].cost = F.f[k].cost_out = Uc[k];
+            if (s == S - 1) {  // k_init_select writes the state
+                F.f[k].field = F.f[k].field_out = Bf[cur][k];
+                F.f[k].cost = F.f[k].cost_out = Bc[cur][k];
+            } else {  // k_inherit reads the coarser final state, writes this scale's
+                F.f[k].field = Bf[prev][k];
+                F.f[k].cost = Bc[prev][k];
+                F.f[k].field_out = Bf[cur][k];
+                F.f[k].cost_out = Bc[cur][k];
+            }
             gw[k] = F.f[k].gw = (w + n - 1) / n;
             gh[k] = F.f[k].gh = (h + n - 1) / n;
             mgw = std::max(mgw, gw[k]);
@@ -1182,34 +1217,22 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
             dim3 g((mgw + 127) / 128, mgh, nf);
             SFF_LAUNCH(k_inherit, g, 128, 0, st, F, n);
         }
-        // iterations alternate between the caller's buffers (U) and the
-        // workspace buffers (T); with an odd count U is first copied to T so
-        // that the last iteration writes U
-        if (I & 1)
-            for (int k = 0; k < nf; ++k) {
-                const size_t np = (size_t)spec[k].width * spec[k].height;
-                cudaMemcpyAsync(Tf[k], U[k], np * 8, cudaMemcpyDeviceToDevice, st);
-                cudaMemcpyAsync(Tc[k], Uc[k], np * 4, cudaMemcpyDeviceToDevice, st);
-            }
         const IterVariant* sv = tile_for_grid(var, s, gw, gh, nf);
         dim3 gi((mgw + sv->tx - 1) / sv->tx, (mgh + sv->ty - 1) / sv->ty, nf);
         for (int it = 0; it < I; ++it) {
-            const bool from_user = ((I - it) & 1) == 0;  // the last iteration reads T and writes U
+            const int in = cur ^ (it & 1);
             for (int k = 0; k < nf; ++k) {
-                F.f[k].field = from_user ? U[k] : Tf[k];
-                F.f[k].cost = from_user ? Uc[k] : Tc[k];
-                F.f[k].field_out = from_user ? Tf[k] : U[k];
-                F.f[k].cost_out = from_user ? Tc[k] : Uc[k];
+                F.f[k].field = Bf[in][k];
+                F.f[k].cost = Bc[in][k];
+                F.f[k].field_out = Bf[in ^ 1][k];
+                F.f[k].cost_out = Bc[in ^ 1][k];
             }
             IterStep H{n, s, kDirs[it % 4][0], kDirs[it % 4][1], it, it == I - 1};
             if (::sff::profiling()) ::sff::profile_mark("k_iteration", st, false);
             sv->k<<<gi, sv->threads, 0, st>>>(F, H);
             if (::sff::profiling()) ::sff::profile_mark("k_iteration", st, true);
         }
-        for (int k = 0; k < nf; ++k) {
-            F.f[k].field = F.f[k].field_out = U[k];
-            F.f[k].cost = F.f[k].cost_out = Uc[k];
-        }
+        prev = cur ^ (I & 1);
     }
     return launch_status();
 }
