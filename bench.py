@@ -275,8 +275,12 @@ def bench_serving(sff, torch, dev, quads, params, tuning, max_requests=240):
     for size in {(im[0].shape[1], im[0].shape[0]) for im in pool}:
         srv.reserve(size, 8)  # resident slots: no allocation while requests wait
     plain = PlainServer(params, tuning, device=dev)
-    simulate(srv, poisson_arrivals(400.0, 24, 8, len(pool), seed=1), pool)  # warm-up: slots allocated
-    simulate(plain, poisson_arrivals(400.0, 24, 8, len(pool), seed=1), pool)
+    # warm-up: slots allocated, and every kernel variant the batch sizes pick
+    # loaded once (a single-quad batch takes other per-scale variants than a
+    # large one; CUDA loads a kernel at its first launch)
+    for warm_rate in (400.0, 20.0):
+        simulate(srv, poisson_arrivals(warm_rate, 24, 8, len(pool), seed=1), pool)
+        simulate(plain, poisson_arrivals(warm_rate, 24, 8, len(pool), seed=1), pool)
     for rate in SERVING_RATES:
         n_requests = max(40, min(max_requests, int(3 * rate)))
         arr = poisson_arrivals(rate, n_requests, 8, len(pool), seed=7)
