@@ -292,6 +292,38 @@ def bench_serving(sff, torch, dev, quads, params, tuning, max_requests=240):
     return out
 
 
+def bench_paper_order(sff, torch, dev, m, q, params, reps=3):
+    """Matching of both fields of the quad in the paper's order (in-place
+    raster sweeps, sff_match_views_sequential) against the checkerboard
+    order (sff_match_views), on the same resident pyramids; CUDA events on
+    one stream, L2 as left by the previous call."""
+    w, h = q.width, q.height
+    ws = torch.empty(sff.workspace_bytes(w, h, params), dtype=torch.uint8, device=dev)
+    f = torch.empty((h, w, 4), dtype=torch.int16, device=dev)
+    c = torch.empty((h, w), dtype=torch.int32, device=dev)
+    L0, R0, L1, R1 = m.pyr
+    stream = torch.cuda.Stream(device=dev)
+
+    def both(fn):
+        fn(L0, L1, R0, R1, w, h, 0, MATCH_SEED, f, c, ws, params, stream=stream)
+        fn(R1, R0, L1, L0, w, h, 1, MATCH_SEED, f, c, ws, params, stream=stream)
+
+    out = {}
+    with torch.cuda.stream(stream):
+        for name, fn in (("paper_order", sff.match_views_sequential), ("checkerboard", sff.match_views)):
+            both(fn)  # warm-up
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                both(fn)
+            b.record(stream)
+            stream.synchronize()
+            out[name] = a.elapsed_time(b) / reps
+    return {"what": "both fields of the quad matched from resident pyramids (initialisation, 4 scales x 12 "
+                    "iterations, random search), ms per quad", "paper_order_ms": out["paper_order"],
+            "checkerboard_ms": out["checkerboard"], "slowdown": out["paper_order"] / out["checkerboard"]}
+
+
 def combine_ranks(t_step: float, px_per_rank: int, world: int, device=None):
     """Whole-job throughput of `world` replicas: every rank matched its own
     quad; the job time is the slowest rank's (max over ranks), the pixels are
@@ -475,6 +507,7 @@ def main():
                        "tuning": {"lanes_per_pixel": tuning.lanes_per_pixel, "tile": [tuning.tile_x, tuning.tile_y]}},
             "roofline": roof, "gpu_launches": int(round(launches_per_step * args.steps)),
             "e2e": e2e, "clocks": clk, "kernels": kernels, "seeds": n_seeds}
+    line["paper_order"] = bench_paper_order(sff, torch, dev, m, q, params)
     if batch is not None:
         line["batched"] = bench_batched(sff, torch, dev, batch[0], batch[1], params, tuning, min(args.steps, 20),
                                         max(1, args.warmup))

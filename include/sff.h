@@ -157,6 +157,25 @@ int sff_match_views(const uint8_t* pyr_ref_dev, const uint8_t* pyr_temporal_dev,
                     const sff_params* params, int16_t* field_dev, int32_t* cost_dev,
                     void* workspace, size_t workspace_bytes, void* stream);
 
+/* sff_match_views with the paper's own propagation order (Sec. 3.1,
+ * "Multi-Scale Propagation": the pixels are visited in scan order, each
+ * taking the better of its predecessors' current vectors, in place).  Each
+ * iteration is one raster sweep over the grid in the iteration's direction
+ * (rows in y direction, pixels in x direction), every pixel comparing first
+ * its horizontal, then its vertical predecessor's vector as updated earlier
+ * in the same sweep (replaced only on strictly lower cost), followed by the
+ * random search of sff_match_views over every non-empty grid pixel.
+ * Everything else (initialisation, inheritance, costs, random draws) is that
+ * of sff_match_views.  A sweep has one dependent step per anti-diagonal of
+ * the grid (W/n + H/n - 1 of them), so this call is much slower than
+ * sff_match_views; it reproduces the sequential scan exactly.  Same
+ * arguments, alignment, workspace and errors as sff_match_views. */
+int sff_match_views_sequential(const uint8_t* pyr_ref_dev, const uint8_t* pyr_temporal_dev,
+                               const uint8_t* pyr_stereo_dev, const uint8_t* pyr_cross_dev,
+                               int32_t width, int32_t height, int32_t mirror, uint64_t seed,
+                               const sff_params* params, int16_t* field_dev, int32_t* cost_dev,
+                               void* workspace, size_t workspace_bytes, void* stream);
+
 /* Both fields of a quad in one pass (Sec. 3.1: the matching field of L0 and
  * the inverse field of R1 used by "Consistency Check").  Identical results to
  *   sff_match_views(L0, L1, R0, R1, mirror 0) -> fwd, fwd_cost

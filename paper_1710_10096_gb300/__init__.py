@@ -117,6 +117,8 @@ def lib():
         L.sff_features.restype = i32
         L.sff_match_views.argtypes = [P, P, P, P, i32, i32, i32, ctypes.c_uint64, PP, P, P, P, sz, P]
         L.sff_match_views.restype = i32
+        L.sff_match_views_sequential.argtypes = [P, P, P, P, i32, i32, i32, ctypes.c_uint64, PP, P, P, P, sz, P]
+        L.sff_match_views_sequential.restype = i32
         L.sff_match_quad.argtypes = [P, P, P, P, i32, i32, ctypes.c_uint64, PP, P, P, P, P, P, sz, P]
         L.sff_match_quad.restype = i32
         L.sff_match_quad_tuned.argtypes = [P, P, P, P, i32, i32, ctypes.c_uint64, PP, ctypes.POINTER(Tuning), P, P, P,
@@ -203,6 +205,18 @@ def match_views(pyr_ref, pyr_temporal, pyr_stereo, pyr_cross, width: int, height
                                  height, int(mirror), int(seed) & (2 ** 64 - 1), ctypes.byref(params), _ptr(field),
                                  _ptr(cost), _ptr(workspace), _nbytes(workspace), _stream(stream)),
            "sff_match_views")
+
+
+def match_views_sequential(pyr_ref, pyr_temporal, pyr_stereo, pyr_cross, width: int, height: int, mirror: int,
+                           seed: int, field, cost, workspace, params: Params = None, stream=None) -> None:
+    """sff_match_views_sequential: the paper's in-place raster sweeps instead of
+    checkerboard half-steps (slow; reproduces the sequential scan exactly)."""
+    params = params or default_params()
+    _check(lib().sff_match_views_sequential(_ptr(pyr_ref), _ptr(pyr_temporal), _ptr(pyr_stereo), _ptr(pyr_cross),
+                                            width, height, int(mirror), int(seed) & (2 ** 64 - 1),
+                                            ctypes.byref(params), _ptr(field), _ptr(cost), _ptr(workspace),
+                                            _nbytes(workspace), _stream(stream)),
+           "sff_match_views_sequential")
 
 
 def match_quad(pyr_l0, pyr_r0, pyr_l1, pyr_r1, width: int, height: int, seed: int, fwd, fwd_cost, inv, inv_cost,

@@ -77,7 +77,7 @@ extern "C" int sff_run_batch(const sff_quad* quads, int32_t n, const sff_params*
         fs[2 * k + 1] = FieldSpec{q.pyramid[3], q.pyramid[1], q.pyramid[2], q.pyramid[0], q.inv, q.inv_cost, 1,
                                   q.width,      q.height,     q.seed,       ws + half};
     }
-    status = run_fields(fs, 2 * n, P, t, st);
+    status = run_fields(fs, 2 * n, P, t, st, false);
     if (status) return status;
 
     // consistency + region filter, then seeds

@@ -220,7 +220,8 @@ int run_seeds(const SeedJob* jobs, int n, cudaStream_t st);
 void filter_carve(void* workspace, int w, int h, int** parent, int** size, int** joinable);
 void seeds_carve(void* workspace, int w, int h, int** best, int** chunk);
 size_t field_ws_bytes(int w, int h, const sff_params& p);
-int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tuning& T, cudaStream_t st);
+int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tuning& T, cudaStream_t st,
+               bool sequential);
 
 // Optional per-kernel event timing (sff_profile_enable).  SFF_LAUNCH wraps
 // every kernel launch of the library.

@@ -1024,6 +1024,85 @@ __global__ void __launch_bounds__(iter_threads<L, TX, TY>()) k_iteration(const _
     }
 }
 
+// ---------------------------------------------------------------------------
+// The paper's own propagation order (departure D4 switched back): each
+// iteration is one in-place raster sweep in the iteration's direction, a
+// pixel taking its two predecessors' current vectors (horizontal first,
+// replaced only on strictly lower cost), then the random search over every
+// non-empty grid pixel.  In sweep coordinates (a, b) a pixel depends on
+// (a - 1, b) and (a, b - 1) only, so the pixels of one anti-diagonal
+// a + b = t are independent: one CTA per field walks the gw + gh - 1
+// diagonals, a barrier between them.  The critical path is that many
+// dependent cost evaluations per iteration, so this order is an order of
+// magnitude slower per quad than the checkerboard; it exists to reproduce
+// the sequential scan exactly.
+constexpr int kSweepLanes = 2;
+constexpr int kSweepThreads = 1024;
+
+__global__ void __launch_bounds__(kSweepThreads) k_sweep(const __grid_constant__ Fields F, int n, int dx, int dy) {
+    constexpr int L = kSweepLanes;
+    constexpr int kGroups = kSweepThreads / L;
+    const Field& A = pick(F);
+    const Views& V = A.V;
+    const int q = threadIdx.x & (L - 1);
+    const unsigned gmask = group_mask<L>();
+    const int grp = threadIdx.x / L;
+    const int gw = A.gw, gh = A.gh;
+    for (int t = 0; t < gw + gh - 1; ++t) {
+        const int b0 = max(0, t - (gw - 1)), b1 = min(gh - 1, t);
+        for (int b = b0 + grp; b <= b1; b += kGroups) {
+            const int a = t - b;
+            const int gx = dx > 0 ? a : gw - 1 - a, gy = dy > 0 ? b : gh - 1 - b;
+            const int x = gx * n, y = gy * n;
+            const size_t si = (size_t)gy * gw + gx;
+            const bool has_a = gx - dx >= 0 && gx - dx < gw, has_b = gy - dy >= 0 && gy - dy < gh;
+            // plain loads: the predecessors were written by this CTA on the
+            // previous diagonal
+            int c = A.cost[si];
+            Vec4 cur = unpack_vec(A.field[si]);
+            const int ca = has_a ? A.cost[si - dx] : kEmpty;
+            const int cb = has_b ? A.cost[si - (size_t)(dy * gw)] : kEmpty;
+            const uint2 wa = has_a ? A.field[si - dx] : make_uint2(0u, 0u);
+            const uint2 wb = has_b ? A.field[si - (size_t)(dy * gw)] : make_uint2(0u, 0u);
+            Slice<L> r;
+            load_slice<L>(V.ref, pix(V.w, x, y), q, r);
+            if (update_pixel<L>(V, r, q, gmask, n, 0, A.key, A.mirror, x, y, 0u, -1, -1, unpack_vec(wa), ca,
+                                unpack_vec(wb), cb, cur, c) &&
+                q == 0) {
+                A.field[si] = pack_vec(cur);
+                A.cost[si] = c;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// The random search of iteration `it` over every non-empty grid pixel, in
+// place (it reads only the pixel itself).  L = 4 lanes per pixel.
+__global__ void __launch_bounds__(256) k_random_search(const __grid_constant__ Fields F, int n, int s, int it) {
+    constexpr int L = 4;
+    const Field& A = pick(F);
+    const Views& V = A.V;
+    const int q = threadIdx.x & (L - 1);
+    const unsigned gmask = group_mask<L>();
+    const int gx = blockIdx.x * (256 / L) + (int)(threadIdx.x / L), gy = blockIdx.y;
+    if (gx >= A.gw || gy >= A.gh) return;  // the whole group
+    const size_t si = (size_t)gy * A.gw + gx;
+    int c = A.cost[si];
+    if (c == kEmpty) return;
+    const int x = gx * n, y = gy * n;
+    const size_t i = pix(V.w, x, y);
+    Vec4 cur = unpack_vec(A.field[si]);
+    Slice<L> r;
+    load_slice<L>(V.ref, i, q, r);
+    if (update_pixel<L>(V, r, q, gmask, n, s, A.key, A.mirror, x, y, (uint32_t)i, it, -1, cur, kEmpty, cur, kEmpty,
+                        cur, c) &&
+        q == 0) {
+        A.field[si] = pack_vec(cur);
+        A.cost[si] = c;
+    }
+}
+
 // Instantiated (lanes per pixel, tile) variants; any of them gives identical
 // results.
 using IterKernel = void (*)(Fields, IterStep);
@@ -1130,7 +1209,8 @@ bool knn_smem_ready() {
 
 // The stage of Sec. 3.1 for nf <= kMaxFields fields (any sizes) sharing the
 // launches.  spec[k].workspace holds field_ws_bytes() of scratch.
-int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tuning& T, cudaStream_t st) {
+int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tuning& T, cudaStream_t st,
+               bool sequential) {
     const IterVariant* var = find_variant(T);
     if (!var || nf < 1 || nf > kMaxFields) return SFF_ERR_ARG;
     const int S = P.num_scales, I = P.iterations;
@@ -1173,10 +1253,11 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
         Bf[1][k] = Tf[k];
         Bc[1][k] = Tc[k];
     }
+    const int flips = sequential ? 0 : (I & 1);  // the sweeps work in place
     auto final_of_scale0 = [&](int b) {
         for (int s = S - 1; s >= 0; --s) {
             if (s < S - 1) b ^= 1;  // inherit into the other buffer
-            b ^= I & 1;             // after the iterations
+            b ^= flips;             // after the iterations
         }
         return b;
     };
@@ -1216,6 +1297,19 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
         } else {
             dim3 g((mgw + 127) / 128, mgh, nf);
             SFF_LAUNCH(k_inherit, g, 128, 0, st, F, n);
+        }
+        if (sequential) {
+            for (int k = 0; k < nf; ++k) {
+                F.f[k].field = F.f[k].field_out = Bf[cur][k];
+                F.f[k].cost = F.f[k].cost_out = Bc[cur][k];
+            }
+            dim3 gr((mgw + 63) / 64, mgh, nf);
+            for (int it = 0; it < I; ++it) {
+                SFF_LAUNCH(k_sweep, dim3(1, 1, nf), kSweepThreads, 0, st, F, n, kDirs[it % 4][0], kDirs[it % 4][1]);
+                SFF_LAUNCH(k_random_search, gr, 256, 0, st, F, n, s, it);
+            }
+            prev = cur;
+            continue;
         }
         const IterVariant* sv = tile_for_grid(var, s, gw, gh, nf);
         dim3 gi((mgw + sv->tx - 1) / sv->tx, (mgh + sv->ty - 1) / sv->ty, nf);
@@ -1265,7 +1359,30 @@ extern "C" int sff_match_views(const uint8_t* pyr_ref_dev, const uint8_t* pyr_te
                 width, height, seed, workspace};
     sff_tuning t;
     sff_default_tuning(&t);
-    return run_fields(&f, 1, *params, t, (cudaStream_t)stream);
+    return run_fields(&f, 1, *params, t, (cudaStream_t)stream, false);
+}
+
+extern "C" int sff_match_views_sequential(const uint8_t* pyr_ref_dev, const uint8_t* pyr_temporal_dev,
+                                          const uint8_t* pyr_stereo_dev, const uint8_t* pyr_cross_dev,
+                                          int32_t width, int32_t height, int32_t mirror, uint64_t seed,
+                                          const sff_params* params, int16_t* field_dev, int32_t* cost_dev,
+                                          void* workspace, size_t workspace_bytes, void* stream) {
+    using namespace sff;
+    if (check_size(width, height) || check_params(params)) return SFF_ERR_ARG;
+    if (!pyr_ref_dev || !pyr_temporal_dev || !pyr_stereo_dev || !pyr_cross_dev || !field_dev || !cost_dev ||
+        !workspace)
+        return SFF_ERR_ARG;
+    if (mirror != 0 && mirror != 1) return SFF_ERR_ARG;
+    if (misaligned_pyr(pyr_ref_dev) || misaligned_pyr(pyr_temporal_dev) || misaligned_pyr(pyr_stereo_dev) ||
+        misaligned_pyr(pyr_cross_dev))
+        return SFF_ERR_ARG;
+    if (((uintptr_t)field_dev & 7) || ((uintptr_t)cost_dev & 3) || ((uintptr_t)workspace & 255)) return SFF_ERR_ARG;
+    if (workspace_bytes < match_ws_bytes(width, height, *params)) return SFF_ERR_WORKSPACE;
+    FieldSpec f{pyr_ref_dev, pyr_temporal_dev, pyr_stereo_dev, pyr_cross_dev, field_dev, cost_dev, mirror,
+                width, height, seed, workspace};
+    sff_tuning t;
+    sff_default_tuning(&t);
+    return run_fields(&f, 1, *params, t, (cudaStream_t)stream, true);
 }
 
 extern "C" int sff_default_tuning(sff_tuning* out) {
@@ -1304,7 +1421,7 @@ extern "C" int sff_match_quad_tuned(const uint8_t* pyr_l0_dev, const uint8_t* py
                        ws},
                       {pyr_r1_dev, pyr_r0_dev, pyr_l1_dev, pyr_l0_dev, inv_dev, inv_cost_dev, 1, width, height, seed,
                        ws + half}};
-    return run_fields(f, 2, *params, *tuning, (cudaStream_t)stream);
+    return run_fields(f, 2, *params, *tuning, (cudaStream_t)stream, false);
 }
 
 extern "C" int sff_match_quad(const uint8_t* pyr_l0_dev, const uint8_t* pyr_r0_dev, const uint8_t* pyr_l1_dev,

@@ -94,6 +94,61 @@ def test_match_views_random_images(env, size, params):
         assert np.array_equal(gf, of)
 
 
+@pytest.mark.parametrize("size,params", [
+    ((64, 48), {}),
+    ((37, 23), {"iterations": 5}),
+    ((96, 40), {"num_scales": 2, "iterations": 3}),
+    ((600, 520), {"iterations": 2}),  # scale-0 diagonals longer than one round of 512 pixel groups
+])
+def test_match_views_sequential_equals_oracle_scan_order(env, size, params):
+    # the paper's in-place raster sweeps (departure D4 switched back): both
+    # fields bit-exact to the oracle's sequential-scan mode
+    torch, sff, orc = env
+    w, h = size
+    imgs = scenegen.random_images(w, h, seed=11 + w + h)
+    p = sff.default_params(**params)
+    pyrs = [_gpu_features(torch, sff, im, p)[0] for im in imgs]
+    ws = torch.empty(sff.workspace_bytes(w, h, p), dtype=torch.uint8, device="cuda")
+    op = _oparams(orc, p)
+    op.order_mode = orc.SEQUENTIAL_SCAN
+    feats = [orc.features(im, op)[0] for im in imgs]
+    for mirror, roles in ((0, (0, 2, 1, 3)), (1, (3, 1, 2, 0))):
+        field = torch.empty((h, w, 4), dtype=torch.int16, device="cuda")
+        cost = torch.empty((h, w), dtype=torch.int32, device="cuda")
+        sff.match_views_sequential(*(pyrs[i] for i in roles), w, h, mirror, 77, field, cost, ws, p)
+        torch.cuda.synchronize()
+        of, oc = orc.match_views(*(feats[i] for i in roles), mirror, 77, op)
+        assert np.array_equal(cost.cpu().numpy(), oc)
+        assert np.array_equal(field.cpu().numpy(), of)
+
+
+def test_match_views_sequential_on_scene(env):
+    # a rendered scene, full parameters: the paper order matches the oracle's
+    torch, sff, orc = env
+    q = scenegen.make_named("planes_256x80", 5)
+    w, h = q.width, q.height
+    p = sff.default_params()
+    imgs = q.images()
+    pyrs = [_gpu_features(torch, sff, im, p)[0] for im in imgs]
+    ws = torch.empty(sff.workspace_bytes(w, h, p), dtype=torch.uint8, device="cuda")
+    op = _oparams(orc, p)
+    op.order_mode = orc.SEQUENTIAL_SCAN
+    feats = [orc.features(im, op)[0] for im in imgs]
+    field = torch.empty((h, w, 4), dtype=torch.int16, device="cuda")
+    cost = torch.empty((h, w), dtype=torch.int32, device="cuda")
+    sff.match_views_sequential(pyrs[0], pyrs[2], pyrs[1], pyrs[3], w, h, 0, 9, field, cost, ws, p)
+    torch.cuda.synchronize()
+    of, oc = orc.match_views(feats[0], feats[2], feats[1], feats[3], 0, 9, op)
+    assert np.array_equal(cost.cpu().numpy(), oc)
+    assert np.array_equal(field.cpu().numpy(), of)
+    # and it differs from the checkerboard order (the two orders are not the same method)
+    fc = torch.empty_like(field)
+    cc = torch.empty_like(cost)
+    sff.match_views(pyrs[0], pyrs[2], pyrs[1], pyrs[3], w, h, 0, 9, fc, cc, ws, p)
+    torch.cuda.synchronize()
+    assert not np.array_equal(fc.cpu().numpy(), of)
+
+
 @pytest.mark.parametrize("size,params", [((256, 80), {}), ((37, 23), {}), ((96, 40), {"num_scales": 2}),
                                          ((130, 70), {"iterations": 3, "knn_temporal": 8})])
 def test_match_quad_equals_two_match_views(env, size, params):
