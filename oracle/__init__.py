@@ -17,6 +17,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sff_oracle.c")
+_SRC_INTERP = os.path.join(_HERE, "sff_interp_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -47,9 +48,11 @@ assert SEED_DTYPE.itemsize == 20
 
 def build(force: bool = False) -> str:
     """Compile the oracle into oracle/liboracle.so (gcc, OpenMP)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_INTERP))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11", _SRC, "-o", tmp])
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11", _SRC, _SRC_INTERP, "-lm",
+                               "-o", tmp])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -77,6 +80,10 @@ def lib():
         L.sffo_coef_order.argtypes = [P, P]
         L.sffo_cost.argtypes = [P, P, P, P, i32, i32, i32, i32, i32, P]
         L.sffo_cost.restype = i32
+        L.sffi_seed_models.argtypes = [P, i32, ctypes.POINTER(InterpParams), P, P, P]
+        L.sffi_interpolate_pixels.argtypes = [P, i32, ctypes.POINTER(InterpParams), P, P, P, P, i32, P, P]
+        L.sffi_nearest.argtypes = [P, i32, i32, i32, i32, i32, P, P, P]
+        L.sffi_set_threads.argtypes = [i32]
         L.sffo_set_threads.argtypes = [i32]
         L.sffo_get_threads.restype = i32
         _lib = L
@@ -90,6 +97,7 @@ def _p(a: np.ndarray):
 
 def set_threads(n: int) -> None:
     lib().sffo_set_threads(int(n))
+    lib().sffi_set_threads(int(n))
 
 
 def get_threads() -> int:
@@ -215,3 +223,70 @@ def run_quad(L0, R0, L1, R1, seed: int, params: Params = None):
     seeds = emit_seeds(fwd, fwd_cost, keep, cerr)
     return dict(feat=(fL0, fR0, fL1, fR1), norm=(nL0, nR0, nL1, nR1), fwd=fwd, fwd_cost=fwd_cost, inv=inv,
                 inv_cost=inv_cost, keep=keep, cerr=cerr, seeds=seeds)
+
+
+# ---------------------------------------------------------------------------
+# Dense interpolation of the seeds (Sec. 3.3), sff_interp_oracle.c
+
+
+class InterpParams(ctypes.Structure):
+    """Neighbourhood sizes and kernel of Sec. 5 (160 / 80 seeds, alpha = 2.2),
+    the distance unit of the Euclidean reading, and the pinhole camera."""
+    _fields_ = [("k_geo", ctypes.c_int32), ("k_motion", ctypes.c_int32), ("alpha", ctypes.c_double),
+                ("dist_unit", ctypes.c_double), ("focal", ctypes.c_double), ("baseline", ctypes.c_double),
+                ("cx", ctypes.c_double), ("cy", ctypes.c_double)]
+
+
+def interp_params(width: int, height: int, focal: float, baseline: float, **over) -> InterpParams:
+    p = dict(k_geo=160, k_motion=80, alpha=2.2, dist_unit=20.0, focal=float(focal), baseline=float(baseline),
+             cx=(width - 1) / 2.0, cy=(height - 1) / 2.0)
+    p.update(over)
+    return InterpParams(**p)
+
+
+def seed_models(seeds, params: InterpParams):
+    """(plane [n, 3], affine [n, 15] = [A | t] rows then the centre, motion
+    neighbour count [n]) of every seed."""
+    seeds = np.ascontiguousarray(seeds, SEED_DTYPE)
+    n = len(seeds)
+    plane = np.zeros((max(n, 1), 3), np.float64)
+    affine = np.zeros((max(n, 1), 15), np.float64)
+    motion = np.zeros(max(n, 1), np.int32)
+    lib().sffi_seed_models(_p(seeds) if n else None, n, ctypes.byref(params), _p(plane), _p(affine), _p(motion))
+    return plane[:n], affine[:n], motion[:n]
+
+
+def interpolate_pixels(seeds, params: InterpParams, pixels, models=None):
+    """Interpolated (u, v, d0, d1) float32 [m, 4] and closest seed [m] at the
+    listed pixels [m, 2] (x, y)."""
+    seeds = np.ascontiguousarray(seeds, SEED_DTYPE)
+    plane, affine, motion = models if models is not None else seed_models(seeds, params)
+    pixels = np.ascontiguousarray(pixels, np.int32).reshape(-1, 2)
+    m = len(pixels)
+    out = np.zeros((max(m, 1), 4), np.float32)
+    closest = np.zeros(max(m, 1), np.int32)
+    plane = np.ascontiguousarray(plane, np.float64)
+    affine = np.ascontiguousarray(affine, np.float64)
+    motion = np.ascontiguousarray(motion, np.int32)
+    lib().sffi_interpolate_pixels(_p(seeds) if len(seeds) else None, len(seeds), ctypes.byref(params),
+                                  _p(plane) if len(seeds) else None, _p(affine) if len(seeds) else None,
+                                  _p(motion) if len(seeds) else None, _p(pixels), m, _p(out), _p(closest))
+    return out[:m], closest[:m]
+
+
+def interpolate(seeds, width: int, height: int, params: InterpParams):
+    """Dense interpolated field float32 [H, W, 4] (u, v, d0, d1)."""
+    ys, xs = np.mgrid[0:height, 0:width]
+    pix = np.stack([xs.ravel(), ys.ravel()], 1).astype(np.int32)
+    out, _ = interpolate_pixels(seeds, params, pix)
+    return out.reshape(height, width, 4)
+
+
+def nearest_seeds(seeds, x: int, y: int, k: int, motion_only: bool = False):
+    """Indices and squared distances of the k nearest seeds to (x, y)."""
+    seeds = np.ascontiguousarray(seeds, SEED_DTYPE)
+    idx = np.zeros(max(k, 1), np.int32)
+    d2 = np.zeros(max(k, 1), np.int64)
+    cnt = ctypes.c_int32(0)
+    lib().sffi_nearest(_p(seeds), len(seeds), x, y, k, int(motion_only), _p(idx), _p(d2), ctypes.byref(cnt))
+    return idx[:cnt.value], d2[:cnt.value]

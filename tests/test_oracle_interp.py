@@ -1,0 +1,114 @@
+"""Pins of the interpolation oracle (Sec. 3.3): closed forms it must reproduce,
+independent of its own formulas."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+
+def _seeds(rows):
+    s = np.zeros(len(rows), oracle.SEED_DTYPE)
+    for k, (x, y, u, v, d0, d1) in enumerate(rows):
+        s[k]["x"], s[k]["y"], s[k]["u"], s[k]["v"], s[k]["d0"], s[k]["d1"] = x, y, u, v, d0, d1
+    return s
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    oracle.build()
+
+
+def _plane_motion_seeds(w, h, step=3, jitter_seed=1):
+    # seeds sampled from a known scene: plane d0 = 40 + x - y, 3D motion
+    # x1 = 0.5 x0 + (B/2, 0, 0): in the image u = d0, v = 0, d1 = 2 d0 (exact
+    # integers at integer positions)
+    rng = np.random.default_rng(jitter_seed)
+    rows = []
+    for by in range(0, h, step):
+        for bx in range(0, w, step):
+            x = min(w - 1, bx + int(rng.integers(0, step)))
+            y = min(h - 1, by + int(rng.integers(0, step)))
+            d0 = 40 + x - y
+            rows.append((x, y, d0, 0, d0, 2 * d0))
+    return _seeds(rows)
+
+
+def test_exact_plane_and_affine_motion_are_reproduced_everywhere():
+    w, h, f, B = 48, 30, 300.0, 0.5
+    s = _plane_motion_seeds(w, h)
+    p = oracle.interp_params(w, h, f, B, k_geo=40, k_motion=24)
+    out = oracle.interpolate(s, w, h, p)
+    ys, xs = np.mgrid[0:h, 0:w]
+    d0 = 40.0 + xs - ys
+    assert np.allclose(out[..., 2], d0, atol=1e-3)      # plane
+    assert np.allclose(out[..., 0], d0, atol=1e-3)      # u = d0 from the X translation
+    assert np.allclose(out[..., 1], 0.0, atol=1e-3)     # v
+    assert np.allclose(out[..., 3], 2 * d0, atol=1e-3)  # d1 from Z halved
+
+
+def test_weighted_plane_of_a_symmetric_star():
+    # the seed at (10, 10) with d0 = 0 and four neighbours 3 px away with
+    # d0 = 6: by symmetry the plane is flat at the weighted mean
+    # 4 * 6 w / (1 + 4 w), w = exp(-alpha * 3 / dist_unit)
+    s = _seeds([(10, 10, 0, 0, 0, 0), (13, 10, 0, 0, 6, 0), (7, 10, 0, 0, 6, 0), (10, 13, 0, 0, 6, 0),
+                (10, 7, 0, 0, 6, 0)])
+    p = oracle.interp_params(32, 32, 300.0, 0.5, k_geo=5, k_motion=5)
+    plane, _, _ = oracle.seed_models(s, p)
+    wgt = math.exp(-2.2 * 3 / 20.0)
+    want = 24 * wgt / (1 + 4 * wgt)
+    assert plane[0][0] == pytest.approx(0.0, abs=1e-6)  # slopes (coordinates centred at the seed)
+    assert plane[0][1] == pytest.approx(0.0, abs=1e-6)
+    assert plane[0][2] == pytest.approx(want, abs=1e-6)
+
+
+def test_neighbourhood_on_a_lattice_and_ties():
+    # seeds on a 3-px lattice: the 5 nearest to a lattice point are itself and
+    # its 4 axis neighbours; with k = 3 the tie at distance 3 goes to the lower
+    # seed indices (raster order: the upper, then the left neighbour)
+    rows = [(x, y, 0, 0, 5, 5) for y in range(0, 15, 3) for x in range(0, 15, 3)]
+    s = _seeds(rows)
+    centre = rows.index((6, 6, 0, 0, 5, 5))
+    idx, d2 = oracle.nearest_seeds(s, 6, 6, 5)
+    assert idx[0] == centre and d2[0] == 0
+    assert sorted((rows[i][0], rows[i][1]) for i in idx[1:]) == [(3, 6), (6, 3), (6, 9), (9, 6)]
+    assert list(d2[1:]) == [9, 9, 9, 9]
+    idx3, _ = oracle.nearest_seeds(s, 6, 6, 3)
+    assert [(rows[i][0], rows[i][1]) for i in idx3] == [(6, 6), (6, 3), (3, 6)]
+
+
+def test_motion_neighbourhood_skips_seeds_that_cannot_be_triangulated():
+    s = _seeds([(5, 5, 0, 0, 4, 4), (6, 5, 0, 0, 0, 4), (7, 5, 0, 0, 4, 0), (9, 5, 0, 0, 3, 3)])
+    idx, _ = oracle.nearest_seeds(s, 5, 5, 4, motion_only=True)
+    assert list(idx) == [0, 3]
+    _, _, motion = oracle.seed_models(s, oracle.interp_params(16, 16, 300.0, 0.5))
+    assert list(motion) == [2, 2, 2, 2]
+
+
+def test_closest_seed_ties_go_to_the_lower_index():
+    s = _seeds([(2, 4, 0, 0, 7, 7), (6, 4, 0, 0, 9, 9)])
+    p = oracle.interp_params(9, 9, 300.0, 0.5, k_geo=1, k_motion=1)
+    out, closest = oracle.interpolate_pixels(s, p, [[4, 4], [5, 4], [3, 4]])
+    assert list(closest) == [0, 1, 0]
+    # one neighbour: a flat plane at the seed's own disparity (the ridge on
+    # the slopes keeps the system solvable)
+    assert out[0][2] == pytest.approx(7.0, abs=1e-4)
+    assert out[1][2] == pytest.approx(9.0, abs=1e-4)
+
+
+def test_no_motion_neighbours_gives_zero_flow_and_equal_disparities():
+    s = _seeds([(4, 4, 3, 1, 6, 0)])  # d1 = 0: not a motion seed
+    p = oracle.interp_params(8, 8, 300.0, 0.5)
+    out, _ = oracle.interpolate_pixels(s, p, [[4, 4]])
+    assert out[0][0] == 0 and out[0][1] == 0
+    assert out[0][3] == pytest.approx(out[0][2])
+
+
+def test_single_motion_neighbour_is_a_translation():
+    # one motion seed: A defaults to the identity, the map is the seed's 3D
+    # translation; the pixel at the seed itself moves exactly like the seed
+    s = _seeds([(6, 5, 3, -2, 8, 10)])
+    p = oracle.interp_params(16, 12, 300.0, 0.5)
+    out, _ = oracle.interpolate_pixels(s, p, [[6, 5]])
+    assert out[0] == pytest.approx([3.0, -2.0, 8.0, 10.0], abs=1e-4)
