@@ -81,6 +81,7 @@ def lib():
         L.sffo_cost.argtypes = [P, P, P, P, i32, i32, i32, i32, i32, P]
         L.sffo_cost.restype = i32
         L.sffi_seed_models.argtypes = [P, i32, ctypes.POINTER(InterpParams), P, P, P]
+        L.sffi_seed_models_of.argtypes = [P, i32, ctypes.POINTER(InterpParams), P, i32, P, P, P]
         L.sffi_interpolate_pixels.argtypes = [P, i32, ctypes.POINTER(InterpParams), P, P, P, P, i32, P, P]
         L.sffi_nearest.argtypes = [P, i32, i32, i32, i32, i32, P, P, P]
         L.sffi_set_threads.argtypes = [i32]
@@ -244,16 +245,31 @@ def interp_params(width: int, height: int, focal: float, baseline: float, **over
     return InterpParams(**p)
 
 
-def seed_models(seeds, params: InterpParams):
+def seed_models(seeds, params: InterpParams, which=None):
     """(plane [n, 3], affine [n, 15] = [A | t] rows then the centre, motion
-    neighbour count [n]) of every seed."""
+    neighbour count [n]) of every seed, or only of the seeds listed in
+    `which` (the other rows stay zero)."""
     seeds = np.ascontiguousarray(seeds, SEED_DTYPE)
     n = len(seeds)
     plane = np.zeros((max(n, 1), 3), np.float64)
     affine = np.zeros((max(n, 1), 15), np.float64)
     motion = np.zeros(max(n, 1), np.int32)
-    lib().sffi_seed_models(_p(seeds) if n else None, n, ctypes.byref(params), _p(plane), _p(affine), _p(motion))
+    if which is None:
+        lib().sffi_seed_models(_p(seeds) if n else None, n, ctypes.byref(params), _p(plane), _p(affine), _p(motion))
+    else:
+        which = np.ascontiguousarray(np.unique(np.asarray(which, np.int64)), np.int32)
+        assert n == 0 or (which.min(initial=0) >= 0 and which.max(initial=0) < n)
+        if len(which):
+            lib().sffi_seed_models_of(_p(seeds), n, ctypes.byref(params), _p(which), len(which), _p(plane),
+                                      _p(affine), _p(motion))
     return plane[:n], affine[:n], motion[:n]
+
+
+def closest_seeds(seeds, pixels):
+    """Closest seed [m] of the listed pixels [m, 2] (x, y), ties to the lower index."""
+    seeds = np.ascontiguousarray(seeds, SEED_DTYPE)
+    pixels = np.asarray(pixels, np.int64).reshape(-1, 2)
+    return np.array([nearest_seeds(seeds, int(x), int(y), 1)[0][0] for x, y in pixels], np.int32)
 
 
 def interpolate_pixels(seeds, params: InterpParams, pixels, models=None):

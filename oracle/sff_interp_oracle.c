@@ -158,77 +158,88 @@ static double ridge_of(const double* M, int n) {
     return 1e-9 * tr / n + 1e-300;
 }
 
-/* Models of every seed: plane[3] (a1, a2, a3 of d0 = a1 (x - xs) + a2 (y - ys)
+/* Models of seed s: plane[3] (a1, a2, a3 of d0 = a1 (x - xs) + a2 (y - ys)
  * + a3), affine[15] (rows of [A | t], then the centre c);
  * has_motion = number of motion neighbours (0: none). */
-void sffi_seed_models(const sffi_seed* seeds, int n, const sffi_params* P, double* plane, double* affine,
-                      int32_t* has_motion) {
+static void fit_seed(const sffi_seed* seeds, int n, const sffi_params* P, int s, nb_t* buf, nb_t* nb,
+                     double* plane, double* affine, int32_t* has_motion) {
+    const int sx = seeds[s].x, sy = seeds[s].y;
+    /* geometry: plane through the k_geo nearest seeds */
+    int c = nearest(seeds, n, sx, sy, P->k_geo, NULL, buf, nb);
+    double M[9] = {0}, b[3] = {0};
+    for (int i = 0; i < c; i++) {
+        const sffi_seed* g = seeds + nb[i].idx;
+        const double w = exp(-P->alpha * sqrt((double)nb[i].d2) / P->dist_unit);
+        const double r[3] = {(double)(g->x - sx), (double)(g->y - sy), 1.0};
+        for (int a = 0; a < 3; a++) {
+            for (int e = 0; e < 3; e++) M[a * 3 + e] += w * r[a] * r[e];
+            b[a] += w * r[a] * g->d0;
+        }
+    }
+    {
+        const double lam = ridge_of(M, 3);
+        M[0] += lam;
+        M[4] += lam;
+    }
+    solve_spd(M, 3, b, 1);
+    memcpy(plane + 3 * (size_t)s, b, sizeof b);
+    /* motion: affine map through the k_motion nearest motion seeds */
+    c = nearest(seeds, n, sx, sy, P->k_motion, motion_seed, buf, nb);
+    double N[16] = {0}, rhs[12] = {0}, cen[3] = {0, 0, 0}, wsum = 0.0;
+    for (int i = 0; i < c; i++) {  /* weighted centroid of the x0 */
+        const sffi_seed* g = seeds + nb[i].idx;
+        const double w = exp(-P->alpha * sqrt((double)nb[i].d2) / P->dist_unit);
+        double X0[3];
+        triangulate(P, g->x, g->y, g->d0, X0);
+        for (int j = 0; j < 3; j++) cen[j] += w * X0[j];
+        wsum += w;
+    }
+    for (int j = 0; j < 3 && c > 0; j++) cen[j] /= wsum;
+    for (int i = 0; i < c; i++) {
+        const sffi_seed* g = seeds + nb[i].idx;
+        const double w = exp(-P->alpha * sqrt((double)nb[i].d2) / P->dist_unit);
+        double X0[3], X1[3];
+        triangulate(P, g->x, g->y, g->d0, X0);
+        triangulate(P, g->x + g->u, g->y + g->v, g->d1, X1);
+        const double r[4] = {X0[0] - cen[0], X0[1] - cen[1], X0[2] - cen[2], 1.0};
+        for (int a = 0; a < 4; a++) {
+            for (int e = 0; e < 4; e++) N[a * 4 + e] += w * r[a] * r[e];
+            for (int j = 0; j < 3; j++) rhs[j * 4 + a] += w * r[a] * X1[j];
+        }
+    }
+    if (c > 0) {
+        const double lam = ridge_of(N, 4);
+        for (int a = 0; a < 3; a++) {
+            N[a * 4 + a] += lam;
+            rhs[a * 4 + a] += lam;  /* towards A = I */
+        }
+        solve_spd(N, 4, rhs, 3);
+    }
+    memcpy(affine + 15 * (size_t)s, rhs, sizeof rhs);
+    memcpy(affine + 15 * (size_t)s + 12, cen, sizeof cen);
+    has_motion[s] = c;
+}
+
+/* Models of the seeds listed in which[0 .. m) (NULL: of all n seeds); the
+ * other entries of plane / affine / has_motion are left untouched. */
+void sffi_seed_models_of(const sffi_seed* seeds, int n, const sffi_params* P, const int32_t* which, int m,
+                         double* plane, double* affine, int32_t* has_motion) {
+    const int cnt = which ? m : n;
     #pragma omp parallel num_threads(g_ithreads)
     {
         nb_t* buf = (nb_t*)malloc(sizeof(nb_t) * (size_t)(n > 0 ? n : 1));
         const int kmax = P->k_geo > P->k_motion ? P->k_geo : P->k_motion;
         nb_t* nb = (nb_t*)malloc(sizeof(nb_t) * (size_t)(kmax > 0 ? kmax : 1));
         #pragma omp for schedule(dynamic, 16)
-        for (int s = 0; s < n; s++) {
-            const int sx = seeds[s].x, sy = seeds[s].y;
-            /* geometry: plane through the k_geo nearest seeds */
-            int c = nearest(seeds, n, sx, sy, P->k_geo, NULL, buf, nb);
-            double M[9] = {0}, b[3] = {0};
-            for (int i = 0; i < c; i++) {
-                const sffi_seed* g = seeds + nb[i].idx;
-                const double w = exp(-P->alpha * sqrt((double)nb[i].d2) / P->dist_unit);
-                const double r[3] = {(double)(g->x - sx), (double)(g->y - sy), 1.0};
-                for (int a = 0; a < 3; a++) {
-                    for (int e = 0; e < 3; e++) M[a * 3 + e] += w * r[a] * r[e];
-                    b[a] += w * r[a] * g->d0;
-                }
-            }
-            {
-                const double lam = ridge_of(M, 3);
-                M[0] += lam;
-                M[4] += lam;
-            }
-            solve_spd(M, 3, b, 1);
-            memcpy(plane + 3 * (size_t)s, b, sizeof b);
-            /* motion: affine map through the k_motion nearest motion seeds */
-            c = nearest(seeds, n, sx, sy, P->k_motion, motion_seed, buf, nb);
-            double N[16] = {0}, rhs[12] = {0}, cen[3] = {0, 0, 0}, wsum = 0.0;
-            for (int i = 0; i < c; i++) {  /* weighted centroid of the x0 */
-                const sffi_seed* g = seeds + nb[i].idx;
-                const double w = exp(-P->alpha * sqrt((double)nb[i].d2) / P->dist_unit);
-                double X0[3];
-                triangulate(P, g->x, g->y, g->d0, X0);
-                for (int j = 0; j < 3; j++) cen[j] += w * X0[j];
-                wsum += w;
-            }
-            for (int j = 0; j < 3 && c > 0; j++) cen[j] /= wsum;
-            for (int i = 0; i < c; i++) {
-                const sffi_seed* g = seeds + nb[i].idx;
-                const double w = exp(-P->alpha * sqrt((double)nb[i].d2) / P->dist_unit);
-                double X0[3], X1[3];
-                triangulate(P, g->x, g->y, g->d0, X0);
-                triangulate(P, g->x + g->u, g->y + g->v, g->d1, X1);
-                const double r[4] = {X0[0] - cen[0], X0[1] - cen[1], X0[2] - cen[2], 1.0};
-                for (int a = 0; a < 4; a++) {
-                    for (int e = 0; e < 4; e++) N[a * 4 + e] += w * r[a] * r[e];
-                    for (int j = 0; j < 3; j++) rhs[j * 4 + a] += w * r[a] * X1[j];
-                }
-            }
-            if (c > 0) {
-                const double lam = ridge_of(N, 4);
-                for (int a = 0; a < 3; a++) {
-                    N[a * 4 + a] += lam;
-                    rhs[a * 4 + a] += lam;  /* towards A = I */
-                }
-                solve_spd(N, 4, rhs, 3);
-            }
-            memcpy(affine + 15 * (size_t)s, rhs, sizeof rhs);
-            memcpy(affine + 15 * (size_t)s + 12, cen, sizeof cen);
-            has_motion[s] = c;
-        }
+        for (int k = 0; k < cnt; k++) fit_seed(seeds, n, P, which ? which[k] : k, buf, nb, plane, affine, has_motion);
         free(buf);
         free(nb);
     }
+}
+
+void sffi_seed_models(const sffi_seed* seeds, int n, const sffi_params* P, double* plane, double* affine,
+                      int32_t* has_motion) {
+    sffi_seed_models_of(seeds, n, P, NULL, 0, plane, affine, has_motion);
 }
 
 /* The models of seed s evaluated at pixel (x, y): out[4] = (u, v, d0, d1). */

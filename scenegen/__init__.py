@@ -29,7 +29,7 @@ from __future__ import annotations
 import dataclasses
 import numpy as np
 
-__all__ = ["Quad", "make_quad", "make_shift_quad", "CONFIG_SIZES"]
+__all__ = ["Quad", "make_quad", "make_shift_quad", "CONFIG_SIZES", "ground_truth", "SEED_RECORD", "sparse_seeds"]
 
 # (family, width, height) of the named workloads.
 CONFIG_SIZES = {
@@ -462,6 +462,52 @@ def make_quad(family: str, width: int, height: int, seed: int, supersample: int 
     else:
         gt, occ = np.zeros((height, width, 4)), np.zeros((height, width), bool)
     return Quad(L0, R0, L1, R1, gt, occ, cam0.f, cam0.B)
+
+
+def ground_truth(family: str, width: int, height: int, seed: int):
+    """(gt [H, W, 4], occluded [H, W], focal, baseline) of the scene that
+    make_quad(family, width, height, seed) renders, without rendering it."""
+    rng = np.random.default_rng(seed)
+    surfs, cam0, cam1, _ = _FAMILIES[family](rng, width, height)
+    gt, occ = _ground_truth(surfs, cam0, cam1, width, height)
+    return gt, occ, cam0.f, cam0.B
+
+
+# 20-byte seed record of the sparse matches (x, y, u, v, d0, d1, cost, cerr)
+SEED_RECORD = np.dtype([("x", "<i2"), ("y", "<i2"), ("u", "<i2"), ("v", "<i2"), ("d0", "<i2"), ("d1", "<i2"),
+                        ("cost", "<i4"), ("cerr", "u1"), ("pad", "u1", (3,))])
+
+
+def sparse_seeds(gt: np.ndarray, occluded: np.ndarray, seed: int, keep: float = 0.6, noise: float = 0.0,
+                 outliers: float = 0.0, block: int = 3) -> np.ndarray:
+    """Synthetic sparse matches with the structure of the matching stage's
+    output: at most one pixel per non-overlapping block x block cell
+    (anchored at (0, 0)), in cell raster order.  Each cell draws a pixel
+    uniformly inside it; a visible pixel is kept with probability `keep` and
+    carries its ground-truth vector plus Gaussian noise of `noise` px, a
+    fraction `outliers` of them a uniform random vector instead, rounded to
+    integers with disparities >= 0.  cost and cerr are random."""
+    rng = np.random.default_rng(seed)
+    H, W = occluded.shape
+    gbw, gbh = -(-W // block), -(-H // block)
+    by, bx = np.mgrid[0:gbh, 0:gbw]
+    x = np.minimum(W - 1, bx * block + rng.integers(0, block, bx.shape))
+    y = np.minimum(H - 1, by * block + rng.integers(0, block, by.shape))
+    take = (rng.random(bx.shape) < keep) & ~occluded[y, x]
+    x, y = x[take], y[take]
+    vec = gt[y, x] + noise * rng.standard_normal((len(x), 4))
+    bad = rng.random(len(x)) < outliers
+    span = np.array([W / 4, H / 8, W / 8, W / 8])
+    vec[bad] = rng.uniform(-1, 1, (int(bad.sum()), 4)) * span
+    vec = np.rint(vec)
+    vec[:, 2:] = np.clip(np.abs(vec[:, 2:]), 0, 32767)
+    vec = np.clip(vec, -32768, 32767)
+    out = np.zeros(len(x), SEED_RECORD)
+    out["x"], out["y"] = x, y
+    out["u"], out["v"], out["d0"], out["d1"] = vec[:, 0], vec[:, 1], vec[:, 2], vec[:, 3]
+    out["cost"] = rng.integers(0, 1 << 20, len(x))
+    out["cerr"] = rng.integers(0, 4, len(x))
+    return out
 
 
 def make_named(name: str, seed: int, **kw) -> Quad:

@@ -112,3 +112,30 @@ def test_single_motion_neighbour_is_a_translation():
     p = oracle.interp_params(16, 12, 300.0, 0.5)
     out, _ = oracle.interpolate_pixels(s, p, [[6, 5]])
     assert out[0] == pytest.approx([3.0, -2.0, 8.0, 10.0], abs=1e-4)
+
+
+def test_models_of_listed_seeds_equal_the_full_fit():
+    s = _plane_motion_seeds(40, 28, jitter_seed=3)
+    s["d0"][::5] += 3  # not an exact plane any more
+    p = oracle.interp_params(40, 28, 300.0, 0.5, k_geo=25, k_motion=12)
+    full = oracle.seed_models(s, p)
+    which = [0, 7, 7, len(s) - 1, 30]
+    part = oracle.seed_models(s, p, which=which)
+    for a, b in zip(full, part):
+        assert np.array_equal(a[sorted(set(which))], b[sorted(set(which))])
+    rest = np.setdiff1d(np.arange(len(s)), which)
+    assert (part[0][rest] == 0).all() and (part[2][rest] == 0).all()
+
+
+def test_synthetic_seeds_have_the_structure_of_sparse_matches():
+    import scenegen
+    gt, occ, f, B = scenegen.ground_truth("driving", 121, 47, 2)
+    s = scenegen.sparse_seeds(gt, occ, 4, keep=0.7, noise=1.0, outliers=0.1)
+    assert s.dtype.itemsize == 20 and s.dtype == oracle.SEED_DTYPE
+    blk = (s["y"] // 3) * (-(-121 // 3)) + s["x"] // 3
+    assert (np.diff(blk) > 0).all()  # one per 3x3 block, block raster order
+    assert (s["x"] >= 0).all() and (s["x"] < 121).all() and (s["y"] >= 0).all() and (s["y"] < 47).all()
+    assert (s["d0"] >= 0).all() and (s["d1"] >= 0).all()
+    assert not occ[s["y"], s["x"]].any()
+    exact = scenegen.sparse_seeds(gt, occ, 4, keep=0.7)
+    assert np.array_equal(exact["d0"], np.rint(gt[exact["y"], exact["x"], 2]))
