@@ -17,6 +17,8 @@
  *     sff_match_views         initialisation + multi-scale propagation + random search
  *     sff_consistency_filter  forward/inverse consistency check + region filter
  *     sff_emit_seeds          3x3 sparsification into seeds (Sec. 3.2)
+ * and the dense interpolation of the seeds (Sec. 3.3):
+ *     sff_interpolate         per-seed plane and affine 3D motion, per-pixel evaluation
  *
  * Conventions for every call:
  *   - Pointers named *_dev, and every image/pyramid/field buffer, are DEVICE
@@ -257,6 +259,64 @@ int sff_emit_seeds_noalloc(const int16_t* fwd_dev, const int32_t* fwd_cost_dev,
                            const uint8_t* keep_dev, const uint8_t* cerr_dev,
                            int32_t width, int32_t height, sff_seed* seeds_dev, int32_t capacity,
                            int32_t* count_dev, void* stream);
+
+/* Dense interpolation of the seeds (Sec. 3.3, "Interpolation Models" and
+ * "Edge-Aware Neighborhood"), with Euclidean pixel distances in place of the
+ * geodesic ones (the edge map comes from a trained boundary detector, which
+ * is not part of this library).
+ *   - Every seed gets two local models, fitted by weighted least squares over
+ *     its nearest seeds, weight exp(-alpha * D / dist_unit) for a neighbour D
+ *     pixels away, ties in the distance order to the lower seed index:
+ *       geometry: the plane d0 = a1 (x - xs) + a2 (y - ys) + a3 over the k_geo
+ *       nearest seeds;
+ *       motion: the affine map X1 = A (X0 - c) + t of 3D points over the
+ *       k_motion nearest motion seeds (d0 >= 1 and d1 >= 1), X0 triangulated
+ *       from (x, y, d0) and X1 from (x + u, y + v, d1) with the pinhole camera
+ *       Z = focal * baseline / d, X = (x - cx) Z / focal, Y = (y - cy) Z / focal,
+ *       c the weighted centroid of the X0.
+ *     The linear parts get a ridge of 1e-9 * trace / dimension towards a flat
+ *     plane and A = I (too few seeds: a constant disparity, a translation).
+ *     Systems are solved by Cholesky factorisation in double precision.
+ *   - Every pixel takes the models of its closest seed (same order) and
+ *     evaluates them: d0 from the plane, then X0 from (x, y, max(d0, 1)),
+ *     X1 = A (X0 - c) + t projected back gives u, v and d1.  Without motion
+ *     neighbours, or when Z1 <= 0, u = v = 0 and d1 = d0.
+ *   - No seeds: the field is all zeros. */
+typedef struct sff_interp_params {
+    int32_t k_geo, k_motion;   /* neighbourhood sizes, 1 ... 1024 */
+    double alpha, dist_unit;   /* weight exp(-alpha * D / dist_unit) */
+    double focal, baseline;    /* pixels; any unit of length */
+    double cx, cy;             /* principal point, pixels */
+} sff_interp_params;
+
+/* Defaults: k_geo 160, k_motion 80, alpha 2.2, dist_unit 20 px, principal
+ * point at the image centre ((W - 1) / 2, (H - 1) / 2).  SFF_ERR_ARG for a
+ * NULL out, a size below 1 or a focal length or baseline that is not > 0. */
+int sff_default_interp_params(int32_t width, int32_t height, double focal, double baseline,
+                              sff_interp_params* out);
+
+/* Scratch of sff_interpolate: one int32 per 3x3 block, 144 bytes of models
+ * and 4 bytes per seed of `capacity`; 0 for invalid arguments. */
+size_t sff_interp_workspace_bytes(int32_t width, int32_t height, int32_t capacity);
+
+/* Interpolates the seeds of sff_emit_seeds (seeds_dev, count_dev: device;
+ * min(*count_dev, capacity) seeds are used) into field_dev: [H][W][4] float
+ * (u, v, d0, d1), device, 16-byte aligned, overwritten.  params: host, read
+ * during the call.  The seeds must lie in the image with at most one seed per
+ * 3x3 block anchored at (0, 0), as sff_emit_seeds writes them.
+ * Errors found on the GPU (a second seed in one block, a seed outside the
+ * image, more than 2048 neighbour candidates of one seed) set bits of a
+ * status word in the workspace (read it with sff_interp_status) and the
+ * field is all zeros. */
+int sff_interpolate(const sff_seed* seeds_dev, const int32_t* count_dev, int32_t capacity, int32_t width,
+                    int32_t height, const sff_interp_params* params, float* field_dev, void* workspace,
+                    size_t workspace_bytes, void* stream);
+
+/* Copies the status word of the last sff_interpolate on `workspace` into
+ * *status_out (host) after a synchronous device-to-host copy (it waits for
+ * the work on the legacy default stream): 0 = no error, bit 0 = a duplicate
+ * or out-of-image seed, bit 1 = too many neighbour candidates. */
+int sff_interp_status(const void* workspace, int32_t width, int32_t height, int32_t capacity, uint32_t* status_out);
 
 /* One quad of a batch: its images, outputs and scratch (device pointers).
  * The four images share one pitch; seeds are written as by sff_emit_seeds. */

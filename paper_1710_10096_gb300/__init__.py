@@ -20,6 +20,7 @@ import numpy as np
 __all__ = ["Params", "Tuning", "SffError", "default_params", "default_tuning", "make_tuning", "pyramid_bytes",
            "workspace_bytes", "quad_workspace_bytes", "features", "match_views", "match_quad", "match_quad_tuned",
            "consistency_filter", "emit_seeds", "run_batch", "QuadBuffers", "BatchMatcher", "QuadMatcher",
+           "InterpParams", "default_interp_params", "interp_workspace_bytes", "interpolate", "interp_status",
            "SEED_DTYPE", "lib", "build"]
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -66,6 +67,13 @@ class QuadDesc(ctypes.Structure):
 
 
 MAX_BATCH = 32
+
+
+class InterpParams(ctypes.Structure):
+    """sff_interp_params: neighbourhood sizes, weight kernel and camera (Sec. 3.3)."""
+    _fields_ = [("k_geo", ctypes.c_int32), ("k_motion", ctypes.c_int32), ("alpha", ctypes.c_double),
+                ("dist_unit", ctypes.c_double), ("focal", ctypes.c_double), ("baseline", ctypes.c_double),
+                ("cx", ctypes.c_double), ("cy", ctypes.c_double)]
 
 
 class KernelTime(ctypes.Structure):
@@ -138,6 +146,15 @@ def lib():
         L.sff_emit_seeds.restype = i32
         L.sff_emit_seeds_noalloc.argtypes = [P, P, P, P, i32, i32, P, i32, P, P]
         L.sff_emit_seeds_noalloc.restype = i32
+        IP = ctypes.POINTER(InterpParams)
+        L.sff_default_interp_params.argtypes = [i32, i32, ctypes.c_double, ctypes.c_double, IP]
+        L.sff_default_interp_params.restype = i32
+        L.sff_interp_workspace_bytes.argtypes = [i32, i32, i32]
+        L.sff_interp_workspace_bytes.restype = sz
+        L.sff_interpolate.argtypes = [P, P, i32, i32, i32, IP, P, P, sz, P]
+        L.sff_interpolate.restype = i32
+        L.sff_interp_status.argtypes = [P, i32, i32, i32, ctypes.POINTER(ctypes.c_uint32)]
+        L.sff_interp_status.restype = i32
         L.sff_profile_enable.argtypes = [i32]
         L.sff_profile_enable.restype = i32
         L.sff_profile_collect.argtypes = [ctypes.POINTER(KernelTime), i32, ctypes.POINTER(i32)]
@@ -288,6 +305,36 @@ def emit_seeds(fwd, fwd_cost, keep, cerr, seeds, capacity: int, count, workspace
     assert _nbytes(seeds) >= 20 * capacity
     _check(lib().sff_emit_seeds(_ptr(fwd), _ptr(fwd_cost), _ptr(keep), _ptr(cerr), w, h, _ptr(seeds), capacity,
                                 _ptr(count), _ptr(workspace), _nbytes(workspace), _stream(stream)), "sff_emit_seeds")
+
+
+def default_interp_params(width: int, height: int, focal: float, baseline: float, **overrides) -> InterpParams:
+    p = InterpParams()
+    _check(lib().sff_default_interp_params(width, height, float(focal), float(baseline), ctypes.byref(p)),
+           "sff_default_interp_params")
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def interp_workspace_bytes(width: int, height: int, capacity: int) -> int:
+    return lib().sff_interp_workspace_bytes(width, height, capacity)
+
+
+def interpolate(seeds, count, capacity: int, width: int, height: int, params: InterpParams, field, workspace,
+                stream=None) -> None:
+    """seeds: CUDA tensor of >= 20 * capacity bytes; count: CUDA int32 [1];
+    field: CUDA float32 [H][W][4] (u, v, d0, d1), overwritten."""
+    assert _nbytes(seeds) >= 20 * capacity and _nbytes(field) >= 16 * width * height
+    _check(lib().sff_interpolate(_ptr(seeds), _ptr(count), capacity, width, height, ctypes.byref(params),
+                                 _ptr(field), _ptr(workspace), _nbytes(workspace), _stream(stream)),
+           "sff_interpolate")
+
+
+def interp_status(workspace, width: int, height: int, capacity: int) -> int:
+    """Error bits the last interpolate on `workspace` set (0: none)."""
+    v = ctypes.c_uint32(0)
+    _check(lib().sff_interp_status(_ptr(workspace), width, height, capacity, ctypes.byref(v)), "sff_interp_status")
+    return v.value
 
 
 def device_timeouts(reset: bool = False) -> int:
