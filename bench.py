@@ -324,6 +324,118 @@ def bench_paper_order(sff, torch, dev, m, q, params, reps=3):
             "checkerboard_ms": out["checkerboard"], "slowdown": out["paper_order"] / out["checkerboard"]}
 
 
+# nominal dense FP64 rate of a GB300 (the double-precision fits are bound by it)
+FP64_PEAK_GFLOPS = 1250.0
+
+
+def field_quality(field, q):
+    """Outlier rates of the dense field against the scene's ground truth on
+    the pixels visible in all four views (the KITTI scene flow measures of
+    Table 1: an estimate is an outlier when its error exceeds 3 px and 5 %
+    of the true value; SF = any of D1, D2, Fl)."""
+    m = ~q.occluded
+    f = field[m].astype(np.float64)
+    g = q.gt[m]
+    e0, e1 = np.abs(f[:, 2] - g[:, 2]), np.abs(f[:, 3] - g[:, 3])
+    ef = np.hypot(f[:, 0] - g[:, 0], f[:, 1] - g[:, 1])
+    d1 = (e0 > 3) & (e0 > 0.05 * np.abs(g[:, 2]))
+    d2 = (e1 > 3) & (e1 > 0.05 * np.abs(g[:, 3]))
+    fl = (ef > 3) & (ef > 0.05 * np.hypot(g[:, 0], g[:, 1]))
+    return {"D1": float(d1.mean()), "D2": float(d2.mean()), "Fl": float(fl.mean()), "SF": float((d1 | d2 | fl).mean()),
+            "epe_flow": float(ef.mean()), "mae_d0": float(e0.mean()), "mae_d1": float(e1.mean()),
+            "pixels": int(m.sum())}
+
+
+def bench_interpolation(sff, torch, dev, m, q, params, steps, warmup, cpu: bool):
+    """Dense interpolation (Sec. 3.3) of the quad's seeds on the GPU: the
+    interpolation alone and the whole method (matching stage + interpolation)
+    as one CUDA graph, both timed with CUDA events after an L2 flush; the
+    per-kernel profile; the FP64 roofline of the model fits; the quality of
+    the dense field; the oracle on a bounded sample."""
+    w, h = q.width, q.height
+    ip = sff.default_interp_params(w, h, q.focal, q.baseline)
+    field = torch.empty((h, w, 4), dtype=torch.float32, device=dev)
+    ws = torch.empty(sff.interp_workspace_bytes(w, h, m.capacity), dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    dev_in = [torch.as_tensor(im).to(dev) for im in q.images()]
+
+    def interp():
+        sff.interpolate(m.seeds, m.count, m.capacity, w, h, ip, field, ws, stream=stream)
+
+    with torch.cuda.stream(stream):
+        m.run(*dev_in, seed=MATCH_SEED, stream=stream)
+        for _ in range(max(1, warmup)):
+            interp()
+        stream.synchronize()
+        sff.profile_enable(True)
+        for _ in range(3):
+            flush.zero_()
+            interp()
+        stream.synchronize()
+        prof = sff.profile_collect()
+        sff.profile_enable(False)
+        g1, g2 = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g1, stream=stream):
+            sff.interpolate(m.seeds, m.count, m.capacity, w, h, ip, field, ws, stream=torch.cuda.current_stream())
+        with torch.cuda.graph(g2, stream=stream):
+            m.run(*dev_in, seed=MATCH_SEED, stream=torch.cuda.current_stream())
+            sff.interpolate(m.seeds, m.count, m.capacity, w, h, ip, field, ws, stream=torch.cuda.current_stream())
+        times = {}
+        for name, g in (("interp", g1), ("method", g2)):
+            for _ in range(max(1, warmup)):
+                g.replay()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for a, b in ev:
+                flush.zero_()
+                a.record(stream)
+                g.replay()
+                b.record(stream)
+            stream.synchronize()
+            times[name] = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    status = sff.interp_status(ws, w, h, m.capacity)
+    n = min(int(m.count.item()), m.capacity)
+    out = {"what": "dense interpolation of the quad's GPU seeds (sff_interpolate) and the whole method "
+                   "(matching stage + interpolation, one CUDA graph); ms per quad, L2 flushed before each",
+           "seeds": n, "status": status, "interp_ms": times["interp"], "method_ms": times["method"],
+           "interp_px_per_s": w * h / (times["interp"] / 1e3), "method_px_per_s": w * h / (times["method"] / 1e3),
+           "params": {"k_geo": ip.k_geo, "k_motion": ip.k_motion, "alpha": ip.alpha, "dist_unit": ip.dist_unit,
+                      "focal": ip.focal, "baseline": ip.baseline}}
+    total = sum(v[1] for v in prof.values())
+    out["kernels"] = {k: {"ms": v[1] / v[0], "share": v[1] / total}
+                      for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    if "k_interp_models" in prof:
+        # algorithmic FP64 work of the weighted normal equations: 20 flops per
+        # plane neighbour, 53 per motion neighbour (centroid 7, centred sums 46)
+        flops = n * (20 * ip.k_geo + 53 * ip.k_motion)
+        t = prof["k_interp_models"][1] / prof["k_interp_models"][0] / 1e3
+        out["roofline"] = {"bound": "fp64", "kernel": "k_interp_models", "achieved": flops / t / 1e9,
+                           "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": flops / t / 1e9 / FP64_PEAK_GFLOPS,
+                           "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak)",
+                           "algo_flops_per_launch": flops, "avg_launch_us": t * 1e6}
+    out["quality"] = field_quality(field.cpu().numpy(), q)
+    if cpu:
+        import oracle
+        oracle.build()
+        cores = os.cpu_count() or 1
+        oracle.set_threads(cores)
+        seeds = sff.seeds_to_numpy(m.seeds.cpu().numpy(), n)
+        op = oracle.interp_params(w, h, q.focal, q.baseline)
+        rng = np.random.default_rng(0)
+        which = rng.choice(n, size=min(n, 1024), replace=False)
+        t0 = time.perf_counter()
+        models = oracle.seed_models(seeds, op, which=which)
+        tm = (time.perf_counter() - t0) * n / len(which)
+        pix = np.stack([rng.integers(0, w, 16384), rng.integers(0, h, 16384)], 1)
+        t0 = time.perf_counter()
+        oracle.interpolate_pixels(seeds, op, pix, models=models)
+        tp = (time.perf_counter() - t0) * w * h / len(pix)
+        out["cpu_baseline"] = {"value": w * h / (tm + tp), "unit": "px/s", "cores": cores, "kind": "oracle",
+                               "sample": f"models of {len(which)} of {n} seeds and 16384 of {w * h} pixels, "
+                                         f"scaled to the whole field ({tm:.1f} s + {tp:.1f} s)"}
+    return out
+
+
 def combine_ranks(t_step: float, px_per_rank: int, world: int, device=None):
     """Whole-job throughput of `world` replicas: every rank matched its own
     quad; the job time is the slowest rank's (max over ranks), the pixels are
@@ -508,6 +620,8 @@ def main():
             "roofline": roof, "gpu_launches": int(round(launches_per_step * args.steps)),
             "e2e": e2e, "clocks": clk, "kernels": kernels, "seeds": n_seeds}
     line["paper_order"] = bench_paper_order(sff, torch, dev, m, q, params)
+    line["interpolation"] = bench_interpolation(sff, torch, dev, m, q, params, min(args.steps, 20),
+                                                max(3, args.warmup), rank == 0 and not args.no_cpu_baseline)
     if batch is not None:
         line["batched"] = bench_batched(sff, torch, dev, batch[0], batch[1], params, tuning, min(args.steps, 20),
                                         max(1, args.warmup))

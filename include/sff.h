@@ -295,8 +295,9 @@ typedef struct sff_interp_params {
 int sff_default_interp_params(int32_t width, int32_t height, double focal, double baseline,
                               sff_interp_params* out);
 
-/* Scratch of sff_interpolate: one int32 per 3x3 block, 144 bytes of models
- * and 4 bytes per seed of `capacity`; 0 for invalid arguments. */
+/* Scratch of sff_interpolate: 4 bytes per 3x3 block, 468 bytes per seed of
+ * `capacity` (points, normal equations, models), 8 bytes per pixel and a
+ * 512 KiB weight table; 0 for invalid arguments. */
 size_t sff_interp_workspace_bytes(int32_t width, int32_t height, int32_t capacity);
 
 /* Interpolates the seeds of sff_emit_seeds (seeds_dev, count_dev: device;
@@ -305,9 +306,10 @@ size_t sff_interp_workspace_bytes(int32_t width, int32_t height, int32_t capacit
  * during the call.  The seeds must lie in the image with at most one seed per
  * 3x3 block anchored at (0, 0), as sff_emit_seeds writes them.
  * Errors found on the GPU (a second seed in one block, a seed outside the
- * image, more than 2048 neighbour candidates of one seed) set bits of a
- * status word in the workspace (read it with sff_interp_status) and the
- * field is all zeros. */
+ * image, more than 6 * max(k_geo, k_motion) + 256 neighbour candidates of
+ * one seed, which needs a very uneven seed density) set bits of a status
+ * word in the workspace (read it with sff_interp_status) and the field is
+ * all zeros. */
 int sff_interpolate(const sff_seed* seeds_dev, const int32_t* count_dev, int32_t capacity, int32_t width,
                     int32_t height, const sff_interp_params* params, float* field_dev, void* workspace,
                     size_t workspace_bytes, void* stream);

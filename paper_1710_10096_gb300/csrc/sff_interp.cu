@@ -50,8 +50,16 @@ namespace {
 
 constexpr int kBlock = 3;            // sparsification block of Sec. 3.2
 constexpr int kModelWarps = 2;       // warps (seeds) per CTA of k_interp_models
-constexpr int kCandidates = 2048;    // candidate slots per warp (16 KB)
 constexpr int kMaxK = 1024;          // largest k_geo / k_motion
+constexpr int kRegKeys = 24;         // candidate keys per lane held in registers during selection
+
+// Candidate slots per seed: the rings up to the bound of the k-th nearest
+// hold about 4/pi times k seeds plus a margin of whole rings; 6 k + 256
+// leaves room for uneven seed density (with k = 160, a lone seed in the
+// middle of a 480 x 480 px hole in a dense seed lattice takes 833).
+__host__ __device__ __forceinline__ int candidate_slots(int kg, int km) {
+    return ((6 * (kg > km ? kg : km) + 256) + 31) & ~31;
+}
 constexpr int kModelDoubles = 18;    // plane 3, [A | t] 12, centre 3
 constexpr int kPointDoubles = 8;     // x0 3, x1 3, d0, pad
 constexpr int kSumDoubles = 32;      // plane sums 9, motion N 10 and R 12, pad
@@ -77,6 +85,7 @@ struct InterpJob {
     unsigned* status;  // error bits
     sff_interp_params p;
     double fb, inv_f;  // focal * baseline, 1 / focal
+    int slots;         // candidate slots per warp of k_interp_models
 };
 
 __device__ __forceinline__ int seed_count(const InterpJob& J) { return min(*J.count, J.capacity); }
@@ -234,28 +243,22 @@ __device__ int tie_threshold(const Candidates& C, bool motion, unsigned D, int n
     return lo;
 }
 
-// Thresholds of the k smallest (d2, index) keys of both neighbourhoods: all
-// candidates (k_geo) and the motion seeds among them (k_motion).  `fa`/`fm`
-// are the sizes of the two sets, `far_a`/`far_m` distances that at least k
-// of their members are within.  The two bisections over d2 share their
-// passes over the candidates.
-__device__ void select_both(const Candidates& C, int kg, int km, int fa, int fm, unsigned far_a, unsigned far_m,
-                            int n, int* scratch, int lane, Threshold& A, Threshold& M) {
-    A = Threshold{0xffffffffu, 0x7fffffff};
-    M = Threshold{0xffffffffu, 0x7fffffff};
-    const bool sa = fa > kg, sm = fm > km;
-    if (!sa && !sm) return;
-    unsigned loA = 0, hiA = sa ? far_a : 0, loM = 0, hiM = sm ? far_m : 0;
+// The k-th smallest d2 of both neighbourhoods, all candidates (k_geo) and
+// the motion seeds among them (k_motion), by bisections that share their
+// passes over the candidates: the smallest D with at least k members
+// within D.  hiA / hiM are distances that at least k members are within
+// (0 skips that set).  each(f) calls f(d2, motion) for every candidate of
+// the lane.
+template <class Each>
+__device__ void bisect_both(Each each, int kg, int km, unsigned hiA, unsigned hiM, unsigned& DA, unsigned& DM) {
+    unsigned loA = 0, loM = 0;
     while (loA < hiA || loM < hiM) {
         const unsigned midA = loA + ((hiA - loA) >> 1), midM = loM + ((hiM - loM) >> 1);
         int ca = 0, cm = 0;
-        for (int j = lane; j < C.m; j += 32) {
-            const int w = C.word[j];
-            int dx, dy;
-            const unsigned d2 = cand_d2(C.pos[j], dx, dy);
+        each([&](unsigned d2, unsigned mot) {
             ca += d2 <= midA;
-            cm += word_motion(w) && d2 <= midM;
-        }
+            cm += mot & (d2 <= midM);
+        });
         ca = warp_sum_i(ca);
         cm = warp_sum_i(cm);
         if (loA < hiA) {
@@ -271,29 +274,71 @@ __device__ void select_both(const Candidates& C, int kg, int km, int fa, int fm,
                 loM = midM + 1;
         }
     }
-    int ba = 0, ea = 0, bm = 0, em = 0;
-    for (int j = lane; j < C.m; j += 32) {
-        const int w = C.word[j];
-        int dx, dy;
-        const unsigned d2 = cand_d2(C.pos[j], dx, dy);
-        ba += d2 < loA;
-        ea += d2 == loA;
-        if (word_motion(w)) {
-            bm += d2 < loM;
-            em += d2 == loM;
+    DA = loA;
+    DM = loM;
+}
+
+// Runs f(each) with each(g) calling g(d2, motion) for the lane's candidates:
+// from keys held in registers when the candidates fit (bit 31 = motion; the
+// filler 0x7fffffff is farther than any bound), else from shared memory.
+template <class F>
+__device__ __forceinline__ void with_keys(const Candidates& C, int lane, F f) {
+    if (C.m <= 32 * kRegKeys) {
+        unsigned key[kRegKeys];
+#pragma unroll
+        for (int t = 0; t < kRegKeys; ++t) {
+            const int j = lane + 32 * t;
+            key[t] = 0x7fffffffu;
+            if (j < C.m) {
+                int dx, dy;
+                key[t] = cand_d2(C.pos[j], dx, dy) | ((unsigned)word_motion(C.word[j]) << 31);
+            }
         }
+        f([&](auto g) {
+#pragma unroll
+            for (int t = 0; t < kRegKeys; ++t) g(key[t] & 0x7fffffffu, key[t] >> 31);
+        });
+    } else {
+        f([&](auto g) {
+            for (int j = lane; j < C.m; j += 32) {
+                int dx, dy;
+                g(cand_d2(C.pos[j], dx, dy), (unsigned)word_motion(C.word[j]));
+            }
+        });
     }
+}
+
+// Thresholds of the k smallest (d2, index) keys of both neighbourhoods.
+// `fa`/`fm` are the sizes of the two sets, `far_a`/`far_m` distances that
+// at least k of their members are within.
+__device__ void select_both(const Candidates& C, int kg, int km, int fa, int fm, unsigned far_a, unsigned far_m,
+                            int n, int* scratch, int lane, Threshold& A, Threshold& M) {
+    A = Threshold{0xffffffffu, 0x7fffffff};
+    M = Threshold{0xffffffffu, 0x7fffffff};
+    const bool sa = fa > kg, sm = fm > km;
+    if (!sa && !sm) return;
+    unsigned DA, DM;
+    int ba = 0, ea = 0, bm = 0, em = 0;
+    with_keys(C, lane, [&](auto each) {
+        bisect_both(each, kg, km, sa ? far_a : 0, sm ? far_m : 0, DA, DM);
+        each([&](unsigned d2, unsigned mot) {
+            ba += d2 < DA;
+            ea += d2 == DA;
+            bm += mot & (d2 < DM);
+            em += mot & (d2 == DM);
+        });
+    });
     ba = warp_sum_i(ba);
     ea = warp_sum_i(ea);
     bm = warp_sum_i(bm);
     em = warp_sum_i(em);
     if (sa) {
-        A.D = loA;
-        if (kg - ba < ea) A.I = tie_threshold(C, false, loA, kg - ba, ea, n, scratch, lane);
+        A.D = DA;
+        if (kg - ba < ea) A.I = tie_threshold(C, false, DA, kg - ba, ea, n, scratch, lane);
     }
     if (sm) {
-        M.D = loM;
-        if (km - bm < em) M.I = tie_threshold(C, true, loM, km - bm, em, n, scratch, lane);
+        M.D = DM;
+        if (km - bm < em) M.I = tie_threshold(C, true, DM, km - bm, em, n, scratch, lane);
     }
 }
 
@@ -347,81 +392,111 @@ __device__ __forceinline__ void solve4(const double (&u)[10], double (&b)[4]) {
     }
 }
 
+// Shared memory of one warp of k_interp_models: candidate positions and map
+// words (J.slots each), the two neighbour lists (k_geo, k_motion slots of
+// 16 bits), 32 ints of scratch.
+__host__ __device__ __forceinline__ size_t warp_smem_bytes(int slots, int kg, int km) {
+    return (size_t)slots * 8 + (((size_t)(kg + km) * 2 + 15) & ~(size_t)15) + 128;
+}
+
 __global__ void __launch_bounds__(kModelWarps * 32) k_interp_models(InterpJob J) {
-    __shared__ uint32_t pos_all[kModelWarps][kCandidates];
-    __shared__ int word_all[kModelWarps][kCandidates];
-    __shared__ uint16_t list_all[kModelWarps][2][kMaxK];  // selected candidate slots
-    __shared__ int scratch_all[kModelWarps][33];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int si = blockIdx.x * kModelWarps + wid;
     const int n = seed_count(J);
     if (si >= n) return;  // warp-uniform
-    int* fill = scratch_all[wid] + 32;
     const int kg = J.p.k_geo, km = J.p.k_motion;
+    unsigned char* mine = smem_raw + (size_t)wid * warp_smem_bytes(J.slots, kg, km);
+    uint32_t* pos = reinterpret_cast<uint32_t*>(mine);
+    int* word = reinterpret_cast<int*>(mine + (size_t)J.slots * 4);
+    uint16_t* la = reinterpret_cast<uint16_t*>(mine + (size_t)J.slots * 8);
+    uint16_t* lm = la + kg;
+    int* scratch = reinterpret_cast<int*>(mine + warp_smem_bytes(J.slots, kg, km) - 128);
     const sff_seed s = J.seeds[si];
     const int bx = s.x / kBlock, by = s.y / kBlock;
     const int rmax = max(J.gbw, J.gbh);
     const unsigned lt = (1u << lane) - 1u;
 
-    // One pass over rings of blocks: rings until both neighbourhoods have
-    // enough members; the largest distance seen up to then bounds the k-th
-    // nearest; then the rings that can still hold a member within that bound.
-    if (lane == 0) *fill = 0;
-    __syncwarp();
-    int fa = 0, fm = 0;
-    unsigned far_a = 0, far_m = 0;
-    for (int q = 0; q <= rmax; ++q) {
-        if (q >= 1 && fa >= kg && fm >= km) {
-            const long long b = 3 * q - 2;
-            if (b * b > (long long)max(far_a, far_m)) break;
-        }
-        int ca = 0, cm = 0;
+    // Candidates by rings of blocks around the seed's block (ring q is at
+    // least 3q - 2 px away).  First the rings until both neighbourhoods have
+    // k members; a set's bound is the largest distance found when it got
+    // them, and from then on a seed is kept only if it is within the bound
+    // of a set it belongs to (so that sparse motion seeds do not drag every
+    // seed in).  Then the k-th smallest distances of the candidates replace
+    // the bounds, and the further rings that can still hold a member within
+    // a bound are scanned.
+    int fill = 0;                                          // candidates kept
+    int fa = 0, fm = 0;                                    // ... of which motion seeds: fm
+    unsigned far_a = 0, far_m = 0;                         // largest distance kept (all / motion)
+    unsigned bound_a = 0xffffffffu, bound_m = 0xffffffffu;  // storage bounds, none yet
+    auto scan = [&](int q) {
         unsigned ma = 0, mm = 0;
-        for (int k = lane; k < ring_cells(q); k += 32) {
-            int ox, oy;
-            ring_cell(q, k, ox, oy);
-            const int cx = bx + ox, cy = by + oy;
-            if (cx < 0 || cy < 0 || cx >= J.gbw || cy >= J.gbh) continue;
-            const int w = J.map[cy * J.gbw + cx];
-            if (w < 0) continue;
-            const int dx = cx * kBlock + ((w >> 2) & 3) - s.x, dy = cy * kBlock + (w & 3) - s.y;
-            const unsigned d2 = (unsigned)(dx * dx + dy * dy);
-            const int slot = atomicAdd(fill, 1);
-            if (slot < kCandidates) {
-                pos_all[wid][slot] = ((uint32_t)(dy & 0xffff) << 16) | (uint32_t)(dx & 0xffff);
-                word_all[wid][slot] = w;
+        for (int base = 0; base < ring_cells(q); base += 32) {
+            const int k = base + lane;
+            int w = -1, dx = 0, dy = 0;
+            unsigned d2 = 0;
+            if (k < ring_cells(q)) {
+                int ox, oy;
+                ring_cell(q, k, ox, oy);
+                const int cx = bx + ox, cy = by + oy;
+                if (cx >= 0 && cy >= 0 && cx < J.gbw && cy < J.gbh) w = J.map[cy * J.gbw + cx];
+                if (w >= 0) {
+                    dx = cx * kBlock + ((w >> 2) & 3) - s.x;
+                    dy = cy * kBlock + (w & 3) - s.y;
+                    d2 = (unsigned)(dx * dx + dy * dy);
+                    if (!(d2 <= bound_a || (word_motion(w) && d2 <= bound_m))) w = -1;
+                }
             }
-            ++ca;
-            ma = max(ma, d2);
-            if (word_motion(w)) {
-                ++cm;
-                mm = max(mm, d2);
+            const unsigned has = __ballot_sync(kFull, w >= 0), mot = __ballot_sync(kFull, w >= 0 && word_motion(w));
+            if (w >= 0) {
+                const int slot = fill + __popc(has & lt);
+                if (slot < J.slots) {
+                    pos[slot] = ((uint32_t)(dy & 0xffff) << 16) | (uint32_t)(dx & 0xffff);
+                    word[slot] = w;
+                }
+                ma = max(ma, d2);
+                if (word_motion(w)) mm = max(mm, d2);
             }
+            fill += __popc(has);
+            fa += __popc(has);
+            fm += __popc(mot);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            ca += __shfl_xor_sync(kFull, ca, o);
-            cm += __shfl_xor_sync(kFull, cm, o);
             ma = max(ma, __shfl_xor_sync(kFull, ma, o));
             mm = max(mm, __shfl_xor_sync(kFull, mm, o));
         }
-        if (fa < kg) far_a = max(far_a, ma);
-        if (fm < km) far_m = max(far_m, mm);
-        fa += ca;
-        fm += cm;
-    }
+        far_a = max(far_a, ma);
+        far_m = max(far_m, mm);
+        if (bound_a == 0xffffffffu && fa >= kg) bound_a = far_a;
+        if (bound_m == 0xffffffffu && fm >= km) bound_m = far_m;
+    };
+    int q = 0;
+    for (; q <= rmax && (fa < kg || fm < km); ++q) scan(q);
     __syncwarp();
-    const Candidates C{pos_all[wid], word_all[wid], *fill};
-    if (C.m > kCandidates) {
+    if (fill > J.slots) {
+        if (lane == 0) atomicOr(J.status, kErrOverflow);
+        return;
+    }
+    if (fa >= kg && fm >= km) {
+        const Candidates C1{pos, word, fill};
+        with_keys(C1, lane, [&](auto each) { bisect_both(each, kg, km, bound_a, bound_m, bound_a, bound_m); });
+        for (; q <= rmax; ++q) {
+            const long long b = 3 * q - 2;
+            if (b * b > (long long)max(bound_a, bound_m)) break;
+            scan(q);
+        }
+        __syncwarp();
+    }
+    const Candidates C{pos, word, fill};
+    if (C.m > J.slots) {
         if (lane == 0) atomicOr(J.status, kErrOverflow);
         return;
     }
     Threshold TA, TM;
-    select_both(C, kg, km, fa, fm, far_a, far_m, n, scratch_all[wid], lane, TA, TM);
+    select_both(C, kg, km, fa, fm, min(bound_a, far_a), min(bound_m, far_m), n, scratch, lane, TA, TM);
 
     // the members of both neighbourhoods, compacted into lists of slots
-    uint16_t* la = list_all[wid][0];
-    uint16_t* lm = list_all[wid][1];
     int na = 0, nm = 0;
     for (int base = 0; base < C.m; base += 32) {
         const int j = base + lane;
@@ -435,13 +510,13 @@ __global__ void __launch_bounds__(kModelWarps * 32) k_interp_models(InterpJob J)
         }
         const unsigned ba = __ballot_sync(kFull, in_a), bm = __ballot_sync(kFull, in_m);
         const int qa = na + __popc(ba & lt), qm = nm + __popc(bm & lt);
-        if (in_a && qa < kMaxK) la[qa] = (uint16_t)j;
-        if (in_m && qm < kMaxK) lm[qm] = (uint16_t)j;
+        if (in_a && qa < kg) la[qa] = (uint16_t)j;
+        if (in_m && qm < km) lm[qm] = (uint16_t)j;
         na += __popc(ba);
         nm += __popc(bm);
     }
     __syncwarp();
-    if (na > kMaxK || nm > kMaxK) {  // unreachable: at most k members are selected
+    if (na > kg || nm > km) {  // unreachable: at most k members are selected
         if (lane == 0) atomicOr(J.status, kErrOverflow);
         return;
     }
@@ -796,12 +871,17 @@ extern "C" int sff_interpolate(const sff_seed* seeds_dev, const int32_t* count_d
     J.p = *params;
     J.fb = params->focal * params->baseline;
     J.inv_f = 1.0 / params->focal;
+    J.slots = candidate_slots(params->k_geo, params->k_motion);
     cudaStream_t st = (cudaStream_t)stream;
     const int clear = max(J.gbw * J.gbh, kWeightTable);
     SFF_LAUNCH(k_interp_clear, dim3((clear + 255) / 256), 256, 0, st, J);
     if (capacity > 0) {
         SFF_LAUNCH(k_interp_prep, dim3((capacity + 255) / 256), 256, 0, st, J);
-        SFF_LAUNCH(k_interp_models, dim3((capacity + kModelWarps - 1) / kModelWarps), kModelWarps * 32, 0, st, J);
+        const size_t smem = kModelWarps * warp_smem_bytes(J.slots, J.p.k_geo, J.p.k_motion);
+        if (smem > 48 * 1024 &&
+            cudaFuncSetAttribute(k_interp_models, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return SFF_ERR_CUDA;
+        SFF_LAUNCH(k_interp_models, dim3((capacity + kModelWarps - 1) / kModelWarps), kModelWarps * 32, smem, st, J);
         SFF_LAUNCH(k_interp_solve, dim3((capacity + 31) / 32), 128, 0, st, J);
     }
     int2* col = reinterpret_cast<int2*>(ws + L.nearest);

@@ -68,6 +68,7 @@ def _scene_seeds(family, w, h, scene_seed, seed, **kw):
     ("movie", 130, 70, 0.3, 1.0, 0.1, dict(k_geo=40, k_motion=24)),   # outliers, large motion
     ("planes", 200, 120, 0.04, 0.0, 0.0, {}),                         # sparse: fewer seeds than k
     ("driving", 200, 120, 0.04, 0.5, 0.0, dict(k_geo=30, k_motion=12, alpha=0.0)),  # sparse, far rings, flat weights
+    ("planes", 200, 120, 1.0, 0.5, 0.0, dict(k_geo=400, k_motion=300)),  # more candidates than registers hold
 ])
 def test_field_equals_oracle(env, family, w, h, keep, noise, outl, over):
     seeds, f, B = _scene_seeds(family, w, h, 3, w + h, keep=keep, noise=noise, outliers=outl)
@@ -138,6 +139,32 @@ def test_full_size_sampled_pixels(env):
     np.testing.assert_allclose(got[pix[:, 1], pix[:, 0]], want, rtol=RTOL, atol=ATOL)
 
 
+def test_lone_seed_in_a_hole(env):
+    # a dense lattice with a 480 x 480 px hole holding one seed: that seed's
+    # neighbourhoods lie on the far side of the hole (833 candidates for
+    # k = 160, more than the registers hold); pixels in and around the hole
+    torch, sff, orc = env
+    w, h = 600, 600
+    ys, xs = np.mgrid[0:200, 0:200]
+    keep = (np.maximum(np.abs(xs - 100), np.abs(ys - 100)) >= 80) | ((xs == 100) & (ys == 100))
+    d = np.zeros(int(keep.sum()), scenegen.SEED_RECORD)
+    d["x"], d["y"] = 3 * xs[keep], 3 * ys[keep]
+    d["d0"] = 20 + d["x"] // 40
+    d["d1"] = d["d0"] + 2 + d["y"] // 100
+    d["u"], d["v"] = 3 + d["y"] // 60, -2
+    got, status = _gpu_interp(env, d, w, h, 400.0, 0.5)
+    assert status == 0
+    rng = np.random.default_rng(3)
+    pix = np.concatenate([np.stack([rng.integers(40, 560, 600), rng.integers(40, 560, 600)], 1),
+                          [[300, 300], [301, 299], [0, 599]]]).astype(np.int32)
+    p = orc.interp_params(w, h, 400.0, 0.5)
+    sd = np.ascontiguousarray(d, orc.SEED_DTYPE)
+    zero = (np.zeros((len(sd), 3)), np.zeros((len(sd), 15)), np.zeros(len(sd), np.int32))
+    _, closest = orc.interpolate_pixels(sd, p, pix, models=zero)
+    want, _ = orc.interpolate_pixels(sd, p, pix, models=orc.seed_models(sd, p, which=closest))
+    np.testing.assert_allclose(got[pix[:, 1], pix[:, 0]], want, rtol=RTOL, atol=ATOL)
+
+
 def test_no_seeds_and_capacity(env):
     w, h = 50, 31
     seeds, f, B = _scene_seeds("planes", w, h, 4, 8, keep=0.5)
@@ -167,10 +194,13 @@ def test_invalid_seed_sets_are_reported(env):
     s["x"], s["y"] = [4, 45, 20], [4, 3, 20]  # x = 45 is outside the image
     got, status = _gpu_interp(env, s, w, h, 300.0, 0.5)
     assert status & 1 and (got == 0).all()
-    # more than 2048 candidates for one neighbourhood: reported, not truncated
-    w, h = 300, 300
-    ys, xs = np.mgrid[0:h:3, 0:w:3]
-    d = np.zeros(xs.size, scenegen.SEED_RECORD)
-    d["x"], d["y"], d["d0"], d["d1"] = xs.ravel(), ys.ravel(), 30, 31
+    # more candidates than the 6 k + 256 slots: a lone seed in the middle of a
+    # 480 x 480 px hole in a dense lattice (8151 candidates for k = 1024):
+    # reported, not truncated
+    w, h = 600, 600
+    ys, xs = np.mgrid[0:200, 0:200]
+    keep = (np.maximum(np.abs(xs - 100), np.abs(ys - 100)) >= 80) | ((xs == 100) & (ys == 100))
+    d = np.zeros(int(keep.sum()), scenegen.SEED_RECORD)
+    d["x"], d["y"], d["d0"], d["d1"] = 3 * xs[keep], 3 * ys[keep], 30, 31
     got, status = _gpu_interp(env, d, w, h, 300.0, 0.5, k_geo=1024, k_motion=4)
     assert status & 2 and (got == 0).all()
