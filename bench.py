@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 32-quad batched and the serving measurements")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-paper-order", action="store_true",
+                    help="skip the comparison with the paper's sequential propagation order")
+    ap.add_argument("--no-interp", action="store_true", help="skip the dense interpolation measurement")
     ap.add_argument("--tuning", default="auto",
                     help="work distribution of the propagation kernels: 'auto' (autotune) or L,TX,TY")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(scenegen.CONFIG_SIZES),
@@ -619,9 +622,11 @@ def main():
                        "tuning": {"lanes_per_pixel": tuning.lanes_per_pixel, "tile": [tuning.tile_x, tuning.tile_y]}},
             "roofline": roof, "gpu_launches": int(round(launches_per_step * args.steps)),
             "e2e": e2e, "clocks": clk, "kernels": kernels, "seeds": n_seeds}
-    line["paper_order"] = bench_paper_order(sff, torch, dev, m, q, params)
-    line["interpolation"] = bench_interpolation(sff, torch, dev, m, q, params, min(args.steps, 20),
-                                                max(3, args.warmup), rank == 0 and not args.no_cpu_baseline)
+    if not args.no_paper_order:
+        line["paper_order"] = bench_paper_order(sff, torch, dev, m, q, params)
+    if not args.no_interp:
+        line["interpolation"] = bench_interpolation(sff, torch, dev, m, q, params, min(args.steps, 20),
+                                                    max(3, args.warmup), rank == 0 and not args.no_cpu_baseline)
     if batch is not None:
         line["batched"] = bench_batched(sff, torch, dev, batch[0], batch[1], params, tuning, min(args.steps, 20),
                                         max(1, args.warmup))

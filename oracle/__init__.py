@@ -18,6 +18,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sff_oracle.c")
 _SRC_INTERP = os.path.join(_HERE, "sff_interp_oracle.c")
+_SRC_SGM = os.path.join(_HERE, "sff_sgm_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -42,16 +43,16 @@ def default_params(**over) -> Params:
 
 
 SEED_DTYPE = np.dtype([("x", "<i2"), ("y", "<i2"), ("u", "<i2"), ("v", "<i2"), ("d0", "<i2"), ("d1", "<i2"),
-                       ("cost", "<i4"), ("cerr", "u1"), ("pad", "u1", (3,))])
+                       ("cost", "<i4"), ("cerr", "u1"), ("kind", "u1"), ("pad", "u1", (2,))])
 assert SEED_DTYPE.itemsize == 20
 
 
 def build(force: bool = False) -> str:
     """Compile the oracle into oracle/liboracle.so (gcc, OpenMP)."""
-    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_INTERP))
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_INTERP), os.path.getmtime(_SRC_SGM))
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11", _SRC, _SRC_INTERP, "-lm",
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11", _SRC, _SRC_INTERP, _SRC_SGM, "-lm",
                                "-o", tmp])
         os.replace(tmp, _LIB)
     return _LIB
@@ -85,6 +86,15 @@ def lib():
         L.sffi_interpolate_pixels.argtypes = [P, i32, ctypes.POINTER(InterpParams), P, P, P, P, i32, P, P]
         L.sffi_nearest.argtypes = [P, i32, i32, i32, i32, i32, P, P, P]
         L.sffi_set_threads.argtypes = [i32]
+        L.sffs_set_threads.argtypes = [i32]
+        L.sffs_grey.argtypes = [P, i32, i32, i32, P]
+        L.sffs_census.argtypes = [P, i32, i32, P]
+        L.sffs_cost_volume.argtypes = [P, P, i32, i32, i32, P]
+        L.sffs_path.argtypes = [P, i32, i32, i32, i32, i32, i32, i32, P]
+        L.sffs_sgm_from_cost.argtypes = [P, i32, i32, i32, i32, i32, P]
+        L.sffs_sgm.argtypes = [P, P, i32, i32, i32, ctypes.POINTER(SgmParams), P]
+        L.sffs_emit_seeds_geo.argtypes = [P, P, P, P, P, i32, i32, i32, P, i32]
+        L.sffs_emit_seeds_geo.restype = i32
         L.sffo_set_threads.argtypes = [i32]
         L.sffo_get_threads.restype = i32
         _lib = L
@@ -99,6 +109,7 @@ def _p(a: np.ndarray):
 def set_threads(n: int) -> None:
     lib().sffo_set_threads(int(n))
     lib().sffi_set_threads(int(n))
+    lib().sffs_set_threads(int(n))
 
 
 def get_threads() -> int:
@@ -306,3 +317,87 @@ def nearest_seeds(seeds, x: int, y: int, k: int, motion_only: bool = False):
     cnt = ctypes.c_int32(0)
     lib().sffi_nearest(_p(seeds), len(seeds), x, y, k, int(motion_only), _p(idx), _p(d2), ctypes.byref(cnt))
     return idx[:cnt.value], d2[:cnt.value]
+
+
+# ---------------------------------------------------------------------------
+# Disparity fill by semi-global matching (Sec. 3.1, last paragraph),
+# sff_sgm_oracle.c
+
+
+class SgmParams(ctypes.Structure):
+    """Disparity range D and the SGM penalties P1, P2."""
+    _fields_ = [("max_disp", ctypes.c_int32), ("p1", ctypes.c_int32), ("p2", ctypes.c_int32)]
+
+
+def sgm_params(**over) -> SgmParams:
+    p = dict(max_disp=128, p1=10, p2=120)
+    p.update(over)
+    return SgmParams(**p)
+
+
+def grey(rgb):
+    rgb = np.ascontiguousarray(rgb, np.uint8)
+    h, w, _ = rgb.shape
+    out = np.empty((h, w), np.uint8)
+    lib().sffs_grey(_p(rgb), 3 * w, w, h, _p(out))
+    return out
+
+
+def census(grey_img):
+    g = np.ascontiguousarray(grey_img, np.uint8)
+    h, w = g.shape
+    out = np.empty((h, w), np.uint64)
+    lib().sffs_census(_p(g), w, h, _p(out))
+    return out
+
+
+def cost_volume(cl, cr, max_disp: int):
+    cl = np.ascontiguousarray(cl, np.uint64)
+    cr = np.ascontiguousarray(cr, np.uint64)
+    h, w = cl.shape
+    out = np.empty((h, w, max_disp), np.uint8)
+    lib().sffs_cost_volume(_p(cl), _p(cr), w, h, max_disp, _p(out))
+    return out
+
+
+def path_costs(C, p1: int, p2: int, rx: int, ry: int):
+    """L_r [H, W, D] uint16 of direction (rx, ry) over the cost volume C [H, W, D] uint8."""
+    C = np.ascontiguousarray(C, np.uint8)
+    h, w, d = C.shape
+    out = np.empty((h, w, d), np.uint16)
+    lib().sffs_path(_p(C), w, h, d, p1, p2, rx, ry, _p(out))
+    return out
+
+
+def sgm_from_cost(C, p1: int, p2: int):
+    C = np.ascontiguousarray(C, np.uint8)
+    h, w, d = C.shape
+    out = np.empty((h, w), np.int16)
+    lib().sffs_sgm_from_cost(_p(C), w, h, d, p1, p2, _p(out))
+    return out
+
+
+def sgm(left, right, params: SgmParams = None):
+    """SGM disparity map int16 [H, W] of L0 (left) against R0 (right)."""
+    params = params or sgm_params()
+    left = np.ascontiguousarray(left, np.uint8)
+    right = np.ascontiguousarray(right, np.uint8)
+    h, w, _ = left.shape
+    out = np.empty((h, w), np.int16)
+    lib().sffs_sgm(_p(left), _p(right), 3 * w, w, h, ctypes.byref(params), _p(out))
+    return out
+
+
+def emit_seeds_geo(fwd, fwd_cost, keep, cerr, sgm_disp, tau_c: int = 1):
+    """Seeds with the disparity fill: the jointly consistent seed of a 3x3
+    block, else its best disparity-only pixel (kind 1)."""
+    h, w, _ = fwd.shape
+    cap = ((w + 2) // 3) * ((h + 2) // 3)
+    out = np.zeros(cap, SEED_DTYPE)
+    f = np.ascontiguousarray(fwd, np.int16)
+    c = np.ascontiguousarray(fwd_cost, np.int32)
+    k = np.ascontiguousarray(keep, np.uint8)
+    e = np.ascontiguousarray(cerr, np.uint8)
+    g = np.ascontiguousarray(sgm_disp, np.int16)
+    n = lib().sffs_emit_seeds_geo(_p(f), _p(c), _p(k), _p(e), _p(g), w, h, tau_c, _p(out), cap)
+    return out[:min(n, cap)]

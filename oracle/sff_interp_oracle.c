@@ -55,7 +55,8 @@ typedef struct {
     int16_t x, y, u, v, d0, d1;
     int32_t cost;
     uint8_t cerr;
-    uint8_t pad[3];
+    uint8_t kind;
+    uint8_t pad[2];
 } sffi_seed;
 
 typedef struct {

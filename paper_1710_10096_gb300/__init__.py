@@ -97,7 +97,7 @@ def profile_collect() -> dict:
 
 # sff_seed of include/sff.h
 SEED_DTYPE = np.dtype([("x", "<i2"), ("y", "<i2"), ("u", "<i2"), ("v", "<i2"), ("d0", "<i2"), ("d1", "<i2"),
-                       ("cost", "<i4"), ("cerr", "u1"), ("pad", "u1", (3,))])
+                       ("cost", "<i4"), ("cerr", "u1"), ("kind", "u1"), ("pad", "u1", (2,))])
 assert SEED_DTYPE.itemsize == 20
 
 

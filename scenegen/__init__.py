@@ -475,7 +475,7 @@ def ground_truth(family: str, width: int, height: int, seed: int):
 
 # 20-byte seed record of the sparse matches (x, y, u, v, d0, d1, cost, cerr)
 SEED_RECORD = np.dtype([("x", "<i2"), ("y", "<i2"), ("u", "<i2"), ("v", "<i2"), ("d0", "<i2"), ("d1", "<i2"),
-                        ("cost", "<i4"), ("cerr", "u1"), ("pad", "u1", (3,))])
+                        ("cost", "<i4"), ("cerr", "u1"), ("kind", "u1"), ("pad", "u1", (2,))])
 
 
 def sparse_seeds(gt: np.ndarray, occluded: np.ndarray, seed: int, keep: float = 0.6, noise: float = 0.0,
