@@ -17,6 +17,8 @@
  *     sff_match_views         initialisation + multi-scale propagation + random search
  *     sff_consistency_filter  forward/inverse consistency check + region filter
  *     sff_emit_seeds          3x3 sparsification into seeds (Sec. 3.2)
+ * the disparity fill (Sec. 3.1, last paragraph):
+ *     sff_sgm, sff_emit_seeds_geo   SGM disparity map, disparity-only seeds
  * and the dense interpolation of the seeds (Sec. 3.3):
  *     sff_interpolate         per-seed plane and affine 3D motion, per-pixel evaluation
  *
@@ -85,12 +87,16 @@ typedef struct sff_tuning {
     int32_t tile_x, tile_y;  /* grid pixels per CTA of the iteration kernel */
 } sff_tuning;
 
-/* One seed of Sec. 3.2: pixel (x, y) of L0, its vector and its scores. 20 bytes. */
+/* One seed of Sec. 3.2: pixel (x, y) of L0, its vector and its scores. 20 bytes.
+ * kind 0: a jointly consistent scene flow match.  kind 1 (only from
+ * sff_emit_seeds_geo): a disparity-only seed of the disparity fill, with
+ * u = v = d1 = 0 and cerr = |d0 - d_sgm|. */
 typedef struct sff_seed {
     int16_t x, y, u, v, d0, d1;
     int32_t cost;   /* matching cost at scale 0 */
     uint8_t cerr;   /* consistency error: sum of |round-trip differences| */
-    uint8_t pad[3];
+    uint8_t kind;   /* 0 scene flow seed, 1 disparity-only seed */
+    uint8_t pad[2];
 } sff_seed;
 
 /* Fills *out with the default parameters.  Returns SFF_ERR_ARG if out is NULL. */
@@ -233,6 +239,50 @@ int sff_emit_seeds(const int16_t* fwd_dev, const int32_t* fwd_cost_dev,
                    const uint8_t* keep_dev, const uint8_t* cerr_dev,
                    int32_t width, int32_t height, sff_seed* seeds_dev, int32_t capacity,
                    int32_t* count_dev, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Disparity fill (Sec. 3.1, last paragraph): the joint filtering removes
+ * more disparities than necessary, so a second disparity map of L0/R0 from
+ * semi-global matching verifies the matching's own d0 where the joint check
+ * failed.  The paper names SGM and the shared threshold tau_c only; this
+ * library's SGM is:
+ *   - grey = (R + 2G + B + 2) >> 2; census over a 9 x 7 window (bit k, in
+ *     row-major window order without the centre, set when the neighbour is
+ *     darker than the centre), coordinates clamped to the image;
+ *   - cost C(p, d) = Hamming distance of the census words of L0 at (x, y)
+ *     and R0 at (max(x - d, 0), y), 0 <= d < max_disp;
+ *   - aggregation along the 4 axes and 4 diagonals:
+ *     L_r(p, d) = C(p, d) + min(L_r(p - r, d), L_r(p - r, d +- 1) + p1,
+ *                               min_k L_r(p - r, k) + p2) - min_k L_r(p - r, k);
+ *   - disparity = argmin_d sum_r L_r(p, d), ties to the lowest d; no
+ *     left-right check. */
+typedef struct sff_sgm_params {
+    int32_t max_disp;  /* disparity range D: 32, 64, 128 or 256 */
+    int32_t p1, p2;    /* penalties, 0 <= p1 <= p2 <= 193 (L_r then fits 8 bits) */
+} sff_sgm_params;
+
+/* Defaults: max_disp 128, p1 10, p2 120.  SFF_ERR_ARG if out is NULL. */
+int sff_default_sgm_params(sff_sgm_params* out);
+
+/* Scratch of sff_sgm: two census words of 8 bytes and 8 * max_disp bytes of
+ * path costs per pixel; 0 for invalid arguments. */
+size_t sff_sgm_workspace_bytes(int32_t width, int32_t height, const sff_sgm_params* params);
+
+/* SGM disparity map of left_dev (L0) against right_dev (R0), H x W x 3 uint8
+ * images with row pitch `pitch_bytes` (>= 3 W), into disp_dev: [H][W] int16
+ * (device, 2-byte aligned). */
+int sff_sgm(const uint8_t* left_dev, const uint8_t* right_dev, int32_t pitch_bytes, int32_t width, int32_t height,
+            const sff_sgm_params* params, int16_t* disp_dev, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Seeds with the disparity fill: as sff_emit_seeds, except that a 3x3 block
+ * without a kept (jointly consistent) match takes, among its pixels that hold
+ * a vector and whose d0 agrees with sgm_dev within params->tau_c, the one
+ * with the lowest |d0 - d_sgm| (then cost, then raster index) as a
+ * disparity-only seed (kind 1).  sgm_dev: [H][W] int16 (sff_sgm).  Workspace
+ * as sff_emit_seeds (sff_workspace_bytes suffices). */
+int sff_emit_seeds_geo(const int16_t* fwd_dev, const int32_t* fwd_cost_dev, const uint8_t* keep_dev,
+                       const uint8_t* cerr_dev, const int16_t* sgm_dev, int32_t width, int32_t height,
+                       const sff_params* params, sff_seed* seeds_dev, int32_t capacity, int32_t* count_dev,
+                       void* workspace, size_t workspace_bytes, void* stream);
 
 /* Allocation-free variant of sff_emit_seeds.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory,

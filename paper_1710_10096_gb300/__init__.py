@@ -20,6 +20,7 @@ import numpy as np
 __all__ = ["Params", "Tuning", "SffError", "default_params", "default_tuning", "make_tuning", "pyramid_bytes",
            "workspace_bytes", "quad_workspace_bytes", "features", "match_views", "match_quad", "match_quad_tuned",
            "consistency_filter", "emit_seeds", "run_batch", "QuadBuffers", "BatchMatcher", "QuadMatcher",
+           "SgmParams", "default_sgm_params", "sgm_workspace_bytes", "sgm", "emit_seeds_geo",
            "InterpParams", "default_interp_params", "interp_workspace_bytes", "interpolate", "interp_status",
            "SEED_DTYPE", "lib", "build"]
 
@@ -74,6 +75,11 @@ class InterpParams(ctypes.Structure):
     _fields_ = [("k_geo", ctypes.c_int32), ("k_motion", ctypes.c_int32), ("alpha", ctypes.c_double),
                 ("dist_unit", ctypes.c_double), ("focal", ctypes.c_double), ("baseline", ctypes.c_double),
                 ("cx", ctypes.c_double), ("cy", ctypes.c_double)]
+
+
+class SgmParams(ctypes.Structure):
+    """sff_sgm_params: disparity range and penalties of the disparity fill."""
+    _fields_ = [("max_disp", ctypes.c_int32), ("p1", ctypes.c_int32), ("p2", ctypes.c_int32)]
 
 
 class KernelTime(ctypes.Structure):
@@ -146,6 +152,15 @@ def lib():
         L.sff_emit_seeds.restype = i32
         L.sff_emit_seeds_noalloc.argtypes = [P, P, P, P, i32, i32, P, i32, P, P]
         L.sff_emit_seeds_noalloc.restype = i32
+        SP = ctypes.POINTER(SgmParams)
+        L.sff_default_sgm_params.argtypes = [SP]
+        L.sff_default_sgm_params.restype = i32
+        L.sff_sgm_workspace_bytes.argtypes = [i32, i32, SP]
+        L.sff_sgm_workspace_bytes.restype = sz
+        L.sff_sgm.argtypes = [P, P, i32, i32, i32, SP, P, P, sz, P]
+        L.sff_sgm.restype = i32
+        L.sff_emit_seeds_geo.argtypes = [P, P, P, P, P, i32, i32, PP, P, i32, P, P, sz, P]
+        L.sff_emit_seeds_geo.restype = i32
         IP = ctypes.POINTER(InterpParams)
         L.sff_default_interp_params.argtypes = [i32, i32, ctypes.c_double, ctypes.c_double, IP]
         L.sff_default_interp_params.restype = i32
@@ -305,6 +320,36 @@ def emit_seeds(fwd, fwd_cost, keep, cerr, seeds, capacity: int, count, workspace
     assert _nbytes(seeds) >= 20 * capacity
     _check(lib().sff_emit_seeds(_ptr(fwd), _ptr(fwd_cost), _ptr(keep), _ptr(cerr), w, h, _ptr(seeds), capacity,
                                 _ptr(count), _ptr(workspace), _nbytes(workspace), _stream(stream)), "sff_emit_seeds")
+
+
+def default_sgm_params(**overrides) -> SgmParams:
+    p = SgmParams()
+    _check(lib().sff_default_sgm_params(ctypes.byref(p)), "sff_default_sgm_params")
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def sgm_workspace_bytes(width: int, height: int, params: SgmParams = None) -> int:
+    return lib().sff_sgm_workspace_bytes(width, height, ctypes.byref(params or default_sgm_params()))
+
+
+def sgm(left, right, disp, workspace, params: SgmParams = None, stream=None) -> None:
+    """left, right: CUDA uint8 [H, W, 3] (L0, R0, same row pitch); disp: CUDA int16 [H, W]."""
+    h, w = left.shape[0], left.shape[1]
+    assert left.stride(0) == right.stride(0)
+    _check(lib().sff_sgm(_ptr(left), _ptr(right), left.stride(0), w, h, ctypes.byref(params or default_sgm_params()),
+                         _ptr(disp), _ptr(workspace), _nbytes(workspace), _stream(stream)), "sff_sgm")
+
+
+def emit_seeds_geo(fwd, fwd_cost, keep, cerr, sgm_disp, seeds, capacity: int, count, workspace,
+                   params: Params = None, stream=None) -> None:
+    """As emit_seeds, with disparity-only seeds (kind 1) where d0 agrees with sgm_disp."""
+    h, w = fwd.shape[0], fwd.shape[1]
+    assert _nbytes(seeds) >= 20 * capacity
+    _check(lib().sff_emit_seeds_geo(_ptr(fwd), _ptr(fwd_cost), _ptr(keep), _ptr(cerr), _ptr(sgm_disp), w, h,
+                                    ctypes.byref(params or default_params()), _ptr(seeds), capacity, _ptr(count),
+                                    _ptr(workspace), _nbytes(workspace), _stream(stream)), "sff_emit_seeds_geo")
 
 
 def default_interp_params(width: int, height: int, focal: float, baseline: float, **overrides) -> InterpParams:

@@ -213,6 +213,8 @@ struct SeedJob {
     sff_seed* out;
     int capacity;
     int* count;
+    const int16_t* sgm;  // disparity map of the fill (nullptr: joint seeds only)
+    int tau_c;           // agreement of d0 with sgm for a disparity-only seed
 };
 constexpr int kMaxQuads = 32;
 int run_filter(const FilterJob* jobs, int n, const sff_params& P, cudaStream_t st);

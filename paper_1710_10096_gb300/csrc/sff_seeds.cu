@@ -1,9 +1,13 @@
 // Sparsification into seeds (Sec. 3.2): per non-overlapping 3x3 block the
 // kept match with the lowest consistency error (then cost, then raster
-// index), compacted in block raster order.
+// index), compacted in block raster order.  With the disparity fill (Sec.
+// 3.1, last paragraph) a block without a kept match takes its pixel whose
+// d0 agrees best with the SGM map (|d0 - sgm| <= tau_c; then cost, then
+// raster index) as a disparity-only seed (kind 1, u = v = d1 = 0).
 //
-// k_block_best:  one thread per block -> raster index of its best pixel or
-//                -1, and the number of seeds of each chunk of 256 blocks.
+// k_block_best:  one thread per block -> raster index i of its best kept
+//                pixel, -(i + 2) for a disparity-only seed, or -1; and the
+//                number of seeds of each chunk of 256 blocks.
 // k_scan_chunks: one CTA: exclusive scan of the chunk counts, total count.
 // k_write_seeds: rank inside the chunk by warp ballots + chunk offset.
 // Scratch (workspace): best[ceil(W/3) * ceil(H/3)] and one int32 per chunk.
@@ -53,9 +57,24 @@ __global__ void __launch_bounds__(kChunk) k_block_best(const __grid_constant__ S
                     bc = c;
                 }
             }
+        if (bi < 0 && Q.sgm) {
+            int ge = 0, gc = 0;
+            for (int y = by; y < min(by + 3, h); ++y)
+                for (int x = bx; x < min(bx + 3, w); ++x) {
+                    const int i = y * w + x;
+                    const int c = Q.fcost[i];
+                    if (c == kEmpty) continue;
+                    const int e = abs(unpack_vec(Q.fwd[i]).d0 - Q.sgm[i]);
+                    if (e <= Q.tau_c && (bi == -1 || e < ge || (e == ge && c < gc))) {
+                        bi = -(i + 2);
+                        ge = e;
+                        gc = c;
+                    }
+                }
+        }
         Q.best[b] = bi;
     }
-    const int n = __syncthreads_count(bi >= 0);
+    const int n = __syncthreads_count(bi != -1);
     if (threadIdx.x == 0) Q.chunk[blockIdx.x] = n;
 }
 
@@ -108,7 +127,7 @@ __global__ void __launch_bounds__(kChunk) k_write_seeds(const __grid_constant__ 
     if ((int)blockIdx.x * kChunk >= nb) return;  // whole CTA beyond this quad's blocks
     const int b = blockIdx.x * kChunk + threadIdx.x;
     const int i = b < nb ? Q.best[b] : -1;
-    const unsigned ballot = __ballot_sync(0xffffffffu, i >= 0);
+    const unsigned ballot = __ballot_sync(0xffffffffu, i != -1);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) warp_base[wid] = __popc(ballot);
     __syncthreads();
@@ -121,20 +140,23 @@ __global__ void __launch_bounds__(kChunk) k_write_seeds(const __grid_constant__ 
         }
     }
     __syncthreads();
-    if (i < 0) return;
+    if (i == -1) return;
     const int pos = Q.chunk[blockIdx.x] + warp_base[wid] + __popc(ballot & ((1u << lane) - 1u));
     if (pos >= Q.capacity) return;
-    const Vec4 a = unpack_vec(Q.fwd[i]);
+    const bool geo = i < -1;
+    const int pi = geo ? -(i + 2) : i;
+    const Vec4 a = unpack_vec(Q.fwd[pi]);
     sff_seed sd;
-    sd.x = (int16_t)(i % w);
-    sd.y = (int16_t)(i / w);
-    sd.u = (int16_t)a.u;
-    sd.v = (int16_t)a.v;
+    sd.x = (int16_t)(pi % w);
+    sd.y = (int16_t)(pi / w);
+    sd.u = geo ? 0 : (int16_t)a.u;
+    sd.v = geo ? 0 : (int16_t)a.v;
     sd.d0 = (int16_t)a.d0;
-    sd.d1 = (int16_t)a.d1;
-    sd.cost = Q.fcost[i];
-    sd.cerr = Q.cerr[i];
-    sd.pad[0] = sd.pad[1] = sd.pad[2] = 0;
+    sd.d1 = geo ? 0 : (int16_t)a.d1;
+    sd.cost = Q.fcost[pi];
+    sd.cerr = geo ? (uint8_t)abs(a.d0 - Q.sgm[pi]) : Q.cerr[pi];
+    sd.kind = geo ? 1 : 0;
+    sd.pad[0] = sd.pad[1] = 0;
     Q.out[pos] = sd;
 }
 
@@ -216,5 +238,24 @@ extern "C" int sff_emit_seeds_noalloc(const int16_t* fwd_dev, const int32_t* fwd
     // (block bests and chunk counts by k_block_best), so nothing is cleared.
     SeedJob job{reinterpret_cast<const uint2*>(fwd_dev), fwd_cost_dev, keep_dev, cerr_dev, width, height, scratch,
                 scratch + kNoAllocMaxBlocks, seeds_dev, capacity, count_dev};
+    return run_seeds(&job, 1, (cudaStream_t)stream);
+}
+
+extern "C" int sff_emit_seeds_geo(const int16_t* fwd_dev, const int32_t* fwd_cost_dev, const uint8_t* keep_dev,
+                                  const uint8_t* cerr_dev, const int16_t* sgm_dev, int32_t width, int32_t height,
+                                  const sff_params* params, sff_seed* seeds_dev, int32_t capacity, int32_t* count_dev,
+                                  void* workspace, size_t workspace_bytes, void* stream) {
+    using namespace sff;
+    if (check_size(width, height) || check_params(params)) return SFF_ERR_ARG;
+    if (!fwd_dev || !fwd_cost_dev || !keep_dev || !cerr_dev || !sgm_dev || !count_dev || !workspace || capacity < 0)
+        return SFF_ERR_ARG;
+    if (capacity > 0 && !seeds_dev) return SFF_ERR_ARG;
+    if (((uintptr_t)fwd_dev & 7) || ((uintptr_t)seeds_dev & 3) || ((uintptr_t)workspace & 255) ||
+        ((uintptr_t)sgm_dev & 1))
+        return SFF_ERR_ARG;
+    if (workspace_bytes < seeds_ws_bytes(width, height)) return SFF_ERR_WORKSPACE;
+    SeedJob job{reinterpret_cast<const uint2*>(fwd_dev), fwd_cost_dev, keep_dev, cerr_dev, width, height, nullptr,
+                nullptr, seeds_dev, capacity, count_dev, sgm_dev, params->tau_c};
+    seeds_carve(workspace, width, height, &job.best, &job.chunk);
     return run_seeds(&job, 1, (cudaStream_t)stream);
 }

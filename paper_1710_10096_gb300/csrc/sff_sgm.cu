@@ -1,0 +1,281 @@
+// Disparity fill (Sec. 3.1, last paragraph): a second disparity map of L0/R0
+// by semi-global matching, which verifies the matching's own d0 where the
+// joint consistency check removed the pixel (the disparity-only seeds are
+// chosen in sff_seeds.cu).
+//
+// SGM as this library reads it (the paper gives no details):
+//   grey = (R + 2G + B + 2) >> 2; census over a 9 x 7 window, bit k (row-major
+//   window order, centre skipped) set when the neighbour is darker than the
+//   centre, coordinates clamped; cost C(p, d) = popcount(census_L(x, y) ^
+//   census_R(max(x - d, 0), y)); 8 directions r (4 axes, 4 diagonals)
+//     L_r(p, d) = C(p, d) + min(L_r(p-r, d), L_r(p-r, d+-1) + P1,
+//                               min_k L_r(p-r, k) + P2) - min_k L_r(p-r, k),
+//   L_r(p, d) = C(p, d) at the first pixel of a path; disparity = argmin_d of
+//   sum_r L_r(p, d), ties to the lowest d.
+//
+// L_r(p, d) lies in [0, 62 + P2], so with P2 <= 193 it is stored exactly in
+// one byte; the costs are recomputed from the census words (two loads and a
+// popcount) instead of being kept as a volume.
+//
+// k_sgm_census: grey and census of both images from a shared-memory tile.
+// k_sgm_paths:  one warp per path line of one direction (blockIdx.z), the
+//               lanes holding D / 32 consecutive disparities each; one step
+//               per pixel: the neighbours' d +- 1 values by shuffles, the
+//               minimum over d by a warp reduction; L_r to [dir][y][x][d].
+// k_sgm_wta:    one warp per pixel: the 8 directions summed per disparity,
+//               the (sum, d) minimum by a warp reduction.
+#include "sff_internal.cuh"
+
+namespace sff {
+namespace {
+
+constexpr int kDirs = 8;
+constexpr int kPathWarps = 4;  // warps (lines) per CTA of k_sgm_paths
+constexpr int kWtaWarps = 8;   // warps (pixels) per CTA of k_sgm_wta
+constexpr int kCensusW = 9, kCensusH = 7;
+constexpr int kTileX = 32, kTileY = 8;
+constexpr int kInf = 1 << 20;
+constexpr unsigned kFull = 0xffffffffu;
+
+struct SgmJob {
+    const uint8_t* img[2];  // L0, R0
+    int pitch, w, h, D, p1, p2;
+    uint64_t* census[2];    // [y][x]
+    uint8_t* paths;         // [dir][y][x][D]
+    int16_t* disp;          // [y][x]
+};
+
+__constant__ int c_dir[kDirs][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}, {1, 1}, {-1, -1}, {1, -1}, {-1, 1}};
+
+__global__ void __launch_bounds__(kTileX * kTileY) k_sgm_census(SgmJob S) {
+    constexpr int TW = kTileX + kCensusW - 1, TH = kTileY + kCensusH - 1;
+    __shared__ uint8_t tile[TH][TW];
+    const uint8_t* img = blockIdx.z ? S.img[1] : S.img[0];  // no dynamic index into the parameter
+    const int x0 = blockIdx.x * kTileX - kCensusW / 2, y0 = blockIdx.y * kTileY - kCensusH / 2;
+    for (int k = threadIdx.y * kTileX + threadIdx.x; k < TW * TH; k += kTileX * kTileY) {
+        const int tx = k % TW, ty = k / TW;
+        const int gx = clampi(x0 + tx, 0, S.w - 1), gy = clampi(y0 + ty, 0, S.h - 1);
+        const uint8_t* p = img + (size_t)gy * S.pitch + 3 * gx;
+        tile[ty][tx] = (uint8_t)((p[0] + 2 * p[1] + p[2] + 2) >> 2);
+    }
+    __syncthreads();
+    const int x = blockIdx.x * kTileX + threadIdx.x, y = blockIdx.y * kTileY + threadIdx.y;
+    if (x >= S.w || y >= S.h) return;
+    const int c = tile[threadIdx.y + kCensusH / 2][threadIdx.x + kCensusW / 2];
+    uint64_t bits = 0;
+    int k = 0;
+#pragma unroll
+    for (int j = 0; j < kCensusH; ++j)
+#pragma unroll
+        for (int i = 0; i < kCensusW; ++i) {
+            if (i == kCensusW / 2 && j == kCensusH / 2) continue;
+            bits |= (uint64_t)(tile[threadIdx.y + j][threadIdx.x + i] < c) << k;
+            ++k;
+        }
+    (blockIdx.z ? S.census[1] : S.census[0])[(size_t)y * S.w + x] = bits;
+}
+
+template <int J>
+__device__ __forceinline__ void store_bytes(uint8_t* p, const int (&v)[J]) {
+    if constexpr (J == 1) {
+        *p = (uint8_t)v[0];
+    } else if constexpr (J == 2) {
+        *reinterpret_cast<uint16_t*>(p) = (uint16_t)(v[0] | (v[1] << 8));
+    } else if constexpr (J == 4) {
+        *reinterpret_cast<uint32_t*>(p) = (uint32_t)v[0] | ((uint32_t)v[1] << 8) | ((uint32_t)v[2] << 16) |
+                                          ((uint32_t)v[3] << 24);
+    } else {
+        static_assert(J == 8, "D = 32, 64, 128 or 256");
+        uint2 w;
+        w.x = (uint32_t)v[0] | ((uint32_t)v[1] << 8) | ((uint32_t)v[2] << 16) | ((uint32_t)v[3] << 24);
+        w.y = (uint32_t)v[4] | ((uint32_t)v[5] << 8) | ((uint32_t)v[6] << 16) | ((uint32_t)v[7] << 24);
+        *reinterpret_cast<uint2*>(p) = w;
+    }
+}
+
+template <int J>
+__global__ void __launch_bounds__(kPathWarps * 32) k_sgm_paths(SgmJob S) {
+    const int dir = blockIdx.z;
+    const int rx = c_dir[dir][0], ry = c_dir[dir][1];
+    const int lane = threadIdx.x & 31;
+    const int line = blockIdx.x * kPathWarps + (threadIdx.x >> 5);
+    const int W = S.w, H = S.h, D = S.D;
+    // the line's first pixel: the pixels whose predecessor is outside the image
+    int x, y, nlines;
+    if (ry == 0) {
+        nlines = H;
+        y = line;
+        x = rx > 0 ? 0 : W - 1;
+    } else if (rx == 0) {
+        nlines = W;
+        x = line;
+        y = ry > 0 ? 0 : H - 1;
+    } else {
+        nlines = W + H - 1;
+        if (line < W) {
+            x = line;
+            y = ry > 0 ? 0 : H - 1;
+        } else {
+            x = rx > 0 ? 0 : W - 1;
+            y = ry > 0 ? 1 + (line - W) : H - 2 - (line - W);
+        }
+    }
+    if (line >= nlines) return;  // warp-uniform
+    const uint64_t* cl = S.census[0];
+    const uint64_t* cr = S.census[1];
+    uint8_t* out = S.paths + (size_t)dir * W * H * D;
+    int prev[J];
+    int m = 0;
+    bool first = true;
+    for (; x >= 0 && y >= 0 && x < W && y < H; x += rx, y += ry) {
+        const size_t p = (size_t)y * W + x;
+        const uint64_t c = cl[p];
+        int cur[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) cur[j] = __popcll(c ^ cr[(size_t)y * W + max(x - (lane * J + j), 0)]);
+        if (!first) {
+            const int lo = __shfl_up_sync(kFull, prev[J - 1], 1);  // d = lane J - 1
+            const int hi = __shfl_down_sync(kFull, prev[0], 1);    // d = lane J + J
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                const int pl = j > 0 ? prev[j - 1] : (lane > 0 ? lo : kInf);
+                const int pr = j < J - 1 ? prev[j + 1] : (lane < 31 ? hi : kInf);
+                const int b = min(min(prev[j], min(pl, pr) + S.p1), m + S.p2);
+                cur[j] += b - m;
+            }
+        }
+        store_bytes<J>(out + p * D + lane * J, cur);
+        int mm = cur[0];
+#pragma unroll
+        for (int j = 1; j < J; ++j) mm = min(mm, cur[j]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mm = min(mm, __shfl_xor_sync(kFull, mm, o));
+        m = mm;
+#pragma unroll
+        for (int j = 0; j < J; ++j) prev[j] = cur[j];
+        first = false;
+    }
+}
+
+template <int J>
+__global__ void __launch_bounds__(kWtaWarps * 32) k_sgm_wta(SgmJob S) {
+    const int lane = threadIdx.x & 31;
+    const size_t p = (size_t)blockIdx.x * kWtaWarps + (threadIdx.x >> 5);
+    const size_t np = (size_t)S.w * S.h;
+    if (p >= np) return;  // warp-uniform
+    int sum[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) sum[j] = 0;
+#pragma unroll
+    for (int r = 0; r < kDirs; ++r) {
+        const uint8_t* q = S.paths + ((size_t)r * np + p) * S.D + lane * J;
+        uint8_t v[J];
+        if constexpr (J == 1) {
+            v[0] = q[0];
+        } else if constexpr (J == 2) {
+            const uint16_t t = *reinterpret_cast<const uint16_t*>(q);
+            v[0] = t & 0xff;
+            v[1] = t >> 8;
+        } else if constexpr (J == 4) {
+            const uint32_t t = *reinterpret_cast<const uint32_t*>(q);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) v[j] = (t >> (8 * j)) & 0xff;
+        } else {
+            const uint2 t = *reinterpret_cast<const uint2*>(q);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                v[j] = (t.x >> (8 * j)) & 0xff;
+                v[4 + j] = (t.y >> (8 * j)) & 0xff;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < J; ++j) sum[j] += v[j];
+    }
+    // key = sum << 8 | d: the smallest key is the lowest sum, then the lowest d
+    unsigned key = 0xffffffffu;
+#pragma unroll
+    for (int j = 0; j < J; ++j) key = min(key, ((unsigned)sum[j] << 8) | (unsigned)(lane * J + j));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) key = min(key, __shfl_xor_sync(kFull, key, o));
+    if (lane == 0) S.disp[p] = (int16_t)(key & 0xff);
+}
+
+int check_sgm(const sff_sgm_params* P) {
+    if (!P) return SFF_ERR_ARG;
+    if (P->max_disp != 32 && P->max_disp != 64 && P->max_disp != 128 && P->max_disp != 256) return SFF_ERR_ARG;
+    if (P->p1 < 0 || P->p2 < P->p1 || P->p2 > 193) return SFF_ERR_ARG;
+    return SFF_OK;
+}
+
+struct SgmLayout {
+    size_t census0, census1, paths, total;
+};
+
+SgmLayout sgm_layout(int w, int h, int D) {
+    const size_t np = (size_t)w * h;
+    SgmLayout L;
+    L.census0 = 0;
+    L.census1 = align256(np * 8);
+    L.paths = L.census1 + align256(np * 8);
+    L.total = L.paths + align256(np * kDirs * D);
+    return L;
+}
+
+template <int J>
+void launch_sgm(const SgmJob& S, cudaStream_t st) {
+    const int lines = max(S.w, S.h) + min(S.w, S.h) - 1;  // the diagonals have the most lines
+    SFF_LAUNCH(k_sgm_paths<J>, dim3((lines + kPathWarps - 1) / kPathWarps, 1, kDirs), kPathWarps * 32, 0, st, S);
+    const size_t np = (size_t)S.w * S.h;
+    SFF_LAUNCH(k_sgm_wta<J>, dim3((unsigned)((np + kWtaWarps - 1) / kWtaWarps)), kWtaWarps * 32, 0, st, S);
+}
+
+}  // namespace
+}  // namespace sff
+
+extern "C" int sff_default_sgm_params(sff_sgm_params* out) {
+    if (!out) return SFF_ERR_ARG;
+    out->max_disp = 128;
+    out->p1 = 10;
+    out->p2 = 120;
+    return SFF_OK;
+}
+
+extern "C" size_t sff_sgm_workspace_bytes(int32_t width, int32_t height, const sff_sgm_params* params) {
+    if (sff::check_size(width, height) || sff::check_sgm(params)) return 0;
+    return sff::sgm_layout(width, height, params->max_disp).total;
+}
+
+extern "C" int sff_sgm(const uint8_t* left_dev, const uint8_t* right_dev, int32_t pitch_bytes, int32_t width,
+                       int32_t height, const sff_sgm_params* params, int16_t* disp_dev, void* workspace,
+                       size_t workspace_bytes, void* stream) {
+    using namespace sff;
+    if (check_size(width, height) || check_sgm(params)) return SFF_ERR_ARG;
+    if (!left_dev || !right_dev || !disp_dev || !workspace || pitch_bytes < 3 * width) return SFF_ERR_ARG;
+    if (((uintptr_t)disp_dev & 1) || ((uintptr_t)workspace & 255)) return SFF_ERR_ARG;
+    const SgmLayout L = sgm_layout(width, height, params->max_disp);
+    if (workspace_bytes < L.total) return SFF_ERR_WORKSPACE;
+    char* ws = reinterpret_cast<char*>(workspace);
+    SgmJob S;
+    S.img[0] = left_dev;
+    S.img[1] = right_dev;
+    S.pitch = pitch_bytes;
+    S.w = width;
+    S.h = height;
+    S.D = params->max_disp;
+    S.p1 = params->p1;
+    S.p2 = params->p2;
+    S.census[0] = reinterpret_cast<uint64_t*>(ws + L.census0);
+    S.census[1] = reinterpret_cast<uint64_t*>(ws + L.census1);
+    S.paths = reinterpret_cast<uint8_t*>(ws + L.paths);
+    S.disp = disp_dev;
+    cudaStream_t st = (cudaStream_t)stream;
+    SFF_LAUNCH(k_sgm_census, dim3((width + kTileX - 1) / kTileX, (height + kTileY - 1) / kTileY, 2),
+               dim3(kTileX, kTileY), 0, st, S);
+    switch (S.D) {
+        case 32: launch_sgm<1>(S, st); break;
+        case 64: launch_sgm<2>(S, st); break;
+        case 128: launch_sgm<4>(S, st); break;
+        default: launch_sgm<8>(S, st); break;
+    }
+    return launch_status();
+}
