@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-paper-order", action="store_true",
                     help="skip the comparison with the paper's sequential propagation order")
     ap.add_argument("--no-interp", action="store_true", help="skip the dense interpolation measurement")
+    ap.add_argument("--no-fill", action="store_true", help="skip the disparity fill (SGM) measurement")
     ap.add_argument("--tuning", default="auto",
                     help="work distribution of the propagation kernels: 'auto' (autotune) or L,TX,TY")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(scenegen.CONFIG_SIZES),
@@ -439,6 +440,117 @@ def bench_interpolation(sff, torch, dev, m, q, params, steps, warmup, cpu: bool)
     return out
 
 
+def bench_fill(sff, torch, dev, m, q, params, steps, warmup, cpu: bool):
+    """Disparity fill (Sec. 3.1, last paragraph) on the quad: the SGM map of
+    L0/R0 (sff_sgm, D = 128) and the seeds with disparity-only entries
+    (sff_emit_seeds_geo), timed with CUDA events after an L2 flush; the
+    per-kernel profile and the HBM roofline of the dominant kernel; the
+    density and accuracy the fill adds, and what it does to the dense field;
+    the oracle's SGM on the host cores."""
+    w, h = q.width, q.height
+    sp = sff.default_sgm_params()
+    D = sp.max_disp
+    stream = torch.cuda.Stream(device=dev)
+    dev_in = [torch.as_tensor(im).to(dev) for im in q.images()]
+    disp = torch.empty((h, w), dtype=torch.int16, device=dev)
+    sws = torch.empty(sff.sgm_workspace_bytes(w, h, sp), dtype=torch.uint8, device=dev)
+    cap = m.capacity
+    gseeds = torch.zeros(20 * cap, dtype=torch.uint8, device=dev)
+    gcount = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws = torch.empty(sff.workspace_bytes(w, h, params), dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def fill(s):
+        sff.sgm(dev_in[0], dev_in[1], disp, sws, sp, stream=s)
+        sff.emit_seeds_geo(m.fwd, m.fwd_cost, m.keep, m.cerr, disp, gseeds, cap, gcount, ws, params, stream=s)
+
+    with torch.cuda.stream(stream):
+        m.run(*dev_in, seed=MATCH_SEED, stream=stream)
+        for _ in range(max(1, warmup)):
+            fill(stream)
+        stream.synchronize()
+        sff.profile_enable(True)
+        for _ in range(3):
+            flush.zero_()
+            fill(stream)
+        stream.synchronize()
+        prof = sff.profile_collect()
+        sff.profile_enable(False)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=stream):
+            fill(torch.cuda.current_stream())
+        for _ in range(max(1, warmup)):
+            g.replay()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            g.replay()
+            b.record(stream)
+        stream.synchronize()
+    t_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    out = {"what": "SGM map of L0/R0 (D = 128, P1 10, P2 120) and the seeds with the disparity fill, one CUDA graph, "
+                   "ms per quad, L2 flushed before each", "ms": t_ms, "px_per_s": w * h / (t_ms / 1e3)}
+    prof = {k.split("<")[0]: v for k, v in prof.items()}
+    total = sum(v[1] for v in prof.values())
+    out["kernels"] = {k: {"ms": v[1] / v[0], "share": v[1] / total}
+                      for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    # algorithmic bytes per pixel: k_sgm_paths reads the D cost bytes and
+    # writes D bytes of path costs in each of the 8 directions; k_sgm_wta
+    # reads the 8 D bytes and writes the 2-byte disparity; k_sgm_cost reads
+    # the census words and writes D bytes
+    algo = {"k_sgm_paths": 16 * D, "k_sgm_wta": 8 * D + 2, "k_sgm_cost": D + 16}
+    dom = max((k for k in prof if k in algo), key=lambda k: prof[k][1], default=None)
+    if dom:
+        peak, peak_src = measured_peak_hbm()
+        t = prof[dom][1] / prof[dom][0] / 1e3
+        achieved = algo[dom] * w * h / t / 1e9
+        out["roofline"] = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                           "frac": achieved / peak, "peak_source": peak_src,
+                           "algo_bytes_per_launch": algo[dom] * w * h, "avg_launch_us": t * 1e6}
+    # what the fill adds, against the scene's ground truth (visible pixels)
+    vis = ~q.occluded
+    d_sgm = disp.cpu().numpy().astype(np.float64)
+    fwd = m.fwd.cpu().numpy()
+    keep = m.keep.cpu().numpy().astype(bool)
+    valid = m.fwd_cost.cpu().numpy() != sff.EMPTY_COST
+    gt0 = q.gt[..., 2]
+
+    def d1(est, mask):
+        e = np.abs(est[mask] - gt0[mask])
+        return float(((e > 3) & (e > 0.05 * np.abs(gt0[mask]))).mean()) if mask.any() else None
+
+    agree = valid & ~keep & (np.abs(fwd[..., 2] - d_sgm) <= params.tau_c)
+    n_all = min(int(gcount.item()), cap)
+    gs = sff.seeds_to_numpy(gseeds.cpu().numpy(), n_all)
+    out["quality"] = {"sgm_D1": d1(d_sgm, vis), "joint_density": float((keep & vis).sum() / vis.sum()),
+                      "joint_D1": d1(fwd[..., 2].astype(np.float64), keep & vis),
+                      "fill_density": float(((keep | agree) & vis).sum() / vis.sum()),
+                      "fill_only_D1": d1(fwd[..., 2].astype(np.float64), agree & vis),
+                      "seeds_joint": int((gs["kind"] == 0).sum()), "seeds_disparity_only": int((gs["kind"] == 1).sum())}
+    # the dense field from the seeds with the fill (geometry from every seed,
+    # motion from the joint seeds)
+    ip = sff.default_interp_params(w, h, q.focal, q.baseline)
+    field = torch.empty((h, w, 4), dtype=torch.float32, device=dev)
+    iws = torch.empty(sff.interp_workspace_bytes(w, h, cap), dtype=torch.uint8, device=dev)
+    sff.interpolate(gseeds, gcount, cap, w, h, ip, field, iws)
+    torch.cuda.synchronize()
+    out["quality"]["field_with_fill"] = field_quality(field.cpu().numpy(), q)
+    if cpu:
+        import oracle
+        oracle.build()
+        cores = os.cpu_count() or 1
+        oracle.set_threads(cores)
+        t0 = time.perf_counter()
+        od = oracle.sgm(q.L0, q.R0, oracle.sgm_params(max_disp=D))
+        tc = time.perf_counter() - t0
+        out["bit_exact_sgm"] = bool(np.array_equal(od, disp.cpu().numpy()))
+        out["cpu_baseline"] = {"value": w * h / tc, "unit": "px/s", "cores": cores, "kind": "oracle",
+                               "sample": f"the whole {w}x{h} SGM map once ({tc:.2f} s), {cores} OpenMP threads "
+                                         "(one per direction)"}
+    return out
+
+
 def combine_ranks(t_step: float, px_per_rank: int, world: int, device=None):
     """Whole-job throughput of `world` replicas: every rank matched its own
     quad; the job time is the slowest rank's (max over ranks), the pixels are
@@ -627,6 +739,9 @@ def main():
     if not args.no_interp:
         line["interpolation"] = bench_interpolation(sff, torch, dev, m, q, params, min(args.steps, 20),
                                                     max(3, args.warmup), rank == 0 and not args.no_cpu_baseline)
+    if not args.no_fill:
+        line["disparity_fill"] = bench_fill(sff, torch, dev, m, q, params, min(args.steps, 20), max(3, args.warmup),
+                                            rank == 0 and not args.no_cpu_baseline)
     if batch is not None:
         line["batched"] = bench_batched(sff, torch, dev, batch[0], batch[1], params, tuning, min(args.steps, 20),
                                         max(1, args.warmup))

@@ -263,8 +263,9 @@ typedef struct sff_sgm_params {
 /* Defaults: max_disp 128, p1 10, p2 120.  SFF_ERR_ARG if out is NULL. */
 int sff_default_sgm_params(sff_sgm_params* out);
 
-/* Scratch of sff_sgm: two census words of 8 bytes and 8 * max_disp bytes of
- * path costs per pixel; 0 for invalid arguments. */
+/* Scratch of sff_sgm: two census words of 8 bytes, max_disp bytes of
+ * matching costs and 8 * max_disp bytes of path costs per pixel; 0 for
+ * invalid arguments. */
 size_t sff_sgm_workspace_bytes(int32_t width, int32_t height, const sff_sgm_params* params);
 
 /* SGM disparity map of left_dev (L0) against right_dev (R0), H x W x 3 uint8

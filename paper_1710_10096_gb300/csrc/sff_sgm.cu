@@ -14,14 +14,17 @@
 //   sum_r L_r(p, d), ties to the lowest d.
 //
 // L_r(p, d) lies in [0, 62 + P2], so with P2 <= 193 it is stored exactly in
-// one byte; the costs are recomputed from the census words (two loads and a
-// popcount) instead of being kept as a volume.
+// one byte.
 //
 // k_sgm_census: grey and census of both images from a shared-memory tile.
+// k_sgm_cost:   the cost volume, one byte per pixel and disparity (a path
+//               step then reads D bytes instead of D census words).
 // k_sgm_paths:  one warp per path line of one direction (blockIdx.z), the
 //               lanes holding D / 32 consecutive disparities each; one step
-//               per pixel: the neighbours' d +- 1 values by shuffles, the
-//               minimum over d by a warp reduction; L_r to [dir][y][x][d].
+//               per pixel, with the costs of the next 8 pixels of the line
+//               already loaded (a step waits on one reduction, not on L2):
+//               the neighbours' d +- 1 values by shuffles, the minimum over
+//               d by one redux; L_r to [dir][y][x][d].
 // k_sgm_wta:    one warp per pixel: the 8 directions summed per disparity,
 //               the (sum, d) minimum by a warp reduction.
 #include "sff_internal.cuh"
@@ -31,6 +34,7 @@ namespace {
 
 constexpr int kDirs = 8;
 constexpr int kPathWarps = 4;  // warps (lines) per CTA of k_sgm_paths
+constexpr int kQueue = 8;      // pixels whose costs a path warp loads ahead
 constexpr int kWtaWarps = 8;   // warps (pixels) per CTA of k_sgm_wta
 constexpr int kCensusW = 9, kCensusH = 7;
 constexpr int kTileX = 32, kTileY = 8;
@@ -41,6 +45,7 @@ struct SgmJob {
     const uint8_t* img[2];  // L0, R0
     int pitch, w, h, D, p1, p2;
     uint64_t* census[2];    // [y][x]
+    uint8_t* cost;          // [y][x][D] matching costs
     uint8_t* paths;         // [dir][y][x][D]
     int16_t* disp;          // [y][x]
 };
@@ -93,6 +98,75 @@ __device__ __forceinline__ void store_bytes(uint8_t* p, const int (&v)[J]) {
     }
 }
 
+// J bytes as one machine word (kept packed while loads are in flight).
+template <int J>
+struct RawOf;
+template <>
+struct RawOf<1> { using T = uint8_t; };
+template <>
+struct RawOf<2> { using T = uint16_t; };
+template <>
+struct RawOf<4> { using T = uint32_t; };
+template <>
+struct RawOf<8> { using T = uint2; };
+
+template <int J>
+__device__ __forceinline__ typename RawOf<J>::T load_raw(const uint8_t* q) {
+    return *reinterpret_cast<const typename RawOf<J>::T*>(q);
+}
+
+template <int J>
+__device__ __forceinline__ void unpack(typename RawOf<J>::T t, int (&v)[J]) {
+    if constexpr (J == 8) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            v[j] = (t.x >> (8 * j)) & 0xff;
+            v[4 + j] = (t.y >> (8 * j)) & 0xff;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < J; ++j) v[j] = ((uint32_t)t >> (8 * j)) & 0xff;
+    }
+}
+
+template <int J>
+__device__ __forceinline__ void load_bytes(const uint8_t* q, int (&v)[J]) {
+    if constexpr (J == 1) {
+        v[0] = q[0];
+    } else if constexpr (J == 2) {
+        const uint16_t t = *reinterpret_cast<const uint16_t*>(q);
+        v[0] = t & 0xff;
+        v[1] = t >> 8;
+    } else if constexpr (J == 4) {
+        const uint32_t t = *reinterpret_cast<const uint32_t*>(q);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) v[j] = (t >> (8 * j)) & 0xff;
+    } else {
+        const uint2 t = *reinterpret_cast<const uint2*>(q);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            v[j] = (t.x >> (8 * j)) & 0xff;
+            v[4 + j] = (t.y >> (8 * j)) & 0xff;
+        }
+    }
+}
+
+// C(p, d) for every pixel: one warp per pixel, J disparities per lane, the
+// J costs of a lane packed into J bytes of [y][x][d].
+template <int J>
+__global__ void __launch_bounds__(kWtaWarps * 32) k_sgm_cost(SgmJob S) {
+    const int lane = threadIdx.x & 31;
+    const size_t p = (size_t)blockIdx.x * kWtaWarps + (threadIdx.x >> 5);
+    if (p >= (size_t)S.w * S.h) return;  // warp-uniform
+    const int x = (int)(p % S.w);
+    const uint64_t c = S.census[0][p];
+    const uint64_t* row = S.census[1] + (p - x);
+    int v[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) v[j] = __popcll(c ^ row[max(x - (lane * J + j), 0)]);
+    store_bytes<J>(S.cost + p * S.D + lane * J, v);
+}
+
 template <int J>
 __global__ void __launch_bounds__(kPathWarps * 32) k_sgm_paths(SgmJob S) {
     const int dir = blockIdx.z;
@@ -121,39 +195,47 @@ __global__ void __launch_bounds__(kPathWarps * 32) k_sgm_paths(SgmJob S) {
         }
     }
     if (line >= nlines) return;  // warp-uniform
-    const uint64_t* cl = S.census[0];
-    const uint64_t* cr = S.census[1];
-    uint8_t* out = S.paths + (size_t)dir * W * H * D;
+    const uint8_t* cost = S.cost + lane * J;
+    uint8_t* out = S.paths + (size_t)dir * W * H * D + lane * J;
+    // steps until the line leaves the image
+    const int n = min(rx > 0 ? W - x : rx < 0 ? x + 1 : 1 << 30, ry > 0 ? H - y : ry < 0 ? y + 1 : 1 << 30);
+    const ptrdiff_t step = (ptrdiff_t)ry * W + rx;  // pixel index increment along the line
+    const size_t p0 = (size_t)y * W + x;
+    // the costs of the next kQueue pixels, loaded ahead and unpacked on use
+    typename RawOf<J>::T q[kQueue];
+#pragma unroll
+    for (int k = 0; k < kQueue; ++k)
+        if (k < n) q[k] = load_raw<J>(cost + (p0 + k * step) * D);
     int prev[J];
     int m = 0;
-    bool first = true;
-    for (; x >= 0 && y >= 0 && x < W && y < H; x += rx, y += ry) {
-        const size_t p = (size_t)y * W + x;
-        const uint64_t c = cl[p];
-        int cur[J];
+    for (int t = 0; t < n; t += kQueue) {
 #pragma unroll
-        for (int j = 0; j < J; ++j) cur[j] = __popcll(c ^ cr[(size_t)y * W + max(x - (lane * J + j), 0)]);
-        if (!first) {
-            const int lo = __shfl_up_sync(kFull, prev[J - 1], 1);  // d = lane J - 1
-            const int hi = __shfl_down_sync(kFull, prev[0], 1);    // d = lane J + J
+        for (int k = 0; k < kQueue; ++k) {
+            if (t + k < n) {  // uniform over the warp
+                const size_t p = p0 + (ptrdiff_t)(t + k) * step;
+                int cur[J];
+                unpack<J>(q[k], cur);
+                if (t + k + kQueue < n) q[k] = load_raw<J>(cost + (p + kQueue * step) * D);
+                if (t + k > 0) {
+                    const int lo = __shfl_up_sync(kFull, prev[J - 1], 1);  // d = lane J - 1
+                    const int hi = __shfl_down_sync(kFull, prev[0], 1);    // d = lane J + J
 #pragma unroll
-            for (int j = 0; j < J; ++j) {
-                const int pl = j > 0 ? prev[j - 1] : (lane > 0 ? lo : kInf);
-                const int pr = j < J - 1 ? prev[j + 1] : (lane < 31 ? hi : kInf);
-                const int b = min(min(prev[j], min(pl, pr) + S.p1), m + S.p2);
-                cur[j] += b - m;
+                    for (int j = 0; j < J; ++j) {
+                        const int pl = j > 0 ? prev[j - 1] : (lane > 0 ? lo : kInf);
+                        const int pr = j < J - 1 ? prev[j + 1] : (lane < 31 ? hi : kInf);
+                        const int b = min(min(prev[j], min(pl, pr) + S.p1), m + S.p2);
+                        cur[j] += b - m;
+                    }
+                }
+                store_bytes<J>(out + p * D, cur);
+                int mm = cur[0];
+#pragma unroll
+                for (int j = 1; j < J; ++j) mm = min(mm, cur[j]);
+                m = __reduce_min_sync(kFull, mm);
+#pragma unroll
+                for (int j = 0; j < J; ++j) prev[j] = cur[j];
             }
         }
-        store_bytes<J>(out + p * D + lane * J, cur);
-        int mm = cur[0];
-#pragma unroll
-        for (int j = 1; j < J; ++j) mm = min(mm, cur[j]);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mm = min(mm, __shfl_xor_sync(kFull, mm, o));
-        m = mm;
-#pragma unroll
-        for (int j = 0; j < J; ++j) prev[j] = cur[j];
-        first = false;
     }
 }
 
@@ -168,26 +250,8 @@ __global__ void __launch_bounds__(kWtaWarps * 32) k_sgm_wta(SgmJob S) {
     for (int j = 0; j < J; ++j) sum[j] = 0;
 #pragma unroll
     for (int r = 0; r < kDirs; ++r) {
-        const uint8_t* q = S.paths + ((size_t)r * np + p) * S.D + lane * J;
-        uint8_t v[J];
-        if constexpr (J == 1) {
-            v[0] = q[0];
-        } else if constexpr (J == 2) {
-            const uint16_t t = *reinterpret_cast<const uint16_t*>(q);
-            v[0] = t & 0xff;
-            v[1] = t >> 8;
-        } else if constexpr (J == 4) {
-            const uint32_t t = *reinterpret_cast<const uint32_t*>(q);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) v[j] = (t >> (8 * j)) & 0xff;
-        } else {
-            const uint2 t = *reinterpret_cast<const uint2*>(q);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                v[j] = (t.x >> (8 * j)) & 0xff;
-                v[4 + j] = (t.y >> (8 * j)) & 0xff;
-            }
-        }
+        int v[J];
+        load_bytes<J>(S.paths + ((size_t)r * np + p) * S.D + lane * J, v);
 #pragma unroll
         for (int j = 0; j < J; ++j) sum[j] += v[j];
     }
@@ -195,8 +259,7 @@ __global__ void __launch_bounds__(kWtaWarps * 32) k_sgm_wta(SgmJob S) {
     unsigned key = 0xffffffffu;
 #pragma unroll
     for (int j = 0; j < J; ++j) key = min(key, ((unsigned)sum[j] << 8) | (unsigned)(lane * J + j));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) key = min(key, __shfl_xor_sync(kFull, key, o));
+    key = __reduce_min_sync(kFull, key);
     if (lane == 0) S.disp[p] = (int16_t)(key & 0xff);
 }
 
@@ -208,7 +271,7 @@ int check_sgm(const sff_sgm_params* P) {
 }
 
 struct SgmLayout {
-    size_t census0, census1, paths, total;
+    size_t census0, census1, cost, paths, total;
 };
 
 SgmLayout sgm_layout(int w, int h, int D) {
@@ -216,16 +279,18 @@ SgmLayout sgm_layout(int w, int h, int D) {
     SgmLayout L;
     L.census0 = 0;
     L.census1 = align256(np * 8);
-    L.paths = L.census1 + align256(np * 8);
+    L.cost = L.census1 + align256(np * 8);
+    L.paths = L.cost + align256(np * D);
     L.total = L.paths + align256(np * kDirs * D);
     return L;
 }
 
 template <int J>
 void launch_sgm(const SgmJob& S, cudaStream_t st) {
+    const size_t np = (size_t)S.w * S.h;
+    SFF_LAUNCH(k_sgm_cost<J>, dim3((unsigned)((np + kWtaWarps - 1) / kWtaWarps)), kWtaWarps * 32, 0, st, S);
     const int lines = max(S.w, S.h) + min(S.w, S.h) - 1;  // the diagonals have the most lines
     SFF_LAUNCH(k_sgm_paths<J>, dim3((lines + kPathWarps - 1) / kPathWarps, 1, kDirs), kPathWarps * 32, 0, st, S);
-    const size_t np = (size_t)S.w * S.h;
     SFF_LAUNCH(k_sgm_wta<J>, dim3((unsigned)((np + kWtaWarps - 1) / kWtaWarps)), kWtaWarps * 32, 0, st, S);
 }
 
@@ -266,6 +331,7 @@ extern "C" int sff_sgm(const uint8_t* left_dev, const uint8_t* right_dev, int32_
     S.p2 = params->p2;
     S.census[0] = reinterpret_cast<uint64_t*>(ws + L.census0);
     S.census[1] = reinterpret_cast<uint64_t*>(ws + L.census1);
+    S.cost = reinterpret_cast<uint8_t*>(ws + L.cost);
     S.paths = reinterpret_cast<uint8_t*>(ws + L.paths);
     S.disp = disp_dev;
     cudaStream_t st = (cudaStream_t)stream;
