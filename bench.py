@@ -551,6 +551,64 @@ def bench_fill(sff, torch, dev, m, q, params, steps, warmup, cpu: bool):
     return out
 
 
+def bench_method(sff, torch, dev, m, q, params, steps, warmup):
+    """The whole method without its trained parts, as one CUDA graph: the
+    matching stage on one stream and the SGM map (which needs only L0 and R0)
+    on a second stream at the same time, then the seeds with the disparity
+    fill and the dense interpolation.  CUDA events around each replay, L2
+    flushed before it."""
+    w, h = q.width, q.height
+    sp = sff.default_sgm_params()
+    ip = sff.default_interp_params(w, h, q.focal, q.baseline)
+    cap = m.capacity
+    dev_in = [torch.as_tensor(im).to(dev) for im in q.images()]
+    disp = torch.empty((h, w), dtype=torch.int16, device=dev)
+    sws = torch.empty(sff.sgm_workspace_bytes(w, h, sp), dtype=torch.uint8, device=dev)
+    seeds = torch.zeros(20 * cap, dtype=torch.uint8, device=dev)
+    count = torch.zeros(1, dtype=torch.int32, device=dev)
+    ws = torch.empty(sff.workspace_bytes(w, h, params), dtype=torch.uint8, device=dev)
+    field = torch.empty((h, w, 4), dtype=torch.float32, device=dev)
+    iws = torch.empty(sff.interp_workspace_bytes(w, h, cap), dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    s1, s2 = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+
+    def method(a, b):
+        fork = torch.cuda.Event()
+        fork.record(a)
+        b.wait_event(fork)
+        sff.sgm(dev_in[0], dev_in[1], disp, sws, sp, stream=b)
+        m.run(*dev_in, seed=MATCH_SEED, stream=a)
+        join = torch.cuda.Event()
+        join.record(b)
+        a.wait_event(join)
+        sff.emit_seeds_geo(m.fwd, m.fwd_cost, m.keep, m.cerr, disp, seeds, cap, count, ws, params, stream=a)
+        sff.interpolate(seeds, count, cap, w, h, ip, field, iws, stream=a)
+
+    with torch.cuda.stream(s1):
+        for _ in range(max(1, warmup)):
+            method(s1, s2)
+        s1.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s1):
+            method(torch.cuda.current_stream(), s2)
+        for _ in range(max(1, warmup)):
+            g.replay()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record(s1)
+            g.replay()
+            b.record(s1)
+        s1.synchronize()
+    t_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    n = min(int(count.item()), cap)
+    kinds = sff.seeds_to_numpy(seeds.cpu().numpy(), n)["kind"]
+    return {"what": "matching stage || SGM map, then seeds with the disparity fill and the dense interpolation, "
+                    "one CUDA graph with two streams, ms per quad, L2 flushed before each",
+            "ms": t_ms, "px_per_s": w * h / (t_ms / 1e3), "seeds": n, "disparity_only_seeds": int((kinds == 1).sum()),
+            "quality": field_quality(field.cpu().numpy(), q)}
+
+
 def combine_ranks(t_step: float, px_per_rank: int, world: int, device=None):
     """Whole-job throughput of `world` replicas: every rank matched its own
     quad; the job time is the slowest rank's (max over ranks), the pixels are
@@ -742,6 +800,8 @@ def main():
     if not args.no_fill:
         line["disparity_fill"] = bench_fill(sff, torch, dev, m, q, params, min(args.steps, 20), max(3, args.warmup),
                                             rank == 0 and not args.no_cpu_baseline)
+    if not (args.no_fill or args.no_interp):
+        line["method"] = bench_method(sff, torch, dev, m, q, params, min(args.steps, 20), max(3, args.warmup))
     if batch is not None:
         line["batched"] = bench_batched(sff, torch, dev, batch[0], batch[1], params, tuning, min(args.steps, 20),
                                         max(1, args.warmup))
