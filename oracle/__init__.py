@@ -19,6 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sff_oracle.c")
 _SRC_INTERP = os.path.join(_HERE, "sff_interp_oracle.c")
 _SRC_SGM = os.path.join(_HERE, "sff_sgm_oracle.c")
+_SRC_SIFT = os.path.join(_HERE, "sff_sift_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
@@ -49,10 +50,13 @@ assert SEED_DTYPE.itemsize == 20
 
 def build(force: bool = False) -> str:
     """Compile the oracle into oracle/liboracle.so (gcc, OpenMP)."""
-    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_INTERP), os.path.getmtime(_SRC_SGM))
+    newest = max(os.path.getmtime(p) for p in (_SRC, _SRC_INTERP, _SRC_SGM, _SRC_SIFT, __file__))
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11", _SRC, _SRC_INTERP, _SRC_SGM, "-lm",
+        # no fused multiply-adds: the float and double sums follow their
+        # written order, as the CUDA path's do
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11", "-ffp-contract=off", _SRC,
+                               _SRC_INTERP, _SRC_SGM, _SRC_SIFT, "-lm",
                                "-o", tmp])
         os.replace(tmp, _LIB)
     return _LIB
@@ -87,6 +91,17 @@ def lib():
         L.sffi_nearest.argtypes = [P, i32, i32, i32, i32, i32, P, P, P]
         L.sffi_set_threads.argtypes = [i32]
         L.sffs_set_threads.argtypes = [i32]
+        L.sfft_set_threads.argtypes = [i32]
+        L.sfft_orientation_bin.argtypes = [i32, i32]
+        L.sfft_orientation_bin.restype = i32
+        L.sfft_descriptors.argtypes = [P, i32, i32, i32, P]
+        L.sfft_pca.argtypes = [P, ctypes.c_int64, P, P]
+        L.sfft_project.argtypes = [P, ctypes.c_int64, P, P, P]
+        L.sfft_phi.argtypes = [P, i32, i32, i32, P, P, P]
+        L.sfft_cost.argtypes = [P, P, P, P, i32, i32, i32, i32, i32, i32, P]
+        L.sfft_cost.restype = ctypes.c_float
+        L.sffo_match_views_sift.argtypes = [P, P, P, P, P, P, P, P, i32, i32, i32, ctypes.c_uint64,
+                                            ctypes.POINTER(Params), P, P]
         L.sffs_grey.argtypes = [P, i32, i32, i32, P]
         L.sffs_census.argtypes = [P, i32, i32, P]
         L.sffs_cost_volume.argtypes = [P, P, i32, i32, i32, P]
@@ -110,6 +125,7 @@ def set_threads(n: int) -> None:
     lib().sffo_set_threads(int(n))
     lib().sffi_set_threads(int(n))
     lib().sffs_set_threads(int(n))
+    lib().sfft_set_threads(int(n))
 
 
 def get_threads() -> int:
@@ -401,3 +417,74 @@ def emit_seeds_geo(fwd, fwd_cost, keep, cerr, sgm_disp, tau_c: int = 1):
     g = np.ascontiguousarray(sgm_disp, np.int16)
     n = lib().sffs_emit_seeds_geo(_p(f), _p(c), _p(k), _p(e), _p(g), w, h, tau_c, _p(out), cap)
     return out[:min(n, cap)]
+
+
+# ---------------------------------------------------------------------------
+# The paper's own matching cost (Eq. 1 with SIFT-PCA features),
+# sff_sift_oracle.c
+
+
+def orientation_bin(dx: int, dy: int) -> int:
+    return lib().sfft_orientation_bin(int(dx), int(dy))
+
+
+def sift_descriptors(rgb_s, s: int):
+    """Descriptors uint8 [H, W, 128] of a scale-s smoothed image."""
+    rgb_s = np.ascontiguousarray(rgb_s, np.uint8)
+    h, w, _ = rgb_s.shape
+    out = np.empty((h, w, 128), np.uint8)
+    lib().sfft_descriptors(_p(rgb_s), w, h, s, _p(out))
+    return out
+
+
+def sift_pca(desc):
+    d = np.ascontiguousarray(desc, np.uint8).reshape(-1, 128)
+    mean = np.empty(128, np.float64)
+    axes = np.empty((3, 128), np.float64)
+    lib().sfft_pca(_p(d), len(d), _p(mean), _p(axes))
+    return mean, axes
+
+
+def sift_project(desc, mean, axes):
+    d = np.ascontiguousarray(desc, np.uint8)
+    flat = d.reshape(-1, 128)
+    out = np.empty((len(flat), 4), np.float32)
+    mean = np.ascontiguousarray(mean, np.float64)
+    axes = np.ascontiguousarray(axes, np.float64)
+    lib().sfft_project(_p(flat), len(flat), _p(mean), _p(axes), _p(out))
+    return out.reshape(d.shape[:-1] + (4,))
+
+
+def sift_phi(images, num_scales: int = 4):
+    """phi float32 [4][S, H, W, 4] of the four images (L0, R0, L1, R1 or any
+    order), with the principal axes (mean [128], axes [3, 128])."""
+    imgs = [np.ascontiguousarray(im, np.uint8) for im in images]
+    h, w, _ = imgs[0].shape
+    phis = [np.empty((num_scales, h, w, 4), np.float32) for _ in range(4)]
+    ip = (ctypes.c_void_p * 4)(*[im.ctypes.data for im in imgs])
+    pp = (ctypes.c_void_p * 4)(*[ph.ctypes.data for ph in phis])
+    mean = np.empty(128, np.float64)
+    axes = np.empty((3, 128), np.float64)
+    lib().sfft_phi(ip, w, h, num_scales, pp, _p(mean), _p(axes))
+    return phis, mean, axes
+
+
+def sift_cost(phi_ref, phi_tmp, phi_ste, phi_crs, n: int, mirror: int, px: int, py: int, u):
+    """The float cost of vector u at (px, py); phi_* [H, W, 4] of one scale."""
+    h, w, _ = phi_ref.shape
+    a = [np.ascontiguousarray(x, np.float32) for x in (phi_ref, phi_tmp, phi_ste, phi_crs)]
+    uu = np.ascontiguousarray(u, np.int16)
+    return lib().sfft_cost(_p(a[0]), _p(a[1]), _p(a[2]), _p(a[3]), w, h, n, -1 if mirror else 1, px, py, _p(uu))
+
+
+def match_views_sift(f_ref, f_tmp, f_ste, f_crs, phi_ref, phi_tmp, phi_ste, phi_crs, w: int, h: int, mirror: int,
+                     seed: int, params: Params = None):
+    """One field with the SIFT-PCA cost; costs as int32 bit patterns of the floats."""
+    params = params or default_params()
+    field = np.empty((h, w, 4), np.int16)
+    cost = np.empty((h, w), np.int32)
+    f = [np.ascontiguousarray(x, np.int8) for x in (f_ref, f_tmp, f_ste, f_crs)]
+    ph = [np.ascontiguousarray(x, np.float32) for x in (phi_ref, phi_tmp, phi_ste, phi_crs)]
+    lib().sffo_match_views_sift(*[_p(x) for x in f], *[_p(x) for x in ph], w, h, int(mirror),
+                                int(seed) & (2 ** 64 - 1), ctypes.byref(params), _p(field), _p(cost))
+    return field, cost

@@ -243,7 +243,15 @@ void sffo_features(const uint8_t* img, int w, int h, const sffo_params* prm, int
 typedef struct {
     const int8_t* ref; const int8_t* tmp; const int8_t* ste; const int8_t* crs;
     int w, h, sigma;
+    /* the paper's own cost instead (Eq. 1 with SIFT-PCA features, see
+       sff_sift_oracle.c): phi planes of the four views at this scale, NULL
+       for the WHT cost; n the scale's stride */
+    const float* pref; const float* ptmp; const float* pste; const float* pcrs;
+    int n;
 } views_t;
+
+float sfft_cost(const float* ref, const float* tmp, const float* ste, const float* crs, int w, int h, int n,
+                int sigma, int px, int py, const int16_t* u);
 
 static int32_t ssd(const int8_t* a, const int8_t* b) {
     int32_t acc = 0;
@@ -257,6 +265,13 @@ static const int8_t* fat(const int8_t* f, int w, int h, int x, int y) {
 }
 
 static int32_t cost_at(const views_t* V, int px, int py, const int16_t* u) {
+    if (V->pref) {
+        /* a non-negative float's bit pattern orders like the float */
+        const float c = sfft_cost(V->pref, V->ptmp, V->pste, V->pcrs, V->w, V->h, V->n, V->sigma, px, py, u);
+        int32_t b;
+        memcpy(&b, &c, sizeof b);
+        return b;
+    }
     const int8_t* a = V->ref + ((size_t)py * V->w + px) * NF;
     int32_t c = 0;
     c += ssd(a, fat(V->tmp, V->w, V->h, px + u[0], py + u[1]));
@@ -268,7 +283,7 @@ static int32_t cost_at(const views_t* V, int px, int py, const int16_t* u) {
 /* Exported for tests: cost of one vector at one pixel, features at one scale. */
 int32_t sffo_cost(const int8_t* ref, const int8_t* tmp, const int8_t* ste, const int8_t* crs,
                   int w, int h, int mirror, int px, int py, const int16_t* u) {
-    views_t V = {ref, tmp, ste, crs, w, h, mirror ? -1 : 1};
+    views_t V = {ref, tmp, ste, crs, w, h, mirror ? -1 : 1, NULL, NULL, NULL, NULL, 1};
     return cost_at(&V, px, py, u);
 }
 
@@ -508,9 +523,32 @@ static uint64_t splitmix64(uint64_t* st) {
  * temporal R0, stereo L1, cross L0).  feat_*: [S][H][W][48] from sffo_features.
  * field: [H][W][4] int16 (u, v, d0, d1), cost: [H][W] int32 (INT32_MAX = empty).
  */
+static void match_views(const int8_t* f_ref, const int8_t* f_tmp, const int8_t* f_ste, const int8_t* f_crs,
+                        const float* const* phi, int w, int h, int mirror, uint64_t seed, const sffo_params* prm,
+                        int16_t* field, int32_t* cost);
+
 void sffo_match_views(const int8_t* f_ref, const int8_t* f_tmp, const int8_t* f_ste, const int8_t* f_crs,
                       int w, int h, int mirror, uint64_t seed, const sffo_params* prm,
                       int16_t* field, int32_t* cost) {
+    match_views(f_ref, f_tmp, f_ste, f_crs, NULL, w, h, mirror, seed, prm, field, cost);
+}
+
+/* The same with the paper's own cost (Eq. 1, SIFT-PCA features): phi_*
+ * [S][H][W][4] of the four views in the roles of the field; the WHT
+ * features still drive the initialisation's nearest-neighbour search (Sec.
+ * 3.1 "Initialization"), whose combinations are scored with this cost.
+ * cost: the float costs as int32 bit patterns. */
+void sffo_match_views_sift(const int8_t* f_ref, const int8_t* f_tmp, const int8_t* f_ste, const int8_t* f_crs,
+                           const float* phi_ref, const float* phi_tmp, const float* phi_ste, const float* phi_crs,
+                           int w, int h, int mirror, uint64_t seed, const sffo_params* prm, int16_t* field,
+                           int32_t* cost) {
+    const float* phi[4] = {phi_ref, phi_tmp, phi_ste, phi_crs};
+    match_views(f_ref, f_tmp, f_ste, f_crs, phi, w, h, mirror, seed, prm, field, cost);
+}
+
+static void match_views(const int8_t* f_ref, const int8_t* f_tmp, const int8_t* f_ste, const int8_t* f_crs,
+                        const float* const* phi, int w, int h, int mirror, uint64_t seed, const sffo_params* prm,
+                        int16_t* field, int32_t* cost) {
     const int S = prm->num_scales;
     const size_t np = (size_t)w * h;
     static const int DIRS[4][2] = {{1, 1}, {-1, -1}, {1, -1}, {-1, 1}};
@@ -523,7 +561,14 @@ void sffo_match_views(const int8_t* f_ref, const int8_t* f_tmp, const int8_t* f_
     for (int s = S - 1; s >= 0; s--) {
         int n = 1 << s;
         size_t off = (size_t)s * np * NF;
-        views_t V = {f_ref + off, f_tmp + off, f_ste + off, f_crs + off, w, h, mirror ? -1 : 1};
+        views_t V = {f_ref + off, f_tmp + off, f_ste + off, f_crs + off, w, h, mirror ? -1 : 1, NULL, NULL, NULL, NULL, n};
+        if (phi) {
+            const size_t po = (size_t)s * np * 4;
+            V.pref = phi[0] + po;
+            V.ptmp = phi[1] + po;
+            V.pste = phi[2] + po;
+            V.pcrs = phi[3] + po;
+        }
 
         if (s == S - 1) {
             /* initialisation on the coarsest scale only (Sec. 3.1) */
