@@ -17,6 +17,8 @@
  *     sff_match_views         initialisation + multi-scale propagation + random search
  *     sff_consistency_filter  forward/inverse consistency check + region filter
  *     sff_emit_seeds          3x3 sparsification into seeds (Sec. 3.2)
+ * the paper's own cost (Sec. 3.1, Eq. 1 with SIFT-PCA features):
+ *     sff_sift_features, sff_match_views_sift
  * the disparity fill (Sec. 3.1, last paragraph):
  *     sff_sgm, sff_emit_seeds_geo   SGM disparity map, disparity-only seeds
  * and the dense interpolation of the seeds (Sec. 3.3):
@@ -310,6 +312,51 @@ int sff_emit_seeds_noalloc(const int16_t* fwd_dev, const int32_t* fwd_cost_dev,
                            const uint8_t* keep_dev, const uint8_t* cerr_dev,
                            int32_t width, int32_t height, sff_seed* seeds_dev, int32_t capacity,
                            int32_t* count_dev, void* stream);
+
+/* The paper's own matching cost (Sec. 3.1 "Matching Cost", Eq. 1): the sum
+ * over a 7 x 7 window (pixel stride n = 2^s at scale s) of the Euclidean
+ * distances between the first three principal components phi of a dense
+ * SIFT descriptor of the reference view and of each of the three other
+ * views; the principal axes are computed over the descriptors of all four
+ * images.  A float mode beside the WHT-SSD cost of sff_match_views.  This
+ * library's dense SIFT (the paper relies on SIFTFlow's without restating
+ * it): grey (R + 2G + B + 2) >> 2 of the scale's smoothed image; gradients
+ * by central differences at stride n; 8 orientation sectors of 45 degrees
+ * (exact integer tests); 4 x 4 cells of 3 x 3 samples at stride n; L2
+ * normalisation, clipping at 0.2, renormalisation, quantisation to uint8
+ * (x 512).  Axes: covariance of the four images' full-resolution descriptors
+ * from exact integer sums, 200 power iterations per axis in double
+ * precision; the same axes at every scale.  Every floating-point operation
+ * follows a fixed order without fused multiply-adds, so results are
+ * reproducible bit for bit. */
+
+/* Scratch of sff_sift_features: about 650 bytes per pixel; 0 for invalid sizes. */
+size_t sff_sift_workspace_bytes(int32_t width, int32_t height);
+
+/* phi of the four images at every scale.  rgb_dev4: host array of 4 device
+ * pointers to H x W x 3 uint8 images with row pitch pitch_bytes; phi_dev4:
+ * host array of 4 device pointers, each to [num_scales][H][W][4] float
+ * (16-byte aligned; the fourth component is 0).  The principal axes are
+ * computed over all four images, so their order does not matter. */
+int sff_sift_features(const uint8_t* const* rgb_dev4, int32_t pitch_bytes, int32_t width, int32_t height,
+                      const sff_params* params, float* const* phi_dev4, void* workspace, size_t workspace_bytes,
+                      void* stream);
+
+/* sff_match_views with the cost of Eq. 1 on phi (sff_sift_features) instead
+ * of the WHT features.  The WHT pyramids still drive the initialisation's
+ * nearest-neighbour search (Sec. 3.1 "Initialization"); all K_T x K_E x K_E
+ * combinations are then scored with this cost, the first minimum in
+ * (temporal, stereo, cross) rank order winning.  phi_*_dev: [S][H][W][4]
+ * float of the views in the field's roles.  cost_dev receives each float
+ * cost as its int32 bit pattern (non-negative floats order like their bit
+ * patterns; SFF_EMPTY_COST stays the empty marker).  Workspace as
+ * sff_match_views. */
+int sff_match_views_sift(const uint8_t* pyr_ref_dev, const uint8_t* pyr_temporal_dev,
+                         const uint8_t* pyr_stereo_dev, const uint8_t* pyr_cross_dev, const float* phi_ref_dev,
+                         const float* phi_temporal_dev, const float* phi_stereo_dev, const float* phi_cross_dev,
+                         int32_t width, int32_t height, int32_t mirror, uint64_t seed, const sff_params* params,
+                         int16_t* field_dev, int32_t* cost_dev, void* workspace, size_t workspace_bytes,
+                         void* stream);
 
 /* Dense interpolation of the seeds (Sec. 3.3, "Interpolation Models" and
  * "Edge-Aware Neighborhood"), with Euclidean pixel distances in place of the

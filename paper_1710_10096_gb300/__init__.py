@@ -20,6 +20,7 @@ import numpy as np
 __all__ = ["Params", "Tuning", "SffError", "default_params", "default_tuning", "make_tuning", "pyramid_bytes",
            "workspace_bytes", "quad_workspace_bytes", "features", "match_views", "match_quad", "match_quad_tuned",
            "consistency_filter", "emit_seeds", "run_batch", "QuadBuffers", "BatchMatcher", "QuadMatcher",
+           "sift_workspace_bytes", "sift_features", "match_views_sift",
            "SgmParams", "default_sgm_params", "sgm_workspace_bytes", "sgm", "emit_seeds_geo",
            "InterpParams", "default_interp_params", "interp_workspace_bytes", "interpolate", "interp_status",
            "SEED_DTYPE", "lib", "build"]
@@ -152,6 +153,12 @@ def lib():
         L.sff_emit_seeds.restype = i32
         L.sff_emit_seeds_noalloc.argtypes = [P, P, P, P, i32, i32, P, i32, P, P]
         L.sff_emit_seeds_noalloc.restype = i32
+        L.sff_sift_workspace_bytes.argtypes = [i32, i32]
+        L.sff_sift_workspace_bytes.restype = sz
+        L.sff_sift_features.argtypes = [ctypes.POINTER(P), i32, i32, i32, PP, ctypes.POINTER(P), P, sz, P]
+        L.sff_sift_features.restype = i32
+        L.sff_match_views_sift.argtypes = [P, P, P, P, P, P, P, P, i32, i32, i32, ctypes.c_uint64, PP, P, P, P, sz, P]
+        L.sff_match_views_sift.restype = i32
         SP = ctypes.POINTER(SgmParams)
         L.sff_default_sgm_params.argtypes = [SP]
         L.sff_default_sgm_params.restype = i32
@@ -320,6 +327,33 @@ def emit_seeds(fwd, fwd_cost, keep, cerr, seeds, capacity: int, count, workspace
     assert _nbytes(seeds) >= 20 * capacity
     _check(lib().sff_emit_seeds(_ptr(fwd), _ptr(fwd_cost), _ptr(keep), _ptr(cerr), w, h, _ptr(seeds), capacity,
                                 _ptr(count), _ptr(workspace), _nbytes(workspace), _stream(stream)), "sff_emit_seeds")
+
+
+def sift_workspace_bytes(width: int, height: int) -> int:
+    return lib().sff_sift_workspace_bytes(width, height)
+
+
+def sift_features(images, phis, workspace, params: Params = None, stream=None) -> None:
+    """images: 4 CUDA uint8 [H, W, 3] with one row pitch; phis: 4 CUDA float32
+    [S, H, W, 4], overwritten with phi of Eq. 1's SIFT-PCA features."""
+    h, w = images[0].shape[0], images[0].shape[1]
+    assert all(im.stride(0) == images[0].stride(0) for im in images) and len(images) == 4 and len(phis) == 4
+    ip = (ctypes.c_void_p * 4)(*[_ptr(im) for im in images])
+    pp = (ctypes.c_void_p * 4)(*[_ptr(p) for p in phis])
+    _check(lib().sff_sift_features(ip, images[0].stride(0), w, h, ctypes.byref(params or default_params()), pp,
+                                   _ptr(workspace), _nbytes(workspace), _stream(stream)), "sff_sift_features")
+
+
+def match_views_sift(pyr_ref, pyr_temporal, pyr_stereo, pyr_cross, phi_ref, phi_temporal, phi_stereo, phi_cross,
+                     width: int, height: int, mirror: int, seed: int, field, cost, workspace,
+                     params: Params = None, stream=None) -> None:
+    """One field with the cost of Eq. 1 on SIFT-PCA features; cost holds float bit patterns."""
+    params = params or default_params()
+    _check(lib().sff_match_views_sift(_ptr(pyr_ref), _ptr(pyr_temporal), _ptr(pyr_stereo), _ptr(pyr_cross),
+                                      _ptr(phi_ref), _ptr(phi_temporal), _ptr(phi_stereo), _ptr(phi_cross), width,
+                                      height, int(mirror), int(seed) & (2 ** 64 - 1), ctypes.byref(params),
+                                      _ptr(field), _ptr(cost), _ptr(workspace), _nbytes(workspace), _stream(stream)),
+           "sff_match_views_sift")
 
 
 def default_sgm_params(**overrides) -> SgmParams:

@@ -1103,6 +1103,239 @@ __global__ void __launch_bounds__(256) k_random_search(const __grid_constant__ F
     }
 }
 
+// ---------------------------------------------------------------------------
+// The paper's own cost (Eq. 1): the sum over a 7 x 7 window (stride n) of the
+// Euclidean distances between the reference view's SIFT-PCA features phi
+// and those of the three other views (sff_sift.cu computes phi).  Every
+// float operation is written out in the definition's order, so a cost does
+// not depend on the compiler or the machine; the non-negative float is kept as its bit
+// pattern, which orders like the float, so the int32 cost state and its
+// comparisons serve unchanged.  These kernels keep the state at full
+// resolution ([y][x]) and update it in place: a half-step writes one colour
+// and reads the other, the search and the inheritance only the pixel
+// itself.  The initialisation's nearest neighbours are still those of the WHT
+// features (Sec. 3.1 "Initialization"); its combinations are scored with
+// this cost.
+struct SiftViews {
+    const float4 *ref, *tmp, *ste, *crs;  // phi of the scale, [y][x]
+    int w, h, n, sigma;
+};
+
+__device__ __forceinline__ float sift_dist(float4 a, float4 b) {
+    const float dx = __fsub_rn(a.x, b.x), dy = __fsub_rn(a.y, b.y), dz = __fsub_rn(a.z, b.z);
+    return __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz)));
+}
+
+__device__ int sift_cost(const SiftViews& S, int px, int py, const Vec4& a) {
+    float c = 0.0f;
+    for (int j = -3; j <= 3; ++j) {
+        const int y = py + j * S.n;
+        const size_t ry = (size_t)clampi(y, 0, S.h - 1) * S.w, ty = (size_t)clampi(y + a.v, 0, S.h - 1) * S.w;
+        for (int i = -3; i <= 3; ++i) {
+            const int x = px + i * S.n;
+            const float4 r = __ldg(S.ref + ry + clampi(x, 0, S.w - 1));
+            const float4 t = __ldg(S.tmp + ty + clampi(x + a.u, 0, S.w - 1));
+            const float4 st = __ldg(S.ste + ry + clampi(x - S.sigma * a.d0, 0, S.w - 1));
+            const float4 cr = __ldg(S.crs + ty + clampi(x + a.u - S.sigma * a.d1, 0, S.w - 1));
+            c = __fadd_rn(c, sift_dist(r, t));
+            c = __fadd_rn(c, sift_dist(r, st));
+            c = __fadd_rn(c, sift_dist(r, cr));
+        }
+    }
+    return __float_as_int(c);
+}
+
+__global__ void k_sift_clear(uint2* field, int* cost, size_t np) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    field[i] = make_uint2(0u, 0u);
+    cost[i] = kEmpty;
+}
+
+// The K nearest epipolar points of one coarsest-grid row by WHT distance, in
+// (distance, x) order, among the points with sigma (xlim - x) >= 0: K rounds,
+// each taking the smallest pair after the previous one.  All lanes return
+// the same list.
+__device__ int warp_row_topk(const RefFeat& r, const int4* rec, const int* rec_n, int n, int gw, int gy, int xlim,
+                             int sigma, int lane, int K, int* kd, int* kx) {
+    const int4* row = rec + (size_t)gy * gw * 3;
+    const int* row_n = rec_n + (size_t)gy * gw;
+    int pd = -1, px = -1, cnt = 0;
+    for (int k = 0; k < K; ++k) {
+        int bd = 0x7fffffff, bx = 0x7fffffff;
+        for (int g = lane; g < gw; g += 32) {
+            const int x = g * n;
+            if (sigma * (xlim - x) < 0) continue;
+            const int4 q0 = __ldg(row + 3 * g), q1 = __ldg(row + 3 * g + 1), q2 = __ldg(row + 3 * g + 2);
+            int dot = 0;
+            dot = __dp4a(r.a[0], q0.x, dot); dot = __dp4a(r.a[1], q0.y, dot);
+            dot = __dp4a(r.a[2], q0.z, dot); dot = __dp4a(r.a[3], q0.w, dot);
+            dot = __dp4a(r.a[4], q1.x, dot); dot = __dp4a(r.a[5], q1.y, dot);
+            dot = __dp4a(r.a[6], q1.z, dot); dot = __dp4a(r.a[7], q1.w, dot);
+            dot = __dp4a(r.a[8], q2.x, dot); dot = __dp4a(r.a[9], q2.y, dot);
+            dot = __dp4a(r.a[10], q2.z, dot); dot = __dp4a(r.a[11], q2.w, dot);
+            const int d = r.n + __ldg(row_n + g) - 2 * dot;
+            const bool after = d > pd || (d == pd && x > px);
+            if (after && (d < bd || (d == bd && x < bx))) {
+                bd = d;
+                bx = x;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const int od = __shfl_xor_sync(0xffffffffu, bd, o), ox = __shfl_xor_sync(0xffffffffu, bx, o);
+            if (od < bd || (od == bd && ox < bx)) {
+                bd = od;
+                bx = ox;
+            }
+        }
+        if (bx == 0x7fffffff) break;
+        kd[k] = bd;
+        kx[k] = bx;
+        pd = bd;
+        px = bx;
+        ++cnt;
+    }
+    return cnt;
+}
+
+// One warp per coarsest-grid query: all K_T x K_E x K_E combinations, each
+// scored by one lane; the first minimum in (temporal, stereo, cross) rank
+// order wins, as in a sequential loop with a strict comparison.
+__global__ void k_sift_init(const __grid_constant__ Fields F, SiftViews S, int n, int knn_t, int knn_e, uint2* field,
+                            int* cost) {
+    const Field& A = F.f[0];
+    const Views& V = A.V;
+    const int gw = A.gw;
+    const int qi = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int lane = threadIdx.x & 31;
+    if (qi >= A.gq) return;  // warp-uniform
+    const int px = (qi % gw) * n, py = (qi / gw) * n;
+    RefFeat r;
+    load_ref(V.ref, pix(V.w, px, py), r);
+    int sd[SFF_MAX_KNN], sx[SFF_MAX_KNN], xd[SFF_MAX_KNN], xx[SFF_MAX_KNN];
+    const int ns = warp_row_topk(r, A.rec, A.rec_n, n, gw, qi / gw, px, V.sigma, lane, knn_e, sd, sx);
+    int best = kEmpty;
+    Vec4 bv = {0, 0, 0, 0};
+    const int2* src = A.best8 + (size_t)qi * 8;
+    for (int k = 0; k < knn_t && k < 8; ++k) {
+        const int2 e = src[k];
+        if (e.x == 0x7fffffff) break;
+        const int tx = (e.y % gw) * n, ty = (e.y / gw) * n;
+        const int nx = warp_row_topk(r, A.rec + (size_t)A.gq * 3, A.rec_n + A.gq, n, gw, e.y / gw, tx, V.sigma, lane,
+                                     knn_e, xd, xx);
+        // lane l scores combination (l / nx, l % nx)
+        unsigned long long key = ~0ull;
+        Vec4 cand = {tx - px, ty - py, 0, 0};
+        for (int l0 = 0; l0 < ns * nx; l0 += 32) {
+            const int l = l0 + lane;
+            if (l < ns * nx) {
+                int sxl = sx[0], cxl = xx[0];
+#pragma unroll
+                for (int t = 0; t < SFF_MAX_KNN; ++t) {
+                    if (t == l / nx) sxl = sx[t];
+                    if (t == l % nx) cxl = xx[t];
+                }
+                Vec4 u = {tx - px, ty - py, V.sigma * (px - sxl), V.sigma * (tx - cxl)};
+                u.u = (int16_t)u.u;
+                u.v = (int16_t)u.v;
+                u.d0 = (int16_t)u.d0;
+                u.d1 = (int16_t)u.d1;
+                const int c = sift_cost(S, px, py, u);
+                const unsigned long long kk = ((unsigned long long)(unsigned)c << 32) | (unsigned)l;
+                if (kk < key) {
+                    key = kk;
+                    cand = u;
+                }
+            }
+        }
+        // the smallest (cost, combination) key of the warp and its lane
+        unsigned long long m = key;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long om = __shfl_xor_sync(0xffffffffu, m, o);
+            m = om < m ? om : m;
+        }
+        const int c = (int)(m >> 32);
+        const int owner = __ffs(__ballot_sync(0xffffffffu, key == m && m != ~0ull)) - 1;
+        if (owner >= 0 && c < best) {
+            best = c;
+            bv.u = __shfl_sync(0xffffffffu, cand.u, owner);
+            bv.v = __shfl_sync(0xffffffffu, cand.v, owner);
+            bv.d0 = __shfl_sync(0xffffffffu, cand.d0, owner);
+            bv.d1 = __shfl_sync(0xffffffffu, cand.d1, owner);
+        }
+    }
+    if (lane == 0) {
+        field[pix(V.w, px, py)] = pack_vec(bv);
+        cost[pix(V.w, px, py)] = best;
+    }
+}
+
+__global__ void k_sift_inherit(SiftViews S, int gw, int gh, uint2* field, int* cost) {
+    const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y;
+    if (gx >= gw || gy >= gh) return;
+    const int x = gx * S.n, y = gy * S.n;
+    const size_t i = pix(S.w, x, y);
+    if (((gx | gy) & 1) == 0 && cost[i] != kEmpty) {
+        cost[i] = sift_cost(S, x, y, unpack_vec(field[i]));
+    } else {
+        cost[i] = kEmpty;
+        field[i] = make_uint2(0u, 0u);
+    }
+}
+
+// Half-step of one colour: the pixel's own vector against its horizontal,
+// then its vertical predecessor's (strictly lower cost wins).
+__global__ void k_sift_half(SiftViews S, int gw, int gh, int colour, int dx, int dy, uint2* field, int* cost) {
+    const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y;
+    if (gx >= gw || gy >= gh || ((gx + gy) & 1) != colour) return;
+    const int x = gx * S.n, y = gy * S.n;
+    const size_t i = pix(S.w, x, y);
+    int bc = cost[i];
+    uint2 bw = field[i];
+    const int qx[2] = {x - dx * S.n, x}, qy[2] = {y, y - dy * S.n};
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        if (qx[k] < 0 || qy[k] < 0 || qx[k] >= S.w || qy[k] >= S.h) continue;
+        const size_t j = pix(S.w, qx[k], qy[k]);
+        if (cost[j] == kEmpty) continue;
+        const uint2 w = field[j];
+        const int c = sift_cost(S, x, y, unpack_vec(w));
+        if (c < bc) {
+            bc = c;
+            bw = w;
+        }
+    }
+    field[i] = bw;
+    cost[i] = bc;
+}
+
+__global__ void k_sift_search(SiftViews S, int gw, int gh, int s, int it, int mirror, uint2 key, uint2* field,
+                              int* cost) {
+    const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y;
+    if (gx >= gw || gy >= gh) return;
+    const int x = gx * S.n, y = gy * S.n;
+    const size_t i = pix(S.w, x, y);
+    const int c0 = cost[i];
+    if (c0 == kEmpty) return;
+    const Vec4 a = unpack_vec(field[i]);
+    const uint4 r = philox4x32_10(make_uint4((uint32_t)i, (uint32_t)it, (uint32_t)(s + 4 * mirror), 0u), key);
+    Vec4 u = {a.u + rs_offset(r.x, S.n), a.v + rs_offset(r.y, S.n), a.d0 + rs_offset(r.z, S.n),
+              a.d1 + rs_offset(r.w, S.n)};
+    if (u.d0 < 0) u.d0 = 0;
+    if (u.d1 < 0) u.d1 = 0;
+    u.u = (int16_t)u.u;
+    u.v = (int16_t)u.v;
+    u.d0 = (int16_t)u.d0;
+    u.d1 = (int16_t)u.d1;
+    const int c = sift_cost(S, x, y, u);
+    if (c < c0) {
+        field[i] = pack_vec(u);
+        cost[i] = c;
+    }
+}
+
 // Instantiated (lanes per pixel, tile) variants; any of them gives identical
 // results.
 using IterKernel = void (*)(Fields, IterStep);
@@ -1331,6 +1564,62 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
     return launch_status();
 }
 
+// One field with the paper's own cost: the WHT K-NN of the coarsest scale as
+// in run_fields, then initialisation, inheritance, half-steps and random
+// search in the kernels above.  phi[4]: [S][H][W] float4 of the views in the
+// field's roles (reference, temporal, stereo, cross).
+int run_field_sift(const FieldSpec& fs, const float* const* phi, const sff_params& P, cudaStream_t st) {
+    const int S = P.num_scales, I = P.iterations, w = fs.width, h = fs.height;
+    static const int kDirs[4][2] = {{1, 1}, {-1, -1}, {1, -1}, {-1, 1}};
+    static Fields F;
+    std::lock_guard<std::mutex> lk(g_fields_mu);
+    memset(&F, 0, sizeof F);
+    const FieldScratch sc = field_scratch(w, h, P);
+    char* ws = reinterpret_cast<char*>(fs.workspace);
+    Field& A = F.f[0];
+    A.best8 = reinterpret_cast<int2*>(ws + sc.best8);
+    A.tk = reinterpret_cast<uint8_t*>(ws + sc.tk);
+    A.rec = reinterpret_cast<int4*>(ws + sc.rec);
+    A.rec_n = reinterpret_cast<int*>(ws + sc.rec_n);
+    A.gq = coarse_gq(w, h, P);
+    A.mirror = fs.mirror;
+    A.key = make_uint2((uint32_t)fs.seed, (uint32_t)(fs.seed >> 32));
+    uint2* field = reinterpret_cast<uint2*>(fs.field);
+    int* cost = fs.cost;
+    const size_t np = (size_t)w * h;
+    SFF_LAUNCH(k_sift_clear, dim3((unsigned)((np + 255) / 256)), 256, 0, st, field, cost, np);
+    for (int s = S - 1; s >= 0; --s) {
+        const int n = 1 << s, gw = (w + n - 1) / n, gh = (h + n - 1) / n;
+        const size_t off = (size_t)s * np;
+        SiftViews SV{reinterpret_cast<const float4*>(phi[0]) + off, reinterpret_cast<const float4*>(phi[1]) + off,
+                     reinterpret_cast<const float4*>(phi[2]) + off, reinterpret_cast<const float4*>(phi[3]) + off,
+                     w, h, n, fs.mirror ? -1 : 1};
+        const dim3 g((gw + 127) / 128, gh);
+        if (s == S - 1) {
+            A.V = Views{plane_of(fs.ref, s, S, w, h), plane_of(fs.tmp, s, S, w, h), plane_of(fs.ste, s, S, w, h),
+                        plane_of(fs.crs, s, S, w, h), w, h, fs.mirror ? -1 : 1};
+            A.gw = gw;
+            A.gh = gh;
+            dim3 g0((tc_rows(A.gq) * 8 + 255) / 256, 4, 1);
+            SFF_LAUNCH(k_gather_grid, g0, 256, 0, st, F, n);
+            if (!knn_smem_ready()) return SFF_ERR_CUDA;
+            dim3 g1((A.gq + kTcRows - 1) / kTcRows, 1, 1);
+            SFF_LAUNCH(k_knn_tc, g1, kTcThreads, kTcSmemBytes, st, F);
+            SFF_LAUNCH(k_sift_init, dim3((A.gq + 7) / 8), 256, 0, st, F, SV, n, P.knn_temporal, P.knn_epipolar, field,
+                       cost);
+        } else {
+            SFF_LAUNCH(k_sift_inherit, g, 128, 0, st, SV, gw, gh, field, cost);
+        }
+        for (int it = 0; it < I; ++it) {
+            for (int colour = 0; colour < 2; ++colour)
+                SFF_LAUNCH(k_sift_half, g, 128, 0, st, SV, gw, gh, colour, kDirs[it % 4][0], kDirs[it % 4][1], field,
+                           cost);
+            SFF_LAUNCH(k_sift_search, g, 128, 0, st, SV, gw, gh, s, it, fs.mirror, A.key, field, cost);
+        }
+    }
+    return launch_status();
+}
+
 namespace {
 
 bool misaligned_pyr(const uint8_t* p) { return ((uintptr_t)p & 15) != 0; }
@@ -1444,4 +1733,30 @@ extern "C" int sff_device_timeouts(uint32_t* out, int32_t reset) {
         if (cudaMemcpyToSymbol(sff::g_wait_timeouts, &z, sizeof z) != cudaSuccess) return SFF_ERR_CUDA;
     }
     return SFF_OK;
+}
+
+extern "C" int sff_match_views_sift(const uint8_t* pyr_ref_dev, const uint8_t* pyr_temporal_dev,
+                                    const uint8_t* pyr_stereo_dev, const uint8_t* pyr_cross_dev,
+                                    const float* phi_ref_dev, const float* phi_temporal_dev,
+                                    const float* phi_stereo_dev, const float* phi_cross_dev, int32_t width,
+                                    int32_t height, int32_t mirror, uint64_t seed, const sff_params* params,
+                                    int16_t* field_dev, int32_t* cost_dev, void* workspace, size_t workspace_bytes,
+                                    void* stream) {
+    using namespace sff;
+    if (check_size(width, height) || check_params(params)) return SFF_ERR_ARG;
+    if (!pyr_ref_dev || !pyr_temporal_dev || !pyr_stereo_dev || !pyr_cross_dev || !field_dev || !cost_dev ||
+        !workspace || !phi_ref_dev || !phi_temporal_dev || !phi_stereo_dev || !phi_cross_dev)
+        return SFF_ERR_ARG;
+    if (mirror != 0 && mirror != 1) return SFF_ERR_ARG;
+    if (misaligned_pyr(pyr_ref_dev) || misaligned_pyr(pyr_temporal_dev) || misaligned_pyr(pyr_stereo_dev) ||
+        misaligned_pyr(pyr_cross_dev))
+        return SFF_ERR_ARG;
+    const float* phi[4] = {phi_ref_dev, phi_temporal_dev, phi_stereo_dev, phi_cross_dev};
+    for (const float* p : phi)
+        if ((uintptr_t)p & 15) return SFF_ERR_ARG;
+    if (((uintptr_t)field_dev & 7) || ((uintptr_t)cost_dev & 3) || ((uintptr_t)workspace & 255)) return SFF_ERR_ARG;
+    if (workspace_bytes < match_ws_bytes(width, height, *params)) return SFF_ERR_WORKSPACE;
+    FieldSpec f{pyr_ref_dev, pyr_temporal_dev, pyr_stereo_dev, pyr_cross_dev, field_dev, cost_dev, mirror,
+                width, height, seed, workspace};
+    return run_field_sift(f, phi, *params, (cudaStream_t)stream);
 }
