@@ -59,6 +59,7 @@ def parse():
                     help="skip the comparison with the paper's sequential propagation order")
     ap.add_argument("--no-interp", action="store_true", help="skip the dense interpolation measurement")
     ap.add_argument("--no-fill", action="store_true", help="skip the disparity fill (SGM) measurement")
+    ap.add_argument("--no-sift", action="store_true", help="skip the SIFT-PCA cost measurement")
     ap.add_argument("--tuning", default="auto",
                     help="work distribution of the propagation kernels: 'auto' (autotune) or L,TX,TY")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(scenegen.CONFIG_SIZES),
@@ -609,6 +610,82 @@ def bench_method(sff, torch, dev, m, q, params, steps, warmup):
             "quality": field_quality(field.cpu().numpy(), q)}
 
 
+def bench_sift(sff, torch, dev, m, q, params, steps, warmup):
+    """The paper's own cost (Eq. 1 with SIFT-PCA features) against the WHT-SSD
+    cost on the quad: the phi features of the four images and both fields
+    with the SIFT cost (CUDA events, L2 flushed before each), and the
+    accuracy of the forward field and of the filtered matches of both modes
+    against the scene's ground truth."""
+    w, h = q.width, q.height
+    S = params.num_scales
+    stream = torch.cuda.Stream(device=dev)
+    dev_in = [torch.as_tensor(im).to(dev) for im in q.images()]
+    phis = [torch.empty((S, h, w, 4), dtype=torch.float32, device=dev) for _ in range(4)]
+    sws = torch.empty(sff.sift_workspace_bytes(w, h), dtype=torch.uint8, device=dev)
+    ws = torch.empty(sff.workspace_bytes(w, h, params), dtype=torch.uint8, device=dev)
+    f = [torch.empty((h, w, 4), dtype=torch.int16, device=dev) for _ in range(2)]
+    c = [torch.empty((h, w), dtype=torch.int32, device=dev) for _ in range(2)]
+    keep = torch.empty((h, w), dtype=torch.uint8, device=dev)
+    cerr = torch.empty((h, w), dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    L0, R0, L1, R1 = m.pyr
+    pL0, pR0, pL1, pR1 = phis
+
+    def feats():
+        sff.sift_features(dev_in, phis, sws, params, stream=stream)
+
+    def fields():
+        sff.match_views_sift(L0, L1, R0, R1, pL0, pL1, pR0, pR1, w, h, 0, MATCH_SEED, f[0], c[0], ws, params,
+                             stream=stream)
+        sff.match_views_sift(R1, R0, L1, L0, pR1, pR0, pL1, pL0, w, h, 1, MATCH_SEED, f[1], c[1], ws, params,
+                             stream=stream)
+
+    times = {}
+    with torch.cuda.stream(stream):
+        m.run(*dev_in, seed=MATCH_SEED, stream=stream)
+        for name, fn in (("features_ms", feats), ("fields_ms", fields)):
+            for _ in range(max(1, warmup)):
+                fn()
+            ev = []
+            for _ in range(steps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                ev.append((a, b))
+            stream.synchronize()
+            times[name] = statistics.mean(x.elapsed_time(y) for x, y in ev)
+        sff.consistency_filter(f[0], c[0], f[1], c[1], keep, cerr, ws, params, stream=stream)
+        stream.synchronize()
+        sff.profile_enable(True)
+        feats()
+        fields()
+        stream.synchronize()
+        prof = sff.profile_collect()
+        sff.profile_enable(False)
+    vis = ~q.occluded
+    gt = q.gt
+
+    def accuracy(field, kept):
+        e = np.abs(field.astype(np.float64) - gt)
+        bad = (e > 3).any(axis=2)
+        out = {"raw_outliers": float(bad[vis].mean()), "raw_epe_flow": float(np.hypot(e[..., 0], e[..., 1])[vis].mean())}
+        k = kept & vis
+        out["filtered_density"] = float(k.sum() / vis.sum())
+        out["filtered_outliers"] = float(bad[k].mean()) if k.any() else None
+        return out
+
+    res = {"what": "the paper's SIFT-PCA cost (Eq. 1) against the WHT-SSD cost on the quad; times per quad with the "
+                   "L2 flushed before each, accuracy against the scene's ground truth (visible pixels; an outlier has a "
+                   "component off by more than 3 px)",
+           "features_ms": times["features_ms"], "fields_ms": times["fields_ms"],
+           "kernels": {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
+           "sift": accuracy(f[0].cpu().numpy(), keep.cpu().numpy().astype(bool)),
+           "wht": accuracy(m.fwd.cpu().numpy(), m.keep.cpu().numpy().astype(bool))}
+    return res
+
+
 def combine_ranks(t_step: float, px_per_rank: int, world: int, device=None):
     """Whole-job throughput of `world` replicas: every rank matched its own
     quad; the job time is the slowest rank's (max over ranks), the pixels are
@@ -802,6 +879,8 @@ def main():
                                             rank == 0 and not args.no_cpu_baseline)
     if not (args.no_fill or args.no_interp):
         line["method"] = bench_method(sff, torch, dev, m, q, params, min(args.steps, 20), max(3, args.warmup))
+    if not args.no_sift:
+        line["sift_cost"] = bench_sift(sff, torch, dev, m, q, params, 3, 1)
     if batch is not None:
         line["batched"] = bench_batched(sff, torch, dev, batch[0], batch[1], params, tuning, min(args.steps, 20),
                                         max(1, args.warmup))

@@ -299,14 +299,22 @@ __global__ void __launch_bounds__(128) k_sift_project(SiftJob J) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, v = blockIdx.z;
     if (x >= J.w) return;
     const size_t p = (size_t)y * J.w + x;
-    const uint8_t* q = J.desc + ((size_t)v * J.h * J.w + p) * kDesc;
+    const uint4* q = reinterpret_cast<const uint4*>(J.desc + ((size_t)v * J.h * J.w + p) * kDesc);
+    float t[3] = {0.0f, 0.0f, 0.0f};
+    for (int k16 = 0; k16 < kDesc / 16; ++k16) {  // 16 components per load, in index order
+        const uint4 w = q[k16];
+        const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int b = 0; b < 16; ++b) {
+            const float qv = (float)((words[b >> 2] >> (8 * (b & 3))) & 0xffu);
+            const int k = k16 * 16 + b;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) t[c] = __fadd_rn(t[c], __fmul_rn(a[c * kDesc + k], qv));
+        }
+    }
     float r[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        float t = 0.0f;
-        for (int k = 0; k < kDesc; ++k) t = __fadd_rn(t, __fmul_rn(a[c * kDesc + k], (float)q[k]));
-        r[c] = __fsub_rn(t, a[3 * kDesc + c]);
-    }
+    for (int c = 0; c < 3; ++c) r[c] = __fsub_rn(t[c], a[3 * kDesc + c]);
     reinterpret_cast<float4*>(phi_of(J, v))[(size_t)J.s * J.w * J.h + p] = make_float4(r[0], r[1], r[2], 0.0f);
 }
 

@@ -94,3 +94,32 @@ def test_sift_cost_on_a_shift_scene(env):
     assert np.array_equal(gf, want[0][0]) and np.array_equal(gc, want[0][1])
     inner = gf[20:-20, 20:-20].reshape(-1, 4)
     assert (inner == np.array([-3, 2, 6, 4])).all(axis=1).mean() > 0.99
+
+
+def test_full_size_phi_and_cost_property(env):
+    # 1242 x 375: phi of all scales bit-exact; the final state's cost at
+    # sampled pixels equals the oracle's cost of the final vector
+    torch, sff, orc = env
+    q = scenegen.make_named("driving_1242x375", 2)
+    images = list(q.images())
+    _, phis = _gpu_phi(env, images, 4)
+    want, _, _ = orc.sift_phi(images, num_scales=4)
+    for g, o in zip(phis, want):
+        assert np.array_equal(g.cpu().numpy(), o)
+    p = sff.default_params()
+    m = sff.QuadMatcher(q.width, q.height, p)
+    dev = [torch.as_tensor(im).cuda() for im in q.images()]
+    m.run(*dev, seed=2024)
+    L0, R0, L1, R1 = m.pyr
+    w, h = q.width, q.height
+    ws = torch.empty(sff.workspace_bytes(w, h, p), dtype=torch.uint8, device="cuda")
+    f = torch.empty((h, w, 4), dtype=torch.int16, device="cuda")
+    c = torch.empty((h, w), dtype=torch.int32, device="cuda")
+    sff.match_views_sift(L0, L1, R0, R1, phis[0], phis[2], phis[1], phis[3], w, h, 0, 2024, f, c, ws, p)
+    torch.cuda.synchronize()
+    field, cost = f.cpu().numpy(), c.cpu().numpy()
+    rng = np.random.default_rng(4)
+    oL0, oR0, oL1, oR1 = (x[0] for x in want)
+    for x, y in zip(rng.integers(0, w, 300), rng.integers(0, h, 300)):
+        got = np.array([cost[y, x]], np.int32).view(np.float32)[0]
+        assert got == orc.sift_cost(oL0, oL1, oR0, oR1, 1, 0, int(x), int(y), field[y, x])
