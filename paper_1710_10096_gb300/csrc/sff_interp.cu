@@ -51,7 +51,7 @@ namespace {
 constexpr int kBlock = 3;            // sparsification block of Sec. 3.2
 constexpr int kModelWarps = 2;       // warps (seeds) per CTA of k_interp_models
 constexpr int kMaxK = 1024;          // largest k_geo / k_motion
-constexpr int kRegKeys = 24;         // candidate keys per lane held in registers during selection
+constexpr int kRegKeys = 16;         // candidate keys per lane held in registers during selection
 
 // Candidate slots per seed: the rings up to the bound of the k-th nearest
 // hold about 4/pi times k seeds plus a margin of whole rings; 6 k + 256
@@ -308,6 +308,28 @@ __device__ __forceinline__ void with_keys(const Candidates& C, int lane, F f) {
     }
 }
 
+// The k-th smallest distances DA, DM of both sets (hiA / hiM: bounds that
+// at least k members are within; 0 skips a set) and the counts of members
+// below and at them (warp-reduced).  One routine serves the tightening of
+// the ring bound and the final selection, so that its code exists once.
+__device__ __noinline__ void kth_and_counts(const Candidates& C, int kg, int km, unsigned hiA, unsigned hiM,
+                                            int lane, unsigned& DA, unsigned& DM, int (&cnt)[4]) {
+    int ba = 0, ea = 0, bm = 0, em = 0;
+    with_keys(C, lane, [&](auto each) {
+        bisect_both(each, kg, km, hiA, hiM, DA, DM);
+        each([&](unsigned d2, unsigned mot) {
+            ba += d2 < DA;
+            ea += d2 == DA;
+            bm += mot & (d2 < DM);
+            em += mot & (d2 == DM);
+        });
+    });
+    cnt[0] = warp_sum_i(ba);
+    cnt[1] = warp_sum_i(ea);
+    cnt[2] = warp_sum_i(bm);
+    cnt[3] = warp_sum_i(em);
+}
+
 // Thresholds of the k smallest (d2, index) keys of both neighbourhoods.
 // `fa`/`fm` are the sizes of the two sets, `far_a`/`far_m` distances that
 // at least k of their members are within.
@@ -318,27 +340,15 @@ __device__ void select_both(const Candidates& C, int kg, int km, int fa, int fm,
     const bool sa = fa > kg, sm = fm > km;
     if (!sa && !sm) return;
     unsigned DA, DM;
-    int ba = 0, ea = 0, bm = 0, em = 0;
-    with_keys(C, lane, [&](auto each) {
-        bisect_both(each, kg, km, sa ? far_a : 0, sm ? far_m : 0, DA, DM);
-        each([&](unsigned d2, unsigned mot) {
-            ba += d2 < DA;
-            ea += d2 == DA;
-            bm += mot & (d2 < DM);
-            em += mot & (d2 == DM);
-        });
-    });
-    ba = warp_sum_i(ba);
-    ea = warp_sum_i(ea);
-    bm = warp_sum_i(bm);
-    em = warp_sum_i(em);
+    int cnt[4];
+    kth_and_counts(C, kg, km, sa ? far_a : 0, sm ? far_m : 0, lane, DA, DM, cnt);
     if (sa) {
         A.D = DA;
-        if (kg - ba < ea) A.I = tie_threshold(C, false, DA, kg - ba, ea, n, scratch, lane);
+        if (kg - cnt[0] < cnt[1]) A.I = tie_threshold(C, false, DA, kg - cnt[0], cnt[1], n, scratch, lane);
     }
     if (sm) {
         M.D = DM;
-        if (km - bm < em) M.I = tie_threshold(C, true, DM, km - bm, em, n, scratch, lane);
+        if (km - cnt[2] < cnt[3]) M.I = tie_threshold(C, true, DM, km - cnt[2], cnt[3], n, scratch, lane);
     }
 }
 
@@ -480,7 +490,8 @@ __global__ void __launch_bounds__(kModelWarps * 32) k_interp_models(InterpJob J)
     }
     if (fa >= kg && fm >= km) {
         const Candidates C1{pos, word, fill};
-        with_keys(C1, lane, [&](auto each) { bisect_both(each, kg, km, bound_a, bound_m, bound_a, bound_m); });
+        int cnt[4];
+        kth_and_counts(C1, kg, km, bound_a, bound_m, lane, bound_a, bound_m, cnt);
         for (; q <= rmax; ++q) {
             const long long b = 3 * q - 2;
             if (b * b > (long long)max(bound_a, bound_m)) break;
