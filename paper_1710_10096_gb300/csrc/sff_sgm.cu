@@ -168,8 +168,8 @@ __global__ void __launch_bounds__(kWtaWarps * 32) k_sgm_cost(SgmJob S) {
 }
 
 template <int J>
-__global__ void __launch_bounds__(kPathWarps * 32) k_sgm_paths(SgmJob S, int dir0) {
-    const int dir = dir0 + blockIdx.z;
+__global__ void __launch_bounds__(kPathWarps * 32) k_sgm_paths(SgmJob S) {
+    const int dir = blockIdx.z;
     const int rx = c_dir[dir][0], ry = c_dir[dir][1];
     const int lane = threadIdx.x & 31;
     const int line = blockIdx.x * kPathWarps + (threadIdx.x >> 5);
@@ -290,7 +290,7 @@ void launch_sgm(const SgmJob& S, cudaStream_t st) {
     const size_t np = (size_t)S.w * S.h;
     SFF_LAUNCH(k_sgm_cost<J>, dim3((unsigned)((np + kWtaWarps - 1) / kWtaWarps)), kWtaWarps * 32, 0, st, S);
     const int lines = S.w + S.h - 1;  // the diagonals have the most lines
-    SFF_LAUNCH(k_sgm_paths<J>, dim3((lines + kPathWarps - 1) / kPathWarps, 1, kDirs), kPathWarps * 32, 0, st, S, 0);
+    SFF_LAUNCH(k_sgm_paths<J>, dim3((lines + kPathWarps - 1) / kPathWarps, 1, kDirs), kPathWarps * 32, 0, st, S);
     SFF_LAUNCH(k_sgm_wta<J>, dim3((unsigned)((np + kWtaWarps - 1) / kWtaWarps)), kWtaWarps * 32, 0, st, S);
 }
 
