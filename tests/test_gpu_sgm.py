@@ -117,3 +117,35 @@ def test_whole_stage_with_fill(env):
     assert np.array_equal(disp.cpu().numpy(), odisp)
     n = int(count.item())
     assert sff.seeds_to_numpy(seeds.cpu().numpy(), n).tobytes() == want.tobytes()
+
+
+def test_interpolation_of_seeds_with_the_fill(env):
+    # each side interpolates its own seeds with disparity-only entries: those
+    # join the plane fits only (d1 = 0 keeps them out of the motion fits)
+    torch, sff, orc = env
+    q = scenegen.make_named("planes_256x80", 5)
+    w, h = q.width, q.height
+    m = sff.QuadMatcher(w, h)
+    dev = [torch.as_tensor(im).cuda() for im in q.images()]
+    m.run(*dev, seed=5)
+    p = sff.default_sgm_params(max_disp=64)
+    disp = torch.empty((h, w), dtype=torch.int16, device="cuda")
+    sws = torch.empty(sff.sgm_workspace_bytes(w, h, p), dtype=torch.uint8, device="cuda")
+    sff.sgm(dev[0], dev[1], disp, sws, p)
+    cap = sff.seed_capacity(w, h)
+    seeds = torch.zeros(20 * cap, dtype=torch.uint8, device="cuda")
+    count = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ws = torch.empty(sff.workspace_bytes(w, h), dtype=torch.uint8, device="cuda")
+    sff.emit_seeds_geo(m.fwd, m.fwd_cost, m.keep, m.cerr, disp, seeds, cap, count, ws)
+    ip = sff.default_interp_params(w, h, q.focal, q.baseline)
+    field = torch.empty((h, w, 4), dtype=torch.float32, device="cuda")
+    iws = torch.empty(sff.interp_workspace_bytes(w, h, cap), dtype=torch.uint8, device="cuda")
+    sff.interpolate(seeds, count, cap, w, h, ip, field, iws)
+    torch.cuda.synchronize()
+    ref = orc.run_quad(*q.images(), seed=5)
+    od = orc.sgm(q.L0, q.R0, orc.sgm_params(max_disp=64))
+    os_ = orc.emit_seeds_geo(ref["fwd"], ref["fwd_cost"], ref["keep"], ref["cerr"], od, tau_c=1)
+    assert (os_["kind"] == 1).sum() > 0
+    want = orc.interpolate(os_, w, h, orc.interp_params(w, h, q.focal, q.baseline))
+    assert sff.interp_status(iws, w, h, cap) == 0
+    np.testing.assert_allclose(field.cpu().numpy(), want, rtol=1e-5, atol=1e-3)
