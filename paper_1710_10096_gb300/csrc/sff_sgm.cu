@@ -21,10 +21,10 @@
 //               step then reads D bytes instead of D census words).
 // k_sgm_paths:  one warp per path line of one direction (blockIdx.z), the
 //               lanes holding D / 32 consecutive disparities each; one step
-//               per pixel, with the costs of the next 8 pixels of the line
-//               already loaded (a step waits on one reduction, not on L2):
-//               the neighbours' d +- 1 values by shuffles, the minimum over
-//               d by one redux; L_r to [dir][y][x][d].
+//               per pixel, the costs of the next 32 pixels of the line in
+//               flight into a shared-memory ring (cp.async): the
+//               neighbours' d +- 1 values by shuffles, the minimum over d
+//               by one redux; L_r to [dir][y][x][d].
 // k_sgm_wta:    one warp per pixel: the 8 directions summed per disparity,
 //               the (sum, d) minimum by a warp reduction.
 #include "sff_internal.cuh"
@@ -34,7 +34,7 @@ namespace {
 
 constexpr int kDirs = 8;
 constexpr int kPathWarps = 4;  // warps (lines) per CTA of k_sgm_paths
-constexpr int kQueue = 8;      // pixels whose costs a path warp loads ahead
+constexpr int kRing = 32;      // pixels whose costs a path warp has in flight (shared-memory ring)
 constexpr int kWtaWarps = 8;   // warps (pixels) per CTA of k_sgm_wta
 constexpr int kCensusW = 9, kCensusH = 7;
 constexpr int kTileX = 32, kTileY = 8;
@@ -195,48 +195,126 @@ __global__ void __launch_bounds__(kPathWarps * 32) k_sgm_paths(SgmJob S) {
         }
     }
     if (line >= nlines) return;  // warp-uniform
-    const uint8_t* cost = S.cost + lane * J;
     uint8_t* out = S.paths + (size_t)dir * W * H * D + lane * J;
     // steps until the line leaves the image
     const int n = min(rx > 0 ? W - x : rx < 0 ? x + 1 : 1 << 30, ry > 0 ? H - y : ry < 0 ? y + 1 : 1 << 30);
     const ptrdiff_t step = (ptrdiff_t)ry * W + rx;  // pixel index increment along the line
     const size_t p0 = (size_t)y * W + x;
-    // the costs of the next kQueue pixels, loaded ahead and unpacked on use
-    typename RawOf<J>::T q[kQueue];
-#pragma unroll
-    for (int k = 0; k < kQueue; ++k)
-        if (k < n) q[k] = load_raw<J>(cost + (p0 + k * step) * D);
-    int prev[J];
-    int m = 0;
-    for (int t = 0; t < n; t += kQueue) {
-#pragma unroll
-        for (int k = 0; k < kQueue; ++k) {
-            if (t + k < n) {  // uniform over the warp
-                const size_t p = p0 + (ptrdiff_t)(t + k) * step;
-                int cur[J];
-                unpack<J>(q[k], cur);
-                if (t + k + kQueue < n) q[k] = load_raw<J>(cost + (p + kQueue * step) * D);
-                if (t + k > 0) {
-                    const int lo = __shfl_up_sync(kFull, prev[J - 1], 1);  // d = lane J - 1
-                    const int hi = __shfl_down_sync(kFull, prev[0], 1);    // d = lane J + J
-#pragma unroll
-                    for (int j = 0; j < J; ++j) {
-                        const int pl = j > 0 ? prev[j - 1] : (lane > 0 ? lo : kInf);
-                        const int pr = j < J - 1 ? prev[j + 1] : (lane < 31 ? hi : kInf);
-                        const int b = min(min(prev[j], min(pl, pr) + S.p1), m + S.p2);
-                        cur[j] += b - m;
+    // The costs of the next kRing pixels of the line stream into a ring in
+    // shared memory with cp.async (one commit group per pixel, so a step
+    // waits only for its own pixel's group); the copy is spread over the
+    // lanes in 4-byte pieces.
+    extern __shared__ __align__(16) uint8_t ring_all[];
+    uint8_t* ring = ring_all + (size_t)(threadIdx.x >> 5) * kRing * D;
+    const uint8_t* line_cost = S.cost;
+    auto fetch = [&](int t) {  // pixel t of the line into its ring slot
+        if (t < n) {
+            const uint8_t* src = line_cost + (p0 + (ptrdiff_t)t * step) * D;
+            uint8_t* dst = ring + (t % kRing) * D;
+            for (int b = 4 * lane; b < D; b += 128) {
+                const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + b);
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(src + b) : "memory");
+            }
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    for (int t = 0; t < kRing; ++t) fetch(t);
+    auto take = [&](int t) {  // pixel t's costs, this lane's J bytes
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(kRing - 1) : "memory");
+        __syncwarp();
+        const typename RawOf<J>::T r = load_raw<J>(ring + (t % kRing) * D + lane * J);
+        __syncwarp();  // every lane has read the slot before it is refilled
+        fetch(t + kRing);
+        return r;
+    };
+    if constexpr (J == 1) {
+        int prev = 0, m = 0;
+        for (int t = 0; t < n; ++t) {
+            {
+                {
+                    const size_t p = p0 + (ptrdiff_t)t * step;
+                    int cur[1];
+                    unpack<1>(take(t), cur);
+                    if (t > 0) {
+                        const int lo = __shfl_up_sync(kFull, prev, 1), hi = __shfl_down_sync(kFull, prev, 1);
+                        const int pl = lane > 0 ? lo : kInf, pr = lane < 31 ? hi : kInf;
+                        cur[0] += min(min(prev, min(pl, pr) + S.p1), m + S.p2) - m;
                     }
+                    store_bytes<1>(out + p * D, cur);
+                    m = __reduce_min_sync(kFull, cur[0]);
+                    prev = cur[0];
                 }
-                store_bytes<J>(out + p * D, cur);
-                int mm = cur[0];
+            }
+        }
+    } else {
+        // Two disparities per 32-bit word (16-bit halves; every value stays
+        // below 2^16 and every difference taken is >= 0, so plain 32-bit
+        // adds and subtracts act on both halves) and the recurrence on the
+        // DPX add-min instructions:
+        //   min(P, Lm + P1, Rp + P1, m + P2) = min(min(Lm + P1, m + P2),
+        //                                          min(Rp + P1, P)).
+        // Lm / Rp: the pair of each half's d - 1 / d + 1 values, from byte
+        // permutes of neighbouring pairs (the outer ones from the
+        // neighbouring lanes); beyond the disparity range 0x7fff.
+        constexpr int NP = J / 2;
+        const uint32_t p1x2 = (uint32_t)S.p1 * 0x00010001u;
+        uint32_t prev[NP];
+        uint32_t m = 0;
+        for (int t = 0; t < n; ++t) {
+            {
+                {
+                    const size_t p = p0 + (ptrdiff_t)t * step;
+                    const typename RawOf<J>::T raw = take(t);
+                    uint32_t c2[NP];  // costs as 16-bit pairs
+                    if constexpr (J == 2) {
+                        c2[0] = __byte_perm((uint32_t)raw, 0u, 0x4140);
+                    } else if constexpr (J == 4) {
+                        c2[0] = __byte_perm((uint32_t)raw, 0u, 0x4140);
+                        c2[1] = __byte_perm((uint32_t)raw, 0u, 0x4342);
+                    } else {
+                        c2[0] = __byte_perm(raw.x, 0u, 0x4140);
+                        c2[1] = __byte_perm(raw.x, 0u, 0x4342);
+                        c2[2] = __byte_perm(raw.y, 0u, 0x4140);
+                        c2[3] = __byte_perm(raw.y, 0u, 0x4342);
+                    }
+                    uint32_t cur[NP];
+                    if (t > 0) {
+                        const uint32_t lo = __shfl_up_sync(kFull, prev[NP - 1], 1);  // its high half: d = lane J - 1
+                        const uint32_t hi = __shfl_down_sync(kFull, prev[0], 1);     // its low half: d = lane J + J
+                        const uint32_t left = lane > 0 ? lo : 0x7fff0000u, right = lane < 31 ? hi : 0x00007fffu;
+                        const uint32_t mp2 = (m + (uint32_t)S.p2) * 0x00010001u, m2 = m * 0x00010001u;
 #pragma unroll
-                for (int j = 1; j < J; ++j) mm = min(mm, cur[j]);
-                m = __reduce_min_sync(kFull, mm);
+                        for (int j = 0; j < NP; ++j) {
+                            const uint32_t lm = __byte_perm(j > 0 ? prev[j - 1] : left, prev[j], 0x5432);
+                            const uint32_t rp = __byte_perm(prev[j], j < NP - 1 ? prev[j + 1] : right, 0x5432);
+                            const uint32_t b = __vminu2(__viaddmin_u16x2(lm, p1x2, mp2),
+                                                             __viaddmin_u16x2(rp, p1x2, prev[j]));
+                            cur[j] = b + c2[j] - m2;
+                        }
+                    } else {
 #pragma unroll
-                for (int j = 0; j < J; ++j) prev[j] = cur[j];
+                        for (int j = 0; j < NP; ++j) cur[j] = c2[j];
+                    }
+                    // back to bytes (every value < 256)
+                    if constexpr (J == 2) {
+                        *reinterpret_cast<uint16_t*>(out + p * D) = (uint16_t)__byte_perm(cur[0], 0u, 0x4420);
+                    } else if constexpr (J == 4) {
+                        *reinterpret_cast<uint32_t*>(out + p * D) = __byte_perm(cur[0], cur[1], 0x6420);
+                    } else {
+                        *reinterpret_cast<uint2*>(out + p * D) =
+                            make_uint2(__byte_perm(cur[0], cur[1], 0x6420), __byte_perm(cur[2], cur[3], 0x6420));
+                    }
+                    uint32_t mm = cur[0];
+#pragma unroll
+                    for (int j = 1; j < NP; ++j) mm = __vminu2(mm, cur[j]);
+                    m = __reduce_min_sync(kFull, min(mm & 0xffffu, mm >> 16));
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) prev[j] = cur[j];
+                }
             }
         }
     }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
 template <int J>
@@ -286,12 +364,17 @@ SgmLayout sgm_layout(int w, int h, int D) {
 }
 
 template <int J>
-void launch_sgm(const SgmJob& S, cudaStream_t st) {
+int launch_sgm(const SgmJob& S, cudaStream_t st) {
     const size_t np = (size_t)S.w * S.h;
     SFF_LAUNCH(k_sgm_cost<J>, dim3((unsigned)((np + kWtaWarps - 1) / kWtaWarps)), kWtaWarps * 32, 0, st, S);
     const int lines = S.w + S.h - 1;  // the diagonals have the most lines
-    SFF_LAUNCH(k_sgm_paths<J>, dim3((lines + kPathWarps - 1) / kPathWarps, 1, kDirs), kPathWarps * 32, 0, st, S);
+    const size_t ring = (size_t)kPathWarps * kRing * S.D;
+    if (ring > 48 * 1024 &&
+        cudaFuncSetAttribute(k_sgm_paths<J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ring) != cudaSuccess)
+        return SFF_ERR_CUDA;
+    SFF_LAUNCH(k_sgm_paths<J>, dim3((lines + kPathWarps - 1) / kPathWarps, 1, kDirs), kPathWarps * 32, ring, st, S);
     SFF_LAUNCH(k_sgm_wta<J>, dim3((unsigned)((np + kWtaWarps - 1) / kWtaWarps)), kWtaWarps * 32, 0, st, S);
+    return SFF_OK;
 }
 
 }  // namespace
@@ -337,11 +420,7 @@ extern "C" int sff_sgm(const uint8_t* left_dev, const uint8_t* right_dev, int32_
     cudaStream_t st = (cudaStream_t)stream;
     SFF_LAUNCH(k_sgm_census, dim3((width + kTileX - 1) / kTileX, (height + kTileY - 1) / kTileY, 2),
                dim3(kTileX, kTileY), 0, st, S);
-    switch (S.D) {
-        case 32: launch_sgm<1>(S, st); break;
-        case 64: launch_sgm<2>(S, st); break;
-        case 128: launch_sgm<4>(S, st); break;
-        default: launch_sgm<8>(S, st); break;
-    }
-    return launch_status();
+    const int rc = S.D == 32 ? launch_sgm<1>(S, st) : S.D == 64 ? launch_sgm<2>(S, st)
+                   : S.D == 128 ? launch_sgm<4>(S, st) : launch_sgm<8>(S, st);
+    return rc != SFF_OK ? rc : launch_status();
 }
