@@ -104,3 +104,58 @@ def test_tuning_space(sff):
         assert sff.make_tuning(*cand).as_tuple() == cand
     with pytest.raises(sff.SffError):
         sff.make_tuning(3, 32, 8)
+
+
+def test_extension_rows_without_gpu(sff):
+    # defaults, workspace sizes and argument checks of the paper-order,
+    # disparity-fill, interpolation and SIFT-cost entry points: all on the
+    # host, before anything reaches CUDA
+    L = sff.lib()
+    p = sff.default_params()
+    P = ctypes.byref(p)
+    fake = ctypes.c_void_p(0x10000)
+    null = ctypes.c_void_p(0)
+    ws = sff.workspace_bytes(64, 48, p)
+    # paper order
+    assert L.sff_match_views_sequential(fake, fake, fake, fake, 64, 48, 2, 1, P, fake, fake, fake, ws, null) == -1
+    assert L.sff_match_views_sequential(fake, fake, fake, fake, 64, 48, 0, 1, P, fake, fake, fake, 0, null) == -3
+    # disparity fill: defaults (Hirschmueller-style penalties), parameter limits
+    sp = sff.default_sgm_params()
+    assert (sp.max_disp, sp.p1, sp.p2) == (128, 10, 120)
+    assert sff.sgm_workspace_bytes(64, 48, sp) >= 64 * 48 * (2 * 8 + 9 * 128)
+    for bad in (dict(max_disp=96), dict(max_disp=512), dict(p1=-1), dict(p1=30, p2=20), dict(p2=194)):
+        assert sff.sgm_workspace_bytes(64, 48, sff.default_sgm_params(**bad)) == 0
+    SP = ctypes.byref(sp)
+    sws = sff.sgm_workspace_bytes(64, 48, sp)
+    assert L.sff_sgm(null, fake, 192, 64, 48, SP, fake, fake, sws, null) == -1
+    assert L.sff_sgm(fake, fake, 100, 64, 48, SP, fake, fake, sws, null) == -1      # pitch < 3 W
+    assert L.sff_sgm(fake, fake, 192, 64, 48, SP, ctypes.c_void_p(0x10001), fake, sws, null) == -1  # odd disp
+    assert L.sff_sgm(fake, fake, 192, 64, 48, SP, fake, fake, 16, null) == -3
+    assert L.sff_emit_seeds_geo(fake, fake, fake, fake, null, 64, 48, P, fake, 10, fake, fake, ws, null) == -1
+    assert L.sff_emit_seeds_geo(fake, fake, fake, fake, fake, 64, 48, P, fake, 10, fake, fake, 0, null) == -3
+    # interpolation: defaults of Sec. 5 and the principal point at the centre
+    ip = sff.default_interp_params(101, 40, 700.0, 0.5)
+    assert (ip.k_geo, ip.k_motion, ip.alpha, ip.dist_unit) == (160, 80, 2.2, 20.0)
+    assert (ip.cx, ip.cy, ip.focal, ip.baseline) == (50.0, 19.5, 700.0, 0.5)
+    IP = ctypes.byref(ip)
+    with pytest.raises(sff.SffError):
+        sff.default_interp_params(64, 48, 0.0, 0.5)
+    iws = sff.interp_workspace_bytes(64, 48, 400)
+    assert iws > 0 and sff.interp_workspace_bytes(7, 48, 400) == 0 and sff.interp_workspace_bytes(64, 48, -1) == 0
+    assert L.sff_interpolate(null, fake, 400, 64, 48, IP, fake, fake, iws, null) == -1
+    assert L.sff_interpolate(fake, fake, 400, 64, 48, IP, ctypes.c_void_p(0x10004), fake, iws, null) == -1  # field
+    assert L.sff_interpolate(fake, fake, 400, 64, 48, IP, fake, fake, 16, null) == -3
+    for bad in (dict(k_geo=0), dict(k_motion=1025), dict(alpha=-1.0), dict(dist_unit=0.0)):
+        b = sff.default_interp_params(64, 48, 700.0, 0.5, **bad)
+        assert L.sff_interpolate(fake, fake, 400, 64, 48, ctypes.byref(b), fake, fake, iws, null) == -1
+    # SIFT-PCA cost
+    assert sff.sift_workspace_bytes(64, 48) > 64 * 48 * 4 * 128 and sff.sift_workspace_bytes(64, 7) == 0
+    four = (ctypes.c_void_p * 4)(fake, fake, fake, fake)
+    some_null = (ctypes.c_void_p * 4)(fake, null, fake, fake)
+    fws = sff.sift_workspace_bytes(64, 48)
+    assert L.sff_sift_features(four, 192, 64, 48, P, some_null, fake, fws, null) == -1
+    assert L.sff_sift_features(four, 192, 64, 48, P, four, fake, 16, null) == -3
+    assert L.sff_match_views_sift(fake, fake, fake, fake, fake, fake, fake, ctypes.c_void_p(0x10004), 64, 48, 0, 1, P,
+                                  fake, fake, fake, ws, null) == -1  # phi not 16-byte aligned
+    assert L.sff_match_views_sift(fake, fake, fake, fake, fake, fake, fake, fake, 64, 48, 0, 1, P, fake, fake, fake,
+                                  0, null) == -3
