@@ -42,7 +42,8 @@
  * Pins: tests/test_oracle_interp.py (an exact plane and an exact affine 3D
  * motion reproduced at every pixel, the weighted mean of a symmetric star,
  * lattice neighbourhoods and ties, motion-seed selection, the one-seed
- * defaults).
+ * defaults, and on random seeds the fits against numpy's weighted least
+ * squares and its solve of the same normal equations).
  */
 #include <math.h>
 #include <stdint.h>

@@ -139,3 +139,57 @@ def test_synthetic_seeds_have_the_structure_of_sparse_matches():
     assert not occ[s["y"], s["x"]].any()
     exact = scenegen.sparse_seeds(gt, occ, 4, keep=0.7)
     assert np.array_equal(exact["d0"], np.rint(gt[exact["y"], exact["x"], 2]))
+
+
+def test_fits_agree_with_weighted_least_squares():
+    # random non-degenerate seeds: the ridge (1e-9 of the trace) is negligible,
+    # so every seed's plane and affine map are numpy's weighted least-squares
+    # solutions over the same neighbours with the same weights
+    rng = np.random.default_rng(7)
+    rows = []
+    for by in range(0, 36, 3):
+        for bx in range(0, 48, 3):
+            if rng.random() < 0.7:
+                x, y = bx + int(rng.integers(0, 3)), by + int(rng.integers(0, 3))
+                rows.append((x, y, int(rng.integers(-9, 10)), int(rng.integers(-5, 6)), int(rng.integers(5, 60)),
+                             int(rng.integers(5, 60))))
+    s = _seeds(rows)
+    f, B = 400.0, 0.5
+    p = oracle.interp_params(48, 36, f, B, k_geo=25, k_motion=15)
+    plane, affine, motion = oracle.seed_models(s, p)
+    cx, cy = p.cx, p.cy
+
+    def tri(x, y, d):
+        Z = f * B / d
+        return np.array([(x - cx) * Z / f, (y - cy) * Z / f, Z])
+
+    for i in rng.choice(len(s), 25, replace=False):
+        sx, sy = int(s["x"][i]), int(s["y"][i])
+        idx, d2 = oracle.nearest_seeds(s, sx, sy, 25)
+        w = np.exp(-2.2 * np.sqrt(d2.astype(np.float64)) / 20.0)
+        A = np.stack([s["x"][idx] - sx, s["y"][idx] - sy, np.ones(len(idx))], 1).astype(np.float64)
+        sol = np.linalg.lstsq(A * np.sqrt(w)[:, None], s["d0"][idx] * np.sqrt(w), rcond=None)[0]
+        assert np.allclose(plane[i], sol, rtol=1e-7, atol=1e-7)
+        idx, d2 = oracle.nearest_seeds(s, sx, sy, 15, motion_only=True)
+        w = np.exp(-2.2 * np.sqrt(d2.astype(np.float64)) / 20.0)
+        X0 = np.array([tri(s["x"][j], s["y"][j], s["d0"][j]) for j in idx])
+        X1 = np.array([tri(s["x"][j] + s["u"][j], s["y"][j] + s["v"][j], s["d1"][j]) for j in idx])
+        c = (w[:, None] * X0).sum(0) / w.sum()
+        D = np.concatenate([X0 - c, np.ones((len(idx), 1))], 1)
+        # normal equations with the ridge of the reading (1e-9 trace / 4 on the
+        # linear part, towards A = I), solved by numpy: with depths of 3-40 m
+        # the ridge moves A by ~1e-5 relative, so it is part of the check
+        N = (D * w[:, None]).T @ D
+        R = (D * w[:, None]).T @ X1  # [4, 3]
+        lam = 1e-9 * np.trace(N) / 4
+        for a in range(3):
+            N[a, a] += lam
+            R[a, a] += lam
+        At = np.linalg.solve(N, R)  # [4, 3]: rows of A^T, then t
+        assert motion[i] == len(idx)
+        assert np.allclose(affine[i][12:], c, rtol=1e-10, atol=1e-10)
+        assert np.allclose(affine[i][:12].reshape(3, 4), At.T, rtol=1e-8, atol=1e-8)
+        # and without the ridge the weighted least-squares solution is within
+        # the ridge's reach
+        Aw = np.linalg.lstsq(D * np.sqrt(w)[:, None], X1 * np.sqrt(w)[:, None], rcond=None)[0]
+        assert np.allclose(affine[i][:12].reshape(3, 4), Aw.T, rtol=1e-3, atol=1e-3)
