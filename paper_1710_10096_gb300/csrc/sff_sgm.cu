@@ -151,20 +151,35 @@ __device__ __forceinline__ void load_bytes(const uint8_t* q, int (&v)[J]) {
     }
 }
 
-// C(p, d) for every pixel: one warp per pixel, J disparities per lane, the
+// C(p, d) for every pixel.  One CTA per segment of kCostSeg pixels of a row:
+// the right image's census words the segment needs (x - D + 1 .. the
+// segment's end, positions clamped at 0) are staged in shared memory once;
+// each warp then takes pixels of the segment, J disparities per lane, the
 // J costs of a lane packed into J bytes of [y][x][d].
+constexpr int kCostSeg = 64;
+constexpr int kCostThreads = 256;
+
 template <int J>
-__global__ void __launch_bounds__(kWtaWarps * 32) k_sgm_cost(SgmJob S) {
+__global__ void __launch_bounds__(kCostThreads) k_sgm_cost(SgmJob S) {
+    constexpr int D = 32 * J;
+    __shared__ uint64_t right[kCostSeg + D - 1];
+    const int y = blockIdx.y, x0 = blockIdx.x * kCostSeg;
+    const uint64_t* rrow = S.census[1] + (size_t)y * S.w;
+    const int base = x0 - (D - 1);  // census position of right[0]
+    for (int i = threadIdx.x; i < kCostSeg + D - 1; i += kCostThreads)
+        right[i] = rrow[min(max(base + i, 0), S.w - 1)];
+    __syncthreads();
     const int lane = threadIdx.x & 31;
-    const size_t p = (size_t)blockIdx.x * kWtaWarps + (threadIdx.x >> 5);
-    if (p >= (size_t)S.w * S.h) return;  // warp-uniform
-    const int x = (int)(p % S.w);
-    const uint64_t c = S.census[0][p];
-    const uint64_t* row = S.census[1] + (p - x);
-    int v[J];
+    for (int k = threadIdx.x >> 5; k < kCostSeg; k += kCostThreads / 32) {
+        const int x = x0 + k;
+        if (x >= S.w) break;  // uniform over the warp
+        const size_t p = (size_t)y * S.w + x;
+        const uint64_t c = S.census[0][p];
+        int v[J];
 #pragma unroll
-    for (int j = 0; j < J; ++j) v[j] = __popcll(c ^ row[max(x - (lane * J + j), 0)]);
-    store_bytes<J>(S.cost + p * S.D + lane * J, v);
+        for (int j = 0; j < J; ++j) v[j] = __popcll(c ^ right[max(x - (lane * J + j), 0) - base]);
+        store_bytes<J>(S.cost + p * D + lane * J, v);
+    }
 }
 
 template <int J>
@@ -366,7 +381,7 @@ SgmLayout sgm_layout(int w, int h, int D) {
 template <int J>
 int launch_sgm(const SgmJob& S, cudaStream_t st) {
     const size_t np = (size_t)S.w * S.h;
-    SFF_LAUNCH(k_sgm_cost<J>, dim3((unsigned)((np + kWtaWarps - 1) / kWtaWarps)), kWtaWarps * 32, 0, st, S);
+    SFF_LAUNCH(k_sgm_cost<J>, dim3((S.w + kCostSeg - 1) / kCostSeg, S.h), kCostThreads, 0, st, S);
     const int lines = S.w + S.h - 1;  // the diagonals have the most lines
     const size_t ring = (size_t)kPathWarps * kRing * S.D;
     if (ring > 48 * 1024 &&
