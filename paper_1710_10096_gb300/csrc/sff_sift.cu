@@ -374,13 +374,10 @@ extern "C" int sff_sift_features(const uint8_t* const* rgb_dev4, int32_t pitch_b
     J.proj = reinterpret_cast<float*>(ws + L.proj);
     cudaStream_t st = (cudaStream_t)stream;
     const dim3 g((width + 127) / 128, height, 4);
-    static bool smem_ready = false;
-    if (!smem_ready) {
-        if (cudaFuncSetAttribute(k_sift_axes, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kDesc * kDesc * (int)sizeof(double)) != cudaSuccess)
-            return SFF_ERR_CUDA;
-        smem_ready = true;
-    }
+    // the attribute is per device: set it on the current one at every call
+    if (cudaFuncSetAttribute(k_sift_axes, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kDesc * kDesc * (int)sizeof(double)) != cudaSuccess)
+        return SFF_ERR_CUDA;
     for (int s = 0; s < params->num_scales; ++s) {
         J.s = s;
         J.n = 1 << s;
