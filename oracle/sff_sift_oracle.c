@@ -32,7 +32,10 @@
  *     the four images from exact integer sums, in double precision; its top
  *     three eigenvectors by 200 power iterations from the all-ones vector,
  *     each deflated by the previous ones, normalised, sign such that the
- *     largest component is positive; the same axes at every scale;
+ *     largest component is positive; every dot product of the iteration
+ *     (matrix rows, deflation, norm) as four partial sums over the indices
+ *     mod 4, each in index order by fused multiply-adds, combined as
+ *     (s0 + s1) + (s2 + s3); the same axes at every scale;
  *   - phi_c = sum_k fl(a_ck) fl(q_k) (sequential, single precision) minus
  *     fl(sum_k a_ck mu_k) (double precision); stored as 4 floats per pixel;
  *   - cost: the window's 49 pixels p + n (i, j), i, j in -3..3, row-major,
@@ -122,6 +125,16 @@ void sfft_descriptors(const uint8_t* rgb_s, int w, int h, int s, uint8_t* desc) 
     free(bin);
 }
 
+/* Dot product of two 128-vectors as in the power iteration: four partial
+ * sums over the indices k = 0, 1, 2, 3 mod 4, each accumulated in index
+ * order by fused multiply-adds (one rounding each), combined as
+ * (s0 + s1) + (s2 + s3). */
+static double dot128(const double* a, const double* b) {
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int k = 0; k < 128; k++) s[k & 3] = fma(a[k], b[k], s[k & 3]);
+    return (s[0] + s[1]) + (s[2] + s[3]);
+}
+
 /* Principal axes of n_desc descriptors [n_desc][128]: mean[128] and
  * axes[3][128] (double precision). */
 void sfft_pca(const uint8_t* desc, int64_t n_desc, double* mean, double* axes) {
@@ -159,19 +172,12 @@ void sfft_pca(const uint8_t* desc, int64_t n_desc, double* mean, double* axes) {
         double v[128], wv[128];
         for (int i = 0; i < 128; i++) v[i] = 1.0;
         for (int it = 0; it < 200; it++) {
-            for (int i = 0; i < 128; i++) {
-                double t = 0.0;
-                for (int j = 0; j < 128; j++) t = t + C[i * 128 + j] * v[j];
-                wv[i] = t;
-            }
+            for (int i = 0; i < 128; i++) wv[i] = dot128(C + i * 128, v);
             for (int e = 0; e < c; e++) {
-                double d = 0.0;
-                for (int i = 0; i < 128; i++) d = d + axes[e * 128 + i] * wv[i];
+                const double d = dot128(axes + e * 128, wv);
                 for (int i = 0; i < 128; i++) wv[i] = wv[i] - d * axes[e * 128 + i];
             }
-            double ss = 0.0;
-            for (int i = 0; i < 128; i++) ss = ss + wv[i] * wv[i];
-            const double nr = sqrt(ss);
+            const double nr = sqrt(dot128(wv, wv));
             for (int i = 0; i < 128; i++) v[i] = nr > 0.0 ? wv[i] / nr : 0.0;
         }
         int big = 0;

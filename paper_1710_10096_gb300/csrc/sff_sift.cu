@@ -18,11 +18,14 @@
 //   - axes: exact integer sums over the full-resolution descriptors of the
 //     four images, covariance in double precision, 200 power iterations per
 //     axis from the all-ones vector with deflation, sign of the largest
-//     component positive;
+//     component positive; each dot product of an iteration as four partial
+//     sums over the indices mod 4, each by fused multiply-adds in index
+//     order, combined as (s0 + s1) + (s2 + s3);
 //   - phi_c = sum_k fl(a_ck) q_k in single precision, minus fl(a_c . mean).
 // Every floating-point operation is written out with the _rn intrinsics, in
-// the order of the definition: no fused multiply-adds, no reassociation, so
-// the results are reproducible bit for bit on any IEEE machine.
+// the order of the definition: fused multiply-adds only where the definition
+// names them (the power iteration's dot products), no reassociation, so the
+// results are reproducible bit for bit on any IEEE machine.
 //
 // k_sift_grey:    smoothed grey image of one scale (4 images, blockIdx.z).
 // k_sift_grad:    magnitude and orientation sector per pixel.
@@ -234,43 +237,59 @@ __global__ void __launch_bounds__(kCovThreads) k_sift_cov(SiftJob J, size_t coun
     flush();
 }
 
-// One CTA of 128 threads: thread i owns row i.  Sequential sums (norms,
-// projections of the deflation, the sign) are taken by thread 0 in index
-// order, as the definition reads.
+// Dot product of two 128-vectors in shared memory as in the power
+// iteration: threads 0-3 each accumulate the indices of one residue mod 4 in
+// index order by fused multiply-adds; thread 0 combines (s0 + s1) + (s2 + s3)
+// into *out.  Called by the whole CTA (two barriers).
+__device__ __forceinline__ void dot128_cta(const double* a, const double* b, double* part, double* out) {
+    const int i = threadIdx.x;
+    if (i < 4) {
+        double t = 0.0;
+#pragma unroll 8
+        for (int k = i; k < kDesc; k += 4) t = __fma_rn(a[k], b[k], t);
+        part[i] = t;
+    }
+    __syncthreads();
+    if (i == 0) *out = __dadd_rn(__dadd_rn(part[0], part[1]), __dadd_rn(part[2], part[3]));
+    __syncthreads();
+}
+
+// One CTA of 128 threads: thread i owns row i of the covariance, kept
+// column-major in shared memory (Ct[j][i] = C(i, j)) so that a warp reads 32
+// consecutive doubles at every step of its rows.  Every dot product of the
+// iteration is four partial sums over the indices mod 4 in index order by
+// fused multiply-adds, combined as (s0 + s1) + (s2 + s3).
 __global__ void __launch_bounds__(kDesc) k_sift_axes(SiftJob J, double count) {
-    extern __shared__ double C[];  // [128][128]
-    __shared__ double mean[kDesc], v[kDesc], wv[kDesc], bc;
+    extern __shared__ double Ct[];  // [128][128], column-major covariance
+    __shared__ double mean[kDesc], v[kDesc], wv[kDesc], ax[3][kDesc], part[4], bc;
     const int i = threadIdx.x;
     mean[i] = __ddiv_rn((double)J.s1[i], count);
     __syncthreads();
     for (int j = 0; j < kDesc; ++j)
-        C[i * kDesc + j] = __dsub_rn(__ddiv_rn((double)J.s2[i * kDesc + j], count), __dmul_rn(mean[i], mean[j]));
+        Ct[j * kDesc + i] = __dsub_rn(__ddiv_rn((double)J.s2[i * kDesc + j], count), __dmul_rn(mean[i], mean[j]));
     __syncthreads();
     for (int c = 0; c < 3; ++c) {
         v[i] = 1.0;
         __syncthreads();
         for (int it = 0; it < kPowerIters; ++it) {
-            double t = 0.0;
-            for (int j = 0; j < kDesc; ++j) t = __dadd_rn(t, __dmul_rn(C[i * kDesc + j], v[j]));
-            wv[i] = t;
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+#pragma unroll 4
+            for (int k = 0; k < kDesc; k += 4) {
+                s0 = __fma_rn(Ct[(k + 0) * kDesc + i], v[k + 0], s0);
+                s1 = __fma_rn(Ct[(k + 1) * kDesc + i], v[k + 1], s1);
+                s2 = __fma_rn(Ct[(k + 2) * kDesc + i], v[k + 2], s2);
+                s3 = __fma_rn(Ct[(k + 3) * kDesc + i], v[k + 3], s3);
+            }
+            wv[i] = __dadd_rn(__dadd_rn(s0, s1), __dadd_rn(s2, s3));
             __syncthreads();
             for (int e = 0; e < c; ++e) {
-                if (i == 0) {
-                    double d = 0.0;
-                    for (int k = 0; k < kDesc; ++k) d = __dadd_rn(d, __dmul_rn(J.axes[e * kDesc + k], wv[k]));
-                    bc = d;
-                }
-                __syncthreads();
-                wv[i] = __dsub_rn(wv[i], __dmul_rn(bc, J.axes[e * kDesc + i]));
+                dot128_cta(ax[e], wv, part, &bc);
+                wv[i] = __dsub_rn(wv[i], __dmul_rn(bc, ax[e][i]));
                 __syncthreads();
             }
-            if (i == 0) {
-                double ss = 0.0;
-                for (int k = 0; k < kDesc; ++k) ss = __dadd_rn(ss, __dmul_rn(wv[k], wv[k]));
-                bc = __dsqrt_rn(ss);
-            }
-            __syncthreads();
-            v[i] = bc > 0.0 ? __ddiv_rn(wv[i], bc) : 0.0;
+            dot128_cta(wv, wv, part, &bc);
+            const double nr = __dsqrt_rn(bc);
+            v[i] = nr > 0.0 ? __ddiv_rn(wv[i], nr) : 0.0;
             __syncthreads();
         }
         if (i == 0) {
@@ -280,14 +299,16 @@ __global__ void __launch_bounds__(kDesc) k_sift_axes(SiftJob J, double count) {
             bc = v[big] < 0.0 ? -1.0 : 1.0;
         }
         __syncthreads();
-        J.axes[c * kDesc + i] = __dmul_rn(bc, v[i]);
+        ax[c][i] = __dmul_rn(bc, v[i]);
+        J.axes[c * kDesc + i] = ax[c][i];
         __syncthreads();
     }
-    // single-precision projection weights and biases fl(a_c . mean)
-    for (int c = 0; c < 3; ++c) J.proj[c * kDesc + i] = (float)J.axes[c * kDesc + i];
+    // single-precision projection weights and biases fl(a_c . mean), the
+    // bias a sequential sum
+    for (int c = 0; c < 3; ++c) J.proj[c * kDesc + i] = (float)ax[c][i];
     if (i < 3) {
         double b = 0.0;
-        for (int k = 0; k < kDesc; ++k) b = __dadd_rn(b, __dmul_rn(J.axes[i * kDesc + k], mean[k]));
+        for (int k = 0; k < kDesc; ++k) b = __dadd_rn(b, __dmul_rn(ax[i][k], mean[k]));
         J.proj[3 * kDesc + i] = (float)b;
     }
 }
