@@ -352,7 +352,7 @@ def field_quality(field, q):
 
 
 def bench_interpolation(sff, torch, dev, m, q, params, steps, warmup, cpu: bool):
-    """Dense interpolation (Sec. 3.3) of the quad's seeds on the GPU: the
+    """Dense interpolation (Sec. 3.2) of the quad's seeds on the GPU: the
     interpolation alone and the whole method (matching stage + interpolation)
     as one CUDA graph, both timed with CUDA events after an L2 flush; the
     per-kernel profile; the FP64 roofline of the model fits; the quality of

@@ -21,7 +21,7 @@
  *     sff_sift_features, sff_match_views_sift
  * the disparity fill (Sec. 3.1, last paragraph):
  *     sff_sgm, sff_emit_seeds_geo   SGM disparity map, disparity-only seeds
- * and the dense interpolation of the seeds (Sec. 3.3):
+ * and the dense interpolation of the seeds (Sec. 3.2):
  *     sff_interpolate         per-seed plane and affine 3D motion, per-pixel evaluation
  *
  * Conventions for every call:
@@ -358,7 +358,7 @@ int sff_match_views_sift(const uint8_t* pyr_ref_dev, const uint8_t* pyr_temporal
                          int16_t* field_dev, int32_t* cost_dev, void* workspace, size_t workspace_bytes,
                          void* stream);
 
-/* Dense interpolation of the seeds (Sec. 3.3, "Interpolation Models" and
+/* Dense interpolation of the seeds (Sec. 3.2, "Interpolation Models" and
  * "Edge-Aware Neighborhood"), with Euclidean pixel distances in place of the
  * geodesic ones (the edge map comes from a trained boundary detector, which
  * is not part of this library).

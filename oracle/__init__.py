@@ -254,7 +254,7 @@ def run_quad(L0, R0, L1, R1, seed: int, params: Params = None):
 
 
 # ---------------------------------------------------------------------------
-# Dense interpolation of the seeds (Sec. 3.3), sff_interp_oracle.c
+# Dense interpolation of the seeds (Sec. 3.2), sff_interp_oracle.c
 
 
 class InterpParams(ctypes.Structure):

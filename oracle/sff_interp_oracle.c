@@ -1,6 +1,6 @@
 /*
  * Plain CPU oracle of SceneFlowFields' dense interpolation of the seeds
- * (Schuster et al., WACV 2018, Sec. 3.3 "Interpolation Models" and
+ * (Schuster et al., WACV 2018, Sec. 3.2 "Interpolation Models" and
  * "Edge-Aware Neighborhood"), with a Euclidean neighbourhood in place of
  * the geodesic one (the trained boundary detector is not available).
  *

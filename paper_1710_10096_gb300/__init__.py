@@ -72,7 +72,7 @@ MAX_BATCH = 32
 
 
 class InterpParams(ctypes.Structure):
-    """sff_interp_params: neighbourhood sizes, weight kernel and camera (Sec. 3.3)."""
+    """sff_interp_params: neighbourhood sizes, weight kernel and camera (Sec. 3.2)."""
     _fields_ = [("k_geo", ctypes.c_int32), ("k_motion", ctypes.c_int32), ("alpha", ctypes.c_double),
                 ("dist_unit", ctypes.c_double), ("focal", ctypes.c_double), ("baseline", ctypes.c_double),
                 ("cx", ctypes.c_double), ("cy", ctypes.c_double)]

@@ -1,4 +1,4 @@
-// Dense interpolation of the seeds (Sec. 3.3, "Interpolation Models" and
+// Dense interpolation of the seeds (Sec. 3.2, "Interpolation Models" and
 // "Edge-Aware Neighborhood"), with Euclidean distances in place of the
 // geodesic ones (the trained boundary detector is not part of this stage).
 //

@@ -1,4 +1,4 @@
-"""Dense interpolation of the seeds (Sec. 3.3) on the GPU vs the CPU oracle,
+"""Dense interpolation of the seeds (Sec. 3.2) on the GPU vs the CPU oracle,
 through the C ABI.
 
 Both sides fit and evaluate in double precision with the same neighbour

@@ -1,4 +1,4 @@
-"""Pins of the interpolation oracle (Sec. 3.3): closed forms it must reproduce,
+"""Pins of the interpolation oracle (Sec. 3.2): closed forms it must reproduce,
 independent of its own formulas."""
 import math
 
