@@ -29,8 +29,8 @@
 //
 // k_sift_grey:    smoothed grey image of one scale (4 images, blockIdx.z).
 // k_sift_grad:    magnitude and orientation sector per pixel.
-// k_sift_desc:    the quantised descriptor, three passes over the 16 cells
-//                 (norm, clipped norm, output) instead of 128 registers.
+// k_sift_desc:    the quantised descriptor: the 128 sums once into shared
+//                 memory, then the norm, the clipped norm and the output.
 // k_sift_cov:     64 descriptors per step in shared memory, transposed;
 //                 every thread accumulates 64 of the 128 x 128 products with
 //                 dp4a, flushed into 64-bit sums.
@@ -45,6 +45,8 @@ namespace sff {
 namespace {
 
 constexpr int kDesc = 128;
+constexpr int kDescThreads = 128;                                         // threads of k_sift_desc
+constexpr size_t kDescSmem = (size_t)kDesc * kDescThreads * sizeof(float);  // its 128 sums per thread
 constexpr int kCovPix = 64;       // descriptors per step of k_sift_cov
 constexpr int kCovThreads = 256;
 constexpr int kCovFlush = 16384;  // descriptors between flushes of the 32-bit partial sums
@@ -139,8 +141,14 @@ __device__ __forceinline__ void cell_hist(const SiftJob& J, const float* mag, co
         }
 }
 
-__global__ void __launch_bounds__(128) k_sift_desc(SiftJob J) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, v = blockIdx.z;
+// The descriptor of one pixel per thread.  The 128 sums are taken once and
+// kept in shared memory as [bin][thread] (a warp touches 32 consecutive
+// words); the second pass stores each clipped value back in its slot for the
+// third.  Every value is the same arithmetic as a recomputation would give.
+__global__ void __launch_bounds__(kDescThreads) k_sift_desc(SiftJob J) {
+    extern __shared__ float hs[];  // [kDesc][kDescThreads]
+    const int t = threadIdx.x;
+    const int x = blockIdx.x * blockDim.x + t, y = blockIdx.y, v = blockIdx.z;
     if (x >= J.w) return;
     const size_t plane = (size_t)v * J.h * J.w;
     const float* mag = J.mag + plane;
@@ -150,35 +158,29 @@ __global__ void __launch_bounds__(128) k_sift_desc(SiftJob J) {
     for (int c = 0; c < 16; ++c) {
         cell_hist(J, mag, bin, x, y, c & 3, c >> 2, h);
 #pragma unroll
-        for (int b = 0; b < 8; ++b) ss = __fadd_rn(ss, __fmul_rn(h[b], h[b]));
+        for (int b = 0; b < 8; ++b) {
+            ss = __fadd_rn(ss, __fmul_rn(h[b], h[b]));
+            hs[(c * 8 + b) * kDescThreads + t] = h[b];
+        }
     }
     const float nr = __fsqrt_rn(ss);
     float ss2 = 0.0f;
-    for (int c = 0; c < 16; ++c) {
-        cell_hist(J, mag, bin, x, y, c & 3, c >> 2, h);
-#pragma unroll
-        for (int b = 0; b < 8; ++b) {
-            float u = h[b];
-            if (nr > 0.0f) {
-                u = __fdiv_rn(u, nr);
-                if (u > 0.2f) u = 0.2f;
-            }
-            ss2 = __fadd_rn(ss2, __fmul_rn(u, u));
+    for (int k = 0; k < kDesc; ++k) {
+        float u = hs[k * kDescThreads + t];
+        if (nr > 0.0f) {
+            u = __fdiv_rn(u, nr);
+            if (u > 0.2f) u = 0.2f;
         }
+        hs[k * kDescThreads + t] = u;
+        ss2 = __fadd_rn(ss2, __fmul_rn(u, u));
     }
     const float nr2 = __fsqrt_rn(ss2);
     uint8_t* out = J.desc + (plane + (size_t)y * J.w + x) * kDesc;
     for (int c = 0; c < 16; ++c) {
-        cell_hist(J, mag, bin, x, y, c & 3, c >> 2, h);
         uint32_t word[2] = {0u, 0u};
 #pragma unroll
         for (int b = 0; b < 8; ++b) {
-            float u = h[b];
-            if (nr > 0.0f) {
-                u = __fdiv_rn(u, nr);
-                if (u > 0.2f) u = 0.2f;
-            }
-            u = nr2 > 0.0f ? __fdiv_rn(u, nr2) : 0.0f;
+            const float u = nr2 > 0.0f ? __fdiv_rn(hs[(c * 8 + b) * kDescThreads + t], nr2) : 0.0f;
             const int q = (int)__fadd_rn(__fmul_rn(u, 512.0f), 0.5f);
             word[b >> 2] |= (uint32_t)min(q, 255) << (8 * (b & 3));
         }
@@ -395,16 +397,18 @@ extern "C" int sff_sift_features(const uint8_t* const* rgb_dev4, int32_t pitch_b
     J.proj = reinterpret_cast<float*>(ws + L.proj);
     cudaStream_t st = (cudaStream_t)stream;
     const dim3 g((width + 127) / 128, height, 4);
-    // the attribute is per device: set it on the current one at every call
+    const dim3 gd((width + kDescThreads - 1) / kDescThreads, height, 4);
+    // the attributes are per device: set them on the current one at every call
     if (cudaFuncSetAttribute(k_sift_axes, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kDesc * kDesc * (int)sizeof(double)) != cudaSuccess)
+                             kDesc * kDesc * (int)sizeof(double)) != cudaSuccess ||
+        cudaFuncSetAttribute(k_sift_desc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDescSmem) != cudaSuccess)
         return SFF_ERR_CUDA;
     for (int s = 0; s < params->num_scales; ++s) {
         J.s = s;
         J.n = 1 << s;
         SFF_LAUNCH(k_sift_grey, g, 128, 0, st, J);
         SFF_LAUNCH(k_sift_grad, g, 128, 0, st, J);
-        SFF_LAUNCH(k_sift_desc, g, 128, 0, st, J);
+        SFF_LAUNCH(k_sift_desc, gd, kDescThreads, kDescSmem, st, J);
         if (s == 0) {  // the principal axes of the full-resolution descriptors
             if (cudaMemsetAsync(J.s1, 0, L.axes - L.s1, st) != cudaSuccess) return SFF_ERR_CUDA;
             const size_t count = 4 * (size_t)width * height;

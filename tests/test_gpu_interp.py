@@ -98,6 +98,33 @@ def test_lattice_ties(env):
         np.testing.assert_allclose(got, want, rtol=RTOL, atol=ATOL)
 
 
+def test_more_than_32_seeds_tied_at_the_kth_distance(env):
+    # 48 seeds on one lattice circle (dx^2 + dy^2 = 5525) around a centre
+    # seed, in a shuffled order and with random values: the centre's k-th
+    # neighbour is a 48-way tie, more than a warp ranks in registers, so the
+    # index threshold comes from the bisection over seed indices; a wrong
+    # choice of tied seeds changes the centre's fits and the field around it
+    r = 74
+    circle = [(dx, dy) for dx in range(-r, r + 1) for dy in range(-r, r + 1) if dx * dx + dy * dy == 5525]
+    assert len(circle) == 48
+    w, h, cx, cy = 170, 160, 85, 80
+    rng = np.random.default_rng(48)
+    s = np.zeros(len(circle) + 1, scenegen.SEED_RECORD)
+    s["x"] = [cx + dx for dx, _ in circle] + [cx]
+    s["y"] = [cy + dy for _, dy in circle] + [cy]
+    s["d0"] = rng.integers(20, 60, len(s))
+    s["d1"] = s["d0"] + rng.integers(-3, 4, len(s))
+    s["u"] = rng.integers(-10, 11, len(s))
+    s["v"] = rng.integers(-5, 6, len(s))
+    s["d1"][rng.choice(len(circle), 8, replace=False)] = 0  # 40 tied motion seeds
+    s = s[rng.permutation(len(s))]
+    for kg, km in ((10, 5), (40, 30), (48, 40)):
+        got, status = _gpu_interp(env, s, w, h, 500.0, 0.3, k_geo=kg, k_motion=km)
+        want = _oracle_interp(env[2], s, w, h, 500.0, 0.3, k_geo=kg, k_motion=km)
+        assert status == 0
+        np.testing.assert_allclose(got, want, rtol=RTOL, atol=ATOL)
+
+
 def test_end_to_end_after_the_matching_stage(env):
     # the seeds of the whole matching stage, each side on its own: the GPU
     # interpolates the GPU's seeds, the oracle the oracle's

@@ -78,6 +78,32 @@ def test_neighbourhood_on_a_lattice_and_ties():
     assert [(rows[i][0], rows[i][1]) for i in idx3] == [(6, 6), (6, 3), (3, 6)]
 
 
+def _circle_offsets(r2):
+    """The lattice points (dx, dy) with dx^2 + dy^2 = r2."""
+    r = math.isqrt(r2)
+    return [(dx, dy) for dx in range(-r, r + 1) for dy in range(-r, r + 1) if dx * dx + dy * dy == r2]
+
+
+def test_more_than_32_seeds_tied_at_the_kth_distance():
+    # 5525 = 5^2 * 13 * 17 is a sum of two squares in 48 ways (4 (3 * 2 * 2)
+    # lattice points), so a seed at the centre of that circle sees 48 seeds
+    # tied at its k-th distance; listed in a shuffled order, the neighbourhood
+    # is the centre and the k - 1 tied seeds of lowest index, by brute force
+    circle = _circle_offsets(5525)
+    assert len(circle) == 48
+    rng = np.random.default_rng(5525)
+    rows = [(85 + dx, 80 + dy, 0, 0, 20, 20) for dx, dy in circle] + [(85, 80, 0, 0, 20, 20)]
+    rows = [rows[i] for i in rng.permutation(len(rows))]
+    s = _seeds(rows)
+    d2 = (s["x"].astype(np.int64) - 85) ** 2 + (s["y"].astype(np.int64) - 80) ** 2
+    brute = np.lexsort((np.arange(len(s)), d2))
+    for k in (1, 2, 10, 33, 48, 49):
+        idx, dk = oracle.nearest_seeds(s, 85, 80, k)
+        assert list(idx) == list(brute[:k])
+        assert list(dk) == list(d2[brute[:k]])
+        assert sorted(idx[1:]) == list(idx[1:])  # the tied seeds in index order
+
+
 def test_motion_neighbourhood_skips_seeds_that_cannot_be_triangulated():
     s = _seeds([(5, 5, 0, 0, 4, 4), (6, 5, 0, 0, 0, 4), (7, 5, 0, 0, 4, 0), (9, 5, 0, 0, 3, 3)])
     idx, _ = oracle.nearest_seeds(s, 5, 5, 4, motion_only=True)
