@@ -121,30 +121,11 @@ __global__ void k_sift_grad(SiftJob J) {
     J.bin[o] = (uint8_t)sector_of(dx, dy);
 }
 
-// The 8 bins of cell (cx, cy) of pixel (x, y): its 3 x 3 samples in
-// row-major order; adding +0 to the other bins leaves them unchanged.
-__device__ __forceinline__ void cell_hist(const SiftJob& J, const float* mag, const uint8_t* bin, int x, int y,
-                                          int cx, int cy, float (&h)[8]) {
-#pragma unroll
-    for (int b = 0; b < 8; ++b) h[b] = 0.0f;
-#pragma unroll
-    for (int sj = 0; sj < 3; ++sj)
-#pragma unroll
-        for (int si = 0; si < 3; ++si) {
-            const int qx = clampi(x + (cx * 3 + si - 6) * J.n, 0, J.w - 1);
-            const int qy = clampi(y + (cy * 3 + sj - 6) * J.n, 0, J.h - 1);
-            const size_t q = (size_t)qy * J.w + qx;
-            const float m = mag[q];
-            const int k = bin[q];
-#pragma unroll
-            for (int b = 0; b < 8; ++b) h[b] = __fadd_rn(h[b], k == b ? m : 0.0f);
-        }
-}
-
-// The descriptor of one pixel per thread.  The 128 sums are taken once and
-// kept in shared memory as [bin][thread] (a warp touches 32 consecutive
-// words); the second pass stores each clipped value back in its slot for the
-// third.  Every value is the same arithmetic as a recomputation would give.
+// The descriptor of one pixel per thread.  The 128 sums are accumulated in
+// shared memory as [bin][thread]: each sample adds its magnitude to its own
+// bin only, in the samples' row-major order within each cell (a thread owns
+// one column, so a warp's accesses fall in 32 distinct banks whatever the
+// bins).  The second pass stores each clipped value back for the third.
 __global__ void __launch_bounds__(kDescThreads) k_sift_desc(SiftJob J) {
     extern __shared__ float hs[];  // [kDesc][kDescThreads]
     const int t = threadIdx.x;
@@ -153,15 +134,25 @@ __global__ void __launch_bounds__(kDescThreads) k_sift_desc(SiftJob J) {
     const size_t plane = (size_t)v * J.h * J.w;
     const float* mag = J.mag + plane;
     const uint8_t* bin = J.bin + plane;
-    float h[8];
-    float ss = 0.0f;
-    for (int c = 0; c < 16; ++c) {
-        cell_hist(J, mag, bin, x, y, c & 3, c >> 2, h);
+    for (int k = 0; k < kDesc; ++k) hs[k * kDescThreads + t] = 0.0f;
+    for (int cy = 0; cy < 4; ++cy)
+        for (int sj = 0; sj < 3; ++sj) {
+            const int qy = clampi(y + (cy * 3 + sj - 6) * J.n, 0, J.h - 1);
+            const float* mrow = mag + (size_t)qy * J.w;
+            const uint8_t* brow = bin + (size_t)qy * J.w;
 #pragma unroll
-        for (int b = 0; b < 8; ++b) {
-            ss = __fadd_rn(ss, __fmul_rn(h[b], h[b]));
-            hs[(c * 8 + b) * kDescThreads + t] = h[b];
+            for (int cx = 0; cx < 4; ++cx)
+#pragma unroll
+                for (int si = 0; si < 3; ++si) {
+                    const int qx = clampi(x + (cx * 3 + si - 6) * J.n, 0, J.w - 1);
+                    float* slot = hs + ((cy * 4 + cx) * 8 + brow[qx]) * kDescThreads + t;
+                    *slot = __fadd_rn(*slot, mrow[qx]);
+                }
         }
+    float ss = 0.0f;
+    for (int k = 0; k < kDesc; ++k) {
+        const float h = hs[k * kDescThreads + t];
+        ss = __fadd_rn(ss, __fmul_rn(h, h));
     }
     const float nr = __fsqrt_rn(ss);
     float ss2 = 0.0f;
