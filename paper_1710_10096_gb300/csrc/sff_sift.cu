@@ -29,8 +29,8 @@
 //
 // k_sift_grey:    smoothed grey image of one scale (4 images, blockIdx.z).
 // k_sift_grad:    magnitude and orientation sector per pixel.
-// k_sift_desc:    the quantised descriptor: the 128 sums once into shared
-//                 memory, then the norm, the clipped norm and the output.
+// k_sift_desc:    the quantised descriptor, four threads per pixel with 32
+//                 sums each in registers; the norms handed along in bin order.
 // k_sift_cov:     64 descriptors per step in shared memory, transposed;
 //                 every thread accumulates 64 of the 128 x 128 products with
 //                 dp4a, flushed into 64-bit sums.
@@ -45,8 +45,7 @@ namespace sff {
 namespace {
 
 constexpr int kDesc = 128;
-constexpr int kDescThreads = 128;                                         // threads of k_sift_desc
-constexpr size_t kDescSmem = (size_t)kDesc * kDescThreads * sizeof(float);  // its 128 sums per thread
+constexpr int kDescThreads = 128;  // threads of k_sift_desc: 32 pixels, four threads each
 constexpr int kCovPix = 64;       // descriptors per step of k_sift_cov
 constexpr int kCovThreads = 256;
 constexpr int kCovFlush = 16384;  // descriptors between flushes of the 32-bit partial sums
@@ -121,61 +120,78 @@ __global__ void k_sift_grad(SiftJob J) {
     J.bin[o] = (uint8_t)sector_of(dx, dy);
 }
 
-// The descriptor of one pixel per thread.  The 128 sums are accumulated in
-// shared memory as [bin][thread]: each sample adds its magnitude to its own
-// bin only, in the samples' row-major order within each cell (a thread owns
-// one column, so a warp's accesses fall in 32 distinct banks whatever the
-// bins).  The second pass stores each clipped value back for the third.
+// Sum of squares of the 128 values of a pixel's four-thread group in bin
+// order: thread r of the group holds bins 32 r .. 32 r + 31 and continues
+// the running sum of threads 0 .. r - 1, so the sum is the sequential one.
+// Every lane of the warp calls it.
+__device__ __forceinline__ float group_sum_sq(const float (&h)[32], int r, int lane) {
+    float ss = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (r == q) {
+#pragma unroll
+            for (int b = 0; b < 32; ++b) ss = __fadd_rn(ss, __fmul_rn(h[b], h[b]));
+        }
+        ss = __shfl_sync(0xffffffffu, ss, (lane & ~3) | q);
+    }
+    return ss;
+}
+
+// The descriptor of one pixel per four threads: thread r of the group holds
+// the 32 sums of cell row r (bins 32 r .. 32 r + 31 in descriptor order) in
+// registers.  A bin's sum adds +0 for the samples of the other sectors,
+// which leaves it bit-identical to adding only its own samples.  Threads
+// past the image's edge compute on the last column and store nothing, so
+// that every lane takes part in the shuffles.
 __global__ void __launch_bounds__(kDescThreads) k_sift_desc(SiftJob J) {
-    extern __shared__ float hs[];  // [kDesc][kDescThreads]
-    const int t = threadIdx.x;
-    const int x = blockIdx.x * blockDim.x + t, y = blockIdx.y, v = blockIdx.z;
-    if (x >= J.w) return;
+    const int lane = threadIdx.x & 31, r = threadIdx.x & 3;
+    const int x = blockIdx.x * (kDescThreads / 4) + (threadIdx.x >> 2), y = blockIdx.y, v = blockIdx.z;
+    const bool valid = x < J.w;
+    const int xs = valid ? x : J.w - 1;
     const size_t plane = (size_t)v * J.h * J.w;
     const float* mag = J.mag + plane;
     const uint8_t* bin = J.bin + plane;
-    for (int k = 0; k < kDesc; ++k) hs[k * kDescThreads + t] = 0.0f;
-    for (int cy = 0; cy < 4; ++cy)
-        for (int sj = 0; sj < 3; ++sj) {
-            const int qy = clampi(y + (cy * 3 + sj - 6) * J.n, 0, J.h - 1);
-            const float* mrow = mag + (size_t)qy * J.w;
-            const uint8_t* brow = bin + (size_t)qy * J.w;
+    float h[32];
 #pragma unroll
-            for (int cx = 0; cx < 4; ++cx)
+    for (int b = 0; b < 32; ++b) h[b] = 0.0f;
 #pragma unroll
-                for (int si = 0; si < 3; ++si) {
-                    const int qx = clampi(x + (cx * 3 + si - 6) * J.n, 0, J.w - 1);
-                    float* slot = hs + ((cy * 4 + cx) * 8 + brow[qx]) * kDescThreads + t;
-                    *slot = __fadd_rn(*slot, mrow[qx]);
-                }
-        }
-    float ss = 0.0f;
-    for (int k = 0; k < kDesc; ++k) {
-        const float h = hs[k * kDescThreads + t];
-        ss = __fadd_rn(ss, __fmul_rn(h, h));
+    for (int sj = 0; sj < 3; ++sj) {
+        const int qy = clampi(y + (r * 3 + sj - 6) * J.n, 0, J.h - 1);
+        const float* mrow = mag + (size_t)qy * J.w;
+        const uint8_t* brow = bin + (size_t)qy * J.w;
+#pragma unroll
+        for (int cx = 0; cx < 4; ++cx)
+#pragma unroll
+            for (int si = 0; si < 3; ++si) {
+                const int qx = clampi(xs + (cx * 3 + si - 6) * J.n, 0, J.w - 1);
+                const float m = mrow[qx];
+                const int k = brow[qx];
+#pragma unroll
+                for (int b = 0; b < 8; ++b) h[cx * 8 + b] = __fadd_rn(h[cx * 8 + b], k == b ? m : 0.0f);
+            }
     }
-    const float nr = __fsqrt_rn(ss);
-    float ss2 = 0.0f;
-    for (int k = 0; k < kDesc; ++k) {
-        float u = hs[k * kDescThreads + t];
-        if (nr > 0.0f) {
-            u = __fdiv_rn(u, nr);
-            if (u > 0.2f) u = 0.2f;
-        }
-        hs[k * kDescThreads + t] = u;
-        ss2 = __fadd_rn(ss2, __fmul_rn(u, u));
-    }
-    const float nr2 = __fsqrt_rn(ss2);
-    uint8_t* out = J.desc + (plane + (size_t)y * J.w + x) * kDesc;
-    for (int c = 0; c < 16; ++c) {
-        uint32_t word[2] = {0u, 0u};
+    const float nr = __fsqrt_rn(group_sum_sq(h, r, lane));
+    if (nr > 0.0f) {
 #pragma unroll
-        for (int b = 0; b < 8; ++b) {
-            const float u = nr2 > 0.0f ? __fdiv_rn(hs[(c * 8 + b) * kDescThreads + t], nr2) : 0.0f;
-            const int q = (int)__fadd_rn(__fmul_rn(u, 512.0f), 0.5f);
-            word[b >> 2] |= (uint32_t)min(q, 255) << (8 * (b & 3));
+        for (int b = 0; b < 32; ++b) {
+            h[b] = __fdiv_rn(h[b], nr);
+            if (h[b] > 0.2f) h[b] = 0.2f;
         }
-        *reinterpret_cast<uint2*>(out + c * 8) = make_uint2(word[0], word[1]);
+    }
+    const float nr2 = __fsqrt_rn(group_sum_sq(h, r, lane));
+    uint32_t word[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) word[i] = 0u;
+#pragma unroll
+    for (int b = 0; b < 32; ++b) {
+        const float u = nr2 > 0.0f ? __fdiv_rn(h[b], nr2) : 0.0f;
+        const int q = (int)__fadd_rn(__fmul_rn(u, 512.0f), 0.5f);
+        word[b >> 2] |= (uint32_t)min(q, 255) << (8 * (b & 3));
+    }
+    if (valid) {
+        uint4* out = reinterpret_cast<uint4*>(J.desc + (plane + (size_t)y * J.w + x) * kDesc + 32 * r);
+        out[0] = make_uint4(word[0], word[1], word[2], word[3]);
+        out[1] = make_uint4(word[4], word[5], word[6], word[7]);
     }
 }
 
@@ -388,18 +404,17 @@ extern "C" int sff_sift_features(const uint8_t* const* rgb_dev4, int32_t pitch_b
     J.proj = reinterpret_cast<float*>(ws + L.proj);
     cudaStream_t st = (cudaStream_t)stream;
     const dim3 g((width + 127) / 128, height, 4);
-    const dim3 gd((width + kDescThreads - 1) / kDescThreads, height, 4);
-    // the attributes are per device: set them on the current one at every call
+    const dim3 gd((width + kDescThreads / 4 - 1) / (kDescThreads / 4), height, 4);
+    // the attribute is per device: set it on the current one at every call
     if (cudaFuncSetAttribute(k_sift_axes, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             kDesc * kDesc * (int)sizeof(double)) != cudaSuccess ||
-        cudaFuncSetAttribute(k_sift_desc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDescSmem) != cudaSuccess)
+                             kDesc * kDesc * (int)sizeof(double)) != cudaSuccess)
         return SFF_ERR_CUDA;
     for (int s = 0; s < params->num_scales; ++s) {
         J.s = s;
         J.n = 1 << s;
         SFF_LAUNCH(k_sift_grey, g, 128, 0, st, J);
         SFF_LAUNCH(k_sift_grad, g, 128, 0, st, J);
-        SFF_LAUNCH(k_sift_desc, gd, kDescThreads, kDescSmem, st, J);
+        SFF_LAUNCH(k_sift_desc, gd, kDescThreads, 0, st, J);
         if (s == 0) {  // the principal axes of the full-resolution descriptors
             if (cudaMemsetAsync(J.s1, 0, L.axes - L.s1, st) != cudaSuccess) return SFF_ERR_CUDA;
             const size_t count = 4 * (size_t)width * height;
