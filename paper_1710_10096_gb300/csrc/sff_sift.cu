@@ -143,7 +143,7 @@ __device__ __forceinline__ float group_sum_sq(const float (&h)[32], int r, int l
 // which leaves it bit-identical to adding only its own samples.  Threads
 // past the image's edge compute on the last column and store nothing, so
 // that every lane takes part in the shuffles.
-__global__ void __launch_bounds__(kDescThreads) k_sift_desc(SiftJob J) {
+__global__ void __launch_bounds__(kDescThreads, 7) k_sift_desc(SiftJob J) {
     const int lane = threadIdx.x & 31, r = threadIdx.x & 3;
     const int x = blockIdx.x * (kDescThreads / 4) + (threadIdx.x >> 2), y = blockIdx.y, v = blockIdx.z;
     const bool valid = x < J.w;
