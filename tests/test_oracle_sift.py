@@ -46,6 +46,29 @@ def test_descriptor_closed_forms():
         assert (d[m:h - m, m:w - m] == want).all()
 
 
+def test_descriptor_cell_layout_on_a_ramp_that_ends_inside_a_cell():
+    # grey 4 min(x, 21): at pixel (20, 20) the sample columns are 14..25 and
+    # the gradient dx = g(q + 1) - g(q - 1) is 8 for q <= 20, 4 at q = 21 and
+    # 0 beyond, dy = 0 (sector 0).  Cell columns 0..3 then hold 72, 72, 36
+    # and 0 in every cell row: norm 216, so 1/3 (clipped to 0.2) and 1/6;
+    # renormalised by sqrt(8 * 0.04 + 4 / 36), quantised to 156 and 130
+    h, w = 40, 40
+    g = np.repeat((4 * np.minimum(np.arange(w), 21)).astype(np.uint8)[None, :], h, axis=0)
+    d = oracle.sift_descriptors(np.repeat(g[..., None], 3, axis=2), 0)[20, 20]
+    want = np.zeros(128, np.uint8)
+    for cy in range(4):
+        for cx, val in enumerate((156, 156, 130, 0)):
+            want[(cy * 4 + cx) * 8] = val
+    assert np.array_equal(d, want)
+    # the same edge seen along y: the cells' roles move from columns to rows
+    dt = oracle.sift_descriptors(np.repeat(g.T[..., None], 3, axis=2), 0)[20, 20]
+    want_t = np.zeros(128, np.uint8)
+    for cy, val in enumerate((156, 156, 130, 0)):
+        for cx in range(4):
+            want_t[(cy * 4 + cx) * 8 + 2] = val
+    assert np.array_equal(dt, want_t)
+
+
 def test_principal_axes_of_known_variances():
     # a full factorial design: the three varying coordinates are exactly
     # uncorrelated, so the principal axes are the unit vectors, ordered by
@@ -92,6 +115,31 @@ def test_cost_is_zero_at_the_true_vector_and_clamps():
     c1 = oracle.sift_cost(L0, L1, R0, R1, 1, 0, 40, 30, np.array([500, 0, 0, 0], np.int16))
     c2 = oracle.sift_cost(L0, L1, R0, R1, 1, 0, 40, 30, np.array([900, 0, 0, 0], np.int16))
     assert c1 == c2
+
+
+def test_cost_sums_three_distances_over_a_7x7_window_at_stride_n():
+    h, w = 40, 48
+    zero = np.zeros((h, w, 4), np.float32)
+
+    def const(a, b, c):
+        x = np.zeros((h, w, 4), np.float32)
+        x[..., :3] = (a, b, c)
+        return x
+
+    # constant features: every window pixel adds |(3, 4, 0)| = 5 (temporal),
+    # |(0, 0, 2)| = 2 (stereo) and |(1, 2, 2)| = 3 (cross), exactly
+    u = np.array([2, -1, 3, 5], np.int16)
+    for n in (1, 2):
+        assert oracle.sift_cost(zero, const(3, 4, 0), const(0, 0, 2), const(1, 2, 2), n, 0, 20, 20, u) == 49.0 * 10
+    # one marked pixel in the temporal view, vector 0: it counts only where it
+    # lies on the window's grid, offsets -3n .. 3n at stride n
+    for n in (1, 2):
+        for (ox, oy), hits in (((3 * n, -3 * n), 1), ((-3 * n, 2 * n), 1), ((4 * n, 0), 0), ((0, -4 * n), 0),
+                               ((n + 1, 0), 1 if n == 1 else 0)):
+            tmp = zero.copy()
+            tmp[20 + oy, 24 + ox, :3] = (3.0, 4.0, 0.0)
+            c = oracle.sift_cost(zero, tmp, zero, zero, n, 0, 24, 20, np.zeros(4, np.int16))
+            assert c == 5.0 * hits, (n, ox, oy)
 
 
 def test_matching_with_the_sift_cost_recovers_integer_shifts():
