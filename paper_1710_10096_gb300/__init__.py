@@ -226,13 +226,45 @@ def _nbytes(t) -> int:
     return t.numel() * t.element_size()
 
 
+def _buf(t, nbytes: int, what: str):
+    """A buffer the library writes or reads densely: a contiguous CUDA tensor
+    of at least `nbytes` bytes.  The C ABI sees only its pointer, so the size
+    is checked here."""
+    if not getattr(t, "is_cuda", False):
+        raise ValueError(f"{what}: expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: expected a contiguous tensor")
+    if _nbytes(t) < nbytes:
+        raise ValueError(f"{what}: {_nbytes(t)} bytes, at least {nbytes} needed")
+    return t.data_ptr()
+
+
+def _image(t, what: str, shape=None) -> int:
+    """An H x W x 3 uint8 CUDA image whose rows may be padded (pixels packed);
+    returns its row pitch in bytes."""
+    if not getattr(t, "is_cuda", False) or t.dim() != 3 or t.shape[2] != 3 or t.element_size() != 1:
+        raise ValueError(f"{what}: expected a CUDA uint8 [H, W, 3] tensor")
+    if t.stride(2) != 1 or t.stride(1) != 3 or t.stride(0) < 3 * t.shape[1]:
+        raise ValueError(f"{what}: pixels must be packed, rows at a pitch of at least 3 W bytes")
+    if shape is not None and tuple(t.shape[:2]) != tuple(shape):
+        raise ValueError(f"{what}: shape {tuple(t.shape[:2])}, expected {tuple(shape)}")
+    return t.stride(0)
+
+
+def _pyramids(pyrs, width: int, height: int, params: Params, what: str):
+    pb = pyramid_bytes(width, height, params)
+    if pb == 0:
+        raise SffError(f"{what}: invalid size {width}x{height} or parameters")
+    return [_buf(t, pb, f"{what} pyramid") for t in pyrs]
+
+
 def features(rgb, pyramid, workspace, params: Params = None, stream=None) -> None:
     """sff_features on a [H, W, 3] uint8 CUDA tensor (rows may be padded)."""
     params = params or default_params()
-    assert rgb.is_cuda and rgb.dtype.itemsize == 1 and rgb.dim() == 3 and rgb.shape[2] == 3
-    assert rgb.stride(2) == 1 and rgb.stride(1) == 3
+    pitch = _image(rgb, "sff_features rgb")
     h, w = rgb.shape[0], rgb.shape[1]
-    _check(lib().sff_features(_ptr(rgb), w, h, rgb.stride(0), ctypes.byref(params), _ptr(pyramid), _ptr(workspace),
+    (pp,) = _pyramids([pyramid], w, h, params, "sff_features")
+    _check(lib().sff_features(_ptr(rgb), w, h, pitch, ctypes.byref(params), pp, _buf(workspace, 0, "workspace"),
                               _nbytes(workspace), _stream(stream)), "sff_features")
 
 
@@ -240,9 +272,10 @@ def match_views(pyr_ref, pyr_temporal, pyr_stereo, pyr_cross, width: int, height
                 field, cost, workspace, params: Params = None, stream=None) -> None:
     """sff_match_views; field [H, W, 4] int16 and cost [H, W] int32 CUDA tensors."""
     params = params or default_params()
-    _check(lib().sff_match_views(_ptr(pyr_ref), _ptr(pyr_temporal), _ptr(pyr_stereo), _ptr(pyr_cross), width,
-                                 height, int(mirror), int(seed) & (2 ** 64 - 1), ctypes.byref(params), _ptr(field),
-                                 _ptr(cost), _ptr(workspace), _nbytes(workspace), _stream(stream)),
+    pr = _pyramids([pyr_ref, pyr_temporal, pyr_stereo, pyr_cross], width, height, params, "sff_match_views")
+    _check(lib().sff_match_views(*pr, width, height, int(mirror), int(seed) & (2 ** 64 - 1), ctypes.byref(params),
+                                 _buf(field, 8 * width * height, "field"), _buf(cost, 4 * width * height, "cost"),
+                                 _buf(workspace, 0, "workspace"), _nbytes(workspace), _stream(stream)),
            "sff_match_views")
 
 
@@ -251,9 +284,11 @@ def match_views_sequential(pyr_ref, pyr_temporal, pyr_stereo, pyr_cross, width: 
     """sff_match_views_sequential: the paper's in-place raster sweeps instead of
     checkerboard half-steps (slow; reproduces the sequential scan exactly)."""
     params = params or default_params()
-    _check(lib().sff_match_views_sequential(_ptr(pyr_ref), _ptr(pyr_temporal), _ptr(pyr_stereo), _ptr(pyr_cross),
-                                            width, height, int(mirror), int(seed) & (2 ** 64 - 1),
-                                            ctypes.byref(params), _ptr(field), _ptr(cost), _ptr(workspace),
+    pr = _pyramids([pyr_ref, pyr_temporal, pyr_stereo, pyr_cross], width, height, params,
+                   "sff_match_views_sequential")
+    _check(lib().sff_match_views_sequential(*pr, width, height, int(mirror), int(seed) & (2 ** 64 - 1),
+                                            ctypes.byref(params), _buf(field, 8 * width * height, "field"),
+                                            _buf(cost, 4 * width * height, "cost"), _buf(workspace, 0, "workspace"),
                                             _nbytes(workspace), _stream(stream)),
            "sff_match_views_sequential")
 
@@ -262,9 +297,12 @@ def match_quad(pyr_l0, pyr_r0, pyr_l1, pyr_r1, width: int, height: int, seed: in
                workspace, params: Params = None, stream=None) -> None:
     """sff_match_quad: forward field of L0 and inverse field of R1 in shared launches."""
     params = params or default_params()
-    _check(lib().sff_match_quad(_ptr(pyr_l0), _ptr(pyr_r0), _ptr(pyr_l1), _ptr(pyr_r1), width, height,
-                                int(seed) & (2 ** 64 - 1), ctypes.byref(params), _ptr(fwd), _ptr(fwd_cost), _ptr(inv),
-                                _ptr(inv_cost), _ptr(workspace), _nbytes(workspace), _stream(stream)),
+    n = width * height
+    pr = _pyramids([pyr_l0, pyr_r0, pyr_l1, pyr_r1], width, height, params, "sff_match_quad")
+    _check(lib().sff_match_quad(*pr, width, height, int(seed) & (2 ** 64 - 1), ctypes.byref(params),
+                                _buf(fwd, 8 * n, "fwd"), _buf(fwd_cost, 4 * n, "fwd_cost"), _buf(inv, 8 * n, "inv"),
+                                _buf(inv_cost, 4 * n, "inv_cost"), _buf(workspace, 0, "workspace"),
+                                _nbytes(workspace), _stream(stream)),
            "sff_match_quad")
 
 
@@ -285,10 +323,13 @@ def match_quad_tuned(pyr_l0, pyr_r0, pyr_l1, pyr_r1, width: int, height: int, se
                      fwd_cost, inv, inv_cost, workspace, params: Params = None, stream=None) -> None:
     """sff_match_quad_tuned: match_quad with an explicit work distribution."""
     params = params or default_params()
-    _check(lib().sff_match_quad_tuned(_ptr(pyr_l0), _ptr(pyr_r0), _ptr(pyr_l1), _ptr(pyr_r1), width, height,
-                                      int(seed) & (2 ** 64 - 1), ctypes.byref(params), ctypes.byref(tuning),
-                                      _ptr(fwd), _ptr(fwd_cost), _ptr(inv), _ptr(inv_cost), _ptr(workspace),
-                                      _nbytes(workspace), _stream(stream)), "sff_match_quad_tuned")
+    n = width * height
+    pr = _pyramids([pyr_l0, pyr_r0, pyr_l1, pyr_r1], width, height, params, "sff_match_quad_tuned")
+    _check(lib().sff_match_quad_tuned(*pr, width, height, int(seed) & (2 ** 64 - 1), ctypes.byref(params),
+                                      ctypes.byref(tuning), _buf(fwd, 8 * n, "fwd"), _buf(fwd_cost, 4 * n, "fwd_cost"),
+                                      _buf(inv, 8 * n, "inv"), _buf(inv_cost, 4 * n, "inv_cost"),
+                                      _buf(workspace, 0, "workspace"), _nbytes(workspace), _stream(stream)),
+           "sff_match_quad_tuned")
 
 
 def split_pyramid(pyr, width: int, height: int, params: Params = None):
@@ -314,19 +355,25 @@ def split_pyramid(pyr, width: int, height: int, params: Params = None):
 
 def consistency_filter(fwd, fwd_cost, inv, inv_cost, keep, cerr, workspace, params: Params = None,
                        stream=None) -> None:
+    """fwd, inv: CUDA int16 [H, W, 4]; costs: int32 [H, W]; keep, cerr: uint8 [H, W], overwritten."""
     params = params or default_params()
     h, w = fwd.shape[0], fwd.shape[1]
-    _check(lib().sff_consistency_filter(_ptr(fwd), _ptr(fwd_cost), _ptr(inv), _ptr(inv_cost), w, h,
-                                        ctypes.byref(params), _ptr(keep), _ptr(cerr), _ptr(workspace),
-                                        _nbytes(workspace), _stream(stream)), "sff_consistency_filter")
+    n = w * h
+    _check(lib().sff_consistency_filter(_buf(fwd, 8 * n, "fwd"), _buf(fwd_cost, 4 * n, "fwd_cost"),
+                                        _buf(inv, 8 * n, "inv"), _buf(inv_cost, 4 * n, "inv_cost"), w, h,
+                                        ctypes.byref(params), _buf(keep, n, "keep"), _buf(cerr, n, "cerr"),
+                                        _buf(workspace, 0, "workspace"), _nbytes(workspace), _stream(stream)),
+           "sff_consistency_filter")
 
 
 def emit_seeds(fwd, fwd_cost, keep, cerr, seeds, capacity: int, count, workspace, stream=None) -> None:
     """seeds: CUDA uint8 tensor of >= 20 * capacity bytes; count: CUDA int32 tensor [1]."""
     h, w = fwd.shape[0], fwd.shape[1]
-    assert _nbytes(seeds) >= 20 * capacity
-    _check(lib().sff_emit_seeds(_ptr(fwd), _ptr(fwd_cost), _ptr(keep), _ptr(cerr), w, h, _ptr(seeds), capacity,
-                                _ptr(count), _ptr(workspace), _nbytes(workspace), _stream(stream)), "sff_emit_seeds")
+    n = w * h
+    _check(lib().sff_emit_seeds(_buf(fwd, 8 * n, "fwd"), _buf(fwd_cost, 4 * n, "fwd_cost"), _buf(keep, n, "keep"),
+                                _buf(cerr, n, "cerr"), w, h, _buf(seeds, 20 * capacity, "seeds"), capacity,
+                                _buf(count, 4, "count"), _buf(workspace, 0, "workspace"), _nbytes(workspace),
+                                _stream(stream)), "sff_emit_seeds")
 
 
 def sift_workspace_bytes(width: int, height: int) -> int:
@@ -336,12 +383,17 @@ def sift_workspace_bytes(width: int, height: int) -> int:
 def sift_features(images, phis, workspace, params: Params = None, stream=None) -> None:
     """images: 4 CUDA uint8 [H, W, 3] with one row pitch; phis: 4 CUDA float32
     [S, H, W, 4], overwritten with phi of Eq. 1's SIFT-PCA features."""
+    params = params or default_params()
+    if len(images) != 4 or len(phis) != 4:
+        raise ValueError("sff_sift_features: four images and four phi buffers")
     h, w = images[0].shape[0], images[0].shape[1]
-    assert all(im.stride(0) == images[0].stride(0) for im in images) and len(images) == 4 and len(phis) == 4
+    pitch = _image(images[0], "sff_sift_features image")
+    if any(_image(im, "sff_sift_features image", (h, w)) != pitch for im in images):
+        raise ValueError("sff_sift_features: the four images must share one row pitch")
     ip = (ctypes.c_void_p * 4)(*[_ptr(im) for im in images])
-    pp = (ctypes.c_void_p * 4)(*[_ptr(p) for p in phis])
-    _check(lib().sff_sift_features(ip, images[0].stride(0), w, h, ctypes.byref(params or default_params()), pp,
-                                   _ptr(workspace), _nbytes(workspace), _stream(stream)), "sff_sift_features")
+    pp = (ctypes.c_void_p * 4)(*[_buf(p, 16 * params.num_scales * w * h, "phi") for p in phis])
+    _check(lib().sff_sift_features(ip, pitch, w, h, ctypes.byref(params), pp, _buf(workspace, 0, "workspace"),
+                                   _nbytes(workspace), _stream(stream)), "sff_sift_features")
 
 
 def match_views_sift(pyr_ref, pyr_temporal, pyr_stereo, pyr_cross, phi_ref, phi_temporal, phi_stereo, phi_cross,
@@ -349,10 +401,13 @@ def match_views_sift(pyr_ref, pyr_temporal, pyr_stereo, pyr_cross, phi_ref, phi_
                      params: Params = None, stream=None) -> None:
     """One field with the cost of Eq. 1 on SIFT-PCA features; cost holds float bit patterns."""
     params = params or default_params()
-    _check(lib().sff_match_views_sift(_ptr(pyr_ref), _ptr(pyr_temporal), _ptr(pyr_stereo), _ptr(pyr_cross),
-                                      _ptr(phi_ref), _ptr(phi_temporal), _ptr(phi_stereo), _ptr(phi_cross), width,
-                                      height, int(mirror), int(seed) & (2 ** 64 - 1), ctypes.byref(params),
-                                      _ptr(field), _ptr(cost), _ptr(workspace), _nbytes(workspace), _stream(stream)),
+    pr = _pyramids([pyr_ref, pyr_temporal, pyr_stereo, pyr_cross], width, height, params, "sff_match_views_sift")
+    ph = [_buf(p, 16 * params.num_scales * width * height, "phi") for p in (phi_ref, phi_temporal, phi_stereo,
+                                                                          phi_cross)]
+    _check(lib().sff_match_views_sift(*pr, *ph, width, height, int(mirror), int(seed) & (2 ** 64 - 1),
+                                      ctypes.byref(params), _buf(field, 8 * width * height, "field"),
+                                      _buf(cost, 4 * width * height, "cost"), _buf(workspace, 0, "workspace"),
+                                      _nbytes(workspace), _stream(stream)),
            "sff_match_views_sift")
 
 
@@ -371,19 +426,24 @@ def sgm_workspace_bytes(width: int, height: int, params: SgmParams = None) -> in
 def sgm(left, right, disp, workspace, params: SgmParams = None, stream=None) -> None:
     """left, right: CUDA uint8 [H, W, 3] (L0, R0, same row pitch); disp: CUDA int16 [H, W]."""
     h, w = left.shape[0], left.shape[1]
-    assert left.stride(0) == right.stride(0)
-    _check(lib().sff_sgm(_ptr(left), _ptr(right), left.stride(0), w, h, ctypes.byref(params or default_sgm_params()),
-                         _ptr(disp), _ptr(workspace), _nbytes(workspace), _stream(stream)), "sff_sgm")
+    pitch = _image(left, "sff_sgm left")
+    if _image(right, "sff_sgm right", (h, w)) != pitch:
+        raise ValueError("sff_sgm: left and right must share one row pitch")
+    _check(lib().sff_sgm(_ptr(left), _ptr(right), pitch, w, h, ctypes.byref(params or default_sgm_params()),
+                         _buf(disp, 2 * w * h, "disp"), _buf(workspace, 0, "workspace"), _nbytes(workspace),
+                         _stream(stream)), "sff_sgm")
 
 
 def emit_seeds_geo(fwd, fwd_cost, keep, cerr, sgm_disp, seeds, capacity: int, count, workspace,
                    params: Params = None, stream=None) -> None:
     """As emit_seeds, with disparity-only seeds (kind 1) where d0 agrees with sgm_disp."""
     h, w = fwd.shape[0], fwd.shape[1]
-    assert _nbytes(seeds) >= 20 * capacity
-    _check(lib().sff_emit_seeds_geo(_ptr(fwd), _ptr(fwd_cost), _ptr(keep), _ptr(cerr), _ptr(sgm_disp), w, h,
-                                    ctypes.byref(params or default_params()), _ptr(seeds), capacity, _ptr(count),
-                                    _ptr(workspace), _nbytes(workspace), _stream(stream)), "sff_emit_seeds_geo")
+    n = w * h
+    _check(lib().sff_emit_seeds_geo(_buf(fwd, 8 * n, "fwd"), _buf(fwd_cost, 4 * n, "fwd_cost"), _buf(keep, n, "keep"),
+                                    _buf(cerr, n, "cerr"), _buf(sgm_disp, 2 * n, "sgm_disp"), w, h,
+                                    ctypes.byref(params or default_params()), _buf(seeds, 20 * capacity, "seeds"),
+                                    capacity, _buf(count, 4, "count"), _buf(workspace, 0, "workspace"),
+                                    _nbytes(workspace), _stream(stream)), "sff_emit_seeds_geo")
 
 
 def default_interp_params(width: int, height: int, focal: float, baseline: float, **overrides) -> InterpParams:
@@ -403,9 +463,9 @@ def interpolate(seeds, count, capacity: int, width: int, height: int, params: In
                 stream=None) -> None:
     """seeds: CUDA tensor of >= 20 * capacity bytes; count: CUDA int32 [1];
     field: CUDA float32 [H][W][4] (u, v, d0, d1), overwritten."""
-    assert _nbytes(seeds) >= 20 * capacity and _nbytes(field) >= 16 * width * height
-    _check(lib().sff_interpolate(_ptr(seeds), _ptr(count), capacity, width, height, ctypes.byref(params),
-                                 _ptr(field), _ptr(workspace), _nbytes(workspace), _stream(stream)),
+    _check(lib().sff_interpolate(_buf(seeds, 20 * capacity, "seeds"), _buf(count, 4, "count"), capacity, width,
+                                 height, ctypes.byref(params), _buf(field, 16 * width * height, "field"),
+                                 _buf(workspace, 0, "workspace"), _nbytes(workspace), _stream(stream)),
            "sff_interpolate")
 
 
@@ -466,8 +526,8 @@ class QuadBuffers:
         imgs = list(images) if images is not None else list(self.dev_in.unbind(0))
         pitch = imgs[0].stride(0)
         for im in imgs:
-            assert im.is_cuda and im.stride(0) == pitch and im.stride(1) == 3 and im.stride(2) == 1
-            assert tuple(im.shape) == (self.height, self.width, 3)
+            if _image(im, "quad image", (self.height, self.width)) != pitch:
+                raise ValueError("quad images: the four images must share one row pitch")
         d = QuadDesc()
         for k in range(4):
             d.rgb[k] = imgs[k].data_ptr()
