@@ -38,6 +38,19 @@ def test_perturbation_threshold(orc, comp, delta):
     assert (cerr[inside] == abs(delta)).all()
 
 
+def test_consistency_error_saturates_at_255(orc):
+    # cerr is the sum of the four absolute round-trip differences, saturated
+    # to a byte: one component off by 200 gives 200, by 300 gives 255
+    h, w = 12, 16
+    for delta, want in ((200, 200), (254, 254), (255, 255), (300, 255)):
+        fwd, fc, inv, ic = _const_fields(h, w, 1, 0, 2, 2)
+        inv[..., 0] += delta
+        keep, cerr = orc.consistency_check(fwd, fc, inv, ic)
+        assert not keep.any()
+        # column 0's cross match (x + u - d1 = -1) is outside: 255 untested
+        assert (cerr[:, 1:] == want).all() and (cerr[:, 0] == 255).all(), delta
+
+
 def test_empty_vectors_rejected(orc):
     h, w = 10, 12
     fwd, fc, inv, ic = _const_fields(h, w, 0, 0, 1, 1)
@@ -112,6 +125,24 @@ def test_region_filter_hand_built(orc):
     assert out[13:18, 3:8].all()
     assert out[22:35, 22:35].all()
     assert out[3:8, 21:26].all()
+
+
+def test_region_of_exactly_s_c_pixels_is_kept(orc):
+    # two regions with joinable rejected neighbours: 10 x 15 = 150 = s_c
+    # pixels (kept) and the same less one corner, 149 pixels (removed)
+    h, w = 40, 60
+    fwd = np.zeros((h, w, 4), np.int16)
+    fc = np.zeros((h, w), np.int32)
+    keep = np.zeros((h, w), np.uint8)
+    fwd[1:14, 1:19, 0] = 7
+    keep[2:12, 2:17] = 1
+    fwd[20:33, 30:48, 0] = 11
+    keep[21:31, 31:46] = 1
+    keep[21, 31] = 0
+    assert keep[2:12, 2:17].sum() == 150 and keep[21:31, 31:46].sum() == 149
+    out = orc.region_filter(fwd, fc, keep, orc.default_params()).astype(bool)
+    assert out[2:12, 2:17].all()
+    assert not out[21:31, 31:46].any()
 
 
 def test_seeds_block_argmin(orc):
