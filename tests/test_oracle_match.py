@@ -62,6 +62,24 @@ def test_init_exhaustive(orc):
         assert (cost[1::2, :] == EMPTY).all() and (cost[:, 1::2] == EMPTY).all()
 
 
+def test_init_ties_go_to_the_first_combination(orc):
+    # a constant image: every feature is the same, so every combination
+    # costs 0.  The nearest-neighbour lists then hold the lowest raster
+    # indices, and the first combination wins: the temporal point (0, 0),
+    # the stereo and cross points of lowest x that the sign of d allows
+    # (x = 0 for the left-reference pass, x = px / tx for the mirrored one)
+    img = np.full((16, 20, 3), 90, np.uint8)
+    p = orc.default_params(num_scales=2, iterations=0)
+    F = orc.features(img, p)[0]
+    for mirror in (0, 1):
+        fld, cost = orc.match_views(F, F, F, F, mirror, 1, p)
+        for py in range(0, 16, 2):
+            for px in range(0, 20, 2):
+                want = (-px, -py, 0 if mirror else px, 0)
+                assert tuple(int(v) for v in fld[py, px]) == want, (mirror, px, py)
+                assert cost[py, px] == 0
+
+
 def test_init_knn_leaves(orc):
     # with K_T = 4 the chosen temporal match is one of the 4 nearest grid points
     imgs = scenegen.random_images(40, 24, 22)
