@@ -125,6 +125,29 @@ def test_more_than_32_seeds_tied_at_the_kth_distance(env):
         np.testing.assert_allclose(got, want, rtol=RTOL, atol=ATOL)
 
 
+def _rows(rows):
+    s = np.zeros(len(rows), scenegen.SEED_RECORD)
+    for k, (x, y, u, v, d0, d1) in enumerate(rows):
+        s[k]["x"], s[k]["y"], s[k]["u"], s[k]["v"], s[k]["d0"], s[k]["d1"] = x, y, u, v, d0, d1
+    return s
+
+
+@pytest.mark.parametrize("rows,w,h,kg,km", [
+    # every seed at unit disparity: the reprojection at max(d0, 1) = 1
+    ([(x, y, 3, 0, 1, 1) for y in range(1, 24, 3) for x in range(1, 30, 3)], 30, 24, 12, 8),
+    # a plane that falls below d0 = 1 left of the first seed
+    ([(5, 10, 3, 0, 1, 1), (15, 10, 0, 0, 3, 3)], 21, 21, 2, 1),
+    # a seed whose translation moves its near plane behind the camera
+    ([(5, 10, 0, 0, 2, 40), (15, 10, 0, 0, 12, 13)], 21, 21, 2, 1),
+])
+def test_reprojection_edge_cases(env, rows, w, h, kg, km):
+    s = _rows(rows)
+    got, status = _gpu_interp(env, s, w, h, 300.0, 0.5, k_geo=kg, k_motion=km)
+    want = _oracle_interp(env[2], s, w, h, 300.0, 0.5, k_geo=kg, k_motion=km)
+    assert status == 0
+    np.testing.assert_allclose(got, want, rtol=RTOL, atol=ATOL)
+
+
 def test_end_to_end_after_the_matching_stage(env):
     # the seeds of the whole matching stage, each side on its own: the GPU
     # interpolates the GPU's seeds, the oracle the oracle's

@@ -104,6 +104,43 @@ def test_more_than_32_seeds_tied_at_the_kth_distance():
         assert sorted(idx[1:]) == list(idx[1:])  # the tied seeds in index order
 
 
+def test_reprojection_at_unit_disparity():
+    # every seed at d0 = d1 = 1 (depth f B) moving 3 px right: the 3D motion
+    # is the translation (3 B, 0, 0) and the plane d0 = 1, so every pixel is
+    # reprojected at max(d0, 1) = 1 and moves by exactly (3, 0) with d1 = 1
+    rows = [(x, y, 3, 0, 1, 1) for y in range(1, 24, 3) for x in range(1, 30, 3)]
+    s = _seeds(rows)
+    out = oracle.interpolate(s, 30, 24, oracle.interp_params(30, 24, 400.0, 0.5, k_geo=12, k_motion=8))
+    np.testing.assert_allclose(out[..., 0], 3.0, atol=1e-6)
+    np.testing.assert_allclose(out[..., 1], 0.0, atol=1e-6)
+    np.testing.assert_allclose(out[..., 2], 1.0, atol=1e-6)
+    np.testing.assert_allclose(out[..., 3], 1.0, atol=1e-6)
+    # a plane that falls below 1: seed A (5, 10) at d0 = 1 moving 3 px, seed B
+    # (15, 10) at d0 = 3 tilts A's plane to 1 + 0.2 (x - 5), 0.4 at x = 2;
+    # the reprojection uses max(d0, 1) = 1, so A's translation still moves the
+    # pixel by exactly 3 px with d1 = 1 (at depth f B / 0.4 it would be 1.2 px)
+    s2 = _seeds([(5, 10, 3, 0, 1, 1), (15, 10, 0, 0, 3, 3)])
+    p2 = oracle.interp_params(21, 21, 300.0, 0.5, k_geo=2, k_motion=1)
+    o2, closest = oracle.interpolate_pixels(s2, p2, [[2, 10]])
+    assert list(closest) == [0]
+    np.testing.assert_allclose(o2[0], [3.0, 0.0, 0.4, 1.0], atol=1e-5)
+
+
+def test_points_moved_behind_the_camera_get_no_flow():
+    # seed A at (5, 10) with d0 = 2 and d1 = 40 (depth f B / 2 -> f B / 40:
+    # its own translation is -0.475 f B in Z); seed B at (15, 10) with d0 = 12
+    # tilts A's plane to d0 = 2 + (x - 5).  At x = 9, closest to A, the plane
+    # gives d0 = 6, depth f B / 6 < 0.475 f B: the moved point is behind the
+    # camera, so u = v = 0 and d1 = d0 there; at x = 5 it is A's own motion
+    s = _seeds([(5, 10, 0, 0, 2, 40), (15, 10, 0, 0, 12, 13)])
+    f, B = 300.0, 0.5
+    p = oracle.interp_params(21, 21, f, B, k_geo=2, k_motion=1)
+    out, closest = oracle.interpolate_pixels(s, p, [[9, 10], [5, 10]])
+    assert list(closest) == [0, 0]
+    np.testing.assert_allclose(out[0], [0.0, 0.0, 6.0, 6.0], atol=1e-5)
+    np.testing.assert_allclose(out[1], [0.0, 0.0, 2.0, 40.0], atol=1e-5)
+
+
 def test_motion_neighbourhood_skips_seeds_that_cannot_be_triangulated():
     s = _seeds([(5, 5, 0, 0, 4, 4), (6, 5, 0, 0, 0, 4), (7, 5, 0, 0, 4, 0), (9, 5, 0, 0, 3, 3)])
     idx, _ = oracle.nearest_seeds(s, 5, 5, 4, motion_only=True)
