@@ -64,6 +64,26 @@ def _brute_path(C, p1, p2):
     return best
 
 
+def test_a_single_preference_travels_along_the_eight_rays():
+    # a flat cost volume with one pixel q0 that prefers d* = 5: only the path
+    # of direction r reaches q0 + k r through q0, so the sum over the 8
+    # directions prefers d* exactly on the 8 rays from q0 (and at q0); every
+    # other pixel sees flat sums and takes the lowest disparity, 0
+    H, W, D, dstar = 21, 23, 8, 5
+    C = np.full((H, W, D), 6, np.uint8)
+    qy, qx = 10, 11
+    C[qy, qx] = 30
+    C[qy, qx, dstar] = 0
+    disp = oracle.sgm_from_cost(C, 10, 120)
+    want = np.zeros((H, W), np.int16)
+    for rx, ry in [(1, 0), (-1, 0), (0, 1), (0, -1), (1, 1), (-1, -1), (1, -1), (-1, 1)]:
+        k = 0
+        while 0 <= qx + k * rx < W and 0 <= qy + k * ry < H:
+            want[qy + k * ry, qx + k * rx] = dstar
+            k += 1
+    assert np.array_equal(disp, want)
+
+
 @pytest.mark.parametrize("rx,ry", [(1, 0), (-1, 0), (0, 1), (0, -1), (1, 1), (-1, -1), (1, -1), (-1, 1)])
 def test_path_costs_are_shortest_paths(rx, ry):
     # L_r(p, .) equals the brute-force minimum over disparity sequences along
@@ -80,6 +100,10 @@ def test_path_costs_are_shortest_paths(rx, ry):
             line = line[::-1]
             b = _brute_path(np.array([C[yy, xx] for xx, yy in line]), p1, p2)
             assert np.array_equal(L[y, x] - L[y, x].min(), b - b.min()), (x, y)
+            # the exact normalised values: the brute-force minimum ending at p
+            # less the one ending at p - r (C itself at the first pixel)
+            prev = _brute_path(np.array([C[yy, xx] for xx, yy in line[:-1]]), p1, p2).min() if len(line) > 1 else 0
+            assert np.array_equal(L[y, x], b - prev), (x, y)
 
 
 def test_no_penalties_is_winner_takes_all():
