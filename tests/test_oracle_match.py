@@ -80,6 +80,53 @@ def test_init_ties_go_to_the_first_combination(orc):
                 assert cost[py, px] == 0
 
 
+def _constant_cost_fill(H, W, mirror, iters):
+    """The propagation when every cost ties (constant features): a vector
+    moves only into an empty pixel, which takes its first non-empty
+    predecessor, (x - dx n, y) before (x, y - dy n), as of the start of its
+    half-step; the colour-0 pixels ((x + y) / n even) go first; the
+    iterations take the directions (1, 1), (-1, -1), (1, -1), (-1, 1) in
+    turn.  Two scales: the coarsest grid (n = 2) holds its first
+    combinations and keeps them; at n = 1 its points keep their vectors and
+    every other pixel starts empty.  Random search never wins a tie."""
+    vec = {(x, y): (-x, -y, 0 if mirror else x, 0) for y in range(0, H, 2) for x in range(0, W, 2)}
+    dirs = [(1, 1), (-1, -1), (1, -1), (-1, 1)]
+    for it in range(iters):
+        dx, dy = dirs[it % 4]
+        for colour in (0, 1):
+            snap = dict(vec)
+            for y in range(H):
+                for x in range(W):
+                    if (x + y) % 2 != colour or (x, y) in snap:
+                        continue
+                    for q in ((x - dx, y), (x, y - dy)):
+                        if q in snap:
+                            vec[(x, y)] = snap[q]
+                            break
+    return vec
+
+
+@pytest.mark.parametrize("iters", [1, 2, 3, 4])
+def test_propagation_order_on_tied_costs(orc, iters):
+    # pins the checkerboard colours, each iteration's predecessors and
+    # direction, the candidates' order, strict improvement in propagation and
+    # random search, and which points carry over from the coarser scale
+    H, W = 9, 10
+    p = orc.default_params(num_scales=2, iterations=iters)
+    F = orc.features(np.full((H, W, 3), 90, np.uint8), p)[0]
+    for mirror in (0, 1):
+        fld, cost = orc.match_views(F, F, F, F, mirror, 1, p)
+        want = _constant_cost_fill(H, W, mirror, iters)
+        for y in range(H):
+            for x in range(W):
+                if (x, y) in want:
+                    assert tuple(int(v) for v in fld[y, x]) == want[(x, y)] and cost[y, x] == 0, (mirror, x, y)
+                else:
+                    assert cost[y, x] == EMPTY, (mirror, x, y)
+        if iters == 1:
+            assert sum((x, y) not in want for y in range(H) for x in range(W)) == 20  # the (odd, odd) pixels
+
+
 def test_init_knn_leaves(orc):
     # with K_T = 4 the chosen temporal match is one of the 4 nearest grid points
     imgs = scenegen.random_images(40, 24, 22)
