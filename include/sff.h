@@ -326,9 +326,11 @@ int sff_emit_seeds_noalloc(const int16_t* fwd_dev, const int32_t* fwd_cost_dev,
  * normalisation, clipping at 0.2, renormalisation, quantisation to uint8
  * (x 512).  Axes: covariance of the four images' full-resolution descriptors
  * from exact integer sums, 200 power iterations per axis in double
- * precision; the same axes at every scale.  Every floating-point operation
- * follows a fixed order without fused multiply-adds, so results are
- * reproducible bit for bit. */
+ * precision, each dot product of an iteration as four partial sums over the
+ * indices mod 4 (fused multiply-adds in index order) combined as
+ * (s0 + s1) + (s2 + s3); the same axes at every scale.  Every floating-point
+ * operation follows this fixed order, fused multiply-adds only there, so
+ * results are reproducible bit for bit. */
 
 /* Scratch of sff_sift_features: about 650 bytes per pixel; 0 for invalid sizes. */
 size_t sff_sift_workspace_bytes(int32_t width, int32_t height);
