@@ -26,7 +26,7 @@ import numpy as np
 
 from . import QuadBuffers, default_params, default_tuning, run_batch, seeds_to_numpy
 
-__all__ = ["Request", "Server", "PlainServer", "simulate", "poisson_arrivals"]
+__all__ = ["Request", "Server", "PlainServer", "simulate", "poisson_arrivals", "validate_request"]
 
 
 @dataclasses.dataclass
@@ -47,6 +47,35 @@ class Request:
     @property
     def latency(self) -> float:
         return self.t_done - self.t_arrival
+
+
+def validate_request(req: Request):
+    """Why a request cannot be served (None if it can): four uint8 H x W x 3
+    host images of one size within the library's limits (8 .. 16384 px)."""
+    ims = req.images
+    if not isinstance(ims, (tuple, list)) or len(ims) != 4:
+        return "a request holds four images (L0, R0, L1, R1)"
+    for k, im in enumerate(ims):
+        if not isinstance(im, np.ndarray) or im.dtype != np.uint8 or im.ndim != 3 or im.shape[2] != 3:
+            return f"image {k}: expected a uint8 numpy array [H, W, 3]"
+        if im.shape != ims[0].shape:
+            return f"image {k}: shape {im.shape}, image 0 has {ims[0].shape}"
+    h, w = ims[0].shape[:2]
+    if not (8 <= w <= 16384 and 8 <= h <= 16384):
+        return f"size {w}x{h} outside 8..16384"
+    return None
+
+
+def _submit(req: Request, lock, pending, done) -> None:
+    """Queues a request, or finishes it at once with its error when it is malformed."""
+    err = validate_request(req)
+    with lock:
+        if err is None:
+            pending.append(req)
+        else:
+            req.error = err
+            req.t_done = req.t_arrival
+            done.append(req)
 
 
 class _Slot:
@@ -90,8 +119,7 @@ class Server:
         self._sizes_cache = {}
 
     def submit(self, req: Request) -> None:
-        with self._lock:
-            self.pending.append(req)
+        _submit(req, self._lock, self.pending, self.done)
 
     def reserve(self, size, count: int) -> int:
         """Pre-allocate up to `count` idle slots of `size` within the budget
@@ -221,8 +249,7 @@ class PlainServer:
         self.batches = 0
 
     def submit(self, req: Request) -> None:
-        with self._lock:
-            self.pending.append(req)
+        _submit(req, self._lock, self.pending, self.done)
 
     def step(self, now_fn) -> None:
         import torch

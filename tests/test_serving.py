@@ -35,6 +35,32 @@ def test_summary():
     assert s["sustained_px_per_s"] == 100 * 200 / 0.1
 
 
+def test_malformed_requests_are_rejected_at_submission():
+    import collections
+    import threading
+
+    from paper_1710_10096_gb300.serve import Request, _submit, validate_request
+    good = (np.zeros((20, 30, 3), np.uint8),) * 4
+    assert validate_request(Request(0, 0, good, 1)) is None
+    bad = {
+        "three images": good[:3],
+        "other size": good[:3] + (np.zeros((20, 31, 3), np.uint8),),
+        "float": (np.zeros((20, 30, 3), np.float32),) * 4,
+        "grey": (np.zeros((20, 30), np.uint8),) * 4,
+        "too small": (np.zeros((7, 30, 3), np.uint8),) * 4,
+    }
+    for name, ims in bad.items():
+        assert validate_request(Request(0, 0, ims, 1)) is not None, name
+    # submission: a malformed request is finished at once with its error and
+    # never queued, so it can take no slot
+    lock, pending, done = threading.Lock(), collections.deque(), []
+    _submit(Request(1, 0, good, 1, t_arrival=2.0), lock, pending, done)
+    r = Request(2, 0, bad["other size"], 1, t_arrival=3.0)
+    _submit(r, lock, pending, done)
+    assert [q.rid for q in pending] == [1] and done == [r]
+    assert r.error and r.t_done == r.t_arrival
+
+
 @pytest.fixture(scope="module")
 def gpu():
     torch = pytest.importorskip("torch")
