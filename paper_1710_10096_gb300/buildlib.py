@@ -7,6 +7,7 @@ not depend on which libcudart PyTorch ships.
 """
 from __future__ import annotations
 
+import fcntl
 import glob
 import os
 import shutil
@@ -44,9 +45,20 @@ def _stale() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
+    """Compiles and links the library when a source is newer than it (or when
+    forced).  Processes that build at the same time (ranks, test workers)
+    take turns on a lock file; a process that waited finds the library fresh."""
     if not force and not _stale():
         return LIB
     os.makedirs(BUILD_DIR, exist_ok=True)
+    with open(os.path.join(BUILD_DIR, "build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        if not force and not _stale():
+            return LIB
+        return _build_locked(verbose, extra_flags)
+
+
+def _build_locked(verbose: bool, extra_flags) -> str:
     cc = nvcc()
     procs = []
     objs = []
