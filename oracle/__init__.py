@@ -53,8 +53,9 @@ def build(force: bool = False) -> str:
     newest = max(os.path.getmtime(p) for p in (_SRC, _SRC_INTERP, _SRC_SGM, _SRC_SIFT, __file__))
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
-        # no fused multiply-adds: the float and double sums follow their
-        # written order, as the CUDA path's do
+        # no contracted multiply-adds: the float and double sums follow their
+        # written order, as the CUDA path's do; explicit fma() calls stay
+        # (only where a reading names them), correctly rounded
         subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11", "-ffp-contract=off", _SRC,
                                _SRC_INTERP, _SRC_SGM, _SRC_SIFT, "-lm",
                                "-o", tmp])
