@@ -710,7 +710,7 @@ def run_reference(args):
     oracle.build()
     cores = os.cpu_count() or 1
     oracle.set_threads(cores)
-    q = scenegen.make_named(WORKLOAD, SCENE_SEED)
+    q = scenegen.make_named(args.workload, SCENE_SEED)
     # calibrate on one warm-up; shrink each step to a band of rows if the whole
     # run would exceed about two minutes
     t0 = time.perf_counter()
@@ -735,7 +735,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "px/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "width": q.width, "height": rows, "quads_per_step": 1},
+            "config": {"workload": args.workload, "width": q.width, "height": rows, "quads_per_step": 1},
             "cpu_baseline": {"value": value, "unit": "px/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "px/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
