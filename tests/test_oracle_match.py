@@ -127,6 +127,53 @@ def test_propagation_order_on_tied_costs(orc, iters):
             assert sum((x, y) not in want for y in range(H) for x in range(W)) == 20  # the (odd, odd) pixels
 
 
+def _rs_offset(r, n):
+    # reading D5: j = mulhi(r, 4 n), offset = floor((j + 1) / 2) - n
+    j = (int(r) * 4 * n) >> 32
+    return (j + 1) // 2 - n
+
+
+def _first_accepted(orc, seed, scale, mirror, iters, need):
+    """Offsets of the first random-search draw of pixel 0 whose u offset is
+    at least `need` (counter = (pixel 0, iteration, scale + 4 pass, 0), key =
+    the seed's two words), with d0, d1 clamped at 0; None if no iteration's is."""
+    key = np.array([seed & 0xffffffff, seed >> 32], np.uint32)
+    n = 1 << scale
+    for it in range(iters):
+        o = [_rs_offset(r, n) for r in orc.philox4x32_10(np.array([0, it, scale + 4 * mirror, 0], np.uint32), key)]
+        if o[0] >= need:
+            return (o[0], o[1], max(0, o[2]), max(0, o[3]))
+    return None
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 12345, 2 ** 40 + 7])
+def test_random_search_draws(orc, seed):
+    # a 2 x 1 image, two scales.  The coarsest grid holds only pixel 0, which
+    # has no predecessors, and its best temporal target (x = 1, cost 0; x = 0
+    # costs 100) is off that grid: only random search can move it, and it
+    # does at the first draw that reaches x = 1, with all four offsets of
+    # that draw.  At full resolution pixel 1 then copies pixel 0.  When no
+    # coarse draw reaches x = 1, pixel 1 takes pixel 0's initial vector
+    # (target x = 1 from there) and pixel 0 waits for a full-resolution draw.
+    ref = np.zeros((2, 1, 2, 48), np.int8)
+    ref[..., 0] = 10
+    tmp = np.zeros((2, 1, 2, 48), np.int8)
+    tmp[:, :, 1, 0] = 10
+    for mirror in (0, 1):
+        for iters in (1, 3, 12):
+            p = orc.default_params(num_scales=2, iterations=iters)
+            fld, cost = orc.match_views(ref, tmp, ref, ref, mirror, seed, p)
+            got = [tuple(int(v) for v in fld[0, x]) for x in range(2)]
+            coarse = _first_accepted(orc, seed, 1, mirror, iters, 1)
+            if coarse is not None:
+                assert got == [coarse, coarse], (mirror, iters)
+                assert list(cost[0]) == [0, 0]
+                continue
+            fine = _first_accepted(orc, seed, 0, mirror, iters, 1)
+            assert got == [fine or (0, 0, 0, 0), (0, 0, 0, 0)], (mirror, iters)
+            assert list(cost[0]) == [0 if fine else 100, 0]
+
+
 def test_init_knn_leaves(orc):
     # with K_T = 4 the chosen temporal match is one of the 4 nearest grid points
     imgs = scenegen.random_images(40, 24, 22)
