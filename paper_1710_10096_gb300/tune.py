@@ -61,12 +61,21 @@ def save_cache(path: str) -> None:
         json.dump({f"{k[0]}|{','.join(map(str, k[1]))}": v for k, v in _CACHE.items()}, f, indent=1)
 
 
-def load_cache(path: str) -> None:
+def load_cache(path: str) -> int:
+    """Adds the tunings of a file written by save_cache; entries that this
+    build does not support (another build's tuning space) are skipped.
+    Returns the number of entries taken."""
     if not os.path.exists(path):
-        return
-    for k, v in json.load(open(path)).items():
+        return 0
+    with open(path) as f:
+        entries = json.load(f)
+    taken = 0
+    for k, v in entries.items():
         b, p = k.split("|")
-        _CACHE[(b, tuple(int(x) for x in p.split(",")))] = tuple(v)
+        if tuple(v) in TUNING_SPACE:
+            _CACHE[(b, tuple(int(x) for x in p.split(",")))] = tuple(v)
+            taken += 1
+    return taken
 
 
 __all__ = ["autotune", "size_bucket", "save_cache", "load_cache", "default_tuning"]
