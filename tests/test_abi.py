@@ -159,3 +159,47 @@ def test_extension_rows_without_gpu(sff):
                                   fake, fake, fake, ws, null) == -1  # phi not 16-byte aligned
     assert L.sff_match_views_sift(fake, fake, fake, fake, fake, fake, fake, fake, 64, 48, 0, 1, P, fake, fake, fake,
                                   0, null) == -3
+
+
+def test_batch_arguments_without_gpu(sff):
+    # sff_run_batch checks every quad before its first launch; each call
+    # below carries at least one invalid field, so none reaches CUDA
+    L = sff.lib()
+    p = sff.default_params()
+    P = ctypes.byref(p)
+    null = ctypes.c_void_p(0)
+    w, h = 64, 48
+    qws = sff.quad_workspace_bytes(w, h, p)
+    assert qws > 0
+
+    def quad(**over):
+        q = sff.QuadDesc()
+        for k in range(4):
+            q.rgb[k] = 0x10000
+            q.pyramid[k] = 0x20000
+        q.pitch_bytes, q.width, q.height, q.seed = 3 * w, w, h, 1
+        q.fwd, q.fwd_cost, q.inv, q.inv_cost = 0x30000, 0x40000, 0x50000, 0x60000
+        q.keep, q.cerr, q.seeds, q.capacity, q.count = 0x70000, 0x80000, 0x90000, 400, 0xa0000
+        q.workspace, q.workspace_bytes = 0xb0000, qws
+        for k, v in over.items():
+            setattr(q, k, v)
+        return q
+
+    def run(quads, params=P):
+        arr = (sff.QuadDesc * max(1, len(quads)))(*quads)
+        return L.sff_run_batch(arr, len(quads), params, None, null)
+
+    bad_quads = [dict(width=7), dict(pitch_bytes=3 * w - 1), dict(workspace=0), dict(capacity=-1), dict(fwd=0),
+                 dict(count=0), dict(seeds=0), dict(fwd=0x30004), dict(fwd_cost=0x40002), dict(workspace=0xb0010)]
+    for over in bad_quads:
+        assert run([quad(**over)]) == -1, over
+    assert run([quad(workspace_bytes=qws - 1)]) == -3
+    # a bad quad after a good one is still caught before any launch
+    assert run([quad(), quad(keep=0)]) == -1
+    assert run([quad(), quad(workspace_bytes=16)]) == -3
+    # the batch itself
+    assert L.sff_run_batch(None, 1, P, None, null) == -1
+    assert run([]) == -1
+    assert run([quad(width=7)] * (sff.MAX_BATCH + 1)) == -1
+    bad = sff.default_params(num_scales=9)
+    assert run([quad(width=7)], ctypes.byref(bad)) == -1
