@@ -20,7 +20,11 @@ _SRC = os.path.join(_HERE, "sff_oracle.c")
 _SRC_INTERP = os.path.join(_HERE, "sff_interp_oracle.c")
 _SRC_SGM = os.path.join(_HERE, "sff_sgm_oracle.c")
 _SRC_SIFT = os.path.join(_HERE, "sff_sift_oracle.c")
-_LIB = os.path.join(_HERE, "liboracle.so")
+SOURCES = (_SRC, _SRC_INTERP, _SRC_SGM, _SRC_SIFT)
+# SFF_ORACLE_LIB names a library built elsewhere by compile_library() (the
+# planted-mistake tests load a deliberately broken copy this way)
+_PREBUILT = os.environ.get("SFF_ORACLE_LIB")
+_LIB = _PREBUILT or os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 NF = 48
@@ -48,18 +52,25 @@ SEED_DTYPE = np.dtype([("x", "<i2"), ("y", "<i2"), ("u", "<i2"), ("v", "<i2"), (
 assert SEED_DTYPE.itemsize == 20
 
 
+def compile_library(sources, out: str) -> str:
+    """gcc (OpenMP) of the given C files into the shared library `out`."""
+    tmp = out + f".tmp{os.getpid()}"
+    # no contracted multiply-adds: the float and double sums follow their
+    # written order, as the CUDA path's do; explicit fma() calls stay (only
+    # where a reading names them), correctly rounded
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11", "-ffp-contract=off", *sources,
+                           "-lm", "-o", tmp])
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle into oracle/liboracle.so (gcc, OpenMP)."""
-    newest = max(os.path.getmtime(p) for p in (_SRC, _SRC_INTERP, _SRC_SGM, _SRC_SIFT, __file__))
+    if _PREBUILT:
+        return _LIB
+    newest = max(os.path.getmtime(p) for p in (*SOURCES, __file__))
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
-        tmp = _LIB + f".tmp{os.getpid()}"
-        # no contracted multiply-adds: the float and double sums follow their
-        # written order, as the CUDA path's do; explicit fma() calls stay
-        # (only where a reading names them), correctly rounded
-        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11", "-ffp-contract=off", _SRC,
-                               _SRC_INTERP, _SRC_SGM, _SRC_SIFT, "-lm",
-                               "-o", tmp])
-        os.replace(tmp, _LIB)
+        compile_library(SOURCES, _LIB)
     return _LIB
 
 
