@@ -150,6 +150,20 @@ MUTATIONS = [
     ("bias sign", SIFT, "phi[p * 4 + c] = t - bias[c];", "phi[p * 4 + c] = t + bias[c];", "tests/test_oracle_sift.py"),
     ("axis sign convention", SIFT, "const double sg = v[big] < 0.0 ? -1.0 : 1.0;",
      "const double sg = v[big] < 0.0 ? 1.0 : -1.0;", "tests/test_oracle_sift.py"),
+    ("cost window 5 x 5", SIFT, "    for (int j = -3; j <= 3; j++)\n        for (int i = -3; i <= 3; i++) {\n"
+     "            const int x = px + i * n, y = py + j * n;",
+     "    for (int j = -2; j <= 2; j++)\n        for (int i = -2; i <= 2; i++) {\n"
+     "            const int x = px + i * n, y = py + j * n;", "tests/test_oracle_sift.py"),
+    ("cost window at stride 1", SIFT, "const int x = px + i * n, y = py + j * n;", "const int x = px + i, y = py + j;",
+     "tests/test_oracle_sift.py"),
+    ("cost without the cross view", SIFT, "            c = c + dist3(a, r);\n", "", "tests/test_oracle_sift.py"),
+    ("cost cross view shifted by d0", SIFT,
+     "clampi(x + u[0] - sigma * u[3], 0, w - 1)) * 4;", "clampi(x + u[0] - sigma * u[2], 0, w - 1)) * 4;",
+     "tests/test_oracle_sift.py"),
+    ("squared distances", SIFT, "return sqrtf((dx * dx + dy * dy) + dz * dz);", "return (dx * dx + dy * dy) + dz * dz;",
+     "tests/test_oracle_sift.py"),
+    ("third component dropped", SIFT, "return sqrtf((dx * dx + dy * dy) + dz * dz);", "return sqrtf(dx * dx + dy * dy);",
+     "tests/test_oracle_sift.py"),
     # dense interpolation
     ("Y from cx", INTERP, "X[1] = (y - P->cy) * Z / P->focal;", "X[1] = (y - P->cx) * Z / P->focal;",
      "tests/test_oracle_interp.py"),
