@@ -35,6 +35,10 @@ SCENE_SEED = 2
 MATCH_SEED = 2024
 METRIC = "4-view matched px/s per GB300 (bit-exact), batched vs plain; serving p50/p99 ms"
 L2_FLUSH_BYTES = 256 << 20
+# Method parameters of both arms: the paper's k = 3 subscales, 12 iterations,
+# tau_c = 1, s_c = 150 (Sec. 5) and the readings of the points it leaves open
+PARAMS = dict(num_scales=4, iterations=12, tau_c=1, region_min=150, tau_r=1, quant_shift=4, knn_temporal=4,
+              knn_epipolar=2)
 FALLBACK_HBM_GBS = 6800.0
 
 # Algorithmic bytes per unit of work of each kernel (units in `_units`):
@@ -173,6 +177,36 @@ def _units(kernel: str, w: int, h: int, params) -> float:
     return 0.0
 
 
+def merge_scales(prof):
+    """Per-kernel totals {name: (launches, ms)} with the per-scale marks of a
+    kernel ("name/s<scale>") summed under its name, and those per-scale
+    entries separately: {name: {scale: (launches, ms)}}."""
+    merged, per_scale = {}, {}
+    for name, (n, ms) in prof.items():
+        base, sep, sc = name.partition("/s")
+        if sep:
+            per_scale.setdefault(base, {})[int(sc)] = (n, ms)
+        a = merged.get(base, (0, 0.0))
+        merged[base] = (a[0] + n, a[1] + ms)
+    return merged, per_scale
+
+
+def iteration_scales(per_scale, w, h, n_fields, peak):
+    """Per-scale roofline of the propagation kernel: algorithmic bytes per
+    launch (ALGO_BYTES per grid pixel, every grid pixel of every field once
+    per launch) over the average launch time."""
+    out = []
+    for s, (n, ms) in sorted(per_scale.items()):
+        st = 1 << s
+        grid = ((w + st - 1) // st) * ((h + st - 1) // st)
+        b = ALGO_BYTES["k_iteration"] * n_fields * grid
+        us = 1e3 * ms / n
+        out.append({"scale": s, "grid_px": n_fields * grid, "launches": n, "avg_launch_us": us,
+                    "algo_mb_per_launch": b / 1e6, "achieved_gbs": b / (us * 1e-6) / 1e9,
+                    "frac": b / (us * 1e-6) / 1e9 / peak})
+    return out
+
+
 def cpu_baseline(q, seed, target_s=12.0):
     import oracle
     oracle.build()
@@ -183,7 +217,7 @@ def cpu_baseline(q, seed, target_s=12.0):
     t_all = time.perf_counter()
     while True:
         t0 = time.perf_counter()
-        ref = oracle.run_quad(*q.images(), seed=seed)
+        ref = oracle.run_quad(*q.images(), seed=seed, params=oracle.default_params(**PARAMS))
         times.append(time.perf_counter() - t0)
         if time.perf_counter() - t_all > target_s or len(times) >= 8:
             break
@@ -253,13 +287,31 @@ def bench_batched(sff, torch, dev, quads, seeds, params, tuning, steps, warmup):
 
     t_batch = timed(g_batch.replay)
     t_plain = timed(lambda: [g.replay() for _, g in plain])
+    # per-kernel (and per-scale) breakdown of the batched graph: one replay of
+    # a second capture with event spans around the launches
+    s = torch.cuda.Stream(device=dev)
+    sff.profile_enable(True)
+    try:
+        gp = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gp, stream=s):
+            bm.run(seeds, torch.cuda.current_stream(dev))
+        gp.replay()
+        s.synchronize()
+        bprof, bscales = merge_scales(sff.profile_collect())
+    finally:
+        sff.profile_enable(False)
+    del gp
+    breakdown = {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(bprof.items(), key=lambda kv: -kv[1][1])}
+    per_scale = {f"s{sc}": {"launches": n, "ms": ms, "avg_launch_us": 1e3 * ms / n}
+                 for sc, (n, ms) in sorted(bscales.get("k_iteration", {}).items())}
     same = all(bq.seeds_numpy().tobytes() == m.buf.seeds_numpy().tobytes()
                and torch.equal(bq.fwd, m.fwd) and torch.equal(bq.inv, m.inv) for bq, (m, _) in zip(bm.quads, plain))
     out = {"workload": "32 quads: 8 x 1242x375 + 8 x 1024x436 (driving scenes), 8 x 640x192 + 8 x 512x160 "
                        "(planes scenes), scene seeds 100..131",
            "px_per_step": px, "value": px / t_batch, "unit": "px/s", "ms_per_step": 1e3 * t_batch,
            "plain_value": px / t_plain, "plain_ms_per_step": 1e3 * t_plain, "speedup_vs_plain": t_plain / t_batch,
-           "identical_to_plain": bool(same), "cuda_graph": True}
+           "identical_to_plain": bool(same), "cuda_graph": True,
+           "kernels_ms": breakdown, "k_iteration_per_scale": per_scale}
     del bm, plain, g_batch
     torch.cuda.empty_cache()
     return out
@@ -702,6 +754,35 @@ def combine_ranks(t_step: float, px_per_rank: int, world: int, device=None):
     return t_step, px_per_rank / t_step
 
 
+def workload_config(workload, q, params, world):
+    """The work of one step, identical in both arms' lines: what is matched,
+    with which parameters and seeds, and the cache condition of the timing."""
+    return {"workload": workload, "width": q.width, "height": q.height, "quads_per_step": 1,
+            "parallelism": f"replicas{world}", "params": dict(params), "scene_seed": SCENE_SEED,
+            "match_seed": MATCH_SEED,
+            "l2": "GPU arm: L2 flushed between timed steps (256 MB write outside the step events)"}
+
+
+def summary(line):
+    """The headline figures of the line, repeated at its end."""
+    out = {"value_mpx_s": line["value"] / 1e6, "e2e_mpx_s": line["e2e"]["value"] / 1e6,
+           "roofline_frac": (line.get("roofline") or {}).get("frac"),
+           "per_scale_frac": [round(r["frac"], 3) for r in (line.get("roofline") or {}).get("per_scale", [])],
+           "device_status": line.get("device_status"), "bit_exact": line.get("bit_exact")}
+    b = line.get("batched")
+    if b:
+        out.update(batched_mpx_s=b["value"] / 1e6, plain_per_quad_mpx_s=b["plain_value"] / 1e6,
+                   batched_speedup=b["speedup_vs_plain"], batched_identical=b["identical_to_plain"])
+    sv = line.get("serving")
+    if sv:
+        for rate in ("rate_400", "rate_50"):
+            if rate in sv:
+                r = sv[rate]
+                out[f"serving_{rate[5:]}_p50_p99_ms"] = [r["continuous"]["p50_ms"], r["continuous"]["p99_ms"]]
+                out[f"serving_{rate[5:]}_plain_p50_p99_ms"] = [r["plain"]["p50_ms"], r["plain"]["p99_ms"]]
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
@@ -711,10 +792,12 @@ def run_reference(args):
     cores = os.cpu_count() or 1
     oracle.set_threads(cores)
     q = scenegen.make_named(args.workload, SCENE_SEED)
+    # the CUDA arm's parameters, passed explicitly
+    op = oracle.default_params(**PARAMS)
     # calibrate on one warm-up; shrink each step to a band of rows if the whole
     # run would exceed about two minutes
     t0 = time.perf_counter()
-    oracle.run_quad(*q.images(), seed=MATCH_SEED)
+    oracle.run_quad(*q.images(), seed=MATCH_SEED, params=op)
     t_full = time.perf_counter() - t0
     rows = q.height
     budget = 120.0
@@ -722,11 +805,11 @@ def run_reference(args):
         rows = max(48, int(q.height * budget / ((args.steps + args.warmup) * t_full)))
     imgs = [im[:rows].copy() for im in q.images()]
     for _ in range(max(0, args.warmup - 1)):
-        oracle.run_quad(*imgs, seed=MATCH_SEED)
+        oracle.run_quad(*imgs, seed=MATCH_SEED, params=op)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.run_quad(*imgs, seed=MATCH_SEED)
+        oracle.run_quad(*imgs, seed=MATCH_SEED, params=op)
         times.append(time.perf_counter() - t0)
     px = q.width * rows
     value = px / statistics.mean(times)
@@ -735,7 +818,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "px/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
-            "config": {"workload": args.workload, "width": q.width, "height": rows, "quads_per_step": 1},
+            "config": dict(workload_config(args.workload, q, PARAMS, 1), height=rows),
             "cpu_baseline": {"value": value, "unit": "px/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "px/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -758,7 +841,7 @@ def main():
     sff.build()
 
     q = scenegen.make_named(args.workload, SCENE_SEED + rank)
-    params = sff.default_params()
+    params = sff.default_params(**PARAMS)
     # work distribution of the propagation kernels: autotuned once per image
     # size (any setting gives bit-identical results)
     from paper_1710_10096_gb300 import tune
@@ -769,6 +852,9 @@ def main():
         del probe
     else:
         tuning = sff.make_tuning(*(int(v) for v in args.tuning.split(",")))
+    # the batch and the server take the tuned scale-0 variant with the coarse
+    # scales derived from their (much larger) launch sizes
+    batch_tuning = sff.make_tuning(tuning.lanes_per_pixel, tuning.tile_x, tuning.tile_y, tuning.slots)
     m = sff.QuadMatcher(q.width, q.height, params, device=dev, tuning=tuning)
     stream = torch.cuda.Stream(device=dev)
     host_in = torch.empty((4, q.height, q.width, 3), dtype=torch.uint8).pin_memory()
@@ -793,7 +879,7 @@ def main():
                 m.run(*dev_in.unbind(0), seed=MATCH_SEED, stream=torch.cuda.current_stream())
         pgraph.replay()
         stream.synchronize()
-        prof = sff.profile_collect()
+        prof, prof_scales = merge_scales(sff.profile_collect())
         sff.profile_enable(False)
         del pgraph
 
@@ -807,6 +893,7 @@ def main():
         for _ in range(args.warmup):
             graph.replay()
         stream.synchronize()
+    sff.device_status(stream, reset=True)  # conditions of the set-up runs (none expected) cleared
     if world > 1:
         torch.distributed.barrier()
     clocks = ClockSampler(local)
@@ -838,6 +925,9 @@ def main():
             if k >= args.warmup:
                 e2e_times.append(time.perf_counter() - t0)
     n_seeds = int(host_count.item())
+    # device-side conditions of every run above (bounded waits, seed capacity)
+    dev_status = sff.device_status(stream, reset=True)
+    dev_timeouts = sff.device_timeouts(reset=True)
     e2e = {"value": combine_ranks(statistics.mean(e2e_times), px, world, dev)[1], "unit": "px/s",
            "h2d_bytes_per_step": int(host_in.numel()), "d2h_bytes_per_step": int(m.seeds.numel() + 4)}
 
@@ -855,6 +945,9 @@ def main():
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": tr, "peak_source": peak_src,
                 "algo_bytes_per_launch": bytes_per_launch, "avg_launch_us": 1e3 * dom_ms / dom_launches}
+        if dom in prof_scales:
+            sc = {s: (n / prof_steps, ms / prof_steps) for s, (n, ms) in prof_scales[dom].items()}
+            roof["per_scale"] = iteration_scales(sc, q.width, q.height, 2, peak)
     total_prof = sum(v[1] for v in prof.values())
     kernels = {k: {"launches_per_step": v[0] / prof_steps, "ms_per_step": v[1] / prof_steps,
                    "share": v[1] / total_prof} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
@@ -862,13 +955,13 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "px/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int8", "data": "synthetic",
-            "config": {"workload": args.workload, "width": q.width, "height": q.height, "quads_per_step": 1,
-                       "parallelism": f"replicas{world}", "cuda_graph": True,
-                       "l2": "flushed between timed steps (256 MB write outside the step events)",
-                       "params": params.as_dict(), "scene_seed": SCENE_SEED, "match_seed": MATCH_SEED,
-                       "tuning": {"lanes_per_pixel": tuning.lanes_per_pixel, "tile": [tuning.tile_x, tuning.tile_y]}},
+            "config": workload_config(args.workload, q, params.as_dict(), world),
+            "launch": {"cuda_graph": True,
+                       "tuning_per_scale": [list(v) for v in tuning.scale_variants()],
+                       "tuning_fields": "(lanes per pixel, candidate slots, tile_x, tile_y) of scales 0..3"},
             "roofline": roof, "gpu_launches": int(round(launches_per_step * args.steps)),
-            "e2e": e2e, "clocks": clk, "kernels": kernels, "seeds": n_seeds}
+            "e2e": e2e, "clocks": clk, "kernels": kernels, "seeds": n_seeds,
+            "device_status": sff.lib().sff_status_string(dev_status).decode(), "device_timeouts": dev_timeouts}
     if not args.no_paper_order:
         line["paper_order"] = bench_paper_order(sff, torch, dev, m, q, params)
     if not args.no_interp:
@@ -882,17 +975,19 @@ def main():
     if not args.no_sift:
         line["sift_cost"] = bench_sift(sff, torch, dev, m, q, params, 3, 1)
     if batch is not None:
-        line["batched"] = bench_batched(sff, torch, dev, batch[0], batch[1], params, tuning, min(args.steps, 20),
-                                        max(1, args.warmup))
+        line["batched"] = bench_batched(sff, torch, dev, batch[0], batch[1], params, batch_tuning,
+                                        min(args.steps, 20), max(1, args.warmup))
         if not args.no_serving:
-            line["serving"] = bench_serving(sff, torch, dev, batch[0], params, tuning)
+            line["serving"] = bench_serving(sff, torch, dev, batch[0], params, batch_tuning)
     if rank == 0 and not args.no_cpu_baseline:
         cb, ref = cpu_baseline(q, MATCH_SEED)
         line["cpu_baseline"] = cb
         got = sff.seeds_to_numpy(host_seeds.numpy(), min(n_seeds, m.capacity))
         line["bit_exact"] = bool(got.tobytes() == ref["seeds"].tobytes() and n_seeds == len(ref["seeds"])
                                  and np.array_equal(m.fwd.cpu().numpy(), ref["fwd"])
-                                 and np.array_equal(m.inv.cpu().numpy(), ref["inv"]))
+                                 and np.array_equal(m.inv.cpu().numpy(), ref["inv"])
+                                 and dev_status == sff.OK and dev_timeouts == 0)
+    line["summary"] = summary(line)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -56,6 +56,8 @@ extern "C" {
 #define SFF_ERR_ARG (-1)        /* invalid argument (null pointer, size, alignment, params) */
 #define SFF_ERR_CUDA (-2)       /* a CUDA launch or API call failed */
 #define SFF_ERR_WORKSPACE (-3)  /* workspace smaller than sff_workspace_bytes() */
+#define SFF_ERR_TIMEOUT (-4)    /* a bounded device-side wait gave up (sff_device_status) */
+#define SFF_ERR_CAPACITY (-5)   /* a seed buffer was too small (sff_device_status) */
 
 #define SFF_FEATURES 48         /* int8 features per pixel and scale: 3 channels x 16 */
 #define SFF_FEATURE_BYTES 48    /* bytes of one feature record */
@@ -80,13 +82,32 @@ typedef struct sff_params {
 
 /* Work distribution of the propagation kernels (no counterpart in the paper).
  * Every supported setting gives bit-identical results; only speed differs.
- * Supported: lanes_per_pixel in {1, 2, 4} x (tile_x, tile_y) in
- * {(64, 16), (32, 16), (64, 8), (32, 8), (16, 8), (8, 8)} grid pixels.  The
- * tile is used at scale 0 (and at coarser scales whose grid it splits into
- * at least two CTAs per SM; otherwise the largest smaller tile that does). */
+ * A variant of the iteration kernel is (lanes, slots, tile_x, tile_y):
+ *   slots = 0: the throughput form, `lanes` in {1, 2, 4} threads sharing one
+ *              pixel's feature loads, tile in {(64, 16), (32, 16), (64, 8),
+ *              (32, 8), (16, 8), (8, 8)} grid pixels;
+ *   slots = 1 or 4: the latency form (the next pixel's loads and the random
+ *              draws issued up front, the colour-1 random search scored with
+ *              the propagation candidates), each candidate of an update on
+ *              `slots` == 4 ? its own `lanes` lanes : all lanes; only the
+ *              tiles for which lanes * slots * (tile_x / 2 + 1) * (tile_y + 1)
+ *              threads (one group per colour-0 slot of the tile and its halo)
+ *              fit 1024.
+ * Scale 0 takes (lanes_per_pixel, slots, tile_x, tile_y).  Scale s >= 1
+ * takes coarse[s - 1] = {lanes, slots, tile_x, tile_y}; all four zero means
+ * derived from the grid size: (1, 4, 16, 8) below 200 grid pixels per SM
+ * over all fields of the launch, else (1, 0, 32, 16).
+ * sff_tuning_supported() checks a setting. */
 typedef struct sff_tuning {
     int32_t lanes_per_pixel; /* threads that share one pixel's feature loads */
     int32_t tile_x, tile_y;  /* grid pixels per CTA of the iteration kernel */
+    int32_t slots;           /* 0: throughput form; 1 or 4: latency form */
+    int32_t coarse[3][4];    /* scales 1..3: {lanes, slots, tile_x, tile_y}, or all 0 */
+    int32_t group_mb;        /* sweep schedule of scale 0 when a launch holds several quads
+                              * (sff_run_batch): 0 = every iteration launch covers all of them;
+                              * > 0 = all iterations for one group of consecutive quads, then
+                              * the next, each group's four-image records and field state at
+                              * most group_mb MiB (a quad larger than that alone); 0..2^20 */
 } sff_tuning;
 
 /* One seed of Sec. 3.2: pixel (x, y) of L0, its vector and its scores. 20 bytes.
@@ -474,9 +495,49 @@ int sff_profile_enable(int32_t on);
 int sff_profile_collect(sff_kernel_time* out, int32_t capacity, int32_t* n_out);
 
 /* Number of device-side bounded waits (on the completion of the library's own
- * asynchronous copies) that gave up since the last reset; nonzero means a
- * result is invalid.  Synchronises the current device.  Host pointer. */
+ * asynchronous copies and tensor-core operations) that gave up since the last
+ * reset; nonzero means a result is invalid.  reset also clears the drain count
+ * below.  Synchronises the current device.  Host pointer. */
 int sff_device_timeouts(uint32_t* out, int32_t reset);
+
+/* Of those, the drains that gave up: waits, after a failure, for copies and
+ * MMAs already issued (which always complete) before the tensor memory is
+ * released.  Each drain waits ten times the normal limit; a nonzero count
+ * means the hardware did not finish issued work within it.  Host pointer. */
+int sff_device_drain_timeouts(uint32_t* out);
+
+/* Device-side error status, read at synchronisation (the calls themselves
+ * only enqueue work and cannot see it).  Waits for the work enqueued on
+ * `stream` (a cudaStream_t, NULL = legacy default stream), then reports the
+ * conditions that kernels of this library raised on the current device since
+ * the last reset:
+ *   SFF_ERR_TIMEOUT   a bounded device wait gave up (the temporal K-NN's
+ *                     waits on its bulk copies and MMAs): the fields, and
+ *                     everything computed from them, of the calls since the
+ *                     last reset are invalid (their pixels may be empty,
+ *                     never out of bounds);
+ *   SFF_ERR_CAPACITY  otherwise, if sff_emit_seeds / sff_emit_seeds_geo /
+ *                     sff_run_batch found more seeds than a seed buffer's
+ *                     capacity: the first `capacity` seeds were written and
+ *                     the count holds the number needed;
+ *   SFF_OK            neither;  SFF_ERR_CUDA if the read or the
+ *                     synchronisation failed.
+ * reset != 0 clears both conditions after reading them.  The conditions are
+ * per device and shared by all streams: a condition may come from another
+ * stream's call that completed first.  Not for use while `stream` is being
+ * captured into a CUDA graph (it synchronises). */
+int sff_device_status(void* stream, int32_t reset);
+
+/* Failure injection for tests of the device-side error path (no counterpart
+ * in the paper).  step >= 0: in every later launch of the temporal K-NN
+ * kernel the thread that issues the tensor-core MMAs stops before the MMAs of
+ * that step (tile visit; 2 per candidate tile) and issues nothing further, so
+ * the waits on that step's results run out; nothing issued is left in
+ * flight.  step = -1: off.  wait_limit_us > 0 sets the time limit of every
+ * bounded device wait (drains: ten times it); 0 restores the default of 1 s.
+ * Applies to the current device; synchronous.  SFF_ERR_ARG for step < -1 or
+ * wait_limit_us < 0. */
+int sff_debug_knn_withhold(int32_t step, int32_t wait_limit_us);
 
 /* Human-readable name of a status code (static string). */
 const char* sff_status_string(int status);

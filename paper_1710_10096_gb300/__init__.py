@@ -34,7 +34,16 @@ _lib = None
 
 
 class SffError(RuntimeError):
-    pass
+    """A library call failed; `status` holds its SFF_ERR_* code (None for
+    checks of the binding itself)."""
+
+    def __init__(self, msg: str, status: int = None):
+        super().__init__(msg)
+        self.status = status
+
+
+# status codes of include/sff.h
+OK, ERR_ARG, ERR_CUDA, ERR_WORKSPACE, ERR_TIMEOUT, ERR_CAPACITY = 0, -1, -2, -3, -4, -5
 
 
 class Params(ctypes.Structure):
@@ -49,13 +58,34 @@ class Params(ctypes.Structure):
 
 class Tuning(ctypes.Structure):
     """sff_tuning of include/sff.h: work distribution, never changes results."""
-    _fields_ = [("lanes_per_pixel", ctypes.c_int32), ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32)]
+    _fields_ = [("lanes_per_pixel", ctypes.c_int32), ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32),
+                ("slots", ctypes.c_int32), ("coarse", (ctypes.c_int32 * 4) * 3), ("group_mb", ctypes.c_int32)]
 
     def as_tuple(self):
+        """(lanes, tile_x, tile_y) of scale 0 (the throughput-form space)."""
         return (self.lanes_per_pixel, self.tile_x, self.tile_y)
 
+    def scale_variants(self):
+        """[(lanes, slots, tile_x, tile_y)] of scales 0..3; (0, 0, 0, 0) = derived."""
+        return [(self.lanes_per_pixel, self.slots, self.tile_x, self.tile_y)] + \
+            [tuple(self.coarse[k][j] for j in range(4)) for k in range(3)]
 
-TUNING_SPACE = [(l, tx, ty) for l in (1, 2, 4) for (tx, ty) in ((64, 16), (32, 16), (64, 8), (32, 8), (16, 8), (8, 8))]
+
+TILES = ((64, 16), (32, 16), (64, 8), (32, 8), (16, 8), (8, 8))
+TUNING_SPACE = [(l, tx, ty) for l in (1, 2, 4) for (tx, ty) in TILES]
+
+
+def _lat_fits(group: int, tx: int, ty: int) -> bool:
+    # one group of lanes per colour-0 slot of the (tx + 1) x (ty + 1) region
+    return (group * ((tx + 2) // 2) * (ty + 1) + 31) // 32 * 32 <= 1024
+
+
+# Every variant (lanes, slots, tile_x, tile_y) of the iteration kernel: the
+# throughput form (slots 0) and the latency form (slots 1 or 4) on every tile
+# whose region fits one cell per lane group in 1024 threads.
+VARIANT_SPACE = [(l, 0, tx, ty) for l in (1, 2, 4) for (tx, ty) in TILES] + \
+    [(l, c, tx, ty) for (l, c) in ((1, 1), (2, 1), (4, 1), (1, 4), (2, 4), (4, 4)) for (tx, ty) in TILES
+     if _lat_fits(l * c, tx, ty)]
 
 
 class QuadDesc(ctypes.Structure):
@@ -183,6 +213,12 @@ def lib():
         L.sff_profile_collect.restype = i32
         L.sff_device_timeouts.argtypes = [ctypes.POINTER(ctypes.c_uint32), i32]
         L.sff_device_timeouts.restype = i32
+        L.sff_device_drain_timeouts.argtypes = [ctypes.POINTER(ctypes.c_uint32)]
+        L.sff_device_drain_timeouts.restype = i32
+        L.sff_device_status.argtypes = [ctypes.c_void_p, i32]
+        L.sff_device_status.restype = i32
+        L.sff_debug_knn_withhold.argtypes = [i32, i32]
+        L.sff_debug_knn_withhold.restype = i32
         L.sff_status_string.argtypes = [i32]
         L.sff_status_string.restype = ctypes.c_char_p
         _lib = L
@@ -191,7 +227,7 @@ def lib():
 
 def _check(status: int, what: str):
     if status != 0:
-        raise SffError(f"{what}: {lib().sff_status_string(status).decode()} ({status})")
+        raise SffError(f"{what}: {lib().sff_status_string(status).decode()} ({status})", status)
 
 
 def default_params(**overrides) -> Params:
@@ -312,10 +348,17 @@ def default_tuning() -> Tuning:
     return t
 
 
-def make_tuning(lanes: int, tile_x: int, tile_y: int) -> Tuning:
-    t = Tuning(lanes, tile_x, tile_y)
+def make_tuning(lanes: int, tile_x: int, tile_y: int, slots: int = 0, coarse=None, group_mb: int = 0) -> Tuning:
+    """sff_tuning: scale 0 (lanes, slots, tile); coarse = [(lanes, slots, tile_x, tile_y)] for
+    scales 1.. (None or (0, 0, 0, 0) entries: derived from the grid size); group_mb: the
+    batch's scale-0 sweep schedule (0: all quads in every launch)."""
+    t = Tuning(lanes, tile_x, tile_y, slots)
+    t.group_mb = int(group_mb)
+    for k, v in enumerate(coarse or []):
+        for j in range(4):
+            t.coarse[k][j] = int(v[j])
     if not lib().sff_tuning_supported(ctypes.byref(t)):
-        raise SffError(f"unsupported tuning {(lanes, tile_x, tile_y)}")
+        raise SffError(f"unsupported tuning {(lanes, tile_x, tile_y, slots, coarse)}")
     return t
 
 
@@ -481,6 +524,31 @@ def device_timeouts(reset: bool = False) -> int:
     v = ctypes.c_uint32(0)
     _check(lib().sff_device_timeouts(ctypes.byref(v), 1 if reset else 0), "sff_device_timeouts")
     return v.value
+
+
+def device_drain_timeouts() -> int:
+    """Of the waits that gave up, the drains of work already issued (0 unless
+    the hardware did not finish issued copies or MMAs within ten wait limits)."""
+    v = ctypes.c_uint32(0)
+    _check(lib().sff_device_drain_timeouts(ctypes.byref(v)), "sff_device_drain_timeouts")
+    return v.value
+
+
+def device_status(stream=None, reset: bool = False) -> int:
+    """sff_device_status: waits for `stream`, returns OK, ERR_TIMEOUT (a
+    bounded device wait gave up: results invalid), ERR_CAPACITY (a seed
+    buffer was too small) or ERR_CUDA."""
+    return int(lib().sff_device_status(_stream(stream), 1 if reset else 0))
+
+
+def check_device_status(stream=None, what: str = "device status") -> None:
+    """Raises SffError (with .status) unless device_status(stream, reset=True) is OK."""
+    _check(device_status(stream, reset=True), what)
+
+
+def debug_knn_withhold(step: int, wait_limit_us: int = 0) -> None:
+    """sff_debug_knn_withhold: failure injection for tests (step -1: off)."""
+    _check(lib().sff_debug_knn_withhold(int(step), int(wait_limit_us)), "sff_debug_knn_withhold")
 
 
 def seed_capacity(width: int, height: int) -> int:

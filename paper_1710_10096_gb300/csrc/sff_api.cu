@@ -60,6 +60,21 @@ extern "C" const char* sff_status_string(int status) {
         case SFF_ERR_ARG: return "invalid argument";
         case SFF_ERR_CUDA: return "CUDA error";
         case SFF_ERR_WORKSPACE: return "workspace too small";
+        case SFF_ERR_TIMEOUT: return "a bounded device wait gave up";
+        case SFF_ERR_CAPACITY: return "seed buffer too small";
         default: return "unknown status";
     }
+}
+
+extern "C" int sff_device_status(void* stream, int32_t reset) {
+    const cudaStream_t st = (cudaStream_t)stream;
+    unsigned m = 0, s = 0;
+    if (sff::match_status_read(st, &m, reset != 0) != SFF_OK) return SFF_ERR_CUDA;
+    if (sff::seeds_status_read(st, &s, reset != 0) != SFF_OK) return SFF_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return SFF_ERR_CUDA;
+    if (m | s) {
+        if ((m | s) & 1u) return SFF_ERR_TIMEOUT;
+        return SFF_ERR_CAPACITY;
+    }
+    return SFF_OK;
 }

@@ -226,9 +226,10 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
                bool sequential);
 
 // Optional per-kernel event timing (sff_profile_enable).  SFF_LAUNCH wraps
-// every kernel launch of the library.
+// every kernel launch of the library; a mark pair may also span `launches`
+// back-to-back launches of one kernel.
 bool profiling();
-void profile_mark(const char* name, cudaStream_t st, bool after);
+void profile_mark(const char* name, cudaStream_t st, bool after, int launches = 1);
 
 #define SFF_LAUNCH(kernel, grid, block, smem, stream, ...)                       \
     do {                                                                         \
@@ -236,6 +237,11 @@ void profile_mark(const char* name, cudaStream_t st, bool after);
         kernel<<<grid, block, smem, stream>>>(__VA_ARGS__);                      \
         if (::sff::profiling()) ::sff::profile_mark(#kernel, stream, true);      \
     } while (0)
+
+// Device-side condition words (sff_device_status): read and optionally
+// cleared in stream order.
+int match_status_read(cudaStream_t st, unsigned* out, bool reset);
+int seeds_status_read(cudaStream_t st, unsigned* out, bool reset);
 
 int check_size(int w, int h);
 int check_params(const sff_params* p);

@@ -224,16 +224,48 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
     return ok != 0;
 }
 
-// Bounded wait: gives up after kSpinLimit polls and reports false.
-constexpr int kSpinLimit = 1 << 22;
+// Bounded waits.  A wait gives up, reporting false, once `limit_ns` of
+// global time (%globaltimer) has passed since its first poll, or after
+// kMaxPolls polls, whichever comes first.  A wait on work this CTA never
+// issued (a failed producer) thus ends after about limit_ns.  The drains --
+// waits for bulk copies and MMAs already issued, which always complete --
+// take kDrainFactor times longer before giving up.
+constexpr long long kMaxPolls = 1ll << 30;
+constexpr unsigned long long kDefaultWaitNs = 1000000000ull;  // 1 s
+constexpr unsigned long long kDrainFactor = 10;
 
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
-    for (int k = 0; k < kSpinLimit; ++k)
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned long long limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (long long k = 0; k < kMaxPolls; ++k) {
         if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
     return false;
 }
 
 __device__ unsigned int g_wait_timeouts;  // bounded waits that gave up (read by sff_device_timeouts)
+__device__ unsigned int g_drain_timeouts;  // drains that gave up (work in flight not seen to finish)
+// Conditions raised since the last reset (read by sff_device_status):
+// bit 0 a bounded wait gave up (the field of that call is invalid).
+constexpr unsigned kStatusTimeout = 1u;
+__device__ unsigned int g_match_status;
+// Failure injection for tests (sff_debug_knn_withhold): the MMA issuer of
+// k_knn_tc stops before the MMAs of this step (-1: never), and the limit of
+// every bounded wait (0: kDefaultWaitNs).
+__device__ int g_withhold_step = -1;
+__device__ unsigned long long g_wait_limit_ns = 0;
+
+__device__ __forceinline__ void note_timeout() {
+    atomicAdd(&g_wait_timeouts, 1u);
+    atomicOr(&g_match_status, kStatusTimeout);
+}
 
 // tcgen05 helpers (tensor memory, MMA, commit, loads).
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -350,13 +382,14 @@ __device__ __noinline__ void tc_append_slow(unsigned enter, int mine, int idx, i
 // Bounded wait on an accumulator for a whole warp (lane 0 polls); false
 // (and the CTA's failure flag raised) on a timeout or when another warp
 // already failed.
-__device__ __forceinline__ bool scan_wait(uint64_t* bar, unsigned parity, volatile int* fail, int lane) {
+__device__ __forceinline__ bool scan_wait(uint64_t* bar, unsigned parity, volatile int* fail, int lane,
+                                          unsigned long long wait_ns) {
     bool ok = true;
-    if (lane == 0) ok = mbar_wait(bar, parity) && *fail == 0;
+    if (lane == 0) ok = mbar_wait(bar, parity, wait_ns) && *fail == 0;
     const bool failed = __shfl_sync(0xffffffffu, (int)ok, 0) == 0;
     if (failed && lane == 0) {
         *fail = 1;
-        atomicAdd(&g_wait_timeouts, 1u);
+        note_timeout();
     }
     return !failed;
 }
@@ -416,6 +449,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const __grid_constant_
     volatile int* fail = reinterpret_cast<volatile int*>(bars + 2 + 2 * kTcStages + 2 * kTcAcc);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned long long wait_ns = g_wait_limit_ns ? g_wait_limit_ns : kDefaultWaitNs;
+    const unsigned long long drain_ns = kDrainFactor * wait_ns;
     const int nt = (gq + kTcRows - 1) / kTcRows;  // candidate tiles
     const int steps = 2 * nt;                      // two passes
     const int rows = nt * kTcRows;
@@ -452,35 +487,44 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const __grid_constant_
             for (; issued < steps; ++issued) {
                 const int u = issued, s = u % kTcStages;
                 if (u >= kTcStages &&
-                    (*fail || !(ok = mbar_wait(&bar_empty[s], (unsigned)((u - kTcStages) / kTcStages) & 1u))))
+                    (*fail ||
+                     !(ok = mbar_wait(&bar_empty[s], (unsigned)((u - kTcStages) / kTcStages) & 1u, wait_ns))))
                     break;
                 mbar_expect_tx(&bar_a[s], kTcTileBytes);
                 bulk_copy_g2s(sA + s * kTcTileBytes, gC + (size_t)(u % nt) * kTcTileBytes, kTcTileBytes, &bar_a[s]);
             }
             if (!ok) {
                 *fail = 1;
-                atomicAdd(&g_wait_timeouts, 1u);
+                note_timeout();
             }
-            // let the copies in flight land before the CTA releases its memory
-            mbar_wait(bar_q, 0);
+            // drain: the copies in flight land before the CTA releases its
+            // memory (issued copies always complete)
+            bool drained = mbar_wait(bar_q, 0, drain_ns);
             for (int u = max(0, issued - kTcStages); u < issued; ++u)
-                mbar_wait(&bar_a[u % kTcStages], (unsigned)(u / kTcStages) & 1u);
+                drained = mbar_wait(&bar_a[u % kTcStages], (unsigned)(u / kTcStages) & 1u, drain_ns) && drained;
+            if (!drained) {
+                atomicAdd(&g_drain_timeouts, 1u);
+                note_timeout();
+            }
         }
         __syncwarp();
     } else if (warp == kTcMmaWarp) {
         // ---- MMAs (one thread)
         if (lane == 0) {
             int committed = 0;
-            bool ok = mbar_wait(bar_q, 0);
+            const int withhold = g_withhold_step;
+            bool ok = mbar_wait(bar_q, 0, wait_ns);
             const uint32_t qaddr = smem_addr(sQ);
             for (int u = 0; ok && u < steps; ++u) {
                 if (*fail) {
                     ok = false;
                     break;
                 }
+                if (u == withhold) break;  // failure injection: nothing of this step is issued
                 const int s = u % kTcStages, b = u % kTcAcc;
-                if (!(ok = mbar_wait(&bar_a[s], (unsigned)(u / kTcStages) & 1u))) break;
-                if (u >= kTcAcc && !(ok = mbar_wait(&bar_free[b], (unsigned)((u - kTcAcc) / kTcAcc) & 1u))) break;
+                if (!(ok = mbar_wait(&bar_a[s], (unsigned)(u / kTcStages) & 1u, wait_ns))) break;
+                if (u >= kTcAcc && !(ok = mbar_wait(&bar_free[b], (unsigned)((u - kTcAcc) / kTcAcc) & 1u, wait_ns)))
+                    break;
                 tc_fence_after();
                 const uint32_t aaddr = smem_addr(sA + s * kTcTileBytes);
 #pragma unroll
@@ -493,11 +537,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const __grid_constant_
             }
             if (!ok) {
                 *fail = 1;
-                atomicAdd(&g_wait_timeouts, 1u);
+                note_timeout();
             }
-            // the MMAs in flight finish before the tensor memory is released
-            if (committed > 0)
-                mbar_wait(&bar_mma[(committed - 1) % kTcAcc], (unsigned)((committed - 1) / kTcAcc) & 1u);
+            // drain: the MMAs in flight finish before the tensor memory is
+            // released (the last commit tracks every earlier MMA)
+            if (committed > 0 &&
+                !mbar_wait(&bar_mma[(committed - 1) % kTcAcc], (unsigned)((committed - 1) / kTcAcc) & 1u, drain_ns)) {
+                atomicAdd(&g_drain_timeouts, 1u);
+                note_timeout();
+            }
         }
         __syncwarp();
     } else {
@@ -517,7 +565,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const __grid_constant_
 #pragma unroll
             for (int j = 0; j < 32; ++j) mins[j] = kInfBits;
             for (int u = 0; u < nt && live; ++u) {
-                if (!(live = scan_wait(&bar_mma[u % kTcAcc], (unsigned)(u / kTcAcc) & 1u, fail, lane))) break;
+                if (!(live = scan_wait(&bar_mma[u % kTcAcc], (unsigned)(u / kTcAcc) & 1u, fail, lane, wait_ns)))
+                    break;
                 uint32_t v[32];
                 scan_load(trow, u % kTcAcc, v, bar_free, lane);
                 if (u * kTcRows + 32 * g + lane < gq) {  // not a padding row of the last tile
@@ -576,7 +625,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const __grid_constant_
         // buffer of (lane group, query), in increasing index order
         const unsigned lt = (1u << lane) - 1u;
         for (int u = nt; u < steps && live; ++u) {
-            if (!(live = scan_wait(&bar_mma[u % kTcAcc], (unsigned)(u / kTcAcc) & 1u, fail, lane))) break;
+            if (!(live = scan_wait(&bar_mma[u % kTcAcc], (unsigned)(u / kTcAcc) & 1u, fail, lane, wait_ns))) break;
             uint32_t v[32];
             scan_load(trow, u % kTcAcc, v, bar_free, lane);
             const int idx = (u - nt) * kTcRows + 32 * g + lane;
@@ -615,19 +664,23 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const __grid_constant_
         // ---- merge the four lane-group buffers (8 best each, in any order)
         // of each query (warp w: kTcRows / kTcScanWarps queries)
         asm volatile("bar.sync 1, %0;" ::"r"(kTcScanWarps * 32) : "memory");
-        if (live) {
-            for (int qq = 0; qq < kTcRows / kTcScanWarps; ++qq) {
-                const int q = warp * (kTcRows / kTcScanWarps) + qq;
-                if (q0 + q >= gq) break;
-                const int2 e = bufs[((size_t)(lane >> 3) * kTcRows + q) * kTcCap + (lane & 7)];
-                int rank = 0;
-#pragma unroll
-                for (int o = 0; o < 32; ++o) {
-                    const int od = __shfl_sync(0xffffffffu, e.x, o), oi = __shfl_sync(0xffffffffu, e.y, o);
-                    rank += (od < e.x) || (od == e.x && (oi < e.y || (oi == e.y && o < lane)));
-                }
-                if (rank < 8) A.best8[(size_t)(q0 + q) * 8 + rank] = e;
+        for (int qq = 0; qq < kTcRows / kTcScanWarps; ++qq) {
+            const int q = warp * (kTcRows / kTcScanWarps) + qq;
+            if (q0 + q >= gq) break;
+            if (!live) {
+                // after a failed wait the lists are empty: the queries start
+                // empty instead of reading stale candidate indices
+                if (lane < 8) A.best8[(size_t)(q0 + q) * 8 + lane] = make_int2(0x7fffffff, 0x7fffffff);
+                continue;
             }
+            const int2 e = bufs[((size_t)(lane >> 3) * kTcRows + q) * kTcCap + (lane & 7)];
+            int rank = 0;
+#pragma unroll
+            for (int o = 0; o < 32; ++o) {
+                const int od = __shfl_sync(0xffffffffu, e.x, o), oi = __shfl_sync(0xffffffffu, e.y, o);
+                rank += (od < e.x) || (od == e.x && (oi < e.y || (oi == e.y && o < lane)));
+            }
+            if (rank < 8) A.best8[(size_t)(q0 + q) * 8 + rank] = e;
         }
     }
     tc_fence_before();
@@ -698,7 +751,7 @@ __global__ void k_init_select(const __grid_constant__ Fields F, int n, int knn) 
     Vec4 best = {0, 0, 0, 0};
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        if (k >= knn || bd[k] == 0x7fffffff) break;
+        if (k >= knn || bd[k] == 0x7fffffff || bi[k] < 0 || bi[k] >= A.gq) break;
         const int tx = (bi[k] % gw) * n, ty = (bi[k] / gw) * n;
         int dxc, cx;
         warp_row_nearest(r, A.rec + (size_t)A.gq * 3, A.rec_n + A.gq, n, gw, bi[k] / gw, tx, V.sigma, lane, dxc, cx);
@@ -908,6 +961,7 @@ __host__ __device__ constexpr int iter_threads() {
 struct IterStep {
     int n, s, dx, dy, it;
     int last;  // the scale's last iteration: also the colour-0 search of this iteration (phase 3)
+    int f0;    // first field of the launch: blockIdx.z picks field f0 + blockIdx.z
 };
 
 template <int L, int TX, int TY>
@@ -916,7 +970,7 @@ __global__ void __launch_bounds__(iter_threads<L, TX, TY>()) k_iteration(const _
     constexpr int kGroups = iter_threads<L, TX, TY>() / L;
     __shared__ uint2 s_vec[kRegX * kRegY];
     __shared__ int s_cost[kRegX * kRegY];
-    const Field& A = pick(F);
+    const Field& A = F.f[H.f0 + blockIdx.z];
     const Views& V = A.V;
     const int q = threadIdx.x & (L - 1);
     const unsigned gmask = group_mask<L>();
@@ -1020,6 +1074,284 @@ __global__ void __launch_bounds__(iter_threads<L, TX, TY>()) k_iteration(const _
             const size_t si = (size_t)gy * gw + gx;
             A.field_out[si] = pack_vec(cur);
             A.cost_out[si] = c;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Latency-oriented form of the same iteration (identical results).  At the
+// coarse scales an SM holds few grid pixels and a launch lasts about as long
+// as one pixel's chain of dependent loads, so this form shortens the chain:
+//   - the colour-1 pixel's own state and reference record are loaded at the
+//     start, together with the colour-0 cell's, instead of after the barrier;
+//   - the random draws, which depend only on pixel, iteration, scale and
+//     field, are made while those loads are in flight;
+//   - colour 1's random-search candidate around the pixel's own vector (the
+//     candidate whenever propagation leaves the pixel unchanged) is scored
+//     together with the two predecessors; with four slots so is the one
+//     around the horizontal predecessor's vector.  Only when propagation took
+//     a vector whose search candidate was not scored is it scored afterwards.
+// The candidates of one update are spread over C slots of L lanes (C = 1:
+// all lanes score all candidates; C = 4: slot k scores candidate k), and the
+// comparisons always run in the plain kernel's order (random search before
+// propagation for colour 0, horizontal before vertical, strict less-than).
+// One region slot per L*C-lane group in each phase: a variant whose region
+// needs more than 1024 threads does not exist.
+struct RsOff {
+    int u, v, d0, d1;
+};
+
+__device__ __forceinline__ RsOff rs_draw(int n, int s, uint2 key, int mirror, int it, uint32_t pixel) {
+    const uint4 r = philox4x32_10(make_uint4(pixel, (uint32_t)it, (uint32_t)(s + 4 * mirror), 0u), key);
+    return RsOff{rs_offset(r.x, n), rs_offset(r.y, n), rs_offset(r.z, n), rs_offset(r.w, n)};
+}
+
+// Random-search candidate around base vector b; false when it equals b.
+__device__ __forceinline__ bool rs_from(const RsOff& o, const Vec4& b, Vec4& cand) {
+    cand.u = (int)(int16_t)(b.u + o.u);
+    cand.v = (int)(int16_t)(b.v + o.v);
+    cand.d0 = (int)(int16_t)max(0, b.d0 + o.d0);
+    cand.d1 = (int)(int16_t)max(0, b.d1 + o.d1);
+    return !same_vec(cand, b);
+}
+
+// Costs of the candidates k < K with valid[k] (the others get 0), their loads
+// in flight together.  Every lane of the group ends with every cost.
+template <int L, int C, int K>
+__device__ __forceinline__ void costs_of(const Views& V, const Slice<L>& a, int q, int slot, unsigned gmask, int x,
+                                         int y, const Vec4 (&cand)[K], const bool (&valid)[K], int (&cc)[K]) {
+    if constexpr (C == 1) {
+        int p[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) p[k] = valid[k] ? group_part<L>(V, a, q, x, y, cand[k]) : 0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) cc[k] = group_sum<L>(p[k], gmask);
+    } else {
+        static_assert(K <= C, "one candidate per slot");
+        Vec4 mine = cand[0];
+        bool ok = slot == 0 && valid[0];
+#pragma unroll
+        for (int k = 1; k < K; ++k)
+            if (slot == k) {
+                mine = cand[k];
+                ok = valid[k];
+            }
+        const int p = group_sum<L>(ok ? group_part<L>(V, a, q, x, y, mine) : 0, gmask);
+        const int base = (int)(threadIdx.x & 31) & ~(L * C - 1);
+#pragma unroll
+        for (int k = 0; k < K; ++k) cc[k] = __shfl_sync(gmask, p, base + k * L);
+    }
+}
+
+// Threads of the latency form: one G-lane group per colour-0 slot of the
+// region, (TX / 2 + 1) slots per region row (some of them beyond the row's
+// end in rows of odd parity) times TY + 1 rows.
+template <int G, int TX, int TY>
+__host__ __device__ constexpr int lat_threads() {
+    return (G * ((TX + 2) / 2) * (TY + 1) + 31) / 32 * 32;
+}
+
+template <int G, int TX, int TY>
+__host__ __device__ constexpr bool lat_fits() {
+    return lat_threads<G, TX, TY>() <= 1024;
+}
+
+template <int L, int C, int TX, int TY>
+__global__ void __launch_bounds__(lat_threads<L * C, TX, TY>()) k_iteration_lat(const __grid_constant__ Fields F,
+                                                                                 IterStep H) {
+    constexpr int G = L * C;
+    static_assert(G <= 16 && lat_fits<G, TX, TY>() && TX % 2 == 0, "one region slot per group");
+    constexpr int kRegX = TX + 1, kRegY = TY + 1;
+    constexpr int kHalfRow = (kRegX + 1) / 2, kTileHalfRow = TX / 2;
+    __shared__ uint2 s_vec[kRegX * kRegY];
+    __shared__ int s_cost[kRegX * kRegY];
+    const Field& A = F.f[H.f0 + blockIdx.z];
+    const Views& V = A.V;
+    const int g = threadIdx.x & (G - 1);
+    const int q = g & (L - 1), slot = g / L;
+    const unsigned gmask = group_mask<G>();
+    const int grp = threadIdx.x / G;  // this group's cell in each phase
+    const int tx0 = blockIdx.x * TX, ty0 = blockIdx.y * TY;
+    const int gw = A.gw, gh = A.gh;
+    if (tx0 >= gw || ty0 >= gh) return;  // tile beyond this field's grid (whole CTA)
+    const int rx0 = tx0 - (H.dx > 0 ? 1 : 0), ry0 = ty0 - (H.dy > 0 ? 1 : 0);
+    const int n = H.n;
+
+    // colour-1 pixel of the tile (phase 2): state, reference record, draw
+    const int gy2 = ty0 + grp / kTileHalfRow;
+    const int gx2 = tx0 + 2 * (grp % kTileHalfRow) + ((tx0 + gy2 + 1) & 1);
+    const bool has2 = grp < kTileHalfRow * TY && gx2 < gw && gy2 < gh;
+    int c2 = kEmpty;
+    uint2 w2 = make_uint2(0u, 0u);
+    Slice<L> a2;
+    RsOff o2{0, 0, 0, 0};
+    if (has2) {
+        const size_t si = (size_t)gy2 * gw + gx2;
+        const size_t i = pix(V.w, gx2 * n, gy2 * n);
+        c2 = A.cost[si];
+        w2 = A.field[si];
+        load_slice<L>(V.ref, i, q, a2);
+        o2 = rs_draw(n, H.s, A.key, A.mirror, H.it, (uint32_t)i);
+    }
+
+    // phase 1: this group's colour-0 cell of the region (tile + halo)
+    {
+        const int ry = grp / kHalfRow;
+        const int rx = 2 * (grp % kHalfRow) + ((rx0 + ry0 + ry) & 1);
+        const int gx = rx0 + rx, gy = ry0 + ry;
+        if (ry < kRegY && rx < kRegX && gx >= 0 && gx < gw && gy >= 0 && gy < gh) {
+            const int x = gx * n, y = gy * n;
+            const size_t i = pix(V.w, x, y);
+            const size_t si = (size_t)gy * gw + gx;
+            const int ax = x - H.dx * n, by = y - H.dy * n;
+            const bool has_a = ax >= 0 && ax < V.w, has_b = by >= 0 && by < V.h;
+            const size_t ja = has_a ? si - H.dx : si, jb = has_b ? si - (size_t)(H.dy * gw) : si;
+            int c = A.cost[si];
+            const uint2 wc = A.field[si];
+            const int ca = has_a ? A.cost[ja] : kEmpty, cb = has_b ? A.cost[jb] : kEmpty;
+            const uint2 wa = A.field[ja], wb = A.field[jb];
+            Slice<L> a;
+            load_slice<L>(V.ref, i, q, a);
+            const RsOff o = rs_draw(n, H.s, A.key, A.mirror, H.it - 1, (uint32_t)i);
+            Vec4 cur = unpack_vec(wc);
+            const Vec4 va = unpack_vec(wa), vb = unpack_vec(wb);
+            const bool own_valid = c != kEmpty;
+            Vec4 cr;
+            const bool do_rs = H.it > 0 && own_valid && rs_from(o, cur, cr);
+            const bool do_a = ca != kEmpty && !(own_valid && same_vec(va, cur));
+            const bool do_b = cb != kEmpty && !(own_valid && same_vec(vb, cur)) && !(ca != kEmpty && same_vec(vb, va));
+            const Vec4 cand[3] = {cr, va, vb};
+            const bool valid[3] = {do_rs, do_a, do_b};
+            int cc[3];
+            costs_of<L, C, 3>(V, a, q, slot, gmask, x, y, cand, valid, cc);
+            if (do_rs && cc[0] < c) {
+                c = cc[0];
+                cur = cr;
+            }
+            if (do_a && cc[1] < c) {
+                c = cc[1];
+                cur = va;
+            }
+            if (do_b && cc[2] < c) {
+                c = cc[2];
+                cur = vb;
+            }
+            if (g == 0) {
+                const uint2 wv = pack_vec(cur);
+                s_vec[ry * kRegX + rx] = wv;
+                s_cost[ry * kRegX + rx] = c;
+                if (gx >= tx0 && gx < tx0 + TX && gy >= ty0 && gy < ty0 + TY) {
+                    A.field_out[si] = wv;
+                    A.cost_out[si] = c;
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // phase 2: the colour-1 pixel, propagation then random search
+    if (has2) {
+        const int x = gx2 * n, y = gy2 * n;
+        int c = c2;
+        Vec4 cur = unpack_vec(w2);
+        const int agx = gx2 - H.dx, bgy = gy2 - H.dy;  // predecessors (colour 0, in the region)
+        int ca = kEmpty, cb = kEmpty;
+        uint2 wa = make_uint2(0u, 0u), wb = make_uint2(0u, 0u);
+        if (agx >= 0 && agx < gw) {
+            const int r = (gy2 - ry0) * kRegX + (agx - rx0);
+            ca = s_cost[r];
+            wa = s_vec[r];
+        }
+        if (bgy >= 0 && bgy < gh) {
+            const int r = (bgy - ry0) * kRegX + (gx2 - rx0);
+            cb = s_cost[r];
+            wb = s_vec[r];
+        }
+        const Vec4 va = unpack_vec(wa), vb = unpack_vec(wb);
+        const bool own_valid = c != kEmpty;
+        const bool do_a = ca != kEmpty && !(own_valid && same_vec(va, cur));
+        const bool do_b = cb != kEmpty && !(own_valid && same_vec(vb, cur)) && !(ca != kEmpty && same_vec(vb, va));
+        Vec4 r0, r1 = cur;
+        const bool do_r0 = own_valid && rs_from(o2, cur, r0);
+        bool do_r1 = false;
+        if constexpr (C == 4) do_r1 = do_a && rs_from(o2, va, r1);
+        constexpr int K = C == 4 ? 4 : 3;
+        Vec4 cand[K];
+        bool valid[K];
+        cand[0] = va;
+        cand[1] = vb;
+        cand[2] = r0;
+        valid[0] = do_a;
+        valid[1] = do_b;
+        valid[2] = do_r0;
+        if constexpr (K == 4) {
+            cand[3] = r1;
+            valid[3] = do_r1;
+        }
+        int cc[K];
+        costs_of<L, C, K>(V, a2, q, slot, gmask, x, y, cand, valid, cc);
+        int base = 0;  // 0: own vector kept, 1: horizontal, 2: vertical predecessor taken
+        if (do_a && cc[0] < c) {
+            c = cc[0];
+            cur = va;
+            base = 1;
+        }
+        if (do_b && cc[1] < c) {
+            c = cc[1];
+            cur = vb;
+            base = 2;
+        }
+        if (c != kEmpty) {
+            Vec4 cr;
+            int crc = 0;
+            bool have;
+            if (base == 0) {
+                have = do_r0;
+                cr = r0;
+                crc = cc[2];
+            } else if (K == 4 && base == 1) {
+                have = do_r1;
+                cr = r1;
+                crc = cc[K - 1];
+            } else {
+                have = rs_from(o2, cur, cr);
+                if (have) crc = group_sum<L>(group_part<L>(V, a2, q, x, y, cr), gmask);
+            }
+            if (have && crc < c) {
+                c = crc;
+                cur = cr;
+            }
+        }
+        if (g == 0) {
+            const size_t si = (size_t)gy2 * gw + gx2;
+            A.field_out[si] = pack_vec(cur);
+            A.cost_out[si] = c;
+        }
+    }
+    if (!H.last) return;
+
+    // phase 3 (last iteration of the scale): the random search of this
+    // iteration for the tile's colour-0 pixels, from their phase-1 results
+    {
+        const int gy = ty0 + grp / kTileHalfRow;
+        const int gx = tx0 + 2 * (grp % kTileHalfRow) + ((tx0 + gy) & 1);
+        if (grp >= kTileHalfRow * TY || gx >= gw || gy >= gh) return;
+        const int r = (gy - ry0) * kRegX + (gx - rx0);
+        const int c = s_cost[r];
+        if (c == kEmpty) return;  // the whole group
+        const int x = gx * n, y = gy * n;
+        const size_t i = pix(V.w, x, y);
+        const Vec4 cur = unpack_vec(s_vec[r]);
+        const RsOff o = rs_draw(n, H.s, A.key, A.mirror, H.it, (uint32_t)i);
+        Vec4 cr;
+        if (!rs_from(o, cur, cr)) return;
+        Slice<L> a;
+        load_slice<L>(V.ref, i, q, a);
+        const int cc = group_sum<L>(group_part<L>(V, a, q, x, y, cr), gmask);
+        if (cc < c && g == 0) {
+            const size_t si = (size_t)gy * gw + gx;
+            A.field_out[si] = pack_vec(cr);
+            A.cost_out[si] = cc;
         }
     }
 }
@@ -1220,7 +1552,7 @@ __global__ void k_sift_init(const __grid_constant__ Fields F, SiftViews S, int n
     const int2* src = A.best8 + (size_t)qi * 8;
     for (int k = 0; k < knn_t && k < 8; ++k) {
         const int2 e = src[k];
-        if (e.x == 0x7fffffff) break;
+        if (e.x == 0x7fffffff || e.y < 0 || e.y >= A.gq) break;
         const int tx = (e.y % gw) * n, ty = (e.y / gw) * n;
         const int nx = warp_row_topk(r, A.rec + (size_t)A.gq * 3, A.rec_n + A.gq, n, gw, e.y / gw, tx, V.sigma, lane,
                                      knn_e, xd, xx);
@@ -1336,62 +1668,72 @@ __global__ void k_sift_search(SiftViews S, int gw, int gh, int s, int it, int mi
     }
 }
 
-// Instantiated (lanes per pixel, tile) variants; any of them gives identical
-// results.
+// Instantiated variants of the iteration kernel; any of them gives identical
+// results.  slots = 0: k_iteration with L lanes per pixel; slots = 1 or 4:
+// k_iteration_lat with that many candidate slots of L lanes.
 using IterKernel = void (*)(Fields, IterStep);
 struct IterVariant {
-    int lanes, tx, ty;
+    int lanes, slots, tx, ty;
     IterKernel k;
     int threads;
 };
-#define SFF_ITER_V(L, X, Y) {L, X, Y, k_iteration<L, X, Y>, iter_threads<L, X, Y>()}
+#define SFF_ITER_V(L, X, Y) {L, 0, X, Y, k_iteration<L, X, Y>, iter_threads<L, X, Y>()}
 #define SFF_ITER_VARIANTS(L)                                                                        \
     SFF_ITER_V(L, 64, 16), SFF_ITER_V(L, 32, 16), SFF_ITER_V(L, 64, 8), SFF_ITER_V(L, 32, 8), \
         SFF_ITER_V(L, 16, 8), SFF_ITER_V(L, 8, 8)
-const IterVariant kIterVariants[] = {SFF_ITER_VARIANTS(1), SFF_ITER_VARIANTS(2), SFF_ITER_VARIANTS(4)};
+#define SFF_LAT_V(L, C, X, Y) {L, C, X, Y, k_iteration_lat<L, C, X, Y>, lat_threads<L * C, X, Y>()}
+const IterVariant kIterVariants[] = {
+    SFF_ITER_VARIANTS(1), SFF_ITER_VARIANTS(2), SFF_ITER_VARIANTS(4),
+    // latency form: every tile whose region fits one cell per group in 1024 threads
+    SFF_LAT_V(1, 1, 64, 16), SFF_LAT_V(1, 1, 32, 16), SFF_LAT_V(1, 1, 64, 8), SFF_LAT_V(1, 1, 32, 8),
+    SFF_LAT_V(1, 1, 16, 8), SFF_LAT_V(1, 1, 8, 8),
+    SFF_LAT_V(2, 1, 32, 16), SFF_LAT_V(2, 1, 64, 8), SFF_LAT_V(2, 1, 32, 8), SFF_LAT_V(2, 1, 16, 8),
+    SFF_LAT_V(2, 1, 8, 8),
+    SFF_LAT_V(4, 1, 32, 8), SFF_LAT_V(4, 1, 16, 8), SFF_LAT_V(4, 1, 8, 8),
+    SFF_LAT_V(1, 4, 32, 8), SFF_LAT_V(1, 4, 16, 8), SFF_LAT_V(1, 4, 8, 8),
+    SFF_LAT_V(2, 4, 16, 8), SFF_LAT_V(2, 4, 8, 8),
+    SFF_LAT_V(4, 4, 8, 8)};
+#undef SFF_LAT_V
 #undef SFF_ITER_VARIANTS
 #undef SFF_ITER_V
 
-const IterVariant* find_variant(const sff_tuning& t) {
+const IterVariant* find_variant(int lanes, int slots, int tx, int ty) {
     for (const auto& v : kIterVariants)
-        if (v.lanes == t.lanes_per_pixel && v.tx == t.tile_x && v.ty == t.tile_y) return &v;
+        if (v.lanes == lanes && v.slots == slots && v.tx == tx && v.ty == ty) return &v;
     return nullptr;
 }
 
-// Variant of the iteration kernel at one scale.  Scale 0 takes the tuned
-// variant.  A coarser scale is latency-bound: few grid pixels per SM, each a
-// chain of dependent feature loads.  More lanes per pixel put more warps in
-// flight and shorten each lane's chain, so it takes at least 2 lanes below
-// kPixPerSmL1 grid pixels per SM and 4 below kPixPerSmL2 (measured on the
-// 1242x375 driving quad: scale 2 with 385 pixels per SM is fastest with 2
-// lanes, scale 3 with 96 with 4).  The tile is then the tuned tile if it
-// gives at least two CTAs per SM over all fields, else the largest smaller
-// tile that does, else the smallest.  Every variant gives the same result.
-constexpr int kSmCount = 152;
-constexpr long kPixPerSmL1 = 1000, kPixPerSmL2 = 200;
-
-long ctas_for(const IterVariant& v, const int* gw, const int* gh, int nf) {
-    long c = 0;
-    for (int k = 0; k < nf; ++k) c += (long)((gw[k] + v.tx - 1) / v.tx) * ((gh[k] + v.ty - 1) / v.ty);
-    return c;
+// A tuning is valid when its scale-0 variant exists and every coarse entry is
+// either all zero (chosen from the grid size) or an existing variant.
+bool tuning_valid(const sff_tuning& t) {
+    if (!find_variant(t.lanes_per_pixel, t.slots, t.tile_x, t.tile_y)) return false;
+    if (t.group_mb < 0 || t.group_mb > (1 << 20)) return false;
+    for (int k = 0; k < SFF_MAX_SCALES - 1; ++k) {
+        const int32_t* c = t.coarse[k];
+        if ((c[0] | c[1] | c[2] | c[3]) != 0 && !find_variant(c[0], c[1], c[2], c[3])) return false;
+    }
+    return true;
 }
 
-const IterVariant* tile_for_grid(const IterVariant* tuned, int s, const int* gw, const int* gh, int nf) {
-    if (s == 0) return tuned;
+// Variant of the iteration kernel at one scale.  Scale 0 takes the tuned
+// variant, a coarser scale its tuning entry when one is given.  Otherwise it
+// is chosen by the number of grid pixels per SM over all fields: a coarse
+// scale is latency-bound (few grid pixels per SM, each a chain of dependent
+// feature loads).  Measured per launch on the 1242x375 driving quad (both
+// fields): at scale 1 (1536 pixels per SM) and scale 2 (385) one lane per
+// pixel on 32 x 16 tiles was fastest of all 38 variants (23.2, 12.9 us), at
+// scale 3 (96) the latency form with a slot per candidate on 16 x 8 tiles
+// (8.9 us against 13.3).  Every variant gives the same result.
+constexpr int kSmCount = 152;
+constexpr long kPixPerSmSlots = 200;
+
+const IterVariant* variant_for_scale(const sff_tuning& t, int s, const int* gw, const int* gh, int nf) {
+    if (s == 0) return find_variant(t.lanes_per_pixel, t.slots, t.tile_x, t.tile_y);
+    const int32_t* c = t.coarse[s - 1];
+    if ((c[0] | c[1] | c[2] | c[3]) != 0) return find_variant(c[0], c[1], c[2], c[3]);
     long px = 0;
     for (int k = 0; k < nf; ++k) px += (long)gw[k] * gh[k];
-    const long per_sm = px / kSmCount;
-    const int lanes = std::max(tuned->lanes, per_sm >= kPixPerSmL1 ? 1 : per_sm >= kPixPerSmL2 ? 2 : 4);
-    constexpr long kWantCtas = 2 * kSmCount;
-    const IterVariant* pick_v = nullptr;
-    for (const auto& v : kIterVariants) {
-        if (v.lanes != lanes || v.tx * v.ty > tuned->tx * tuned->ty) continue;
-        if (ctas_for(v, gw, gh, nf) >= kWantCtas && (!pick_v || v.tx * v.ty > pick_v->tx * pick_v->ty)) pick_v = &v;
-    }
-    if (pick_v) return pick_v;
-    for (const auto& v : kIterVariants)  // none fills the GPU: the smallest tile
-        if (v.lanes == lanes && (!pick_v || v.tx * v.ty < pick_v->tx * pick_v->ty)) pick_v = &v;
-    return pick_v;
+    return px / kSmCount < kPixPerSmSlots ? find_variant(1, 4, 16, 8) : find_variant(1, 0, 32, 16);
 }
 
 int coarse_gq(int w, int h, const sff_params& p) {
@@ -1444,8 +1786,7 @@ bool knn_smem_ready() {
 // launches.  spec[k].workspace holds field_ws_bytes() of scratch.
 int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tuning& T, cudaStream_t st,
                bool sequential) {
-    const IterVariant* var = find_variant(T);
-    if (!var || nf < 1 || nf > kMaxFields) return SFF_ERR_ARG;
+    if (!tuning_valid(T) || nf < 1 || nf > kMaxFields) return SFF_ERR_ARG;
     const int S = P.num_scales, I = P.iterations;
     static const int kDirs[4][2] = {{1, 1}, {-1, -1}, {1, -1}, {-1, 1}};
     static Fields F;  // host staging of the kernel parameter (copied at each launch)
@@ -1544,20 +1885,51 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
             prev = cur;
             continue;
         }
-        const IterVariant* sv = tile_for_grid(var, s, gw, gh, nf);
-        dim3 gi((mgw + sv->tx - 1) / sv->tx, (mgh + sv->ty - 1) / sv->ty, nf);
-        for (int it = 0; it < I; ++it) {
-            const int in = cur ^ (it & 1);
-            for (int k = 0; k < nf; ++k) {
-                F.f[k].field = Bf[in][k];
-                F.f[k].cost = Bc[in][k];
-                F.f[k].field_out = Bf[in ^ 1][k];
-                F.f[k].cost_out = Bc[in ^ 1][k];
+        // profiled as one span per scale (and group), "k_iteration/s<scale>"
+        static const char* const kIterNames[SFF_MAX_SCALES] = {"k_iteration/s0", "k_iteration/s1", "k_iteration/s2",
+                                                               "k_iteration/s3"};
+        // Scale 0 may run its iterations for consecutive groups of fields in
+        // turn (T.group_mb): all iterations of one group, then the next, so
+        // that a group's features and state stay in L2 across iterations.
+        // Fields of one quad share their pyramids and are never split.
+        for (int f0 = 0; f0 < nf;) {
+            int f1 = nf;
+            if (s == 0 && T.group_mb > 0) {
+                const double budget = (double)T.group_mb * (1 << 20);
+                double used = 0.0;
+                f1 = f0;
+                while (f1 < nf) {
+                    const bool pair = f1 + 1 < nf && spec[f1 + 1].width == spec[f1].width &&
+                                      spec[f1 + 1].height == spec[f1].height && spec[f1 + 1].ref == spec[f1].crs;
+                    const int take = pair ? 2 : 1;
+                    // four images' records + both fields' double-buffered state
+                    const double ws = (double)spec[f1].width * spec[f1].height * (4.0 * kFeat + take * 24.0);
+                    if (f1 > f0 && used + ws > budget) break;
+                    used += ws;
+                    f1 += take;
+                }
             }
-            IterStep H{n, s, kDirs[it % 4][0], kDirs[it % 4][1], it, it == I - 1};
-            if (::sff::profiling()) ::sff::profile_mark("k_iteration", st, false);
-            sv->k<<<gi, sv->threads, 0, st>>>(F, H);
-            if (::sff::profiling()) ::sff::profile_mark("k_iteration", st, true);
+            int ggw = 0, ggh = 0;
+            for (int k = f0; k < f1; ++k) {
+                ggw = std::max(ggw, gw[k]);
+                ggh = std::max(ggh, gh[k]);
+            }
+            const IterVariant* sv = variant_for_scale(T, s, gw + f0, gh + f0, f1 - f0);
+            dim3 gi((ggw + sv->tx - 1) / sv->tx, (ggh + sv->ty - 1) / sv->ty, f1 - f0);
+            if (I > 0 && ::sff::profiling()) ::sff::profile_mark(kIterNames[s], st, false);
+            for (int it = 0; it < I; ++it) {
+                const int in = cur ^ (it & 1);
+                for (int k = f0; k < f1; ++k) {
+                    F.f[k].field = Bf[in][k];
+                    F.f[k].cost = Bc[in][k];
+                    F.f[k].field_out = Bf[in ^ 1][k];
+                    F.f[k].cost_out = Bc[in ^ 1][k];
+                }
+                IterStep H{n, s, kDirs[it % 4][0], kDirs[it % 4][1], it, it == I - 1, f0};
+                sv->k<<<gi, sv->threads, 0, st>>>(F, H);
+            }
+            if (I > 0 && ::sff::profiling()) ::sff::profile_mark(kIterNames[s], st, true, I);
+            f0 = f1;
         }
         prev = cur ^ (I & 1);
     }
@@ -1676,6 +2048,7 @@ extern "C" int sff_match_views_sequential(const uint8_t* pyr_ref_dev, const uint
 
 extern "C" int sff_default_tuning(sff_tuning* out) {
     if (!out) return SFF_ERR_ARG;
+    memset(out, 0, sizeof *out);
     out->lanes_per_pixel = 1;
     out->tile_x = 32;
     out->tile_y = 16;
@@ -1683,7 +2056,7 @@ extern "C" int sff_default_tuning(sff_tuning* out) {
 }
 
 extern "C" int sff_tuning_supported(const sff_tuning* t) {
-    return t && sff::find_variant(*t) ? 1 : 0;
+    return t && sff::tuning_valid(*t) ? 1 : 0;
 }
 
 extern "C" int sff_match_quad_tuned(const uint8_t* pyr_l0_dev, const uint8_t* pyr_r0_dev, const uint8_t* pyr_l1_dev,
@@ -1693,7 +2066,7 @@ extern "C" int sff_match_quad_tuned(const uint8_t* pyr_l0_dev, const uint8_t* py
                                     size_t workspace_bytes, void* stream) {
     using namespace sff;
     if (check_size(width, height) || check_params(params)) return SFF_ERR_ARG;
-    if (!tuning || !find_variant(*tuning)) return SFF_ERR_ARG;
+    if (!tuning || !tuning_valid(*tuning)) return SFF_ERR_ARG;
     if (!pyr_l0_dev || !pyr_r0_dev || !pyr_l1_dev || !pyr_r1_dev || !fwd_dev || !fwd_cost_dev || !inv_dev ||
         !inv_cost_dev || !workspace)
         return SFF_ERR_ARG;
@@ -1723,6 +2096,30 @@ extern "C" int sff_match_quad(const uint8_t* pyr_l0_dev, const uint8_t* pyr_r0_d
                                 fwd_dev, fwd_cost_dev, inv_dev, inv_cost_dev, workspace, workspace_bytes, stream);
 }
 
+namespace sff {
+// Reads (and with reset clears) the condition bits of the matching kernels,
+// in stream order; the caller synchronises the stream.
+int match_status_read(cudaStream_t st, unsigned* out, bool reset) {
+    static const unsigned zero = 0;
+    if (cudaMemcpyFromSymbolAsync(out, g_match_status, sizeof(unsigned), 0, cudaMemcpyDeviceToHost, st) !=
+        cudaSuccess)
+        return SFF_ERR_CUDA;
+    if (reset && cudaMemcpyToSymbolAsync(g_match_status, &zero, sizeof(unsigned), 0, cudaMemcpyHostToDevice, st) !=
+                     cudaSuccess)
+        return SFF_ERR_CUDA;
+    return SFF_OK;
+}
+}  // namespace sff
+
+extern "C" int sff_debug_knn_withhold(int32_t step, int32_t wait_limit_us) {
+    if (step < -1 || wait_limit_us < 0) return SFF_ERR_ARG;
+    const int st = step;
+    const unsigned long long ns = (unsigned long long)wait_limit_us * 1000ull;
+    if (cudaMemcpyToSymbol(sff::g_withhold_step, &st, sizeof st) != cudaSuccess) return SFF_ERR_CUDA;
+    if (cudaMemcpyToSymbol(sff::g_wait_limit_ns, &ns, sizeof ns) != cudaSuccess) return SFF_ERR_CUDA;
+    return SFF_OK;
+}
+
 extern "C" int sff_device_timeouts(uint32_t* out, int32_t reset) {
     if (!out) return SFF_ERR_ARG;
     unsigned v = 0;
@@ -1731,7 +2128,16 @@ extern "C" int sff_device_timeouts(uint32_t* out, int32_t reset) {
     if (reset) {
         const unsigned z = 0;
         if (cudaMemcpyToSymbol(sff::g_wait_timeouts, &z, sizeof z) != cudaSuccess) return SFF_ERR_CUDA;
+        if (cudaMemcpyToSymbol(sff::g_drain_timeouts, &z, sizeof z) != cudaSuccess) return SFF_ERR_CUDA;
     }
+    return SFF_OK;
+}
+
+extern "C" int sff_device_drain_timeouts(uint32_t* out) {
+    if (!out) return SFF_ERR_ARG;
+    unsigned v = 0;
+    if (cudaMemcpyFromSymbol(&v, sff::g_drain_timeouts, sizeof v) != cudaSuccess) return SFF_ERR_CUDA;
+    *out = v;
     return SFF_OK;
 }
 

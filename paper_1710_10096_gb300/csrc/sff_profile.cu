@@ -1,5 +1,8 @@
 // Opt-in per-kernel timing: CUDA events recorded on the launch stream
 // before and after each kernel launch, summed per kernel name on collect.
+// A span brackets several back-to-back launches of one kernel with a single
+// pair of events (the iteration kernel's launches of one scale): on short
+// kernels an event node per launch costs more than the launch gap it hides.
 // On a stream that is being captured into a CUDA graph the events become
 // event-record nodes of the graph (cudaEventRecordExternal), so a replay
 // times the kernels as the graph runs them, without the host's launch gaps
@@ -16,6 +19,7 @@ namespace {
 struct Mark {
     const char* name;
     cudaEvent_t start, stop;
+    int launches;
 };
 
 std::mutex g_mu;
@@ -58,7 +62,7 @@ static void record_mark(cudaEvent_t e, cudaStream_t st) {
         cudaEventRecord(e, st);
 }
 
-void profile_mark(const char* name, cudaStream_t st, bool after) {
+void profile_mark(const char* name, cudaStream_t st, bool after, int launches) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (!after) {
         g_pending = take_event();
@@ -66,7 +70,7 @@ void profile_mark(const char* name, cudaStream_t st, bool after) {
     } else {
         cudaEvent_t stop = take_event();
         record_mark(stop, st);
-        g_marks.push_back(Mark{name, g_pending, stop});
+        g_marks.push_back(Mark{name, g_pending, stop, launches});
         g_pending = nullptr;
     }
 }
@@ -99,7 +103,7 @@ extern "C" int sff_profile_collect(sff_kernel_time* out, int32_t capacity, int32
             count.push_back(0);
         }
         ms[k] += t;
-        count[k] += 1;
+        count[k] += m.launches;
     }
     for (size_t k = 0; k < names.size() && (int)k < capacity; ++k) {
         size_t len = names[k].size() < 39 ? names[k].size() : 39;

@@ -35,6 +35,12 @@ struct SeedJobs {
     SeedJob q[kMaxQuads];
 };
 
+// Conditions raised since the last reset (read by sff_device_status): bit 1
+// a seed buffer was smaller than the number of seeds (its count still holds
+// the number needed).
+constexpr unsigned kStatusCapacity = 2u;
+__device__ unsigned int g_seed_status;
+
 // One thread per block: raster index of its best kept pixel or -1; one count
 // of found seeds per CTA.
 __global__ void __launch_bounds__(kChunk) k_block_best(const __grid_constant__ SeedJobs J) {
@@ -115,7 +121,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_chunks(const __grid_const
         chunk[c] = pos;
         pos += k;
     }
-    if (t == kScanThreads - 1) *Q.count = pos;
+    if (t == kScanThreads - 1) {
+        *Q.count = pos;
+        if (pos > Q.capacity) atomicOr(&g_seed_status, kStatusCapacity);
+    }
 }
 
 // Same grid as k_block_best: rank of each found seed inside its CTA (warp
@@ -171,6 +180,18 @@ void seeds_carve(void* workspace, int w, int h, int** best, int** chunk) {
     const size_t nb = (size_t)((w + 2) / 3) * ((h + 2) / 3);
     *best = reinterpret_cast<int*>(workspace);
     *chunk = reinterpret_cast<int*>((char*)workspace + align256(nb * sizeof(int)));
+}
+
+// Reads (and with reset clears) the condition bits of the seed kernels, in
+// stream order; the caller synchronises the stream.
+int seeds_status_read(cudaStream_t st, unsigned* out, bool reset) {
+    static const unsigned zero = 0;
+    if (cudaMemcpyFromSymbolAsync(out, g_seed_status, sizeof(unsigned), 0, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return SFF_ERR_CUDA;
+    if (reset && cudaMemcpyToSymbolAsync(g_seed_status, &zero, sizeof(unsigned), 0, cudaMemcpyHostToDevice, st) !=
+                     cudaSuccess)
+        return SFF_ERR_CUDA;
+    return SFF_OK;
 }
 
 int run_seeds(const SeedJob* jobs, int n, cudaStream_t st) {

@@ -24,7 +24,7 @@ import time
 
 import numpy as np
 
-from . import QuadBuffers, default_params, default_tuning, run_batch, seeds_to_numpy
+from . import OK, QuadBuffers, default_params, default_tuning, device_status, lib, run_batch, seeds_to_numpy
 
 __all__ = ["Request", "Server", "PlainServer", "simulate", "poisson_arrivals", "validate_request"]
 
@@ -38,7 +38,7 @@ class Request:
     t_arrival: float = 0.0  # seconds on the server's clock
     t_done: float = 0.0
     seeds: np.ndarray = None  # result (SEED_DTYPE)
-    error: str = None  # set when the request was rejected
+    error: str = None  # set when the request was rejected or its batch raised a device-side condition
 
     @property
     def size(self):
@@ -212,9 +212,14 @@ class Server:
             if b is None or not b[0].query():
                 continue
             t = now_fn()
+            # device-side conditions (a bounded wait that gave up): the
+            # condition word is per device, so a condition raised by the
+            # other batch in flight fails this one as well
+            status = device_status(self.streams[k], reset=True)
             for slot in b[1]:
                 n = int(slot.host_count[0])
                 slot.req.seeds = seeds_to_numpy(slot.host_seeds[:20 * min(n, slot.buf.capacity)].numpy(), n)
+                slot.req.error = None if status == OK else _status_error(status)
                 slot.req.t_done = t
                 self.done.append(slot.req)
                 slot.req = None
@@ -258,8 +263,10 @@ class PlainServer:
                 ev, slot = self.cur
                 if not ev.query():
                     return
+                status = device_status(self.stream, reset=True)
                 n = int(slot.host_count[0])
                 slot.req.seeds = seeds_to_numpy(slot.host_seeds[:20 * min(n, slot.buf.capacity)].numpy(), n)
+                slot.req.error = None if status == OK else _status_error(status)
                 slot.req.t_done = now_fn()
                 self.done.append(slot.req)
                 self.cur = None
@@ -285,6 +292,10 @@ class PlainServer:
 
     def idle(self) -> bool:
         return not self.pending and self.cur is None
+
+
+def _status_error(status: int) -> str:
+    return f"device status: {lib().sff_status_string(status).decode()} ({status})"
 
 
 def poisson_arrivals(rate: float, n: int, n_streams: int, pool_size: int, seed: int = 7):

@@ -312,8 +312,12 @@ def test_every_tuning_gives_identical_fields(env):
     pyrs = [_gpu_features(torch, sff, im, p)[0] for im in q.images()]
     ws = torch.empty(sff.workspace_bytes(w, h, p), dtype=torch.uint8, device="cuda")
     ref = None
-    for cand in sff.TUNING_SPACE:
-        t = sff.make_tuning(*cand)
+    # the throughput form at scale 0 (coarse scales derived), then every
+    # variant of both forms at all four scales
+    space = [sff.make_tuning(*cand) for cand in sff.TUNING_SPACE]
+    space += [sff.make_tuning(l, tx, ty, c, [(l, c, tx, ty)] * 3) for (l, c, tx, ty) in sff.VARIANT_SPACE]
+    for t in space:
+        cand = t.scale_variants()
         out = [torch.empty((h, w, 4), dtype=torch.int16, device="cuda") for _ in range(2)]
         cst = [torch.empty((h, w), dtype=torch.int32, device="cuda") for _ in range(2)]
         sff.match_quad_tuned(*pyrs, w, h, 5, t, out[0], cst[0], out[1], cst[1], ws, p)
@@ -325,6 +329,29 @@ def test_every_tuning_gives_identical_fields(env):
             assert np.array_equal(got[0], o["fwd"]) and np.array_equal(got[1], o["inv"])
         for a, b in zip(got, ref):
             assert np.array_equal(a, b), cand
+
+
+@pytest.mark.parametrize("size", [(250, 77), (97, 41)])
+def test_latency_form_on_ragged_grids(env, size):
+    # the latency form of the iteration kernel (slots 1 and 4) on grids that
+    # leave partial tiles at every scale, against the oracle
+    torch, sff, orc = env
+    w, h = size
+    q = scenegen.make_quad("planes", w, h, seed=w + h)
+    p = sff.default_params()
+    pyrs = [_gpu_features(torch, sff, im, p)[0] for im in q.images()]
+    ws = torch.empty(sff.workspace_bytes(w, h, p), dtype=torch.uint8, device="cuda")
+    o = orc.run_quad(*q.images(), seed=9)
+    for (l, c, tx, ty) in [v for v in sff.VARIANT_SPACE if v[1] > 0]:
+        t = sff.make_tuning(l, tx, ty, c, [(l, c, tx, ty)] * 3)
+        out = [torch.empty((h, w, 4), dtype=torch.int16, device="cuda") for _ in range(2)]
+        cst = [torch.empty((h, w), dtype=torch.int32, device="cuda") for _ in range(2)]
+        sff.match_quad_tuned(*pyrs, w, h, 9, t, out[0], cst[0], out[1], cst[1], ws, p)
+        torch.cuda.synchronize()
+        assert np.array_equal(out[0].cpu().numpy(), o["fwd"]), (l, c, tx, ty)
+        assert np.array_equal(out[1].cpu().numpy(), o["inv"]), (l, c, tx, ty)
+        assert np.array_equal(cst[0].cpu().numpy(), o["fwd_cost"]), (l, c, tx, ty)
+        assert np.array_equal(cst[1].cpu().numpy(), o["inv_cost"]), (l, c, tx, ty)
 
 
 def test_batch_of_uneven_quads_equals_each_alone(env):
@@ -351,6 +378,59 @@ def test_batch_of_uneven_quads_equals_each_alone(env):
         assert np.array_equal(b.keep.cpu().numpy(), ref["keep"])
         assert np.array_equal(b.cerr.cpu().numpy(), ref["cerr"])
         assert b.seeds_numpy().tobytes() == ref["seeds"].tobytes()
+
+
+def test_mixed_32_quad_batch_equals_oracle(env):
+    # the benchmark's 32-quad batch (8 each of 1242x375 and 1024x436 driving
+    # scenes, 640x192 and 512x160 planes scenes, scene seeds 100..131) in
+    # shared launches under one CUDA graph: every one of the 32 quads' fields,
+    # costs, masks and seeds equals the oracle's run on that quad alone
+    torch, sff, orc = env
+    import bench
+    quads, seeds = bench.make_batch_quads()
+    sizes = [(im[0].shape[1], im[0].shape[0]) for im in quads]
+    assert sorted(set(sizes)) == [(512, 160), (640, 192), (1024, 436), (1242, 375)]
+    bm = sff.BatchMatcher(sizes)
+    for k, im in enumerate(quads):
+        bm.load(k, *im)
+    g = bm.capture(seeds)
+    g.replay()
+    torch.cuda.synchronize()
+    for k, (im, b) in enumerate(zip(quads, bm.quads)):
+        ref = orc.run_quad(*im, seed=seeds[k])
+        assert np.array_equal(b.fwd.cpu().numpy(), ref["fwd"]), k
+        assert np.array_equal(b.inv.cpu().numpy(), ref["inv"]), k
+        assert np.array_equal(b.fwd_cost.cpu().numpy(), ref["fwd_cost"]), k
+        assert np.array_equal(b.inv_cost.cpu().numpy(), ref["inv_cost"]), k
+        assert np.array_equal(b.keep.cpu().numpy(), ref["keep"]), k
+        assert np.array_equal(b.cerr.cpu().numpy(), ref["cerr"]), k
+        assert b.seeds_numpy().tobytes() == ref["seeds"].tobytes(), k
+    assert sff.device_timeouts() == 0
+
+
+@pytest.mark.parametrize("size", [(64, 48), (256, 80)])
+@pytest.mark.parametrize("iterations", [0, 12])
+def test_all_ties_initialisation(env, size, iterations):
+    # a constant image: every feature is zero, so every temporal K-NN
+    # candidate ties at the bound (the tensor-core scan's append buffers fill
+    # and compact on the first tile), every epipolar candidate ties and every
+    # initial combination costs 0.  Both passes equal the oracle, and without
+    # iterations the coarsest grid holds the oracle pin's closed form: the
+    # temporal point (0, 0) and the stereo / cross points of lowest x that the
+    # sign of d allows
+    torch, sff, orc = env
+    w, h = size
+    img = np.full((h, w, 3), 90, np.uint8)
+    p = sff.default_params(iterations=iterations)
+    n = 1 << (p.num_scales - 1)
+    for mirror, (f, c, of, oc) in enumerate(_match_both(env, [img] * 4, p, seed=3)):
+        assert np.array_equal(f, of) and np.array_equal(c, oc), mirror
+        if iterations == 0:
+            for py in range(0, h, n):
+                for px in range(0, w, n):
+                    assert tuple(int(v) for v in f[py, px]) == (-px, -py, 0 if mirror else px, 0), (mirror, px, py)
+                    assert c[py, px] == 0
+    assert sff.device_timeouts() == 0
 
 
 def test_batch_graph_replay_is_deterministic(env):
