@@ -48,6 +48,10 @@ FALLBACK_HBM_GBS = 6800.0
 #   k_features    per pixel and scale: packed smoothed pixel 4 B in, 48 B
 #                 record + 4 B norm out
 ALGO_BYTES = {"k_iteration": 24 + 52 + 3 * 52, "k_features": 4 + 52}
+# Algorithmic integer work of the iteration kernel per grid pixel and
+# iteration: 3 candidates (random search, 2 predecessors) x 3 views x one
+# 48-element int8 dot product = 432 MACs = 108 dp4a.
+ALGO_DP4A = {"k_iteration": 3 * 3 * 48 // 4}
 
 
 def parse():
@@ -191,19 +195,22 @@ def merge_scales(prof):
     return merged, per_scale
 
 
-def iteration_scales(per_scale, w, h, n_fields, peak):
+def iteration_scales(per_scale, w, h, n_fields, peak, dp4a_peak=None):
     """Per-scale roofline of the propagation kernel: algorithmic bytes per
     launch (ALGO_BYTES per grid pixel, every grid pixel of every field once
-    per launch) over the average launch time."""
+    per launch) over the average launch time, and the same for its dp4a."""
     out = []
     for s, (n, ms) in sorted(per_scale.items()):
         st = 1 << s
         grid = ((w + st - 1) // st) * ((h + st - 1) // st)
         b = ALGO_BYTES["k_iteration"] * n_fields * grid
         us = 1e3 * ms / n
-        out.append({"scale": s, "grid_px": n_fields * grid, "launches": n, "avg_launch_us": us,
-                    "algo_mb_per_launch": b / 1e6, "achieved_gbs": b / (us * 1e-6) / 1e9,
-                    "frac": b / (us * 1e-6) / 1e9 / peak})
+        r = {"scale": s, "grid_px": n_fields * grid, "launches": n, "avg_launch_us": us,
+             "algo_mb_per_launch": b / 1e6, "achieved_gbs": b / (us * 1e-6) / 1e9,
+             "frac": b / (us * 1e-6) / 1e9 / peak}
+        if dp4a_peak:
+            r["int_frac"] = ALGO_DP4A["k_iteration"] * n_fields * grid / (us * 1e-6) / dp4a_peak
+        out.append(r)
     return out
 
 
@@ -854,7 +861,8 @@ def main():
         tuning = sff.make_tuning(*(int(v) for v in args.tuning.split(",")))
     # the batch and the server take the tuned scale-0 variant with the coarse
     # scales derived from their (much larger) launch sizes
-    batch_tuning = sff.make_tuning(tuning.lanes_per_pixel, tuning.tile_x, tuning.tile_y, tuning.slots)
+    batch_tuning = sff.make_tuning(tuning.lanes_per_pixel, tuning.tile_x, tuning.tile_y, tuning.slots,
+                                   min_ctas=tuning.min_ctas)
     m = sff.QuadMatcher(q.width, q.height, params, device=dev, tuning=tuning)
     stream = torch.cuda.Stream(device=dev)
     host_in = torch.empty((4, q.height, q.width, 3), dtype=torch.uint8).pin_memory()
@@ -931,6 +939,10 @@ def main():
     e2e = {"value": combine_ranks(statistics.mean(e2e_times), px, world, dev)[1], "unit": "px/s",
            "h2d_bytes_per_step": int(host_in.numel()), "d2h_bytes_per_step": int(m.seeds.numel() + 4)}
 
+    # integer peaks of this GPU, measured now (the other roofline of the
+    # integer cost evaluations)
+    int_peak = {"dp4a_per_s": sff.int_peak("dp4a", stream), "imad_per_s": sff.int_peak("imad", stream),
+                "source": "measured in this run (sff_int_peak: 8 chains per thread, 8 x 256 threads per SM)"}
     # roofline of the dominant kernel (largest share of profiled time)
     launches_per_step = sum(v[0] for v in prof.values()) / prof_steps
     dom = max(prof, key=lambda k: prof[k][1])
@@ -945,9 +957,18 @@ def main():
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": tr, "peak_source": peak_src,
                 "algo_bytes_per_launch": bytes_per_launch, "avg_launch_us": 1e3 * dom_ms / dom_launches}
+        roof["hbm_frac"] = achieved / peak
+        if dom in ALGO_DP4A:
+            dp4a = ALGO_DP4A[dom] * units / dom_launches
+            roof["int_peak"] = int_peak
+            roof["int_frac"] = dp4a / (dom_ms / dom_launches / 1e3) / int_peak["dp4a_per_s"]
+            roof["int_ops"] = f"{ALGO_DP4A[dom]} dp4a per grid pixel and iteration (3 candidates x 3 views x 48 MAC)"
+            # the binding roofline is the larger fraction
+            if roof["int_frac"] > roof["hbm_frac"]:
+                roof.update(bound="int", frac=roof["int_frac"])
         if dom in prof_scales:
             sc = {s: (n / prof_steps, ms / prof_steps) for s, (n, ms) in prof_scales[dom].items()}
-            roof["per_scale"] = iteration_scales(sc, q.width, q.height, 2, peak)
+            roof["per_scale"] = iteration_scales(sc, q.width, q.height, 2, peak, int_peak["dp4a_per_s"])
     total_prof = sum(v[1] for v in prof.values())
     kernels = {k: {"launches_per_step": v[0] / prof_steps, "ms_per_step": v[1] / prof_steps,
                    "share": v[1] / total_prof} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}

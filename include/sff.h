@@ -82,32 +82,39 @@ typedef struct sff_params {
 
 /* Work distribution of the propagation kernels (no counterpart in the paper).
  * Every supported setting gives bit-identical results; only speed differs.
- * A variant of the iteration kernel is (lanes, slots, tile_x, tile_y):
+ * A variant of the iteration kernel is (lanes, slots, tile_x, tile_y, min_ctas):
  *   slots = 0: the throughput form, `lanes` in {1, 2, 4} threads sharing one
  *              pixel's feature loads, tile in {(64, 16), (32, 16), (64, 8),
- *              (32, 8), (16, 8), (8, 8)} grid pixels;
+ *              (32, 8), (16, 8), (8, 8)} grid pixels, min_ctas 0; and with one
+ *              lane, (tile, min_ctas) in {(64 x 16, 2), (32 x 16, 4), (32 x 8,
+ *              7), (32 x 8, 8)}: registers budgeted for that many resident
+ *              CTAs per SM;
  *   slots = 1 or 4: the latency form (the next pixel's loads and the random
  *              draws issued up front, the colour-1 random search scored with
  *              the propagation candidates), each candidate of an update on
  *              `slots` == 4 ? its own `lanes` lanes : all lanes; only the
  *              tiles for which lanes * slots * (tile_x / 2 + 1) * (tile_y + 1)
  *              threads (one group per colour-0 slot of the tile and its halo)
- *              fit 1024.
- * Scale 0 takes (lanes_per_pixel, slots, tile_x, tile_y).  Scale s >= 1
- * takes coarse[s - 1] = {lanes, slots, tile_x, tile_y}; all four zero means
- * derived from the grid size: (1, 4, 16, 8) below 200 grid pixels per SM
- * over all fields of the launch, else (1, 0, 32, 16).
+ *              fit 1024; min_ctas 0.
+ * Scale 0 takes (lanes_per_pixel, slots, tile_x, tile_y, min_ctas).  Scale
+ * s >= 1 takes coarse[s - 1] = {lanes, slots, tile_x, tile_y, min_ctas}; all zero means
+ * derived from the grid size: (1, 4, 16, 8, 0) below 200 grid pixels per SM
+ * over all fields of the launch, else (1, 0, 32, 16, 0).
  * sff_tuning_supported() checks a setting. */
 typedef struct sff_tuning {
     int32_t lanes_per_pixel; /* threads that share one pixel's feature loads */
     int32_t tile_x, tile_y;  /* grid pixels per CTA of the iteration kernel */
     int32_t slots;           /* 0: throughput form; 1 or 4: latency form */
-    int32_t coarse[3][4];    /* scales 1..3: {lanes, slots, tile_x, tile_y}, or all 0 */
+    int32_t min_ctas;        /* throughput form compiled for >= this many resident CTAs per SM (0: none) */
+    int32_t coarse[3][5];    /* scales 1..3: {lanes, slots, tile_x, tile_y, min_ctas}, or all 0 */
     int32_t group_mb;        /* sweep schedule of scale 0 when a launch holds several quads
                               * (sff_run_batch): 0 = every iteration launch covers all of them;
                               * > 0 = all iterations for one group of consecutive quads, then
                               * the next, each group's four-image records and field state at
                               * most group_mb MiB (a quad larger than that alone); 0..2^20 */
+    int32_t pair_fields;     /* CTA order of the iteration kernel: 0 = field after field;
+                              * 1 = a quad's forward and inverse field alternate tile by tile
+                              * (their CTAs read the same four images side by side) */
 } sff_tuning;
 
 /* One seed of Sec. 3.2: pixel (x, y) of L0, its vector and its scores. 20 bytes.
@@ -323,7 +330,10 @@ int sff_emit_seeds_geo(const int16_t* fwd_dev, const int32_t* fwd_cost_dev, cons
  *     4.7 million pixels) are rejected with SFF_ERR_ARG before any work.
  *   - The first call on a device looks up the array's device address (with
  *     that device current) and caches it; make that first call before any
- *     stream capture on the device.
+ *     stream capture on the device.  The cache is per device number and does
+ *     not survive cudaDeviceReset (the module is loaded again, possibly at
+ *     another address): do not call this entry point on a device after
+ *     resetting it in the same process.
  *   - All calls share the one array: calls that may overlap on the GPU (other
  *     streams, other threads) race and must be ordered by the caller.  The
  *     array keeps the previous call's contents; every entry a call reads is
@@ -505,6 +515,16 @@ int sff_device_timeouts(uint32_t* out, int32_t reset);
  * released.  Each drain waits ten times the normal limit; a nonzero count
  * means the hardware did not finish issued work within it.  Host pointer. */
 int sff_device_drain_timeouts(uint32_t* out);
+
+/* Integer throughput of the current device, measured (no counterpart in the
+ * paper; the roofline of the integer cost evaluations): kind 0 = dp4a (one
+ * 4-way int8 dot product with int32 accumulate per op), kind 1 = 32-bit
+ * integer multiply-add.  Eight independent chains per thread, 8 CTAs of 256
+ * threads per SM, best of three timed launches (CUDA events on `stream`)
+ * after a warm-up; *ops_per_s receives the operations per second.
+ * Synchronises `stream`; allocates nothing.  SFF_ERR_ARG for another kind or
+ * a NULL pointer. */
+int sff_int_peak(int32_t kind, double* ops_per_s, void* stream);
 
 /* Device-side error status, read at synchronisation (the calls themselves
  * only enqueue work and cannot see it).  Waits for the work enqueued on

@@ -59,16 +59,17 @@ class Params(ctypes.Structure):
 class Tuning(ctypes.Structure):
     """sff_tuning of include/sff.h: work distribution, never changes results."""
     _fields_ = [("lanes_per_pixel", ctypes.c_int32), ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32),
-                ("slots", ctypes.c_int32), ("coarse", (ctypes.c_int32 * 4) * 3), ("group_mb", ctypes.c_int32)]
+                ("slots", ctypes.c_int32), ("min_ctas", ctypes.c_int32), ("coarse", (ctypes.c_int32 * 5) * 3),
+                ("group_mb", ctypes.c_int32), ("pair_fields", ctypes.c_int32)]
 
     def as_tuple(self):
         """(lanes, tile_x, tile_y) of scale 0 (the throughput-form space)."""
         return (self.lanes_per_pixel, self.tile_x, self.tile_y)
 
     def scale_variants(self):
-        """[(lanes, slots, tile_x, tile_y)] of scales 0..3; (0, 0, 0, 0) = derived."""
-        return [(self.lanes_per_pixel, self.slots, self.tile_x, self.tile_y)] + \
-            [tuple(self.coarse[k][j] for j in range(4)) for k in range(3)]
+        """[(lanes, slots, tile_x, tile_y, min_ctas)] of scales 0..3; all zero = derived."""
+        return [(self.lanes_per_pixel, self.slots, self.tile_x, self.tile_y, self.min_ctas)] + \
+            [tuple(self.coarse[k][j] for j in range(5)) for k in range(3)]
 
 
 TILES = ((64, 16), (32, 16), (64, 8), (32, 8), (16, 8), (8, 8))
@@ -80,11 +81,14 @@ def _lat_fits(group: int, tx: int, ty: int) -> bool:
     return (group * ((tx + 2) // 2) * (ty + 1) + 31) // 32 * 32 <= 1024
 
 
-# Every variant (lanes, slots, tile_x, tile_y) of the iteration kernel: the
-# throughput form (slots 0) and the latency form (slots 1 or 4) on every tile
-# whose region fits one cell per lane group in 1024 threads.
-VARIANT_SPACE = [(l, 0, tx, ty) for l in (1, 2, 4) for (tx, ty) in TILES] + \
-    [(l, c, tx, ty) for (l, c) in ((1, 1), (2, 1), (4, 1), (1, 4), (2, 4), (4, 4)) for (tx, ty) in TILES
+# Every variant (lanes, slots, tile_x, tile_y, min_ctas) of the iteration
+# kernel: the throughput form (slots 0), four of its one-lane tiles also with a
+# register budget for min_ctas resident CTAs per SM, and the latency form
+# (slots 1 or 4) on every tile whose region fits one cell per lane group in
+# 1024 threads.
+VARIANT_SPACE = [(l, 0, tx, ty, 0) for l in (1, 2, 4) for (tx, ty) in TILES] + \
+    [(1, 0, 64, 16, 2), (1, 0, 32, 16, 4), (1, 0, 32, 8, 7), (1, 0, 32, 8, 8)] + \
+    [(l, c, tx, ty, 0) for (l, c) in ((1, 1), (2, 1), (4, 1), (1, 4), (2, 4), (4, 4)) for (tx, ty) in TILES
      if _lat_fits(l * c, tx, ty)]
 
 
@@ -219,6 +223,8 @@ def lib():
         L.sff_device_status.restype = i32
         L.sff_debug_knn_withhold.argtypes = [i32, i32]
         L.sff_debug_knn_withhold.restype = i32
+        L.sff_int_peak.argtypes = [i32, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+        L.sff_int_peak.restype = i32
         L.sff_status_string.argtypes = [i32]
         L.sff_status_string.restype = ctypes.c_char_p
         _lib = L
@@ -348,14 +354,18 @@ def default_tuning() -> Tuning:
     return t
 
 
-def make_tuning(lanes: int, tile_x: int, tile_y: int, slots: int = 0, coarse=None, group_mb: int = 0) -> Tuning:
-    """sff_tuning: scale 0 (lanes, slots, tile); coarse = [(lanes, slots, tile_x, tile_y)] for
-    scales 1.. (None or (0, 0, 0, 0) entries: derived from the grid size); group_mb: the
-    batch's scale-0 sweep schedule (0: all quads in every launch)."""
-    t = Tuning(lanes, tile_x, tile_y, slots)
+def make_tuning(lanes: int, tile_x: int, tile_y: int, slots: int = 0, coarse=None, group_mb: int = 0,
+                pair_fields: int = 0, min_ctas: int = 0) -> Tuning:
+    """sff_tuning: scale 0 (lanes, slots, tile, min_ctas); coarse = [(lanes, slots, tile_x,
+    tile_y[, min_ctas])] for scales 1.. (None or all-zero entries: derived from the grid
+    size); group_mb: the batch's scale-0 sweep schedule (0: all quads in every launch);
+    pair_fields: a quad's two fields alternate tile by tile in each launch."""
+    t = Tuning(lanes, tile_x, tile_y, slots, min_ctas)
     t.group_mb = int(group_mb)
+    t.pair_fields = int(pair_fields)
     for k, v in enumerate(coarse or []):
-        for j in range(4):
+        v = tuple(v) + (0,) * (5 - len(v))
+        for j in range(5):
             t.coarse[k][j] = int(v[j])
     if not lib().sff_tuning_supported(ctypes.byref(t)):
         raise SffError(f"unsupported tuning {(lanes, tile_x, tile_y, slots, coarse)}")
@@ -544,6 +554,13 @@ def device_status(stream=None, reset: bool = False) -> int:
 def check_device_status(stream=None, what: str = "device status") -> None:
     """Raises SffError (with .status) unless device_status(stream, reset=True) is OK."""
     _check(device_status(stream, reset=True), what)
+
+
+def int_peak(kind: str = "dp4a", stream=None) -> float:
+    """Measured integer throughput (ops/s) of the current device: "dp4a" or "imad"."""
+    v = ctypes.c_double(0.0)
+    _check(lib().sff_int_peak({"dp4a": 0, "imad": 1}[kind], ctypes.byref(v), _stream(stream)), "sff_int_peak")
+    return v.value
 
 
 def debug_knn_withhold(step: int, wait_limit_us: int = 0) -> None:

@@ -961,21 +961,33 @@ __host__ __device__ constexpr int iter_threads() {
 struct IterStep {
     int n, s, dx, dy, it;
     int last;  // the scale's last iteration: also the colour-0 search of this iteration (phase 3)
-    int f0;    // first field of the launch: blockIdx.z picks field f0 + blockIdx.z
+    int f0;    // first field of the launch
+    int pair;  // 0: blockIdx.z picks field f0 + z; 1: fields f0 + 2z and f0 + 2z + 1 (one quad's
+               // forward and inverse) alternate along blockIdx.x, so their CTAs of one tile
+               // position run side by side
 };
 
-template <int L, int TX, int TY>
-__global__ void __launch_bounds__(iter_threads<L, TX, TY>()) k_iteration(const __grid_constant__ Fields F, IterStep H) {
+// Field and tile column of this CTA.
+__device__ __forceinline__ int iter_field(const IterStep& H) {
+    return H.f0 + (H.pair ? 2 * (int)blockIdx.z + (int)(blockIdx.x & 1) : (int)blockIdx.z);
+}
+__device__ __forceinline__ int iter_tile_x(const IterStep& H) { return H.pair ? (int)(blockIdx.x >> 1) : (int)blockIdx.x; }
+
+// MB > 0: compiled for at least MB resident CTAs per SM (a register budget
+// of 64K / (MB x threads)), so that a launch of few CTAs per SM fits one wave.
+template <int L, int TX, int TY, int MB>
+__global__ void __launch_bounds__(iter_threads<L, TX, TY>(), MB) k_iteration(const __grid_constant__ Fields F,
+                                                                              IterStep H) {
     constexpr int kRegX = TX + 1, kRegY = TY + 1;
     constexpr int kGroups = iter_threads<L, TX, TY>() / L;
     __shared__ uint2 s_vec[kRegX * kRegY];
     __shared__ int s_cost[kRegX * kRegY];
-    const Field& A = F.f[H.f0 + blockIdx.z];
+    const Field& A = F.f[iter_field(H)];
     const Views& V = A.V;
     const int q = threadIdx.x & (L - 1);
     const unsigned gmask = group_mask<L>();
     const int grp = threadIdx.x / L;
-    const int tx0 = blockIdx.x * TX, ty0 = blockIdx.y * TY;
+    const int tx0 = iter_tile_x(H) * TX, ty0 = blockIdx.y * TY;
     const int gw = A.gw, gh = A.gh;
     if (tx0 >= gw || ty0 >= gh) return;  // tile beyond this field's grid (whole CTA)
     const int rx0 = tx0 - (H.dx > 0 ? 1 : 0), ry0 = ty0 - (H.dy > 0 ? 1 : 0);  // region origin
@@ -1165,13 +1177,13 @@ __global__ void __launch_bounds__(lat_threads<L * C, TX, TY>()) k_iteration_lat(
     constexpr int kHalfRow = (kRegX + 1) / 2, kTileHalfRow = TX / 2;
     __shared__ uint2 s_vec[kRegX * kRegY];
     __shared__ int s_cost[kRegX * kRegY];
-    const Field& A = F.f[H.f0 + blockIdx.z];
+    const Field& A = F.f[iter_field(H)];
     const Views& V = A.V;
     const int g = threadIdx.x & (G - 1);
     const int q = g & (L - 1), slot = g / L;
     const unsigned gmask = group_mask<G>();
     const int grp = threadIdx.x / G;  // this group's cell in each phase
-    const int tx0 = blockIdx.x * TX, ty0 = blockIdx.y * TY;
+    const int tx0 = iter_tile_x(H) * TX, ty0 = blockIdx.y * TY;
     const int gw = A.gw, gh = A.gh;
     if (tx0 >= gw || ty0 >= gh) return;  // tile beyond this field's grid (whole CTA)
     const int rx0 = tx0 - (H.dx > 0 ? 1 : 0), ry0 = ty0 - (H.dy > 0 ? 1 : 0);
@@ -1673,17 +1685,20 @@ __global__ void k_sift_search(SiftViews S, int gw, int gh, int s, int it, int mi
 // k_iteration_lat with that many candidate slots of L lanes.
 using IterKernel = void (*)(Fields, IterStep);
 struct IterVariant {
-    int lanes, slots, tx, ty;
+    int lanes, slots, tx, ty, ctas;
     IterKernel k;
     int threads;
 };
-#define SFF_ITER_V(L, X, Y) {L, 0, X, Y, k_iteration<L, X, Y>, iter_threads<L, X, Y>()}
+#define SFF_ITER_V(L, X, Y) {L, 0, X, Y, 0, k_iteration<L, X, Y, 0>, iter_threads<L, X, Y>()}
+#define SFF_ITER_VB(L, X, Y, MB) {L, 0, X, Y, MB, k_iteration<L, X, Y, MB>, iter_threads<L, X, Y>()}
 #define SFF_ITER_VARIANTS(L)                                                                        \
     SFF_ITER_V(L, 64, 16), SFF_ITER_V(L, 32, 16), SFF_ITER_V(L, 64, 8), SFF_ITER_V(L, 32, 8), \
         SFF_ITER_V(L, 16, 8), SFF_ITER_V(L, 8, 8)
-#define SFF_LAT_V(L, C, X, Y) {L, C, X, Y, k_iteration_lat<L, C, X, Y>, lat_threads<L * C, X, Y>()}
+#define SFF_LAT_V(L, C, X, Y) {L, C, X, Y, 0, k_iteration_lat<L, C, X, Y>, lat_threads<L * C, X, Y>()}
 const IterVariant kIterVariants[] = {
     SFF_ITER_VARIANTS(1), SFF_ITER_VARIANTS(2), SFF_ITER_VARIANTS(4),
+    // throughput form with a register budget for more resident CTAs per SM
+    SFF_ITER_VB(1, 64, 16, 2), SFF_ITER_VB(1, 32, 16, 4), SFF_ITER_VB(1, 32, 8, 7), SFF_ITER_VB(1, 32, 8, 8),
     // latency form: every tile whose region fits one cell per group in 1024 threads
     SFF_LAT_V(1, 1, 64, 16), SFF_LAT_V(1, 1, 32, 16), SFF_LAT_V(1, 1, 64, 8), SFF_LAT_V(1, 1, 32, 8),
     SFF_LAT_V(1, 1, 16, 8), SFF_LAT_V(1, 1, 8, 8),
@@ -1695,22 +1710,23 @@ const IterVariant kIterVariants[] = {
     SFF_LAT_V(4, 4, 8, 8)};
 #undef SFF_LAT_V
 #undef SFF_ITER_VARIANTS
+#undef SFF_ITER_VB
 #undef SFF_ITER_V
 
-const IterVariant* find_variant(int lanes, int slots, int tx, int ty) {
+const IterVariant* find_variant(int lanes, int slots, int tx, int ty, int ctas) {
     for (const auto& v : kIterVariants)
-        if (v.lanes == lanes && v.slots == slots && v.tx == tx && v.ty == ty) return &v;
+        if (v.lanes == lanes && v.slots == slots && v.tx == tx && v.ty == ty && v.ctas == ctas) return &v;
     return nullptr;
 }
 
 // A tuning is valid when its scale-0 variant exists and every coarse entry is
 // either all zero (chosen from the grid size) or an existing variant.
 bool tuning_valid(const sff_tuning& t) {
-    if (!find_variant(t.lanes_per_pixel, t.slots, t.tile_x, t.tile_y)) return false;
-    if (t.group_mb < 0 || t.group_mb > (1 << 20)) return false;
+    if (!find_variant(t.lanes_per_pixel, t.slots, t.tile_x, t.tile_y, t.min_ctas)) return false;
+    if (t.group_mb < 0 || t.group_mb > (1 << 20) || (t.pair_fields != 0 && t.pair_fields != 1)) return false;
     for (int k = 0; k < SFF_MAX_SCALES - 1; ++k) {
         const int32_t* c = t.coarse[k];
-        if ((c[0] | c[1] | c[2] | c[3]) != 0 && !find_variant(c[0], c[1], c[2], c[3])) return false;
+        if ((c[0] | c[1] | c[2] | c[3] | c[4]) != 0 && !find_variant(c[0], c[1], c[2], c[3], c[4])) return false;
     }
     return true;
 }
@@ -1728,12 +1744,12 @@ constexpr int kSmCount = 152;
 constexpr long kPixPerSmSlots = 200;
 
 const IterVariant* variant_for_scale(const sff_tuning& t, int s, const int* gw, const int* gh, int nf) {
-    if (s == 0) return find_variant(t.lanes_per_pixel, t.slots, t.tile_x, t.tile_y);
+    if (s == 0) return find_variant(t.lanes_per_pixel, t.slots, t.tile_x, t.tile_y, t.min_ctas);
     const int32_t* c = t.coarse[s - 1];
-    if ((c[0] | c[1] | c[2] | c[3]) != 0) return find_variant(c[0], c[1], c[2], c[3]);
+    if ((c[0] | c[1] | c[2] | c[3] | c[4]) != 0) return find_variant(c[0], c[1], c[2], c[3], c[4]);
     long px = 0;
     for (int k = 0; k < nf; ++k) px += (long)gw[k] * gh[k];
-    return px / kSmCount < kPixPerSmSlots ? find_variant(1, 4, 16, 8) : find_variant(1, 0, 32, 16);
+    return px / kSmCount < kPixPerSmSlots ? find_variant(1, 4, 16, 8, 0) : find_variant(1, 0, 32, 16, 0);
 }
 
 int coarse_gq(int w, int h, const sff_params& p) {
@@ -1915,7 +1931,13 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
                 ggh = std::max(ggh, gh[k]);
             }
             const IterVariant* sv = variant_for_scale(T, s, gw + f0, gh + f0, f1 - f0);
-            dim3 gi((ggw + sv->tx - 1) / sv->tx, (ggh + sv->ty - 1) / sv->ty, f1 - f0);
+            // pairs: every field f0 + 2j, f0 + 2j + 1 one quad's two fields
+            bool pair = T.pair_fields != 0 && ((f1 - f0) & 1) == 0;
+            for (int k = f0; pair && k < f1; k += 2)
+                pair = spec[k + 1].width == spec[k].width && spec[k + 1].height == spec[k].height &&
+                       spec[k + 1].ref == spec[k].crs;
+            const unsigned tiles_x = (ggw + sv->tx - 1) / sv->tx;
+            dim3 gi(pair ? 2 * tiles_x : tiles_x, (ggh + sv->ty - 1) / sv->ty, pair ? (f1 - f0) / 2 : f1 - f0);
             if (I > 0 && ::sff::profiling()) ::sff::profile_mark(kIterNames[s], st, false);
             for (int it = 0; it < I; ++it) {
                 const int in = cur ^ (it & 1);
@@ -1925,7 +1947,7 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
                     F.f[k].field_out = Bf[in ^ 1][k];
                     F.f[k].cost_out = Bc[in ^ 1][k];
                 }
-                IterStep H{n, s, kDirs[it % 4][0], kDirs[it % 4][1], it, it == I - 1, f0};
+                IterStep H{n, s, kDirs[it % 4][0], kDirs[it % 4][1], it, it == I - 1, f0, pair ? 1 : 0};
                 sv->k<<<gi, sv->threads, 0, st>>>(F, H);
             }
             if (I > 0 && ::sff::profiling()) ::sff::profile_mark(kIterNames[s], st, true, I);

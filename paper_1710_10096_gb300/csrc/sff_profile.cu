@@ -116,3 +116,88 @@ extern "C" int sff_profile_collect(sff_kernel_time* out, int32_t capacity, int32
     sff::release_all();
     return status;
 }
+
+// ---------------------------------------------------------------------------
+// Integer peaks for the roofline of the matching kernels: dp4a and 32-bit
+// multiply-add throughput measured with CUDA events.  Each thread runs eight
+// independent dependency chains (enough to hide the pipeline latency with
+// several warps per scheduler); a result is stored only when it equals a
+// value the inputs never produce, which keeps the chains live.
+namespace sff {
+namespace {
+
+__device__ int g_peak_sink;
+
+constexpr int kPeakChains = 8;
+
+__global__ void __launch_bounds__(256) k_peak_dp4a(int iters, int seed) {
+    int acc[kPeakChains];
+    const int b = (int)(threadIdx.x * 0x01010101u) ^ seed;
+#pragma unroll
+    for (int k = 0; k < kPeakChains; ++k) acc[k] = (int)(threadIdx.x + 97 * k + blockIdx.x);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r)
+#pragma unroll
+            for (int k = 0; k < kPeakChains; ++k) acc[k] = __dp4a(acc[k], b, acc[k]);
+    }
+    int x = 0;
+#pragma unroll
+    for (int k = 0; k < kPeakChains; ++k) x ^= acc[k];
+    if (x == 0x7fedcba9) g_peak_sink = x;
+}
+
+__global__ void __launch_bounds__(256) k_peak_imad(int iters, int seed) {
+    int acc[kPeakChains];
+    const int b = (int)(threadIdx.x | 1u) ^ seed, c = (int)blockIdx.x;
+#pragma unroll
+    for (int k = 0; k < kPeakChains; ++k) acc[k] = (int)(threadIdx.x + 97 * k);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int r = 0; r < 16; ++r)
+#pragma unroll
+            for (int k = 0; k < kPeakChains; ++k) acc[k] = acc[k] * b + c;
+    }
+    int x = 0;
+#pragma unroll
+    for (int k = 0; k < kPeakChains; ++k) x ^= acc[k];
+    if (x == 0x7fedcba9) g_peak_sink = x;
+}
+
+}  // namespace
+}  // namespace sff
+
+extern "C" int sff_int_peak(int32_t kind, double* ops_per_s, void* stream) {
+    if (!ops_per_s || (kind != 0 && kind != 1)) return SFF_ERR_ARG;
+    const cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return SFF_ERR_CUDA;
+    constexpr int kThreads = 256, kPerSm = 8, kIters = 4096;
+    const int blocks = sms * kPerSm;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return SFF_ERR_CUDA;
+    int status = SFF_OK;
+    float best_ms = 0.f;
+    for (int rep = 0; rep < 4 && status == SFF_OK; ++rep) {  // the first launch warms up
+        cudaEventRecord(a, st);
+        if (kind == 0)
+            sff::k_peak_dp4a<<<blocks, kThreads, 0, st>>>(kIters, rep);
+        else
+            sff::k_peak_imad<<<blocks, kThreads, 0, st>>>(kIters, rep);
+        cudaEventRecord(b, st);
+        float ms = 0.f;
+        if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, a, b) != cudaSuccess)
+            status = SFF_ERR_CUDA;
+        else if (rep > 0 && (best_ms == 0.f || ms < best_ms))
+            best_ms = ms;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (status != SFF_OK || best_ms <= 0.f) return status ? status : SFF_ERR_CUDA;
+    const double ops = (double)blocks * kThreads * kIters * 16.0 * sff::kPeakChains;
+    *ops_per_s = ops / (best_ms * 1e-3);
+    return SFF_OK;
+}

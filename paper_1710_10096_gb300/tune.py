@@ -24,14 +24,14 @@ def size_bucket(width: int, height: int) -> str:
 
 
 def _tuning_of(per_scale) -> Tuning:
-    l, c, tx, ty = per_scale[0]
-    return make_tuning(l, tx, ty, c, per_scale[1:])
+    l, c, tx, ty, mb = per_scale[0]
+    return make_tuning(l, tx, ty, c, per_scale[1:], min_ctas=mb)
 
 
 def scale_times(pyramids, width: int, height: int, variant, params=None, reps: int = 3, stream=None) -> dict:
     """{scale: us per launch} of the iteration kernel with `variant`
-    (lanes, slots, tile_x, tile_y) at every scale, timed as one span of
-    events per scale in a CUDA graph of `reps` matching runs."""
+    (lanes, slots, tile_x, tile_y, min_ctas) at every scale, timed as one span
+    of events per scale in a CUDA graph of `reps` matching runs."""
     import torch
     params = params or default_params()
     dev = pyramids[0].device
@@ -39,8 +39,8 @@ def scale_times(pyramids, width: int, height: int, variant, params=None, reps: i
     out = [torch.empty((height, width, 4), dtype=torch.int16, device=dev) for _ in range(2)]
     cst = [torch.empty((height, width), dtype=torch.int32, device=dev) for _ in range(2)]
     s = stream or torch.cuda.Stream(device=dev)
-    l, c, tx, ty = variant
-    t = make_tuning(l, tx, ty, c, [variant] * (params.num_scales - 1))
+    l, c, tx, ty, mb = variant
+    t = make_tuning(l, tx, ty, c, [variant] * (params.num_scales - 1), min_ctas=mb)
     with torch.cuda.stream(s):
         match_quad_tuned(*pyramids, width, height, 1, t, out[0], cst[0], out[1], cst[1], ws, params, s)
         s.synchronize()
@@ -82,7 +82,7 @@ def autotune(pyramids, width: int, height: int, params=None, reps: int = 3, spac
         if verbose:
             print(f"variant {tuple(v)}: " + " ".join(f"s{s} {us:.2f} us" for s, us in sorted(times.items())))
     d = default_tuning().scale_variants()
-    per_scale = [best[s] if s < S and best[s] is not None else (d[s] if s == 0 else (0, 0, 0, 0)) for s in range(4)]
+    per_scale = [best[s] if s < S and best[s] is not None else (d[s] if s == 0 else (0,) * 5) for s in range(4)]
     _CACHE[key] = per_scale
     return _tuning_of(per_scale)
 
@@ -105,10 +105,10 @@ def load_cache(path: str) -> int:
     space = set(VARIANT_SPACE)
     for k, vs in entries.items():
         b, p = k.split("|")
-        if not (isinstance(vs, list) and len(vs) == 4 and all(isinstance(v, list) and len(v) == 4 for v in vs)):
+        if not (isinstance(vs, list) and len(vs) == 4 and all(isinstance(v, list) and len(v) == 5 for v in vs)):
             continue
         vs = [tuple(v) for v in vs]
-        if tuple(vs[0]) in space and all(v in space or v == (0, 0, 0, 0) for v in vs[1:]):
+        if tuple(vs[0]) in space and all(v in space or v == (0,) * 5 for v in vs[1:]):
             _CACHE[(b, tuple(int(x) for x in p.split(",")))] = vs
             taken += 1
     return taken

@@ -29,7 +29,8 @@ from __future__ import annotations
 import dataclasses
 import numpy as np
 
-__all__ = ["Quad", "make_quad", "make_shift_quad", "CONFIG_SIZES", "ground_truth", "SEED_RECORD", "sparse_seeds"]
+__all__ = ["Quad", "make_quad", "make_shift_quad", "CONFIG_SIZES", "ground_truth", "scene_ranges", "SEED_RECORD",
+           "sparse_seeds"]
 
 # (family, width, height) of the named workloads.
 CONFIG_SIZES = {
@@ -51,6 +52,11 @@ class Quad:
     occluded: np.ndarray  # [H, W] bool: not visible in all four views
     focal: float
     baseline: float
+    out_of_frame: np.ndarray = None  # [H, W] bool: of those, leaving the frame of a view
+
+    def ranges(self) -> dict:
+        """Measured ranges of the scene (scene_ranges)."""
+        return scene_ranges(self.gt, self.occluded, self.out_of_frame)
 
     @property
     def width(self) -> int:
@@ -262,13 +268,32 @@ def _ground_truth(surfs, cam0: _Camera, cam1: _Camera, W, H):
     gt = np.stack([x1 - xs, y1 - ys, f * B / Z0, f * B / Z1], -1)
     # visibility of the same surface point in R0, L1 and R1
     vis = sid >= 0
+    oof = np.zeros((H, W), bool)
     for cam, right, time, X in ((cam0, True, 0, X0), (cam1, False, 1, X1), (cam1, True, 1, X1)):
         px, py, Zp = cam.project(X, right)
         inside = (px >= -0.5) & (px <= W - 0.5) & (py >= -0.5) & (py <= H - 0.5) & (Zp > 0)
         sid2, Z2, _, _ = _raycast(surfs, cam, right, time, np.where(inside, px, 0.0), np.where(inside, py, 0.0))
         same = (sid2 == sid) & (np.abs(Z2 - Zp) <= 0.01 * np.abs(Zp) + 1e-3)
         vis &= inside & same
-    return gt, ~vis
+        oof |= (sid >= 0) & ~inside
+    return gt, ~vis, oof
+
+
+def scene_ranges(gt: np.ndarray, occluded: np.ndarray, out_of_frame: np.ndarray = None) -> dict:
+    """Ranges of a scene's ground truth over its visible pixels: disparity d0,
+    flow u and v, the fraction of pixels hidden by another surface in some
+    view while inside every frame ("occluded"), and of pixels leaving a
+    view's frame ("out_of_frame")."""
+    vis = ~occluded
+    r = {"d0_px": [round(float(gt[..., 2][vis].min()), 1), round(float(gt[..., 2][vis].max()), 1)],
+         "u_px": [round(float(gt[..., 0][vis].min()), 1), round(float(gt[..., 0][vis].max()), 1)],
+         "v_px": [round(float(gt[..., 1][vis].min()), 1), round(float(gt[..., 1][vis].max()), 1)]}
+    if out_of_frame is not None:
+        r["occluded"] = round(float((occluded & ~out_of_frame).mean()), 4)
+        r["out_of_frame"] = round(float(out_of_frame.mean()), 4)
+    else:
+        r["not_visible"] = round(float(occluded.mean()), 4)
+    return r
 
 
 def _finish(img, rng, noise_sigma=0.0, gain=1.0):
@@ -319,7 +344,9 @@ def _scene_planes(rng, W, H):
     surfs.append(_surface(rng, [0, 0, zb], [1, 0, 0], [0, 1, 0], half_w, half_h, zb, f))
     movers = {1, 2}
     for k in range(5):
-        z = 3.6 + 14.0 * rng.random()
+        # the two movers near the camera, so that their 0.2-0.3 m translation
+        # gives flows up to ~16 px
+        z = 3.8 + 1.7 * rng.random() if k in movers else 3.6 + 14.0 * rng.random()
         x = (rng.random() - 0.5) * z * W / f * 0.8
         y = (rng.random() - 0.5) * z * H / f * 0.6
         n = np.array([rng.normal() * 0.3, rng.normal() * 0.2, -1.0])
@@ -335,7 +362,7 @@ def _scene_planes(rng, W, H):
             R = _rot(_rand_unit(rng), np.deg2rad(2.0) * rng.random())
             ang = 2 * np.pi * rng.random()
             t = np.array([np.cos(ang), 0.5 * np.sin(ang), 0.3 * rng.normal()])
-            t *= (0.15 + 0.15 * rng.random()) / np.linalg.norm(t)
+            t *= (0.2 + 0.1 * rng.random()) / np.linalg.norm(t)
         surfs.append(_surface(rng, [x, y, z], a1, a2, e1, e2, z, f, R, t))
     cam0 = _Camera(C=np.zeros(3), R=np.eye(3), f=f, cx=(W - 1) / 2, cy=(H - 1) / 2, B=B)
     # small ego-motion so that static surfaces also move in the image
@@ -357,8 +384,15 @@ def _scene_driving(rng, W, H):
     for side in (-1, 1):
         x = side * (7.0 + 3.0 * rng.random())
         surfs.append(_surface(rng, [x, -2.0, 55.0], [0, 0, 1], [0, 1, 0], 50.0, 3.7, 20.0, f))
+    # a car parked on the left 3.05-3.25 m ahead: disparities up to ~127 px
+    # and flows beyond 100 px under the forward ego-motion
+    zc = 3.05 + 0.2 * rng.random()
+    car = np.array([1.7, 1.4, 3.8])
+    for (c, a1, a2, e1, e2) in _box_faces(np.array([-(1.9 + 0.3 * rng.random()), 1.65 - 0.7, zc + car[2] / 2]),
+                                          car, 0.0):
+        surfs.append(_surface(rng, c, a1, a2, e1, e2, zc, f))
     # boxes and planes
-    n_obj = 0
+    n_obj = 4
     while n_obj < 16:
         z = 5.0 + 45.0 * rng.random()
         x = (rng.random() - 0.5) * 16.0
@@ -435,7 +469,7 @@ def _scene_movie(rng, W, H):
         e1 = z * W / f * 0.08
         e2 = z * H / f * 0.12
         R = _rot(_rand_unit(rng), np.deg2rad(5.0) * rng.random())
-        t = np.array([(rng.random() - 0.5) * 2.0, (rng.random() - 0.5) * 0.8, -0.5 * rng.random()]) * z / f * 200
+        t = np.array([(rng.random() - 0.5) * 2.0, (rng.random() - 0.5) * 0.8, -0.5 * rng.random()]) * z / f * 250
         surfs.append(_surface(rng, [x, y, z], [1, 0, 0], [0, 1, 0], e1, e2, z, f, R, t))
     cam0 = _Camera(C=np.zeros(3), R=np.eye(3), f=f, cx=(W - 1) / 2, cy=(H - 1) / 2, B=B)
     cam1 = _Camera(C=np.array([0.15, 0.0, 0.3]), R=_rot(np.array([0, 1.0, 0]), np.deg2rad(1.5)), f=f,
@@ -458,10 +492,10 @@ def make_quad(family: str, width: int, height: int, seed: int, supersample: int 
         imgs.append(_finish(img, rng, extra["noise"], extra["gain"][k]))
     L0, R0, L1, R1 = imgs
     if with_gt:
-        gt, occ = _ground_truth(surfs, cam0, cam1, width, height)
+        gt, occ, oof = _ground_truth(surfs, cam0, cam1, width, height)
     else:
-        gt, occ = np.zeros((height, width, 4)), np.zeros((height, width), bool)
-    return Quad(L0, R0, L1, R1, gt, occ, cam0.f, cam0.B)
+        gt, occ, oof = np.zeros((height, width, 4)), np.zeros((height, width), bool), None
+    return Quad(L0, R0, L1, R1, gt, occ, cam0.f, cam0.B, oof)
 
 
 def ground_truth(family: str, width: int, height: int, seed: int):
@@ -469,7 +503,7 @@ def ground_truth(family: str, width: int, height: int, seed: int):
     make_quad(family, width, height, seed) renders, without rendering it."""
     rng = np.random.default_rng(seed)
     surfs, cam0, cam1, _ = _FAMILIES[family](rng, width, height)
-    gt, occ = _ground_truth(surfs, cam0, cam1, width, height)
+    gt, occ, _ = _ground_truth(surfs, cam0, cam1, width, height)
     return gt, occ, cam0.f, cam0.B
 
 

@@ -315,7 +315,9 @@ def test_every_tuning_gives_identical_fields(env):
     # the throughput form at scale 0 (coarse scales derived), then every
     # variant of both forms at all four scales
     space = [sff.make_tuning(*cand) for cand in sff.TUNING_SPACE]
-    space += [sff.make_tuning(l, tx, ty, c, [(l, c, tx, ty)] * 3) for (l, c, tx, ty) in sff.VARIANT_SPACE]
+    space += [sff.make_tuning(v[0], v[2], v[3], v[1], [v] * 3, min_ctas=v[4]) for v in sff.VARIANT_SPACE]
+    # the schedules: the two fields of the quad alternating tile by tile
+    space += [sff.make_tuning(1, 32, 16, 0, None, 0, 1), sff.make_tuning(1, 8, 8, 4, [(1, 4, 8, 8)] * 3, 0, 1)]
     for t in space:
         cand = t.scale_variants()
         out = [torch.empty((h, w, 4), dtype=torch.int16, device="cuda") for _ in range(2)]
@@ -333,8 +335,9 @@ def test_every_tuning_gives_identical_fields(env):
 
 @pytest.mark.parametrize("size", [(250, 77), (97, 41)])
 def test_latency_form_on_ragged_grids(env, size):
-    # the latency form of the iteration kernel (slots 1 and 4) on grids that
-    # leave partial tiles at every scale, against the oracle
+    # the latency form of the iteration kernel (slots 1 and 4) and the
+    # register-budgeted throughput form on grids that leave partial tiles at
+    # every scale, against the oracle
     torch, sff, orc = env
     w, h = size
     q = scenegen.make_quad("planes", w, h, seed=w + h)
@@ -342,16 +345,16 @@ def test_latency_form_on_ragged_grids(env, size):
     pyrs = [_gpu_features(torch, sff, im, p)[0] for im in q.images()]
     ws = torch.empty(sff.workspace_bytes(w, h, p), dtype=torch.uint8, device="cuda")
     o = orc.run_quad(*q.images(), seed=9)
-    for (l, c, tx, ty) in [v for v in sff.VARIANT_SPACE if v[1] > 0]:
-        t = sff.make_tuning(l, tx, ty, c, [(l, c, tx, ty)] * 3)
+    for (l, c, tx, ty, mb) in [v for v in sff.VARIANT_SPACE if v[1] > 0 or v[4] > 0]:
+        t = sff.make_tuning(l, tx, ty, c, [(l, c, tx, ty, mb)] * 3, min_ctas=mb)
         out = [torch.empty((h, w, 4), dtype=torch.int16, device="cuda") for _ in range(2)]
         cst = [torch.empty((h, w), dtype=torch.int32, device="cuda") for _ in range(2)]
         sff.match_quad_tuned(*pyrs, w, h, 9, t, out[0], cst[0], out[1], cst[1], ws, p)
         torch.cuda.synchronize()
-        assert np.array_equal(out[0].cpu().numpy(), o["fwd"]), (l, c, tx, ty)
-        assert np.array_equal(out[1].cpu().numpy(), o["inv"]), (l, c, tx, ty)
-        assert np.array_equal(cst[0].cpu().numpy(), o["fwd_cost"]), (l, c, tx, ty)
-        assert np.array_equal(cst[1].cpu().numpy(), o["inv_cost"]), (l, c, tx, ty)
+        assert np.array_equal(out[0].cpu().numpy(), o["fwd"]), (l, c, tx, ty, mb)
+        assert np.array_equal(out[1].cpu().numpy(), o["inv"]), (l, c, tx, ty, mb)
+        assert np.array_equal(cst[0].cpu().numpy(), o["fwd_cost"]), (l, c, tx, ty, mb)
+        assert np.array_equal(cst[1].cpu().numpy(), o["inv_cost"]), (l, c, tx, ty, mb)
 
 
 def test_batch_of_uneven_quads_equals_each_alone(env):
@@ -365,19 +368,24 @@ def test_batch_of_uneven_quads_equals_each_alone(env):
         q = (scenegen.make_shift_quad(w, h, sd, u=-3, v=2, d0=4, d1=6) if fam == "shift"
              else scenegen.make_quad(fam, w, h, sd))
         quads.append((q, ms))
+    refs = [orc.run_quad(*q.images(), seed=ms) for q, ms in quads]
     bm = sff.BatchMatcher([(q.width, q.height) for q, _ in quads])
     for k, (q, _) in enumerate(quads):
         bm.load(k, *q.images())
-    bm.run([ms for _, ms in quads])
-    torch.cuda.synchronize()
-    for (q, ms), b in zip(quads, bm.quads):
-        ref = orc.run_quad(*q.images(), seed=ms)
-        assert np.array_equal(b.fwd.cpu().numpy(), ref["fwd"])
-        assert np.array_equal(b.inv.cpu().numpy(), ref["inv"])
-        assert np.array_equal(b.fwd_cost.cpu().numpy(), ref["fwd_cost"])
-        assert np.array_equal(b.keep.cpu().numpy(), ref["keep"])
-        assert np.array_equal(b.cerr.cpu().numpy(), ref["cerr"])
-        assert b.seeds_numpy().tobytes() == ref["seeds"].tobytes()
+    # sweep schedules of scale 0: all quads in every launch, every quad alone
+    # (a budget below any quad), about two quads per group, and each with the
+    # two fields of a quad alternating tile by tile
+    for group_mb, pair in ((0, 0), (1, 0), (4, 0), (0, 1), (4, 1)):
+        bm.tuning = sff.make_tuning(1, 32, 16, 0, None, group_mb, pair)
+        bm.run([ms for _, ms in quads])
+        torch.cuda.synchronize()
+        for (q, ms), b, ref in zip(quads, bm.quads, refs):
+            assert np.array_equal(b.fwd.cpu().numpy(), ref["fwd"]), (group_mb, pair)
+            assert np.array_equal(b.inv.cpu().numpy(), ref["inv"]), (group_mb, pair)
+            assert np.array_equal(b.fwd_cost.cpu().numpy(), ref["fwd_cost"]), (group_mb, pair)
+            assert np.array_equal(b.keep.cpu().numpy(), ref["keep"]), (group_mb, pair)
+            assert np.array_equal(b.cerr.cpu().numpy(), ref["cerr"]), (group_mb, pair)
+            assert b.seeds_numpy().tobytes() == ref["seeds"].tobytes(), (group_mb, pair)
 
 
 def test_mixed_32_quad_batch_equals_oracle(env):

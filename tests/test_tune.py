@@ -26,15 +26,16 @@ def test_cache_round_trip_skips_unsupported_entries(tmp_path):
     try:
         tune._CACHE.clear()
         params = tuple(sff.default_params().as_dict().values())
-        good = [sff.VARIANT_SPACE[1], (1, 0, 32, 16), (0, 0, 0, 0), (1, 4, 16, 8)]
+        good = [sff.VARIANT_SPACE[1], (1, 0, 32, 16, 4), (0, 0, 0, 0, 0), (1, 4, 16, 8, 0)]
         tune._CACHE[("1280x384", params)] = good
         path = tmp_path / "tuning.json"
         tune.save_cache(str(path))
         data = json.loads(path.read_text())
         pk = ",".join(map(str, params))
-        data["640x192|" + pk] = [[3, 0, 32, 8]] * 4  # not a supported variant
-        data["512x160|" + pk] = [[4, 4, 16, 8]] * 4  # a region that does not fit 1024 threads
-        data["256x96|" + pk] = [1, 0, 32, 8]  # the old (one variant) format
+        data["640x192|" + pk] = [[3, 0, 32, 8, 0]] * 4  # not a supported variant
+        data["512x160|" + pk] = [[4, 4, 16, 8, 0]] * 4  # a region that does not fit 1024 threads
+        data["256x96|" + pk] = [1, 0, 32, 8]  # an old (one variant) format
+        data["128x64|" + pk] = [[1, 0, 32, 8]] * 4  # an old (four-field variant) format
         path.write_text(json.dumps(data))
         tune._CACHE.clear()
         assert tune.load_cache(str(path)) == 1
@@ -51,13 +52,14 @@ def test_variant_space_matches_the_library():
     # every listed variant is accepted at every scale; nearby settings that
     # the library does not instantiate are refused
     for v in sff.VARIANT_SPACE:
-        l, c, tx, ty = v
-        t = sff.make_tuning(l, tx, ty, c, [v] * 3)
+        l, c, tx, ty, mb = v
+        t = sff.make_tuning(l, tx, ty, c, [v] * 3, min_ctas=mb)
         assert t.scale_variants() == [v] * 4
-    for bad in [(4, 4, 16, 8), (2, 4, 32, 8), (4, 1, 64, 8), (2, 1, 64, 16), (1, 2, 32, 8), (3, 0, 32, 8)]:
+    for bad in [(4, 4, 16, 8, 0), (2, 4, 32, 8, 0), (4, 1, 64, 8, 0), (2, 1, 64, 16, 0), (1, 2, 32, 8, 0),
+                (3, 0, 32, 8, 0), (1, 0, 32, 16, 3), (2, 0, 32, 16, 4), (1, 1, 32, 16, 4)]:
         assert bad not in sff.VARIANT_SPACE
         with pytest.raises(sff.SffError):
-            sff.make_tuning(bad[0], bad[2], bad[3], bad[1])
+            sff.make_tuning(bad[0], bad[2], bad[3], bad[1], min_ctas=bad[4])
         with pytest.raises(sff.SffError):
             sff.make_tuning(1, 32, 16, 0, [bad])
-    assert len(sff.VARIANT_SPACE) == 38
+    assert len(sff.VARIANT_SPACE) == 42
