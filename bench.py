@@ -258,11 +258,15 @@ def bench_batched(sff, torch, dev, quads, seeds, params, tuning, steps, warmup):
     """Matched px/s of the 32-quad batch: one CUDA graph of shared launches
     (sff_run_batch) vs the plain per-quad form (one graph per quad, replayed
     one after the other); outputs compared for identity."""
+    from paper_1710_10096_gb300 import tune
     sizes = [(im[0].shape[1], im[0].shape[0]) for im in quads]
     px = sum(w * h for w, h in sizes)
     bm = sff.BatchMatcher(sizes, params, device=dev, tuning=tuning)
     for k, im in enumerate(quads):
         bm.load(k, *im)
+    # the batch's own scale-0 variant and schedules (autotuned on the batch);
+    # the plain per-quad form below keeps the tuning passed in
+    batch_tuning = tune.autotune_batch(bm, seeds)
     g_batch = bm.capture(seeds)
     # plain: one matcher + graph per quad
     plain = []
@@ -318,6 +322,12 @@ def bench_batched(sff, torch, dev, quads, seeds, params, tuning, steps, warmup):
            "px_per_step": px, "value": px / t_batch, "unit": "px/s", "ms_per_step": 1e3 * t_batch,
            "plain_value": px / t_plain, "plain_ms_per_step": 1e3 * t_plain, "speedup_vs_plain": t_plain / t_batch,
            "identical_to_plain": bool(same), "cuda_graph": True,
+           "tuning": {"scale0": list(batch_tuning.scale_variants()[0]), "pair_fields": batch_tuning.pair_fields,
+                      "alternate_order": batch_tuning.alternate_order,
+                      "coarse": "derived from the batch's grid sizes",
+                      "plain_per_quad": {"scale0": list(tuning.scale_variants()[0]), "pair_fields": tuning.pair_fields,
+                                         "alternate_order": tuning.alternate_order,
+                                         "coarse": "derived from each quad's grid sizes"}},
            "kernels_ms": breakdown, "k_iteration_per_scale": per_scale}
     del bm, plain, g_batch
     torch.cuda.empty_cache()
@@ -766,7 +776,7 @@ def workload_config(workload, q, params, world):
     with which parameters and seeds, and the cache condition of the timing."""
     return {"workload": workload, "width": q.width, "height": q.height, "quads_per_step": 1,
             "parallelism": f"replicas{world}", "params": dict(params), "scene_seed": SCENE_SEED,
-            "match_seed": MATCH_SEED,
+            "match_seed": MATCH_SEED, "scene_ranges": q.ranges(),
             "l2": "GPU arm: L2 flushed between timed steps (256 MB write outside the step events)"}
 
 
@@ -861,8 +871,8 @@ def main():
         tuning = sff.make_tuning(*(int(v) for v in args.tuning.split(",")))
     # the batch and the server take the tuned scale-0 variant with the coarse
     # scales derived from their (much larger) launch sizes
-    batch_tuning = sff.make_tuning(tuning.lanes_per_pixel, tuning.tile_x, tuning.tile_y, tuning.slots,
-                                   min_ctas=tuning.min_ctas)
+    batch_tuning = sff.make_tuning(tuning.lanes_per_pixel, tuning.tile_x, tuning.tile_y, tuning.slots, None, 0,
+                                   tuning.pair_fields, tuning.min_ctas, tuning.alternate_order & 1)
     m = sff.QuadMatcher(q.width, q.height, params, device=dev, tuning=tuning)
     stream = torch.cuda.Stream(device=dev)
     host_in = torch.empty((4, q.height, q.width, 3), dtype=torch.uint8).pin_memory()
@@ -979,7 +989,9 @@ def main():
             "config": workload_config(args.workload, q, params.as_dict(), world),
             "launch": {"cuda_graph": True,
                        "tuning_per_scale": [list(v) for v in tuning.scale_variants()],
-                       "tuning_fields": "(lanes per pixel, candidate slots, tile_x, tile_y) of scales 0..3"},
+                       "tuning_fields": "(lanes per pixel, candidate slots, tile_x, tile_y, min CTAs per SM) of "
+                                        "scales 0..3",
+                       "pair_fields": tuning.pair_fields, "alternate_order_bits": tuning.alternate_order},
             "roofline": roof, "gpu_launches": int(round(launches_per_step * args.steps)),
             "e2e": e2e, "clocks": clk, "kernels": kernels, "seeds": n_seeds,
             "device_status": sff.lib().sff_status_string(dev_status).decode(), "device_timeouts": dev_timeouts}

@@ -115,6 +115,9 @@ typedef struct sff_tuning {
     int32_t pair_fields;     /* CTA order of the iteration kernel: 0 = field after field;
                               * 1 = a quad's forward and inverse field alternate tile by tile
                               * (their CTAs read the same four images side by side) */
+    int32_t alternate_order; /* bit s set (s = 0..3): at scale s every other iteration launch
+                              * visits its tiles last-to-first, so that it starts on what the
+                              * previous launch read last (still in L2); 0..15 */
 } sff_tuning;
 
 /* One seed of Sec. 3.2: pixel (x, y) of L0, its vector and its scores. 20 bytes.
@@ -161,6 +164,19 @@ size_t sff_workspace_bytes(int32_t width, int32_t height, const sff_params* para
 int sff_features(const uint8_t* rgb_dev, int32_t width, int32_t height, int32_t pitch_bytes,
                  const sff_params* params, uint8_t* pyramid_dev,
                  void* workspace, size_t workspace_bytes, void* stream);
+
+/* sff_features with the transform on the tensor cores: per scale and
+ * channel, the kept coefficients of 128 pixels of a row as one matrix product
+ * of their 8x8 patches (fp16, exact integers 0..255) with the 16 kept
+ * Walsh-Hadamard basis products (+-1), accumulated in fp32 (exact: every
+ * partial sum is an integer of magnitude <= 16320).  Same arguments, same
+ * pyramid, bit for bit, as sff_features (Sec. 3.1, "Initialization").  Its
+ * only device waits (for the MMAs of a tile) are bounded: a wait that gives
+ * up leaves that image's records of the scale incomplete and raises
+ * SFF_ERR_TIMEOUT in sff_device_status. */
+int sff_features_tc(const uint8_t* rgb_dev, int32_t width, int32_t height, int32_t pitch_bytes,
+                    const sff_params* params, uint8_t* pyramid_dev,
+                    void* workspace, size_t workspace_bytes, void* stream);
 
 /* One dense scene-flow field (Sec. 3.1, "Initialization" and "Multi-Scale
  * Propagation"; "Consistency Check" for the inverse field).

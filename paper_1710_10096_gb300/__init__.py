@@ -60,7 +60,7 @@ class Tuning(ctypes.Structure):
     """sff_tuning of include/sff.h: work distribution, never changes results."""
     _fields_ = [("lanes_per_pixel", ctypes.c_int32), ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32),
                 ("slots", ctypes.c_int32), ("min_ctas", ctypes.c_int32), ("coarse", (ctypes.c_int32 * 5) * 3),
-                ("group_mb", ctypes.c_int32), ("pair_fields", ctypes.c_int32)]
+                ("group_mb", ctypes.c_int32), ("pair_fields", ctypes.c_int32), ("alternate_order", ctypes.c_int32)]
 
     def as_tuple(self):
         """(lanes, tile_x, tile_y) of scale 0 (the throughput-form space)."""
@@ -164,6 +164,8 @@ def lib():
         L.sff_workspace_bytes.restype = sz
         L.sff_features.argtypes = [P, i32, i32, i32, PP, P, P, sz, P]
         L.sff_features.restype = i32
+        L.sff_features_tc.argtypes = [P, i32, i32, i32, PP, P, P, sz, P]
+        L.sff_features_tc.restype = i32
         L.sff_match_views.argtypes = [P, P, P, P, i32, i32, i32, ctypes.c_uint64, PP, P, P, P, sz, P]
         L.sff_match_views.restype = i32
         L.sff_match_views_sequential.argtypes = [P, P, P, P, i32, i32, i32, ctypes.c_uint64, PP, P, P, P, sz, P]
@@ -300,14 +302,16 @@ def _pyramids(pyrs, width: int, height: int, params: Params, what: str):
     return [_buf(t, pb, f"{what} pyramid") for t in pyrs]
 
 
-def features(rgb, pyramid, workspace, params: Params = None, stream=None) -> None:
-    """sff_features on a [H, W, 3] uint8 CUDA tensor (rows may be padded)."""
+def features(rgb, pyramid, workspace, params: Params = None, stream=None, tensor: bool = False) -> None:
+    """sff_features (tensor=True: sff_features_tc, same result) on a [H, W, 3]
+    uint8 CUDA tensor (rows may be padded)."""
     params = params or default_params()
-    pitch = _image(rgb, "sff_features rgb")
+    name = "sff_features_tc" if tensor else "sff_features"
+    pitch = _image(rgb, name + " rgb")
     h, w = rgb.shape[0], rgb.shape[1]
-    (pp,) = _pyramids([pyramid], w, h, params, "sff_features")
-    _check(lib().sff_features(_ptr(rgb), w, h, pitch, ctypes.byref(params), pp, _buf(workspace, 0, "workspace"),
-                              _nbytes(workspace), _stream(stream)), "sff_features")
+    (pp,) = _pyramids([pyramid], w, h, params, name)
+    _check(getattr(lib(), name)(_ptr(rgb), w, h, pitch, ctypes.byref(params), pp, _buf(workspace, 0, "workspace"),
+                                _nbytes(workspace), _stream(stream)), name)
 
 
 def match_views(pyr_ref, pyr_temporal, pyr_stereo, pyr_cross, width: int, height: int, mirror: int, seed: int,
@@ -355,7 +359,7 @@ def default_tuning() -> Tuning:
 
 
 def make_tuning(lanes: int, tile_x: int, tile_y: int, slots: int = 0, coarse=None, group_mb: int = 0,
-                pair_fields: int = 0, min_ctas: int = 0) -> Tuning:
+                pair_fields: int = 0, min_ctas: int = 0, alternate_order: int = 0) -> Tuning:
     """sff_tuning: scale 0 (lanes, slots, tile, min_ctas); coarse = [(lanes, slots, tile_x,
     tile_y[, min_ctas])] for scales 1.. (None or all-zero entries: derived from the grid
     size); group_mb: the batch's scale-0 sweep schedule (0: all quads in every launch);
@@ -363,6 +367,7 @@ def make_tuning(lanes: int, tile_x: int, tile_y: int, slots: int = 0, coarse=Non
     t = Tuning(lanes, tile_x, tile_y, slots, min_ctas)
     t.group_mb = int(group_mb)
     t.pair_fields = int(pair_fields)
+    t.alternate_order = int(alternate_order)
     for k, v in enumerate(coarse or []):
         v = tuple(v) + (0,) * (5 - len(v))
         for j in range(5):

@@ -68,13 +68,12 @@ extern "C" const char* sff_status_string(int status) {
 
 extern "C" int sff_device_status(void* stream, int32_t reset) {
     const cudaStream_t st = (cudaStream_t)stream;
-    unsigned m = 0, s = 0;
+    unsigned m = 0, s = 0, f = 0;
     if (sff::match_status_read(st, &m, reset != 0) != SFF_OK) return SFF_ERR_CUDA;
     if (sff::seeds_status_read(st, &s, reset != 0) != SFF_OK) return SFF_ERR_CUDA;
+    if (sff::features_status_read(st, &f, reset != 0) != SFF_OK) return SFF_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return SFF_ERR_CUDA;
-    if (m | s) {
-        if ((m | s) & 1u) return SFF_ERR_TIMEOUT;
-        return SFF_ERR_CAPACITY;
-    }
+    if ((m & 1u) || f) return SFF_ERR_TIMEOUT;
+    if (s) return SFF_ERR_CAPACITY;
     return SFF_OK;
 }

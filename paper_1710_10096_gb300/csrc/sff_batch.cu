@@ -29,7 +29,7 @@ extern "C" size_t sff_quad_workspace_bytes(int32_t width, int32_t height, const 
 extern "C" int sff_run_batch(const sff_quad* quads, int32_t n, const sff_params* params, const sff_tuning* tuning,
                              void* stream) {
     using namespace sff;
-    if (!quads || n < 1 || n > SFF_MAX_BATCH || check_params(params)) return SFF_ERR_ARG;
+    if (!quads || n < 1 || n > SFF_MAX_BATCH || n > kMaxQuads || check_params(params)) return SFF_ERR_ARG;
     sff_tuning t;
     if (tuning) {
         t = *tuning;

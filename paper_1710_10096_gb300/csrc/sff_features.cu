@@ -17,9 +17,12 @@
 //             rows.  The coefficients are quantised, packed and written as
 //             one 48-byte record per pixel; the norm is a dp4a of the packed
 //             bytes with themselves.
+#include <cuda_fp16.h>
+
 #include <mutex>
 
 #include "sff_internal.cuh"
+#include "sff_tc.cuh"
 
 namespace sff {
 namespace {
@@ -237,6 +240,217 @@ __global__ void __launch_bounds__(128) k_features(const __grid_constant__ ImageJ
     if (second) write_record(b_rg, b_b, qshift, feat, cs, rs, i + (size_t)n * w, norms + i + (size_t)n * w);
 }
 
+// ---------------------------------------------------------------------------
+// The same features with the transform on the tensor cores (k_features_tc).
+//
+// For one scale and channel, the 16 kept coefficients of the pixels of a row
+// segment are one matrix product D = A B^T: A is the 128 x 64 matrix of the
+// pixels' 8x8 patches (row p: P[i][j] of pixel p, k = 8 i + j), B the 16 x 64
+// matrix of the kept Walsh products (row m: walsh(ky(m), i) walsh(kx(m), j)).
+// Patch values are integers 0..255 and B entries +-1, exact in fp16; every
+// product and partial sum is an integer of magnitude <= 64 * 255 = 16320,
+// exact in the fp32 accumulator whatever the order of the sums.  One CTA of
+// 128 threads walks down a column of tiles (128 pixels of one row, the rows y,
+// y + n, y + 2n, ... of one residue class), so each step stages one new patch
+// row: the 8 patch rows of the current tile are a ring of smoothed rows in
+// shared memory (fp16 per channel).  A is stored MN-major (8 consecutive
+// pixels of one (channel, i, j) in 16 bytes), so each 16-byte chunk of A is 8
+// consecutive fp16 of one staged row starting at column 8 g + n j: aligned
+// vector copies (at n = 1 from a copy of the row shifted by one element when
+// the start is odd).  Per tile: 3 channels x 4 MMAs (M 128, N 16, K 16) into
+// tensor memory, one commit, then each thread reads its pixel's 48
+// coefficients (TMEM lane = pixel), quantises and stores the record.
+constexpr int kTcfPx = 128;                    // pixels per tile = M = threads
+constexpr int kTcfSeg = 16;                    // tiles (rows) per CTA
+constexpr int kTcfRowCols = kTcfPx + 7 * 8;    // staged columns for the widest stride (n = 8)
+constexpr int kTcfKGroup = kTcfPx * 16;        // bytes between K groups of A (2048)
+constexpr int kTcfABytes = 24 * kTcfKGroup;    // 3 channels x 8 patch rows of 8 K-columns: 48 KB
+constexpr int kTcfBBytes = 16 * 64 * 2;        // 16 coefficients x 64 patch entries, fp16: 2 KB
+constexpr int kTcfRingBytes = 2 * 3 * 8 * kTcfRowCols * 2;  // two copies x 3 channels x 8 rows, fp16
+constexpr int kTcfOffB = kTcfABytes;
+constexpr int kTcfOffRing = kTcfOffB + kTcfBBytes;
+constexpr int kTcfOffBar = kTcfOffRing + kTcfRingBytes;
+constexpr int kTcfSmemBytes = kTcfOffBar + 64 + 1024;  // + alignment slack
+constexpr int kTcfCols = 64;                           // TMEM columns (48 used)
+// instruction descriptor, kind::f16: fp32 D (bits 4-5 = 1), fp16 A and B
+// (bits 7-12 = 0), A MN-major (bit 15), B K-major, N = 16, M = 128
+constexpr uint32_t kTcfIdesc = (1u << 4) | (1u << 15) | ((16u >> 3) << 17) | ((uint32_t)(kTcfPx >> 4) << 24);
+
+__device__ unsigned int g_features_status;  // bit 0: a bounded wait of k_features_tc gave up
+
+template <int S>
+__global__ void __launch_bounds__(kTcfPx) k_features_tc(const __grid_constant__ ImageJobs J, int NS, int qshift) {
+    constexpr int n = 1 << S;
+    constexpr int kCols = kTcfPx + 7 * n;  // staged columns: x0 - 3n .. x0 + 127 + 4n
+    extern __shared__ uint8_t smem_raw[];
+    const ImageJob& job = J.im[blockIdx.z];
+    const int w = job.w, h = job.h;
+    const int tiles_x = (w + kTcfPx - 1) / kTcfPx;
+    const int rows_n = (h + n - 1) / n;  // rows per residue class (at most)
+    const int segs = (rows_n + kTcfSeg - 1) / kTcfSeg;
+    const int item = blockIdx.x;  // (segment, residue, tile column)
+    if (item >= tiles_x * n * segs) return;  // CTA-uniform, before any allocation
+    const int tx = item % tiles_x, ph = (item / tiles_x) % n, seg = item / (tiles_x * n);
+    const int x0 = tx * kTcfPx;
+    const int y_first = ph + seg * kTcfSeg * n;
+    if (y_first >= h) return;
+    uint8_t* sm = smem_raw + ((1024 - (smem_addr(smem_raw) & 1023)) & 1023);
+    uint8_t* sA = sm;
+    uint8_t* sB = sm + kTcfOffB;
+    __half* ring = reinterpret_cast<__half*>(sm + kTcfOffRing);  // [copy][c][slot][col]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + kTcfOffBar);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kTcfOffBar + 8);
+    const int t = threadIdx.x;
+    const size_t np = (size_t)w * h;
+    const int* rgp = reinterpret_cast<const int*>(job.sm) + (size_t)S * np;
+    const int* bp = reinterpret_cast<const int*>(job.sm) + (size_t)NS * np + (size_t)S * np;
+
+    if (t == 0) {
+        mbar_init(bar, 1);
+        mbar_fence_init();
+    }
+    if (t < 32) tmem_alloc(tmem_slot, kTcfCols);
+    // B: row m (kept coefficient), column k = 8 i + j, K-major core matrices
+    for (int e = t; e < 16 * 64; e += kTcfPx) {
+        const int m = e >> 6, k = e & 63, i = k >> 3, j = k & 7;
+        const int v = walsh(order_ky(m), i) * walsh(order_kx(m), j);
+        *reinterpret_cast<__half*>(sB + (k >> 3) * 256 + (m >> 3) * 128 + (m & 7) * 16 + (k & 7) * 2) =
+            __int2half_rn(v);
+    }
+    // stages image row yi into ring slot `slot` (both copies at n = 1)
+    auto stage = [&](int slot, int yi) {
+        const size_t row = (size_t)clampi(yi, 0, h - 1) * w;
+        for (int c0 = t; c0 < kCols; c0 += kTcfPx) {
+            const int x = clampi(x0 - 3 * n + c0, 0, w - 1);
+            const int rg = __ldg(rgp + row + x), b = __ldg(bp + row + x);
+            const __half v[3] = {__int2half_rn(rg & 0xffff), __int2half_rn(rg >> 16), __int2half_rn(b)};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                ring[((0 * 3 + c) * 8 + slot) * kTcfRowCols + c0] = v[c];
+                if (n == 1 && c0 > 0) ring[((1 * 3 + c) * 8 + slot) * kTcfRowCols + c0 - 1] = v[c];
+            }
+        }
+    };
+    for (int i = 0; i < 8; ++i) stage(i, y_first + n * (i - 3));
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const unsigned long long wait_ns = kDefaultWaitNs;
+    bool failed = false;
+    int failed_k = -1;  // the tile whose wait gave up (its MMAs may still run)
+    int4* feat = reinterpret_cast<int4*>(job.pyr + (size_t)S * np * kFeat);
+    int* norms = reinterpret_cast<int*>(job.pyr + (size_t)NS * np * kFeat) + (size_t)S * np;
+    const size_t cs = chunk_planes(S) ? np : 1, rs = chunk_planes(S) ? 1 : 3;
+
+    for (int k = 0; k < kTcfSeg; ++k) {
+        const int y = y_first + k * n;
+        if (y >= h) break;  // CTA-uniform
+        if (k > 0) {
+            stage((k + 7) & 7, y + 4 * n);  // the slot of the previous tile's patch row 0
+            __syncthreads();
+        }
+        // A: 384 units (channel, patch row i, pixel group g), 3 per thread;
+        // each writes the 8 chunks j of its core matrix
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+            const int unit = t + u * kTcfPx;
+            const int g = unit & 15, ci = unit >> 4, c = ci >> 3, i = ci & 7;
+            const int slot = (k + i) & 7;
+            uint8_t* dst = sA + ci * kTcfKGroup + g * 128;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int o = 8 * g + n * j;  // first staged column of the chunk
+                uint4 v;
+                if (n == 1 && (j & 1)) {
+                    const uint32_t* src =
+                        reinterpret_cast<const uint32_t*>(ring + ((1 * 3 + c) * 8 + slot) * kTcfRowCols + o - 1);
+                    v = make_uint4(src[0], src[1], src[2], src[3]);
+                } else if (n >= 8) {
+                    v = *reinterpret_cast<const uint4*>(ring + ((0 * 3 + c) * 8 + slot) * kTcfRowCols + o);
+                } else if (n >= 4) {
+                    const uint2* src = reinterpret_cast<const uint2*>(ring + ((0 * 3 + c) * 8 + slot) * kTcfRowCols + o);
+                    v = make_uint4(src[0].x, src[0].y, src[1].x, src[1].y);
+                } else {
+                    const uint32_t* src =
+                        reinterpret_cast<const uint32_t*>(ring + ((0 * 3 + c) * 8 + slot) * kTcfRowCols + o);
+                    v = make_uint4(src[0], src[1], src[2], src[3]);
+                }
+                *reinterpret_cast<uint4*>(dst + j * 16) = v;
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // A visible to the tensor core
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (t == 0 && !failed) {
+            const uint32_t a0 = smem_addr(sA), b0 = smem_addr(sB);
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    tc_mma(tmem + (uint32_t)(16 * c), smem_desc(a0 + (c * 8 + 2 * kk) * kTcfKGroup, kTcfKGroup, 128),
+                           smem_desc(b0 + 2 * kk * 256, 256, 128), kTcfIdesc, kk > 0);
+            tc_commit(bar);
+        }
+        // every thread waits for the MMAs of this tile (bounded)
+        bool ok = !failed && mbar_wait(bar, (unsigned)(k & 1), wait_ns);
+        ok = __syncthreads_and(ok);
+        if (!ok) {
+            if (t == 0) atomicOr(&g_features_status, 1u);
+            failed = true;
+            failed_k = k;
+            break;
+        }
+        tc_fence_after();
+        // epilogue: this thread's pixel = TMEM lane t
+        uint32_t r[48];
+        {
+            uint32_t q0[32];
+            tmem_ld32(tmem + ((uint32_t)(32 * (t >> 5)) << 16), q0, 0);
+            tmem_ld_wait(q0);
+#pragma unroll
+            for (int e = 0; e < 32; ++e) r[e] = q0[e];
+            uint32_t q1[32];
+            tmem_ld32(tmem + ((uint32_t)(32 * (t >> 5)) << 16), q1, 32);
+            tmem_ld_wait(q1);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) r[32 + e] = q1[e];
+        }
+        tc_fence_before();
+        const int x = x0 + t;
+        if (x < w) {
+            int words[12];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    int v[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) v[e] = ((int)__uint_as_float(r[16 * c + 4 * q + e])) >> qshift;
+                    words[4 * c + q] = pack4_sat(v[0], v[1], v[2], v[3]);
+                }
+            int nn = 0;
+#pragma unroll
+            for (int e = 0; e < 12; ++e) nn = __dp4a(words[e], words[e], nn);
+            const size_t i = (size_t)y * w + x;
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                feat[c * cs + i * rs] = make_int4(words[4 * c], words[4 * c + 1], words[4 * c + 2], words[4 * c + 3]);
+            norms[i] = nn;
+        }
+    }
+    if (failed && t == 0 && !mbar_wait(bar, (unsigned)(failed_k & 1), kDrainFactor * wait_ns)) {
+        // drain: the MMAs of the failed tile complete before the tensor
+        // memory is released; a drain that gives up is recorded (bit 1)
+        atomicOr(&g_features_status, 2u);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (t < 32) tmem_dealloc(tmem, kTcfCols);
+}
+
 }  // namespace
 
 // Scratch of one image: the smoothed scale space as two int32 planes per
@@ -245,8 +459,40 @@ size_t features_ws_bytes(int w, int h, const sff_params& p) {
     return align256((size_t)2 * p.num_scales * w * h * sizeof(int));
 }
 
-int run_features(const ImageJob* jobs, int n, const sff_params& P, cudaStream_t st) {
-    if (n < 1 || n > kMaxImages) return SFF_ERR_ARG;
+// Opts the tensor-core kernels into their dynamic shared memory, once per device.
+bool features_tc_ready() {
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done[dev]) {
+        if (cudaFuncSetAttribute(k_features_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcfSmemBytes) ||
+            cudaFuncSetAttribute(k_features_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcfSmemBytes) ||
+            cudaFuncSetAttribute(k_features_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcfSmemBytes) ||
+            cudaFuncSetAttribute(k_features_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcfSmemBytes))
+            return false;
+        done[dev] = true;
+    }
+    return true;
+}
+
+// Reads (and with reset clears) the condition bits of the feature kernels,
+// in stream order; the caller synchronises the stream.
+int features_status_read(cudaStream_t st, unsigned* out, bool reset) {
+    static const unsigned zero = 0;
+    if (cudaMemcpyFromSymbolAsync(out, g_features_status, sizeof(unsigned), 0, cudaMemcpyDeviceToHost, st) !=
+        cudaSuccess)
+        return SFF_ERR_CUDA;
+    if (reset && cudaMemcpyToSymbolAsync(g_features_status, &zero, sizeof(unsigned), 0, cudaMemcpyHostToDevice, st) !=
+                     cudaSuccess)
+        return SFF_ERR_CUDA;
+    return SFF_OK;
+}
+
+int run_features(const ImageJob* jobs, int n, const sff_params& P, cudaStream_t st, int form) {
+    if (n < 1 || n > kMaxImages || (form != kFeaturesButterfly && form != kFeaturesTensor)) return SFF_ERR_ARG;
+    if (form == kFeaturesTensor && !features_tc_ready()) return SFF_ERR_CUDA;
     static ImageJobs J;  // host staging of the kernel parameter (copied at each launch)
     static std::mutex mu;
     std::lock_guard<std::mutex> lk(mu);
@@ -260,6 +506,18 @@ int run_features(const ImageJob* jobs, int n, const sff_params& P, cudaStream_t 
     SFF_LAUNCH(k_smooth, gs, 256, 0, st, J, P.num_scales);
     for (int s = 0; s < P.num_scales; ++s) {
         const int nn = 1 << s;
+        if (form == kFeaturesTensor) {
+            // (segment, residue, tile column) items of the largest image
+            const int items = ((mw + kTcfPx - 1) / kTcfPx) * nn * (((mh + nn - 1) / nn + kTcfSeg - 1) / kTcfSeg);
+            const dim3 gt(items, 1, n);
+            switch (s) {
+                case 0: SFF_LAUNCH(k_features_tc<0>, gt, kTcfPx, kTcfSmemBytes, st, J, P.num_scales, P.quant_shift); break;
+                case 1: SFF_LAUNCH(k_features_tc<1>, gt, kTcfPx, kTcfSmemBytes, st, J, P.num_scales, P.quant_shift); break;
+                case 2: SFF_LAUNCH(k_features_tc<2>, gt, kTcfPx, kTcfSmemBytes, st, J, P.num_scales, P.quant_shift); break;
+                default: SFF_LAUNCH(k_features_tc<3>, gt, kTcfPx, kTcfSmemBytes, st, J, P.num_scales, P.quant_shift); break;
+            }
+            continue;
+        }
         // pair rows: ceil(H / 2n) pairs per residue class of rows mod n
         dim3 gf((mw + 127) / 128, ((mh + 2 * nn - 1) / (2 * nn)) * nn, n);
         SFF_LAUNCH(k_features, gf, 128, 0, st, J, s, P.num_scales, P.quant_shift);
@@ -279,4 +537,16 @@ extern "C" int sff_features(const uint8_t* rgb_dev, int32_t width, int32_t heigh
     if (workspace_bytes < features_ws_bytes(width, height, *params)) return SFF_ERR_WORKSPACE;
     ImageJob job{rgb_dev, pitch_bytes, width, height, (uint32_t*)workspace, pyramid_dev};
     return run_features(&job, 1, *params, (cudaStream_t)stream);
+}
+
+extern "C" int sff_features_tc(const uint8_t* rgb_dev, int32_t width, int32_t height, int32_t pitch_bytes,
+                            const sff_params* params, uint8_t* pyramid_dev, void* workspace,
+                            size_t workspace_bytes, void* stream) {
+    using namespace sff;
+    if (check_size(width, height) || check_params(params)) return SFF_ERR_ARG;
+    if (!rgb_dev || !pyramid_dev || !workspace || pitch_bytes < 3 * width) return SFF_ERR_ARG;
+    if (((uintptr_t)pyramid_dev & 15) || ((uintptr_t)workspace & 255)) return SFF_ERR_ARG;
+    if (workspace_bytes < features_ws_bytes(width, height, *params)) return SFF_ERR_WORKSPACE;
+    ImageJob job{rgb_dev, pitch_bytes, width, height, (uint32_t*)workspace, pyramid_dev};
+    return run_features(&job, 1, *params, (cudaStream_t)stream, kFeaturesTensor);
 }

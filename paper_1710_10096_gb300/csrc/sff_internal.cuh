@@ -173,7 +173,12 @@ struct FieldSpec {
     uint64_t seed;
     void* workspace;
 };
-constexpr int kMaxBatchFields = 64;
+// Capacity of the per-launch job tables (kernel parameters): quads per
+// shared launch, and the fields and images of that many quads.
+#ifndef SFF_TABLE_QUADS
+#define SFF_TABLE_QUADS 32
+#endif
+constexpr int kMaxBatchFields = 2 * SFF_TABLE_QUADS;
 
 // One image of a features launch: input, smoothed scale space (workspace,
 // features_ws_bytes) and pyramid.  Up to kMaxImages share a launch.
@@ -183,11 +188,14 @@ struct ImageJob {
     uint32_t* sm;
     uint8_t* pyr;
 };
-constexpr int kMaxImages = 128;
+constexpr int kMaxImages = 4 * SFF_TABLE_QUADS;
 struct ImageJobs {
     ImageJob im[kMaxImages];
 };
-int run_features(const ImageJob* jobs, int n, const sff_params& P, cudaStream_t st);
+// Forms of the feature transform: butterflies on the CUDA cores, or the
+// kept coefficients as a matrix product on the tensor cores.
+constexpr int kFeaturesButterfly = 0, kFeaturesTensor = 1;
+int run_features(const ImageJob* jobs, int n, const sff_params& P, cudaStream_t st, int form = kFeaturesButterfly);
 
 // One quad of a consistency-filter / seeds launch (up to kMaxQuads).
 struct FilterJob {
@@ -216,7 +224,7 @@ struct SeedJob {
     const int16_t* sgm;  // disparity map of the fill (nullptr: joint seeds only)
     int tau_c;           // agreement of d0 with sgm for a disparity-only seed
 };
-constexpr int kMaxQuads = 32;
+constexpr int kMaxQuads = SFF_TABLE_QUADS;
 int run_filter(const FilterJob* jobs, int n, const sff_params& P, cudaStream_t st);
 int run_seeds(const SeedJob* jobs, int n, cudaStream_t st);
 void filter_carve(void* workspace, int w, int h, int** parent, int** size, int** joinable);
@@ -242,6 +250,7 @@ void profile_mark(const char* name, cudaStream_t st, bool after, int launches = 
 // cleared in stream order.
 int match_status_read(cudaStream_t st, unsigned* out, bool reset);
 int seeds_status_read(cudaStream_t st, unsigned* out, bool reset);
+int features_status_read(cudaStream_t st, unsigned* out, bool reset);
 
 int check_size(int w, int h);
 int check_params(const sff_params* p);

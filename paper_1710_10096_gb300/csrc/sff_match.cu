@@ -41,6 +41,7 @@
 #include <mutex>
 
 #include "sff_internal.cuh"
+#include "sff_tc.cuh"
 
 namespace sff {
 namespace {
@@ -189,67 +190,6 @@ __global__ void k_gather_grid(const __grid_constant__ Fields F, int n) {
     *reinterpret_cast<uint4*>(base + off) = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-// mbarrier and bulk-copy helpers.  Addresses and sizes are multiples of 16 bytes.
-__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
-__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded waits.  A wait gives up, reporting false, once `limit_ns` of
-// global time (%globaltimer) has passed since its first poll, or after
-// kMaxPolls polls, whichever comes first.  A wait on work this CTA never
-// issued (a failed producer) thus ends after about limit_ns.  The drains --
-// waits for bulk copies and MMAs already issued, which always complete --
-// take kDrainFactor times longer before giving up.
-constexpr long long kMaxPolls = 1ll << 30;
-constexpr unsigned long long kDefaultWaitNs = 1000000000ull;  // 1 s
-constexpr unsigned long long kDrainFactor = 10;
-
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned long long limit_ns) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    for (long long k = 0; k < kMaxPolls; ++k) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > limit_ns) return false;
-    }
-    return false;
-}
-
 __device__ unsigned int g_wait_timeouts;  // bounded waits that gave up (read by sff_device_timeouts)
 __device__ unsigned int g_drain_timeouts;  // drains that gave up (work in flight not seen to finish)
 // Conditions raised since the last reset (read by sff_device_status):
@@ -265,66 +205,6 @@ __device__ unsigned long long g_wait_limit_ns = 0;
 __device__ __forceinline__ void note_timeout() {
     atomicAdd(&g_wait_timeouts, 1u);
     atomicOr(&g_match_status, kStatusTimeout);
-}
-
-// tcgen05 helpers (tensor memory, MMA, commit, loads).
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)),
-                 "r"(ncols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-
-// shared-memory matrix descriptor: start, leading (K-direction) and stride
-// (row-group) byte offsets, descriptor version 1, no swizzle
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
-           (1ull << 46);
-}
-
-__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-__device__ __forceinline__ void tc_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
-                 : "memory");
-}
-
-// 32 lanes x 32 consecutive columns: thread t gets lane (base + t).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32], int o) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
-        "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr + (uint32_t)o));
-}
-
-// Waits for the warp's tensor-memory loads; the registers are operands so
-// that no use of them moves above the wait.
-__device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[32]) {
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
-                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
-                   "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
-                   "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
-                   "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
-                 :
-                 : "memory");
 }
 
 // Reduces a buffer of `cnt` (<= kTcCap) candidates of one (lane group,
@@ -965,13 +845,22 @@ struct IterStep {
     int pair;  // 0: blockIdx.z picks field f0 + z; 1: fields f0 + 2z and f0 + 2z + 1 (one quad's
                // forward and inverse) alternate along blockIdx.x, so their CTAs of one tile
                // position run side by side
+    int rev;   // the block indices taken in reverse: CTAs are issued in increasing linear
+               // index, so a launch with rev = 1 visits the tiles last-to-first and first reads
+               // what the previous launch read last (still in L2)
 };
 
-// Field and tile column of this CTA.
-__device__ __forceinline__ int iter_field(const IterStep& H) {
-    return H.f0 + (H.pair ? 2 * (int)blockIdx.z + (int)(blockIdx.x & 1) : (int)blockIdx.z);
+// Block indices of this CTA in visiting order.
+__device__ __forceinline__ int3 iter_block(const IterStep& H) {
+    if (!H.rev) return make_int3((int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z);
+    return make_int3((int)(gridDim.x - 1 - blockIdx.x), (int)(gridDim.y - 1 - blockIdx.y),
+                     (int)(gridDim.z - 1 - blockIdx.z));
 }
-__device__ __forceinline__ int iter_tile_x(const IterStep& H) { return H.pair ? (int)(blockIdx.x >> 1) : (int)blockIdx.x; }
+// Field and tile column of this CTA.
+__device__ __forceinline__ int iter_field(const IterStep& H, int3 b) {
+    return H.f0 + (H.pair ? 2 * b.z + (b.x & 1) : b.z);
+}
+__device__ __forceinline__ int iter_tile_x(const IterStep& H, int3 b) { return H.pair ? (b.x >> 1) : b.x; }
 
 // MB > 0: compiled for at least MB resident CTAs per SM (a register budget
 // of 64K / (MB x threads)), so that a launch of few CTAs per SM fits one wave.
@@ -982,12 +871,13 @@ __global__ void __launch_bounds__(iter_threads<L, TX, TY>(), MB) k_iteration(con
     constexpr int kGroups = iter_threads<L, TX, TY>() / L;
     __shared__ uint2 s_vec[kRegX * kRegY];
     __shared__ int s_cost[kRegX * kRegY];
-    const Field& A = F.f[iter_field(H)];
+    const int3 blk = iter_block(H);
+    const Field& A = F.f[iter_field(H, blk)];
     const Views& V = A.V;
     const int q = threadIdx.x & (L - 1);
     const unsigned gmask = group_mask<L>();
     const int grp = threadIdx.x / L;
-    const int tx0 = iter_tile_x(H) * TX, ty0 = blockIdx.y * TY;
+    const int tx0 = iter_tile_x(H, blk) * TX, ty0 = blk.y * TY;
     const int gw = A.gw, gh = A.gh;
     if (tx0 >= gw || ty0 >= gh) return;  // tile beyond this field's grid (whole CTA)
     const int rx0 = tx0 - (H.dx > 0 ? 1 : 0), ry0 = ty0 - (H.dy > 0 ? 1 : 0);  // region origin
@@ -1177,13 +1067,14 @@ __global__ void __launch_bounds__(lat_threads<L * C, TX, TY>()) k_iteration_lat(
     constexpr int kHalfRow = (kRegX + 1) / 2, kTileHalfRow = TX / 2;
     __shared__ uint2 s_vec[kRegX * kRegY];
     __shared__ int s_cost[kRegX * kRegY];
-    const Field& A = F.f[iter_field(H)];
+    const int3 blk = iter_block(H);
+    const Field& A = F.f[iter_field(H, blk)];
     const Views& V = A.V;
     const int g = threadIdx.x & (G - 1);
     const int q = g & (L - 1), slot = g / L;
     const unsigned gmask = group_mask<G>();
     const int grp = threadIdx.x / G;  // this group's cell in each phase
-    const int tx0 = iter_tile_x(H) * TX, ty0 = blockIdx.y * TY;
+    const int tx0 = iter_tile_x(H, blk) * TX, ty0 = blk.y * TY;
     const int gw = A.gw, gh = A.gh;
     if (tx0 >= gw || ty0 >= gh) return;  // tile beyond this field's grid (whole CTA)
     const int rx0 = tx0 - (H.dx > 0 ? 1 : 0), ry0 = ty0 - (H.dy > 0 ? 1 : 0);
@@ -1723,7 +1614,9 @@ const IterVariant* find_variant(int lanes, int slots, int tx, int ty, int ctas) 
 // either all zero (chosen from the grid size) or an existing variant.
 bool tuning_valid(const sff_tuning& t) {
     if (!find_variant(t.lanes_per_pixel, t.slots, t.tile_x, t.tile_y, t.min_ctas)) return false;
-    if (t.group_mb < 0 || t.group_mb > (1 << 20) || (t.pair_fields != 0 && t.pair_fields != 1)) return false;
+    if (t.group_mb < 0 || t.group_mb > (1 << 20) || (t.pair_fields != 0 && t.pair_fields != 1) ||
+        t.alternate_order < 0 || t.alternate_order > 15)
+        return false;
     for (int k = 0; k < SFF_MAX_SCALES - 1; ++k) {
         const int32_t* c = t.coarse[k];
         if ((c[0] | c[1] | c[2] | c[3] | c[4]) != 0 && !find_variant(c[0], c[1], c[2], c[3], c[4])) return false;
@@ -1947,7 +1840,8 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
                     F.f[k].field_out = Bf[in ^ 1][k];
                     F.f[k].cost_out = Bc[in ^ 1][k];
                 }
-                IterStep H{n, s, kDirs[it % 4][0], kDirs[it % 4][1], it, it == I - 1, f0, pair ? 1 : 0};
+                IterStep H{n,      s,  kDirs[it % 4][0], kDirs[it % 4][1], it, it == I - 1, f0, pair ? 1 : 0,
+                           ((T.alternate_order >> s) & 1) ? (it & 1) : 0};
                 sv->k<<<gi, sv->threads, 0, st>>>(F, H);
             }
             if (I > 0 && ::sff::profiling()) ::sff::profile_mark(kIterNames[s], st, true, I);

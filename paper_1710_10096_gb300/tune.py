@@ -1,10 +1,13 @@
 """Autotuner of the propagation work distribution.
 
 Every variant of the iteration kernel (lanes per pixel, candidate slots,
-tile; VARIANT_SPACE) is run at all scales of the caller's pyramids, and the
-launches of each scale are timed as one span of CUDA events inside a CUDA
-graph (sff_profile_enable), so that each scale gets its own fastest variant.
-All variants give bit-identical results (tested), so the choice only affects
+tile, resident CTAs; VARIANT_SPACE) is run at all scales of the caller's
+pyramids, and the launches of each scale are timed as one span of CUDA events
+inside a CUDA graph (sff_profile_enable), so that each scale gets its own
+fastest variant.  Then the schedules are tried on those variants: a quad's two
+fields alternating tile by tile (pair_fields), and, per scale, every other
+launch visiting its tiles last-to-first (a bit of alternate_order).  All
+settings give bit-identical results (tested), so the choice only affects
 speed.  Results are cached per image-size bucket.
 """
 from __future__ import annotations
@@ -23,15 +26,17 @@ def size_bucket(width: int, height: int) -> str:
     return f"{(width + 63) // 64 * 64}x{(height + 31) // 32 * 32}"
 
 
-def _tuning_of(per_scale) -> Tuning:
-    l, c, tx, ty, mb = per_scale[0]
-    return make_tuning(l, tx, ty, c, per_scale[1:], min_ctas=mb)
+def _tuning_of(entry) -> Tuning:
+    """Tuning of a cache entry: {"variants": [4 x (lanes, slots, tile_x, tile_y, min_ctas)],
+    "pair": 0 | 1, "alt": bits}."""
+    vs = entry["variants"]
+    l, c, tx, ty, mb = vs[0]
+    return make_tuning(l, tx, ty, c, vs[1:], 0, entry["pair"], mb, entry["alt"])
 
 
-def scale_times(pyramids, width: int, height: int, variant, params=None, reps: int = 3, stream=None) -> dict:
-    """{scale: us per launch} of the iteration kernel with `variant`
-    (lanes, slots, tile_x, tile_y, min_ctas) at every scale, timed as one span
-    of events per scale in a CUDA graph of `reps` matching runs."""
+def scale_times(pyramids, width: int, height: int, tuning: Tuning, params=None, reps: int = 3, stream=None) -> dict:
+    """{scale: us per launch} of the iteration kernel with `tuning`, timed as
+    one span of events per scale in a CUDA graph of `reps` matching runs."""
     import torch
     params = params or default_params()
     dev = pyramids[0].device
@@ -39,17 +44,15 @@ def scale_times(pyramids, width: int, height: int, variant, params=None, reps: i
     out = [torch.empty((height, width, 4), dtype=torch.int16, device=dev) for _ in range(2)]
     cst = [torch.empty((height, width), dtype=torch.int32, device=dev) for _ in range(2)]
     s = stream or torch.cuda.Stream(device=dev)
-    l, c, tx, ty, mb = variant
-    t = make_tuning(l, tx, ty, c, [variant] * (params.num_scales - 1), min_ctas=mb)
     with torch.cuda.stream(s):
-        match_quad_tuned(*pyramids, width, height, 1, t, out[0], cst[0], out[1], cst[1], ws, params, s)
+        match_quad_tuned(*pyramids, width, height, 1, tuning, out[0], cst[0], out[1], cst[1], ws, params, s)
         s.synchronize()
         profile_enable(True)
         try:
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=s):
                 for _ in range(reps):
-                    match_quad_tuned(*pyramids, width, height, 1, t, out[0], cst[0], out[1], cst[1], ws, params,
+                    match_quad_tuned(*pyramids, width, height, 1, tuning, out[0], cst[0], out[1], cst[1], ws, params,
                                      torch.cuda.current_stream(dev))
             g.replay()
             s.synchronize()
@@ -66,7 +69,8 @@ def scale_times(pyramids, width: int, height: int, variant, params=None, reps: i
 
 def autotune(pyramids, width: int, height: int, params=None, reps: int = 3, space=None, stream=None,
              verbose: bool = False) -> Tuning:
-    """Fastest variant per scale for W x H, measured on the given L0/R0/L1/R1 pyramids."""
+    """Fastest variant per scale, then the fastest schedules on them, for
+    W x H, measured on the given L0/R0/L1/R1 pyramids."""
     params = params or default_params()
     key = (size_bucket(width, height), tuple(params.as_dict().values()))
     if key in _CACHE:
@@ -75,43 +79,105 @@ def autotune(pyramids, width: int, height: int, params=None, reps: int = 3, spac
     best = [None] * 4
     best_us = [float("inf")] * 4
     for v in (space or VARIANT_SPACE):
-        times = scale_times(pyramids, width, height, tuple(v), params, reps, stream)
+        v = tuple(v)
+        t = make_tuning(v[0], v[2], v[3], v[1], [v] * (S - 1), min_ctas=v[4])
+        times = scale_times(pyramids, width, height, t, params, reps, stream)
         for s, us in times.items():
             if us < best_us[s]:
-                best[s], best_us[s] = tuple(v), us
+                best[s], best_us[s] = v, us
         if verbose:
-            print(f"variant {tuple(v)}: " + " ".join(f"s{s} {us:.2f} us" for s, us in sorted(times.items())))
+            print(f"variant {v}: " + " ".join(f"s{s} {us:.2f} us" for s, us in sorted(times.items())))
     d = default_tuning().scale_variants()
-    per_scale = [best[s] if s < S and best[s] is not None else (d[s] if s == 0 else (0,) * 5) for s in range(4)]
-    _CACHE[key] = per_scale
-    return _tuning_of(per_scale)
+    variants = [best[s] if s < S and best[s] is not None else (d[s] if s == 0 else (0,) * 5) for s in range(4)]
+    # schedules on the chosen variants
+    full = (1 << S) - 1
+    sched = {}
+    for pair in (0, 1):
+        for alt in (0, full):
+            t = _tuning_of({"variants": variants, "pair": pair, "alt": alt})
+            sched[(pair, alt)] = scale_times(pyramids, width, height, t, params, reps, stream)
+            if verbose:
+                print(f"pair {pair} alt {alt}: " +
+                      " ".join(f"s{s} {us:.2f} us" for s, us in sorted(sched[(pair, alt)].items())))
+
+    def total(pair):
+        return sum(min(sched[(pair, 0)][s], sched[(pair, full)][s]) for s in range(S))
+
+    pair = min((0, 1), key=total)
+    alt = sum(1 << s for s in range(S) if sched[(pair, full)][s] < sched[(pair, 0)][s])
+    entry = {"variants": variants, "pair": pair, "alt": alt}
+    _CACHE[key] = entry
+    return _tuning_of(entry)
+
+
+def autotune_batch(batch, seeds, space=None, reps: int = 3, verbose: bool = False) -> Tuning:
+    """Fastest scale-0 variant and schedules (pair_fields, alternate_order of
+    scale 0) for the quads of `batch` (a BatchMatcher, its images loaded),
+    timed on CUDA-graph replays of the whole batch; the coarse scales take the
+    variants derived from the batch's grid sizes.  Leaves the batch with the
+    chosen tuning."""
+    import statistics
+
+    import torch
+    cands = space or [v for v in VARIANT_SPACE if v[0] == 1 and v[1] == 0]
+    dev = batch.device
+    s = torch.cuda.Stream(device=dev)
+    best, best_ms = None, float("inf")
+    for v in cands:
+        for pair in (0, 1):
+            for alt in (0, 1):
+                batch.tuning = make_tuning(v[0], v[2], v[3], v[1], None, 0, pair, v[4], alt)
+                g = batch.capture(seeds)
+                with torch.cuda.stream(s):
+                    g.replay()
+                    s.synchronize()
+                    ts = []
+                    for _ in range(reps):
+                        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        a.record(s)
+                        g.replay()
+                        b.record(s)
+                        b.synchronize()
+                        ts.append(a.elapsed_time(b))
+                del g
+                ms = statistics.median(ts)
+                if verbose:
+                    print(f"batch {tuple(v)} pair {pair} alt {alt}: {ms:.3f} ms")
+                if ms < best_ms:
+                    best, best_ms = batch.tuning, ms
+    batch.tuning = best
+    return best
 
 
 def save_cache(path: str) -> None:
     with open(path, "w") as f:
-        json.dump({f"{k[0]}|{','.join(map(str, k[1]))}": [list(v) for v in vs] for k, vs in _CACHE.items()}, f,
-                  indent=1)
+        json.dump({f"{k[0]}|{','.join(map(str, k[1]))}": {"variants": [list(v) for v in e["variants"]],
+                                                          "pair": e["pair"], "alt": e["alt"]}
+                   for k, e in _CACHE.items()}, f, indent=1)
 
 
 def load_cache(path: str) -> int:
     """Adds the tunings of a file written by save_cache; entries that this
-    build does not support (another build's variant space) are skipped.
-    Returns the number of entries taken."""
+    build does not support (another build's variant space or format) are
+    skipped.  Returns the number of entries taken."""
     if not os.path.exists(path):
         return 0
     with open(path) as f:
         entries = json.load(f)
     taken = 0
     space = set(VARIANT_SPACE)
-    for k, vs in entries.items():
+    for k, e in entries.items():
         b, p = k.split("|")
-        if not (isinstance(vs, list) and len(vs) == 4 and all(isinstance(v, list) and len(v) == 5 for v in vs)):
+        if not (isinstance(e, dict) and isinstance(e.get("variants"), list) and len(e["variants"]) == 4 and
+                all(isinstance(v, list) and len(v) == 5 for v in e["variants"]) and e.get("pair") in (0, 1) and
+                isinstance(e.get("alt"), int) and 0 <= e["alt"] <= 15):
             continue
-        vs = [tuple(v) for v in vs]
-        if tuple(vs[0]) in space and all(v in space or v == (0,) * 5 for v in vs[1:]):
-            _CACHE[(b, tuple(int(x) for x in p.split(",")))] = vs
+        vs = [tuple(v) for v in e["variants"]]
+        if vs[0] in space and all(v in space or v == (0,) * 5 for v in vs[1:]):
+            _CACHE[(b, tuple(int(x) for x in p.split(",")))] = {"variants": vs, "pair": e["pair"], "alt": e["alt"]}
             taken += 1
     return taken
 
 
-__all__ = ["autotune", "scale_times", "size_bucket", "save_cache", "load_cache", "default_tuning"]
+__all__ = ["autotune", "autotune_batch", "scale_times", "size_bucket", "save_cache", "load_cache",
+           "default_tuning"]

@@ -56,6 +56,26 @@ def test_features_bit_exact(env, size, qshift):
     assert np.array_equal(gnorm, norm)
 
 
+@pytest.mark.parametrize("size", [(8, 8), (37, 23), (130, 70), (256, 80), (300, 9), (1242, 375)])
+@pytest.mark.parametrize("qshift", [4, 0])
+def test_features_tensor_core_bit_exact(env, size, qshift):
+    # the transform as a tensor-core matrix product (sff_features_tc): every
+    # record and norm equals the oracle's (and so the butterfly form's)
+    torch, sff, orc = env
+    w, h = size
+    img = scenegen.random_images(w, h, seed=w * 1000 + h + 7, n=1)[0]
+    p = sff.default_params(quant_shift=qshift)
+    pyr = torch.empty(sff.pyramid_bytes(w, h, p), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(sff.workspace_bytes(w, h, p), dtype=torch.uint8, device="cuda")
+    sff.device_status(reset=True)
+    sff.features(torch.as_tensor(img).cuda(), pyr, ws, p, tensor=True)
+    assert sff.device_status(reset=True) == sff.OK
+    gfeat, gnorm = (a.cpu().numpy() for a in sff.split_pyramid(pyr, w, h, p))
+    feat, norm = orc.features(img, _oparams(orc, p))
+    assert np.array_equal(gfeat, feat)
+    assert np.array_equal(gnorm, norm)
+
+
 def _match_both(env, imgs, p, seed):
     torch, sff, orc = env
     h, w, _ = imgs[0].shape
@@ -316,8 +336,11 @@ def test_every_tuning_gives_identical_fields(env):
     # variant of both forms at all four scales
     space = [sff.make_tuning(*cand) for cand in sff.TUNING_SPACE]
     space += [sff.make_tuning(v[0], v[2], v[3], v[1], [v] * 3, min_ctas=v[4]) for v in sff.VARIANT_SPACE]
-    # the schedules: the two fields of the quad alternating tile by tile
-    space += [sff.make_tuning(1, 32, 16, 0, None, 0, 1), sff.make_tuning(1, 8, 8, 4, [(1, 4, 8, 8)] * 3, 0, 1)]
+    # the schedules: the two fields of the quad alternating tile by tile, and
+    # every other launch visiting its tiles last-to-first
+    space += [sff.make_tuning(1, 32, 16, 0, None, 0, 1), sff.make_tuning(1, 8, 8, 4, [(1, 4, 8, 8)] * 3, 0, 1),
+              sff.make_tuning(1, 32, 8, 0, None, 0, 0, 0, 1), sff.make_tuning(1, 32, 8, 0, None, 0, 1, 0, 15),
+              sff.make_tuning(2, 16, 8, 1, [(1, 4, 16, 8)] * 3, 0, 1, 0, 10)]
     for t in space:
         cand = t.scale_variants()
         out = [torch.empty((h, w, 4), dtype=torch.int16, device="cuda") for _ in range(2)]
@@ -375,17 +398,17 @@ def test_batch_of_uneven_quads_equals_each_alone(env):
     # sweep schedules of scale 0: all quads in every launch, every quad alone
     # (a budget below any quad), about two quads per group, and each with the
     # two fields of a quad alternating tile by tile
-    for group_mb, pair in ((0, 0), (1, 0), (4, 0), (0, 1), (4, 1)):
-        bm.tuning = sff.make_tuning(1, 32, 16, 0, None, group_mb, pair)
+    for group_mb, pair, alt in ((0, 0, 0), (1, 0, 0), (4, 0, 0), (0, 1, 0), (4, 1, 0), (0, 0, 1), (4, 1, 1)):
+        bm.tuning = sff.make_tuning(1, 32, 16, 0, None, group_mb, pair, 0, alt)
         bm.run([ms for _, ms in quads])
         torch.cuda.synchronize()
         for (q, ms), b, ref in zip(quads, bm.quads, refs):
-            assert np.array_equal(b.fwd.cpu().numpy(), ref["fwd"]), (group_mb, pair)
-            assert np.array_equal(b.inv.cpu().numpy(), ref["inv"]), (group_mb, pair)
-            assert np.array_equal(b.fwd_cost.cpu().numpy(), ref["fwd_cost"]), (group_mb, pair)
-            assert np.array_equal(b.keep.cpu().numpy(), ref["keep"]), (group_mb, pair)
-            assert np.array_equal(b.cerr.cpu().numpy(), ref["cerr"]), (group_mb, pair)
-            assert b.seeds_numpy().tobytes() == ref["seeds"].tobytes(), (group_mb, pair)
+            assert np.array_equal(b.fwd.cpu().numpy(), ref["fwd"]), (group_mb, pair, alt)
+            assert np.array_equal(b.inv.cpu().numpy(), ref["inv"]), (group_mb, pair, alt)
+            assert np.array_equal(b.fwd_cost.cpu().numpy(), ref["fwd_cost"]), (group_mb, pair, alt)
+            assert np.array_equal(b.keep.cpu().numpy(), ref["keep"]), (group_mb, pair, alt)
+            assert np.array_equal(b.cerr.cpu().numpy(), ref["cerr"]), (group_mb, pair, alt)
+            assert b.seeds_numpy().tobytes() == ref["seeds"].tobytes(), (group_mb, pair, alt)
 
 
 def test_mixed_32_quad_batch_equals_oracle(env):

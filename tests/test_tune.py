@@ -26,22 +26,28 @@ def test_cache_round_trip_skips_unsupported_entries(tmp_path):
     try:
         tune._CACHE.clear()
         params = tuple(sff.default_params().as_dict().values())
-        good = [sff.VARIANT_SPACE[1], (1, 0, 32, 16, 4), (0, 0, 0, 0, 0), (1, 4, 16, 8, 0)]
+        good = {"variants": [sff.VARIANT_SPACE[1], (1, 0, 32, 16, 4), (0, 0, 0, 0, 0), (1, 4, 16, 8, 0)],
+                "pair": 1, "alt": 5}
         tune._CACHE[("1280x384", params)] = good
         path = tmp_path / "tuning.json"
         tune.save_cache(str(path))
         data = json.loads(path.read_text())
         pk = ",".join(map(str, params))
-        data["640x192|" + pk] = [[3, 0, 32, 8, 0]] * 4  # not a supported variant
-        data["512x160|" + pk] = [[4, 4, 16, 8, 0]] * 4  # a region that does not fit 1024 threads
+        ok = data["1280x384|" + pk]
+        data["640x192|" + pk] = dict(ok, variants=[[3, 0, 32, 8, 0]] * 4)  # not a supported variant
+        data["512x160|" + pk] = dict(ok, variants=[[4, 4, 16, 8, 0]] * 4)  # region beyond 1024 threads
+        data["448x160|" + pk] = dict(ok, pair=2)  # not a schedule
+        data["384x160|" + pk] = dict(ok, alt=16)  # not a scale bit mask
         data["256x96|" + pk] = [1, 0, 32, 8]  # an old (one variant) format
-        data["128x64|" + pk] = [[1, 0, 32, 8]] * 4  # an old (four-field variant) format
+        data["128x64|" + pk] = [[1, 0, 32, 8, 0]] * 4  # an old (list of variants) format
         path.write_text(json.dumps(data))
         tune._CACHE.clear()
         assert tune.load_cache(str(path)) == 1
-        assert tune._CACHE == {("1280x384", params): [tuple(v) for v in good]}
-        t = tune._tuning_of(tune._CACHE[("1280x384", params)])
-        assert t.scale_variants() == [tuple(v) for v in good]
+        e = tune._CACHE[("1280x384", params)]
+        assert e == {"variants": [tuple(v) for v in good["variants"]], "pair": 1, "alt": 5}
+        t = tune._tuning_of(e)
+        assert t.scale_variants() == [tuple(v) for v in good["variants"]]
+        assert (t.pair_fields, t.alternate_order) == (1, 5)
         assert tune.load_cache(str(tmp_path / "missing.json")) == 0
     finally:
         tune._CACHE.clear()
@@ -63,3 +69,6 @@ def test_variant_space_matches_the_library():
         with pytest.raises(sff.SffError):
             sff.make_tuning(1, 32, 16, 0, [bad])
     assert len(sff.VARIANT_SPACE) == 42
+    for bad_sched in [dict(group_mb=-1), dict(pair_fields=2), dict(alternate_order=16), dict(alternate_order=-1)]:
+        with pytest.raises(sff.SffError):
+            sff.make_tuning(1, 32, 16, 0, None, **bad_sched)
