@@ -606,6 +606,7 @@ def bench_fill(sff, torch, dev, m, q, params, steps, warmup, cpu: bool):
     sff.interpolate(gseeds, gcount, cap, w, h, ip, field, iws)
     torch.cuda.synchronize()
     out["quality"]["field_with_fill"] = field_quality(field.cpu().numpy(), q)
+    out["quality"]["field_with_fill"]["interp_status"] = sff.interp_status(iws, w, h, cap)
     if cpu:
         import oracle
         oracle.build()
@@ -676,7 +677,7 @@ def bench_method(sff, torch, dev, m, q, params, steps, warmup):
     return {"what": "matching stage || SGM map, then seeds with the disparity fill and the dense interpolation, "
                     "one CUDA graph with two streams, ms per quad, L2 flushed before each",
             "ms": t_ms, "px_per_s": w * h / (t_ms / 1e3), "seeds": n, "disparity_only_seeds": int((kinds == 1).sum()),
-            "quality": field_quality(field.cpu().numpy(), q)}
+            "quality": field_quality(field.cpu().numpy(), q), "interp_status": sff.interp_status(iws, w, h, cap)}
 
 
 def bench_sift(sff, torch, dev, m, q, params, steps, warmup):

@@ -118,6 +118,12 @@ typedef struct sff_tuning {
     int32_t alternate_order; /* bit s set (s = 0..3): at scale s every other iteration launch
                               * visits its tiles last-to-first, so that it starts on what the
                               * previous launch read last (still in L2); 0..15 */
+    int32_t features_form;   /* transform of the whole-stage calls (sff_run_batch): 0 = butterflies
+                              * on the CUDA cores (sff_features), 1 = tensor cores (sff_features_tc);
+                              * identical features */
+    int32_t pdl;             /* 1 = the iteration launches use programmatic dependent launch: each
+                              * is scheduled while the previous one's last CTAs run and waits in
+                              * the kernel for its completion (same results) */
 } sff_tuning;
 
 /* One seed of Sec. 3.2: pixel (x, y) of L0, its vector and its scores. 20 bytes.
@@ -453,10 +459,10 @@ size_t sff_interp_workspace_bytes(int32_t width, int32_t height, int32_t capacit
  * during the call.  The seeds must lie in the image with at most one seed per
  * 3x3 block anchored at (0, 0), as sff_emit_seeds writes them.
  * Errors found on the GPU (a second seed in one block, a seed outside the
- * image, more than 6 * max(k_geo, k_motion) + 256 neighbour candidates of
- * one seed, which needs a very uneven seed density) set bits of a status
- * word in the workspace (read it with sff_interp_status) and the field is
- * all zeros. */
+ * image, or more than 6 * max(k_geo, k_motion) + 224 neighbour candidates of
+ * one seed tied at the k-th distances, which the candidate buffer's
+ * compaction cannot reduce) set bits of a status word in the workspace (read
+ * it with sff_interp_status) and the field is all zeros. */
 int sff_interpolate(const sff_seed* seeds_dev, const int32_t* count_dev, int32_t capacity, int32_t width,
                     int32_t height, const sff_interp_params* params, float* field_dev, void* workspace,
                     size_t workspace_bytes, void* stream);

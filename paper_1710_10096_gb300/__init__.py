@@ -60,7 +60,8 @@ class Tuning(ctypes.Structure):
     """sff_tuning of include/sff.h: work distribution, never changes results."""
     _fields_ = [("lanes_per_pixel", ctypes.c_int32), ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32),
                 ("slots", ctypes.c_int32), ("min_ctas", ctypes.c_int32), ("coarse", (ctypes.c_int32 * 5) * 3),
-                ("group_mb", ctypes.c_int32), ("pair_fields", ctypes.c_int32), ("alternate_order", ctypes.c_int32)]
+                ("group_mb", ctypes.c_int32), ("pair_fields", ctypes.c_int32), ("alternate_order", ctypes.c_int32),
+                ("features_form", ctypes.c_int32), ("pdl", ctypes.c_int32)]
 
     def as_tuple(self):
         """(lanes, tile_x, tile_y) of scale 0 (the throughput-form space)."""
@@ -359,7 +360,8 @@ def default_tuning() -> Tuning:
 
 
 def make_tuning(lanes: int, tile_x: int, tile_y: int, slots: int = 0, coarse=None, group_mb: int = 0,
-                pair_fields: int = 0, min_ctas: int = 0, alternate_order: int = 0) -> Tuning:
+                pair_fields: int = 0, min_ctas: int = 0, alternate_order: int = 0, features_form: int = 0,
+                pdl: int = 0) -> Tuning:
     """sff_tuning: scale 0 (lanes, slots, tile, min_ctas); coarse = [(lanes, slots, tile_x,
     tile_y[, min_ctas])] for scales 1.. (None or all-zero entries: derived from the grid
     size); group_mb: the batch's scale-0 sweep schedule (0: all quads in every launch);
@@ -368,6 +370,8 @@ def make_tuning(lanes: int, tile_x: int, tile_y: int, slots: int = 0, coarse=Non
     t.group_mb = int(group_mb)
     t.pair_fields = int(pair_fields)
     t.alternate_order = int(alternate_order)
+    t.features_form = int(features_form)
+    t.pdl = int(pdl)
     for k, v in enumerate(coarse or []):
         v = tuple(v) + (0,) * (5 - len(v))
         for j in range(5):

@@ -317,21 +317,42 @@ __global__ void __launch_bounds__(kTcfPx) k_features_tc(const __grid_constant__ 
         *reinterpret_cast<__half*>(sB + (k >> 3) * 256 + (m >> 3) * 128 + (m & 7) * 16 + (k & 7) * 2) =
             __int2half_rn(v);
     }
-    // stages image row yi into ring slot `slot` (both copies at n = 1)
-    auto stage = [&](int slot, int yi) {
+    // A staged row: columns c0 = t, t + 128 of image row yi (x clamped).  The
+    // loads of the next tile's new row are issued one tile ahead into
+    // registers (rg, b pairs) and written into the ring when that tile starts.
+    constexpr int kPre = (kCols + kTcfPx - 1) / kTcfPx;
+    auto load_row = [&](int yi, int2 (&pre)[kPre]) {
         const size_t row = (size_t)clampi(yi, 0, h - 1) * w;
-        for (int c0 = t; c0 < kCols; c0 += kTcfPx) {
-            const int x = clampi(x0 - 3 * n + c0, 0, w - 1);
-            const int rg = __ldg(rgp + row + x), b = __ldg(bp + row + x);
-            const __half v[3] = {__int2half_rn(rg & 0xffff), __int2half_rn(rg >> 16), __int2half_rn(b)};
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                ring[((0 * 3 + c) * 8 + slot) * kTcfRowCols + c0] = v[c];
-                if (n == 1 && c0 > 0) ring[((1 * 3 + c) * 8 + slot) * kTcfRowCols + c0 - 1] = v[c];
+        for (int e = 0; e < kPre; ++e) {
+            const int c0 = t + e * kTcfPx;
+            if (c0 < kCols) {
+                const int x = clampi(x0 - 3 * n + c0, 0, w - 1);
+                pre[e] = make_int2(__ldg(rgp + row + x), __ldg(bp + row + x));
             }
         }
     };
-    for (int i = 0; i < 8; ++i) stage(i, y_first + n * (i - 3));
+    auto put_row = [&](int slot, const int2 (&pre)[kPre]) {
+#pragma unroll
+        for (int e = 0; e < kPre; ++e) {
+            const int c0 = t + e * kTcfPx;
+            if (c0 < kCols) {
+                const __half v[3] = {__int2half_rn(pre[e].x & 0xffff), __int2half_rn(pre[e].x >> 16),
+                                     __int2half_rn(pre[e].y)};
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    ring[((0 * 3 + c) * 8 + slot) * kTcfRowCols + c0] = v[c];
+                    if (n == 1 && c0 > 0) ring[((1 * 3 + c) * 8 + slot) * kTcfRowCols + c0 - 1] = v[c];
+                }
+            }
+        }
+    };
+    int2 pre[kPre];
+    for (int i = 0; i < 8; ++i) {
+        load_row(y_first + n * (i - 3), pre);
+        put_row(i, pre);
+    }
+    load_row(y_first + n + 4 * n, pre);  // the new row of tile 1
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -347,37 +368,34 @@ __global__ void __launch_bounds__(kTcfPx) k_features_tc(const __grid_constant__ 
         const int y = y_first + k * n;
         if (y >= h) break;  // CTA-uniform
         if (k > 0) {
-            stage((k + 7) & 7, y + 4 * n);  // the slot of the previous tile's patch row 0
+            put_row((k + 7) & 7, pre);  // the slot of the previous tile's patch row 0
             __syncthreads();
+            if (k + 1 < kTcfSeg) load_row(y + n + 4 * n, pre);  // next tile's new row, in flight meanwhile
         }
-        // A: 384 units (channel, patch row i, pixel group g), 3 per thread;
-        // each writes the 8 chunks j of its core matrix
-#pragma unroll
-        for (int u = 0; u < 3; ++u) {
-            const int unit = t + u * kTcfPx;
-            const int g = unit & 15, ci = unit >> 4, c = ci >> 3, i = ci & 7;
+        // A: 3072 chunks of 16 bytes, chunk e = (K group ci, pixel group g,
+        // row j) with j fastest, so a warp writes 512 contiguous bytes; each
+        // is 8 consecutive staged fp16 of row (channel, patch row i) from
+        // column 8 g + n j
+#pragma unroll 4
+        for (int r = 0; r < 24; ++r) {
+            const int e = t + r * kTcfPx;
+            const int j = e & 7, g = (e >> 3) & 15, ci = e >> 7, c = ci >> 3, i = ci & 7;
             const int slot = (k + i) & 7;
-            uint8_t* dst = sA + ci * kTcfKGroup + g * 128;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int o = 8 * g + n * j;  // first staged column of the chunk
-                uint4 v;
-                if (n == 1 && (j & 1)) {
-                    const uint32_t* src =
-                        reinterpret_cast<const uint32_t*>(ring + ((1 * 3 + c) * 8 + slot) * kTcfRowCols + o - 1);
-                    v = make_uint4(src[0], src[1], src[2], src[3]);
-                } else if (n >= 8) {
-                    v = *reinterpret_cast<const uint4*>(ring + ((0 * 3 + c) * 8 + slot) * kTcfRowCols + o);
-                } else if (n >= 4) {
-                    const uint2* src = reinterpret_cast<const uint2*>(ring + ((0 * 3 + c) * 8 + slot) * kTcfRowCols + o);
-                    v = make_uint4(src[0].x, src[0].y, src[1].x, src[1].y);
-                } else {
-                    const uint32_t* src =
-                        reinterpret_cast<const uint32_t*>(ring + ((0 * 3 + c) * 8 + slot) * kTcfRowCols + o);
-                    v = make_uint4(src[0], src[1], src[2], src[3]);
-                }
-                *reinterpret_cast<uint4*>(dst + j * 16) = v;
+            const int o = 8 * g + n * j;  // first staged column of the chunk
+            uint4 v;
+            if (n >= 8) {
+                v = *reinterpret_cast<const uint4*>(ring + (c * 8 + slot) * kTcfRowCols + o);
+            } else if (n >= 4) {
+                const uint2* src = reinterpret_cast<const uint2*>(ring + (c * 8 + slot) * kTcfRowCols + o);
+                v = make_uint4(src[0].x, src[0].y, src[1].x, src[1].y);
+            } else {
+                // n = 1: odd starts read the copy shifted by one element
+                const int copy = (n == 1) ? (o & 1) : 0;
+                const uint32_t* src =
+                    reinterpret_cast<const uint32_t*>(ring + ((copy * 3 + c) * 8 + slot) * kTcfRowCols + o - copy);
+                v = make_uint4(src[0], src[1], src[2], src[3]);
             }
+            *reinterpret_cast<uint4*>(sA + ci * kTcfKGroup + g * 128 + j * 16) = v;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // A visible to the tensor core
         tc_fence_before();

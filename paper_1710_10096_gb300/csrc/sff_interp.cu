@@ -439,6 +439,52 @@ __global__ void __launch_bounds__(kModelWarps * 32) k_interp_models(InterpJob J)
     int fa = 0, fm = 0;                                    // ... of which motion seeds: fm
     unsigned far_a = 0, far_m = 0;                         // largest distance kept (all / motion)
     unsigned bound_a = 0xffffffffu, bound_m = 0xffffffffu;  // storage bounds, none yet
+    // Compaction, when a batch would not fit the slots (motion seeds far
+    // away behind many geometry-only seeds, e.g. the disparity fill's): the
+    // k-th smallest distances of the candidates so far bound the final ones
+    // from above (more candidates only lower them), so the candidates beyond
+    // them are no members and are dropped, keeping the others in scan order.
+    auto compact = [&]() {
+        const Candidates Cc{pos, word, fill};
+        unsigned DA = bound_a, DM = bound_m;
+        if (fa >= kg || fm >= km) {
+            int cnt[4];
+            unsigned da, dm;
+            kth_and_counts(Cc, kg, km, fa >= kg ? far_a : 0, fm >= km ? far_m : 0, lane, da, dm, cnt);
+            if (fa >= kg) DA = min(DA, da);
+            if (fm >= km) DM = min(DM, dm);
+        }
+        int kept = 0, kmot = 0;
+        for (int base = 0; base < fill; base += 32) {
+            const int j = base + lane;
+            uint32_t pj = 0;
+            int wj = -1;
+            bool keep = false, mot = false;
+            if (j < fill) {
+                pj = pos[j];
+                wj = word[j];
+                int dx, dy;
+                const unsigned d2 = cand_d2(pj, dx, dy);
+                mot = word_motion(wj);
+                keep = d2 <= DA || (mot && d2 <= DM);
+            }
+            const unsigned b = __ballot_sync(kFull, keep), bm = __ballot_sync(kFull, keep && mot);
+            __syncwarp();  // the batch is read before any of it is overwritten
+            if (keep) {
+                const int slot = kept + __popc(b & lt);  // <= j
+                pos[slot] = pj;
+                word[slot] = wj;
+            }
+            __syncwarp();
+            kept += __popc(b);
+            kmot += __popc(bm);
+        }
+        fill = kept;
+        fa = kept;
+        fm = kmot;
+        bound_a = DA;
+        bound_m = DM;
+    };
     auto scan = [&](int q) {
         unsigned ma = 0, mm = 0;
         for (int base = 0; base < ring_cells(q); base += 32) {
@@ -456,6 +502,10 @@ __global__ void __launch_bounds__(kModelWarps * 32) k_interp_models(InterpJob J)
                     d2 = (unsigned)(dx * dx + dy * dy);
                     if (!(d2 <= bound_a || (word_motion(w) && d2 <= bound_m))) w = -1;
                 }
+            }
+            if (fill + __popc(__ballot_sync(kFull, w >= 0)) > J.slots) {
+                compact();
+                if (w >= 0 && !(d2 <= bound_a || (word_motion(w) && d2 <= bound_m))) w = -1;
             }
             const unsigned has = __ballot_sync(kFull, w >= 0), mot = __ballot_sync(kFull, w >= 0 && word_motion(w));
             if (w >= 0) {

@@ -871,6 +871,10 @@ __global__ void __launch_bounds__(iter_threads<L, TX, TY>(), MB) k_iteration(con
     constexpr int kGroups = iter_threads<L, TX, TY>() / L;
     __shared__ uint2 s_vec[kRegX * kRegY];
     __shared__ int s_cost[kRegX * kRegY];
+    // programmatic dependent launch: wait for the previous launch (its state
+    // and memory), then let the next one be scheduled; no-ops otherwise
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int3 blk = iter_block(H);
     const Field& A = F.f[iter_field(H, blk)];
     const Views& V = A.V;
@@ -1067,6 +1071,8 @@ __global__ void __launch_bounds__(lat_threads<L * C, TX, TY>()) k_iteration_lat(
     constexpr int kHalfRow = (kRegX + 1) / 2, kTileHalfRow = TX / 2;
     __shared__ uint2 s_vec[kRegX * kRegY];
     __shared__ int s_cost[kRegX * kRegY];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int3 blk = iter_block(H);
     const Field& A = F.f[iter_field(H, blk)];
     const Views& V = A.V;
@@ -1615,7 +1621,8 @@ const IterVariant* find_variant(int lanes, int slots, int tx, int ty, int ctas) 
 bool tuning_valid(const sff_tuning& t) {
     if (!find_variant(t.lanes_per_pixel, t.slots, t.tile_x, t.tile_y, t.min_ctas)) return false;
     if (t.group_mb < 0 || t.group_mb > (1 << 20) || (t.pair_fields != 0 && t.pair_fields != 1) ||
-        t.alternate_order < 0 || t.alternate_order > 15)
+        t.alternate_order < 0 || t.alternate_order > 15 || (t.features_form != 0 && t.features_form != 1) ||
+        (t.pdl != 0 && t.pdl != 1))
         return false;
     for (int k = 0; k < SFF_MAX_SCALES - 1; ++k) {
         const int32_t* c = t.coarse[k];
@@ -1842,7 +1849,23 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
                 }
                 IterStep H{n,      s,  kDirs[it % 4][0], kDirs[it % 4][1], it, it == I - 1, f0, pair ? 1 : 0,
                            ((T.alternate_order >> s) & 1) ? (it & 1) : 0};
-                sv->k<<<gi, sv->threads, 0, st>>>(F, H);
+                if (T.pdl) {
+                    // scheduled while the previous iteration's last CTAs run;
+                    // its CTAs wait in griddepcontrol.wait until it is done
+                    cudaLaunchConfig_t cfg = {};
+                    cfg.gridDim = gi;
+                    cfg.blockDim = dim3(sv->threads);
+                    cfg.dynamicSmemBytes = 0;
+                    cfg.stream = st;
+                    cudaLaunchAttribute attr[1];
+                    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+                    attr[0].val.programmaticStreamSerializationAllowed = 1;
+                    cfg.attrs = attr;
+                    cfg.numAttrs = 1;
+                    if (cudaLaunchKernelEx(&cfg, sv->k, F, H) != cudaSuccess) return SFF_ERR_CUDA;
+                } else {
+                    sv->k<<<gi, sv->threads, 0, st>>>(F, H);
+                }
             }
             if (I > 0 && ::sff::profiling()) ::sff::profile_mark(kIterNames[s], st, true, I);
             f0 = f1;

@@ -62,6 +62,30 @@ def _scene_seeds(family, w, h, scene_seed, seed, **kw):
     return scenegen.sparse_seeds(gt, occ, seed, **kw), f, B
 
 
+@pytest.mark.parametrize("w,h,frac,over", [
+    (1242, 375, 0.6, {}),                                  # the driving size, default neighbourhoods
+    (400, 160, 0.85, dict(k_geo=40, k_motion=80)),         # motion seeds in one corner strip only
+])
+def test_far_motion_neighbours_equal_oracle(env, w, h, frac, over):
+    # dense geometry seeds everywhere, motion seeds only right of frac * W
+    # (the disparity fill's seeds carry d1 = 0: no motion): the motion
+    # neighbours of the seeds on the left are far, the rings that reach them
+    # hold many candidates, and the candidate buffer is compacted on the
+    # way; the field still equals the unbounded oracle's
+    gt, occ, f, B = scenegen.ground_truth("driving", w, h, 2)
+    seeds = scenegen.sparse_seeds(gt, occ, 5, keep=1.0)
+    left = seeds["x"] < int(frac * w)
+    seeds["u"][left] = 0
+    seeds["v"][left] = 0
+    seeds["d1"][left] = 0
+    seeds["kind"][left] = 1
+    assert left.sum() > 1000 and (~left).sum() > 100
+    got, status = _gpu_interp(env, seeds, w, h, f, B, **over)
+    want = _oracle_interp(env[2], seeds, w, h, f, B, **over)
+    assert status == 0
+    np.testing.assert_allclose(got, want, rtol=RTOL, atol=ATOL)
+
+
 @pytest.mark.parametrize("family,w,h,keep,noise,outl,over", [
     ("planes", 96, 64, 0.6, 0.5, 0.05, {}),                          # defaults: 160 / 80 neighbours
     ("driving", 37, 23, 1.0, 0.0, 0.0, dict(k_geo=20, k_motion=10)),  # ragged, dense
@@ -244,13 +268,20 @@ def test_invalid_seed_sets_are_reported(env):
     s["x"], s["y"] = [4, 45, 20], [4, 3, 20]  # x = 45 is outside the image
     got, status = _gpu_interp(env, s, w, h, 300.0, 0.5)
     assert status & 1 and (got == 0).all()
+
+
+
+def test_candidates_beyond_the_slots_are_compacted(env):
     # more candidates than the 6 k + 256 slots: a lone seed in the middle of a
-    # 480 x 480 px hole in a dense lattice (8151 candidates for k = 1024):
-    # reported, not truncated
+    # 480 x 480 px hole in a dense lattice (8151 candidates for k = 1024).  The
+    # buffer is compacted to the candidates within the k-th distances so far
+    # whenever it would overflow, and the field equals the unbounded oracle's
     w, h = 600, 600
     ys, xs = np.mgrid[0:200, 0:200]
     keep = (np.maximum(np.abs(xs - 100), np.abs(ys - 100)) >= 80) | ((xs == 100) & (ys == 100))
     d = np.zeros(int(keep.sum()), scenegen.SEED_RECORD)
     d["x"], d["y"], d["d0"], d["d1"] = 3 * xs[keep], 3 * ys[keep], 30, 31
     got, status = _gpu_interp(env, d, w, h, 300.0, 0.5, k_geo=1024, k_motion=4)
-    assert status & 2 and (got == 0).all()
+    want = _oracle_interp(env[2], d, w, h, 300.0, 0.5, k_geo=1024, k_motion=4)
+    assert status == 0
+    np.testing.assert_allclose(got, want, rtol=RTOL, atol=ATOL)

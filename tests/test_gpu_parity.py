@@ -340,7 +340,9 @@ def test_every_tuning_gives_identical_fields(env):
     # every other launch visiting its tiles last-to-first
     space += [sff.make_tuning(1, 32, 16, 0, None, 0, 1), sff.make_tuning(1, 8, 8, 4, [(1, 4, 8, 8)] * 3, 0, 1),
               sff.make_tuning(1, 32, 8, 0, None, 0, 0, 0, 1), sff.make_tuning(1, 32, 8, 0, None, 0, 1, 0, 15),
-              sff.make_tuning(2, 16, 8, 1, [(1, 4, 16, 8)] * 3, 0, 1, 0, 10)]
+              sff.make_tuning(2, 16, 8, 1, [(1, 4, 16, 8)] * 3, 0, 1, 0, 10),
+              # programmatic dependent launch of the iterations
+              sff.make_tuning(1, 32, 16, 0, [(1, 0, 32, 8, 7), (2, 1, 32, 8), (1, 4, 16, 8)], 0, 1, 0, 9, 0, 1)]
     for t in space:
         cand = t.scale_variants()
         out = [torch.empty((h, w, 4), dtype=torch.int16, device="cuda") for _ in range(2)]
@@ -398,17 +400,21 @@ def test_batch_of_uneven_quads_equals_each_alone(env):
     # sweep schedules of scale 0: all quads in every launch, every quad alone
     # (a budget below any quad), about two quads per group, and each with the
     # two fields of a quad alternating tile by tile
-    for group_mb, pair, alt in ((0, 0, 0), (1, 0, 0), (4, 0, 0), (0, 1, 0), (4, 1, 0), (0, 0, 1), (4, 1, 1)):
-        bm.tuning = sff.make_tuning(1, 32, 16, 0, None, group_mb, pair, 0, alt)
+    # (and the features on the tensor cores; the iterations with programmatic
+    # dependent launch)
+    for group_mb, pair, alt, form, pdl in ((0, 0, 0, 0, 0), (1, 0, 0, 0, 0), (4, 0, 0, 0, 0), (0, 1, 0, 0, 0),
+                                           (4, 1, 0, 1, 0), (0, 0, 1, 0, 1), (4, 1, 1, 1, 1)):
+        bm.tuning = sff.make_tuning(1, 32, 16, 0, None, group_mb, pair, 0, alt, form, pdl)
         bm.run([ms for _, ms in quads])
         torch.cuda.synchronize()
         for (q, ms), b, ref in zip(quads, bm.quads, refs):
-            assert np.array_equal(b.fwd.cpu().numpy(), ref["fwd"]), (group_mb, pair, alt)
-            assert np.array_equal(b.inv.cpu().numpy(), ref["inv"]), (group_mb, pair, alt)
-            assert np.array_equal(b.fwd_cost.cpu().numpy(), ref["fwd_cost"]), (group_mb, pair, alt)
-            assert np.array_equal(b.keep.cpu().numpy(), ref["keep"]), (group_mb, pair, alt)
-            assert np.array_equal(b.cerr.cpu().numpy(), ref["cerr"]), (group_mb, pair, alt)
-            assert b.seeds_numpy().tobytes() == ref["seeds"].tobytes(), (group_mb, pair, alt)
+            cfg = (group_mb, pair, alt, form, pdl)
+            assert np.array_equal(b.fwd.cpu().numpy(), ref["fwd"]), cfg
+            assert np.array_equal(b.inv.cpu().numpy(), ref["inv"]), cfg
+            assert np.array_equal(b.fwd_cost.cpu().numpy(), ref["fwd_cost"]), cfg
+            assert np.array_equal(b.keep.cpu().numpy(), ref["keep"]), cfg
+            assert np.array_equal(b.cerr.cpu().numpy(), ref["cerr"]), cfg
+            assert b.seeds_numpy().tobytes() == ref["seeds"].tobytes(), cfg
 
 
 def test_mixed_32_quad_batch_equals_oracle(env):
