@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--no-interp", action="store_true", help="skip the dense interpolation measurement")
     ap.add_argument("--no-fill", action="store_true", help="skip the disparity fill (SGM) measurement")
     ap.add_argument("--no-sift", action="store_true", help="skip the SIFT-PCA cost measurement")
+    ap.add_argument("--tuning-cache", default=None,
+                    help="file of autotuned settings: read if present (no autotuning launches), written after "
+                         "autotuning otherwise")
     ap.add_argument("--tuning", default="auto",
                     help="work distribution of the propagation kernels: 'auto' (autotune) or L,TX,TY")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(scenegen.CONFIG_SIZES),
@@ -864,10 +867,14 @@ def main():
     # size (any setting gives bit-identical results)
     from paper_1710_10096_gb300 import tune
     if args.tuning == "auto":
+        if args.tuning_cache:
+            tune.load_cache(args.tuning_cache)
         probe = sff.QuadMatcher(q.width, q.height, params, device=dev)
         probe.run(*[torch.as_tensor(im).to(dev) for im in q.images()], seed=MATCH_SEED)
         tuning = tune.autotune(probe.pyr, q.width, q.height, params, reps=3)
         del probe
+        if args.tuning_cache and rank == 0:
+            tune.save_cache(args.tuning_cache)
     else:
         tuning = sff.make_tuning(*(int(v) for v in args.tuning.split(",")))
     # the batch and the server take the tuned scale-0 variant with the coarse
@@ -992,7 +999,8 @@ def main():
                        "tuning_per_scale": [list(v) for v in tuning.scale_variants()],
                        "tuning_fields": "(lanes per pixel, candidate slots, tile_x, tile_y, min CTAs per SM) of "
                                         "scales 0..3",
-                       "pair_fields": tuning.pair_fields, "alternate_order_bits": tuning.alternate_order},
+                       "pair_fields": tuning.pair_fields, "alternate_order_bits": tuning.alternate_order,
+                       "pdl_bits": tuning.pdl},
             "roofline": roof, "gpu_launches": int(round(launches_per_step * args.steps)),
             "e2e": e2e, "clocks": clk, "kernels": kernels, "seeds": n_seeds,
             "device_status": sff.lib().sff_status_string(dev_status).decode(), "device_timeouts": dev_timeouts}

@@ -86,9 +86,9 @@ typedef struct sff_params {
  *   slots = 0: the throughput form, `lanes` in {1, 2, 4} threads sharing one
  *              pixel's feature loads, tile in {(64, 16), (32, 16), (64, 8),
  *              (32, 8), (16, 8), (8, 8)} grid pixels, min_ctas 0; and with one
- *              lane, (tile, min_ctas) in {(64 x 16, 2), (32 x 16, 4), (32 x 8,
- *              7), (32 x 8, 8)}: registers budgeted for that many resident
- *              CTAs per SM;
+ *              lane, (tile, min_ctas) in {(64 x 16, 2), (32 x 16, 3), (32 x 16,
+ *              4), (32 x 8, 6), (32 x 8, 7), (32 x 8, 8), (16 x 8, 12)}:
+ *              registers budgeted for that many resident CTAs per SM;
  *   slots = 1 or 4: the latency form (the next pixel's loads and the random
  *              draws issued up front, the colour-1 random search scored with
  *              the propagation candidates), each candidate of an update on
@@ -121,9 +121,10 @@ typedef struct sff_tuning {
     int32_t features_form;   /* transform of the whole-stage calls (sff_run_batch): 0 = butterflies
                               * on the CUDA cores (sff_features), 1 = tensor cores (sff_features_tc);
                               * identical features */
-    int32_t pdl;             /* 1 = the iteration launches use programmatic dependent launch: each
-                              * is scheduled while the previous one's last CTAs run and waits in
-                              * the kernel for its completion (same results) */
+    int32_t pdl;             /* bit s set (s = 0..3): the iteration launches of scale s use
+                              * programmatic dependent launch: each is scheduled while the previous
+                              * one's last CTAs run and waits in the kernel for its completion
+                              * (same results); 0..15 */
 } sff_tuning;
 
 /* One seed of Sec. 3.2: pixel (x, y) of L0, its vector and its scores. 20 bytes.

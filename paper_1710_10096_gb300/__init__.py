@@ -83,12 +83,13 @@ def _lat_fits(group: int, tx: int, ty: int) -> bool:
 
 
 # Every variant (lanes, slots, tile_x, tile_y, min_ctas) of the iteration
-# kernel: the throughput form (slots 0), four of its one-lane tiles also with a
+# kernel: the throughput form (slots 0), its one-lane tiles also with a
 # register budget for min_ctas resident CTAs per SM, and the latency form
 # (slots 1 or 4) on every tile whose region fits one cell per lane group in
 # 1024 threads.
 VARIANT_SPACE = [(l, 0, tx, ty, 0) for l in (1, 2, 4) for (tx, ty) in TILES] + \
-    [(1, 0, 64, 16, 2), (1, 0, 32, 16, 4), (1, 0, 32, 8, 7), (1, 0, 32, 8, 8)] + \
+    [(1, 0, 64, 16, 2), (1, 0, 32, 16, 3), (1, 0, 32, 16, 4), (1, 0, 32, 8, 6), (1, 0, 32, 8, 7), (1, 0, 32, 8, 8),
+     (1, 0, 16, 8, 12)] + \
     [(l, c, tx, ty, 0) for (l, c) in ((1, 1), (2, 1), (4, 1), (1, 4), (2, 4), (4, 4)) for (tx, ty) in TILES
      if _lat_fits(l * c, tx, ty)]
 

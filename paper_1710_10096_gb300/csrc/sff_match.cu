@@ -1595,7 +1595,8 @@ struct IterVariant {
 const IterVariant kIterVariants[] = {
     SFF_ITER_VARIANTS(1), SFF_ITER_VARIANTS(2), SFF_ITER_VARIANTS(4),
     // throughput form with a register budget for more resident CTAs per SM
-    SFF_ITER_VB(1, 64, 16, 2), SFF_ITER_VB(1, 32, 16, 4), SFF_ITER_VB(1, 32, 8, 7), SFF_ITER_VB(1, 32, 8, 8),
+    SFF_ITER_VB(1, 64, 16, 2), SFF_ITER_VB(1, 32, 16, 3), SFF_ITER_VB(1, 32, 16, 4), SFF_ITER_VB(1, 32, 8, 6),
+    SFF_ITER_VB(1, 32, 8, 7), SFF_ITER_VB(1, 32, 8, 8), SFF_ITER_VB(1, 16, 8, 12),
     // latency form: every tile whose region fits one cell per group in 1024 threads
     SFF_LAT_V(1, 1, 64, 16), SFF_LAT_V(1, 1, 32, 16), SFF_LAT_V(1, 1, 64, 8), SFF_LAT_V(1, 1, 32, 8),
     SFF_LAT_V(1, 1, 16, 8), SFF_LAT_V(1, 1, 8, 8),
@@ -1622,7 +1623,7 @@ bool tuning_valid(const sff_tuning& t) {
     if (!find_variant(t.lanes_per_pixel, t.slots, t.tile_x, t.tile_y, t.min_ctas)) return false;
     if (t.group_mb < 0 || t.group_mb > (1 << 20) || (t.pair_fields != 0 && t.pair_fields != 1) ||
         t.alternate_order < 0 || t.alternate_order > 15 || (t.features_form != 0 && t.features_form != 1) ||
-        (t.pdl != 0 && t.pdl != 1))
+        t.pdl < 0 || t.pdl > 15)
         return false;
     for (int k = 0; k < SFF_MAX_SCALES - 1; ++k) {
         const int32_t* c = t.coarse[k];
@@ -1849,7 +1850,7 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
                 }
                 IterStep H{n,      s,  kDirs[it % 4][0], kDirs[it % 4][1], it, it == I - 1, f0, pair ? 1 : 0,
                            ((T.alternate_order >> s) & 1) ? (it & 1) : 0};
-                if (T.pdl) {
+                if ((T.pdl >> s) & 1) {
                     // scheduled while the previous iteration's last CTAs run;
                     // its CTAs wait in griddepcontrol.wait until it is done
                     cudaLaunchConfig_t cfg = {};

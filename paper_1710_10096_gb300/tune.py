@@ -28,10 +28,10 @@ def size_bucket(width: int, height: int) -> str:
 
 def _tuning_of(entry) -> Tuning:
     """Tuning of a cache entry: {"variants": [4 x (lanes, slots, tile_x, tile_y, min_ctas)],
-    "pair": 0 | 1, "alt": bits}."""
+    "pair": 0 | 1, "alt": scale bits, "pdl": scale bits}."""
     vs = entry["variants"]
     l, c, tx, ty, mb = vs[0]
-    return make_tuning(l, tx, ty, c, vs[1:], 0, entry["pair"], mb, entry["alt"])
+    return make_tuning(l, tx, ty, c, vs[1:], 0, entry["pair"], mb, entry["alt"], 0, entry.get("pdl", 0))
 
 
 def scale_times(pyramids, width: int, height: int, tuning: Tuning, params=None, reps: int = 3, stream=None) -> dict:
@@ -89,23 +89,29 @@ def autotune(pyramids, width: int, height: int, params=None, reps: int = 3, spac
             print(f"variant {v}: " + " ".join(f"s{s} {us:.2f} us" for s, us in sorted(times.items())))
     d = default_tuning().scale_variants()
     variants = [best[s] if s < S and best[s] is not None else (d[s] if s == 0 else (0,) * 5) for s in range(4)]
-    # schedules on the chosen variants
+    # schedules on the chosen variants: pairing for the whole run, and per
+    # scale the best of reversed order on / off x dependent launch on / off
     full = (1 << S) - 1
+    combos = [(a, d) for a in (0, full) for d in (0, full)]
     sched = {}
     for pair in (0, 1):
-        for alt in (0, full):
-            t = _tuning_of({"variants": variants, "pair": pair, "alt": alt})
-            sched[(pair, alt)] = scale_times(pyramids, width, height, t, params, reps, stream)
+        for alt, pdl in combos:
+            t = _tuning_of({"variants": variants, "pair": pair, "alt": alt, "pdl": pdl})
+            sched[(pair, alt, pdl)] = scale_times(pyramids, width, height, t, params, reps, stream)
             if verbose:
-                print(f"pair {pair} alt {alt}: " +
-                      " ".join(f"s{s} {us:.2f} us" for s, us in sorted(sched[(pair, alt)].items())))
+                print(f"pair {pair} alt {alt} pdl {pdl}: " +
+                      " ".join(f"s{s} {us:.2f} us" for s, us in sorted(sched[(pair, alt, pdl)].items())))
+
+    def best_combo(pair, s):
+        return min(combos, key=lambda c: sched[(pair, c[0], c[1])][s])
 
     def total(pair):
-        return sum(min(sched[(pair, 0)][s], sched[(pair, full)][s]) for s in range(S))
+        return sum(sched[(pair, *best_combo(pair, s))][s] for s in range(S))
 
     pair = min((0, 1), key=total)
-    alt = sum(1 << s for s in range(S) if sched[(pair, full)][s] < sched[(pair, 0)][s])
-    entry = {"variants": variants, "pair": pair, "alt": alt}
+    alt = sum(1 << s for s in range(S) if best_combo(pair, s)[0])
+    pdl = sum(1 << s for s in range(S) if best_combo(pair, s)[1])
+    entry = {"variants": variants, "pair": pair, "alt": alt, "pdl": pdl}
     _CACHE[key] = entry
     return _tuning_of(entry)
 
@@ -152,7 +158,7 @@ def autotune_batch(batch, seeds, space=None, reps: int = 3, verbose: bool = Fals
 def save_cache(path: str) -> None:
     with open(path, "w") as f:
         json.dump({f"{k[0]}|{','.join(map(str, k[1]))}": {"variants": [list(v) for v in e["variants"]],
-                                                          "pair": e["pair"], "alt": e["alt"]}
+                                                          "pair": e["pair"], "alt": e["alt"], "pdl": e.get("pdl", 0)}
                    for k, e in _CACHE.items()}, f, indent=1)
 
 
@@ -170,11 +176,13 @@ def load_cache(path: str) -> int:
         b, p = k.split("|")
         if not (isinstance(e, dict) and isinstance(e.get("variants"), list) and len(e["variants"]) == 4 and
                 all(isinstance(v, list) and len(v) == 5 for v in e["variants"]) and e.get("pair") in (0, 1) and
-                isinstance(e.get("alt"), int) and 0 <= e["alt"] <= 15):
+                isinstance(e.get("alt"), int) and 0 <= e["alt"] <= 15 and isinstance(e.get("pdl", 0), int) and
+                0 <= e.get("pdl", 0) <= 15):
             continue
         vs = [tuple(v) for v in e["variants"]]
         if vs[0] in space and all(v in space or v == (0,) * 5 for v in vs[1:]):
-            _CACHE[(b, tuple(int(x) for x in p.split(",")))] = {"variants": vs, "pair": e["pair"], "alt": e["alt"]}
+            _CACHE[(b, tuple(int(x) for x in p.split(",")))] = {"variants": vs, "pair": e["pair"], "alt": e["alt"],
+                                                                "pdl": e.get("pdl", 0)}
             taken += 1
     return taken
 

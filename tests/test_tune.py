@@ -27,7 +27,7 @@ def test_cache_round_trip_skips_unsupported_entries(tmp_path):
         tune._CACHE.clear()
         params = tuple(sff.default_params().as_dict().values())
         good = {"variants": [sff.VARIANT_SPACE[1], (1, 0, 32, 16, 4), (0, 0, 0, 0, 0), (1, 4, 16, 8, 0)],
-                "pair": 1, "alt": 5}
+                "pair": 1, "alt": 5, "pdl": 8}
         tune._CACHE[("1280x384", params)] = good
         path = tmp_path / "tuning.json"
         tune.save_cache(str(path))
@@ -38,16 +38,17 @@ def test_cache_round_trip_skips_unsupported_entries(tmp_path):
         data["512x160|" + pk] = dict(ok, variants=[[4, 4, 16, 8, 0]] * 4)  # region beyond 1024 threads
         data["448x160|" + pk] = dict(ok, pair=2)  # not a schedule
         data["384x160|" + pk] = dict(ok, alt=16)  # not a scale bit mask
+        data["320x160|" + pk] = dict(ok, pdl=-1)  # not a scale bit mask
         data["256x96|" + pk] = [1, 0, 32, 8]  # an old (one variant) format
         data["128x64|" + pk] = [[1, 0, 32, 8, 0]] * 4  # an old (list of variants) format
         path.write_text(json.dumps(data))
         tune._CACHE.clear()
         assert tune.load_cache(str(path)) == 1
         e = tune._CACHE[("1280x384", params)]
-        assert e == {"variants": [tuple(v) for v in good["variants"]], "pair": 1, "alt": 5}
+        assert e == {"variants": [tuple(v) for v in good["variants"]], "pair": 1, "alt": 5, "pdl": 8}
         t = tune._tuning_of(e)
         assert t.scale_variants() == [tuple(v) for v in good["variants"]]
-        assert (t.pair_fields, t.alternate_order) == (1, 5)
+        assert (t.pair_fields, t.alternate_order, t.pdl) == (1, 5, 8)
         assert tune.load_cache(str(tmp_path / "missing.json")) == 0
     finally:
         tune._CACHE.clear()
@@ -62,13 +63,14 @@ def test_variant_space_matches_the_library():
         t = sff.make_tuning(l, tx, ty, c, [v] * 3, min_ctas=mb)
         assert t.scale_variants() == [v] * 4
     for bad in [(4, 4, 16, 8, 0), (2, 4, 32, 8, 0), (4, 1, 64, 8, 0), (2, 1, 64, 16, 0), (1, 2, 32, 8, 0),
-                (3, 0, 32, 8, 0), (1, 0, 32, 16, 3), (2, 0, 32, 16, 4), (1, 1, 32, 16, 4)]:
+                (3, 0, 32, 8, 0), (1, 0, 32, 16, 5), (2, 0, 32, 16, 4), (1, 1, 32, 16, 4)]:
         assert bad not in sff.VARIANT_SPACE
         with pytest.raises(sff.SffError):
             sff.make_tuning(bad[0], bad[2], bad[3], bad[1], min_ctas=bad[4])
         with pytest.raises(sff.SffError):
             sff.make_tuning(1, 32, 16, 0, [bad])
-    assert len(sff.VARIANT_SPACE) == 42
-    for bad_sched in [dict(group_mb=-1), dict(pair_fields=2), dict(alternate_order=16), dict(alternate_order=-1)]:
+    assert len(sff.VARIANT_SPACE) == 45
+    for bad_sched in [dict(group_mb=-1), dict(pair_fields=2), dict(alternate_order=16), dict(alternate_order=-1),
+                      dict(pdl=16), dict(features_form=2)]:
         with pytest.raises(sff.SffError):
             sff.make_tuning(1, 32, 16, 0, None, **bad_sched)
