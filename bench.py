@@ -73,6 +73,9 @@ def parse():
                          "autotuning otherwise")
     ap.add_argument("--tuning", default="auto",
                     help="work distribution of the propagation kernels: 'auto' (autotune) or L,TX,TY")
+    ap.add_argument("--features-form", default="butterfly", choices=["butterfly", "tensor"],
+                    help="WHT features of the timed stage: butterflies on the CUDA cores or the tensor-core "
+                         "form (identical features)")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(scenegen.CONFIG_SIZES),
                     help="scene (profiling uses the small planes_256x80 case)")
     return ap.parse_args()
@@ -185,14 +188,15 @@ def _units(kernel: str, w: int, h: int, params) -> float:
 
 
 def merge_scales(prof):
-    """Per-kernel totals {name: (launches, ms)} with the per-scale marks of a
-    kernel ("name/s<scale>") summed under its name, and those per-scale
-    entries separately: {name: {scale: (launches, ms)}}."""
+    """Per-kernel totals {name: (launches, ms)} of a profile_collect(with_units=True)
+    record, with the per-scale marks of a kernel ("name/s<scale>") summed under
+    its name, and those per-scale entries separately: {name: {scale: (units, ms,
+    launches)}}, units being iterations (a fused scale is one launch)."""
     merged, per_scale = {}, {}
-    for name, (n, ms) in prof.items():
+    for name, (n, ms, units) in prof.items():
         base, sep, sc = name.partition("/s")
         if sep:
-            per_scale.setdefault(base, {})[int(sc)] = (n, ms)
+            per_scale.setdefault(base, {})[int(sc)] = (units, ms, n)
         a = merged.get(base, (0, 0.0))
         merged[base] = (a[0] + n, a[1] + ms)
     return merged, per_scale
@@ -200,16 +204,19 @@ def merge_scales(prof):
 
 def iteration_scales(per_scale, w, h, n_fields, peak, dp4a_peak=None):
     """Per-scale roofline of the propagation kernel: algorithmic bytes per
-    launch (ALGO_BYTES per grid pixel, every grid pixel of every field once
-    per launch) over the average launch time, and the same for its dp4a."""
+    iteration (ALGO_BYTES per grid pixel, every grid pixel of every field once
+    per iteration) over the average time per iteration, and the same for its
+    dp4a.  per_scale: {scale: (iterations, ms, launches)}; a scale whose
+    iterations run as separate launches has one launch per iteration, a fused
+    one a single launch."""
     out = []
-    for s, (n, ms) in sorted(per_scale.items()):
+    for s, (n, ms, launches) in sorted(per_scale.items()):
         st = 1 << s
         grid = ((w + st - 1) // st) * ((h + st - 1) // st)
         b = ALGO_BYTES["k_iteration"] * n_fields * grid
         us = 1e3 * ms / n
-        r = {"scale": s, "grid_px": n_fields * grid, "launches": n, "avg_launch_us": us,
-             "algo_mb_per_launch": b / 1e6, "achieved_gbs": b / (us * 1e-6) / 1e9,
+        r = {"scale": s, "grid_px": n_fields * grid, "iterations": n, "launches": launches,
+             "avg_iteration_us": us, "algo_mb_per_iteration": b / 1e6, "achieved_gbs": b / (us * 1e-6) / 1e9,
              "frac": b / (us * 1e-6) / 1e9 / peak}
         if dp4a_peak:
             r["int_frac"] = ALGO_DP4A["k_iteration"] * n_fields * grid / (us * 1e-6) / dp4a_peak
@@ -311,13 +318,13 @@ def bench_batched(sff, torch, dev, quads, seeds, params, tuning, steps, warmup):
             bm.run(seeds, torch.cuda.current_stream(dev))
         gp.replay()
         s.synchronize()
-        bprof, bscales = merge_scales(sff.profile_collect())
+        bprof, bscales = merge_scales(sff.profile_collect(with_units=True))
     finally:
         sff.profile_enable(False)
     del gp
     breakdown = {k: {"launches": v[0], "ms": v[1]} for k, v in sorted(bprof.items(), key=lambda kv: -kv[1][1])}
-    per_scale = {f"s{sc}": {"launches": n, "ms": ms, "avg_launch_us": 1e3 * ms / n}
-                 for sc, (n, ms) in sorted(bscales.get("k_iteration", {}).items())}
+    per_scale = {f"s{sc}": {"launches": nl, "iterations": n, "ms": ms, "avg_iteration_us": 1e3 * ms / n}
+                 for sc, (n, ms, nl) in sorted(bscales.get("k_iteration", {}).items())}
     same = all(bq.seeds_numpy().tobytes() == m.buf.seeds_numpy().tobytes()
                and torch.equal(bq.fwd, m.fwd) and torch.equal(bq.inv, m.inv) for bq, (m, _) in zip(bm.quads, plain))
     out = {"workload": "32 quads: 8 x 1242x375 + 8 x 1024x436 (driving scenes), 8 x 640x192 + 8 x 512x160 "
@@ -877,6 +884,7 @@ def main():
             tune.save_cache(args.tuning_cache)
     else:
         tuning = sff.make_tuning(*(int(v) for v in args.tuning.split(",")))
+    tuning.features_form = 1 if args.features_form == "tensor" else 0
     # the batch and the server take the tuned scale-0 variant with the coarse
     # scales derived from their (much larger) launch sizes
     batch_tuning = sff.make_tuning(tuning.lanes_per_pixel, tuning.tile_x, tuning.tile_y, tuning.slots, None, 0,
@@ -905,7 +913,7 @@ def main():
                 m.run(*dev_in.unbind(0), seed=MATCH_SEED, stream=torch.cuda.current_stream())
         pgraph.replay()
         stream.synchronize()
-        prof, prof_scales = merge_scales(sff.profile_collect())
+        prof, prof_scales = merge_scales(sff.profile_collect(with_units=True))
         sff.profile_enable(False)
         del pgraph
 
@@ -985,7 +993,7 @@ def main():
             if roof["int_frac"] > roof["hbm_frac"]:
                 roof.update(bound="int", frac=roof["int_frac"])
         if dom in prof_scales:
-            sc = {s: (n / prof_steps, ms / prof_steps) for s, (n, ms) in prof_scales[dom].items()}
+            sc = {s: (n / prof_steps, ms / prof_steps, nl / prof_steps) for s, (n, ms, nl) in prof_scales[dom].items()}
             roof["per_scale"] = iteration_scales(sc, q.width, q.height, 2, peak, int_peak["dp4a_per_s"])
     total_prof = sum(v[1] for v in prof.values())
     kernels = {k: {"launches_per_step": v[0] / prof_steps, "ms_per_step": v[1] / prof_steps,
@@ -1000,7 +1008,8 @@ def main():
                        "tuning_fields": "(lanes per pixel, candidate slots, tile_x, tile_y, min CTAs per SM) of "
                                         "scales 0..3",
                        "pair_fields": tuning.pair_fields, "alternate_order_bits": tuning.alternate_order,
-                       "pdl_bits": tuning.pdl},
+                       "pdl_bits": tuning.pdl, "fuse_bits": tuning.fuse,
+                       "features_form": args.features_form},
             "roofline": roof, "gpu_launches": int(round(launches_per_step * args.steps)),
             "e2e": e2e, "clocks": clk, "kernels": kernels, "seeds": n_seeds,
             "device_status": sff.lib().sff_status_string(dev_status).decode(), "device_timeouts": dev_timeouts}

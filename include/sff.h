@@ -125,6 +125,19 @@ typedef struct sff_tuning {
                               * programmatic dependent launch: each is scheduled while the previous
                               * one's last CTAs run and waits in the kernel for its completion
                               * (same results); 0..15 */
+    int32_t fuse;            /* bit s set (s = 1..3): all iterations of scale s run in one
+                              * cooperative launch (every CTA resident, each taking tiles
+                              * blockIdx.x + k * gridDim.x), a bounded grid barrier between
+                              * iterations instead of a launch boundary (same results).  The
+                              * scale's variant must have a fused form: a derived one (all-zero
+                              * coarse entry) or (lanes, slots, tile_x x tile_y, min_ctas) one of
+                              * (1,0,32x16,0), (1,0,32x16,4), (1,0,32x8,0), (1,0,32x8,7),
+                              * (2,0,32x8,0), (1,1,32x16,0), (1,1,32x8,0), (1,1,16x8,0),
+                              * (1,1,8x8,0), (2,1,32x8,0), (2,1,16x8,0), (2,1,8x8,0),
+                              * (1,4,16x8,0), (1,4,8x8,0), (2,4,8x8,0); bit 0 clear, and no
+                              * bit shared with pdl or alternate_order; 0..14.  A
+                              * barrier wait that runs out (1 s) raises SFF_ERR_TIMEOUT in
+                              * sff_device_status. */
 } sff_tuning;
 
 /* One seed of Sec. 3.2: pixel (x, y) of L0, its vector and its scores. 20 bytes.
@@ -517,6 +530,9 @@ int sff_run_batch(const sff_quad* quads, int32_t n, const sff_params* params, co
 typedef struct sff_kernel_time {
     char name[40];       /* kernel name */
     int32_t launches;    /* launches recorded */
+    int32_t units;       /* work units they covered: iterations for the iteration kernel
+                          * (a fused scale is one launch of all its iterations), else
+                          * the launches */
     double total_ms;     /* summed event-to-event time */
 } sff_kernel_time;
 
@@ -581,6 +597,16 @@ int sff_device_status(void* stream, int32_t reset);
  * Applies to the current device; synchronous.  SFF_ERR_ARG for step < -1 or
  * wait_limit_us < 0. */
 int sff_debug_knn_withhold(int32_t step, int32_t wait_limit_us);
+
+/* Failure injection for the grid barrier of the fused iteration launches
+ * (sff_tuning.fuse; no counterpart in the paper).  barrier >= 0: in every
+ * later fused launch, CTA 0 leaves before arriving at that barrier (after
+ * iteration `barrier`), so the other CTAs' bounded waits run out and raise
+ * SFF_ERR_TIMEOUT; nothing is left in flight.  barrier = -1: off.
+ * wait_limit_us as in sff_debug_knn_withhold (the same limit).  Applies to
+ * the current device; synchronous.  SFF_ERR_ARG for barrier < -1 or
+ * wait_limit_us < 0. */
+int sff_debug_barrier_withhold(int32_t barrier, int32_t wait_limit_us);
 
 /* Human-readable name of a status code (static string). */
 const char* sff_status_string(int status);

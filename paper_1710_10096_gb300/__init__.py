@@ -61,7 +61,7 @@ class Tuning(ctypes.Structure):
     _fields_ = [("lanes_per_pixel", ctypes.c_int32), ("tile_x", ctypes.c_int32), ("tile_y", ctypes.c_int32),
                 ("slots", ctypes.c_int32), ("min_ctas", ctypes.c_int32), ("coarse", (ctypes.c_int32 * 5) * 3),
                 ("group_mb", ctypes.c_int32), ("pair_fields", ctypes.c_int32), ("alternate_order", ctypes.c_int32),
-                ("features_form", ctypes.c_int32), ("pdl", ctypes.c_int32)]
+                ("features_form", ctypes.c_int32), ("pdl", ctypes.c_int32), ("fuse", ctypes.c_int32)]
 
     def as_tuple(self):
         """(lanes, tile_x, tile_y) of scale 0 (the throughput-form space)."""
@@ -93,6 +93,12 @@ VARIANT_SPACE = [(l, 0, tx, ty, 0) for l in (1, 2, 4) for (tx, ty) in TILES] + \
     [(l, c, tx, ty, 0) for (l, c) in ((1, 1), (2, 1), (4, 1), (1, 4), (2, 4), (4, 4)) for (tx, ty) in TILES
      if _lat_fits(l * c, tx, ty)]
 
+# Variants that also exist in the fused form (all iterations of a coarse
+# scale in one cooperative launch: sff_tuning.fuse).
+FUSED_SPACE = [(1, 0, 32, 16, 0), (1, 0, 32, 16, 4), (1, 0, 32, 8, 0), (1, 0, 32, 8, 7), (2, 0, 32, 8, 0),
+               (1, 1, 32, 16, 0), (1, 1, 32, 8, 0), (1, 1, 16, 8, 0), (1, 1, 8, 8, 0), (2, 1, 32, 8, 0),
+               (2, 1, 16, 8, 0), (2, 1, 8, 8, 0), (1, 4, 16, 8, 0), (1, 4, 8, 8, 0), (2, 4, 8, 8, 0)]
+
 
 class QuadDesc(ctypes.Structure):
     """sff_quad of include/sff.h."""
@@ -121,7 +127,8 @@ class SgmParams(ctypes.Structure):
 
 class KernelTime(ctypes.Structure):
     """sff_kernel_time of include/sff.h."""
-    _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int32), ("total_ms", ctypes.c_double)]
+    _fields_ = [("name", ctypes.c_char * 40), ("launches", ctypes.c_int32), ("units", ctypes.c_int32),
+                ("total_ms", ctypes.c_double)]
 
 
 def profile_enable(on: bool = True) -> None:
@@ -129,12 +136,18 @@ def profile_enable(on: bool = True) -> None:
     _check(lib().sff_profile_enable(1 if on else 0), "sff_profile_enable")
 
 
-def profile_collect() -> dict:
-    """{kernel name: (launches, total ms)} of the launches recorded since enabling."""
+def profile_collect(with_units: bool = False) -> dict:
+    """{kernel name: (launches, total ms)} of the launches recorded since
+    enabling; with_units: (launches, total ms, work units), the units being
+    iterations for the iteration kernel (a fused scale is one launch of all
+    its iterations) and launches for the others."""
     cap = 64
     buf = (KernelTime * cap)()
     n = ctypes.c_int32(0)
     _check(lib().sff_profile_collect(buf, cap, ctypes.byref(n)), "sff_profile_collect")
+    if with_units:
+        return {buf[k].name.decode(): (buf[k].launches, buf[k].total_ms, buf[k].units)
+                for k in range(min(n.value, cap))}
     return {buf[k].name.decode(): (buf[k].launches, buf[k].total_ms) for k in range(min(n.value, cap))}
 
 
@@ -227,6 +240,8 @@ def lib():
         L.sff_device_status.restype = i32
         L.sff_debug_knn_withhold.argtypes = [i32, i32]
         L.sff_debug_knn_withhold.restype = i32
+        L.sff_debug_barrier_withhold.argtypes = [i32, i32]
+        L.sff_debug_barrier_withhold.restype = i32
         L.sff_int_peak.argtypes = [i32, ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
         L.sff_int_peak.restype = i32
         L.sff_status_string.argtypes = [i32]
@@ -362,17 +377,19 @@ def default_tuning() -> Tuning:
 
 def make_tuning(lanes: int, tile_x: int, tile_y: int, slots: int = 0, coarse=None, group_mb: int = 0,
                 pair_fields: int = 0, min_ctas: int = 0, alternate_order: int = 0, features_form: int = 0,
-                pdl: int = 0) -> Tuning:
+                pdl: int = 0, fuse: int = 0) -> Tuning:
     """sff_tuning: scale 0 (lanes, slots, tile, min_ctas); coarse = [(lanes, slots, tile_x,
     tile_y[, min_ctas])] for scales 1.. (None or all-zero entries: derived from the grid
     size); group_mb: the batch's scale-0 sweep schedule (0: all quads in every launch);
-    pair_fields: a quad's two fields alternate tile by tile in each launch."""
+    pair_fields: a quad's two fields alternate tile by tile in each launch; alternate_order,
+    pdl, fuse: per-scale bits of the launch schedule (see sff_tuning)."""
     t = Tuning(lanes, tile_x, tile_y, slots, min_ctas)
     t.group_mb = int(group_mb)
     t.pair_fields = int(pair_fields)
     t.alternate_order = int(alternate_order)
     t.features_form = int(features_form)
     t.pdl = int(pdl)
+    t.fuse = int(fuse)
     for k, v in enumerate(coarse or []):
         v = tuple(v) + (0,) * (5 - len(v))
         for j in range(5):
@@ -578,6 +595,11 @@ def debug_knn_withhold(step: int, wait_limit_us: int = 0) -> None:
     _check(lib().sff_debug_knn_withhold(int(step), int(wait_limit_us)), "sff_debug_knn_withhold")
 
 
+def debug_barrier_withhold(barrier: int, wait_limit_us: int = 0) -> None:
+    """sff_debug_barrier_withhold: failure injection for tests (barrier -1: off)."""
+    _check(lib().sff_debug_barrier_withhold(int(barrier), int(wait_limit_us)), "sff_debug_barrier_withhold")
+
+
 def seed_capacity(width: int, height: int) -> int:
     return ((width + 2) // 3) * ((height + 2) // 3)
 
@@ -720,7 +742,7 @@ class QuadMatcher:
         ws = workspace_bytes(self.width, self.height, p)
         w = self.workspace[:ws]
         for img, pyr in zip((L0, R0, L1, R1), self.pyr):
-            features(img, pyr, w, p, stream)
+            features(img, pyr, w, p, stream, tensor=self.tuning.features_form == 1)
         pL0, pR0, pL1, pR1 = self.pyr
         match_quad_tuned(pL0, pR0, pL1, pR1, self.width, self.height, seed, self.tuning, self.fwd, self.fwd_cost,
                          self.inv, self.inv_cost, w, p, stream)

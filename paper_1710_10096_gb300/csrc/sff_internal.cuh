@@ -237,7 +237,9 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
 // every kernel launch of the library; a mark pair may also span `launches`
 // back-to-back launches of one kernel.
 bool profiling();
-void profile_mark(const char* name, cudaStream_t st, bool after, int launches = 1);
+// units: the work units the span covers (iterations of the iteration kernel);
+// -1 = one per launch.
+void profile_mark(const char* name, cudaStream_t st, bool after, int launches = 1, int units = -1);
 
 #define SFF_LAUNCH(kernel, grid, block, smem, stream, ...)                       \
     do {                                                                         \

@@ -66,6 +66,7 @@ struct Field {
     int4* rec;    // [2][gq][3] int8 records of the stereo and cross images' coarsest grid
     int* rec_n;   // [2][gq] their norms
     uint2 key;  // Philox key: the seed of the field's quad
+    unsigned* sync;  // grid-barrier counter of a fused iteration launch (zeroed before each scale)
 };
 
 // Up to kMaxFields fields of any sizes share every launch (blockIdx.z picks
@@ -609,6 +610,7 @@ __device__ __forceinline__ void warp_row_nearest(const RefFeat& r, const int4* r
 __global__ void k_init_select(const __grid_constant__ Fields F, int n, int knn) {
     const Field& A = pick(F);
     const Views& V = A.V;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *A.sync = 0u;  // for this scale's fused iterations
     const int gw = A.gw;
     const int qi = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
@@ -653,6 +655,7 @@ __global__ void k_init_select(const __grid_constant__ Fields F, int n, int knn) 
 __global__ void k_inherit(const __grid_constant__ Fields F, int n) {
     const Field& A = pick(F);
     const Views& V = A.V;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *A.sync = 0u;  // for this scale's fused iterations
     const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y;
     if (gx >= A.gw || gy >= A.gh) return;
     const int x = gx * n, y = gy * n;
@@ -862,30 +865,57 @@ __device__ __forceinline__ int iter_field(const IterStep& H, int3 b) {
 }
 __device__ __forceinline__ int iter_tile_x(const IterStep& H, int3 b) { return H.pair ? (b.x >> 1) : b.x; }
 
-// MB > 0: compiled for at least MB resident CTAs per SM (a register budget
-// of 64K / (MB x threads)), so that a launch of few CTAs per SM fits one wave.
-template <int L, int TX, int TY, int MB>
-__global__ void __launch_bounds__(iter_threads<L, TX, TY>(), MB) k_iteration(const __grid_constant__ Fields F,
-                                                                              IterStep H) {
+// State of one iteration of a tile: the buffers it reads and writes and the
+// step's scale, sweep direction and iteration.
+struct TileStep {
+    const uint2* fin;
+    const int* cin;
+    uint2* fout;
+    int* cout;
+    int n, s, dx, dy, it, last;
+};
+
+// State loads and stores of the latency form.  kCg: through L2 only
+// (ld/st.global.cg), for a launch whose CTAs read in one iteration what other
+// CTAs wrote in the previous one (the fused form): an L1 line kept from an
+// earlier iteration could hold stale state.
+template <bool kCg>
+__device__ __forceinline__ int ld_cost(const int* p) {
+    if constexpr (kCg) return __ldcg(p);
+    else return *p;
+}
+template <bool kCg>
+__device__ __forceinline__ uint2 ld_vec(const uint2* p) {
+    if constexpr (kCg) return __ldcg(p);
+    else return *p;
+}
+template <bool kCg>
+__device__ __forceinline__ void st_state(const TileStep& T, size_t i, uint2 v, int c) {
+    if constexpr (kCg) {
+        __stcg(T.fout + i, v);
+        __stcg(T.cout + i, c);
+    } else {
+        T.fout[i] = v;
+        T.cout[i] = c;
+    }
+}
+
+// One iteration of the throughput form over the tile at grid (tx0, ty0) of
+// field A, with the shared-memory region s_vec / s_cost.  Every thread of
+// the CTA calls it; it contains one __syncthreads.
+template <int L, int TX, int TY, bool kCg>
+__device__ __forceinline__ void iter_tile(const Field& A, const TileStep& T, int tx0, int ty0, uint2* s_vec,
+                                          int* s_cost) {
     constexpr int kRegX = TX + 1, kRegY = TY + 1;
     constexpr int kGroups = iter_threads<L, TX, TY>() / L;
-    __shared__ uint2 s_vec[kRegX * kRegY];
-    __shared__ int s_cost[kRegX * kRegY];
-    // programmatic dependent launch: wait for the previous launch (its state
-    // and memory), then let the next one be scheduled; no-ops otherwise
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    const int3 blk = iter_block(H);
-    const Field& A = F.f[iter_field(H, blk)];
     const Views& V = A.V;
     const int q = threadIdx.x & (L - 1);
     const unsigned gmask = group_mask<L>();
     const int grp = threadIdx.x / L;
-    const int tx0 = iter_tile_x(H, blk) * TX, ty0 = blk.y * TY;
     const int gw = A.gw, gh = A.gh;
     if (tx0 >= gw || ty0 >= gh) return;  // tile beyond this field's grid (whole CTA)
-    const int rx0 = tx0 - (H.dx > 0 ? 1 : 0), ry0 = ty0 - (H.dy > 0 ? 1 : 0);  // region origin
-    const int n = H.n;
+    const int rx0 = tx0 - (T.dx > 0 ? 1 : 0), ry0 = ty0 - (T.dy > 0 ? 1 : 0);  // region origin
+    const int n = T.n;
 
     // phase 1: colour-0 pixels of the region (tile + halo)
     constexpr int kHalfRow = (kRegX + 1) / 2;
@@ -897,26 +927,23 @@ __global__ void __launch_bounds__(iter_threads<L, TX, TY>(), MB) k_iteration(con
         const int x = gx * n, y = gy * n;
         const size_t i = pix(V.w, x, y);            // image pixel: records, random stream
         const size_t si = (size_t)gy * gw + gx;      // compact state of the scale's grid
-        const int ax = x - H.dx * n, by = y - H.dy * n;
+        const int ax = x - T.dx * n, by = y - T.dy * n;
         const bool has_a = ax >= 0 && ax < V.w, has_b = by >= 0 && by < V.h;
-        const size_t ja = has_a ? si - H.dx : si, jb = has_b ? si - (size_t)(H.dy * gw) : si;
-        int c = A.cost[si];
-        const uint2 wc = A.field[si];
-        const int ca = has_a ? A.cost[ja] : kEmpty, cb = has_b ? A.cost[jb] : kEmpty;
-        const uint2 wa = A.field[ja], wb = A.field[jb];
+        const size_t ja = has_a ? si - T.dx : si, jb = has_b ? si - (size_t)(T.dy * gw) : si;
+        int c = ld_cost<kCg>(T.cin + si);
+        const uint2 wc = ld_vec<kCg>(T.fin + si);
+        const int ca = has_a ? ld_cost<kCg>(T.cin + ja) : kEmpty, cb = has_b ? ld_cost<kCg>(T.cin + jb) : kEmpty;
+        const uint2 wa = ld_vec<kCg>(T.fin + ja), wb = ld_vec<kCg>(T.fin + jb);
         Slice<L> a;
         load_slice<L>(V.ref, i, q, a);
         Vec4 cur = unpack_vec(wc);
-        update_pixel<L>(V, a, q, gmask, n, H.s, A.key, A.mirror, x, y, (uint32_t)i, H.it - 1, -1, unpack_vec(wa), ca,
+        update_pixel<L>(V, a, q, gmask, n, T.s, A.key, A.mirror, x, y, (uint32_t)i, T.it - 1, -1, unpack_vec(wa), ca,
                         unpack_vec(wb), cb, cur, c);
         if (q == 0) {
             const uint2 wv = pack_vec(cur);
             s_vec[ry * kRegX + rx] = wv;
             s_cost[ry * kRegX + rx] = c;
-            if (gx >= tx0 && gx < tx0 + TX && gy >= ty0 && gy < ty0 + TY) {
-                A.field_out[si] = wv;
-                A.cost_out[si] = c;
-            }
+            if (gx >= tx0 && gx < tx0 + TX && gy >= ty0 && gy < ty0 + TY) st_state<kCg>(T, si, wv, c);
         }
     }
     __syncthreads();
@@ -931,11 +958,11 @@ __global__ void __launch_bounds__(iter_threads<L, TX, TY>(), MB) k_iteration(con
         const int x = gx * n, y = gy * n;
         const size_t i = pix(V.w, x, y);
         const size_t si = (size_t)gy * gw + gx;
-        int c = A.cost[si];
-        Vec4 cur = unpack_vec(A.field[si]);
+        int c = ld_cost<kCg>(T.cin + si);
+        Vec4 cur = unpack_vec(ld_vec<kCg>(T.fin + si));
         Slice<L> a;
         load_slice<L>(V.ref, i, q, a);
-        const int agx = gx - H.dx, bgy = gy - H.dy;  // predecessors (colour 0, in the region)
+        const int agx = gx - T.dx, bgy = gy - T.dy;  // predecessors (colour 0, in the region)
         int ca = kEmpty, cb = kEmpty;
         uint2 wa = make_uint2(0u, 0u), wb = make_uint2(0u, 0u);
         if (agx >= 0 && agx < gw) {
@@ -948,14 +975,11 @@ __global__ void __launch_bounds__(iter_threads<L, TX, TY>(), MB) k_iteration(con
             cb = s_cost[r];
             wb = s_vec[r];
         }
-        update_pixel<L>(V, a, q, gmask, n, H.s, A.key, A.mirror, x, y, (uint32_t)i, -1, H.it, unpack_vec(wa), ca,
+        update_pixel<L>(V, a, q, gmask, n, T.s, A.key, A.mirror, x, y, (uint32_t)i, -1, T.it, unpack_vec(wa), ca,
                         unpack_vec(wb), cb, cur, c);
-        if (q == 0) {
-            A.field_out[si] = pack_vec(cur);
-            A.cost_out[si] = c;
-        }
+        if (q == 0) st_state<kCg>(T, si, pack_vec(cur), c);
     }
-    if (!H.last) return;
+    if (!T.last) return;
 
     // phase 3 (last iteration of the scale): the random search of this
     // iteration for the tile's colour-0 pixels, from their phase-1 results in
@@ -974,14 +998,28 @@ __global__ void __launch_bounds__(iter_threads<L, TX, TY>(), MB) k_iteration(con
         Vec4 cur = unpack_vec(s_vec[r]);
         Slice<L> a;
         load_slice<L>(V.ref, i, q, a);
-        if (update_pixel<L>(V, a, q, gmask, n, H.s, A.key, A.mirror, x, y, (uint32_t)i, H.it, -1, cur, kEmpty, cur,
+        if (update_pixel<L>(V, a, q, gmask, n, T.s, A.key, A.mirror, x, y, (uint32_t)i, T.it, -1, cur, kEmpty, cur,
                             kEmpty, cur, c) &&
-            q == 0) {
-            const size_t si = (size_t)gy * gw + gx;
-            A.field_out[si] = pack_vec(cur);
-            A.cost_out[si] = c;
-        }
+            q == 0)
+            st_state<kCg>(T, (size_t)gy * gw + gx, pack_vec(cur), c);
     }
+}
+
+// MB > 0: compiled for at least MB resident CTAs per SM (a register budget
+// of 64K / (MB x threads)), so that a launch of few CTAs per SM fits one wave.
+template <int L, int TX, int TY, int MB>
+__global__ void __launch_bounds__(iter_threads<L, TX, TY>(), MB) k_iteration(const __grid_constant__ Fields F,
+                                                                              IterStep H) {
+    __shared__ uint2 s_vec[(TX + 1) * (TY + 1)];
+    __shared__ int s_cost[(TX + 1) * (TY + 1)];
+    // programmatic dependent launch: wait for the previous launch (its state
+    // and memory), then let the next one be scheduled; no-ops otherwise
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const int3 blk = iter_block(H);
+    const Field& A = F.f[iter_field(H, blk)];
+    const TileStep T{A.field, A.cost, A.field_out, A.cost_out, H.n, H.s, H.dx, H.dy, H.it, H.last};
+    iter_tile<L, TX, TY, false>(A, T, iter_tile_x(H, blk) * TX, blk.y * TY, s_vec, s_cost);
 }
 
 // ---------------------------------------------------------------------------
@@ -1062,29 +1100,25 @@ __host__ __device__ constexpr bool lat_fits() {
     return lat_threads<G, TX, TY>() <= 1024;
 }
 
-template <int L, int C, int TX, int TY>
-__global__ void __launch_bounds__(lat_threads<L * C, TX, TY>()) k_iteration_lat(const __grid_constant__ Fields F,
-                                                                                 IterStep H) {
+// One iteration of the latency form over the tile at grid (tx0, ty0) of
+// field A, with the shared-memory region s_vec / s_cost.  Every thread of
+// the CTA calls it; it contains one __syncthreads.
+template <int L, int C, int TX, int TY, bool kCg>
+__device__ __forceinline__ void lat_tile(const Field& A, const TileStep& T, int tx0, int ty0, uint2* s_vec,
+                                         int* s_cost) {
     constexpr int G = L * C;
     static_assert(G <= 16 && lat_fits<G, TX, TY>() && TX % 2 == 0, "one region slot per group");
     constexpr int kRegX = TX + 1, kRegY = TY + 1;
     constexpr int kHalfRow = (kRegX + 1) / 2, kTileHalfRow = TX / 2;
-    __shared__ uint2 s_vec[kRegX * kRegY];
-    __shared__ int s_cost[kRegX * kRegY];
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    const int3 blk = iter_block(H);
-    const Field& A = F.f[iter_field(H, blk)];
     const Views& V = A.V;
     const int g = threadIdx.x & (G - 1);
     const int q = g & (L - 1), slot = g / L;
     const unsigned gmask = group_mask<G>();
     const int grp = threadIdx.x / G;  // this group's cell in each phase
-    const int tx0 = iter_tile_x(H, blk) * TX, ty0 = blk.y * TY;
     const int gw = A.gw, gh = A.gh;
     if (tx0 >= gw || ty0 >= gh) return;  // tile beyond this field's grid (whole CTA)
-    const int rx0 = tx0 - (H.dx > 0 ? 1 : 0), ry0 = ty0 - (H.dy > 0 ? 1 : 0);
-    const int n = H.n;
+    const int rx0 = tx0 - (T.dx > 0 ? 1 : 0), ry0 = ty0 - (T.dy > 0 ? 1 : 0);
+    const int n = T.n;
 
     // colour-1 pixel of the tile (phase 2): state, reference record, draw
     const int gy2 = ty0 + grp / kTileHalfRow;
@@ -1097,10 +1131,10 @@ __global__ void __launch_bounds__(lat_threads<L * C, TX, TY>()) k_iteration_lat(
     if (has2) {
         const size_t si = (size_t)gy2 * gw + gx2;
         const size_t i = pix(V.w, gx2 * n, gy2 * n);
-        c2 = A.cost[si];
-        w2 = A.field[si];
+        c2 = ld_cost<kCg>(T.cin + si);
+        w2 = ld_vec<kCg>(T.fin + si);
         load_slice<L>(V.ref, i, q, a2);
-        o2 = rs_draw(n, H.s, A.key, A.mirror, H.it, (uint32_t)i);
+        o2 = rs_draw(n, T.s, A.key, A.mirror, T.it, (uint32_t)i);
     }
 
     // phase 1: this group's colour-0 cell of the region (tile + halo)
@@ -1112,21 +1146,21 @@ __global__ void __launch_bounds__(lat_threads<L * C, TX, TY>()) k_iteration_lat(
             const int x = gx * n, y = gy * n;
             const size_t i = pix(V.w, x, y);
             const size_t si = (size_t)gy * gw + gx;
-            const int ax = x - H.dx * n, by = y - H.dy * n;
+            const int ax = x - T.dx * n, by = y - T.dy * n;
             const bool has_a = ax >= 0 && ax < V.w, has_b = by >= 0 && by < V.h;
-            const size_t ja = has_a ? si - H.dx : si, jb = has_b ? si - (size_t)(H.dy * gw) : si;
-            int c = A.cost[si];
-            const uint2 wc = A.field[si];
-            const int ca = has_a ? A.cost[ja] : kEmpty, cb = has_b ? A.cost[jb] : kEmpty;
-            const uint2 wa = A.field[ja], wb = A.field[jb];
+            const size_t ja = has_a ? si - T.dx : si, jb = has_b ? si - (size_t)(T.dy * gw) : si;
+            int c = ld_cost<kCg>(T.cin + si);
+            const uint2 wc = ld_vec<kCg>(T.fin + si);
+            const int ca = has_a ? ld_cost<kCg>(T.cin + ja) : kEmpty, cb = has_b ? ld_cost<kCg>(T.cin + jb) : kEmpty;
+            const uint2 wa = ld_vec<kCg>(T.fin + ja), wb = ld_vec<kCg>(T.fin + jb);
             Slice<L> a;
             load_slice<L>(V.ref, i, q, a);
-            const RsOff o = rs_draw(n, H.s, A.key, A.mirror, H.it - 1, (uint32_t)i);
+            const RsOff o = rs_draw(n, T.s, A.key, A.mirror, T.it - 1, (uint32_t)i);
             Vec4 cur = unpack_vec(wc);
             const Vec4 va = unpack_vec(wa), vb = unpack_vec(wb);
             const bool own_valid = c != kEmpty;
             Vec4 cr;
-            const bool do_rs = H.it > 0 && own_valid && rs_from(o, cur, cr);
+            const bool do_rs = T.it > 0 && own_valid && rs_from(o, cur, cr);
             const bool do_a = ca != kEmpty && !(own_valid && same_vec(va, cur));
             const bool do_b = cb != kEmpty && !(own_valid && same_vec(vb, cur)) && !(ca != kEmpty && same_vec(vb, va));
             const Vec4 cand[3] = {cr, va, vb};
@@ -1149,10 +1183,7 @@ __global__ void __launch_bounds__(lat_threads<L * C, TX, TY>()) k_iteration_lat(
                 const uint2 wv = pack_vec(cur);
                 s_vec[ry * kRegX + rx] = wv;
                 s_cost[ry * kRegX + rx] = c;
-                if (gx >= tx0 && gx < tx0 + TX && gy >= ty0 && gy < ty0 + TY) {
-                    A.field_out[si] = wv;
-                    A.cost_out[si] = c;
-                }
+                if (gx >= tx0 && gx < tx0 + TX && gy >= ty0 && gy < ty0 + TY) st_state<kCg>(T, si, wv, c);
             }
         }
     }
@@ -1163,7 +1194,7 @@ __global__ void __launch_bounds__(lat_threads<L * C, TX, TY>()) k_iteration_lat(
         const int x = gx2 * n, y = gy2 * n;
         int c = c2;
         Vec4 cur = unpack_vec(w2);
-        const int agx = gx2 - H.dx, bgy = gy2 - H.dy;  // predecessors (colour 0, in the region)
+        const int agx = gx2 - T.dx, bgy = gy2 - T.dy;  // predecessors (colour 0, in the region)
         int ca = kEmpty, cb = kEmpty;
         uint2 wa = make_uint2(0u, 0u), wb = make_uint2(0u, 0u);
         if (agx >= 0 && agx < gw) {
@@ -1232,12 +1263,10 @@ __global__ void __launch_bounds__(lat_threads<L * C, TX, TY>()) k_iteration_lat(
             }
         }
         if (g == 0) {
-            const size_t si = (size_t)gy2 * gw + gx2;
-            A.field_out[si] = pack_vec(cur);
-            A.cost_out[si] = c;
+            st_state<kCg>(T, (size_t)gy2 * gw + gx2, pack_vec(cur), c);
         }
     }
-    if (!H.last) return;
+    if (!T.last) return;
 
     // phase 3 (last iteration of the scale): the random search of this
     // iteration for the tile's colour-0 pixels, from their phase-1 results
@@ -1251,16 +1280,127 @@ __global__ void __launch_bounds__(lat_threads<L * C, TX, TY>()) k_iteration_lat(
         const int x = gx * n, y = gy * n;
         const size_t i = pix(V.w, x, y);
         const Vec4 cur = unpack_vec(s_vec[r]);
-        const RsOff o = rs_draw(n, H.s, A.key, A.mirror, H.it, (uint32_t)i);
+        const RsOff o = rs_draw(n, T.s, A.key, A.mirror, T.it, (uint32_t)i);
         Vec4 cr;
         if (!rs_from(o, cur, cr)) return;
         Slice<L> a;
         load_slice<L>(V.ref, i, q, a);
         const int cc = group_sum<L>(group_part<L>(V, a, q, x, y, cr), gmask);
-        if (cc < c && g == 0) {
-            const size_t si = (size_t)gy * gw + gx;
-            A.field_out[si] = pack_vec(cr);
-            A.cost_out[si] = cc;
+        if (cc < c && g == 0) st_state<kCg>(T, (size_t)gy * gw + gx, pack_vec(cr), cc);
+    }
+}
+
+template <int L, int C, int TX, int TY>
+__global__ void __launch_bounds__(lat_threads<L * C, TX, TY>()) k_iteration_lat(const __grid_constant__ Fields F,
+                                                                                 IterStep H) {
+    __shared__ uint2 s_vec[(TX + 1) * (TY + 1)];
+    __shared__ int s_cost[(TX + 1) * (TY + 1)];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const int3 blk = iter_block(H);
+    const Field& A = F.f[iter_field(H, blk)];
+    const TileStep T{A.field, A.cost, A.field_out, A.cost_out, H.n, H.s, H.dx, H.dy, H.it, H.last};
+    lat_tile<L, C, TX, TY, false>(A, T, iter_tile_x(H, blk) * TX, blk.y * TY, s_vec, s_cost);
+}
+
+// ---------------------------------------------------------------------------
+// Fused form of a coarse scale: all iterations of the scale in one
+// cooperative launch (every CTA resident), a grid barrier between
+// iterations instead of a launch boundary.  Each CTA takes tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ... of every field in turn and runs
+// the latency form's iteration on each; iteration `it` reads the buffers
+// (field, cost) when even and (field_out, cost_out) when odd and writes the
+// other pair, exactly as the separate launches do, so the results are the
+// same.  At a coarse scale an SM holds a few hundred grid pixels and a
+// launch lasts a few microseconds, about as long as the gap between two
+// dependent launches that the barrier replaces.
+struct FusedStep {
+    int n, s, iters;
+    int f0, nf;              // fields f0 .. f0 + nf - 1
+    int tiles_x, tiles_y;    // tile grid of the largest field
+    unsigned* sync;          // barrier counter, zero at launch
+};
+
+// Failure injection for tests (sff_debug_barrier_withhold): CTA 0 of a fused
+// launch leaves before arriving at this barrier (-1: never), so that the
+// other CTAs' bounded waits run out.
+__device__ int g_withhold_barrier = -1;
+
+// Grid barrier number b (0, 1, ...) of a cooperative launch: the counter
+// reaches (b + 1) * gridDim.x when every CTA has arrived.  Thread 0 arrives
+// with a release reduction (after the CTA barrier, so the release covers
+// the whole CTA's stores) and polls with acquire loads, which order the
+// CTA's later loads after the other CTAs' stores; it gives up after
+// limit_ns.  Measured on GB300: about 1.25 us per barrier at 120-150 CTAs,
+// 1.8 us at 456, 3.4 us at 1064 (a fence after the poll added 0.3 us).
+// Every thread of the CTA calls it; false when the wait gave up (the caller
+// leaves).
+__device__ __forceinline__ bool grid_barrier(unsigned* ctr, int b, unsigned long long limit_ns) {
+    __syncthreads();
+    int ok = 1;
+    if (threadIdx.x == 0) {
+        const unsigned target = (unsigned)(b + 1) * gridDim.x;
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ctr) : "memory");
+        const unsigned long long t0 = global_ns();
+        for (;;) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+            if (v >= target) break;
+            if (global_ns() - t0 > limit_ns) {
+                ok = 0;
+                break;
+            }
+        }
+    }
+    return __syncthreads_and(ok) != 0;
+}
+
+// Threads and resident CTAs per SM of a fused variant: C = 0 is the
+// throughput form, C > 0 the latency form with C slots.  MB > 0 is the
+// throughput form's register budget for MB resident CTAs; otherwise the
+// budget is about 100 registers a thread (without one, the loop over
+// iterations and tiles takes about 130 and the larger CTAs fit once per SM;
+// at 80 every latency variant spills).
+template <int L, int C, int TX, int TY>
+__host__ __device__ constexpr int fused_threads() {
+    return C == 0 ? iter_threads<L, TX, TY>() : lat_threads<L * C, TX, TY>();
+}
+template <int L, int C, int TX, int TY, int MB>
+__host__ __device__ constexpr int fused_min_blocks() {
+    return MB > 0 ? MB
+                  : (65536 / (fused_threads<L, C, TX, TY>() * 100) > 1 ? 65536 / (fused_threads<L, C, TX, TY>() * 100)
+                                                                        : 1);
+}
+
+template <int L, int C, int TX, int TY, int MB>
+__global__ void __launch_bounds__(fused_threads<L, C, TX, TY>(), fused_min_blocks<L, C, TX, TY, MB>())
+    k_iteration_fused(const __grid_constant__ Fields F, FusedStep H) {
+    __shared__ uint2 s_vec[(TX + 1) * (TY + 1)];
+    __shared__ int s_cost[(TX + 1) * (TY + 1)];
+    const unsigned long long wait_ns = g_wait_limit_ns ? g_wait_limit_ns : kDefaultWaitNs;
+    const int withhold = g_withhold_barrier;
+    const int per = H.tiles_x * H.tiles_y, total = per * H.nf;
+    for (int it = 0; it < H.iters; ++it) {
+        // sweep directions of iteration it: (1,1), (-1,-1), (1,-1), (-1,1), ...
+        const int m = it & 3;
+        const int dx = (m == 0 || m == 2) ? 1 : -1, dy = (m == 0 || m == 3) ? 1 : -1;
+        const bool odd = (it & 1) != 0;
+        for (int t = blockIdx.x; t < total; t += gridDim.x) {
+            const Field& A = F.f[H.f0 + t / per];
+            const int r = t % per;
+            const TileStep T{odd ? A.field_out : A.field, odd ? A.cost_out : A.cost, odd ? A.field : A.field_out,
+                             odd ? A.cost : A.cost_out, H.n, H.s, dx, dy, it, it == H.iters - 1};
+            if constexpr (C == 0)
+                iter_tile<L, TX, TY, true>(A, T, (r % H.tiles_x) * TX, (r / H.tiles_x) * TY, s_vec, s_cost);
+            else
+                lat_tile<L, C, TX, TY, true>(A, T, (r % H.tiles_x) * TX, (r / H.tiles_x) * TY, s_vec, s_cost);
+            __syncthreads();  // the region arrays are reused by the next tile
+        }
+        if (it + 1 == H.iters) break;
+        if (withhold == it && blockIdx.x == 0) return;  // injected: never arrives
+        if (!grid_barrier(H.sync, it, wait_ns)) {
+            if (threadIdx.x == 0) note_timeout();
+            return;
         }
     }
 }
@@ -1617,17 +1757,66 @@ const IterVariant* find_variant(int lanes, int slots, int tx, int ty, int ctas) 
     return nullptr;
 }
 
+// Variants that also exist in the fused form (k_iteration_fused).
+using FusedKernel = void (*)(Fields, FusedStep);
+struct FusedVariant {
+    int lanes, slots, tx, ty, ctas;
+    FusedKernel k;
+    int threads;
+};
+#define SFF_FUSED_V(L, C, X, Y, MB) {L, C, X, Y, MB, k_iteration_fused<L, C, X, Y, MB>, fused_threads<L, C, X, Y>()}
+const FusedVariant kFusedVariants[] = {
+    // throughput form
+    SFF_FUSED_V(1, 0, 32, 16, 0), SFF_FUSED_V(1, 0, 32, 16, 4), SFF_FUSED_V(1, 0, 32, 8, 0),
+    SFF_FUSED_V(1, 0, 32, 8, 7), SFF_FUSED_V(2, 0, 32, 8, 0),
+    // latency form
+    SFF_FUSED_V(1, 1, 32, 16, 0), SFF_FUSED_V(1, 1, 32, 8, 0), SFF_FUSED_V(1, 1, 16, 8, 0), SFF_FUSED_V(1, 1, 8, 8, 0),
+    SFF_FUSED_V(2, 1, 32, 8, 0), SFF_FUSED_V(2, 1, 16, 8, 0), SFF_FUSED_V(2, 1, 8, 8, 0), SFF_FUSED_V(1, 4, 16, 8, 0),
+    SFF_FUSED_V(1, 4, 8, 8, 0), SFF_FUSED_V(2, 4, 8, 8, 0)};
+#undef SFF_FUSED_V
+constexpr int kNumFused = (int)(sizeof kFusedVariants / sizeof kFusedVariants[0]);
+
+const FusedVariant* find_fused(int lanes, int slots, int tx, int ty, int ctas) {
+    for (const auto& v : kFusedVariants)
+        if (v.lanes == lanes && v.slots == slots && v.tx == tx && v.ty == ty && v.ctas == ctas) return &v;
+    return nullptr;
+}
+
+// CTAs of a fused variant that can be resident at once on this device (the
+// largest grid of its cooperative launch); 0 on error.
+int fused_capacity(const FusedVariant* v) {
+    static std::mutex mu;
+    static int cap[64][kNumFused] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    const int idx = (int)(v - kFusedVariants);
+    std::lock_guard<std::mutex> lk(mu);
+    if (cap[dev][idx] == 0) {
+        int per_sm = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, v->k, v->threads, 0) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return 0;
+        cap[dev][idx] = per_sm * sms;
+    }
+    return cap[dev][idx];
+}
+
 // A tuning is valid when its scale-0 variant exists and every coarse entry is
 // either all zero (chosen from the grid size) or an existing variant.
 bool tuning_valid(const sff_tuning& t) {
     if (!find_variant(t.lanes_per_pixel, t.slots, t.tile_x, t.tile_y, t.min_ctas)) return false;
     if (t.group_mb < 0 || t.group_mb > (1 << 20) || (t.pair_fields != 0 && t.pair_fields != 1) ||
         t.alternate_order < 0 || t.alternate_order > 15 || (t.features_form != 0 && t.features_form != 1) ||
-        t.pdl < 0 || t.pdl > 15)
+        t.pdl < 0 || t.pdl > 15 || t.fuse < 0 || t.fuse > 15 || (t.fuse & 1) ||
+        (t.fuse & (t.pdl | t.alternate_order)) != 0)
         return false;
     for (int k = 0; k < SFF_MAX_SCALES - 1; ++k) {
         const int32_t* c = t.coarse[k];
         if ((c[0] | c[1] | c[2] | c[3] | c[4]) != 0 && !find_variant(c[0], c[1], c[2], c[3], c[4])) return false;
+        // a fused scale's variant has a fused form (both derived variants do)
+        if (((t.fuse >> (k + 1)) & 1) && (c[0] | c[1] | c[2] | c[3] | c[4]) != 0 &&
+            !find_fused(c[0], c[1], c[2], c[3], c[4]))
+            return false;
     }
     return true;
 }
@@ -1662,7 +1851,7 @@ int coarse_gq(int w, int h, const sff_params& p) {
 // (whole 16 KB tiles, so every bulk copy starts and ends on 16 bytes), then
 // a second state buffer (field + cost) for the double-buffered iterations.
 struct FieldScratch {
-    size_t best8, tk, rec, rec_n, field, cost, total;
+    size_t best8, tk, rec, rec_n, field, cost, sync, total;
 };
 FieldScratch field_scratch(int w, int h, const sff_params& p) {
     const int gq = coarse_gq(w, h, p);
@@ -1673,7 +1862,8 @@ FieldScratch field_scratch(int w, int h, const sff_params& p) {
     f.rec_n = f.rec + align256((size_t)2 * gq * kFeat);
     f.field = f.rec_n + align256((size_t)2 * gq * sizeof(int));
     f.cost = f.field + align256((size_t)w * h * 8);
-    f.total = f.cost + align256((size_t)w * h * 4);
+    f.sync = f.cost + align256((size_t)w * h * 4);
+    f.total = f.sync + 256;
     return f;
 }
 
@@ -1722,6 +1912,7 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
         F.f[k].tk = reinterpret_cast<uint8_t*>(ws + sc.tk);
         F.f[k].rec = reinterpret_cast<int4*>(ws + sc.rec);
         F.f[k].rec_n = reinterpret_cast<int*>(ws + sc.rec_n);
+        F.f[k].sync = reinterpret_cast<unsigned*>(ws + sc.sync);
         F.f[k].gq = coarse_gq(fs.width, fs.height, P);
         F.f[k].mirror = fs.mirror;
         F.f[k].key = make_uint2((uint32_t)fs.seed, (uint32_t)(fs.seed >> 32));
@@ -1839,8 +2030,37 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
                        spec[k + 1].ref == spec[k].crs;
             const unsigned tiles_x = (ggw + sv->tx - 1) / sv->tx;
             dim3 gi(pair ? 2 * tiles_x : tiles_x, (ggh + sv->ty - 1) / sv->ty, pair ? (f1 - f0) / 2 : f1 - f0);
+            const bool fuse = ((T.fuse >> s) & 1) != 0 && I > 0;
             if (I > 0 && ::sff::profiling()) ::sff::profile_mark(kIterNames[s], st, false);
-            for (int it = 0; it < I; ++it) {
+            if (fuse) {
+                // one cooperative launch for all iterations (a variant with a
+                // fused form: validated, or one of the derived ones)
+                const FusedVariant* fv = find_fused(sv->lanes, sv->slots, sv->tx, sv->ty, sv->ctas);
+                if (!fv) return SFF_ERR_ARG;
+                const int cap = fused_capacity(fv);
+                if (cap <= 0) return SFF_ERR_CUDA;
+                const int tiles_x = (ggw + sv->tx - 1) / sv->tx, tiles_y = (ggh + sv->ty - 1) / sv->ty;
+                const int total = tiles_x * tiles_y * (f1 - f0);
+                for (int k = f0; k < f1; ++k) {
+                    F.f[k].field = Bf[cur][k];
+                    F.f[k].cost = Bc[cur][k];
+                    F.f[k].field_out = Bf[cur ^ 1][k];
+                    F.f[k].cost_out = Bc[cur ^ 1][k];
+                }
+                FusedStep FH{n, s, I, f0, f1 - f0, tiles_x, tiles_y, F.f[f0].sync};
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3((unsigned)std::min(total, cap));
+                cfg.blockDim = dim3(fv->threads);
+                cfg.dynamicSmemBytes = 0;
+                cfg.stream = st;
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeCooperative;
+                attr[0].val.cooperative = 1;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                if (cudaLaunchKernelEx(&cfg, fv->k, F, FH) != cudaSuccess) return SFF_ERR_CUDA;
+            }
+            for (int it = 0; it < (fuse ? 0 : I); ++it) {
                 const int in = cur ^ (it & 1);
                 for (int k = f0; k < f1; ++k) {
                     F.f[k].field = Bf[in][k];
@@ -1868,7 +2088,7 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
                     sv->k<<<gi, sv->threads, 0, st>>>(F, H);
                 }
             }
-            if (I > 0 && ::sff::profiling()) ::sff::profile_mark(kIterNames[s], st, true, I);
+            if (I > 0 && ::sff::profiling()) ::sff::profile_mark(kIterNames[s], st, true, fuse ? 1 : I, I);
             f0 = f1;
         }
         prev = cur ^ (I & 1);
@@ -2056,6 +2276,15 @@ extern "C" int sff_debug_knn_withhold(int32_t step, int32_t wait_limit_us) {
     const int st = step;
     const unsigned long long ns = (unsigned long long)wait_limit_us * 1000ull;
     if (cudaMemcpyToSymbol(sff::g_withhold_step, &st, sizeof st) != cudaSuccess) return SFF_ERR_CUDA;
+    if (cudaMemcpyToSymbol(sff::g_wait_limit_ns, &ns, sizeof ns) != cudaSuccess) return SFF_ERR_CUDA;
+    return SFF_OK;
+}
+
+extern "C" int sff_debug_barrier_withhold(int32_t barrier, int32_t wait_limit_us) {
+    if (barrier < -1 || wait_limit_us < 0) return SFF_ERR_ARG;
+    const int b = barrier;
+    const unsigned long long ns = (unsigned long long)wait_limit_us * 1000ull;
+    if (cudaMemcpyToSymbol(sff::g_withhold_barrier, &b, sizeof b) != cudaSuccess) return SFF_ERR_CUDA;
     if (cudaMemcpyToSymbol(sff::g_wait_limit_ns, &ns, sizeof ns) != cudaSuccess) return SFF_ERR_CUDA;
     return SFF_OK;
 }

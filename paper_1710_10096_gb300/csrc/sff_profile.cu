@@ -19,7 +19,7 @@ namespace {
 struct Mark {
     const char* name;
     cudaEvent_t start, stop;
-    int launches;
+    int launches, units;
 };
 
 std::mutex g_mu;
@@ -62,7 +62,7 @@ static void record_mark(cudaEvent_t e, cudaStream_t st) {
         cudaEventRecord(e, st);
 }
 
-void profile_mark(const char* name, cudaStream_t st, bool after, int launches) {
+void profile_mark(const char* name, cudaStream_t st, bool after, int launches, int units) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (!after) {
         g_pending = take_event();
@@ -70,7 +70,7 @@ void profile_mark(const char* name, cudaStream_t st, bool after, int launches) {
     } else {
         cudaEvent_t stop = take_event();
         record_mark(stop, st);
-        g_marks.push_back(Mark{name, g_pending, stop, launches});
+        g_marks.push_back(Mark{name, g_pending, stop, launches, units < 0 ? launches : units});
         g_pending = nullptr;
     }
 }
@@ -89,7 +89,7 @@ extern "C" int sff_profile_collect(sff_kernel_time* out, int32_t capacity, int32
     std::lock_guard<std::mutex> lk(sff::g_mu);
     std::vector<std::string> names;
     std::vector<double> ms;
-    std::vector<int> count;
+    std::vector<int> count, units;
     int status = SFF_OK;
     for (auto& m : sff::g_marks) {
         if (cudaEventSynchronize(m.stop) != cudaSuccess) status = SFF_ERR_CUDA;
@@ -101,15 +101,18 @@ extern "C" int sff_profile_collect(sff_kernel_time* out, int32_t capacity, int32
             names.emplace_back(m.name);
             ms.push_back(0.0);
             count.push_back(0);
+            units.push_back(0);
         }
         ms[k] += t;
         count[k] += m.launches;
+        units[k] += m.units;
     }
     for (size_t k = 0; k < names.size() && (int)k < capacity; ++k) {
         size_t len = names[k].size() < 39 ? names[k].size() : 39;
         names[k].copy(out[k].name, len);
         out[k].name[len] = 0;
         out[k].launches = count[k];
+        out[k].units = units[k];
         out[k].total_ms = ms[k];
     }
     *n_out = (int32_t)names.size();

@@ -6,17 +6,19 @@ pyramids, and the launches of each scale are timed as one span of CUDA events
 inside a CUDA graph (sff_profile_enable), so that each scale gets its own
 fastest variant.  Then the schedules are tried on those variants: a quad's two
 fields alternating tile by tile (pair_fields), and, per scale, every other
-launch visiting its tiles last-to-first (a bit of alternate_order).  All
-settings give bit-identical results (tested), so the choice only affects
-speed.  Results are cached per image-size bucket.
+launch visiting its tiles last-to-first (a bit of alternate_order) and
+programmatic dependent launch (a bit of pdl).  A coarse scale may instead
+run all its iterations in one cooperative launch (a bit of fuse) with the
+fastest of FUSED_SPACE.  All settings give bit-identical results (tested),
+so the choice only affects speed.  Results are cached per image-size bucket.
 """
 from __future__ import annotations
 
 import json
 import os
 
-from . import (VARIANT_SPACE, Tuning, default_params, default_tuning, make_tuning, match_quad_tuned, profile_collect,
-               profile_enable, workspace_bytes)
+from . import (FUSED_SPACE, VARIANT_SPACE, Tuning, default_params, default_tuning, make_tuning, match_quad_tuned,
+               profile_collect, profile_enable, workspace_bytes)
 
 _CACHE: dict = {}
 
@@ -28,15 +30,16 @@ def size_bucket(width: int, height: int) -> str:
 
 def _tuning_of(entry) -> Tuning:
     """Tuning of a cache entry: {"variants": [4 x (lanes, slots, tile_x, tile_y, min_ctas)],
-    "pair": 0 | 1, "alt": scale bits, "pdl": scale bits}."""
+    "pair": 0 | 1, "alt": scale bits, "pdl": scale bits, "fuse": scale bits}."""
     vs = entry["variants"]
     l, c, tx, ty, mb = vs[0]
-    return make_tuning(l, tx, ty, c, vs[1:], 0, entry["pair"], mb, entry["alt"], 0, entry.get("pdl", 0))
+    return make_tuning(l, tx, ty, c, vs[1:], 0, entry["pair"], mb, entry["alt"], 0, entry.get("pdl", 0),
+                       entry.get("fuse", 0))
 
 
 def scale_times(pyramids, width: int, height: int, tuning: Tuning, params=None, reps: int = 3, stream=None) -> dict:
-    """{scale: us per launch} of the iteration kernel with `tuning`, timed as
-    one span of events per scale in a CUDA graph of `reps` matching runs."""
+    """{scale: us per iteration} of the iteration kernel with `tuning`, timed
+    as one span of events per scale in a CUDA graph of `reps` matching runs."""
     import torch
     params = params or default_params()
     dev = pyramids[0].device
@@ -56,14 +59,14 @@ def scale_times(pyramids, width: int, height: int, tuning: Tuning, params=None, 
                                      torch.cuda.current_stream(dev))
             g.replay()
             s.synchronize()
-            prof = profile_collect()
+            prof = profile_collect(with_units=True)
         finally:
             profile_enable(False)
     res = {}
-    for name, (n, ms) in prof.items():
+    for name, (_, ms, units) in prof.items():
         base, sep, sc = name.partition("/s")
         if base == "k_iteration" and sep:
-            res[int(sc)] = 1e3 * ms / n
+            res[int(sc)] = 1e3 * ms / units
     return res
 
 
@@ -89,6 +92,18 @@ def autotune(pyramids, width: int, height: int, params=None, reps: int = 3, spac
             print(f"variant {v}: " + " ".join(f"s{s} {us:.2f} us" for s, us in sorted(times.items())))
     d = default_tuning().scale_variants()
     variants = [best[s] if s < S and best[s] is not None else (d[s] if s == 0 else (0,) * 5) for s in range(4)]
+    # the fused form of the coarse scales: every scale >= 1 fused with one variant
+    fused, fused_us = [None] * 4, [float("inf")] * 4
+    coarse_bits = sum(1 << s for s in range(1, S))
+    for v in (FUSED_SPACE if coarse_bits else []):
+        t = make_tuning(variants[0][0], variants[0][2], variants[0][3], variants[0][1], [v] * (S - 1),
+                        min_ctas=variants[0][4], fuse=coarse_bits)
+        times = scale_times(pyramids, width, height, t, params, reps, stream)
+        for s, us in times.items():
+            if s >= 1 and us < fused_us[s]:
+                fused[s], fused_us[s] = tuple(v), us
+        if verbose:
+            print(f"fused {tuple(v)}: " + " ".join(f"s{s} {us:.2f} us" for s, us in sorted(times.items())))
     # schedules on the chosen variants: pairing for the whole run, and per
     # scale the best of reversed order on / off x dependent launch on / off
     full = (1 << S) - 1
@@ -105,13 +120,20 @@ def autotune(pyramids, width: int, height: int, params=None, reps: int = 3, spac
     def best_combo(pair, s):
         return min(combos, key=lambda c: sched[(pair, c[0], c[1])][s])
 
+    def scale_us(pair, s):
+        return min(sched[(pair, *best_combo(pair, s))][s], fused_us[s])
+
     def total(pair):
-        return sum(sched[(pair, *best_combo(pair, s))][s] for s in range(S))
+        return sum(scale_us(pair, s) for s in range(S))
 
     pair = min((0, 1), key=total)
-    alt = sum(1 << s for s in range(S) if best_combo(pair, s)[0])
-    pdl = sum(1 << s for s in range(S) if best_combo(pair, s)[1])
-    entry = {"variants": variants, "pair": pair, "alt": alt, "pdl": pdl}
+    fuse = sum(1 << s for s in range(1, S) if fused_us[s] < sched[(pair, *best_combo(pair, s))][s])
+    for s in range(1, S):
+        if (fuse >> s) & 1:
+            variants[s] = fused[s]
+    alt = sum(1 << s for s in range(S) if best_combo(pair, s)[0] and not (fuse >> s) & 1)
+    pdl = sum(1 << s for s in range(S) if best_combo(pair, s)[1] and not (fuse >> s) & 1)
+    entry = {"variants": variants, "pair": pair, "alt": alt, "pdl": pdl, "fuse": fuse}
     _CACHE[key] = entry
     return _tuning_of(entry)
 
@@ -158,7 +180,8 @@ def autotune_batch(batch, seeds, space=None, reps: int = 3, verbose: bool = Fals
 def save_cache(path: str) -> None:
     with open(path, "w") as f:
         json.dump({f"{k[0]}|{','.join(map(str, k[1]))}": {"variants": [list(v) for v in e["variants"]],
-                                                          "pair": e["pair"], "alt": e["alt"], "pdl": e.get("pdl", 0)}
+                                                          "pair": e["pair"], "alt": e["alt"], "pdl": e.get("pdl", 0),
+                                                          "fuse": e.get("fuse", 0)}
                    for k, e in _CACHE.items()}, f, indent=1)
 
 
@@ -172,17 +195,21 @@ def load_cache(path: str) -> int:
         entries = json.load(f)
     taken = 0
     space = set(VARIANT_SPACE)
+    fused_space = set(FUSED_SPACE)
     for k, e in entries.items():
         b, p = k.split("|")
         if not (isinstance(e, dict) and isinstance(e.get("variants"), list) and len(e["variants"]) == 4 and
                 all(isinstance(v, list) and len(v) == 5 for v in e["variants"]) and e.get("pair") in (0, 1) and
                 isinstance(e.get("alt"), int) and 0 <= e["alt"] <= 15 and isinstance(e.get("pdl", 0), int) and
-                0 <= e.get("pdl", 0) <= 15):
+                0 <= e.get("pdl", 0) <= 15 and isinstance(e.get("fuse", 0), int) and 0 <= e.get("fuse", 0) <= 14 and
+                e.get("fuse", 0) % 2 == 0 and e.get("fuse", 0) & (e["alt"] | e.get("pdl", 0)) == 0):
             continue
         vs = [tuple(v) for v in e["variants"]]
-        if vs[0] in space and all(v in space or v == (0,) * 5 for v in vs[1:]):
+        fuse = e.get("fuse", 0)
+        if vs[0] in space and all(v in space or v == (0,) * 5 for v in vs[1:]) and \
+                all(vs[s] in fused_space or vs[s] == (0,) * 5 for s in range(1, 4) if (fuse >> s) & 1):
             _CACHE[(b, tuple(int(x) for x in p.split(",")))] = {"variants": vs, "pair": e["pair"], "alt": e["alt"],
-                                                                "pdl": e.get("pdl", 0)}
+                                                                "pdl": e.get("pdl", 0), "fuse": fuse}
             taken += 1
     return taken
 

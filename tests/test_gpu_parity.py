@@ -382,6 +382,61 @@ def test_latency_form_on_ragged_grids(env, size):
         assert np.array_equal(cst[1].cpu().numpy(), o["inv_cost"]), (l, c, tx, ty, mb)
 
 
+@pytest.mark.parametrize("size,iterations", [((250, 77), 12), ((97, 41), 12), ((250, 77), 5), ((97, 41), 1)])
+def test_fused_coarse_scales_on_ragged_grids(env, size, iterations):
+    # all iterations of each coarse scale in one cooperative launch (every
+    # fused variant), with even, odd and single iteration counts (the buffer
+    # parity and the no-barrier case), against the oracle
+    torch, sff, orc = env
+    w, h = size
+    q = scenegen.make_quad("planes", w, h, seed=w + h + iterations)
+    p = sff.default_params(iterations=iterations)
+    pyrs = [_gpu_features(torch, sff, im, p)[0] for im in q.images()]
+    ws = torch.empty(sff.workspace_bytes(w, h, p), dtype=torch.uint8, device="cuda")
+    o = orc.run_quad(*q.images(), seed=13, params=_oparams(orc, p))
+    sff.device_status(reset=True)
+    for v in sff.FUSED_SPACE + [None]:  # None: the variants derived from the grid sizes
+        t = sff.make_tuning(1, 32, 16, 0, None if v is None else [v] * 3, fuse=14)
+        out = [torch.empty((h, w, 4), dtype=torch.int16, device="cuda") for _ in range(2)]
+        cst = [torch.empty((h, w), dtype=torch.int32, device="cuda") for _ in range(2)]
+        sff.match_quad_tuned(*pyrs, w, h, 13, t, out[0], cst[0], out[1], cst[1], ws, p)
+        torch.cuda.synchronize()
+        assert np.array_equal(out[0].cpu().numpy(), o["fwd"]), v
+        assert np.array_equal(out[1].cpu().numpy(), o["inv"]), v
+        assert np.array_equal(cst[0].cpu().numpy(), o["fwd_cost"]), v
+        assert np.array_equal(cst[1].cpu().numpy(), o["inv_cost"]), v
+    assert sff.device_status(reset=True) == sff.OK
+
+
+def test_fused_scales_with_more_tiles_than_resident_ctas(env):
+    # 1242x375 driving quad, 8x8 tiles: scale 1 has 2 x 78 x 24 = 3744 tiles,
+    # more than the cooperative grid holds, so each CTA loops over tiles;
+    # scales 1 and 2 fused, 3 not, one fused scale with a 4-slot variant, and
+    # the throughput form fused
+    torch, sff, orc = env
+    q = scenegen.make_named("driving_1242x375", 3)
+    w, h = q.width, q.height
+    p = sff.default_params()
+    pyrs = [_gpu_features(torch, sff, im, p)[0] for im in q.images()]
+    ws = torch.empty(sff.workspace_bytes(w, h, p), dtype=torch.uint8, device="cuda")
+    o = orc.run_quad(*q.images(), seed=21)
+    sff.device_status(reset=True)
+    for coarse, fuse in [([(1, 1, 8, 8), (1, 1, 8, 8), (1, 4, 16, 8)], 6), ([(2, 1, 8, 8), (1, 4, 8, 8), (0,) * 5], 2),
+                         ([(1, 1, 32, 16), (2, 1, 32, 8), (1, 4, 16, 8)], 14),
+                         # throughput form: scale 1 in 2 x 20 x 12 tiles of 32x16, 2 CTAs per SM
+                         ([(1, 0, 32, 16), (1, 0, 32, 8, 7), (1, 0, 32, 8)], 14)]:
+        t = sff.make_tuning(1, 32, 16, 0, coarse, 0, 1, 0, 1, 0, 1, fuse=fuse)
+        out = [torch.empty((h, w, 4), dtype=torch.int16, device="cuda") for _ in range(2)]
+        cst = [torch.empty((h, w), dtype=torch.int32, device="cuda") for _ in range(2)]
+        sff.match_quad_tuned(*pyrs, w, h, 21, t, out[0], cst[0], out[1], cst[1], ws, p)
+        torch.cuda.synchronize()
+        assert np.array_equal(out[0].cpu().numpy(), o["fwd"]), (coarse, fuse)
+        assert np.array_equal(out[1].cpu().numpy(), o["inv"]), (coarse, fuse)
+        assert np.array_equal(cst[0].cpu().numpy(), o["fwd_cost"]), (coarse, fuse)
+        assert np.array_equal(cst[1].cpu().numpy(), o["inv_cost"]), (coarse, fuse)
+    assert sff.device_status(reset=True) == sff.OK
+
+
 def test_batch_of_uneven_quads_equals_each_alone(env):
     # quads of different sizes and seeds in shared launches (sff_run_batch):
     # every quad's fields, masks and seeds equal the oracle's run on it alone

@@ -2,11 +2,13 @@
 
 A bounded device wait that runs out, and a seed buffer smaller than the
 number of seeds, are reported when the caller synchronises; the context stays
-usable and the next run is exact.  The wait is made to run out with the
-library's failure injection (sff_debug_knn_withhold): the thread that issues
-the temporal K-NN's tensor-core MMAs stops before one step and issues nothing
-further, so the warps waiting for that step's results give up after a short
-limit.  Nothing faults: no copy or MMA is left in flight when the CTA exits.
+usable and the next run is exact.  The waits are made to run out with the
+library's failure injection: the thread that issues the temporal K-NN's
+tensor-core MMAs stops before one step and issues nothing further
+(sff_debug_knn_withhold), so the warps waiting for that step's results give
+up after a short limit; or one CTA of a fused iteration launch leaves before
+a grid barrier (sff_debug_barrier_withhold), so the others' barrier waits
+give up.  Nothing faults: no copy or MMA is left in flight when a CTA exits.
 """
 import os
 
@@ -96,3 +98,34 @@ def test_small_seed_buffer_reports_capacity(env):
         sff.emit_seeds(m.fwd, m.fwd_cost, m.keep, m.cerr, seeds, cap, count, ws)
         sff.check_device_status()
     assert e.value.status == sff.ERR_CAPACITY
+
+
+def test_withheld_grid_barrier_times_out_and_is_reported(env):
+    torch, sff, orc = env
+    q = scenegen.make_quad("planes", 512, 160, seed=33)
+    # scales 1..3 fused: every launch has 11 barriers
+    t = sff.make_tuning(1, 32, 16, 0, [(1, 1, 16, 8), (2, 1, 16, 8), (1, 4, 16, 8)], fuse=14)
+    m = sff.QuadMatcher(q.width, q.height, tuning=t)
+    dev = [torch.as_tensor(im).cuda() for im in q.images()]
+    sff.device_status(reset=True)
+    m.run(*dev, seed=7)
+    assert sff.device_status(reset=True) == sff.OK
+    sff.device_timeouts(reset=True)
+    try:
+        for barrier in (0, 10):
+            sff.debug_barrier_withhold(barrier, wait_limit_us=20000)
+            m.run(*dev, seed=7)
+            assert sff.device_status(reset=True) == sff.ERR_TIMEOUT, barrier
+            assert sff.device_timeouts(reset=True) > 0, barrier
+    finally:
+        sff.debug_barrier_withhold(-1, 0)
+    # the context is usable, the counters were zeroed again before each
+    # scale, and the next run is exact and clean
+    m.run(*dev, seed=7)
+    assert sff.device_status(reset=True) == sff.OK
+    assert sff.device_timeouts() == 0
+    ref = orc.run_quad(*q.images(), seed=7)
+    assert np.array_equal(m.fwd.cpu().numpy(), ref["fwd"])
+    assert np.array_equal(m.inv.cpu().numpy(), ref["inv"])
+    got = sff.seeds_to_numpy(m.seeds.cpu().numpy(), int(m.count.item()))
+    assert got.tobytes() == ref["seeds"].tobytes()
