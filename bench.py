@@ -157,18 +157,19 @@ def measured_peak_hbm():
     return FALLBACK_HBM_GBS, "fallback"
 
 
-def ncu_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from profiles/dram_traffic.txt, or None
-    when missing or taken on a different version of the kernel's source."""
+def ncu_traffic(kernel: str, launches_per_stage: float):
+    """DRAM bytes per launch of `kernel`: its bytes per stage from
+    profiles/dram_traffic.txt over its launches per stage, or None when missing
+    or taken on a different version of the kernel's source."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.txt")
-    if not os.path.exists(p):
+    if not os.path.exists(p) or launches_per_stage <= 0:
         return None
     for line in open(p):
         f = line.split()
         if len(f) >= 4 and f[0] == kernel and not line.startswith("#"):
             src = os.path.join(ROOT, "paper_1710_10096_gb300", "csrc", f[3])
             if os.path.exists(src) and hashlib.sha1(open(src, "rb").read()).hexdigest()[:12] == f[2]:
-                return float(f[1])
+                return float(f[1]) / launches_per_stage
     return None
 
 
@@ -979,7 +980,7 @@ def main():
         units = _units(dom, q.width, q.height, params) * prof_steps
         bytes_per_launch = ALGO_BYTES[dom] * units / dom_launches
         achieved = bytes_per_launch / (dom_ms / dom_launches / 1e3) / 1e9
-        tr = ncu_traffic(dom)
+        tr = ncu_traffic(dom, dom_launches / prof_steps)
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": tr, "peak_source": peak_src,
                 "algo_bytes_per_launch": bytes_per_launch, "avg_launch_us": 1e3 * dom_ms / dom_launches}
