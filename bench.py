@@ -14,6 +14,7 @@ on the host cores, on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import ctypes
 import hashlib
 import json
 import os
@@ -76,6 +77,9 @@ def parse():
     ap.add_argument("--features-form", default="butterfly", choices=["butterfly", "tensor"],
                     help="WHT features of the timed stage: butterflies on the CUDA cores or the tensor-core "
                          "form (identical features)")
+    ap.add_argument("--tma", action="store_true",
+                    help="scale 0 with TMA-staged reference records (sff_tuning.tma; the scale-0 variant must "
+                         "have that form)")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(scenegen.CONFIG_SIZES),
                     help="scene (profiling uses the small planes_256x80 case)")
     return ap.parse_args()
@@ -886,6 +890,10 @@ def main():
     else:
         tuning = sff.make_tuning(*(int(v) for v in args.tuning.split(",")))
     tuning.features_form = 1 if args.features_form == "tensor" else 0
+    if args.tma:
+        tuning.tma = 1
+        if not sff.lib().sff_tuning_supported(ctypes.byref(tuning)):
+            raise SystemExit(f"--tma: scale-0 variant {tuning.scale_variants()[0]} has no TMA form")
     # the batch and the server take the tuned scale-0 variant with the coarse
     # scales derived from their (much larger) launch sizes
     batch_tuning = sff.make_tuning(tuning.lanes_per_pixel, tuning.tile_x, tuning.tile_y, tuning.slots, None, 0,
@@ -1009,7 +1017,7 @@ def main():
                        "tuning_fields": "(lanes per pixel, candidate slots, tile_x, tile_y, min CTAs per SM) of "
                                         "scales 0..3",
                        "pair_fields": tuning.pair_fields, "alternate_order_bits": tuning.alternate_order,
-                       "pdl_bits": tuning.pdl, "fuse_bits": tuning.fuse,
+                       "pdl_bits": tuning.pdl, "fuse_bits": tuning.fuse, "tma": tuning.tma,
                        "features_form": args.features_form},
             "roofline": roof, "gpu_launches": int(round(launches_per_step * args.steps)),
             "e2e": e2e, "clocks": clk, "kernels": kernels, "seeds": n_seeds,

@@ -138,6 +138,11 @@ typedef struct sff_tuning {
                               * bit shared with pdl or alternate_order; 0..14.  A
                               * barrier wait that runs out (1 s) raises SFF_ERR_TIMEOUT in
                               * sff_device_status. */
+    int32_t tma;             /* 1: at scale 0 each CTA of the iteration kernel stages its
+                              * region's reference records in shared memory with one tensor
+                              * copy (TMA) instead of per-thread loads (same results); the
+                              * scale-0 variant must be (1, 0, 32x16 or 32x8) with min_ctas
+                              * 0, or 32x16 with 3, or 32x8 with 7; 0 or 1 */
 } sff_tuning;
 
 /* One seed of Sec. 3.2: pixel (x, y) of L0, its vector and its scores. 20 bytes.

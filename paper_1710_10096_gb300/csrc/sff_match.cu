@@ -40,6 +40,8 @@
 #include <cstring>
 #include <mutex>
 
+#include <cuda.h>  // CUtensorMap and its encoder's signature (resolved at run time)
+
 #include "sff_internal.cuh"
 #include "sff_tc.cuh"
 
@@ -902,10 +904,14 @@ __device__ __forceinline__ void st_state(const TileStep& T, size_t i, uint2 v, i
 
 // One iteration of the throughput form over the tile at grid (tx0, ty0) of
 // field A, with the shared-memory region s_vec / s_cost.  Every thread of
-// the CTA calls it; it contains one __syncthreads.
-template <int L, int TX, int TY, bool kCg>
+// the CTA calls it; it contains one __syncthreads.  kTma: the reference
+// records of the region (tile + halo) come from s_ref, where a tensor copy
+// completing on `bar` stages them as [chunk][region row][region column];
+// each thread waits for it (bounded by wait_ns) before its first read.
+template <int L, int TX, int TY, bool kCg, bool kTma = false>
 __device__ __forceinline__ void iter_tile(const Field& A, const TileStep& T, int tx0, int ty0, uint2* s_vec,
-                                          int* s_cost) {
+                                          int* s_cost, const int4* s_ref = nullptr, uint64_t* bar = nullptr,
+                                          unsigned long long wait_ns = 0) {
     constexpr int kRegX = TX + 1, kRegY = TY + 1;
     constexpr int kGroups = iter_threads<L, TX, TY>() / L;
     const Views& V = A.V;
@@ -916,6 +922,25 @@ __device__ __forceinline__ void iter_tile(const Field& A, const TileStep& T, int
     if (tx0 >= gw || ty0 >= gh) return;  // tile beyond this field's grid (whole CTA)
     const int rx0 = tx0 - (T.dx > 0 ? 1 : 0), ry0 = ty0 - (T.dy > 0 ? 1 : 0);  // region origin
     const int n = T.n;
+    bool staged = false;  // this thread has seen the tensor copy complete
+    // reference record of image pixel i, region cell r
+    auto ref_slice = [&](size_t i, int r, Slice<L>& a) {
+        if constexpr (kTma) {
+            if (!staged) {
+                if (!mbar_wait(bar, 0, wait_ns)) note_timeout();
+                staged = true;
+            }
+            a.nrm = 0;
+#pragma unroll
+            for (int k = 0; k < Slice<L>::kChunks; ++k) {
+                const int j = q + k * L;
+                a.c[k] = j < 3 ? s_ref[j * (kRegX * kRegY) + r] : make_int4(0, 0, 0, 0);
+                a.nrm = dot4(a.c[k], a.c[k], a.nrm);
+            }
+        } else {
+            load_slice<L>(V.ref, i, q, a);
+        }
+    };
 
     // phase 1: colour-0 pixels of the region (tile + halo)
     constexpr int kHalfRow = (kRegX + 1) / 2;
@@ -935,7 +960,7 @@ __device__ __forceinline__ void iter_tile(const Field& A, const TileStep& T, int
         const int ca = has_a ? ld_cost<kCg>(T.cin + ja) : kEmpty, cb = has_b ? ld_cost<kCg>(T.cin + jb) : kEmpty;
         const uint2 wa = ld_vec<kCg>(T.fin + ja), wb = ld_vec<kCg>(T.fin + jb);
         Slice<L> a;
-        load_slice<L>(V.ref, i, q, a);
+        ref_slice(i, ry * kRegX + rx, a);
         Vec4 cur = unpack_vec(wc);
         update_pixel<L>(V, a, q, gmask, n, T.s, A.key, A.mirror, x, y, (uint32_t)i, T.it - 1, -1, unpack_vec(wa), ca,
                         unpack_vec(wb), cb, cur, c);
@@ -961,7 +986,7 @@ __device__ __forceinline__ void iter_tile(const Field& A, const TileStep& T, int
         int c = ld_cost<kCg>(T.cin + si);
         Vec4 cur = unpack_vec(ld_vec<kCg>(T.fin + si));
         Slice<L> a;
-        load_slice<L>(V.ref, i, q, a);
+        ref_slice(i, (gy - ry0) * kRegX + (gx - rx0), a);
         const int agx = gx - T.dx, bgy = gy - T.dy;  // predecessors (colour 0, in the region)
         int ca = kEmpty, cb = kEmpty;
         uint2 wa = make_uint2(0u, 0u), wb = make_uint2(0u, 0u);
@@ -997,7 +1022,7 @@ __device__ __forceinline__ void iter_tile(const Field& A, const TileStep& T, int
         const size_t i = pix(V.w, x, y);
         Vec4 cur = unpack_vec(s_vec[r]);
         Slice<L> a;
-        load_slice<L>(V.ref, i, q, a);
+        ref_slice(i, r, a);
         if (update_pixel<L>(V, a, q, gmask, n, T.s, A.key, A.mirror, x, y, (uint32_t)i, T.it, -1, cur, kEmpty, cur,
                             kEmpty, cur, c) &&
             q == 0)
@@ -1020,6 +1045,51 @@ __global__ void __launch_bounds__(iter_threads<L, TX, TY>(), MB) k_iteration(con
     const Field& A = F.f[iter_field(H, blk)];
     const TileStep T{A.field, A.cost, A.field_out, A.cost_out, H.n, H.s, H.dx, H.dy, H.it, H.last};
     iter_tile<L, TX, TY, false>(A, T, iter_tile_x(H, blk) * TX, blk.y * TY, s_vec, s_cost);
+}
+
+// Tensor maps of the scale-0 reference records of every field of a launch:
+// the three 16-byte chunk planes of an image as a 4D tensor {4 x u32, W, H, 3}.
+struct RefMaps {
+    CUtensorMap m[kMaxFields];
+};
+
+// Scale-0 throughput form with the reference records of the tile's region
+// staged in shared memory by one tensor copy per CTA (TMA), issued before
+// the state loads so that both are in flight together.  The candidates'
+// records stay gathers: their addresses depend on the vectors, and the window
+// they span is larger than the records read (the tile plus the spread of the
+// vectors and the random search).
+template <int L, int TX, int TY, int MB>
+__global__ void __launch_bounds__(iter_threads<L, TX, TY>(), MB)
+    k_iteration_tma(const __grid_constant__ Fields F, IterStep H, const __grid_constant__ RefMaps M) {
+    __shared__ __align__(128) int4 s_ref[3 * (TX + 1) * (TY + 1)];
+    __shared__ uint2 s_vec[(TX + 1) * (TY + 1)];
+    __shared__ int s_cost[(TX + 1) * (TY + 1)];
+    __shared__ __align__(8) uint64_t bar;
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const int3 blk = iter_block(H);
+    const int f = iter_field(H, blk);
+    const Field& A = F.f[f];
+    const int tx0 = iter_tile_x(H, blk) * TX, ty0 = blk.y * TY;
+    if (tx0 >= A.gw || ty0 >= A.gh) return;  // tile beyond this field's grid (whole CTA)
+    const unsigned long long wait_ns = g_wait_limit_ns ? g_wait_limit_ns : kDefaultWaitNs;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+        mbar_expect_tx(&bar, (unsigned)sizeof(s_ref));
+        // box {4, TX + 1, TY + 1, 3} at the region origin; a negative origin
+        // (the halo at the image border) reads zeros, never used
+        tma_load_4d(s_ref, &M.m[f], 0, tx0 - (H.dx > 0 ? 1 : 0), ty0 - (H.dy > 0 ? 1 : 0), 0, &bar);
+    }
+    __syncthreads();
+    const TileStep T{A.field, A.cost, A.field_out, A.cost_out, H.n, H.s, H.dx, H.dy, H.it, H.last};
+    iter_tile<L, TX, TY, false, true>(A, T, tx0, ty0, s_vec, s_cost, s_ref, &bar, wait_ns);
+    // no CTA leaves with its copy in flight
+    if (threadIdx.x == 0 && !mbar_wait(&bar, 0, kDrainFactor * wait_ns)) {
+        atomicAdd(&g_drain_timeouts, 1u);
+        note_timeout();
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1782,6 +1852,61 @@ const FusedVariant* find_fused(int lanes, int slots, int tx, int ty, int ctas) {
     return nullptr;
 }
 
+// Scale-0 throughput variants that also exist with TMA-staged reference
+// records (k_iteration_tma, sff_tuning.tma).
+using TmaKernel = void (*)(Fields, IterStep, RefMaps);
+struct TmaVariant {
+    int lanes, tx, ty, ctas;
+    TmaKernel k;
+    int threads;
+};
+#define SFF_TMA_V(L, X, Y, MB) {L, X, Y, MB, k_iteration_tma<L, X, Y, MB>, iter_threads<L, X, Y>()}
+const TmaVariant kTmaVariants[] = {SFF_TMA_V(1, 32, 16, 0), SFF_TMA_V(1, 32, 16, 3), SFF_TMA_V(1, 32, 8, 0),
+                                   SFF_TMA_V(1, 32, 8, 7)};
+#undef SFF_TMA_V
+static_assert(sizeof(Fields) + sizeof(IterStep) + sizeof(RefMaps) <= 32000, "kernel parameters of k_iteration_tma");
+
+const TmaVariant* find_tma(int lanes, int slots, int tx, int ty, int ctas) {
+    if (slots != 0) return nullptr;
+    for (const auto& v : kTmaVariants)
+        if (v.lanes == lanes && v.tx == tx && v.ty == ty && v.ctas == ctas) return &v;
+    return nullptr;
+}
+
+// cuTensorMapEncodeTiled, resolved from the driver at run time (the library
+// links only the runtime).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// Tensor map of the scale-0 reference records of a w x h image (chunk planes
+// of pyramid `pyr`, 16-byte aligned) with the box of one TX x TY tile's region.
+bool encode_ref_map(CUtensorMap* m, const uint8_t* pyr, int w, int h, int S, int tx, int ty) {
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc || !chunk_planes(0)) return false;
+    const Plane P = plane_of(pyr, 0, S, w, h);
+    const cuuint64_t dim[4] = {4, (cuuint64_t)w, (cuuint64_t)h, 3};
+    const cuuint64_t stride[3] = {16, (cuuint64_t)16 * w, (cuuint64_t)16 * w * h};
+    const cuuint32_t box[4] = {4, (cuuint32_t)(tx + 1), (cuuint32_t)(ty + 1), 3};
+    const cuuint32_t estride[4] = {1, 1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT32, 4, const_cast<int4*>(P.f), dim, stride, box, estride,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // CTAs of a fused variant that can be resident at once on this device (the
 // largest grid of its cooperative launch); 0 on error.
 int fused_capacity(const FusedVariant* v) {
@@ -1808,8 +1933,9 @@ bool tuning_valid(const sff_tuning& t) {
     if (t.group_mb < 0 || t.group_mb > (1 << 20) || (t.pair_fields != 0 && t.pair_fields != 1) ||
         t.alternate_order < 0 || t.alternate_order > 15 || (t.features_form != 0 && t.features_form != 1) ||
         t.pdl < 0 || t.pdl > 15 || t.fuse < 0 || t.fuse > 15 || (t.fuse & 1) ||
-        (t.fuse & (t.pdl | t.alternate_order)) != 0)
+        (t.fuse & (t.pdl | t.alternate_order)) != 0 || (t.tma != 0 && t.tma != 1))
         return false;
+    if (t.tma && !find_tma(t.lanes_per_pixel, t.slots, t.tile_x, t.tile_y, t.min_ctas)) return false;
     for (int k = 0; k < SFF_MAX_SCALES - 1; ++k) {
         const int32_t* c = t.coarse[k];
         if ((c[0] | c[1] | c[2] | c[3] | c[4]) != 0 && !find_variant(c[0], c[1], c[2], c[3], c[4])) return false;
@@ -1897,6 +2023,7 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
     const int S = P.num_scales, I = P.iterations;
     static const int kDirs[4][2] = {{1, 1}, {-1, -1}, {1, -1}, {-1, 1}};
     static Fields F;  // host staging of the kernel parameter (copied at each launch)
+    static RefMaps RM;  // tensor maps of the TMA variant (scale 0)
     std::lock_guard<std::mutex> lk(g_fields_mu);
     memset(&F, 0, sizeof F);
     uint2* U[kMaxFields];
@@ -2060,6 +2187,15 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
                 cfg.numAttrs = 1;
                 if (cudaLaunchKernelEx(&cfg, fv->k, F, FH) != cudaSuccess) return SFF_ERR_CUDA;
             }
+            // scale 0 with TMA-staged reference records: one tensor map per field
+            const TmaVariant* tv = nullptr;
+            if (s == 0 && T.tma && !fuse && I > 0) {
+                tv = find_tma(sv->lanes, sv->slots, sv->tx, sv->ty, sv->ctas);
+                if (!tv) return SFF_ERR_ARG;
+                for (int k = f0; k < f1; ++k)
+                    if (!encode_ref_map(&RM.m[k], spec[k].ref, spec[k].width, spec[k].height, S, sv->tx, sv->ty))
+                        return SFF_ERR_CUDA;
+            }
             for (int it = 0; it < (fuse ? 0 : I); ++it) {
                 const int in = cur ^ (it & 1);
                 for (int k = f0; k < f1; ++k) {
@@ -2070,7 +2206,20 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
                 }
                 IterStep H{n,      s,  kDirs[it % 4][0], kDirs[it % 4][1], it, it == I - 1, f0, pair ? 1 : 0,
                            ((T.alternate_order >> s) & 1) ? (it & 1) : 0};
-                if ((T.pdl >> s) & 1) {
+                if (tv) {
+                    // TMA-staged reference records (scale 0)
+                    cudaLaunchConfig_t cfg = {};
+                    cfg.gridDim = gi;
+                    cfg.blockDim = dim3(tv->threads);
+                    cfg.dynamicSmemBytes = 0;
+                    cfg.stream = st;
+                    cudaLaunchAttribute attr[1];
+                    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+                    attr[0].val.programmaticStreamSerializationAllowed = 1;
+                    cfg.attrs = attr;
+                    cfg.numAttrs = ((T.pdl >> s) & 1) ? 1 : 0;
+                    if (cudaLaunchKernelEx(&cfg, tv->k, F, H, RM) != cudaSuccess) return SFF_ERR_CUDA;
+                } else if ((T.pdl >> s) & 1) {
                     // scheduled while the previous iteration's last CTAs run;
                     // its CTAs wait in griddepcontrol.wait until it is done
                     cudaLaunchConfig_t cfg = {};

@@ -9,7 +9,8 @@ fields alternating tile by tile (pair_fields), and, per scale, every other
 launch visiting its tiles last-to-first (a bit of alternate_order) and
 programmatic dependent launch (a bit of pdl).  A coarse scale may instead
 run all its iterations in one cooperative launch (a bit of fuse) with the
-fastest of FUSED_SPACE.  All settings give bit-identical results (tested),
+fastest of FUSED_SPACE, and scale 0 may stage its reference records with
+tensor copies (tma) when its variant is in TMA_SPACE.  All settings give bit-identical results (tested),
 so the choice only affects speed.  Results are cached per image-size bucket.
 """
 from __future__ import annotations
@@ -17,7 +18,7 @@ from __future__ import annotations
 import json
 import os
 
-from . import (FUSED_SPACE, VARIANT_SPACE, Tuning, default_params, default_tuning, make_tuning, match_quad_tuned,
+from . import (FUSED_SPACE, TMA_SPACE, VARIANT_SPACE, Tuning, default_params, default_tuning, make_tuning, match_quad_tuned,
                profile_collect, profile_enable, workspace_bytes)
 
 _CACHE: dict = {}
@@ -30,11 +31,11 @@ def size_bucket(width: int, height: int) -> str:
 
 def _tuning_of(entry) -> Tuning:
     """Tuning of a cache entry: {"variants": [4 x (lanes, slots, tile_x, tile_y, min_ctas)],
-    "pair": 0 | 1, "alt": scale bits, "pdl": scale bits, "fuse": scale bits}."""
+    "pair": 0 | 1, "alt": scale bits, "pdl": scale bits, "fuse": scale bits, "tma": 0 | 1}."""
     vs = entry["variants"]
     l, c, tx, ty, mb = vs[0]
     return make_tuning(l, tx, ty, c, vs[1:], 0, entry["pair"], mb, entry["alt"], 0, entry.get("pdl", 0),
-                       entry.get("fuse", 0))
+                       entry.get("fuse", 0), entry.get("tma", 0))
 
 
 def scale_times(pyramids, width: int, height: int, tuning: Tuning, params=None, reps: int = 3, stream=None) -> dict:
@@ -133,7 +134,15 @@ def autotune(pyramids, width: int, height: int, params=None, reps: int = 3, spac
             variants[s] = fused[s]
     alt = sum(1 << s for s in range(S) if best_combo(pair, s)[0] and not (fuse >> s) & 1)
     pdl = sum(1 << s for s in range(S) if best_combo(pair, s)[1] and not (fuse >> s) & 1)
-    entry = {"variants": variants, "pair": pair, "alt": alt, "pdl": pdl, "fuse": fuse}
+    entry = {"variants": variants, "pair": pair, "alt": alt, "pdl": pdl, "fuse": fuse, "tma": 0}
+    # scale 0 with TMA-staged reference records, on the chosen schedule
+    if tuple(variants[0]) in TMA_SPACE:
+        plain = scale_times(pyramids, width, height, _tuning_of(entry), params, reps, stream)
+        staged = scale_times(pyramids, width, height, _tuning_of(dict(entry, tma=1)), params, reps, stream)
+        if verbose:
+            print(f"scale 0 tma 0: {plain[0]:.2f} us, tma 1: {staged[0]:.2f} us")
+        if staged[0] < plain[0]:
+            entry["tma"] = 1
     _CACHE[key] = entry
     return _tuning_of(entry)
 
@@ -181,7 +190,7 @@ def save_cache(path: str) -> None:
     with open(path, "w") as f:
         json.dump({f"{k[0]}|{','.join(map(str, k[1]))}": {"variants": [list(v) for v in e["variants"]],
                                                           "pair": e["pair"], "alt": e["alt"], "pdl": e.get("pdl", 0),
-                                                          "fuse": e.get("fuse", 0)}
+                                                          "fuse": e.get("fuse", 0), "tma": e.get("tma", 0)}
                    for k, e in _CACHE.items()}, f, indent=1)
 
 
@@ -202,14 +211,17 @@ def load_cache(path: str) -> int:
                 all(isinstance(v, list) and len(v) == 5 for v in e["variants"]) and e.get("pair") in (0, 1) and
                 isinstance(e.get("alt"), int) and 0 <= e["alt"] <= 15 and isinstance(e.get("pdl", 0), int) and
                 0 <= e.get("pdl", 0) <= 15 and isinstance(e.get("fuse", 0), int) and 0 <= e.get("fuse", 0) <= 14 and
-                e.get("fuse", 0) % 2 == 0 and e.get("fuse", 0) & (e["alt"] | e.get("pdl", 0)) == 0):
+                e.get("fuse", 0) % 2 == 0 and e.get("fuse", 0) & (e["alt"] | e.get("pdl", 0)) == 0 and
+                e.get("tma", 0) in (0, 1)):
             continue
         vs = [tuple(v) for v in e["variants"]]
         fuse = e.get("fuse", 0)
         if vs[0] in space and all(v in space or v == (0,) * 5 for v in vs[1:]) and \
-                all(vs[s] in fused_space or vs[s] == (0,) * 5 for s in range(1, 4) if (fuse >> s) & 1):
+                all(vs[s] in fused_space or vs[s] == (0,) * 5 for s in range(1, 4) if (fuse >> s) & 1) and \
+                (e.get("tma", 0) == 0 or vs[0] in set(TMA_SPACE)):
             _CACHE[(b, tuple(int(x) for x in p.split(",")))] = {"variants": vs, "pair": e["pair"], "alt": e["alt"],
-                                                                "pdl": e.get("pdl", 0), "fuse": fuse}
+                                                                "pdl": e.get("pdl", 0), "fuse": fuse,
+                                                                "tma": e.get("tma", 0)}
             taken += 1
     return taken
 

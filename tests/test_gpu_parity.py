@@ -437,6 +437,36 @@ def test_fused_scales_with_more_tiles_than_resident_ctas(env):
     assert sff.device_status(reset=True) == sff.OK
 
 
+@pytest.mark.parametrize("size", [(250, 77), (97, 41), (8, 8), (1242, 375)])
+def test_tma_staged_reference_records(env, size):
+    # scale 0 with each CTA's region of reference records staged by one
+    # tensor copy (every TMA variant; plain and paired / reversed / dependent
+    # launches), on ragged grids, the minimum image (the box larger than the
+    # image) and the full driving quad, against the oracle
+    torch, sff, orc = env
+    w, h = size
+    q = (scenegen.make_named("driving_1242x375", 4) if size == (1242, 375)
+         else scenegen.make_quad("planes", w, h, seed=w * h % 97))
+    p = sff.default_params()
+    pyrs = [_gpu_features(torch, sff, im, p)[0] for im in q.images()]
+    ws = torch.empty(sff.workspace_bytes(w, h, p), dtype=torch.uint8, device="cuda")
+    o = orc.run_quad(*q.images(), seed=17)
+    sff.device_status(reset=True)
+    for v in sff.TMA_SPACE:
+        for pair, alt, pdl in ((0, 0, 0), (1, 1, 1)):
+            t = sff.make_tuning(v[0], v[2], v[3], v[1], None, 0, pair, v[4], alt, 0, pdl, tma=1)
+            out = [torch.empty((h, w, 4), dtype=torch.int16, device="cuda") for _ in range(2)]
+            cst = [torch.empty((h, w), dtype=torch.int32, device="cuda") for _ in range(2)]
+            sff.match_quad_tuned(*pyrs, w, h, 17, t, out[0], cst[0], out[1], cst[1], ws, p)
+            torch.cuda.synchronize()
+            cfg = (v, pair, alt, pdl)
+            assert np.array_equal(out[0].cpu().numpy(), o["fwd"]), cfg
+            assert np.array_equal(out[1].cpu().numpy(), o["inv"]), cfg
+            assert np.array_equal(cst[0].cpu().numpy(), o["fwd_cost"]), cfg
+            assert np.array_equal(cst[1].cpu().numpy(), o["inv_cost"]), cfg
+    assert sff.device_status(reset=True) == sff.OK
+
+
 def test_batch_of_uneven_quads_equals_each_alone(env):
     # quads of different sizes and seeds in shared launches (sff_run_batch):
     # every quad's fields, masks and seeds equal the oracle's run on it alone
@@ -456,14 +486,15 @@ def test_batch_of_uneven_quads_equals_each_alone(env):
     # (a budget below any quad), about two quads per group, and each with the
     # two fields of a quad alternating tile by tile
     # (and the features on the tensor cores; the iterations with programmatic
-    # dependent launch)
-    for group_mb, pair, alt, form, pdl in ((0, 0, 0, 0, 0), (1, 0, 0, 0, 0), (4, 0, 0, 0, 0), (0, 1, 0, 0, 0),
-                                           (4, 1, 0, 1, 0), (0, 0, 1, 0, 1), (4, 1, 1, 1, 1)):
-        bm.tuning = sff.make_tuning(1, 32, 16, 0, None, group_mb, pair, 0, alt, form, pdl)
+    # dependent launch; scale 0 with TMA-staged reference records)
+    for group_mb, pair, alt, form, pdl, tma in ((0, 0, 0, 0, 0, 0), (1, 0, 0, 0, 0, 0), (4, 0, 0, 0, 0, 0),
+                                                (0, 1, 0, 0, 0, 0), (4, 1, 0, 1, 0, 0), (0, 0, 1, 0, 1, 0),
+                                                (4, 1, 1, 1, 1, 0), (0, 1, 1, 0, 1, 1), (4, 0, 0, 0, 0, 1)):
+        bm.tuning = sff.make_tuning(1, 32, 16, 0, None, group_mb, pair, 0, alt, form, pdl, tma=tma)
         bm.run([ms for _, ms in quads])
         torch.cuda.synchronize()
         for (q, ms), b, ref in zip(quads, bm.quads, refs):
-            cfg = (group_mb, pair, alt, form, pdl)
+            cfg = (group_mb, pair, alt, form, pdl, tma)
             assert np.array_equal(b.fwd.cpu().numpy(), ref["fwd"]), cfg
             assert np.array_equal(b.inv.cpu().numpy(), ref["inv"]), cfg
             assert np.array_equal(b.fwd_cost.cpu().numpy(), ref["fwd_cost"]), cfg

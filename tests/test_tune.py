@@ -27,7 +27,7 @@ def test_cache_round_trip_skips_unsupported_entries(tmp_path):
         tune._CACHE.clear()
         params = tuple(sff.default_params().as_dict().values())
         good = {"variants": [sff.VARIANT_SPACE[1], (1, 0, 32, 16, 4), (0, 0, 0, 0, 0), (1, 4, 16, 8, 0)],
-                "pair": 1, "alt": 5, "pdl": 0, "fuse": 8}
+                "pair": 1, "alt": 5, "pdl": 0, "fuse": 8, "tma": 0}
         tune._CACHE[("1280x384", params)] = good
         path = tmp_path / "tuning.json"
         tune.save_cache(str(path))
@@ -42,13 +42,16 @@ def test_cache_round_trip_skips_unsupported_entries(tmp_path):
         data["320x128|" + pk] = dict(ok, variants=ok["variants"][:3] + [[4, 4, 8, 8, 0]], fuse=8)  # no fused form
         data["320x96|" + pk] = dict(ok, fuse=1)  # scale 0 is never fused
         data["320x64|" + pk] = dict(ok, pdl=8)  # fused and dependent launch on one scale
+        data["320x32|" + pk] = dict(ok, variants=[[2, 0, 32, 8, 0]] + ok["variants"][1:], tma=1)  # no TMA form
+        data["288x32|" + pk] = dict(ok, tma=2)  # not 0 / 1
         data["256x96|" + pk] = [1, 0, 32, 8]  # an old (one variant) format
         data["128x64|" + pk] = [[1, 0, 32, 8, 0]] * 4  # an old (list of variants) format
         path.write_text(json.dumps(data))
         tune._CACHE.clear()
         assert tune.load_cache(str(path)) == 1
         e = tune._CACHE[("1280x384", params)]
-        assert e == {"variants": [tuple(v) for v in good["variants"]], "pair": 1, "alt": 5, "pdl": 0, "fuse": 8}
+        assert e == {"variants": [tuple(v) for v in good["variants"]], "pair": 1, "alt": 5, "pdl": 0, "fuse": 8,
+                     "tma": 0}
         t = tune._tuning_of(e)
         assert t.scale_variants() == [tuple(v) for v in good["variants"]]
         assert (t.pair_fields, t.alternate_order, t.pdl, t.fuse) == (1, 5, 0, 8)
@@ -103,3 +106,18 @@ def test_fused_space_matches_the_library():
     # derived coarse variants (all-zero entries) always have a fused form
     assert sff.make_tuning(1, 32, 16, 0, None, fuse=14).fuse == 14
     assert sff.make_tuning(1, 32, 16, 0, [fv, (0,) * 5, fv], fuse=4).fuse == 4
+
+
+def test_tma_space_matches_the_library():
+    # every TMA variant is accepted as the scale-0 variant with tma = 1;
+    # other scale-0 variants and values other than 0 / 1 are refused
+    for v in sff.TMA_SPACE:
+        assert v in sff.VARIANT_SPACE
+        t = sff.make_tuning(v[0], v[2], v[3], v[1], None, min_ctas=v[4], tma=1)
+        assert t.tma == 1 and t.scale_variants()[0] == v
+    for v in [(1, 0, 64, 16, 0), (2, 0, 32, 8, 0), (1, 1, 32, 8, 0), (1, 0, 32, 16, 4)]:
+        assert v not in sff.TMA_SPACE
+        with pytest.raises(sff.SffError):
+            sff.make_tuning(v[0], v[2], v[3], v[1], None, min_ctas=v[4], tma=1)
+    with pytest.raises(sff.SffError):
+        sff.make_tuning(1, 32, 16, 0, None, tma=2)
