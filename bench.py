@@ -73,7 +73,9 @@ def parse():
                     help="file of autotuned settings: read if present (no autotuning launches), written after "
                          "autotuning otherwise")
     ap.add_argument("--tuning", default="auto",
-                    help="work distribution of the propagation kernels: 'auto' (autotune) or L,TX,TY")
+                    help="work distribution of the propagation kernels: 'auto' (autotune), L,TX,TY, or an "
+                         "autotuner entry as JSON: {\"variants\": [4 x [lanes, slots, tile_x, tile_y, "
+                         "min_ctas]], \"pair\": 0|1, \"alt\": bits, \"pdl\": bits, \"fuse\": bits}")
     ap.add_argument("--features-form", default="butterfly", choices=["butterfly", "tensor"],
                     help="WHT features of the timed stage: butterflies on the CUDA cores or the tensor-core "
                          "form (identical features)")
@@ -887,6 +889,8 @@ def main():
         del probe
         if args.tuning_cache and rank == 0:
             tune.save_cache(args.tuning_cache)
+    elif args.tuning.lstrip().startswith("{"):
+        tuning = tune._tuning_of(json.loads(args.tuning))
     else:
         tuning = sff.make_tuning(*(int(v) for v in args.tuning.split(",")))
     tuning.features_form = 1 if args.features_form == "tensor" else 0
