@@ -48,7 +48,7 @@ FALLBACK_HBM_GBS = 6800.0
 #                 48 B + norm 4 B, one 52 B target record per view = 232 B
 #   k_features    per pixel and scale: packed smoothed pixel 4 B in, 48 B
 #                 record + 4 B norm out
-ALGO_BYTES = {"k_iteration": 24 + 52 + 3 * 52, "k_features": 4 + 52}
+ALGO_BYTES = {"k_iteration": 24 + 52 + 3 * 52, "k_features": 8 + 52}
 # Algorithmic integer work of the iteration kernel per grid pixel and
 # iteration: 3 candidates (random search, 2 predecessors) x 3 views x one
 # 48-element int8 dot product = 432 MACs = 108 dp4a.
@@ -192,6 +192,70 @@ def _units(kernel: str, w: int, h: int, params) -> float:
     if kernel == "k_features":
         return 4.0 * S * w * h
     return 0.0
+
+
+def measured_peak_bf16():
+    """Dense bf16 tensor peak (TFLOP/s) for a kernel timed alone: the burst
+    figure of MEASURED_PEAKS.json, else the profiling fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            if "bf16_tflops" in d:
+                return float(d["bf16_tflops"]), "measured"
+        except (ValueError, KeyError, TypeError):
+            pass
+    return 1900.0, "fallback"
+
+
+def stage_rooflines(prof, steps, w, h, params, hbm_peak, bf16_peak, per_step_ms):
+    """Roofline of every stage kernel of one quad step with its own bound and
+    algorithmic work, and the stage's speed-of-light fraction: the sum over
+    kernels of (work / peak) over the measured step time.  prof: {kernel:
+    (launches, ms)} summed over `steps` steps.  Work per step (W x H = L0):
+    - k_smooth: 4 images x (3 B read + 8 B x S scales written) per pixel;
+    - k_features: 4 images x S scales x (8 B read + 48 B record + 4 B norm);
+    - k_iteration: 232 B per grid pixel per iteration, both fields;
+    - k_knn_tc: one pass of the coarsest grid's distance product, 2 fields x
+      2 x gq^2 x 64 bf16 FLOP (the kernel makes two passes by design);
+    - k_consistency: 26 B per pixel; the region filter (k_cc_*): 10 B per
+      pixel; the seeds (k_block_best, k_scan_chunks, k_write_seeds): 16 B per
+      pixel."""
+    S = params.num_scales
+    px = w * h
+    nq = (1 << (S - 1))
+    gq = ((w + nq - 1) // nq) * ((h + nq - 1) // nq)
+    work = {"k_smooth": ("hbm", 4.0 * px * (3 + 8 * S)),
+            "k_features": ("hbm", 4.0 * S * px * ALGO_BYTES["k_features"]),
+            "k_features_tc": ("hbm", 4.0 * S * px * ALGO_BYTES["k_features"]),
+            "k_iteration": ("hbm", ALGO_BYTES["k_iteration"] * _units("k_iteration", w, h, params)),
+            "k_knn_tc": ("tensor", 2.0 * 2.0 * gq * gq * 64),
+            "k_consistency": ("hbm", 26.0 * px)}
+    groups = {"region filter (k_cc_*)": (("k_cc_local", "k_cc_border", "k_cc_stats", "k_cc_remove"), 10.0 * px),
+              "seeds (k_block_best, k_scan_chunks, k_write_seeds)": (("k_block_best", "k_scan_chunks",
+                                                                       "k_write_seeds"), 16.0 * px)}
+    out, sol_ms = {}, 0.0
+    for k, (bound, amount) in work.items():
+        if k not in prof:
+            continue
+        ms = prof[k][1] / steps
+        peak = hbm_peak * 1e9 if bound == "hbm" else bf16_peak * 1e12
+        achieved = amount / (ms * 1e-3)
+        out[k] = {"bound": bound, "ms_per_step": ms, "achieved": achieved / (1e9 if bound == "hbm" else 1e12),
+                  "unit": "GB/s" if bound == "hbm" else "TFLOP/s", "frac": achieved / peak,
+                  "work_per_step": amount}
+        sol_ms += amount / peak * 1e3
+    for name, (ks, amount) in groups.items():
+        ms = sum(prof[k][1] for k in ks if k in prof) / steps
+        if ms <= 0:
+            continue
+        out[name] = {"bound": "hbm", "ms_per_step": ms, "achieved": amount / (ms * 1e-3) / 1e9, "unit": "GB/s",
+                     "frac": amount / (ms * 1e-3) / (hbm_peak * 1e9), "work_per_step": amount}
+        sol_ms += amount / (hbm_peak * 1e9) * 1e3
+    out["stage"] = {"speed_of_light_ms": sol_ms, "ms_per_step": per_step_ms, "frac": sol_ms / per_step_ms,
+                    "what": "sum over the kernels above of work / peak, over the measured step time (kernels "
+                            "without a work definition count as zero)"}
+    return out
 
 
 def merge_scales(prof):
@@ -804,6 +868,10 @@ def summary(line):
            "roofline_frac": (line.get("roofline") or {}).get("frac"),
            "per_scale_frac": [round(r["frac"], 3) for r in (line.get("roofline") or {}).get("per_scale", [])],
            "device_status": line.get("device_status"), "bit_exact": line.get("bit_exact")}
+    st = line.get("stage_rooflines")
+    if st:
+        out["stage_speed_of_light_frac"] = st["stage"]["frac"]
+        out["kernel_fracs"] = {k: round(v["frac"], 3) for k, v in st.items() if k not in ("stage", "peaks")}
     b = line.get("batched")
     if b:
         out.update(batched_mpx_s=b["value"] / 1e6, plain_per_quad_mpx_s=b["plain_value"] / 1e6,
@@ -1011,6 +1079,10 @@ def main():
     total_prof = sum(v[1] for v in prof.values())
     kernels = {k: {"launches_per_step": v[0] / prof_steps, "ms_per_step": v[1] / prof_steps,
                    "share": v[1] / total_prof} for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    bf16_peak, bf16_src = measured_peak_bf16()
+    stage_roof = stage_rooflines(prof, prof_steps, q.width, q.height, params, peak, bf16_peak, 1e3 * t_step)
+    stage_roof["peaks"] = {"hbm_gbs": peak, "hbm_source": peak_src, "bf16_tflops": bf16_peak,
+                           "bf16_source": bf16_src + " (burst)"}
 
     line = {"metric": METRIC, "value": value, "unit": "px/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_step, "higher_is_better": True, "scaling": "weak",
@@ -1023,7 +1095,7 @@ def main():
                        "pair_fields": tuning.pair_fields, "alternate_order_bits": tuning.alternate_order,
                        "pdl_bits": tuning.pdl, "fuse_bits": tuning.fuse, "tma": tuning.tma,
                        "features_form": args.features_form},
-            "roofline": roof, "gpu_launches": int(round(launches_per_step * args.steps)),
+            "roofline": roof, "stage_rooflines": stage_roof, "gpu_launches": int(round(launches_per_step * args.steps)),
             "e2e": e2e, "clocks": clk, "kernels": kernels, "seeds": n_seeds,
             "device_status": sff.lib().sff_status_string(dev_status).decode(), "device_timeouts": dev_timeouts}
     if not args.no_paper_order:
