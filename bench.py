@@ -76,9 +76,9 @@ def parse():
                     help="work distribution of the propagation kernels: 'auto' (autotune), L,TX,TY, or an "
                          "autotuner entry as JSON: {\"variants\": [4 x [lanes, slots, tile_x, tile_y, "
                          "min_ctas]], \"pair\": 0|1, \"alt\": bits, \"pdl\": bits, \"fuse\": bits}")
-    ap.add_argument("--features-form", default="butterfly", choices=["butterfly", "tensor"],
-                    help="WHT features of the timed stage: butterflies on the CUDA cores or the tensor-core "
-                         "form (identical features)")
+    ap.add_argument("--features-form", default="butterfly", choices=["butterfly", "tensor", "separable"],
+                    help="WHT features of the timed stage: butterflies on the CUDA cores, the tensor-core "
+                         "form, or separable butterflies through shared memory (identical features)")
     ap.add_argument("--tma", action="store_true",
                     help="scale 0 with TMA-staged reference records (sff_tuning.tma; the scale-0 variant must "
                          "have that form)")
@@ -961,7 +961,7 @@ def main():
         tuning = tune._tuning_of(json.loads(args.tuning))
     else:
         tuning = sff.make_tuning(*(int(v) for v in args.tuning.split(",")))
-    tuning.features_form = 1 if args.features_form == "tensor" else 0
+    tuning.features_form = {"butterfly": 0, "tensor": 1, "separable": 2}[args.features_form]
     if args.tma:
         tuning.tma = 1
         if not sff.lib().sff_tuning_supported(ctypes.byref(tuning)):

@@ -119,8 +119,8 @@ typedef struct sff_tuning {
                               * visits its tiles last-to-first, so that it starts on what the
                               * previous launch read last (still in L2); 0..15 */
     int32_t features_form;   /* transform of the whole-stage calls (sff_run_batch): 0 = butterflies
-                              * on the CUDA cores (sff_features), 1 = tensor cores (sff_features_tc);
-                              * identical features */
+                              * on the CUDA cores (sff_features), 1 = tensor cores (sff_features_tc),
+                              * 2 = separable butterflies (sff_features_sep); identical features */
     int32_t pdl;             /* bit s set (s = 0..3): the iteration launches of scale s use
                               * programmatic dependent launch: each is scheduled while the previous
                               * one's last CTAs run and waits in the kernel for its completion
@@ -202,6 +202,17 @@ int sff_features(const uint8_t* rgb_dev, int32_t width, int32_t height, int32_t 
 int sff_features_tc(const uint8_t* rgb_dev, int32_t width, int32_t height, int32_t pitch_bytes,
                     const sff_params* params, uint8_t* pyramid_dev,
                     void* workspace, size_t workspace_bytes, void* stream);
+
+/* sff_features with the transform separated: the 8-point Walsh-Hadamard
+ * transform of each smoothed row segment (an image row at the 8 sample
+ * columns of one pixel's patch) is computed once and shared, through shared
+ * memory, by the 8 pixels whose patches contain it; each pixel then
+ * transforms its 8 rows column-wise for the kept coefficients only.  Same
+ * arguments, same pyramid, bit for bit, as sff_features (Sec. 3.1,
+ * "Initialization"). */
+int sff_features_sep(const uint8_t* rgb_dev, int32_t width, int32_t height, int32_t pitch_bytes,
+                     const sff_params* params, uint8_t* pyramid_dev,
+                     void* workspace, size_t workspace_bytes, void* stream);
 
 /* One dense scene-flow field (Sec. 3.1, "Initialization" and "Multi-Scale
  * Propagation"; "Consistency Check" for the inverse field).

@@ -186,6 +186,8 @@ def lib():
         L.sff_features.restype = i32
         L.sff_features_tc.argtypes = [P, i32, i32, i32, PP, P, P, sz, P]
         L.sff_features_tc.restype = i32
+        L.sff_features_sep.argtypes = [P, i32, i32, i32, PP, P, P, sz, P]
+        L.sff_features_sep.restype = i32
         L.sff_match_views.argtypes = [P, P, P, P, i32, i32, i32, ctypes.c_uint64, PP, P, P, P, sz, P]
         L.sff_match_views.restype = i32
         L.sff_match_views_sequential.argtypes = [P, P, P, P, i32, i32, i32, ctypes.c_uint64, PP, P, P, P, sz, P]
@@ -324,11 +326,15 @@ def _pyramids(pyrs, width: int, height: int, params: Params, what: str):
     return [_buf(t, pb, f"{what} pyramid") for t in pyrs]
 
 
-def features(rgb, pyramid, workspace, params: Params = None, stream=None, tensor: bool = False) -> None:
-    """sff_features (tensor=True: sff_features_tc, same result) on a [H, W, 3]
-    uint8 CUDA tensor (rows may be padded)."""
+def features(rgb, pyramid, workspace, params: Params = None, stream=None, tensor: bool = False,
+             form: int = None) -> None:
+    """sff_features on a [H, W, 3] uint8 CUDA tensor (rows may be padded), in
+    the transform form `form` (0: sff_features, 1: sff_features_tc, 2:
+    sff_features_sep; all give the same pyramid); tensor=True is form 1."""
     params = params or default_params()
-    name = "sff_features_tc" if tensor else "sff_features"
+    if form is None:
+        form = 1 if tensor else 0
+    name = {0: "sff_features", 1: "sff_features_tc", 2: "sff_features_sep"}[int(form)]
     pitch = _image(rgb, name + " rgb")
     h, w = rgb.shape[0], rgb.shape[1]
     (pp,) = _pyramids([pyramid], w, h, params, name)
@@ -749,7 +755,7 @@ class QuadMatcher:
         ws = workspace_bytes(self.width, self.height, p)
         w = self.workspace[:ws]
         for img, pyr in zip((L0, R0, L1, R1), self.pyr):
-            features(img, pyr, w, p, stream, tensor=self.tuning.features_form == 1)
+            features(img, pyr, w, p, stream, form=self.tuning.features_form)
         pL0, pR0, pL1, pR1 = self.pyr
         match_quad_tuned(pL0, pR0, pL1, pR1, self.width, self.height, seed, self.tuning, self.fwd, self.fwd_cost,
                          self.inv, self.inv_cost, w, p, stream)

@@ -63,7 +63,9 @@ extern "C" int sff_run_batch(const sff_quad* quads, int32_t n, const sff_params*
             img[4 * k + j] = ImageJob{q.rgb[j], q.pitch_bytes, q.width, q.height,
                                       reinterpret_cast<uint32_t*>((char*)q.workspace + j * fw), q.pyramid[j]};
     }
-    int status = run_features(img, 4 * n, P, st, t.features_form ? kFeaturesTensor : kFeaturesButterfly);
+    static_assert(kFeaturesButterfly == 0 && kFeaturesTensor == 1 && kFeaturesSeparable == 2,
+                  "sff_tuning.features_form values");
+    int status = run_features(img, 4 * n, P, st, t.features_form);
     if (status) return status;
 
     // both fields of every quad (pyramids in the order L0, R0, L1, R1)

@@ -192,9 +192,10 @@ constexpr int kMaxImages = 4 * SFF_TABLE_QUADS;
 struct ImageJobs {
     ImageJob im[kMaxImages];
 };
-// Forms of the feature transform: butterflies on the CUDA cores, or the
-// kept coefficients as a matrix product on the tensor cores.
-constexpr int kFeaturesButterfly = 0, kFeaturesTensor = 1;
+// Forms of the feature transform: butterflies on the CUDA cores, the kept
+// coefficients as a matrix product on the tensor cores, or separable
+// butterflies with each row transform computed once per CTA in shared memory.
+constexpr int kFeaturesButterfly = 0, kFeaturesTensor = 1, kFeaturesSeparable = 2;
 int run_features(const ImageJob* jobs, int n, const sff_params& P, cudaStream_t st, int form = kFeaturesButterfly);
 
 // One quad of a consistency-filter / seeds launch (up to kMaxQuads).

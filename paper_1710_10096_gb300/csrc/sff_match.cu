@@ -1931,7 +1931,7 @@ int fused_capacity(const FusedVariant* v) {
 bool tuning_valid(const sff_tuning& t) {
     if (!find_variant(t.lanes_per_pixel, t.slots, t.tile_x, t.tile_y, t.min_ctas)) return false;
     if (t.group_mb < 0 || t.group_mb > (1 << 20) || (t.pair_fields != 0 && t.pair_fields != 1) ||
-        t.alternate_order < 0 || t.alternate_order > 15 || (t.features_form != 0 && t.features_form != 1) ||
+        t.alternate_order < 0 || t.alternate_order > 15 || t.features_form < 0 || t.features_form > 2 ||
         t.pdl < 0 || t.pdl > 15 || t.fuse < 0 || t.fuse > 15 || (t.fuse & 1) ||
         (t.fuse & (t.pdl | t.alternate_order)) != 0 || (t.tma != 0 && t.tma != 1))
         return false;

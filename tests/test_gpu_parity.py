@@ -76,6 +76,27 @@ def test_features_tensor_core_bit_exact(env, size, qshift):
     assert np.array_equal(gnorm, norm)
 
 
+@pytest.mark.parametrize("size", [(8, 8), (37, 23), (130, 70), (256, 80), (300, 9), (40, 410), (1242, 375)])
+@pytest.mark.parametrize("qshift", [4, 0])
+def test_features_separable_bit_exact(env, size, qshift):
+    # the separable form (sff_features_sep: row transforms shared through
+    # shared memory, tiles of 32 columns x 24 rows of one residue class mod n;
+    # 40 x 410 gives several tiles per residue at every scale): every record
+    # and norm equals the oracle's
+    torch, sff, orc = env
+    w, h = size
+    img = scenegen.random_images(w, h, seed=w * 1000 + h + 11, n=1)[0]
+    p = sff.default_params(quant_shift=qshift)
+    pyr = torch.empty(sff.pyramid_bytes(w, h, p), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(sff.workspace_bytes(w, h, p), dtype=torch.uint8, device="cuda")
+    sff.features(torch.as_tensor(img).cuda(), pyr, ws, p, form=2)
+    torch.cuda.synchronize()
+    gfeat, gnorm = (a.cpu().numpy() for a in sff.split_pyramid(pyr, w, h, p))
+    feat, norm = orc.features(img, _oparams(orc, p))
+    assert np.array_equal(gfeat, feat)
+    assert np.array_equal(gnorm, norm)
+
+
 def _match_both(env, imgs, p, seed):
     torch, sff, orc = env
     h, w, _ = imgs[0].shape
@@ -485,11 +506,13 @@ def test_batch_of_uneven_quads_equals_each_alone(env):
     # sweep schedules of scale 0: all quads in every launch, every quad alone
     # (a budget below any quad), about two quads per group, and each with the
     # two fields of a quad alternating tile by tile
-    # (and the features on the tensor cores; the iterations with programmatic
-    # dependent launch; scale 0 with TMA-staged reference records)
+    # (and the features on the tensor cores or in the separable form; the
+    # iterations with programmatic dependent launch; scale 0 with TMA-staged
+    # reference records)
     for group_mb, pair, alt, form, pdl, tma in ((0, 0, 0, 0, 0, 0), (1, 0, 0, 0, 0, 0), (4, 0, 0, 0, 0, 0),
                                                 (0, 1, 0, 0, 0, 0), (4, 1, 0, 1, 0, 0), (0, 0, 1, 0, 1, 0),
-                                                (4, 1, 1, 1, 1, 0), (0, 1, 1, 0, 1, 1), (4, 0, 0, 0, 0, 1)):
+                                                (4, 1, 1, 1, 1, 0), (0, 1, 1, 0, 1, 1), (4, 0, 0, 0, 0, 1),
+                                                (0, 1, 1, 2, 1, 0)):
         bm.tuning = sff.make_tuning(1, 32, 16, 0, None, group_mb, pair, 0, alt, form, pdl, tma=tma)
         bm.run([ms for _, ms in quads])
         torch.cuda.synchronize()

@@ -77,7 +77,7 @@ def test_variant_space_matches_the_library():
             sff.make_tuning(1, 32, 16, 0, [bad])
     assert len(sff.VARIANT_SPACE) == 45
     for bad_sched in [dict(group_mb=-1), dict(pair_fields=2), dict(alternate_order=16), dict(alternate_order=-1),
-                      dict(pdl=16), dict(features_form=2)]:
+                      dict(pdl=16), dict(features_form=3), dict(features_form=-1)]:
         with pytest.raises(sff.SffError):
             sff.make_tuning(1, 32, 16, 0, None, **bad_sched)
 
