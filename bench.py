@@ -76,9 +76,9 @@ def parse():
                     help="work distribution of the propagation kernels: 'auto' (autotune), L,TX,TY, or an "
                          "autotuner entry as JSON: {\"variants\": [4 x [lanes, slots, tile_x, tile_y, "
                          "min_ctas]], \"pair\": 0|1, \"alt\": bits, \"pdl\": bits, \"fuse\": bits}")
-    ap.add_argument("--features-form", default="butterfly", choices=["butterfly", "tensor", "separable"],
-                    help="WHT features of the timed stage: butterflies on the CUDA cores, the tensor-core "
-                         "form, or separable butterflies through shared memory (identical features)")
+    ap.add_argument("--features-form", default="separable", choices=["separable", "tensor", "pairs"],
+                    help="WHT features of the timed stage: separable butterflies through shared memory (the "
+                         "default), the tensor-core form, or butterflies per pixel pair (identical features)")
     ap.add_argument("--tma", action="store_true",
                     help="scale 0 with TMA-staged reference records (sff_tuning.tma; the scale-0 variant must "
                          "have that form)")
@@ -228,6 +228,7 @@ def stage_rooflines(prof, steps, w, h, params, hbm_peak, bf16_peak, per_step_ms)
     work = {"k_smooth": ("hbm", 4.0 * px * (3 + 8 * S)),
             "k_features": ("hbm", 4.0 * S * px * ALGO_BYTES["k_features"]),
             "k_features_tc": ("hbm", 4.0 * S * px * ALGO_BYTES["k_features"]),
+            "k_features_sep": ("hbm", 4.0 * S * px * ALGO_BYTES["k_features"]),
             "k_iteration": ("hbm", ALGO_BYTES["k_iteration"] * _units("k_iteration", w, h, params)),
             "k_knn_tc": ("tensor", 2.0 * 2.0 * gq * gq * 64),
             "k_consistency": ("hbm", 26.0 * px)}
@@ -961,7 +962,7 @@ def main():
         tuning = tune._tuning_of(json.loads(args.tuning))
     else:
         tuning = sff.make_tuning(*(int(v) for v in args.tuning.split(",")))
-    tuning.features_form = {"butterfly": 0, "tensor": 1, "separable": 2}[args.features_form]
+    tuning.features_form = {"separable": 0, "tensor": 1, "pairs": 2}[args.features_form]
     if args.tma:
         tuning.tma = 1
         if not sff.lib().sff_tuning_supported(ctypes.byref(tuning)):

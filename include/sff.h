@@ -118,9 +118,10 @@ typedef struct sff_tuning {
     int32_t alternate_order; /* bit s set (s = 0..3): at scale s every other iteration launch
                               * visits its tiles last-to-first, so that it starts on what the
                               * previous launch read last (still in L2); 0..15 */
-    int32_t features_form;   /* transform of the whole-stage calls (sff_run_batch): 0 = butterflies
-                              * on the CUDA cores (sff_features), 1 = tensor cores (sff_features_tc),
-                              * 2 = separable butterflies (sff_features_sep); identical features */
+    int32_t features_form;   /* transform of the whole-stage calls (sff_run_batch): 0 = separable
+                              * butterflies (sff_features), 1 = tensor cores (sff_features_tc),
+                              * 2 = butterflies per pixel pair (sff_features_pairs); identical
+                              * features */
     int32_t pdl;             /* bit s set (s = 0..3): the iteration launches of scale s use
                               * programmatic dependent launch: each is scheduled while the previous
                               * one's last CTAs run and waits in the kernel for its completion
@@ -184,6 +185,10 @@ size_t sff_workspace_bytes(int32_t width, int32_t height, const sff_params* para
  *   order; the 16 AC coefficients (ky, kx) with the lowest ky+kx (ties: lower
  *   ky) are kept per channel and quantised to clamp(floor(T / 2^quant_shift),
  *   -128, 127).
+ * Computed separably: the 8-point Walsh transform of each row segment (an
+ * image row at one patch's 8 sample columns) once, shared through shared
+ * memory by the 8 pixels whose patches contain it, then per pixel the column
+ * transforms of the kept coefficients only (integer sums, exact in any order).
  * rgb_dev: W x H x 3 uint8, rows pitch_bytes apart (pitch >= 3W).
  * pyramid_dev: sff_pyramid_bytes() bytes, 16-byte aligned; fully overwritten. */
 int sff_features(const uint8_t* rgb_dev, int32_t width, int32_t height, int32_t pitch_bytes,
@@ -203,16 +208,14 @@ int sff_features_tc(const uint8_t* rgb_dev, int32_t width, int32_t height, int32
                     const sff_params* params, uint8_t* pyramid_dev,
                     void* workspace, size_t workspace_bytes, void* stream);
 
-/* sff_features with the transform separated: the 8-point Walsh-Hadamard
- * transform of each smoothed row segment (an image row at the 8 sample
- * columns of one pixel's patch) is computed once and shared, through shared
- * memory, by the 8 pixels whose patches contain it; each pixel then
- * transforms its 8 rows column-wise for the kept coefficients only.  Same
- * arguments, same pyramid, bit for bit, as sff_features (Sec. 3.1,
- * "Initialization"). */
-int sff_features_sep(const uint8_t* rgb_dev, int32_t width, int32_t height, int32_t pitch_bytes,
-                     const sff_params* params, uint8_t* pyramid_dev,
-                     void* workspace, size_t workspace_bytes, void* stream);
+/* sff_features with the transform per pair of vertically adjacent pixels
+ * (x, y), (x, y + n): one thread computes the 9 row transforms of their two
+ * patches and folds each into both pixels' kept coefficients.  The earlier
+ * form, kept for comparison: same arguments, same pyramid, bit for bit, as
+ * sff_features (Sec. 3.1, "Initialization"). */
+int sff_features_pairs(const uint8_t* rgb_dev, int32_t width, int32_t height, int32_t pitch_bytes,
+                       const sff_params* params, uint8_t* pyramid_dev,
+                       void* workspace, size_t workspace_bytes, void* stream);
 
 /* One dense scene-flow field (Sec. 3.1, "Initialization" and "Multi-Scale
  * Propagation"; "Consistency Check" for the inverse field).

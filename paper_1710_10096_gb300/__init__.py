@@ -186,8 +186,8 @@ def lib():
         L.sff_features.restype = i32
         L.sff_features_tc.argtypes = [P, i32, i32, i32, PP, P, P, sz, P]
         L.sff_features_tc.restype = i32
-        L.sff_features_sep.argtypes = [P, i32, i32, i32, PP, P, P, sz, P]
-        L.sff_features_sep.restype = i32
+        L.sff_features_pairs.argtypes = [P, i32, i32, i32, PP, P, P, sz, P]
+        L.sff_features_pairs.restype = i32
         L.sff_match_views.argtypes = [P, P, P, P, i32, i32, i32, ctypes.c_uint64, PP, P, P, P, sz, P]
         L.sff_match_views.restype = i32
         L.sff_match_views_sequential.argtypes = [P, P, P, P, i32, i32, i32, ctypes.c_uint64, PP, P, P, P, sz, P]
@@ -329,12 +329,12 @@ def _pyramids(pyrs, width: int, height: int, params: Params, what: str):
 def features(rgb, pyramid, workspace, params: Params = None, stream=None, tensor: bool = False,
              form: int = None) -> None:
     """sff_features on a [H, W, 3] uint8 CUDA tensor (rows may be padded), in
-    the transform form `form` (0: sff_features, 1: sff_features_tc, 2:
-    sff_features_sep; all give the same pyramid); tensor=True is form 1."""
+    the transform form `form` (0: sff_features, separable; 1: sff_features_tc;
+    2: sff_features_pairs; all give the same pyramid); tensor=True is form 1."""
     params = params or default_params()
     if form is None:
         form = 1 if tensor else 0
-    name = {0: "sff_features", 1: "sff_features_tc", 2: "sff_features_sep"}[int(form)]
+    name = {0: "sff_features", 1: "sff_features_tc", 2: "sff_features_pairs"}[int(form)]
     pitch = _image(rgb, name + " rgb")
     h, w = rgb.shape[0], rgb.shape[1]
     (pp,) = _pyramids([pyramid], w, h, params, name)

@@ -63,7 +63,7 @@ extern "C" int sff_run_batch(const sff_quad* quads, int32_t n, const sff_params*
             img[4 * k + j] = ImageJob{q.rgb[j], q.pitch_bytes, q.width, q.height,
                                       reinterpret_cast<uint32_t*>((char*)q.workspace + j * fw), q.pyramid[j]};
     }
-    static_assert(kFeaturesButterfly == 0 && kFeaturesTensor == 1 && kFeaturesSeparable == 2,
+    static_assert(kFeaturesSeparable == 0 && kFeaturesTensor == 1 && kFeaturesPairs == 2,
                   "sff_tuning.features_form values");
     int status = run_features(img, 4 * n, P, st, t.features_form);
     if (status) return status;

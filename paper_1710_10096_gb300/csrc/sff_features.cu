@@ -241,31 +241,34 @@ __global__ void __launch_bounds__(128) k_features(const __grid_constant__ ImageJ
 }
 
 // ---------------------------------------------------------------------------
-// Separable form (k_features_sep, identical records).  The row transform of
-// image row yy at column x (the 8-point Walsh transform of the samples
-// yy, x + n (j - 3)) serves every pixel whose patch contains that row: the 8
-// pixels (x, yy - n (i - 3)).  A CTA takes kSepTX columns x kSepTY rows of
-// one residue class of rows mod n (rows r, r + n, r + 2n, ...): it first
-// computes the row transforms of the kSepTY + 7 rows those patches use once,
-// into shared memory (kept sequencies kx = 0..5 of R + 65536 G and of B),
-// then each pixel transforms its 8 patch rows column-wise with one 8-point
-// butterfly per kx, of which only the outputs of the kept (ky, kx) pairs are
-// used (the compiler drops the rest).  The sums are exact integers in any
-// order, so the records equal k_features's.
-constexpr int kSepTX = 32, kSepTY = 24, kSepRows = kSepTY + 7, kSepThreads = 256;
+// Separable form (k_features_sep, the default; identical records).  The row
+// transform of image row yy at column x (the 8-point Walsh transform of the
+// samples yy, x + n (j - 3)) serves every pixel whose patch contains that
+// row: the 8 pixels (x, yy - n (i - 3)).  A CTA takes kSepTX columns x kSepTY
+// rows of one residue class of rows mod n (rows r, r + n, r + 2n, ...): it
+// first computes the row transforms of the kSepTY + 7 rows those patches use
+// once, into shared memory (kept sequencies kx = 0..5 of R + 65536 G and of
+// B), then each thread takes two vertically adjacent pixels, which share 7
+// of their 9 rows, and transforms their rows column-wise with one 8-point
+// butterfly per kx and pixel, of which only the outputs of the kept (ky, kx)
+// pairs are used (the compiler drops the rest).  The sums are exact integers
+// in any order, so the records equal those of k_features (the pixel-pair
+// form above) bit for bit.
+constexpr int kSepTX = 32, kSepTY = 24, kSepRows = kSepTY + 7, kSepThreads = 192;
 
 // Index m of kept coefficient (ky, kx): diagonal t = ky + kx starts at t(t+1)/2 - 1.
 __host__ __device__ constexpr int kept_index(int ky, int kx) { return (ky + kx) * (ky + kx + 1) / 2 - 1 + ky; }
 static_assert(kept_index(0, 1) == 0 && kept_index(1, 0) == 1 && kept_index(4, 0) == 13 && kept_index(1, 4) == 15,
               "kept order");
-// Largest kept ky for sequency kx (the kept set is 1 <= ky + kx <= 4, plus (0, 5) and (1, 4)).
+// Kept ky range for sequency kx (the kept set is 1 <= ky + kx <= 4, plus (0, 5) and (1, 4)).
 __host__ __device__ constexpr int kept_ky_max(int kx) { return kx == 0 ? 4 : kx == 1 ? 3 : kx == 2 ? 2 : kx <= 4 ? 1 : 0; }
 __host__ __device__ constexpr int kept_ky_min(int kx) { return kx == 0 ? 1 : 0; }
 
 __global__ void __launch_bounds__(kSepThreads) k_features_sep(const __grid_constant__ ImageJobs J, int s, int S,
                                                               int qshift, int tiles_per_residue) {
-    // row transforms [row of the tile][column][kx 0..5 of R+65536G, then of B]
-    __shared__ __align__(16) int sR[kSepRows][kSepTX][12];
+    // row transforms [tile row][k][column], k = kx 0..5 of R + 65536 G, then
+    // of B: a warp's 32 columns of one (row, k) in one wavefront
+    __shared__ int sR[kSepRows][12][kSepTX];
     const ImageJob& job = J.im[blockIdx.z];
     const int w = job.w, h = job.h;
     const int n = 1 << s;
@@ -291,48 +294,54 @@ __global__ void __launch_bounds__(kSepThreads) k_features_sep(const __grid_const
         }
         fwht8(a);
         fwht8(b);
-        int4* d = reinterpret_cast<int4*>(&sR[t][lx][0]);
-        d[0] = make_int4(a[seq_to_nat(0)], a[seq_to_nat(1)], a[seq_to_nat(2)], a[seq_to_nat(3)]);
-        d[1] = make_int4(a[seq_to_nat(4)], a[seq_to_nat(5)], b[seq_to_nat(0)], b[seq_to_nat(1)]);
-        d[2] = make_int4(b[seq_to_nat(2)], b[seq_to_nat(3)], b[seq_to_nat(4)], b[seq_to_nat(5)]);
+#pragma unroll
+        for (int kx = 0; kx < 6; ++kx) {
+            sR[t][kx][lx] = a[seq_to_nat(kx)];
+            sR[t][6 + kx][lx] = b[seq_to_nat(kx)];
+        }
     }
     __syncthreads();
-    // phase 2: pixel (x0 + lx, r + n (m0 + ly)) takes tile rows ly .. ly + 7
+    // phase 2: the pixel pair (x0 + lx, r + n (m0 + ly)), ly = ly0, ly0 + 1,
+    // takes tile rows ly0 .. ly0 + 8 (pixel q its rows ly0 + q .. ly0 + q + 7)
     int4* feat = reinterpret_cast<int4*>(job.pyr + (size_t)s * np * kFeat);
     int* norms = reinterpret_cast<int*>(job.pyr + (size_t)S * np * kFeat) + (size_t)s * np;
     const size_t cs = chunk_planes(s) ? np : 1, rs = chunk_planes(s) ? 1 : 3;
-    for (int e = threadIdx.x; e < kSepTY * kSepTX; e += kSepThreads) {
-        const int ly = e / kSepTX, lx = e % kSepTX;
-        const int x = x0 + lx, m = m0 + ly;
+    for (int e = threadIdx.x; e < (kSepTY / 2) * kSepTX; e += kSepThreads) {
+        const int ly0 = 2 * (e / kSepTX), lx = e % kSepTX;
+        const int x = x0 + lx, m = m0 + ly0;
         if (x >= w || m >= rows_r) continue;
-        int v[8][12];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int4* src = reinterpret_cast<const int4*>(&sR[ly + i][lx][0]);
-            const int4 p0 = src[0], p1 = src[1], p2 = src[2];
-            v[i][0] = p0.x; v[i][1] = p0.y; v[i][2] = p0.z; v[i][3] = p0.w;
-            v[i][4] = p1.x; v[i][5] = p1.y; v[i][6] = p1.z; v[i][7] = p1.w;
-            v[i][8] = p2.x; v[i][9] = p2.y; v[i][10] = p2.z; v[i][11] = p2.w;
-        }
-        int arg[16], ab[16];
+        int arg[2][16], ab[2][16];
 #pragma unroll
         for (int kx = 0; kx < 6; ++kx) {
-            int c[8], d[8];
+            int c[9], d[9];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                c[i] = v[i][kx];
-                d[i] = v[i][6 + kx];
+            for (int i = 0; i < 9; ++i) {
+                c[i] = sR[ly0 + i][kx][lx];
+                d[i] = sR[ly0 + i][6 + kx][lx];
             }
-            fwht8(c);
-            fwht8(d);
 #pragma unroll
-            for (int ky = kept_ky_min(kx); ky <= kept_ky_max(kx); ++ky) {
-                arg[kept_index(ky, kx)] = c[seq_to_nat(ky)];
-                ab[kept_index(ky, kx)] = d[seq_to_nat(ky)];
+            for (int q = 0; q < 2; ++q) {
+                int cq[8], dq[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    cq[i] = c[q + i];
+                    dq[i] = d[q + i];
+                }
+                fwht8(cq);
+                fwht8(dq);
+#pragma unroll
+                for (int ky = kept_ky_min(kx); ky <= kept_ky_max(kx); ++ky) {
+                    arg[q][kept_index(ky, kx)] = cq[seq_to_nat(ky)];
+                    ab[q][kept_index(ky, kx)] = dq[seq_to_nat(ky)];
+                }
             }
         }
-        const size_t i = (size_t)(r + n * m) * w + x;
-        write_record(arg, ab, qshift, feat, cs, rs, i, norms + i);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            if (m + q >= rows_r) break;
+            const size_t i = (size_t)(r + n * (m + q)) * w + x;
+            write_record(arg[q], ab[q], qshift, feat, cs, rs, i, norms + i);
+        }
     }
 }
 
@@ -605,8 +614,7 @@ int features_status_read(cudaStream_t st, unsigned* out, bool reset) {
 }
 
 int run_features(const ImageJob* jobs, int n, const sff_params& P, cudaStream_t st, int form) {
-    if (n < 1 || n > kMaxImages ||
-        (form != kFeaturesButterfly && form != kFeaturesTensor && form != kFeaturesSeparable))
+    if (n < 1 || n > kMaxImages || (form != kFeaturesSeparable && form != kFeaturesTensor && form != kFeaturesPairs))
         return SFF_ERR_ARG;
     if (form == kFeaturesTensor && !features_tc_ready()) return SFF_ERR_CUDA;
     static ImageJobs J;  // host staging of the kernel parameter (copied at each launch)
@@ -662,7 +670,7 @@ extern "C" int sff_features(const uint8_t* rgb_dev, int32_t width, int32_t heigh
     return run_features(&job, 1, *params, (cudaStream_t)stream);
 }
 
-extern "C" int sff_features_sep(const uint8_t* rgb_dev, int32_t width, int32_t height, int32_t pitch_bytes,
+extern "C" int sff_features_pairs(const uint8_t* rgb_dev, int32_t width, int32_t height, int32_t pitch_bytes,
                                 const sff_params* params, uint8_t* pyramid_dev, void* workspace,
                                 size_t workspace_bytes, void* stream) {
     using namespace sff;
@@ -671,7 +679,7 @@ extern "C" int sff_features_sep(const uint8_t* rgb_dev, int32_t width, int32_t h
     if (((uintptr_t)pyramid_dev & 15) || ((uintptr_t)workspace & 255)) return SFF_ERR_ARG;
     if (workspace_bytes < features_ws_bytes(width, height, *params)) return SFF_ERR_WORKSPACE;
     ImageJob job{rgb_dev, pitch_bytes, width, height, (uint32_t*)workspace, pyramid_dev};
-    return run_features(&job, 1, *params, (cudaStream_t)stream, kFeaturesSeparable);
+    return run_features(&job, 1, *params, (cudaStream_t)stream, kFeaturesPairs);
 }
 
 extern "C" int sff_features_tc(const uint8_t* rgb_dev, int32_t width, int32_t height, int32_t pitch_bytes,

@@ -192,11 +192,12 @@ constexpr int kMaxImages = 4 * SFF_TABLE_QUADS;
 struct ImageJobs {
     ImageJob im[kMaxImages];
 };
-// Forms of the feature transform: butterflies on the CUDA cores, the kept
-// coefficients as a matrix product on the tensor cores, or separable
-// butterflies with each row transform computed once per CTA in shared memory.
-constexpr int kFeaturesButterfly = 0, kFeaturesTensor = 1, kFeaturesSeparable = 2;
-int run_features(const ImageJob* jobs, int n, const sff_params& P, cudaStream_t st, int form = kFeaturesButterfly);
+// Forms of the feature transform (sff_tuning.features_form): separable
+// butterflies with each row transform computed once per CTA in shared memory
+// (the default), the kept coefficients as a matrix product on the tensor
+// cores, or butterflies per pair of vertically adjacent pixels.
+constexpr int kFeaturesSeparable = 0, kFeaturesTensor = 1, kFeaturesPairs = 2;
+int run_features(const ImageJob* jobs, int n, const sff_params& P, cudaStream_t st, int form = kFeaturesSeparable);
 
 // One quad of a consistency-filter / seeds launch (up to kMaxQuads).
 struct FilterJob {

@@ -43,9 +43,12 @@ def _gpu_features(torch, sff, img, p):
     return pyr, (feat.cpu().numpy(), norm.cpu().numpy())
 
 
-@pytest.mark.parametrize("size", [(8, 8), (37, 23), (130, 70), (256, 80), (300, 9)])
+@pytest.mark.parametrize("size", [(8, 8), (37, 23), (130, 70), (256, 80), (300, 9), (40, 410), (1242, 375)])
 @pytest.mark.parametrize("qshift", [4, 0])
 def test_features_bit_exact(env, size, qshift):
+    # sff_features (the separable form: tiles of 32 columns x 24 rows of one
+    # residue class of rows mod n; 40 x 410 gives several tiles per residue at
+    # every scale, 8 x 8 a single partial tile)
     torch, sff, orc = env
     w, h = size
     img = scenegen.random_images(w, h, seed=w * 1000 + h, n=1)[0]
@@ -76,13 +79,12 @@ def test_features_tensor_core_bit_exact(env, size, qshift):
     assert np.array_equal(gnorm, norm)
 
 
-@pytest.mark.parametrize("size", [(8, 8), (37, 23), (130, 70), (256, 80), (300, 9), (40, 410), (1242, 375)])
+@pytest.mark.parametrize("size", [(8, 8), (37, 23), (130, 70), (256, 80), (300, 9), (1242, 375)])
 @pytest.mark.parametrize("qshift", [4, 0])
-def test_features_separable_bit_exact(env, size, qshift):
-    # the separable form (sff_features_sep: row transforms shared through
-    # shared memory, tiles of 32 columns x 24 rows of one residue class mod n;
-    # 40 x 410 gives several tiles per residue at every scale): every record
-    # and norm equals the oracle's
+def test_features_pixel_pairs_bit_exact(env, size, qshift):
+    # the earlier form (sff_features_pairs: one thread per vertical pixel
+    # pair, 9 row transforms folded into both): every record and norm equals
+    # the oracle's
     torch, sff, orc = env
     w, h = size
     img = scenegen.random_images(w, h, seed=w * 1000 + h + 11, n=1)[0]
