@@ -377,32 +377,37 @@ def _scene_driving(rng, W, H):
     surfs = []
     # ground plane y = +1.65 (y points down), extending far ahead
     surfs.append(_surface(rng, [0, 1.65, 60.0], [1, 0, 0], [0, 0, 1], 60.0, 58.0, 15.0, f, px_per_cell=6.0))
-    # far back wall ("sky" / buildings)
-    zb = 120.0
+    # far back wall ("sky" / distant buildings): disparities below 1 px
+    zb = 450.0
     surfs.append(_surface(rng, [0, -10.0, zb], [1, 0, 0], [0, 1, 0], zb * (W / 2 + 200) / f, zb * (H / 2 + 60) / f, zb, f))
     # side walls (building facades)
     for side in (-1, 1):
         x = side * (7.0 + 3.0 * rng.random())
         surfs.append(_surface(rng, [x, -2.0, 55.0], [0, 0, 1], [0, 1, 0], 50.0, 3.7, 20.0, f))
-    # a car parked on the left 3.05-3.25 m ahead: disparities up to ~127 px
-    # and flows beyond 100 px under the forward ego-motion
-    zc = 3.05 + 0.2 * rng.random()
+    # a car parked on the left 3.04-3.08 m ahead: disparities up to 128 px,
+    # and flows near -150 px under the forward ego-motion where its face
+    # stays inside all four frames
+    zc = 3.04 + 0.04 * rng.random()
     car = np.array([1.7, 1.4, 3.8])
-    for (c, a1, a2, e1, e2) in _box_faces(np.array([-(1.9 + 0.3 * rng.random()), 1.65 - 0.7, zc + car[2] / 2]),
+    for (c, a1, a2, e1, e2) in _box_faces(np.array([-(1.45 + 0.25 * rng.random()), 1.65 - 0.7, zc + car[2] / 2]),
                                           car, 0.0):
         surfs.append(_surface(rng, c, a1, a2, e1, e2, zc, f))
-    # boxes and planes
-    n_obj = 4
-    while n_obj < 16:
-        z = 5.0 + 45.0 * rng.random()
-        x = (rng.random() - 0.5) * 16.0
-        size = np.array([0.6 + 2.0 * rng.random(), 0.8 + 2.0 * rng.random(), 0.6 + 3.0 * rng.random()])
+    # static boxes: with the ground, the back wall, the two facades, the car
+    # and the three movers, 20 planes / boxes
+    n_obj = 0
+    while n_obj < 12:
+        z = 4.5 + 20.0 * rng.random()
+        x = (rng.random() - 0.5) * 12.0
+        if n_obj < 3:  # posts and signs: thin and tall
+            size = np.array([0.3 + 0.4 * rng.random(), 2.5 + 2.0 * rng.random(), 0.3 + 0.4 * rng.random()])
+        else:
+            size = np.array([0.6 + 2.0 * rng.random(), 0.8 + 2.0 * rng.random(), 0.6 + 3.0 * rng.random()])
         y = 1.65 - size[1] / 2
         if z - size[2] / 2 < 4.0:
             continue
         for (c, a1, a2, e1, e2) in _box_faces(np.array([x, y, z]), size, rng.normal() * 0.3):
             surfs.append(_surface(rng, c, a1, a2, e1, e2, z, f))
-        n_obj += 4
+        n_obj += 1
     # three independently moving boxes
     for _ in range(3):
         z = 7.0 + 20.0 * rng.random()
@@ -461,7 +466,7 @@ def _scene_movie(rng, W, H):
         t = _rand_unit(rng) * 0.25 * rng.random()
         surfs.append(_surface(rng, [x, y, z], a1, a2, e1, e2, z, f, R, t,
                               deform=_rbf_field(rng, amp=0.04 * z, sigma=0.5 * max(e1, e2))))
-    # two fast rigid movers (up to ~200 px)
+    # two fast rigid movers (105-155 px sideways before the camera's own motion)
     for _ in range(2):
         z = 3.0 + 4.0 * rng.random()
         x = (rng.random() - 0.5) * z * W / f * 0.5
@@ -469,7 +474,8 @@ def _scene_movie(rng, W, H):
         e1 = z * W / f * 0.08
         e2 = z * H / f * 0.12
         R = _rot(_rand_unit(rng), np.deg2rad(5.0) * rng.random())
-        t = np.array([(rng.random() - 0.5) * 2.0, (rng.random() - 0.5) * 0.8, -0.5 * rng.random()]) * z / f * 250
+        lateral = (0.42 + 0.2 * rng.random()) * (1 if rng.random() < 0.5 else -1)
+        t = np.array([lateral, (rng.random() - 0.5) * 0.8, -0.2 * rng.random()]) * z / f * 250
         surfs.append(_surface(rng, [x, y, z], [1, 0, 0], [0, 1, 0], e1, e2, z, f, R, t))
     cam0 = _Camera(C=np.zeros(3), R=np.eye(3), f=f, cx=(W - 1) / 2, cy=(H - 1) / 2, B=B)
     cam1 = _Camera(C=np.array([0.15, 0.0, 0.3]), R=_rot(np.array([0, 1.0, 0]), np.deg2rad(1.5)), f=f,
