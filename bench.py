@@ -79,6 +79,9 @@ def parse():
     ap.add_argument("--features-form", default="separable", choices=["separable", "tensor", "pairs"],
                     help="WHT features of the timed stage: separable butterflies through shared memory (the "
                          "default), the tensor-core form, or butterflies per pixel pair (identical features)")
+    ap.add_argument("--overlap", type=int, default=1, choices=[0, 1],
+                    help="sff_tuning.overlap: the finer scales' features on a second stream while the K-NN "
+                         "and the coarse scales match (1, the default) or every launch on one stream (0)")
     ap.add_argument("--tma", action="store_true",
                     help="scale 0 with TMA-staged reference records (sff_tuning.tma; the scale-0 variant must "
                          "have that form)")
@@ -218,9 +221,9 @@ def stage_rooflines(prof, steps, w, h, params, hbm_peak, bf16_peak, per_step_ms)
     - k_iteration: 232 B per grid pixel per iteration, both fields;
     - k_knn_tc: one pass of the coarsest grid's distance product, 2 fields x
       2 x gq^2 x 64 bf16 FLOP (the kernel makes two passes by design);
-    - k_consistency: 26 B per pixel; the region filter (k_cc_*): 10 B per
-      pixel; the seeds (k_block_best, k_scan_chunks, k_write_seeds): 16 B per
-      pixel."""
+    - the consistency check (26 B per pixel, in k_cc_local) and the region
+      filter (k_cc_*, 10 B per pixel); the seeds (k_block_best, k_scan_chunks,
+      k_write_seeds): 16 B per pixel."""
     S = params.num_scales
     px = w * h
     nq = (1 << (S - 1))
@@ -230,9 +233,9 @@ def stage_rooflines(prof, steps, w, h, params, hbm_peak, bf16_peak, per_step_ms)
             "k_features_tc": ("hbm", 4.0 * S * px * ALGO_BYTES["k_features"]),
             "k_features_sep": ("hbm", 4.0 * S * px * ALGO_BYTES["k_features"]),
             "k_iteration": ("hbm", ALGO_BYTES["k_iteration"] * _units("k_iteration", w, h, params)),
-            "k_knn_tc": ("tensor", 2.0 * 2.0 * gq * gq * 64),
-            "k_consistency": ("hbm", 26.0 * px)}
-    groups = {"region filter (k_cc_*)": (("k_cc_local", "k_cc_border", "k_cc_stats", "k_cc_remove"), 10.0 * px),
+            "k_knn_tc": ("tensor", 2.0 * 2.0 * gq * gq * 64)}
+    groups = {"consistency + region filter (k_cc_*)": (("k_cc_local", "k_cc_border", "k_cc_stats", "k_cc_remove"),
+                                                       36.0 * px),
               "seeds (k_block_best, k_scan_chunks, k_write_seeds)": (("k_block_best", "k_scan_chunks",
                                                                        "k_write_seeds"), 16.0 * px)}
     out, sol_ms = {}, 0.0
@@ -963,6 +966,7 @@ def main():
     else:
         tuning = sff.make_tuning(*(int(v) for v in args.tuning.split(",")))
     tuning.features_form = {"separable": 0, "tensor": 1, "pairs": 2}[args.features_form]
+    tuning.overlap = args.overlap
     if args.tma:
         tuning.tma = 1
         if not sff.lib().sff_tuning_supported(ctypes.byref(tuning)):
@@ -970,7 +974,8 @@ def main():
     # the batch and the server take the tuned scale-0 variant with the coarse
     # scales derived from their (much larger) launch sizes
     batch_tuning = sff.make_tuning(tuning.lanes_per_pixel, tuning.tile_x, tuning.tile_y, tuning.slots, None, 0,
-                                   tuning.pair_fields, tuning.min_ctas, tuning.alternate_order & 1)
+                                   tuning.pair_fields, tuning.min_ctas, tuning.alternate_order & 1,
+                                   overlap=args.overlap)
     m = sff.QuadMatcher(q.width, q.height, params, device=dev, tuning=tuning)
     stream = torch.cuda.Stream(device=dev)
     host_in = torch.empty((4, q.height, q.width, 3), dtype=torch.uint8).pin_memory()
@@ -1095,7 +1100,7 @@ def main():
                                         "scales 0..3",
                        "pair_fields": tuning.pair_fields, "alternate_order_bits": tuning.alternate_order,
                        "pdl_bits": tuning.pdl, "fuse_bits": tuning.fuse, "tma": tuning.tma,
-                       "features_form": args.features_form},
+                       "overlap": tuning.overlap, "features_form": args.features_form},
             "roofline": roof, "stage_rooflines": stage_roof, "gpu_launches": int(round(launches_per_step * args.steps)),
             "e2e": e2e, "clocks": clk, "kernels": kernels, "seeds": n_seeds,
             "device_status": sff.lib().sff_status_string(dev_status).decode(), "device_timeouts": dev_timeouts}

@@ -144,6 +144,14 @@ typedef struct sff_tuning {
                               * copy (TMA) instead of per-thread loads (same results); the
                               * scale-0 variant must be (1, 0, 32x16 or 32x8) with min_ctas
                               * 0, or 32x16 with 3, or 32x8 with 7; 0 or 1 */
+    int32_t overlap;         /* 1: in sff_run_batch, the features of the scales below the
+                              * coarsest are computed on a second stream of the library (one
+                              * per device and caller stream), forked once the coarsest grid
+                              * is gathered, while the K-NN and the coarse scales match; each
+                              * scale's inheritance waits for its features.  0: every launch
+                              * on the caller's stream.  Same results; under stream capture
+                              * the second stream forks from and joins back into the captured
+                              * stream.  0 or 1 */
 } sff_tuning;
 
 /* One seed of Sec. 3.2: pixel (x, y) of L0, its vector and its scores. 20 bytes.

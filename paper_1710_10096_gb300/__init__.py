@@ -62,7 +62,7 @@ class Tuning(ctypes.Structure):
                 ("slots", ctypes.c_int32), ("min_ctas", ctypes.c_int32), ("coarse", (ctypes.c_int32 * 5) * 3),
                 ("group_mb", ctypes.c_int32), ("pair_fields", ctypes.c_int32), ("alternate_order", ctypes.c_int32),
                 ("features_form", ctypes.c_int32), ("pdl", ctypes.c_int32), ("fuse", ctypes.c_int32),
-                ("tma", ctypes.c_int32)]
+                ("tma", ctypes.c_int32), ("overlap", ctypes.c_int32)]
 
     def as_tuple(self):
         """(lanes, tile_x, tile_y) of scale 0 (the throughput-form space)."""
@@ -388,13 +388,14 @@ def default_tuning() -> Tuning:
 
 def make_tuning(lanes: int, tile_x: int, tile_y: int, slots: int = 0, coarse=None, group_mb: int = 0,
                 pair_fields: int = 0, min_ctas: int = 0, alternate_order: int = 0, features_form: int = 0,
-                pdl: int = 0, fuse: int = 0, tma: int = 0) -> Tuning:
+                pdl: int = 0, fuse: int = 0, tma: int = 0, overlap: int = 1) -> Tuning:
     """sff_tuning: scale 0 (lanes, slots, tile, min_ctas); coarse = [(lanes, slots, tile_x,
     tile_y[, min_ctas])] for scales 1.. (None or all-zero entries: derived from the grid
     size); group_mb: the batch's scale-0 sweep schedule (0: all quads in every launch);
     pair_fields: a quad's two fields alternate tile by tile in each launch; alternate_order,
     pdl, fuse: per-scale bits of the launch schedule; tma: scale-0 reference records staged by
-    tensor copies (see sff_tuning)."""
+    tensor copies; overlap: the finer scales' features on a second stream while the coarse
+    scales match (see sff_tuning)."""
     t = Tuning(lanes, tile_x, tile_y, slots, min_ctas)
     t.group_mb = int(group_mb)
     t.pair_fields = int(pair_fields)
@@ -403,6 +404,7 @@ def make_tuning(lanes: int, tile_x: int, tile_y: int, slots: int = 0, coarse=Non
     t.pdl = int(pdl)
     t.fuse = int(fuse)
     t.tma = int(tma)
+    t.overlap = int(overlap)
     for k, v in enumerate(coarse or []):
         v = tuple(v) + (0,) * (5 - len(v))
         for j in range(5):

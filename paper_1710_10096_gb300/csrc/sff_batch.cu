@@ -5,19 +5,60 @@
 // hold the whole batch.  Every quad's outputs are identical to running the
 // four calls on it alone.
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "sff_internal.cuh"
 
 namespace sff {
 
-// Per-quad scratch: the phases run one after the other, so they share it.
+// Per-quad scratch: the smoothed images of the four views (read by the
+// features of every scale), then the two fields' scratch, which the features
+// of the finer scales may still be reading from the first part; the filter
+// and the seeds, which run after both, reuse the start.
 size_t quad_ws_bytes(int w, int h, const sff_params& p) {
-    size_t b = 4 * features_ws_bytes(w, h, p);  // the four images are smoothed in one launch
-    b = std::max(b, 2 * field_ws_bytes(w, h, p));
+    size_t b = 4 * features_ws_bytes(w, h, p) + 2 * field_ws_bytes(w, h, p);
     b = std::max(b, filter_ws_bytes(w, h));
     b = std::max(b, seeds_ws_bytes(w, h));
     return b;
 }
+
+namespace {
+
+// The second stream of the feature overlap and its events, one set per
+// (device, caller stream), created at the first call on that pair and kept
+// until exit.  Calls on one caller stream are issued in host order, so they
+// may reuse the set.
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t ready[SFF_MAX_SCALES] = {};
+};
+
+std::mutex g_side_mu;
+std::map<std::pair<int, cudaStream_t>, SideStream> g_side;
+
+// The set of the current device and `st`, or nullptr when it cannot be made.
+const SideStream* side_stream(cudaStream_t st) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(g_side_mu);
+    auto it = g_side.find({dev, st});
+    if (it != g_side.end()) return &it->second;
+    SideStream ss;
+    bool ok = cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; ok && k < SFF_MAX_SCALES; ++k)
+        ok = cudaEventCreateWithFlags(&ss.ready[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return &g_side.emplace(std::make_pair(dev, st), ss).first->second;
+}
+
+}  // namespace
 
 }  // namespace sff
 
@@ -65,21 +106,59 @@ extern "C" int sff_run_batch(const sff_quad* quads, int32_t n, const sff_params*
     }
     static_assert(kFeaturesSeparable == 0 && kFeaturesTensor == 1 && kFeaturesPairs == 2,
                   "sff_tuning.features_form values");
-    int status = run_features(img, 4 * n, P, st, t.features_form);
+    // With the overlap, the stream computes the coarsest scale's features
+    // (the K-NN and the first iterations read only those) and gathers the
+    // coarsest grid; then the finer scales' features run on the second
+    // stream, coarse to fine, one event per scale, beside the K-NN (which
+    // leaves SMs idle), the initialisation and the coarse iterations.  The
+    // inheritance into scale s waits for event s, and the wait on the finest
+    // scale's event joins the two streams again.  (Forked before the grid is
+    // gathered instead, the step took the same time: the features' CTAs then
+    // delayed the gathering rather than the K-NN.)
+    const int S = P.num_scales;
+    const SideStream* side = t.overlap && S > 1 ? side_stream(st) : nullptr;
+    int status = side ? run_features(img, 4 * n, P, st, t.features_form, true, S - 1, S - 1)
+                      : run_features(img, 4 * n, P, st, t.features_form);
     if (status) return status;
+    struct Fork {
+        const SideStream* side;
+        const ImageJob* img;
+        int n_img;
+        const sff_params* P;
+        int form;
+        bool forked;
+    } fork{side, img, 4 * n, &P, t.features_form, false};
+    // every event is recorded even after a failed launch, so that the
+    // caller's stream always joins the second one (a capture stays whole)
+    auto fork_fn = [](void* ctx, cudaStream_t main) -> int {
+        Fork& f = *static_cast<Fork*>(ctx);
+        if (cudaEventRecord(f.side->fork, main) != cudaSuccess ||
+            cudaStreamWaitEvent(f.side->s, f.side->fork, 0) != cudaSuccess)
+            return SFF_ERR_CUDA;
+        f.forked = true;
+        int status = SFF_OK;
+        for (int s = f.P->num_scales - 2; s >= 0; --s) {
+            const int st_s = run_features(f.img, f.n_img, *f.P, f.side->s, f.form, false, s, s);
+            if (!status) status = st_s;
+            if (cudaEventRecord(f.side->ready[s], f.side->s) != cudaSuccess && !status) status = SFF_ERR_CUDA;
+        }
+        return status;
+    };
+    const ForkHook hook{fork_fn, &fork};
 
     // both fields of every quad (pyramids in the order L0, R0, L1, R1)
     FieldSpec fs[kMaxBatchFields];
     for (int k = 0; k < n; ++k) {
         const sff_quad& q = quads[k];
-        char* ws = reinterpret_cast<char*>(q.workspace);
+        char* ws = reinterpret_cast<char*>(q.workspace) + 4 * features_ws_bytes(q.width, q.height, P);
         const size_t half = field_ws_bytes(q.width, q.height, P);
         fs[2 * k] = FieldSpec{q.pyramid[0], q.pyramid[2], q.pyramid[1], q.pyramid[3], q.fwd, q.fwd_cost, 0,
                               q.width,      q.height,     q.seed,       ws};
         fs[2 * k + 1] = FieldSpec{q.pyramid[3], q.pyramid[1], q.pyramid[2], q.pyramid[0], q.inv, q.inv_cost, 1,
                                   q.width,      q.height,     q.seed,       ws + half};
     }
-    status = run_fields(fs, 2 * n, P, t, st, false);
+    status = run_fields(fs, 2 * n, P, t, st, false, side ? side->ready : nullptr, side ? &hook : nullptr);
+    if (fork.forked) cudaStreamWaitEvent(st, side->ready[0], 0);  // joined already, unless run_fields failed early
     if (status) return status;
 
     // consistency + region filter, then seeds

@@ -613,9 +613,12 @@ int features_status_read(cudaStream_t st, unsigned* out, bool reset) {
     return SFF_OK;
 }
 
-int run_features(const ImageJob* jobs, int n, const sff_params& P, cudaStream_t st, int form) {
+int run_features(const ImageJob* jobs, int n, const sff_params& P, cudaStream_t st, int form, bool smooth, int s_lo,
+                 int s_hi) {
     if (n < 1 || n > kMaxImages || (form != kFeaturesSeparable && form != kFeaturesTensor && form != kFeaturesPairs))
         return SFF_ERR_ARG;
+    if (s_hi < 0) s_hi = P.num_scales - 1;
+    if (s_lo < 0 || s_hi >= P.num_scales) return SFF_ERR_ARG;
     if (form == kFeaturesTensor && !features_tc_ready()) return SFF_ERR_CUDA;
     static ImageJobs J;  // host staging of the kernel parameter (copied at each launch)
     static std::mutex mu;
@@ -627,8 +630,8 @@ int run_features(const ImageJob* jobs, int n, const sff_params& P, cudaStream_t 
         mh = mh > jobs[k].h ? mh : jobs[k].h;
     }
     dim3 gs((mw + kSmX - 1) / kSmX, (mh + kSmY - 1) / kSmY, n);
-    SFF_LAUNCH(k_smooth, gs, 256, 0, st, J, P.num_scales);
-    for (int s = 0; s < P.num_scales; ++s) {
+    if (smooth) SFF_LAUNCH(k_smooth, gs, 256, 0, st, J, P.num_scales);
+    for (int s = s_lo; s <= s_hi; ++s) {
         const int nn = 1 << s;
         if (form == kFeaturesTensor) {
             // (segment, residue, tile column) items of the largest image

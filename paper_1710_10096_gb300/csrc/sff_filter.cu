@@ -1,8 +1,9 @@
 // Consistency check and region filter (Sec. 3.1, "Consistency Check").
 //
-// k_consistency: per L0 pixel, gather the inverse vector at its cross match
+// Consistency: per L0 pixel, gather the inverse vector at its cross match
 //                in R1 and compare the round trip of all three
-//                correspondences.
+//                correspondences (consistency_at, run by k_cc_local for the
+//                pixels of its tile).
 // Region filter: connected components of kept pixels (4-neighbours whose
 //                vectors differ by at most tau_r) by union-find, first inside
 //                32x32 tiles in shared memory (k_cc_local), then across tile
@@ -25,11 +26,9 @@ struct FilterJobs {
     FilterJob q[kMaxQuads];
 };
 
-__global__ void k_consistency(const __grid_constant__ FilterJobs J, int tau_c) {
-    const FilterJob& Q = J.q[blockIdx.z];
+// Consistency of pixel (x, y): writes keep and cerr, returns keep.
+__device__ __forceinline__ bool consistency_at(const FilterJob& Q, int x, int y, int tau_c) {
     const int w = Q.w, h = Q.h;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    if (x >= w || y >= h) return;
     const size_t i = (size_t)y * w + x;
     uint8_t k = 0, e = 255;
     if (Q.fcost[i] != kEmpty) {
@@ -49,6 +48,7 @@ __global__ void k_consistency(const __grid_constant__ FilterJobs J, int tau_c) {
     }
     Q.keep[i] = k;
     Q.cerr[i] = e;
+    return k != 0;
 }
 
 __device__ __forceinline__ bool close_vec(uint2 a, uint2 b, int tau) {
@@ -123,11 +123,13 @@ __device__ void unite_local(int* lp, int a, int b) {
 // raster index of a local component has no connected upper or left
 // neighbour, starts as a root and stays one, since links always go to the
 // smaller root: every kept pixel's parent becomes that minimum.  Also clears
-// size and joinable for the tile's pixels.
+// size and joinable for the tile's pixels.  The tile's keep and cerr are
+// computed first, by the consistency check of each of its pixels.
 constexpr int kLocalThreads = 256;
 constexpr int kPerThread = kTile * kTile / kLocalThreads;
 
-__global__ void __launch_bounds__(kLocalThreads) k_cc_local(const __grid_constant__ FilterJobs J, int tau_r) {
+__global__ void __launch_bounds__(kLocalThreads) k_cc_local(const __grid_constant__ FilterJobs J, int tau_r,
+                                                            int tau_c) {
     __shared__ int lp[kTile * kTile];
     __shared__ uint2 lf[kTile * kTile];
     __shared__ uint8_t lk[kTile * kTile];
@@ -141,7 +143,7 @@ __global__ void __launch_bounds__(kLocalThreads) k_cc_local(const __grid_constan
         const int x = x0 + (k % kTile), y = y0 + (k / kTile);
         const bool inside = x < w && y < h;
         const size_t i = (size_t)y * w + x;
-        const bool kk = inside && Q.keep[i];
+        const bool kk = inside && consistency_at(Q, x, y, tau_c);
         lk[k] = kk;
         lf[k] = kk ? Q.fwd[i] : make_uint2(0u, 0u);
         if (inside) {
@@ -182,20 +184,30 @@ __global__ void __launch_bounds__(kLocalThreads) k_cc_local(const __grid_constan
     }
 }
 
-// Unions across tile borders only (right column and bottom row of each tile).
+// Unions across tile borders only: one thread per pixel pair that a tile
+// border separates, first the (x, x + 1) pairs of every vertical border
+// (x = 31, 63, ...; all rows), then the (y, y + 1) pairs of every
+// horizontal border (all columns).  The unions are the same whatever their
+// order, and so is every root (the minimum raster index).
 __global__ void k_cc_border(const __grid_constant__ FilterJobs J, int tau_r) {
     const FilterJob& Q = J.q[blockIdx.z];
     const int w = Q.w, h = Q.h;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    if (x >= w || y >= h) return;
-    const bool right = (x % kTile) == kTile - 1 && x + 1 < w;
-    const bool down = (y % kTile) == kTile - 1 && y + 1 < h;
-    if (!right && !down) return;
-    const int i = y * w + x;
-    if (!Q.keep[i]) return;
-    const uint2 a = Q.fwd[i];
-    if (right && Q.keep[i + 1] && close_vec(a, Q.fwd[i + 1], tau_r)) unite(Q.parent, i, i + 1);
-    if (down && Q.keep[i + w] && close_vec(a, Q.fwd[i + w], tau_r)) unite(Q.parent, i, i + w);
+    const int nv = (w - 1) / kTile, nh = (h - 1) / kTile;  // borders with a pixel on both sides
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int i, j;
+    if (t < (long long)nv * h) {
+        const int y = (int)(t / nv), x = ((int)(t % nv) + 1) * kTile - 1;
+        i = y * w + x;
+        j = i + 1;
+    } else if (t < (long long)nv * h + (long long)nh * w) {
+        const long long u = t - (long long)nv * h;
+        const int y = ((int)(u / w) + 1) * kTile - 1, x = (int)(u % w);
+        i = y * w + x;
+        j = i + w;
+    } else {
+        return;
+    }
+    if (Q.keep[i] && Q.keep[j] && close_vec(Q.fwd[i], Q.fwd[j], tau_r)) unite(Q.parent, i, j);
 }
 
 // Root of every kept pixel (written back to parent), component sizes with
@@ -261,9 +273,14 @@ int run_filter(const FilterJob* jobs, int n, const sff_params& P, cudaStream_t s
     }
     dim3 b2(128), g2((mw + 127) / 128, mh, n);
     dim3 gt((mw + kTile - 1) / kTile, (mh + kTile - 1) / kTile, n);
-    SFF_LAUNCH(k_consistency, g2, b2, 0, st, J, P.tau_c);
-    SFF_LAUNCH(k_cc_local, gt, 256, 0, st, J, P.tau_r);
-    SFF_LAUNCH(k_cc_border, g2, b2, 0, st, J, P.tau_r);
+    // border pairs of the largest quad
+    long long pairs = 0;
+    for (int k = 0; k < n; ++k) {
+        const long long p = (long long)((jobs[k].w - 1) / kTile) * jobs[k].h + (long long)((jobs[k].h - 1) / kTile) * jobs[k].w;
+        pairs = pairs > p ? pairs : p;
+    }
+    SFF_LAUNCH(k_cc_local, gt, 256, 0, st, J, P.tau_r, P.tau_c);
+    if (pairs > 0) SFF_LAUNCH(k_cc_border, dim3((unsigned)((pairs + 127) / 128), 1, n), b2, 0, st, J, P.tau_r);
     SFF_LAUNCH(k_cc_stats, g2, b2, 0, st, J, P.tau_r);
     SFF_LAUNCH(k_cc_remove, g2, b2, 0, st, J, P.region_min);
     return launch_status();

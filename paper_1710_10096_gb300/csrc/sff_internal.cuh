@@ -197,7 +197,10 @@ struct ImageJobs {
 // (the default), the kept coefficients as a matrix product on the tensor
 // cores, or butterflies per pair of vertically adjacent pixels.
 constexpr int kFeaturesSeparable = 0, kFeaturesTensor = 1, kFeaturesPairs = 2;
-int run_features(const ImageJob* jobs, int n, const sff_params& P, cudaStream_t st, int form = kFeaturesSeparable);
+// Smooths the images (smooth = true) and computes the records of scales
+// s_lo..s_hi (s_hi < 0: the last scale).
+int run_features(const ImageJob* jobs, int n, const sff_params& P, cudaStream_t st, int form = kFeaturesSeparable,
+                 bool smooth = true, int s_lo = 0, int s_hi = -1);
 
 // One quad of a consistency-filter / seeds launch (up to kMaxQuads).
 struct FilterJob {
@@ -232,8 +235,18 @@ int run_seeds(const SeedJob* jobs, int n, cudaStream_t st);
 void filter_carve(void* workspace, int w, int h, int** parent, int** size, int** joinable);
 void seeds_carve(void* workspace, int w, int h, int** best, int** chunk);
 size_t field_ws_bytes(int w, int h, const sff_params& p);
+// Work issued by the caller of run_fields once the coarsest grid is
+// gathered, right before the K-NN launch (fn(ctx, stream); a nonzero status
+// ends run_fields with it).
+struct ForkHook {
+    int (*fn)(void* ctx, cudaStream_t st);
+    void* ctx;
+};
+
+// scale_ready (optional): per scale s < num_scales - 1, an event that the
+// stream waits on before the first launch that reads scale s's records.
 int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tuning& T, cudaStream_t st,
-               bool sequential);
+               bool sequential, const cudaEvent_t* scale_ready = nullptr, const ForkHook* fork_hook = nullptr);
 
 // Optional per-kernel event timing (sff_profile_enable).  SFF_LAUNCH wraps
 // every kernel launch of the library; a mark pair may also span `launches`

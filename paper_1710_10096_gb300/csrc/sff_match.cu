@@ -1933,7 +1933,8 @@ bool tuning_valid(const sff_tuning& t) {
     if (t.group_mb < 0 || t.group_mb > (1 << 20) || (t.pair_fields != 0 && t.pair_fields != 1) ||
         t.alternate_order < 0 || t.alternate_order > 15 || t.features_form < 0 || t.features_form > 2 ||
         t.pdl < 0 || t.pdl > 15 || t.fuse < 0 || t.fuse > 15 || (t.fuse & 1) ||
-        (t.fuse & (t.pdl | t.alternate_order)) != 0 || (t.tma != 0 && t.tma != 1))
+        (t.fuse & (t.pdl | t.alternate_order)) != 0 || (t.tma != 0 && t.tma != 1) ||
+        (t.overlap != 0 && t.overlap != 1))
         return false;
     if (t.tma && !find_tma(t.lanes_per_pixel, t.slots, t.tile_x, t.tile_y, t.min_ctas)) return false;
     for (int k = 0; k < SFF_MAX_SCALES - 1; ++k) {
@@ -2018,7 +2019,7 @@ bool knn_smem_ready() {
 // The stage of Sec. 3.1 for nf <= kMaxFields fields (any sizes) sharing the
 // launches.  spec[k].workspace holds field_ws_bytes() of scratch.
 int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tuning& T, cudaStream_t st,
-               bool sequential) {
+               bool sequential, const cudaEvent_t* scale_ready, const ForkHook* fork_hook) {
     if (!tuning_valid(T) || nf < 1 || nf > kMaxFields) return SFF_ERR_ARG;
     const int S = P.num_scales, I = P.iterations;
     static const int kDirs[4][2] = {{1, 1}, {-1, -1}, {1, -1}, {-1, 1}};
@@ -2099,11 +2100,17 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
             dim3 g0((tc_rows(mgq) * 8 + 255) / 256, 4, nf);
             SFF_LAUNCH(k_gather_grid, g0, 256, 0, st, F, n);
             if (!knn_smem_ready()) return SFF_ERR_CUDA;
+            if (fork_hook) {
+                const int status = fork_hook->fn(fork_hook->ctx, st);
+                if (status) return status;
+            }
             dim3 g1((mgq + kTcRows - 1) / kTcRows, 1, nf);
             SFF_LAUNCH(k_knn_tc, g1, kTcThreads, kTcSmemBytes, st, F);
             dim3 g2((mgq + 7) / 8, 1, nf);
             SFF_LAUNCH(k_init_select, g2, 256, 0, st, F, n, P.knn_temporal);
         } else {
+            // the features of this scale may still be in flight on another stream
+            if (scale_ready && cudaStreamWaitEvent(st, scale_ready[s], 0) != cudaSuccess) return SFF_ERR_CUDA;
             dim3 g((mgw + 127) / 128, mgh, nf);
             SFF_LAUNCH(k_inherit, g, 128, 0, st, F, n);
         }
@@ -2361,6 +2368,7 @@ extern "C" int sff_default_tuning(sff_tuning* out) {
     out->lanes_per_pixel = 1;
     out->tile_x = 32;
     out->tile_y = 16;
+    out->overlap = 1;
     return SFF_OK;
 }
 

@@ -31,11 +31,12 @@ def size_bucket(width: int, height: int) -> str:
 
 def _tuning_of(entry) -> Tuning:
     """Tuning of a cache entry: {"variants": [4 x (lanes, slots, tile_x, tile_y, min_ctas)],
-    "pair": 0 | 1, "alt": scale bits, "pdl": scale bits, "fuse": scale bits, "tma": 0 | 1}."""
+    "pair": 0 | 1, "alt": scale bits, "pdl": scale bits, "fuse": scale bits, "tma": 0 | 1,
+    "overlap": 0 | 1 (absent: 1)}."""
     vs = entry["variants"]
     l, c, tx, ty, mb = vs[0]
     return make_tuning(l, tx, ty, c, vs[1:], 0, entry["pair"], mb, entry["alt"], 0, entry.get("pdl", 0),
-                       entry.get("fuse", 0), entry.get("tma", 0))
+                       entry.get("fuse", 0), entry.get("tma", 0), entry.get("overlap", 1))
 
 
 def scale_times(pyramids, width: int, height: int, tuning: Tuning, params=None, reps: int = 3, stream=None) -> dict:

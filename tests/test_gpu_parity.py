@@ -510,16 +510,19 @@ def test_batch_of_uneven_quads_equals_each_alone(env):
     # two fields of a quad alternating tile by tile
     # (and the features on the tensor cores or in the separable form; the
     # iterations with programmatic dependent launch; scale 0 with TMA-staged
-    # reference records)
-    for group_mb, pair, alt, form, pdl, tma in ((0, 0, 0, 0, 0, 0), (1, 0, 0, 0, 0, 0), (4, 0, 0, 0, 0, 0),
-                                                (0, 1, 0, 0, 0, 0), (4, 1, 0, 1, 0, 0), (0, 0, 1, 0, 1, 0),
-                                                (4, 1, 1, 1, 1, 0), (0, 1, 1, 0, 1, 1), (4, 0, 0, 0, 0, 1),
-                                                (0, 1, 1, 2, 1, 0)):
-        bm.tuning = sff.make_tuning(1, 32, 16, 0, None, group_mb, pair, 0, alt, form, pdl, tma=tma)
+    # reference records; the finer scales' features on the second stream or
+    # on the caller's)
+    for group_mb, pair, alt, form, pdl, tma, ov in ((0, 0, 0, 0, 0, 0, 1), (1, 0, 0, 0, 0, 0, 1),
+                                                    (4, 0, 0, 0, 0, 0, 0), (0, 1, 0, 0, 0, 0, 0),
+                                                    (4, 1, 0, 1, 0, 0, 1), (0, 0, 1, 0, 1, 0, 1),
+                                                    (4, 1, 1, 1, 1, 0, 0), (0, 1, 1, 0, 1, 1, 1),
+                                                    (4, 0, 0, 0, 0, 1, 1), (0, 1, 1, 2, 1, 0, 1),
+                                                    (0, 1, 1, 2, 1, 0, 0)):
+        bm.tuning = sff.make_tuning(1, 32, 16, 0, None, group_mb, pair, 0, alt, form, pdl, tma=tma, overlap=ov)
         bm.run([ms for _, ms in quads])
         torch.cuda.synchronize()
         for (q, ms), b, ref in zip(quads, bm.quads, refs):
-            cfg = (group_mb, pair, alt, form, pdl, tma)
+            cfg = (group_mb, pair, alt, form, pdl, tma, ov)
             assert np.array_equal(b.fwd.cpu().numpy(), ref["fwd"]), cfg
             assert np.array_equal(b.inv.cpu().numpy(), ref["inv"]), cfg
             assert np.array_equal(b.fwd_cost.cpu().numpy(), ref["fwd_cost"]), cfg
