@@ -106,8 +106,11 @@ extern "C" int sff_run_batch(const sff_quad* quads, int32_t n, const sff_params*
     }
     static_assert(kFeaturesSeparable == 0 && kFeaturesTensor == 1 && kFeaturesPairs == 2,
                   "sff_tuning.features_form values");
-    // With the overlap, the stream computes the coarsest scale's features
-    // (the K-NN and the first iterations read only those) and gathers the
+    // With the overlap, the stream smooths the images (every scale: smoothing
+    // the finer scales on the second stream instead made the step slower, as
+    // the features then ran later, beside more of the iterations), computes
+    // the coarsest scale's features (the K-NN and the first iterations read
+    // only those) and gathers the
     // coarsest grid; then the finer scales' features run on the second
     // stream, coarse to fine, one event per scale, beside the K-NN (which
     // leaves SMs idle), the initialisation and the coarse iterations.  The
@@ -117,7 +120,7 @@ extern "C" int sff_run_batch(const sff_quad* quads, int32_t n, const sff_params*
     // delayed the gathering rather than the K-NN.)
     const int S = P.num_scales;
     const SideStream* side = t.overlap && S > 1 ? side_stream(st) : nullptr;
-    int status = side ? run_features(img, 4 * n, P, st, t.features_form, true, S - 1, S - 1)
+    int status = side ? run_features(img, 4 * n, P, st, t.features_form, true, S - 1, S - 1, 0, S - 1)
                       : run_features(img, 4 * n, P, st, t.features_form);
     if (status) return status;
     struct Fork {

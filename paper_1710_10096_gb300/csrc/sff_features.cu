@@ -51,7 +51,8 @@ constexpr int kSmX = 64, kSmY = 16;  // output tile of k_smooth
 constexpr int kMargin = 4;           // half of the largest box (n = 8)
 constexpr int kRegX = kSmX + 2 * kMargin, kRegY = kSmY + 2 * kMargin;
 
-__global__ void __launch_bounds__(256) k_smooth(const __grid_constant__ ImageJobs J, int S) {
+// Writes the smoothed planes of scales s_lo..s_hi (of S).
+__global__ void __launch_bounds__(256) k_smooth(const __grid_constant__ ImageJobs J, int S, int s_lo, int s_hi) {
     __shared__ int sat[3][kRegY + 1][kRegX + 1];  // summed-area table per channel, zero first row/column
     const ImageJob& job = J.im[blockIdx.z];
     const int w = job.w, h = job.h, pitch = job.pitch;
@@ -89,7 +90,7 @@ __global__ void __launch_bounds__(256) k_smooth(const __grid_constant__ ImageJob
         if (x >= w || y >= h) continue;
         const size_t i = (size_t)y * w + x;
         // scale 0: the pixel itself (region cell (ly + margin, lx + margin))
-        {
+        if (s_lo == 0) {
             const int cy = ly + kMargin + 1, cx = lx + kMargin + 1;
             int v[3];
 #pragma unroll
@@ -98,7 +99,7 @@ __global__ void __launch_bounds__(256) k_smooth(const __grid_constant__ ImageJob
             rg_out[i] = v[0] + 65536 * v[1];
             b_out[i] = v[2];
         }
-        for (int s = 1; s < S; ++s) {
+        for (int s = s_lo > 1 ? s_lo : 1; s <= s_hi; ++s) {
             const int n = 1 << s;
             // box rows/columns -n/2 .. n/2-1 around the pixel, in region cells (+1 for the zero border)
             const int ya = ly + kMargin - n / 2, yb = ly + kMargin + n / 2;  // rows [ya, yb) of the region
@@ -614,11 +615,15 @@ int features_status_read(cudaStream_t st, unsigned* out, bool reset) {
 }
 
 int run_features(const ImageJob* jobs, int n, const sff_params& P, cudaStream_t st, int form, bool smooth, int s_lo,
-                 int s_hi) {
+                 int s_hi, int smooth_lo, int smooth_hi) {
     if (n < 1 || n > kMaxImages || (form != kFeaturesSeparable && form != kFeaturesTensor && form != kFeaturesPairs))
         return SFF_ERR_ARG;
     if (s_hi < 0) s_hi = P.num_scales - 1;
-    if (s_lo < 0 || s_hi >= P.num_scales) return SFF_ERR_ARG;
+    if (smooth_lo < 0) smooth_lo = s_lo;
+    if (s_lo < 0 || s_hi >= P.num_scales || smooth_hi >= P.num_scales || (smooth && smooth_lo > s_lo))
+        return SFF_ERR_ARG;
+    const int nsmooth_hi = smooth_hi < 0 ? s_hi : smooth_hi;
+    if (smooth && nsmooth_hi < s_hi) return SFF_ERR_ARG;  // every computed scale smoothed first
     if (form == kFeaturesTensor && !features_tc_ready()) return SFF_ERR_CUDA;
     static ImageJobs J;  // host staging of the kernel parameter (copied at each launch)
     static std::mutex mu;
@@ -630,7 +635,7 @@ int run_features(const ImageJob* jobs, int n, const sff_params& P, cudaStream_t 
         mh = mh > jobs[k].h ? mh : jobs[k].h;
     }
     dim3 gs((mw + kSmX - 1) / kSmX, (mh + kSmY - 1) / kSmY, n);
-    if (smooth) SFF_LAUNCH(k_smooth, gs, 256, 0, st, J, P.num_scales);
+    if (smooth) SFF_LAUNCH(k_smooth, gs, 256, 0, st, J, P.num_scales, smooth_lo, nsmooth_hi);
     for (int s = s_lo; s <= s_hi; ++s) {
         const int nn = 1 << s;
         if (form == kFeaturesTensor) {

@@ -197,10 +197,11 @@ struct ImageJobs {
 // (the default), the kept coefficients as a matrix product on the tensor
 // cores, or butterflies per pair of vertically adjacent pixels.
 constexpr int kFeaturesSeparable = 0, kFeaturesTensor = 1, kFeaturesPairs = 2;
-// Smooths the images (smooth = true) and computes the records of scales
-// s_lo..s_hi (s_hi < 0: the last scale).
+// With smooth = true, smooths the images at scales smooth_lo..smooth_hi
+// (< 0: s_lo and s_hi; the range must cover s_lo..s_hi); then computes the
+// records of scales s_lo..s_hi (s_hi < 0: the last scale).
 int run_features(const ImageJob* jobs, int n, const sff_params& P, cudaStream_t st, int form = kFeaturesSeparable,
-                 bool smooth = true, int s_lo = 0, int s_hi = -1);
+                 bool smooth = true, int s_lo = 0, int s_hi = -1, int smooth_lo = -1, int smooth_hi = -1);
 
 // One quad of a consistency-filter / seeds launch (up to kMaxQuads).
 struct FilterJob {

@@ -24,8 +24,11 @@
 //                 first-ranked epipolar leaves give the lowest cost and win
 //                 every tie; the result equals scoring all K_T x K_E x K_E
 //                 combinations in order.
-// k_inherit:      grid points of the coarser scale keep their vector and are
-//                 re-scored at this scale; the others start empty.
+// inheritance:    grid points of the coarser scale keep their vector and are
+//                 re-scored at this scale; the others start empty.  Done by
+//                 the first iteration of each finer scale (TileStep::inherit),
+//                 or by k_inherit for the sequential sweeps and for runs
+//                 without iterations.
 // k_iteration:    one whole iteration (both colours of the checkerboard)
 //                 over a tile, L lanes per pixel.  Fused with the random
 //                 search: the search after iteration i of colour 1 runs at
@@ -612,7 +615,8 @@ __device__ __forceinline__ void warp_row_nearest(const RefFeat& r, const int4* r
 __global__ void k_init_select(const __grid_constant__ Fields F, int n, int knn) {
     const Field& A = pick(F);
     const Views& V = A.V;
-    if (blockIdx.x == 0 && threadIdx.x == 0) *A.sync = 0u;  // for this scale's fused iterations
+    // the grid-barrier counters of every scale's fused iterations (one each)
+    if (blockIdx.x == 0 && threadIdx.x < SFF_MAX_SCALES) A.sync[threadIdx.x] = 0u;
     const int gw = A.gw;
     const int qi = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
@@ -657,7 +661,6 @@ __global__ void k_init_select(const __grid_constant__ Fields F, int n, int knn) 
 __global__ void k_inherit(const __grid_constant__ Fields F, int n) {
     const Field& A = pick(F);
     const Views& V = A.V;
-    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *A.sync = 0u;  // for this scale's fused iterations
     const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y;
     if (gx >= A.gw || gy >= A.gh) return;
     const int x = gx * n, y = gy * n;
@@ -853,6 +856,7 @@ struct IterStep {
     int rev;   // the block indices taken in reverse: CTAs are issued in increasing linear
                // index, so a launch with rev = 1 visits the tiles last-to-first and first reads
                // what the previous launch read last (still in L2)
+    int inherit;  // first iteration of a scale that inherits (TileStep::inherit)
 };
 
 // Block indices of this CTA in visiting order.
@@ -875,7 +879,28 @@ struct TileStep {
     uint2* fout;
     int* cout;
     int n, s, dx, dy, it, last;
+    // 1: the first iteration of a scale below the coarsest, which also does
+    // the scale inheritance: fin / cin hold the coarser scale's final state
+    // (its compact grid), a grid pixel with both coordinates even starts
+    // from its coarser counterpart's vector with that vector's cost at this
+    // scale (empty if the counterpart is), and every other pixel starts
+    // empty -- in particular the predecessors of a colour-0 pixel, which are
+    // of colour 1
+    int inherit;
 };
+
+// The inherited state of grid pixel (gx, gy) (TileStep::inherit): the
+// coarser scale's state where both coordinates are even, else empty; the
+// cost is still the coarser scale's (the caller evaluates it at this scale).
+template <bool kCg>
+__device__ __forceinline__ int inherited_state(const TileStep& T, int gx, int gy, int gw, uint2& w) {
+    w = make_uint2(0u, 0u);
+    if ((gx | gy) & 1) return kEmpty;
+    const size_t ic = (size_t)(gy >> 1) * ((gw + 1) >> 1) + (gx >> 1);
+    const int c = kCg ? __ldcg(T.cin + ic) : T.cin[ic];
+    if (c != kEmpty) w = kCg ? __ldcg(T.fin + ic) : T.fin[ic];
+    return c;
+}
 
 // State loads and stores of the latency form.  kCg: through L2 only
 // (ld/st.global.cg), for a launch whose CTAs read in one iteration what other
@@ -955,13 +980,22 @@ __device__ __forceinline__ void iter_tile(const Field& A, const TileStep& T, int
         const int ax = x - T.dx * n, by = y - T.dy * n;
         const bool has_a = ax >= 0 && ax < V.w, has_b = by >= 0 && by < V.h;
         const size_t ja = has_a ? si - T.dx : si, jb = has_b ? si - (size_t)(T.dy * gw) : si;
-        int c = ld_cost<kCg>(T.cin + si);
-        const uint2 wc = ld_vec<kCg>(T.fin + si);
-        const int ca = has_a ? ld_cost<kCg>(T.cin + ja) : kEmpty, cb = has_b ? ld_cost<kCg>(T.cin + jb) : kEmpty;
-        const uint2 wa = ld_vec<kCg>(T.fin + ja), wb = ld_vec<kCg>(T.fin + jb);
+        int c, ca = kEmpty, cb = kEmpty;
+        uint2 wc, wa = make_uint2(0u, 0u), wb = make_uint2(0u, 0u);
+        if (T.inherit) {
+            c = inherited_state<kCg>(T, gx, gy, gw, wc);
+        } else {
+            c = ld_cost<kCg>(T.cin + si);
+            wc = ld_vec<kCg>(T.fin + si);
+            if (has_a) ca = ld_cost<kCg>(T.cin + ja);
+            if (has_b) cb = ld_cost<kCg>(T.cin + jb);
+            wa = ld_vec<kCg>(T.fin + ja);
+            wb = ld_vec<kCg>(T.fin + jb);
+        }
         Slice<L> a;
         ref_slice(i, ry * kRegX + rx, a);
         Vec4 cur = unpack_vec(wc);
+        if (T.inherit && c != kEmpty) c = group_sum<L>(group_part<L>(V, a, q, x, y, cur), gmask);
         update_pixel<L>(V, a, q, gmask, n, T.s, A.key, A.mirror, x, y, (uint32_t)i, T.it - 1, -1, unpack_vec(wa), ca,
                         unpack_vec(wb), cb, cur, c);
         if (q == 0) {
@@ -983,8 +1017,12 @@ __device__ __forceinline__ void iter_tile(const Field& A, const TileStep& T, int
         const int x = gx * n, y = gy * n;
         const size_t i = pix(V.w, x, y);
         const size_t si = (size_t)gy * gw + gx;
-        int c = ld_cost<kCg>(T.cin + si);
-        Vec4 cur = unpack_vec(ld_vec<kCg>(T.fin + si));
+        int c = kEmpty;  // a colour-1 pixel starts empty at an inheriting iteration
+        Vec4 cur = {0, 0, 0, 0};
+        if (!T.inherit) {
+            c = ld_cost<kCg>(T.cin + si);
+            cur = unpack_vec(ld_vec<kCg>(T.fin + si));
+        }
         Slice<L> a;
         ref_slice(i, (gy - ry0) * kRegX + (gx - rx0), a);
         const int agx = gx - T.dx, bgy = gy - T.dy;  // predecessors (colour 0, in the region)
@@ -1043,7 +1081,7 @@ __global__ void __launch_bounds__(iter_threads<L, TX, TY>(), MB) k_iteration(con
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int3 blk = iter_block(H);
     const Field& A = F.f[iter_field(H, blk)];
-    const TileStep T{A.field, A.cost, A.field_out, A.cost_out, H.n, H.s, H.dx, H.dy, H.it, H.last};
+    const TileStep T{A.field, A.cost, A.field_out, A.cost_out, H.n, H.s, H.dx, H.dy, H.it, H.last, H.inherit};
     iter_tile<L, TX, TY, false>(A, T, iter_tile_x(H, blk) * TX, blk.y * TY, s_vec, s_cost);
 }
 
@@ -1083,7 +1121,7 @@ __global__ void __launch_bounds__(iter_threads<L, TX, TY>(), MB)
         tma_load_4d(s_ref, &M.m[f], 0, tx0 - (H.dx > 0 ? 1 : 0), ty0 - (H.dy > 0 ? 1 : 0), 0, &bar);
     }
     __syncthreads();
-    const TileStep T{A.field, A.cost, A.field_out, A.cost_out, H.n, H.s, H.dx, H.dy, H.it, H.last};
+    const TileStep T{A.field, A.cost, A.field_out, A.cost_out, H.n, H.s, H.dx, H.dy, H.it, H.last, H.inherit};
     iter_tile<L, TX, TY, false, true>(A, T, tx0, ty0, s_vec, s_cost, s_ref, &bar, wait_ns);
     // no CTA leaves with its copy in flight
     if (threadIdx.x == 0 && !mbar_wait(&bar, 0, kDrainFactor * wait_ns)) {
@@ -1201,8 +1239,10 @@ __device__ __forceinline__ void lat_tile(const Field& A, const TileStep& T, int 
     if (has2) {
         const size_t si = (size_t)gy2 * gw + gx2;
         const size_t i = pix(V.w, gx2 * n, gy2 * n);
-        c2 = ld_cost<kCg>(T.cin + si);
-        w2 = ld_vec<kCg>(T.fin + si);
+        if (!T.inherit) {  // a colour-1 pixel starts empty at an inheriting iteration
+            c2 = ld_cost<kCg>(T.cin + si);
+            w2 = ld_vec<kCg>(T.fin + si);
+        }
         load_slice<L>(V.ref, i, q, a2);
         o2 = rs_draw(n, T.s, A.key, A.mirror, T.it, (uint32_t)i);
     }
@@ -1219,14 +1259,23 @@ __device__ __forceinline__ void lat_tile(const Field& A, const TileStep& T, int 
             const int ax = x - T.dx * n, by = y - T.dy * n;
             const bool has_a = ax >= 0 && ax < V.w, has_b = by >= 0 && by < V.h;
             const size_t ja = has_a ? si - T.dx : si, jb = has_b ? si - (size_t)(T.dy * gw) : si;
-            int c = ld_cost<kCg>(T.cin + si);
-            const uint2 wc = ld_vec<kCg>(T.fin + si);
-            const int ca = has_a ? ld_cost<kCg>(T.cin + ja) : kEmpty, cb = has_b ? ld_cost<kCg>(T.cin + jb) : kEmpty;
-            const uint2 wa = ld_vec<kCg>(T.fin + ja), wb = ld_vec<kCg>(T.fin + jb);
+            int c, ca = kEmpty, cb = kEmpty;
+            uint2 wc, wa = make_uint2(0u, 0u), wb = make_uint2(0u, 0u);
+            if (T.inherit) {
+                c = inherited_state<kCg>(T, gx, gy, gw, wc);
+            } else {
+                c = ld_cost<kCg>(T.cin + si);
+                wc = ld_vec<kCg>(T.fin + si);
+                if (has_a) ca = ld_cost<kCg>(T.cin + ja);
+                if (has_b) cb = ld_cost<kCg>(T.cin + jb);
+                wa = ld_vec<kCg>(T.fin + ja);
+                wb = ld_vec<kCg>(T.fin + jb);
+            }
             Slice<L> a;
             load_slice<L>(V.ref, i, q, a);
             const RsOff o = rs_draw(n, T.s, A.key, A.mirror, T.it - 1, (uint32_t)i);
             Vec4 cur = unpack_vec(wc);
+            if (T.inherit && c != kEmpty) c = group_sum<L>(group_part<L>(V, a, q, x, y, cur), gmask);
             const Vec4 va = unpack_vec(wa), vb = unpack_vec(wb);
             const bool own_valid = c != kEmpty;
             Vec4 cr;
@@ -1369,7 +1418,7 @@ __global__ void __launch_bounds__(lat_threads<L * C, TX, TY>()) k_iteration_lat(
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int3 blk = iter_block(H);
     const Field& A = F.f[iter_field(H, blk)];
-    const TileStep T{A.field, A.cost, A.field_out, A.cost_out, H.n, H.s, H.dx, H.dy, H.it, H.last};
+    const TileStep T{A.field, A.cost, A.field_out, A.cost_out, H.n, H.s, H.dx, H.dy, H.it, H.last, H.inherit};
     lat_tile<L, C, TX, TY, false>(A, T, iter_tile_x(H, blk) * TX, blk.y * TY, s_vec, s_cost);
 }
 
@@ -1389,6 +1438,7 @@ struct FusedStep {
     int f0, nf;              // fields f0 .. f0 + nf - 1
     int tiles_x, tiles_y;    // tile grid of the largest field
     unsigned* sync;          // barrier counter, zero at launch
+    int inherit;             // iteration 0 also inherits (TileStep::inherit)
 };
 
 // Failure injection for tests (sff_debug_barrier_withhold): CTA 0 of a fused
@@ -1459,7 +1509,8 @@ __global__ void __launch_bounds__(fused_threads<L, C, TX, TY>(), fused_min_block
             const Field& A = F.f[H.f0 + t / per];
             const int r = t % per;
             const TileStep T{odd ? A.field_out : A.field, odd ? A.cost_out : A.cost, odd ? A.field : A.field_out,
-                             odd ? A.cost : A.cost_out, H.n, H.s, dx, dy, it, it == H.iters - 1};
+                             odd ? A.cost : A.cost_out, H.n, H.s, dx, dy, it, it == H.iters - 1,
+                             it == 0 ? H.inherit : 0};
             if constexpr (C == 0)
                 iter_tile<L, TX, TY, true>(A, T, (r % H.tiles_x) * TX, (r / H.tiles_x) * TY, s_vec, s_cost);
             else
@@ -2063,11 +2114,17 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
         Bf[1][k] = Tf[k];
         Bc[1][k] = Tc[k];
     }
+    // With checkerboard iterations the first iteration of each finer scale
+    // also does the inheritance (TileStep::inherit): it reads the coarser
+    // scale's final buffer and writes the other one.  The sequential sweeps
+    // (in place) and a run without iterations inherit with k_inherit into
+    // the other buffer.
+    const bool fused_inherit = !sequential && I > 0;
     const int flips = sequential ? 0 : (I & 1);  // the sweeps work in place
     auto final_of_scale0 = [&](int b) {
         for (int s = S - 1; s >= 0; --s) {
-            if (s < S - 1) b ^= 1;  // inherit into the other buffer
-            b ^= flips;             // after the iterations
+            if (s < S - 1 && !fused_inherit) b ^= 1;  // inherit into the other buffer
+            b ^= flips;                                // after the iterations
         }
         return b;
     };
@@ -2075,7 +2132,8 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
     for (int s = S - 1; s >= 0; --s) {
         const int n = 1 << s;
         int mgw = 0, mgh = 0, mgq = 0;
-        if (s < S - 1) cur = prev ^ 1;
+        const bool inherit = s < S - 1 && fused_inherit;  // the first iteration inherits
+        if (s < S - 1) cur = fused_inherit ? prev : prev ^ 1;
         for (int k = 0; k < nf; ++k) {
             const FieldSpec& fs = spec[k];
             const int w = fs.width, h = fs.height;
@@ -2084,7 +2142,8 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
             if (s == S - 1) {  // k_init_select writes the state
                 F.f[k].field = F.f[k].field_out = Bf[cur][k];
                 F.f[k].cost = F.f[k].cost_out = Bc[cur][k];
-            } else {  // k_inherit reads the coarser final state, writes this scale's
+            } else {  // k_inherit reads the coarser final state, writes this scale's (unless
+                      // the first iteration inherits: it sets its own buffers)
                 F.f[k].field = Bf[prev][k];
                 F.f[k].cost = Bc[prev][k];
                 F.f[k].field_out = Bf[cur][k];
@@ -2111,8 +2170,10 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
         } else {
             // the features of this scale may still be in flight on another stream
             if (scale_ready && cudaStreamWaitEvent(st, scale_ready[s], 0) != cudaSuccess) return SFF_ERR_CUDA;
-            dim3 g((mgw + 127) / 128, mgh, nf);
-            SFF_LAUNCH(k_inherit, g, 128, 0, st, F, n);
+            if (!inherit) {
+                dim3 g((mgw + 127) / 128, mgh, nf);
+                SFF_LAUNCH(k_inherit, g, 128, 0, st, F, n);
+            }
         }
         if (sequential) {
             for (int k = 0; k < nf; ++k) {
@@ -2181,7 +2242,7 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
                     F.f[k].field_out = Bf[cur ^ 1][k];
                     F.f[k].cost_out = Bc[cur ^ 1][k];
                 }
-                FusedStep FH{n, s, I, f0, f1 - f0, tiles_x, tiles_y, F.f[f0].sync};
+                FusedStep FH{n, s, I, f0, f1 - f0, tiles_x, tiles_y, F.f[f0].sync + s, inherit ? 1 : 0};
                 cudaLaunchConfig_t cfg = {};
                 cfg.gridDim = dim3((unsigned)std::min(total, cap));
                 cfg.blockDim = dim3(fv->threads);
@@ -2212,7 +2273,7 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
                     F.f[k].cost_out = Bc[in ^ 1][k];
                 }
                 IterStep H{n,      s,  kDirs[it % 4][0], kDirs[it % 4][1], it, it == I - 1, f0, pair ? 1 : 0,
-                           ((T.alternate_order >> s) & 1) ? (it & 1) : 0};
+                           ((T.alternate_order >> s) & 1) ? (it & 1) : 0, inherit && it == 0 ? 1 : 0};
                 if (tv) {
                     // TMA-staged reference records (scale 0)
                     cudaLaunchConfig_t cfg = {};
