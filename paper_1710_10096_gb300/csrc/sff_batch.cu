@@ -58,6 +58,35 @@ const SideStream* side_stream(cudaStream_t st) {
     return &g_side.emplace(std::make_pair(dev, st), ss).first->second;
 }
 
+// The feature overlap of one sff_run_batch call (sff_tuning.overlap).
+struct Fork {
+    const SideStream* side;
+    const ImageJob* img;
+    int n_img;
+    const sff_params* P;
+    int form;
+    int joined_at;  // the last scale whose event the second stream recorded (-1: none)
+};
+
+// ForkHook of run_fields (before the K-NN): forks the second stream from
+// `main` and issues the features of scales S - 2 .. 0 on it, coarse to
+// fine, each followed by its event.  Every event is recorded even after a
+// failed launch, so that the caller's stream always joins the second one
+// (a capture stays whole).
+int fork_features(void* ctx, cudaStream_t main) {
+    Fork& f = *static_cast<Fork*>(ctx);
+    if (cudaEventRecord(f.side->fork, main) != cudaSuccess || cudaStreamWaitEvent(f.side->s, f.side->fork, 0) != cudaSuccess)
+        return SFF_ERR_CUDA;
+    int status = SFF_OK;
+    for (int s = f.P->num_scales - 2; s >= 0; --s) {
+        const int st_s = run_features(f.img, f.n_img, *f.P, f.side->s, f.form, false, s, s);
+        if (!status) status = st_s;
+        if (cudaEventRecord(f.side->ready[s], f.side->s) != cudaSuccess && !status) status = SFF_ERR_CUDA;
+        f.joined_at = s;
+    }
+    return status;
+}
+
 }  // namespace
 
 }  // namespace sff
@@ -117,37 +146,16 @@ extern "C" int sff_run_batch(const sff_quad* quads, int32_t n, const sff_params*
     // inheritance into scale s waits for event s, and the wait on the finest
     // scale's event joins the two streams again.  (Forked before the grid is
     // gathered instead, the step took the same time: the features' CTAs then
-    // delayed the gathering rather than the K-NN.)
+    // delayed the gathering rather than the K-NN.  Holding the features of
+    // scales 1 and 0 back until the coarsest scale is matched sped up its
+    // fused iterations but slowed scale 1's more: 1.406 against 1.351 ms.)
     const int S = P.num_scales;
     const SideStream* side = t.overlap && S > 1 ? side_stream(st) : nullptr;
     int status = side ? run_features(img, 4 * n, P, st, t.features_form, true, S - 1, S - 1, 0, S - 1)
                       : run_features(img, 4 * n, P, st, t.features_form);
     if (status) return status;
-    struct Fork {
-        const SideStream* side;
-        const ImageJob* img;
-        int n_img;
-        const sff_params* P;
-        int form;
-        bool forked;
-    } fork{side, img, 4 * n, &P, t.features_form, false};
-    // every event is recorded even after a failed launch, so that the
-    // caller's stream always joins the second one (a capture stays whole)
-    auto fork_fn = [](void* ctx, cudaStream_t main) -> int {
-        Fork& f = *static_cast<Fork*>(ctx);
-        if (cudaEventRecord(f.side->fork, main) != cudaSuccess ||
-            cudaStreamWaitEvent(f.side->s, f.side->fork, 0) != cudaSuccess)
-            return SFF_ERR_CUDA;
-        f.forked = true;
-        int status = SFF_OK;
-        for (int s = f.P->num_scales - 2; s >= 0; --s) {
-            const int st_s = run_features(f.img, f.n_img, *f.P, f.side->s, f.form, false, s, s);
-            if (!status) status = st_s;
-            if (cudaEventRecord(f.side->ready[s], f.side->s) != cudaSuccess && !status) status = SFF_ERR_CUDA;
-        }
-        return status;
-    };
-    const ForkHook hook{fork_fn, &fork};
+    Fork fork{side, img, 4 * n, &P, t.features_form, -1};
+    const ForkHook hook{fork_features, &fork};
 
     // both fields of every quad (pyramids in the order L0, R0, L1, R1)
     FieldSpec fs[kMaxBatchFields];
@@ -161,7 +169,8 @@ extern "C" int sff_run_batch(const sff_quad* quads, int32_t n, const sff_params*
                                   q.width,      q.height,     q.seed,       ws + half};
     }
     status = run_fields(fs, 2 * n, P, t, st, false, side ? side->ready : nullptr, side ? &hook : nullptr);
-    if (fork.forked) cudaStreamWaitEvent(st, side->ready[0], 0);  // joined already, unless run_fields failed early
+    // joined already, unless run_fields failed early
+    if (fork.joined_at >= 0) cudaStreamWaitEvent(st, side->ready[fork.joined_at], 0);
     if (status) return status;
 
     // consistency + region filter, then seeds
