@@ -959,8 +959,6 @@ def main():
         probe.run(*[torch.as_tensor(im).to(dev) for im in q.images()], seed=MATCH_SEED)
         tuning = tune.autotune(probe.pyr, q.width, q.height, params, reps=3)
         del probe
-        if args.tuning_cache and rank == 0:
-            tune.save_cache(args.tuning_cache)
     elif args.tuning.lstrip().startswith("{"):
         tuning = tune._tuning_of(json.loads(args.tuning))
     else:
@@ -982,6 +980,12 @@ def main():
     for k, im in enumerate(q.images()):
         host_in[k].copy_(torch.as_tensor(im))
     dev_in = host_in.to(dev)
+    if args.tuning == "auto":
+        # the coarse scales' fused form checked on the whole stage (beside the
+        # overlapped features); a no-op for a tuning read from the cache
+        tuning = tune.refine_stage(m, list(dev_in.unbind(0)), MATCH_SEED)
+        if args.tuning_cache and rank == 0:
+            tune.save_cache(args.tuning_cache)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     # warm-up, then the per-kernel profile: a CUDA graph of prof_steps steps

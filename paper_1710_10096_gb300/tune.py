@@ -22,6 +22,9 @@ from . import (FUSED_SPACE, TMA_SPACE, VARIANT_SPACE, Tuning, default_params, de
                profile_collect, profile_enable, workspace_bytes)
 
 _CACHE: dict = {}
+# per cache key just measured by autotune(): {fused scale: (variant, alt, pdl)
+# of its fastest separate launches}, for refine_stage()
+_UNFUSED: dict = {}
 
 
 def size_bucket(width: int, height: int) -> str:
@@ -130,6 +133,8 @@ def autotune(pyramids, width: int, height: int, params=None, reps: int = 3, spac
 
     pair = min((0, 1), key=total)
     fuse = sum(1 << s for s in range(1, S) if fused_us[s] < sched[(pair, *best_combo(pair, s))][s])
+    # what each fused scale would run as separate launches, for refine_stage
+    _UNFUSED[key] = {s: (tuple(variants[s]), *best_combo(pair, s)) for s in range(1, S) if (fuse >> s) & 1}
     for s in range(1, S):
         if (fuse >> s) & 1:
             variants[s] = fused[s]
@@ -146,6 +151,81 @@ def autotune(pyramids, width: int, height: int, params=None, reps: int = 3, spac
             entry["tma"] = 1
     _CACHE[key] = entry
     return _tuning_of(entry)
+
+
+def _graph_ms(run, reps: int, flush, stream) -> float:
+    """Median milliseconds of `reps` CUDA-graph replays of run(stream), each
+    after an L2 flush (a write of `flush`) outside its events."""
+    import statistics
+
+    import torch
+    run(stream)
+    stream.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        run(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        g.replay()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            g.replay()
+            b.record(stream)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+    del g
+    return statistics.median(ts)
+
+
+def refine_stage(matcher, images, seed: int, reps: int = 7, verbose: bool = False) -> Tuning:
+    """Whole-stage check of the coarse scales' fused form.  With the feature
+    overlap the coarse scales run beside the features of the finer scales,
+    which autotune()'s per-scale spans (matching alone) do not see.  Tries
+    every subset of the tuned fuse bits -- a scale left unfused runs the
+    variant and schedule bits autotune() found for its separate launches --
+    on CUDA-graph replays of matcher.run on `images` (device tensors,
+    L2 flushed between replays), and keeps the fastest if it beats the
+    tuned setting by more than 1 % (differences below that are within the
+    run-to-run spread of a stage), caching the result.  A no-op
+    for a tuning that autotune() did not just measure (e.g. from a cache
+    file).  Leaves matcher.tuning at the chosen setting."""
+    import torch
+    params = matcher.params
+    key = (size_bucket(matcher.width, matcher.height), tuple(params.as_dict().values()))
+    alts = _UNFUSED.pop(key, None)
+    if not alts or key not in _CACHE:
+        return matcher.tuning
+    base = matcher.tuning
+    stream = torch.cuda.Stream(device=matcher.device)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=matcher.device)
+    scales = sorted(alts)
+    best, best_ms = None, float("inf")
+    for mask in range(1 << len(scales)):
+        e = dict(_CACHE[key], variants=list(_CACHE[key]["variants"]))
+        for j, s in enumerate(scales):
+            if (mask >> j) & 1:  # scale s as separate launches
+                v, alt, pdl = alts[s]
+                e["variants"][s] = v
+                e["fuse"] &= ~(1 << s)
+                e["alt"] |= (1 << s) if alt else 0
+                e["pdl"] |= (1 << s) if pdl else 0
+        t = _tuning_of(e)
+        t.features_form, t.overlap, t.tma = base.features_form, base.overlap, base.tma
+        matcher.tuning = t
+        ms = _graph_ms(lambda st: matcher.run(*images, seed=seed, stream=st), reps, flush, stream)
+        if verbose:
+            print(f"stage fuse {e['fuse']}: {ms:.4f} ms")
+        if mask == 0:
+            best, best_ms = e, ms / 1.01  # the tuned setting, with the 1 % margin
+        elif ms < best_ms:
+            best, best_ms = e, ms
+    _CACHE[key] = best
+    matcher.tuning = _tuning_of(best)
+    matcher.tuning.features_form, matcher.tuning.overlap, matcher.tuning.tma = \
+        base.features_form, base.overlap, base.tma
+    return matcher.tuning
 
 
 def autotune_batch(batch, seeds, space=None, reps: int = 3, verbose: bool = False) -> Tuning:
@@ -227,5 +307,5 @@ def load_cache(path: str) -> int:
     return taken
 
 
-__all__ = ["autotune", "autotune_batch", "scale_times", "size_bucket", "save_cache", "load_cache",
+__all__ = ["autotune", "autotune_batch", "refine_stage", "scale_times", "size_bucket", "save_cache", "load_cache",
            "default_tuning"]
