@@ -72,6 +72,7 @@ struct Field {
     int* rec_n;   // [2][gq] their norms
     uint2 key;  // Philox key: the seed of the field's quad
     unsigned* sync;  // grid-barrier counter of a fused iteration launch (zeroed before each scale)
+    uint8_t* stamp;  // change stamps of the current scale's grid (stamp_limits), one plane for all scales
 };
 
 // Up to kMaxFields fields of any sizes share every launch (blockIdx.z picks
@@ -765,6 +766,50 @@ __device__ __forceinline__ bool same_vec(const Vec4& a, const Vec4& b) {
     return a.u == b.u && a.v == b.v && a.d0 == b.d0 && a.d1 == b.d1;
 }
 
+// Change stamps: one byte per grid pixel of the scale (Field::stamp) saying
+// when the pixel's state last changed within the scale:
+//     0           not since the scale's first iteration began,
+//     2 it + 1    a colour-0 pixel, in the first half-step of iteration it
+//                 (its propagation, or the random search of iteration
+//                 it - 1, which the kernels run at that point),
+//     2 it + 2    a colour-1 pixel, in the second half-step of iteration it
+//                 (its propagation or its random search).
+// A candidate taken from a predecessor whose vector has not changed since
+// this pixel last took a candidate from the same neighbour cannot be strictly
+// lower than the pixel's cost: that vector's cost here was computed then (or
+// equalled the pixel's own or the other predecessor's, which were), the
+// pixel kept a cost no higher, and a pixel's cost never rises within a
+// scale.  Such a stale candidate is not evaluated; the results are those of
+// evaluating it.  The horizontal predecessor (the sweep's dx) was last
+// consulted in iteration it - 2 (dx alternates), the vertical one in it - 1
+// for even it and it - 3 for odd it (dy runs +, -, -, +).  A colour-0
+// pixel of iteration i' read its predecessors' states as of the end of
+// iteration i' - 1 (stamps <= 2 i'), a colour-1 pixel read its colour-0
+// predecessors after their half-step of i' (stamps <= 2 i' + 1).  Iteration
+// 0 of a scale writes every grid pixel's stamp; later ones write it only on
+// a change.  The plane is not double-buffered: a stamp read while its owner
+// rewrites it in the same iteration is either the old value or a newer,
+// larger one, which only makes the test fail (the candidate is scored as
+// usual); a pixel computed in another tile's halo reads its own stamp only
+// to pass it on when unchanged, and then no tile rewrites it.
+struct StampLimits {
+    int h, v;  // largest stale stamp of the horizontal / vertical predecessor (-1: none)
+};
+__device__ __forceinline__ StampLimits stamp_limits(int it, int colour) {
+    const int ih = it - 2, iv = (it & 1) ? it - 3 : it - 1;
+    return StampLimits{ih >= 0 ? 2 * ih + colour : -1, iv >= 0 ? 2 * iv + colour : -1};
+}
+template <bool kCg>
+__device__ __forceinline__ int ld_stamp(const uint8_t* p) {
+    if constexpr (kCg) return __ldcg(p);
+    else return *p;
+}
+template <bool kCg>
+__device__ __forceinline__ void st_stamp(uint8_t* p, int v) {
+    if constexpr (kCg) __stcg(p, (unsigned char)v);
+    else *p = (uint8_t)v;
+}
+
 // One half-step of one pixel with own state (cur, c) and predecessor states
 // (va, ca), (vb, cb) (ca/cb = kEmpty when absent).  The costs of the
 // candidates that do not depend on each other -- the random-search candidate
@@ -774,11 +819,13 @@ __device__ __forceinline__ bool same_vec(const Vec4& a, const Vec4& b) {
 // horizontal, vertical, exactly as if evaluated one after the other.  The
 // random search that follows the propagation (colour 1) depends on its
 // result and comes last.  rs_before / rs_after < 0: no search.
+// stale_a / stale_b: the predecessor's vector is one this pixel has already
+// scored (change stamps, below), so it cannot be strictly lower either.
 template <int L>
 __device__ __forceinline__ bool update_pixel(const Views& V, const Slice<L>& a, int q, unsigned gmask, int n, int s,
                                              uint2 key, int mirror, int x, int y, uint32_t pixel, int rs_before,
                                              int rs_after, const Vec4& va, int ca, const Vec4& vb, int cb, Vec4& cur,
-                                             int& c) {
+                                             int& c, bool stale_a = false, bool stale_b = false) {
     bool changed = false;
     Vec4 cr;
     const bool do_rs = rs_before >= 0 && c != kEmpty && rs_candidate(n, s, key, mirror, rs_before, pixel, cur, cr);
@@ -786,8 +833,9 @@ __device__ __forceinline__ bool update_pixel(const Views& V, const Slice<L>& a, 
     // other predecessor, has exactly that candidate's cost and can never be
     // strictly lower: it is not evaluated (the result is unchanged).
     const bool own_valid = c != kEmpty;
-    const bool do_a = ca != kEmpty && !(own_valid && same_vec(va, cur));
-    const bool do_b = cb != kEmpty && !(own_valid && same_vec(vb, cur)) && !(ca != kEmpty && same_vec(vb, va));
+    const bool do_a = ca != kEmpty && !stale_a && !(own_valid && same_vec(va, cur));
+    const bool do_b = cb != kEmpty && !stale_b && !(own_valid && same_vec(vb, cur)) &&
+                      !(ca != kEmpty && same_vec(vb, va));
     const int pr = do_rs ? group_part<L>(V, a, q, x, y, cr) : 0;
     const int pa = do_a ? group_part<L>(V, a, q, x, y, va) : 0;
     const int pb = do_b ? group_part<L>(V, a, q, x, y, vb) : 0;
@@ -887,6 +935,7 @@ struct TileStep {
     // empty -- in particular the predecessors of a colour-0 pixel, which are
     // of colour 1
     int inherit;
+    uint8_t* stamp;  // change stamps (stamp_limits); nullptr: every candidate is scored
 };
 
 // The inherited state of grid pixel (gx, gy) (TileStep::inherit): the
@@ -935,8 +984,8 @@ __device__ __forceinline__ void st_state(const TileStep& T, size_t i, uint2 v, i
 // each thread waits for it (bounded by wait_ns) before its first read.
 template <int L, int TX, int TY, bool kCg, bool kTma = false>
 __device__ __forceinline__ void iter_tile(const Field& A, const TileStep& T, int tx0, int ty0, uint2* s_vec,
-                                          int* s_cost, const int4* s_ref = nullptr, uint64_t* bar = nullptr,
-                                          unsigned long long wait_ns = 0) {
+                                          int* s_cost, uint8_t* s_stamp, const int4* s_ref = nullptr,
+                                          uint64_t* bar = nullptr, unsigned long long wait_ns = 0) {
     constexpr int kRegX = TX + 1, kRegY = TY + 1;
     constexpr int kGroups = iter_threads<L, TX, TY>() / L;
     const Views& V = A.V;
@@ -947,6 +996,8 @@ __device__ __forceinline__ void iter_tile(const Field& A, const TileStep& T, int
     if (tx0 >= gw || ty0 >= gh) return;  // tile beyond this field's grid (whole CTA)
     const int rx0 = tx0 - (T.dx > 0 ? 1 : 0), ry0 = ty0 - (T.dy > 0 ? 1 : 0);  // region origin
     const int n = T.n;
+    const bool stamps = T.stamp != nullptr, read_st = stamps && T.it >= 2;
+    const StampLimits lim = stamp_limits(T.it, 0);  // colour 0; colour 1 is one higher
     bool staged = false;  // this thread has seen the tensor copy complete
     // reference record of image pixel i, region cell r
     auto ref_slice = [&](size_t i, int r, Slice<L>& a) {
@@ -981,6 +1032,7 @@ __device__ __forceinline__ void iter_tile(const Field& A, const TileStep& T, int
         const bool has_a = ax >= 0 && ax < V.w, has_b = by >= 0 && by < V.h;
         const size_t ja = has_a ? si - T.dx : si, jb = has_b ? si - (size_t)(T.dy * gw) : si;
         int c, ca = kEmpty, cb = kEmpty;
+        int so = 0, sa = 0, sb = 0;  // change stamps: own, predecessors
         uint2 wc, wa = make_uint2(0u, 0u), wb = make_uint2(0u, 0u);
         if (T.inherit) {
             c = inherited_state<kCg>(T, gx, gy, gw, wc);
@@ -991,18 +1043,29 @@ __device__ __forceinline__ void iter_tile(const Field& A, const TileStep& T, int
             if (has_b) cb = ld_cost<kCg>(T.cin + jb);
             wa = ld_vec<kCg>(T.fin + ja);
             wb = ld_vec<kCg>(T.fin + jb);
+            if (read_st) {
+                so = ld_stamp<kCg>(T.stamp + si);
+                sa = ld_stamp<kCg>(T.stamp + ja);
+                sb = ld_stamp<kCg>(T.stamp + jb);
+            }
         }
         Slice<L> a;
         ref_slice(i, ry * kRegX + rx, a);
         Vec4 cur = unpack_vec(wc);
         if (T.inherit && c != kEmpty) c = group_sum<L>(group_part<L>(V, a, q, x, y, cur), gmask);
-        update_pixel<L>(V, a, q, gmask, n, T.s, A.key, A.mirror, x, y, (uint32_t)i, T.it - 1, -1, unpack_vec(wa), ca,
-                        unpack_vec(wb), cb, cur, c);
+        const bool changed =
+            update_pixel<L>(V, a, q, gmask, n, T.s, A.key, A.mirror, x, y, (uint32_t)i, T.it - 1, -1, unpack_vec(wa),
+                            ca, unpack_vec(wb), cb, cur, c, read_st && sa <= lim.h, read_st && sb <= lim.v);
         if (q == 0) {
             const uint2 wv = pack_vec(cur);
+            const int st = changed ? 2 * T.it + 1 : so;
             s_vec[ry * kRegX + rx] = wv;
             s_cost[ry * kRegX + rx] = c;
-            if (gx >= tx0 && gx < tx0 + TX && gy >= ty0 && gy < ty0 + TY) st_state<kCg>(T, si, wv, c);
+            s_stamp[ry * kRegX + rx] = (uint8_t)st;
+            if (gx >= tx0 && gx < tx0 + TX && gy >= ty0 && gy < ty0 + TY) {
+                st_state<kCg>(T, si, wv, c);
+                if (stamps && (changed || T.it == 0)) st_stamp<kCg>(T.stamp + si, st);
+            }
         }
     }
     __syncthreads();
@@ -1026,21 +1089,27 @@ __device__ __forceinline__ void iter_tile(const Field& A, const TileStep& T, int
         Slice<L> a;
         ref_slice(i, (gy - ry0) * kRegX + (gx - rx0), a);
         const int agx = gx - T.dx, bgy = gy - T.dy;  // predecessors (colour 0, in the region)
-        int ca = kEmpty, cb = kEmpty;
+        int ca = kEmpty, cb = kEmpty, sa = 0, sb = 0;
         uint2 wa = make_uint2(0u, 0u), wb = make_uint2(0u, 0u);
         if (agx >= 0 && agx < gw) {
             const int r = (gy - ry0) * kRegX + (agx - rx0);
             ca = s_cost[r];
             wa = s_vec[r];
+            sa = s_stamp[r];
         }
         if (bgy >= 0 && bgy < gh) {
             const int r = (bgy - ry0) * kRegX + (gx - rx0);
             cb = s_cost[r];
             wb = s_vec[r];
+            sb = s_stamp[r];
         }
-        update_pixel<L>(V, a, q, gmask, n, T.s, A.key, A.mirror, x, y, (uint32_t)i, -1, T.it, unpack_vec(wa), ca,
-                        unpack_vec(wb), cb, cur, c);
-        if (q == 0) st_state<kCg>(T, si, pack_vec(cur), c);
+        const bool changed =
+            update_pixel<L>(V, a, q, gmask, n, T.s, A.key, A.mirror, x, y, (uint32_t)i, -1, T.it, unpack_vec(wa), ca,
+                            unpack_vec(wb), cb, cur, c, read_st && sa <= lim.h + 1, read_st && sb <= lim.v + 1);
+        if (q == 0) {
+            st_state<kCg>(T, si, pack_vec(cur), c);
+            if (stamps && (changed || T.it == 0)) st_stamp<kCg>(T.stamp + si, changed ? 2 * T.it + 2 : 0);
+        }
     }
     if (!T.last) return;
 
@@ -1075,14 +1144,16 @@ __global__ void __launch_bounds__(iter_threads<L, TX, TY>(), MB) k_iteration(con
                                                                               IterStep H) {
     __shared__ uint2 s_vec[(TX + 1) * (TY + 1)];
     __shared__ int s_cost[(TX + 1) * (TY + 1)];
+    __shared__ uint8_t s_stamp[(TX + 1) * (TY + 1)];
     // programmatic dependent launch: wait for the previous launch (its state
     // and memory), then let the next one be scheduled; no-ops otherwise
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int3 blk = iter_block(H);
     const Field& A = F.f[iter_field(H, blk)];
-    const TileStep T{A.field, A.cost, A.field_out, A.cost_out, H.n, H.s, H.dx, H.dy, H.it, H.last, H.inherit};
-    iter_tile<L, TX, TY, false>(A, T, iter_tile_x(H, blk) * TX, blk.y * TY, s_vec, s_cost);
+    const TileStep T{A.field, A.cost, A.field_out, A.cost_out, H.n, H.s, H.dx, H.dy, H.it, H.last, H.inherit,
+                     A.stamp};
+    iter_tile<L, TX, TY, false>(A, T, iter_tile_x(H, blk) * TX, blk.y * TY, s_vec, s_cost, s_stamp);
 }
 
 // Tensor maps of the scale-0 reference records of every field of a launch:
@@ -1103,6 +1174,7 @@ __global__ void __launch_bounds__(iter_threads<L, TX, TY>(), MB)
     __shared__ __align__(128) int4 s_ref[3 * (TX + 1) * (TY + 1)];
     __shared__ uint2 s_vec[(TX + 1) * (TY + 1)];
     __shared__ int s_cost[(TX + 1) * (TY + 1)];
+    __shared__ uint8_t s_stamp[(TX + 1) * (TY + 1)];
     __shared__ __align__(8) uint64_t bar;
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -1121,8 +1193,9 @@ __global__ void __launch_bounds__(iter_threads<L, TX, TY>(), MB)
         tma_load_4d(s_ref, &M.m[f], 0, tx0 - (H.dx > 0 ? 1 : 0), ty0 - (H.dy > 0 ? 1 : 0), 0, &bar);
     }
     __syncthreads();
-    const TileStep T{A.field, A.cost, A.field_out, A.cost_out, H.n, H.s, H.dx, H.dy, H.it, H.last, H.inherit};
-    iter_tile<L, TX, TY, false, true>(A, T, tx0, ty0, s_vec, s_cost, s_ref, &bar, wait_ns);
+    const TileStep T{A.field, A.cost, A.field_out, A.cost_out, H.n, H.s, H.dx, H.dy, H.it, H.last, H.inherit,
+                     A.stamp};
+    iter_tile<L, TX, TY, false, true>(A, T, tx0, ty0, s_vec, s_cost, s_stamp, s_ref, &bar, wait_ns);
     // no CTA leaves with its copy in flight
     if (threadIdx.x == 0 && !mbar_wait(&bar, 0, kDrainFactor * wait_ns)) {
         atomicAdd(&g_drain_timeouts, 1u);
@@ -1213,7 +1286,7 @@ __host__ __device__ constexpr bool lat_fits() {
 // the CTA calls it; it contains one __syncthreads.
 template <int L, int C, int TX, int TY, bool kCg>
 __device__ __forceinline__ void lat_tile(const Field& A, const TileStep& T, int tx0, int ty0, uint2* s_vec,
-                                         int* s_cost) {
+                                         int* s_cost, uint8_t* s_stamp) {
     constexpr int G = L * C;
     static_assert(G <= 16 && lat_fits<G, TX, TY>() && TX % 2 == 0, "one region slot per group");
     constexpr int kRegX = TX + 1, kRegY = TY + 1;
@@ -1227,6 +1300,8 @@ __device__ __forceinline__ void lat_tile(const Field& A, const TileStep& T, int 
     if (tx0 >= gw || ty0 >= gh) return;  // tile beyond this field's grid (whole CTA)
     const int rx0 = tx0 - (T.dx > 0 ? 1 : 0), ry0 = ty0 - (T.dy > 0 ? 1 : 0);
     const int n = T.n;
+    const bool stamps = T.stamp != nullptr, read_st = stamps && T.it >= 2;
+    const StampLimits lim = stamp_limits(T.it, 0);  // colour 0; colour 1 is one higher
 
     // colour-1 pixel of the tile (phase 2): state, reference record, draw
     const int gy2 = ty0 + grp / kTileHalfRow;
@@ -1260,6 +1335,7 @@ __device__ __forceinline__ void lat_tile(const Field& A, const TileStep& T, int 
             const bool has_a = ax >= 0 && ax < V.w, has_b = by >= 0 && by < V.h;
             const size_t ja = has_a ? si - T.dx : si, jb = has_b ? si - (size_t)(T.dy * gw) : si;
             int c, ca = kEmpty, cb = kEmpty;
+            int so = 0, sa = 0, sb = 0;  // change stamps: own, predecessors
             uint2 wc, wa = make_uint2(0u, 0u), wb = make_uint2(0u, 0u);
             if (T.inherit) {
                 c = inherited_state<kCg>(T, gx, gy, gw, wc);
@@ -1270,6 +1346,11 @@ __device__ __forceinline__ void lat_tile(const Field& A, const TileStep& T, int 
                 if (has_b) cb = ld_cost<kCg>(T.cin + jb);
                 wa = ld_vec<kCg>(T.fin + ja);
                 wb = ld_vec<kCg>(T.fin + jb);
+                if (read_st) {
+                    so = ld_stamp<kCg>(T.stamp + si);
+                    sa = ld_stamp<kCg>(T.stamp + ja);
+                    sb = ld_stamp<kCg>(T.stamp + jb);
+                }
             }
             Slice<L> a;
             load_slice<L>(V.ref, i, q, a);
@@ -1280,8 +1361,10 @@ __device__ __forceinline__ void lat_tile(const Field& A, const TileStep& T, int 
             const bool own_valid = c != kEmpty;
             Vec4 cr;
             const bool do_rs = T.it > 0 && own_valid && rs_from(o, cur, cr);
-            const bool do_a = ca != kEmpty && !(own_valid && same_vec(va, cur));
-            const bool do_b = cb != kEmpty && !(own_valid && same_vec(vb, cur)) && !(ca != kEmpty && same_vec(vb, va));
+            const bool do_a = ca != kEmpty && !(read_st && sa <= lim.h) && !(own_valid && same_vec(va, cur));
+            const bool do_b = cb != kEmpty && !(read_st && sb <= lim.v) && !(own_valid && same_vec(vb, cur)) &&
+                              !(ca != kEmpty && same_vec(vb, va));
+            const int c0 = c;
             const Vec4 cand[3] = {cr, va, vb};
             const bool valid[3] = {do_rs, do_a, do_b};
             int cc[3];
@@ -1300,9 +1383,15 @@ __device__ __forceinline__ void lat_tile(const Field& A, const TileStep& T, int 
             }
             if (g == 0) {
                 const uint2 wv = pack_vec(cur);
+                const bool changed = c != c0;  // an accepted candidate is strictly lower
+                const int st = changed ? 2 * T.it + 1 : so;
                 s_vec[ry * kRegX + rx] = wv;
                 s_cost[ry * kRegX + rx] = c;
-                if (gx >= tx0 && gx < tx0 + TX && gy >= ty0 && gy < ty0 + TY) st_state<kCg>(T, si, wv, c);
+                s_stamp[ry * kRegX + rx] = (uint8_t)st;
+                if (gx >= tx0 && gx < tx0 + TX && gy >= ty0 && gy < ty0 + TY) {
+                    st_state<kCg>(T, si, wv, c);
+                    if (stamps && (changed || T.it == 0)) st_stamp<kCg>(T.stamp + si, st);
+                }
             }
         }
     }
@@ -1314,22 +1403,26 @@ __device__ __forceinline__ void lat_tile(const Field& A, const TileStep& T, int 
         int c = c2;
         Vec4 cur = unpack_vec(w2);
         const int agx = gx2 - T.dx, bgy = gy2 - T.dy;  // predecessors (colour 0, in the region)
-        int ca = kEmpty, cb = kEmpty;
+        int ca = kEmpty, cb = kEmpty, sa = 0, sb = 0;
         uint2 wa = make_uint2(0u, 0u), wb = make_uint2(0u, 0u);
         if (agx >= 0 && agx < gw) {
             const int r = (gy2 - ry0) * kRegX + (agx - rx0);
             ca = s_cost[r];
             wa = s_vec[r];
+            sa = s_stamp[r];
         }
         if (bgy >= 0 && bgy < gh) {
             const int r = (bgy - ry0) * kRegX + (gx2 - rx0);
             cb = s_cost[r];
             wb = s_vec[r];
+            sb = s_stamp[r];
         }
         const Vec4 va = unpack_vec(wa), vb = unpack_vec(wb);
         const bool own_valid = c != kEmpty;
-        const bool do_a = ca != kEmpty && !(own_valid && same_vec(va, cur));
-        const bool do_b = cb != kEmpty && !(own_valid && same_vec(vb, cur)) && !(ca != kEmpty && same_vec(vb, va));
+        const int c0 = c;
+        const bool do_a = ca != kEmpty && !(read_st && sa <= lim.h + 1) && !(own_valid && same_vec(va, cur));
+        const bool do_b = cb != kEmpty && !(read_st && sb <= lim.v + 1) && !(own_valid && same_vec(vb, cur)) &&
+                          !(ca != kEmpty && same_vec(vb, va));
         Vec4 r0, r1 = cur;
         const bool do_r0 = own_valid && rs_from(o2, cur, r0);
         bool do_r1 = false;
@@ -1383,6 +1476,8 @@ __device__ __forceinline__ void lat_tile(const Field& A, const TileStep& T, int 
         }
         if (g == 0) {
             st_state<kCg>(T, (size_t)gy2 * gw + gx2, pack_vec(cur), c);
+            if (stamps && (c != c0 || T.it == 0))
+                st_stamp<kCg>(T.stamp + (size_t)gy2 * gw + gx2, c != c0 ? 2 * T.it + 2 : 0);
         }
     }
     if (!T.last) return;
@@ -1414,12 +1509,14 @@ __global__ void __launch_bounds__(lat_threads<L * C, TX, TY>()) k_iteration_lat(
                                                                                  IterStep H) {
     __shared__ uint2 s_vec[(TX + 1) * (TY + 1)];
     __shared__ int s_cost[(TX + 1) * (TY + 1)];
+    __shared__ uint8_t s_stamp[(TX + 1) * (TY + 1)];
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int3 blk = iter_block(H);
     const Field& A = F.f[iter_field(H, blk)];
-    const TileStep T{A.field, A.cost, A.field_out, A.cost_out, H.n, H.s, H.dx, H.dy, H.it, H.last, H.inherit};
-    lat_tile<L, C, TX, TY, false>(A, T, iter_tile_x(H, blk) * TX, blk.y * TY, s_vec, s_cost);
+    const TileStep T{A.field, A.cost, A.field_out, A.cost_out, H.n, H.s, H.dx, H.dy, H.it, H.last, H.inherit,
+                     A.stamp};
+    lat_tile<L, C, TX, TY, false>(A, T, iter_tile_x(H, blk) * TX, blk.y * TY, s_vec, s_cost, s_stamp);
 }
 
 // ---------------------------------------------------------------------------
@@ -1497,6 +1594,7 @@ __global__ void __launch_bounds__(fused_threads<L, C, TX, TY>(), fused_min_block
     k_iteration_fused(const __grid_constant__ Fields F, FusedStep H) {
     __shared__ uint2 s_vec[(TX + 1) * (TY + 1)];
     __shared__ int s_cost[(TX + 1) * (TY + 1)];
+    __shared__ uint8_t s_stamp[(TX + 1) * (TY + 1)];
     const unsigned long long wait_ns = g_wait_limit_ns ? g_wait_limit_ns : kDefaultWaitNs;
     const int withhold = g_withhold_barrier;
     const int per = H.tiles_x * H.tiles_y, total = per * H.nf;
@@ -1510,11 +1608,13 @@ __global__ void __launch_bounds__(fused_threads<L, C, TX, TY>(), fused_min_block
             const int r = t % per;
             const TileStep T{odd ? A.field_out : A.field, odd ? A.cost_out : A.cost, odd ? A.field : A.field_out,
                              odd ? A.cost : A.cost_out, H.n, H.s, dx, dy, it, it == H.iters - 1,
-                             it == 0 ? H.inherit : 0};
+                             it == 0 ? H.inherit : 0, A.stamp};
             if constexpr (C == 0)
-                iter_tile<L, TX, TY, true>(A, T, (r % H.tiles_x) * TX, (r / H.tiles_x) * TY, s_vec, s_cost);
+                iter_tile<L, TX, TY, true>(A, T, (r % H.tiles_x) * TX, (r / H.tiles_x) * TY, s_vec, s_cost,
+                                           s_stamp);
             else
-                lat_tile<L, C, TX, TY, true>(A, T, (r % H.tiles_x) * TX, (r / H.tiles_x) * TY, s_vec, s_cost);
+                lat_tile<L, C, TX, TY, true>(A, T, (r % H.tiles_x) * TX, (r / H.tiles_x) * TY, s_vec, s_cost,
+                                             s_stamp);
             __syncthreads();  // the region arrays are reused by the next tile
         }
         if (it + 1 == H.iters) break;
@@ -2027,9 +2127,11 @@ int coarse_gq(int w, int h, const sff_params& p) {
 
 // Scratch of one field: K-NN lists and the augmented coarsest-grid rows
 // (whole 16 KB tiles, so every bulk copy starts and ends on 16 bytes), then
-// a second state buffer (field + cost) for the double-buffered iterations.
+// a second state buffer (field + cost) for the double-buffered iterations,
+// the grid-barrier counters and the change stamps (one byte per pixel,
+// reused by every scale).
 struct FieldScratch {
-    size_t best8, tk, rec, rec_n, field, cost, sync, total;
+    size_t best8, tk, rec, rec_n, field, cost, sync, stamp, total;
 };
 FieldScratch field_scratch(int w, int h, const sff_params& p) {
     const int gq = coarse_gq(w, h, p);
@@ -2041,7 +2143,8 @@ FieldScratch field_scratch(int w, int h, const sff_params& p) {
     f.field = f.rec_n + align256((size_t)2 * gq * sizeof(int));
     f.cost = f.field + align256((size_t)w * h * 8);
     f.sync = f.cost + align256((size_t)w * h * 4);
-    f.total = f.sync + 256;
+    f.stamp = f.sync + 256;
+    f.total = f.stamp + align256((size_t)w * h);
     return f;
 }
 
@@ -2092,6 +2195,7 @@ int run_fields(const FieldSpec* spec, int nf, const sff_params& P, const sff_tun
         F.f[k].rec = reinterpret_cast<int4*>(ws + sc.rec);
         F.f[k].rec_n = reinterpret_cast<int*>(ws + sc.rec_n);
         F.f[k].sync = reinterpret_cast<unsigned*>(ws + sc.sync);
+        F.f[k].stamp = reinterpret_cast<uint8_t*>(ws + sc.stamp);
         F.f[k].gq = coarse_gq(fs.width, fs.height, P);
         F.f[k].mirror = fs.mirror;
         F.f[k].key = make_uint2((uint32_t)fs.seed, (uint32_t)(fs.seed >> 32));
