@@ -339,10 +339,15 @@ def make_batch_quads():
         return list(ex.map(_gen_batch_quad, jobs)), [j[3] for j in jobs]
 
 
+# Groups of the batch on concurrent streams (BatchMatcher.streams) tried by the bench
+BATCH_STREAMS = (1, 2, 4)
+
+
 def bench_batched(sff, torch, dev, quads, seeds, params, tuning, steps, warmup):
     """Matched px/s of the 32-quad batch: one CUDA graph of shared launches
-    (sff_run_batch) vs the plain per-quad form (one graph per quad, replayed
-    one after the other); outputs compared for identity."""
+    (sff_run_batch; the quads in 1, 2 or 4 groups on concurrent streams, the
+    fastest kept) vs the plain per-quad form (one graph per quad, replayed one
+    after the other); outputs compared for identity."""
     from paper_1710_10096_gb300 import tune
     sizes = [(im[0].shape[1], im[0].shape[0]) for im in quads]
     px = sum(w * h for w, h in sizes)
@@ -352,7 +357,11 @@ def bench_batched(sff, torch, dev, quads, seeds, params, tuning, steps, warmup):
     # the batch's own scale-0 variant and schedules (autotuned on the batch);
     # the plain per-quad form below keeps the tuning passed in
     batch_tuning = tune.autotune_batch(bm, seeds)
-    g_batch = bm.capture(seeds)
+    group_options = [ns for ns in BATCH_STREAMS if ns <= len(quads)]
+    g_by = {}
+    for ns in group_options:
+        bm.streams = ns
+        g_by[ns] = bm.capture(seeds)
     # plain: one matcher + graph per quad
     plain = []
     for k, im in enumerate(quads):
@@ -381,7 +390,11 @@ def bench_batched(sff, torch, dev, quads, seeds, params, tuning, steps, warmup):
         b.synchronize()
         return a.elapsed_time(b) / steps / 1e3
 
-    t_batch = timed(g_batch.replay)
+    t_by = {ns: timed(g.replay) for ns, g in g_by.items()}
+    best = min(t_by, key=t_by.get)
+    t_batch = t_by[best]
+    bm.streams = best
+    g_by[best].replay()  # the outputs compared below
     t_plain = timed(lambda: [g.replay() for _, g in plain])
     # per-kernel (and per-scale) breakdown of the batched graph: one replay of
     # a second capture with event spans around the launches
@@ -406,7 +419,8 @@ def bench_batched(sff, torch, dev, quads, seeds, params, tuning, steps, warmup):
                        "(planes scenes), scene seeds 100..131",
            "px_per_step": px, "value": px / t_batch, "unit": "px/s", "ms_per_step": 1e3 * t_batch,
            "plain_value": px / t_plain, "plain_ms_per_step": 1e3 * t_plain, "speedup_vs_plain": t_plain / t_batch,
-           "identical_to_plain": bool(same), "cuda_graph": True,
+           "identical_to_plain": bool(same), "cuda_graph": True, "streams": best,
+           "by_streams": {str(ns): {"value": px / t, "ms_per_step": 1e3 * t} for ns, t in sorted(t_by.items())},
            "tuning": {"scale0": list(batch_tuning.scale_variants()[0]), "pair_fields": batch_tuning.pair_fields,
                       "alternate_order": batch_tuning.alternate_order,
                       "coarse": "derived from the batch's grid sizes",
@@ -414,7 +428,7 @@ def bench_batched(sff, torch, dev, quads, seeds, params, tuning, steps, warmup):
                                          "alternate_order": tuning.alternate_order,
                                          "coarse": "derived from each quad's grid sizes"}},
            "kernels_ms": breakdown, "k_iteration_per_scale": per_scale}
-    del bm, plain, g_batch
+    del bm, plain, g_by
     torch.cuda.empty_cache()
     return out
 

@@ -687,9 +687,16 @@ def run_batch(descs, params: Params = None, tuning: Tuning = None, stream=None) 
 
 class BatchMatcher:
     """Buffers for a fixed list of quad sizes; run() matches all of them in
-    shared launches (sff_run_batch), capture() records that into a CUDA graph."""
+    shared launches (sff_run_batch), capture() records that into a CUDA graph.
 
-    def __init__(self, sizes, params: Params = None, device="cuda", tuning: Tuning = None):
+    streams > 1 splits the quads into that many groups (quad k in group
+    k % streams, so every group holds a mix of the sizes) and runs one
+    sff_run_batch per group, each on its own stream forked from the caller's
+    and joined back: the latency-bound phases of one group (the coarse scales,
+    the K-NN) then run beside the throughput-bound ones of another.  Every
+    quad's outputs are the same whatever the grouping."""
+
+    def __init__(self, sizes, params: Params = None, device="cuda", tuning: Tuning = None, streams: int = 1):
         import torch
         if not 1 <= len(sizes) <= MAX_BATCH:
             raise SffError(f"a batch holds 1..{MAX_BATCH} quads")
@@ -697,6 +704,18 @@ class BatchMatcher:
         self.tuning = tuning or default_tuning()
         self.device = torch.device(device)
         self.quads = [QuadBuffers(w, h, self.params, self.device) for (w, h) in sizes]
+        self.streams = streams
+        self._group_streams = []
+
+    @property
+    def streams(self) -> int:
+        return self._streams
+
+    @streams.setter
+    def streams(self, n: int) -> None:
+        if not 1 <= int(n) <= len(self.quads):
+            raise SffError(f"streams must be 1..{len(self.quads)}")
+        self._streams = int(n)
 
     def load(self, k: int, L0, R0, L1, R1) -> None:
         """Copy host (or device) images of quad k into its device input buffer."""
@@ -707,7 +726,20 @@ class BatchMatcher:
 
     def run(self, seeds, stream=None) -> None:
         descs = [q.desc(None, sd) for q, sd in zip(self.quads, seeds)]
-        run_batch(descs, self.params, self.tuning, stream)
+        if self._streams == 1:
+            run_batch(descs, self.params, self.tuning, stream)
+            return
+        import torch
+        main = stream if stream is not None else torch.cuda.current_stream(self.device)
+        while len(self._group_streams) < self._streams:
+            self._group_streams.append(torch.cuda.Stream(device=self.device))
+        groups = self._group_streams[:self._streams]
+        for gs in groups:
+            gs.wait_stream(main)
+        for g, gs in enumerate(groups):
+            run_batch(descs[g::self._streams], self.params, self.tuning, gs)
+        for gs in groups:
+            main.wait_stream(gs)
 
     def capture(self, seeds):
         """A CUDA graph replaying run(seeds) on the current input buffers."""

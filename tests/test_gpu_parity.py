@@ -531,6 +531,45 @@ def test_batch_of_uneven_quads_equals_each_alone(env):
             assert b.seeds_numpy().tobytes() == ref["seeds"].tobytes(), cfg
 
 
+def test_batch_in_stream_groups_equals_oracle(env):
+    # the batch split into groups on concurrent streams (BatchMatcher.streams),
+    # run directly and replayed from a CUDA graph: every quad's outputs equal
+    # the oracle's run on it alone
+    torch, sff, orc = env
+    specs = [("planes", 256, 80, 1, 11), ("planes", 96, 40, 2, 12), ("planes", 130, 70, 3, 13),
+             ("planes", 64, 48, 4, 14), ("shift", 160, 96, 5, 15)]
+    quads = []
+    for fam, w, h, sd, ms in specs:
+        q = (scenegen.make_shift_quad(w, h, sd, u=-3, v=2, d0=4, d1=6) if fam == "shift"
+             else scenegen.make_quad(fam, w, h, sd))
+        quads.append((q, ms))
+    refs = [orc.run_quad(*q.images(), seed=ms) for q, ms in quads]
+    bm = sff.BatchMatcher([(q.width, q.height) for q, _ in quads])
+    for k, (q, _) in enumerate(quads):
+        bm.load(k, *q.images())
+    seeds = [ms for _, ms in quads]
+    for ns in (2, 3, 5):
+        bm.streams = ns
+        for how in ("run", "graph"):
+            for b in bm.quads:
+                b.fwd.zero_()
+                b.seeds.zero_()
+            if how == "run":
+                bm.run(seeds)
+            else:
+                g = bm.capture(seeds)
+                for b in bm.quads:
+                    b.fwd.zero_()
+                    b.seeds.zero_()
+                g.replay()
+            torch.cuda.synchronize()
+            for (q, ms), b, ref in zip(quads, bm.quads, refs):
+                assert np.array_equal(b.fwd.cpu().numpy(), ref["fwd"]), (ns, how)
+                assert np.array_equal(b.inv.cpu().numpy(), ref["inv"]), (ns, how)
+                assert np.array_equal(b.keep.cpu().numpy(), ref["keep"]), (ns, how)
+                assert b.seeds_numpy().tobytes() == ref["seeds"].tobytes(), (ns, how)
+
+
 def test_mixed_32_quad_batch_equals_oracle(env):
     # the benchmark's 32-quad batch (8 each of 1242x375 and 1024x436 driving
     # scenes, 640x192 and 512x160 planes scenes, scene seeds 100..131) in
