@@ -266,6 +266,21 @@ __device__ __noinline__ void tc_append_slow(unsigned enter, int mine, int idx, i
     __syncwarp();
 }
 
+// v[j] for a warp-uniform j in 0..31: a tree of selects on the bits of j
+// (31 selects; a register array cannot be indexed at run time).
+__device__ __forceinline__ uint32_t select32(const uint32_t (&v)[32], int j) {
+    uint32_t a[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) a[k] = (j & 1) ? v[2 * k + 1] : v[2 * k];
+#pragma unroll
+    for (int w = 8; w >= 1; w >>= 1) {
+        const bool hi = (j & (32 / (2 * w))) != 0;
+#pragma unroll
+        for (int k = 0; k < w; ++k) a[k] = hi ? a[2 * k + 1] : a[2 * k];
+    }
+    return a[0];
+}
+
 // Bounded wait on an accumulator for a whole warp (lane 0 polls); false
 // (and the CTA's failure flag raised) on a timeout or when another warp
 // already failed.
@@ -529,9 +544,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_knn_tc(const __grid_constant_
             while (cols) {
                 const int j = __ffs(cols) - 1;
                 cols &= cols - 1;
-                int mine = (int)v[0];
-#pragma unroll
-                for (int k = 1; k < 32; ++k) mine = j == k ? (int)v[k] : mine;
+                const int mine = (int)select32(v, j);
                 const unsigned ent = __ballot_sync(0xffffffffu, (m >> j) & 1u);
                 const int c = mycnt[j];
                 if (c + __popc(ent) <= kTcCap) {
