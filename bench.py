@@ -222,8 +222,10 @@ def stage_rooflines(prof, steps, w, h, params, hbm_peak, bf16_peak, per_step_ms)
     - k_knn_tc: one pass of the coarsest grid's distance product, 2 fields x
       2 x gq^2 x 64 bf16 FLOP (the kernel makes two passes by design);
     - the consistency check (26 B per pixel, in k_cc_local) and the region
-      filter (k_cc_*, 10 B per pixel); the seeds (k_block_best, k_scan_chunks,
-      k_write_seeds): 16 B per pixel."""
+      filter (k_cc_*, 10 B per pixel; in the whole stage its last step, the
+      removal of small joinable regions, runs inside k_block_best, and its
+      bytes stay counted here); the seeds (k_block_best, k_write_seeds):
+      16 B per pixel."""
     S = params.num_scales
     px = w * h
     nq = (1 << (S - 1))
@@ -236,8 +238,7 @@ def stage_rooflines(prof, steps, w, h, params, hbm_peak, bf16_peak, per_step_ms)
             "k_knn_tc": ("tensor", 2.0 * 2.0 * gq * gq * 64)}
     groups = {"consistency + region filter (k_cc_*)": (("k_cc_local", "k_cc_border", "k_cc_stats", "k_cc_remove"),
                                                        36.0 * px),
-              "seeds (k_block_best, k_scan_chunks, k_write_seeds)": (("k_block_best", "k_scan_chunks",
-                                                                       "k_write_seeds"), 16.0 * px)}
+              "seeds (k_block_best, k_write_seeds)": (("k_block_best", "k_write_seeds"), 16.0 * px)}
     out, sol_ms = {}, 0.0
     for k, (bound, amount) in work.items():
         if k not in prof:

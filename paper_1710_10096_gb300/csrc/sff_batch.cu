@@ -16,11 +16,12 @@ namespace sff {
 // Per-quad scratch: the smoothed images of the four views (read by the
 // features of every scale), then the two fields' scratch, which the features
 // of the finer scales may still be reading from the first part; the filter
-// and the seeds, which run after both, reuse the start.
+// and, after it, the seeds, which run after both, reuse the start (the seeds'
+// scratch follows the filter's: the seed kernels read the filter's union-find
+// arrays).
 size_t quad_ws_bytes(int w, int h, const sff_params& p) {
     size_t b = 4 * features_ws_bytes(w, h, p) + 2 * field_ws_bytes(w, h, p);
-    b = std::max(b, filter_ws_bytes(w, h));
-    b = std::max(b, seeds_ws_bytes(w, h));
+    b = std::max(b, filter_ws_bytes(w, h) + seeds_ws_bytes(w, h));
     return b;
 }
 
@@ -182,13 +183,16 @@ extern "C" int sff_run_batch(const sff_quad* quads, int32_t n, const sff_params*
                           q.inv_cost, q.width, q.height, q.keep, q.cerr, nullptr, nullptr, nullptr};
         filter_carve(q.workspace, q.width, q.height, &fj[k].parent, &fj[k].size, &fj[k].joinable);
     }
-    status = run_filter(fj, n, P, st);
+    // the removal of small joinable regions is done by the seed kernels
+    status = run_filter(fj, n, P, st, false);
     if (status) return status;
     for (int k = 0; k < n; ++k) {
         const sff_quad& q = quads[k];
         sj[k] = SeedJob{reinterpret_cast<const uint2*>(q.fwd), q.fwd_cost, q.keep, q.cerr, q.width, q.height,
-                        nullptr, nullptr, q.seeds, q.capacity, q.count};
-        seeds_carve(q.workspace, q.width, q.height, &sj[k].best, &sj[k].chunk);
+                        nullptr, nullptr, q.seeds, q.capacity, q.count, nullptr, 0,
+                        fj[k].parent, fj[k].size, fj[k].joinable, P.region_min, q.keep};
+        seeds_carve(reinterpret_cast<char*>(q.workspace) + filter_ws_bytes(q.width, q.height), q.width, q.height,
+                    &sj[k].best, &sj[k].chunk);
     }
     return run_seeds(sj, n, st);
 }

@@ -260,7 +260,7 @@ void filter_carve(void* workspace, int w, int h, int** parent, int** size, int**
     *joinable = reinterpret_cast<int*>((char*)workspace + 2 * slab);
 }
 
-int run_filter(const FilterJob* jobs, int n, const sff_params& P, cudaStream_t st) {
+int run_filter(const FilterJob* jobs, int n, const sff_params& P, cudaStream_t st, bool remove) {
     if (n < 1 || n > kMaxQuads) return SFF_ERR_ARG;
     static FilterJobs J;  // host staging of the kernel parameter (copied at each launch)
     static std::mutex mu;
@@ -282,7 +282,7 @@ int run_filter(const FilterJob* jobs, int n, const sff_params& P, cudaStream_t s
     SFF_LAUNCH(k_cc_local, gt, 256, 0, st, J, P.tau_r, P.tau_c);
     if (pairs > 0) SFF_LAUNCH(k_cc_border, dim3((unsigned)((pairs + 127) / 128), 1, n), b2, 0, st, J, P.tau_r);
     SFF_LAUNCH(k_cc_stats, g2, b2, 0, st, J, P.tau_r);
-    SFF_LAUNCH(k_cc_remove, g2, b2, 0, st, J, P.region_min);
+    if (remove) SFF_LAUNCH(k_cc_remove, g2, b2, 0, st, J, P.region_min);
     return launch_status();
 }
 

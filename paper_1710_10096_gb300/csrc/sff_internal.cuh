@@ -229,9 +229,20 @@ struct SeedJob {
     int* count;
     const int16_t* sgm;  // disparity map of the fill (nullptr: joint seeds only)
     int tau_c;           // agreement of d0 with sgm for a disparity-only seed
+    // The region filter's last step done by the seed kernels (nullptr: keep is
+    // final): a kept pixel whose component (root parent[i]) is joinable and
+    // smaller than region_min is removed, in keep_rw (the same mask as keep),
+    // before its block is searched.
+    const int* parent;
+    const int* size;
+    const int* joinable;
+    int region_min;
+    uint8_t* keep_rw;
 };
 constexpr int kMaxQuads = SFF_TABLE_QUADS;
-int run_filter(const FilterJob* jobs, int n, const sff_params& P, cudaStream_t st);
+// remove = false: the filter leaves the removal of small joinable regions to
+// the seed kernels (SeedJob::parent ...), which then run on its results.
+int run_filter(const FilterJob* jobs, int n, const sff_params& P, cudaStream_t st, bool remove = true);
 int run_seeds(const SeedJob* jobs, int n, cudaStream_t st);
 void filter_carve(void* workspace, int w, int h, int** parent, int** size, int** joinable);
 void seeds_carve(void* workspace, int w, int h, int** best, int** chunk);

@@ -8,8 +8,10 @@
 // k_block_best:  one thread per block -> raster index i of its best kept
 //                pixel, -(i + 2) for a disparity-only seed, or -1; and the
 //                number of seeds of each chunk of 256 blocks.
-// k_scan_chunks: one CTA: exclusive scan of the chunk counts, total count.
-// k_write_seeds: rank inside the chunk by warp ballots + chunk offset.
+// k_write_seeds: rank inside the chunk by warp ballots + chunk offset (the
+//                sum of the earlier chunks' counts, which each CTA adds up
+//                itself: at most a few thousand values); the last chunk's
+//                CTA writes the total count.
 // Scratch (workspace): best[ceil(W/3) * ceil(H/3)] and one int32 per chunk.
 #include <mutex>
 
@@ -19,7 +21,6 @@ namespace sff {
 namespace {
 
 constexpr int kChunk = 256;        // 3x3 blocks per CTA of k_block_best / k_write_seeds
-constexpr int kScanThreads = 1024;
 
 // Scratch of sff_emit_seeds_noalloc, in a static device array so that the
 // call needs no allocation: one int32 per 3x3 block plus one per chunk of
@@ -56,6 +57,13 @@ __global__ void __launch_bounds__(kChunk) k_block_best(const __grid_constant__ S
             for (int x = bx; x < min(bx + 3, w); ++x) {
                 const int i = y * w + x;
                 if (!Q.keep[i]) continue;
+                if (Q.parent) {  // the region filter's removal (k_cc_remove's rule)
+                    const int root = Q.parent[i];
+                    if (Q.joinable[root] && Q.size[root] < Q.region_min) {
+                        Q.keep_rw[i] = 0;
+                        continue;
+                    }
+                }
                 const int e = Q.cerr[i], c = Q.fcost[i];
                 if (bi < 0 || e < be || (e == be && c < bc)) {  // raster order: ties keep the earlier pixel
                     bi = i;
@@ -84,73 +92,46 @@ __global__ void __launch_bounds__(kChunk) k_block_best(const __grid_constant__ S
     if (threadIdx.x == 0) Q.chunk[blockIdx.x] = n;
 }
 
-// One CTA per quad: exclusive scan of the chunk counts in place; the total
-// to *count.
-__global__ void __launch_bounds__(kScanThreads) k_scan_chunks(const __grid_constant__ SeedJobs J) {
-    __shared__ int warp_sums[kScanThreads / 32];
-    const SeedJob& Q = J.q[blockIdx.z];
-    const int nb = ((Q.w + 2) / 3) * ((Q.h + 2) / 3);
-    const int nchunks = (nb + kChunk - 1) / kChunk;
-    int* chunk = Q.chunk;
-    const int t = threadIdx.x;
-    const int per = (nchunks + kScanThreads - 1) / kScanThreads;
-    const int c0 = min(nchunks, t * per), c1 = min(nchunks, c0 + per);
-    int mine = 0;
-    for (int c = c0; c < c1; ++c) mine += chunk[c];
-    int v = mine;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int u = __shfl_up_sync(0xffffffffu, v, o);
-        if ((t & 31) >= o) v += u;
-    }
-    if ((t & 31) == 31) warp_sums[t >> 5] = v;
-    __syncthreads();
-    if (t < 32) {
-        int s = warp_sums[t];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int u = __shfl_up_sync(0xffffffffu, s, o);
-            if (t >= o) s += u;
-        }
-        warp_sums[t] = s;  // inclusive over warps
-    }
-    __syncthreads();
-    int pos = v - mine + ((t >> 5) ? warp_sums[(t >> 5) - 1] : 0);
-    for (int c = c0; c < c1; ++c) {
-        const int k = chunk[c];
-        chunk[c] = pos;
-        pos += k;
-    }
-    if (t == kScanThreads - 1) {
-        *Q.count = pos;
-        if (pos > Q.capacity) atomicOr(&g_seed_status, kStatusCapacity);
-    }
-}
-
 // Same grid as k_block_best: rank of each found seed inside its CTA (warp
 // ballots + warp offsets) plus the chunk offset gives its output slot.
 __global__ void __launch_bounds__(kChunk) k_write_seeds(const __grid_constant__ SeedJobs J) {
     __shared__ int warp_base[kChunk / 32];
+    __shared__ int warp_prior[kChunk / 32];
+    __shared__ int chunk_base;
     const SeedJob& Q = J.q[blockIdx.z];
     const int w = Q.w, nb = ((Q.w + 2) / 3) * ((Q.h + 2) / 3);
-    if ((int)blockIdx.x * kChunk >= nb) return;  // whole CTA beyond this quad's blocks
+    const int nchunks = (nb + kChunk - 1) / kChunk;
+    if ((int)blockIdx.x >= nchunks) return;  // whole CTA beyond this quad's blocks
+    // seeds of the chunks before this one
+    int prior = 0;
+    for (int c = threadIdx.x; c < (int)blockIdx.x; c += kChunk) prior += Q.chunk[c];
+    prior = __reduce_add_sync(0xffffffffu, prior);
     const int b = blockIdx.x * kChunk + threadIdx.x;
     const int i = b < nb ? Q.best[b] : -1;
     const unsigned ballot = __ballot_sync(0xffffffffu, i != -1);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) warp_base[wid] = __popc(ballot);
+    if (lane == 0) {
+        warp_base[wid] = __popc(ballot);
+        warp_prior[wid] = prior;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        int acc = 0;
+        int acc = 0, base = 0;
         for (int k = 0; k < kChunk / 32; ++k) {
             const int n = warp_base[k];
             warp_base[k] = acc;
             acc += n;
+            base += warp_prior[k];
+        }
+        chunk_base = base;
+        if ((int)blockIdx.x == nchunks - 1) {  // the total
+            *Q.count = base + acc;
+            if (base + acc > Q.capacity) atomicOr(&g_seed_status, kStatusCapacity);
         }
     }
     __syncthreads();
     if (i == -1) return;
-    const int pos = Q.chunk[blockIdx.x] + warp_base[wid] + __popc(ballot & ((1u << lane) - 1u));
+    const int pos = chunk_base + warp_base[wid] + __popc(ballot & ((1u << lane) - 1u));
     if (pos >= Q.capacity) return;
     const bool geo = i < -1;
     const int pi = geo ? -(i + 2) : i;
@@ -206,7 +187,6 @@ int run_seeds(const SeedJob* jobs, int n, cudaStream_t st) {
         mchunks = mchunks > (nb + kChunk - 1) / kChunk ? mchunks : (nb + kChunk - 1) / kChunk;
     }
     SFF_LAUNCH(k_block_best, dim3(mchunks, 1, n), kChunk, 0, st, J);
-    SFF_LAUNCH(k_scan_chunks, dim3(1, 1, n), kScanThreads, 0, st, J);
     SFF_LAUNCH(k_write_seeds, dim3(mchunks, 1, n), kChunk, 0, st, J);
     return launch_status();
 }
