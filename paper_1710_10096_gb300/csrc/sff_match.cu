@@ -638,26 +638,23 @@ __global__ void k_init_select(const __grid_constant__ Fields F, int n, int knn) 
     const int px = (qi % gw) * n, py = (qi / gw) * n;
     RefFeat r;
     load_ref(V.ref, pix(V.w, px, py), r);
-    // the query's temporal top-8 (every lane the same, reads broadcast)
-    int bd[8], bi[8];
+    // the query's temporal top-8 (every lane the same, reads broadcast), read
+    // one entry at a time
     const int2* src = A.best8 + (size_t)qi * 8;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const int2 e = src[k];
-        bd[k] = e.x;
-        bi[k] = e.y;
-    }
     int ds, sx;
     warp_row_nearest(r, A.rec, A.rec_n, n, gw, qi / gw, px, V.sigma, lane, ds, sx);
     int best_c = 0x7fffffff;
     Vec4 best = {0, 0, 0, 0};
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        if (k >= knn || bd[k] == 0x7fffffff || bi[k] < 0 || bi[k] >= A.gq) break;
-        const int tx = (bi[k] % gw) * n, ty = (bi[k] / gw) * n;
+        if (k >= knn) break;
+        const int2 e = src[k];
+        const int bdk = e.x, bik = e.y;
+        if (bdk == 0x7fffffff || bik < 0 || bik >= A.gq) break;
+        const int tx = (bik % gw) * n, ty = (bik / gw) * n;
         int dxc, cx;
-        warp_row_nearest(r, A.rec + (size_t)A.gq * 3, A.rec_n + A.gq, n, gw, bi[k] / gw, tx, V.sigma, lane, dxc, cx);
-        const int c = bd[k] + ds + dxc;
+        warp_row_nearest(r, A.rec + (size_t)A.gq * 3, A.rec_n + A.gq, n, gw, bik / gw, tx, V.sigma, lane, dxc, cx);
+        const int c = bdk + ds + dxc;
         if (c < best_c) {
             best_c = c;
             best.u = tx - px;
