@@ -83,7 +83,7 @@ __device__ void unite(int* parent, int a, int b) {
     }
 }
 
-constexpr int kTile = 32;  // union-find tile: 32 x 32 pixels, 256 threads
+constexpr int kTile = 32;  // union-find tile: 32 x 32 pixels
 
 // Root of k with path halving: every visited node is re-pointed to its
 // grandparent.  Parents only ever point to smaller indices of the same
@@ -125,7 +125,7 @@ __device__ void unite_local(int* lp, int a, int b) {
 // smaller root: every kept pixel's parent becomes that minimum.  Also clears
 // size and joinable for the tile's pixels.  The tile's keep and cerr are
 // computed first, by the consistency check of each of its pixels.
-constexpr int kLocalThreads = 256;
+constexpr int kLocalThreads = 512;
 constexpr int kPerThread = kTile * kTile / kLocalThreads;
 
 __global__ void __launch_bounds__(kLocalThreads) k_cc_local(const __grid_constant__ FilterJobs J, int tau_r,
@@ -279,7 +279,7 @@ int run_filter(const FilterJob* jobs, int n, const sff_params& P, cudaStream_t s
         const long long p = (long long)((jobs[k].w - 1) / kTile) * jobs[k].h + (long long)((jobs[k].h - 1) / kTile) * jobs[k].w;
         pairs = pairs > p ? pairs : p;
     }
-    SFF_LAUNCH(k_cc_local, gt, 256, 0, st, J, P.tau_r, P.tau_c);
+    SFF_LAUNCH(k_cc_local, gt, kLocalThreads, 0, st, J, P.tau_r, P.tau_c);
     if (pairs > 0) SFF_LAUNCH(k_cc_border, dim3((unsigned)((pairs + 127) / 128), 1, n), b2, 0, st, J, P.tau_r);
     SFF_LAUNCH(k_cc_stats, g2, b2, 0, st, J, P.tau_r);
     if (remove) SFF_LAUNCH(k_cc_remove, g2, b2, 0, st, J, P.region_min);
