@@ -53,23 +53,40 @@ __global__ void __launch_bounds__(kChunk) k_block_best(const __grid_constant__ S
     if (b < nb) {
         const int bx = (b % bw) * 3, by = (b / bw) * 3;
         int be = 0, bc = 0;
-        for (int y = by; y < min(by + 3, h); ++y)
-            for (int x = bx; x < min(bx + 3, w); ++x) {
-                const int i = y * w + x;
-                if (!Q.keep[i]) continue;
-                if (Q.parent) {  // the region filter's removal (k_cc_remove's rule)
-                    const int root = Q.parent[i];
-                    if (Q.joinable[root] && Q.size[root] < Q.region_min) {
-                        Q.keep_rw[i] = 0;
-                        continue;
-                    }
+        // the block's up to 9 pixels in raster order, each step's loads issued
+        // for all of them together: kept?, then (with the removal) their
+        // components, then their consistency errors and costs
+        int pi[9];
+        bool kk[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const int y = by + k / 3, x = bx + k % 3;
+            pi[k] = y * w + x;
+            kk[k] = y < h && x < w && Q.keep[pi[k]];
+        }
+        if (Q.parent) {  // the region filter's removal (k_cc_remove's rule)
+            int root[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) root[k] = kk[k] ? Q.parent[pi[k]] : 0;
+#pragma unroll
+            for (int k = 0; k < 9; ++k)
+                if (kk[k] && Q.joinable[root[k]] && Q.size[root[k]] < Q.region_min) {
+                    Q.keep_rw[pi[k]] = 0;
+                    kk[k] = false;
                 }
-                const int e = Q.cerr[i], c = Q.fcost[i];
-                if (bi < 0 || e < be || (e == be && c < bc)) {  // raster order: ties keep the earlier pixel
-                    bi = i;
-                    be = e;
-                    bc = c;
-                }
+        }
+        int ek[9], ck[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            ek[k] = kk[k] ? Q.cerr[pi[k]] : 0;
+            ck[k] = kk[k] ? Q.fcost[pi[k]] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+            if (kk[k] && (bi < 0 || ek[k] < be || (ek[k] == be && ck[k] < bc))) {  // ties keep the earlier pixel
+                bi = pi[k];
+                be = ek[k];
+                bc = ck[k];
             }
         if (bi < 0 && Q.sgm) {
             int ge = 0, gc = 0;
